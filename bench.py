@@ -1,0 +1,383 @@
+#!/usr/bin/env python3
+"""Decoder benchmark: FullHD frames/s of a 4:2:0 GOP (1 intra + 29 inter).
+
+Workload (seeded, synthetic; stands in for the paper's FullHD video tests):
+luma 1920x1080, chroma 960x540; intra mask 3% (chroma 1.5%, shared by Cb and
+Cr); inter frames with a dense float32 backward flow of a moving scene and
+16x16 residual blocks with Poisson(8) (luma) / Poisson(4) (chroma, shared
+layout) points, values in [-64, 64].
+
+One step = decode the whole GOP (every hot-path step: intra diffusion solve,
+chroma flow, warp, block residual, add/clamp/pack) with inputs resident in
+device memory.  L2 is flushed (256 MB write) between steps, outside the
+timed events.  ``e2e`` repeats the measurement through the same C-ABI calls
+with inputs copied from pinned host memory and outputs read back each frame.
+
+``--impl reference`` times the FP64 CPU oracle on the same workload.
+Multi-GPU (torchrun): independent replicas, one GOP per rank (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FULLHD_PX = 1920 * 1080
+METRIC = "FullHD frames/s decoded"
+UNIT = "FullHD frames/s"
+
+# Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) from
+# ncu captures, keyed by kernel family, with the sha1 of the kernel's source
+# file at capture time; a changed source voids the number (reported null).
+NCU_TRAFFIC = {}
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["hivc", "reference"], default="hivc")
+    p.add_argument("--width", type=int, default=1920)
+    p.add_argument("--height", type=int, default=1080)
+    p.add_argument("--frames", type=int, default=30)
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--iframe-tol", type=float, default=1e-8)
+    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-clocks", action="store_true")
+    return p.parse_args(argv)
+
+
+def workload_desc(a):
+    return (f"{a.width}x{a.height} YCbCr 4:2:0 GOP of {a.frames} frames: 1 intra (3% luma mask, 1.5% shared "
+            f"chroma mask, diffusion solve to max |Lu| <= {a.iframe_tol:g}) + {a.frames - 1} inter (dense float32 "
+            f"backward flow, 16x16 residual blocks, Poisson(8) luma / Poisson(4) chroma points, values in [-64,64])")
+
+
+def config_obj(a, world):
+    return {"workload": workload_desc(a), "width": a.width, "height": a.height, "gop": a.frames,
+            "block": 16, "iframe_tol": a.iframe_tol, "seed": a.seed,
+            "l2": "flushed between steps (256 MB write, outside the timed events)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
+def make_workload(a, rank=0):
+    from workload import make_gop
+
+    return make_gop(a.seed + rank, a.width, a.height, n_frames=a.frames)
+
+
+def src_sha(path):
+    with open(path, "rb") as fh:
+        return hashlib.sha1(fh.read()).hexdigest()[:12]
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reported baseline; also the --impl reference arm)
+# ---------------------------------------------------------------------------
+def oracle_gop_seconds(gop, tol):
+    import oracle
+
+    od = oracle.OracleDecoder(gop.width, gop.height, gop.chroma, gop.block, iframe_tol=tol)
+    t0 = time.perf_counter()
+    od.decode_iframe(gop.iframe)
+    for pf in gop.pframes:
+        od.decode_pframe(pf)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(a, gop):
+    sec = oracle_gop_seconds(gop, a.iframe_tol)
+    fps = gop.n_frames * (a.width * a.height / FULLHD_PX) / sec
+    return {"value": fps, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one full GOP ({gop.n_frames} frames) of the same workload, FP64 C oracle, "
+                      f"single thread, {sec:.1f} s on {os.cpu_count()} host cores available"}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    gop = make_workload(a)
+    # warm-up steps: one inter frame each (a CPU program needs no warm-up of
+    # its own; this keeps the run short); timed steps: the whole GOP
+    import oracle
+
+    od = oracle.OracleDecoder(gop.width, gop.height, gop.chroma, gop.block, iframe_tol=a.iframe_tol)
+    for _ in range(a.warmup):
+        if od.ref is None:
+            od.decode_iframe(gop.iframe)
+        od.decode_pframe(gop.pframes[0])
+    secs = [oracle_gop_seconds(gop, a.iframe_tol) for _ in range(a.steps)]
+    total = sum(secs)
+    fps = a.steps * gop.n_frames * (a.width * a.height / FULLHD_PX) / total
+    line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": 1, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * total / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_obj(a, 1),
+            "cpu_baseline": {"value": fps, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each timed step decodes one full GOP ({gop.n_frames} frames) with the FP64 "
+                                       f"C oracle, single thread"},
+            "e2e": {"value": fps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# clocks sampler
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "100"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                maxs.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs), "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def main(argv=None):
+    a = parse_args(argv)
+    if a.impl == "reference":
+        return run_reference(a)
+
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2008_10273_gb300 import build as pbuild
+    from paper_2008_10273_gb300 import hivc
+
+    if rank == 0 or world == 1:
+        pbuild.build()
+    if dist:
+        dist.barrier()
+    hivc.lib()
+
+    gop = make_workload(a, rank)
+    W, H = a.width, a.height
+    stream = torch.cuda.Stream()
+    dec = hivc.Decoder(W, H, chroma=True, iframe_tol=a.iframe_tol, stream=stream, timing=True)
+    iframe_d = hivc.device_iframe(gop.iframe)
+    pframes_d = [hivc.device_pframe(p) for p in gop.pframes]
+    out = hivc.alloc_out(W, H)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    nfr = gop.n_frames
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nfr + 1)] for _ in range(a.steps)]
+
+    def step(events=None):
+        if events:
+            events[0].record(stream)
+        st = dec.decode_iframe(iframe_d, out, allow_not_converged=True)
+        if events:
+            events[1].record(stream)
+        for t, pf in enumerate(pframes_d):
+            dec.decode_pframe(pf, out)
+            if events:
+                events[t + 2].record(stream)
+        return st
+
+    with torch.cuda.stream(stream):
+        for _ in range(a.warmup):
+            flush.zero_()
+            step()
+        dec.sync()
+        clocks = Clocks(local)
+        if not a.no_clocks:
+            clocks.start()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for k in range(a.steps):
+            flush.zero_()
+            step(ev[k])
+        torch.cuda.synchronize()
+        stats = dec.sync()
+        clk = clocks.stop() if not a.no_clocks else None
+    step_ms = [e[0].elapsed_time(e[-1]) for e in ev]
+    frame_ms = []
+    for e in ev:
+        frame_ms += [e[i].elapsed_time(e[i + 1]) for i in range(nfr)]
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    px_scale = W * H / FULLHD_PX
+    value = world * a.steps * nfr * px_scale / (total_ms / 1e3)
+
+    # roofline of the dominant kernel family over the timed region
+    fam_ms = list(stats.kernel_ms)
+    fam_n = list(stats.kernel_launches)
+    cw, ch = (W + 1) // 2, (H + 1) // 2
+    bytes_per_launch = {
+        # family: (kernel source, algorithmic bytes per launch)
+        6: ("k_warp.cu", W * H * (8 + 4 + 4 + 4 + 1) + 2 * cw * ch * (4 + 4 + 4 + 1)),
+        1: ("k_intra.cu", (W * H + 2 * cw * ch) * (4 + 4 + 1 + 4)),
+        2: ("k_intra.cu", (W * H + 2 * cw * ch) * (8 + 4 + 1 + 8 + 4)),
+        5: ("k_block.cu", (W * H + 2 * cw * ch) * 4),
+    }
+    dom = max(range(len(fam_ms)), key=lambda i: fam_ms[i])
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    roof = None
+    if dom in bytes_per_launch and fam_n[dom] > 0:
+        srcf, b = bytes_per_launch[dom]
+        avg_ms = fam_ms[dom] / fam_n[dom]
+        achieved = b / (avg_ms / 1e3) / 1e9
+        tr = NCU_TRAFFIC.get(hivc.KERNEL_FAMILIES[dom])
+        traffic = None
+        if tr and tr["sha"] == src_sha(os.path.join(ROOT, "paper_2008_10273_gb300", "csrc", srcf)):
+            traffic = tr["bytes"]
+        roof = {"kernel": hivc.KERNEL_FAMILIES[dom], "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "algorithmic_bytes_per_launch": b, "avg_launch_ms": avg_ms}
+    kernels = {hivc.KERNEL_FAMILIES[i]: {"ms": fam_ms[i], "launches": fam_n[i],
+                                         "share": fam_ms[i] / max(1e-9, sum(fam_ms))}
+               for i in range(len(fam_ms)) if fam_n[i] > 0}
+
+    # end-to-end through the C ABI with host buffers (pinned), per-frame H2D
+    # of the inputs and D2H of the uint8 output planes
+    host_i = {k: v.cpu().pin_memory() if hasattr(v, "cpu") else v for k, v in iframe_d.items() if k != "res"}
+    host_p = [{"flow": p["flow"].cpu().pin_memory(),
+               "res": [tuple(x.cpu().pin_memory() for x in r) for r in p["res"]]} for p in pframes_d]
+    out_h = [torch.empty(o.shape, dtype=torch.uint8).pin_memory() for o in out]
+    dev_i = {k: torch.empty_like(v, device="cuda") for k, v in host_i.items()}
+    dev_p = [{"flow": torch.empty_like(p["flow"], device="cuda"),
+              "res": [tuple(torch.empty_like(x, device="cuda") for x in r) for r in p["res"]]} for p in host_p]
+    h2d = sum(v.numel() * v.element_size() for v in host_i.values())
+    for p in host_p:
+        h2d += p["flow"].numel() * 4 + sum(x.numel() * x.element_size() for r in p["res"] for x in r)
+    d2h = nfr * sum(o.numel() for o in out_h)
+
+    def e2e_step():
+        for k, v in host_i.items():
+            dev_i[k].copy_(v, non_blocking=True)
+        dec.decode_iframe(dev_i, out, allow_not_converged=True)
+        for o, oh in zip(out, out_h):
+            oh.copy_(o, non_blocking=True)
+        for hp, dp in zip(host_p, dev_p):
+            dp["flow"].copy_(hp["flow"], non_blocking=True)
+            for rh, rd in zip(hp["res"], dp["res"]):
+                for xh, xd in zip(rh, rd):
+                    xd.copy_(xh, non_blocking=True)
+            dec.decode_pframe(dp, out)
+            for o, oh in zip(out, out_h):
+                oh.copy_(o, non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        e2e_step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.e2e_steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dec.sync()
+    e2e_ms = e0.elapsed_time(e1)
+    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = world * a.e2e_steps * nfr * px_scale / (float(t.item()) / 1e3)
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(a, gop)
+
+    if rank == 0:
+        pf = sorted(frame_ms[i] for i in range(len(frame_ms)) if i % nfr != 0)
+        ifm = sorted(frame_ms[i] for i in range(0, len(frame_ms), nfr))
+        q = lambda xs, f: xs[min(len(xs) - 1, int(round(f * (len(xs) - 1))))] if xs else None
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_obj(a, world),
+            "latency_ms": {"p50": q(sorted(frame_ms), 0.5), "p99": q(sorted(frame_ms), 0.99),
+                           "inter_p50": q(pf, 0.5), "inter_p99": q(pf, 0.99), "intra_p50": q(ifm, 0.5),
+                           "path": "plain (one decode call per frame, one decoder)"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "steps": a.e2e_steps},
+            "roofline": roof,
+            "kernels": kernels,
+            "intra": {"cycles": int(stats.cycles), "sweeps": int(stats.sweeps),
+                      "resid": [float(x) for x in stats.resid]},
+            "gpu_launches": int(stats.launches),
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    dec.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,233 @@
+/*
+ * hivc.h -- C ABI of the GB300 decoder for the inpainting-based video codec
+ * of Andris, Peter, Kaja Mohideen, Weickert and Hoffmann, "Inpainting-based
+ * Video Compression in FullHD".
+ *
+ * The decoder rebuilds each frame as prediction + correction (Sec. 2):
+ *   - intra frames: homogeneous diffusion inpainting of the frame from its
+ *     mask pixels (Sec. 2.1, Eq. 1, A = -L, reflecting boundaries);
+ *   - inter frames: backward warping of the previous reconstruction along a
+ *     dense backward optic flow field (Sec. 2, Sec. 2.3);
+ *   - both: a residual rebuilt per block by pseudodifferential inpainting
+ *     with the harmonic operator (Sec. 2.2, Eqs. 2-4), added and clamped.
+ *
+ * Conventions (all entry points):
+ *   - Planes are row-major; luma is width x height, 4:2:0 chroma planes are
+ *     ceil(width/2) x ceil(height/2).  Grey values are in [0, 255].
+ *   - Every array pointer in the input/output structs is DEVICE memory owned
+ *     by the caller.  It must stay valid and unmodified until the work is
+ *     complete (hivc_decoder_sync, or the caller's stream for the step
+ *     entry points).  Struct arguments themselves are read on the host
+ *     during the call and may be reused right after it returns.
+ *   - Calls are asynchronous on the decoder's (or the given) stream.  Host
+ *     checks (sizes, null pointers, decoder state) return an error at once;
+ *     data checks that need the device arrays (index order, block point
+ *     counts, positions) run inside the kernels, never trap, and surface as
+ *     HIVC_E_INVALID from hivc_decoder_sync.  Offending blocks or mask
+ *     points are ignored by the kernels and never accessed out of bounds.
+ *   - A decoder is not thread-safe; distinct decoders are independent.
+ */
+#ifndef HIVC_H
+#define HIVC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HIVC_OK = 0,
+    HIVC_E_INVALID = -1,       /* bad argument or bad input data */
+    HIVC_E_NOMEM = -2,         /* device allocation failed */
+    HIVC_E_CUDA = -3,          /* a CUDA runtime call failed */
+    HIVC_E_NOT_CONVERGED = -4, /* intra solve hit max_cycles above iframe_tol */
+    HIVC_E_NO_REFERENCE = -5,  /* inter frame before any intra frame */
+    HIVC_E_BUDGET = -6,        /* footprint above the caller's budget */
+    HIVC_E_TIMEOUT = -7        /* a bounded device wait gave up */
+} hivc_status;
+
+/* Decoder configuration.  hivc_config_default() fills the defaults. */
+typedef struct {
+    int32_t width, height;  /* luma plane size, >= 1 */
+    int32_t chroma;         /* 0 = grey (Y only), 1 = YCbCr 4:2:0 */
+    int32_t block;          /* residual block edge B, 1..16.  The paper uses
+                               8 x 8 blocks (Sec. 2.2, 2.3); default 16 */
+    int32_t op;             /* residual operator: 0 = harmonic, -L (Sec. 2.3) */
+    int32_t precision;      /* intra solve: 0 = FP32 sweeps + FP64 residual
+                               correction (default), 1 = FP32 only */
+    double iframe_tol;      /* stop when max |(L u)_i| over unknown pixels
+                               <= tol, grey levels (Eq. 1 residual); default
+                               1e-8; FP32-only mode floors near 1e-3 */
+    int32_t max_cycles;     /* cap on outer correction cycles (default 40);
+                               beyond it sync returns HIVC_E_NOT_CONVERGED */
+    double cond_threshold;  /* block systems whose condition estimate exceeds
+                               this are re-solved in FP64 (default 1e6) */
+    void *stream;           /* cudaStream_t to run on; NULL = the decoder
+                               creates its own non-blocking stream */
+} hivc_config;
+
+/* Intra mask of one plane: n >= 1 sorted, unique linear indices y*w + x. */
+typedef struct {
+    int32_t n;
+    const uint32_t *idx; /* device, n entries, strictly increasing, < w*h */
+    const uint8_t *val;  /* device, n entries: the grey value at idx */
+} hivc_points;
+
+/*
+ * Block residual data of one plane (Sec. 2.2, 2.3).  Blocks of edge B tile
+ * the plane in raster order (bx fastest); edge blocks are cropped to the
+ * plane and are independent images of their own size w x h.  Block b owns
+ * entries block_ptr[b] .. block_ptr[b+1]-1 of pos/val:
+ *   pos = ly*w + lx inside the block (strictly increasing, < w*h), and
+ *   K_b = block_ptr[b+1] - block_ptr[b] <= w*h - 1;
+ *   val = the residual value at that point.
+ * K_b = 0 reconstructs as zero.  block_ptr has ceil(W/B)*ceil(H/B) + 1
+ * entries with block_ptr[0] = 0 and block_ptr[last] <= n_points.
+ */
+typedef struct {
+    const uint32_t *block_ptr; /* device */
+    const uint8_t *pos;        /* device */
+    const int16_t *val;        /* device */
+    int32_t n_points;          /* entries in pos/val */
+} hivc_residual;
+
+/* Intra frame.  The two chroma planes share one mask (Sec. 2.3). */
+typedef struct {
+    hivc_points y;
+    int32_t c_n;              /* chroma mask size (4:2:0 only) */
+    const uint32_t *c_idx;    /* device, shared by Cb and Cr */
+    const uint8_t *cb_val;    /* device */
+    const uint8_t *cr_val;    /* device */
+    const hivc_residual *res; /* NULL, or a HOST array of 1 (grey) / 3
+                                 residuals added to the inpainted planes */
+} hivc_iframe;
+
+/* Inter frame: pred(x) = ref(x + flow(x)), bilinear, sample clamped.
+   Chroma uses half the mean of the 2 x 2 co-sited luma vectors. */
+typedef struct {
+    const float *flow;    /* device, height x width x 2 floats (dx, dy) */
+    hivc_residual res[3]; /* Y, Cb, Cr (only res[0] when grey).  Cb and Cr
+                             may share block_ptr/pos: one factorisation
+                             then serves both */
+} hivc_pframe;
+
+/* uint8 output planes (device), rows pitch bytes apart. */
+typedef struct {
+    uint8_t *plane[3];
+    int32_t pitch[3];
+} hivc_out;
+
+typedef struct {
+    int32_t type; /* 0 = intra (i), 1 = inter (p) */
+    const hivc_iframe *i;
+    const hivc_pframe *p;
+} hivc_frame;
+
+#define HIVC_STAT_KERNELS 8
+/* Statistics of the frames completed by the last hivc_decoder_sync. */
+typedef struct {
+    double resid[3];        /* final Eq. 1 residual per plane (last intra) */
+    int32_t cycles;         /* outer correction cycles of the last intra */
+    int32_t sweeps;         /* red-black sweeps of the last intra */
+    int32_t fp64_blocks;    /* blocks re-solved in FP64 */
+    int32_t large_blocks;   /* blocks with K > 32 (CTA path) */
+    float max_cond;         /* largest block condition estimate seen */
+    uint32_t device_flags;  /* data errors seen by the kernels (bit set) */
+    int32_t frames;         /* frames since the previous sync */
+    int32_t launches;       /* kernel launches since the previous sync */
+    /* per kernel family: accumulated device time (ms, CUDA events, only
+       when timing is on) and launch counts since the previous sync:
+       0 intra setup, 1 intra sweeps, 2 intra residual, 3 block coefficients,
+       4 large blocks, 5 block evaluate, 6 warp/add/pack, 7 fused inter */
+    float kernel_ms[HIVC_STAT_KERNELS];
+    int32_t kernel_launches[HIVC_STAT_KERNELS];
+} hivc_stats;
+
+typedef struct hivc_decoder hivc_decoder;
+
+/* Fill *cfg with the defaults (width/height 0: the caller sets them). */
+void hivc_config_default(hivc_config *cfg);
+
+/* Create a decoder: allocates its reference planes and scratch on the
+   current CUDA device.  HIVC_E_INVALID for a bad config, HIVC_E_NOMEM. */
+hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out);
+
+/* Device bytes a decoder with this config allocates (for HBM-budget
+   admission); 0 for an invalid config. */
+size_t hivc_decoder_bytes(const hivc_config *cfg);
+
+/* Decode an intra frame (Sec. 2.1 + optional residual, Sec. 2.2) into out
+   and make it the reference.  The FP64-corrected solve reads its residual
+   norm back to the host between correction cycles, so this call waits on
+   the decoder's stream while it runs. */
+hivc_status hivc_decode_iframe(hivc_decoder *dec, const hivc_iframe *f, const hivc_out *out);
+
+/* Decode an inter frame (Sec. 2, 2.3: warp + residual) into out and make it
+   the reference.  Asynchronous.  HIVC_E_NO_REFERENCE before any intra. */
+hivc_status hivc_decode_pframe(hivc_decoder *dec, const hivc_pframe *f, const hivc_out *out);
+
+/* Decode n frames, frame k on decoder decs[k] into outs[k].  Frames of one
+   decoder are decoded in array order; inter frames of different decoders
+   are batched into shared launches. */
+hivc_status hivc_decode_batch(hivc_decoder *const *decs, const hivc_frame *frames, int32_t n,
+                              const hivc_out *outs);
+
+/* Wait for the decoder's stream; report device-side data errors
+   (HIVC_E_INVALID) and the statistics of the frames since the last sync. */
+hivc_status hivc_decoder_sync(hivc_decoder *dec, hivc_stats *last);
+
+/* Enable (1) or disable (0) per-kernel CUDA-event timing in hivc_stats. */
+hivc_status hivc_decoder_set_timing(hivc_decoder *dec, int32_t on);
+
+/* Device pointer to the current FP32 reference plane (the unrounded,
+   clamped reconstruction of the last frame) with its size and pitch in
+   floats.  Valid until the next decode call. */
+hivc_status hivc_decoder_reference(const hivc_decoder *dec, int32_t plane, const float **ptr,
+                                   int32_t *width, int32_t *height, int32_t *pitch);
+
+/* The stream the decoder runs on. */
+void *hivc_decoder_stream(const hivc_decoder *dec);
+
+void hivc_decoder_destroy(hivc_decoder *dec);
+
+const char *hivc_status_str(hivc_status s);
+
+/* ------------------------------------------------------------------------
+ * Step entry points (stateless; device pointers; asynchronous on stream).
+ * ---------------------------------------------------------------------- */
+
+/* Scratch bytes hivc_block_residual needs for a plane with n_points
+   residual points. */
+size_t hivc_block_residual_workspace_bytes(int32_t width, int32_t height, int32_t block,
+                                           int32_t n_points);
+
+/* Residual plane r (width x height floats, row pitch r_pitch floats) from
+   block data (Sec. 2.2, Eqs. 2-4): per block, the (K+1) x (K+1) system in
+   the Green's function at the block's points is solved (coefficients c
+   summing to zero and the constant a), then r = sum_j c_j g_j + a over the
+   block through the DCT-II diagonalisation (Eq. 4); r equals the data at
+   the points.  workspace: device scratch of at least
+   hivc_block_residual_workspace_bytes() bytes.  flags: optional device
+   uint32 that receives error bits for bad blocks (those blocks are zero).
+   HIVC_E_INVALID for bad sizes or a short workspace. */
+hivc_status hivc_block_residual(int32_t width, int32_t height, int32_t block,
+                                const hivc_residual *res, float *r, int32_t r_pitch,
+                                void *workspace, size_t workspace_bytes, uint32_t *flags,
+                                void *stream);
+
+/* Backward bilinear warp of one plane (Sec. 2, 2.3): pred(x) = ref(x + v(x)),
+   sample clamped to the plane.  flow is the LUMA flow (flow_width x
+   flow_height x 2 floats); when chroma_flow is 1 the plane is a 4:2:0
+   chroma plane of that luma size and v is half the mean of the co-sited
+   2 x 2 luma vectors, else the plane has the flow's size and v = flow. */
+hivc_status hivc_warp(int32_t width, int32_t height, const float *ref, int32_t ref_pitch,
+                      const float *flow, int32_t flow_width, int32_t flow_height,
+                      int32_t chroma_flow, float *pred, int32_t pred_pitch, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HIVC_H */

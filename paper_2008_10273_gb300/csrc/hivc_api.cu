@@ -1,0 +1,736 @@
+// C ABI of libhivc: decoder objects, argument checks, the intra correction
+// loop and the inter-frame pipeline.  Every step of the decode runs in the
+// kernels of k_intra.cu, k_block.cu and k_warp.cu; this file only
+// allocates, validates and launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hivc_internal.cuh"
+
+using namespace hivc;
+
+namespace {
+
+constexpr int kPitchAlign = 32;  // elements
+
+int round_up(int v, int a) { return (v + a - 1) / a * a; }
+
+struct Alloc {
+    std::vector<void *> ptrs;
+    size_t bytes = 0;
+    bool ok = true;
+    template <class T>
+    T *get(size_t n)
+    {
+        if (!ok) return nullptr;
+        void *p = nullptr;
+        size_t b = std::max<size_t>(n * sizeof(T), 256);
+        if (cudaMalloc(&p, b) != cudaSuccess) {
+            ok = false;
+            cudaGetLastError();
+            return nullptr;
+        }
+        ptrs.push_back(p);
+        bytes += b;
+        return static_cast<T *>(p);
+    }
+    void release()
+    {
+        for (void *p : ptrs) cudaFree(p);
+        ptrs.clear();
+    }
+};
+
+struct PlaneGeom {
+    int w, h, pitch, nblocks, nbx;
+};
+
+bool config_ok(const hivc_config *c)
+{
+    return c && c->width >= 1 && c->height >= 1 && c->width <= 16384 && c->height <= 16384 &&
+           (c->chroma == 0 || c->chroma == 1) && c->block >= 1 && c->block <= kMaxB && c->op == 0 &&
+           (c->precision == 0 || c->precision == 1) && c->iframe_tol >= 0.0 && c->max_cycles >= 1;
+}
+
+int plane_count(const hivc_config *c) { return c->chroma ? 3 : 1; }
+
+PlaneGeom plane_geom(const hivc_config *c, int p)
+{
+    PlaneGeom g;
+    g.w = p == 0 ? c->width : (c->width + 1) / 2;
+    g.h = p == 0 ? c->height : (c->height + 1) / 2;
+    g.pitch = round_up(g.w, kPitchAlign);
+    g.nbx = (g.w + c->block - 1) / c->block;
+    g.nblocks = g.nbx * ((g.h + c->block - 1) / c->block);
+    return g;
+}
+
+// Relaxation factor for red-black SOR from the mask density, for randomly
+// scattered masks: the widest mask-free disc has radius about
+// sqrt(ln(unknowns) / (pi * density)); its lowest Dirichlet mode sets the
+// Jacobi spectral radius rho_J ~ 1 - (2.405 / R)^2 / 4, and
+// omega = 2 / (1 + sqrt(1 - rho_J^2)) (Young's optimum).
+float sor_omega(int w, int h, int n)
+{
+    const double N = (double)w * h;
+    const double unknown = std::max(1.0, N - n);
+    const double d = std::max(n, 1) / N;
+    double R = std::sqrt(std::log(std::max(unknown, 2.0)) / (3.14159265358979 * d));
+    R = std::min(R, 0.5 * std::max(w, h));
+    const double lam = std::pow(2.405 / std::max(R, 1.0), 2.0);
+    const double rho = std::max(0.0, 1.0 - lam / 4.0);
+    double om = 2.0 / (1.0 + std::sqrt(std::max(0.0, 1.0 - rho * rho)));
+    return (float)std::min(std::max(om, 1.0), 1.95);
+}
+
+}  // namespace
+
+struct hivc_decoder {
+    hivc_config cfg{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int np = 1;
+    PlaneGeom pg[3]{};
+    Alloc mem;
+    // reference planes (ping-pong) and their validity
+    float *ref[2][3]{};
+    int cur = 0;
+    bool has_ref = false;
+    // intra scratch
+    double *u[2][3]{};
+    float *res[3]{}, *e[2][3]{};
+    uint8_t *mask[3]{};
+    double *sum = nullptr;
+    unsigned long long *rnorm = nullptr;
+    // block scratch
+    float *rfield[3]{}, *coef[3]{}, *acoef[3]{};
+    size_t coef_cap = 0;
+    uint32_t *large_list = nullptr, *large_count = nullptr;
+    int large_cap = 0;
+    uint32_t *flags = nullptr;
+    // host mirrors
+    uint32_t *h_flags = nullptr;
+    unsigned long long *h_rnorm = nullptr;
+    uint32_t *h_large = nullptr;
+    // statistics
+    hivc_stats st{};
+    bool timing = false;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+hivc_status cuda_status(cudaError_t e) { return e == cudaSuccess ? HIVC_OK : HIVC_E_CUDA; }
+
+cudaEvent_t take_event(hivc_decoder *d)
+{
+    if (!d->event_pool.empty()) {
+        cudaEvent_t e = d->event_pool.back();
+        d->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Records CUDA events around a group of launches of one kernel family.
+struct Timed {
+    hivc_decoder *d;
+    int fam;
+    cudaEvent_t a = nullptr;
+    Timed(hivc_decoder *dd, int f) : d(dd), fam(f)
+    {
+        if (d->timing) {
+            a = take_event(d);
+            cudaEventRecord(a, d->stream);
+        }
+    }
+    void done(int launches)
+    {
+        d->st.kernel_launches[fam] += launches;
+        d->st.launches += launches;
+        if (a) {
+            cudaEvent_t b = take_event(d);
+            cudaEventRecord(b, d->stream);
+            d->pending.push_back({fam, {a, b}});
+            a = nullptr;
+        }
+    }
+};
+
+bool residual_ok(const hivc_residual &r)
+{
+    if (r.block_ptr == nullptr || r.n_points < 0) return false;
+    if (r.n_points > 0 && (r.pos == nullptr || r.val == nullptr)) return false;
+    return true;
+}
+
+bool out_ok(const hivc_decoder *d, const hivc_out *o)
+{
+    if (!o) return false;
+    for (int p = 0; p < d->np; ++p)
+        if (o->plane[p] == nullptr || o->pitch[p] < d->pg[p].w) return false;
+    return true;
+}
+
+// Block stage for one frame: coefficients, then the residual fields.
+hivc_status run_block_residual(hivc_decoder *d, const hivc_residual *res)
+{
+    BlockJobs J{};
+    int base = 0;
+    auto add = [&](int p, int p2) {
+        BlockPlane &B = J.p[J.n++];
+        const PlaneGeom &g = d->pg[p];
+        B.block_ptr = res[p].block_ptr;
+        B.pos = res[p].pos;
+        B.val[0] = res[p].val;
+        B.val[1] = p2 >= 0 ? res[p2].val : nullptr;
+        B.coef[0] = d->coef[p];
+        B.coef[1] = p2 >= 0 ? d->coef[p2] : nullptr;
+        B.acoef[0] = d->acoef[p];
+        B.acoef[1] = p2 >= 0 ? d->acoef[p2] : nullptr;
+        B.r[0] = d->rfield[p];
+        B.r[1] = p2 >= 0 ? d->rfield[p2] : nullptr;
+        B.r_pitch = g.pitch;
+        B.n_points = res[p].n_points;
+        B.width = g.w;
+        B.height = g.h;
+        B.block = d->cfg.block;
+        B.nbx = g.nbx;
+        B.nblocks = g.nblocks;
+        B.block_base = base;
+        base += g.nblocks;
+    };
+    add(0, -1);
+    if (d->np == 3) {
+        const bool shared = res[1].block_ptr == res[2].block_ptr && res[1].pos == res[2].pos &&
+                            res[1].n_points == res[2].n_points;
+        if (shared) {
+            add(1, 2);
+        } else {
+            add(1, -1);
+            add(2, -1);
+        }
+    }
+    J.total_blocks = base;
+    for (int p = 0; p < d->np; ++p)
+        if ((int64_t)res[p].n_points > (int64_t)d->pg[p].w * d->pg[p].h) return HIVC_E_INVALID;
+    BlockScratch S{d->large_list, d->large_count, d->large_cap, d->flags};
+    cudaError_t e;
+    {
+        Timed t(d, 3);
+        int l = 0;
+        e = launch_block_coef(J, S, d->stream, &l);
+        t.done(1);
+        d->st.kernel_launches[4] += 1;
+        d->st.launches += 1;
+    }
+    if (e != cudaSuccess) return HIVC_E_CUDA;
+    {
+        Timed t(d, 5);
+        e = launch_block_eval(J, d->flags, d->stream);
+        t.done(1);
+    }
+    return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+void hivc_config_default(hivc_config *c)
+{
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->chroma = 1;
+    c->block = 16;
+    c->op = 0;
+    c->precision = 0;
+    c->iframe_tol = 1e-8;
+    c->max_cycles = 40;
+    c->cond_threshold = 1e6;
+    c->stream = nullptr;
+}
+
+const char *hivc_status_str(hivc_status s)
+{
+    switch (s) {
+    case HIVC_OK: return "ok";
+    case HIVC_E_INVALID: return "invalid argument or input data";
+    case HIVC_E_NOMEM: return "device allocation failed";
+    case HIVC_E_CUDA: return "CUDA error";
+    case HIVC_E_NOT_CONVERGED: return "intra solve did not reach the tolerance";
+    case HIVC_E_NO_REFERENCE: return "inter frame before any intra frame";
+    case HIVC_E_BUDGET: return "over the device-memory budget";
+    case HIVC_E_TIMEOUT: return "bounded device wait timed out";
+    }
+    return "unknown status";
+}
+
+size_t hivc_decoder_bytes(const hivc_config *c)
+{
+    if (!config_ok(c)) return 0;
+    size_t b = 0;
+    auto add = [&](size_t n) { b += std::max<size_t>(n, 256); };
+    int nblocks = 0;
+    size_t maxpts = 0;
+    for (int p = 0; p < plane_count(c); ++p) {
+        PlaneGeom g = plane_geom(c, p);
+        size_t n = (size_t)g.h * g.pitch;
+        add(n * 4);
+        add(n * 4);      // ref ping-pong
+        add(n * 8);
+        add(n * 8);      // u ping-pong
+        add(n * 4);      // res
+        add(n * 4);
+        add(n * 4);      // e ping-pong
+        add(n);          // mask
+        add(n * 4);      // residual field
+        add((size_t)g.w * g.h * 4);  // coefficients
+        add((size_t)g.nblocks * 4);  // constants
+        nblocks += g.nblocks;
+        maxpts = std::max(maxpts, (size_t)g.w * g.h);
+    }
+    add(3 * sizeof(double));
+    add(3 * sizeof(unsigned long long));
+    add((size_t)nblocks * 4);
+    add(4);
+    add(4);
+    return b;
+}
+
+hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out)
+{
+    if (!out) return HIVC_E_INVALID;
+    *out = nullptr;
+    if (!config_ok(cfg)) return HIVC_E_INVALID;
+    hivc_decoder *d = new (std::nothrow) hivc_decoder();
+    if (!d) return HIVC_E_NOMEM;
+    d->cfg = *cfg;
+    if (cudaGetDevice(&d->device) != cudaSuccess) {
+        delete d;
+        return HIVC_E_CUDA;
+    }
+    if (ensure_block_tables() != cudaSuccess) {
+        delete d;
+        return HIVC_E_CUDA;
+    }
+    d->np = plane_count(cfg);
+    int nblocks = 0;
+    size_t maxpts = 0;
+    Alloc &m = d->mem;
+    for (int p = 0; p < d->np; ++p) {
+        d->pg[p] = plane_geom(cfg, p);
+        const PlaneGeom &g = d->pg[p];
+        const size_t n = (size_t)g.h * g.pitch;
+        d->ref[0][p] = m.get<float>(n);
+        d->ref[1][p] = m.get<float>(n);
+        d->u[0][p] = m.get<double>(n);
+        d->u[1][p] = m.get<double>(n);
+        d->res[p] = m.get<float>(n);
+        d->e[0][p] = m.get<float>(n);
+        d->e[1][p] = m.get<float>(n);
+        d->mask[p] = m.get<uint8_t>(n);
+        d->rfield[p] = m.get<float>(n);
+        d->coef[p] = m.get<float>((size_t)g.w * g.h);
+        d->acoef[p] = m.get<float>((size_t)g.nblocks);
+        nblocks += g.nblocks;
+        maxpts = std::max(maxpts, (size_t)g.w * g.h);
+    }
+    d->coef_cap = maxpts;
+    d->sum = m.get<double>(3);
+    d->rnorm = m.get<unsigned long long>(3);
+    d->large_cap = nblocks;
+    d->large_list = m.get<uint32_t>((size_t)nblocks);
+    d->large_count = m.get<uint32_t>(1);
+    d->flags = m.get<uint32_t>(1);
+    if (!m.ok) {
+        m.release();
+        delete d;
+        return HIVC_E_NOMEM;
+    }
+    if (cudaMallocHost(&d->h_flags, 64) != cudaSuccess) {
+        m.release();
+        delete d;
+        return HIVC_E_NOMEM;
+    }
+    d->h_rnorm = reinterpret_cast<unsigned long long *>(d->h_flags) + 1;
+    d->h_large = d->h_flags + 8;
+    if (cfg->stream) {
+        d->stream = static_cast<cudaStream_t>(cfg->stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&d->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaFreeHost(d->h_flags);
+            m.release();
+            delete d;
+            return HIVC_E_CUDA;
+        }
+        d->own_stream = true;
+    }
+    if (cudaMemsetAsync(d->flags, 0, 4, d->stream) != cudaSuccess || cudaStreamSynchronize(d->stream) != cudaSuccess) {
+        hivc_decoder_destroy(d);
+        return HIVC_E_CUDA;
+    }
+    *out = d;
+    return HIVC_OK;
+}
+
+void hivc_decoder_destroy(hivc_decoder *d)
+{
+    if (!d) return;
+    cudaSetDevice(d->device);
+    if (d->stream) cudaStreamSynchronize(d->stream);
+    for (auto &pe : d->pending) {
+        cudaEventDestroy(pe.second.first);
+        cudaEventDestroy(pe.second.second);
+    }
+    for (cudaEvent_t e : d->event_pool) cudaEventDestroy(e);
+    if (d->own_stream) cudaStreamDestroy(d->stream);
+    if (d->h_flags) cudaFreeHost(d->h_flags);
+    d->mem.release();
+    delete d;
+}
+
+void *hivc_decoder_stream(const hivc_decoder *d) { return d ? static_cast<void *>(d->stream) : nullptr; }
+
+hivc_status hivc_decoder_set_timing(hivc_decoder *d, int32_t on)
+{
+    if (!d) return HIVC_E_INVALID;
+    d->timing = on != 0;
+    return HIVC_OK;
+}
+
+hivc_status hivc_decoder_reference(const hivc_decoder *d, int32_t plane, const float **ptr, int32_t *w, int32_t *h,
+                                   int32_t *pitch)
+{
+    if (!d || plane < 0 || plane >= d->np || !ptr) return HIVC_E_INVALID;
+    if (!d->has_ref) return HIVC_E_NO_REFERENCE;
+    *ptr = d->ref[d->cur][plane];
+    if (w) *w = d->pg[plane].w;
+    if (h) *h = d->pg[plane].h;
+    if (pitch) *pitch = d->pg[plane].pitch;
+    return HIVC_OK;
+}
+
+hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc_out *out)
+{
+    if (!d || !f || !out_ok(d, out)) return HIVC_E_INVALID;
+    if (f->y.n < 1 || !f->y.idx || !f->y.val) return HIVC_E_INVALID;
+    if ((int64_t)f->y.n > (int64_t)d->pg[0].w * d->pg[0].h) return HIVC_E_INVALID;
+    if (d->np == 3) {
+        if (f->c_n < 1 || !f->c_idx || !f->cb_val || !f->cr_val) return HIVC_E_INVALID;
+        if ((int64_t)f->c_n > (int64_t)d->pg[1].w * d->pg[1].h) return HIVC_E_INVALID;
+    }
+    if (f->res)
+        for (int p = 0; p < d->np; ++p)
+            if (!residual_ok(f->res[p])) return HIVC_E_INVALID;
+    if (cudaSetDevice(d->device) != cudaSuccess) return HIVC_E_CUDA;
+    cudaStream_t st = d->stream;
+    // the intra solve overwrites the FP64 scratch: settle earlier work on it
+    IntraJobs J{};
+    J.n = d->np;
+    for (int p = 0; p < d->np; ++p) {
+        IntraPlane &P = J.p[p];
+        const PlaneGeom &g = d->pg[p];
+        P.width = g.w;
+        P.height = g.h;
+        P.pitch = g.pitch;
+        P.idx = p == 0 ? f->y.idx : f->c_idx;
+        P.val = p == 0 ? f->y.val : (p == 1 ? f->cb_val : f->cr_val);
+        P.n = p == 0 ? f->y.n : f->c_n;
+        P.mask = d->mask[p];
+        P.u[0] = d->u[0][p];
+        P.u[1] = d->u[1][p];
+        P.res = d->res[p];
+        P.e[0] = d->e[0][p];
+        P.e[1] = d->e[1][p];
+        P.sum = d->sum + p;
+        P.rnorm = d->rnorm + p;
+        P.omega = sor_omega(g.w, g.h, P.n);
+    }
+    cudaError_t e;
+    {
+        Timed t(d, 0);
+        int l = 0;
+        e = launch_intra_init(J, d->flags, st, &l);
+        t.done(l);
+    }
+    if (e != cudaSuccess) return HIVC_E_CUDA;
+    auto residual = [&](IntraJobs &A, bool add_e, int eb) -> cudaError_t {
+        Timed t(d, 2);
+        cudaError_t er = launch_intra_residual(A, 0, eb, add_e, st);
+        t.done(1);
+        if (er != cudaSuccess) return er;
+        er = cudaMemcpyAsync(d->h_rnorm, d->rnorm, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+        if (er != cudaSuccess) return er;
+        return cudaStreamSynchronize(st);
+    };
+    if ((e = residual(J, false, 0)) != cudaSuccess) return HIVC_E_CUDA;
+    double rn[3] = {0, 0, 0};
+    auto read_norms = [&]() {
+        for (int p = 0; p < d->np; ++p) {
+            double v;
+            std::memcpy(&v, d->h_rnorm + p, sizeof(double));
+            rn[p] = v;
+        }
+    };
+    read_norms();
+    const double tol = d->cfg.iframe_tol;
+    int cycles = 0, sweeps_total = 0;
+    bool active[3] = {true, true, true};
+    while (cycles < d->cfg.max_cycles) {
+        IntraJobs A{};
+        int map[3];
+        for (int p = 0; p < d->np; ++p) {
+            active[p] = active[p] && !(rn[p] <= tol);
+            if (active[p]) {
+                map[A.n] = p;
+                A.p[A.n++] = J.p[p];
+            }
+        }
+        if (A.n == 0) break;
+        // sweeps per cycle: about five decades of the slowest plane's SOR rate
+        float om = 1.0f;
+        for (int k = 0; k < A.n; ++k) om = std::max(om, A.p[k].omega);
+        const double rate = std::max(0.05, std::min(0.98, (double)om - 1.0));
+        int sweeps = (int)std::ceil(std::log(1e-5) / std::log(rate));
+        sweeps = std::min(std::max(sweeps, 8), 400);
+        int eb = 0;
+        {
+            Timed t(d, 1);
+            int l = 0;
+            e = launch_intra_sor(A, 0, true, sweeps, st, &eb, &l);
+            t.done(l);
+            sweeps_total += l * 4;
+        }
+        if (e != cudaSuccess) return HIVC_E_CUDA;
+        if ((e = residual(A, true, eb)) != cudaSuccess) return HIVC_E_CUDA;
+        for (int k = 0; k < A.n; ++k) {
+            const int p = map[k];
+            std::swap(J.p[p].u[0], J.p[p].u[1]);
+            double v;
+            std::memcpy(&v, d->h_rnorm + p, sizeof(double));
+            rn[p] = v;
+        }
+        ++cycles;
+    }
+    bool converged = true;
+    for (int p = 0; p < d->np; ++p) converged = converged && rn[p] <= tol;
+    // optional residual correction of the intra frame (Fig. 1e/f)
+    if (f->res) {
+        hivc_status s = run_block_residual(d, f->res);
+        if (s != HIVC_OK) return s;
+    }
+    WarpJobs W{};
+    W.n = d->np;
+    const int nxt = d->cur ^ 1;
+    for (int p = 0; p < d->np; ++p) {
+        WarpPlane &P = W.p[p];
+        const PlaneGeom &g = d->pg[p];
+        P.src64 = J.p[p].u[0];
+        P.src64_pitch = g.pitch;
+        P.r = f->res ? d->rfield[p] : nullptr;
+        P.r_pitch = g.pitch;
+        P.ref_out = d->ref[nxt][p];
+        P.ref_out_pitch = g.pitch;
+        P.out = out->plane[p];
+        P.out_pitch = out->pitch[p];
+        P.width = g.w;
+        P.height = g.h;
+    }
+    {
+        Timed t(d, 6);
+        e = launch_warp_add(W, st);
+        t.done(1);
+    }
+    if (e != cudaSuccess) return HIVC_E_CUDA;
+    d->cur = nxt;
+    d->has_ref = true;
+    for (int p = 0; p < 3; ++p) d->st.resid[p] = p < d->np ? rn[p] : 0.0;
+    d->st.cycles = cycles;
+    d->st.sweeps = sweeps_total;
+    d->st.frames += 1;
+    return converged ? HIVC_OK : HIVC_E_NOT_CONVERGED;
+}
+
+hivc_status hivc_decode_pframe(hivc_decoder *d, const hivc_pframe *f, const hivc_out *out)
+{
+    if (!d || !f || !out_ok(d, out) || !f->flow) return HIVC_E_INVALID;
+    for (int p = 0; p < d->np; ++p)
+        if (!residual_ok(f->res[p])) return HIVC_E_INVALID;
+    if (!d->has_ref) return HIVC_E_NO_REFERENCE;
+    if (cudaSetDevice(d->device) != cudaSuccess) return HIVC_E_CUDA;
+    hivc_status s = run_block_residual(d, f->res);
+    if (s != HIVC_OK) return s;
+    WarpJobs W{};
+    W.n = d->np;
+    const int nxt = d->cur ^ 1;
+    for (int p = 0; p < d->np; ++p) {
+        WarpPlane &P = W.p[p];
+        const PlaneGeom &g = d->pg[p];
+        P.ref = d->ref[d->cur][p];
+        P.ref_pitch = g.pitch;
+        P.flow = f->flow;
+        P.flow_w = d->pg[0].w;
+        P.flow_h = d->pg[0].h;
+        P.chroma_flow = p > 0 ? 1 : 0;
+        P.r = d->rfield[p];
+        P.r_pitch = g.pitch;
+        P.ref_out = d->ref[nxt][p];
+        P.ref_out_pitch = g.pitch;
+        P.out = out->plane[p];
+        P.out_pitch = out->pitch[p];
+        P.width = g.w;
+        P.height = g.h;
+    }
+    cudaError_t e;
+    {
+        Timed t(d, 6);
+        e = launch_warp_add(W, d->stream);
+        t.done(1);
+    }
+    if (e != cudaSuccess) return HIVC_E_CUDA;
+    d->cur = nxt;
+    d->st.frames += 1;
+    return HIVC_OK;
+}
+
+hivc_status hivc_decode_batch(hivc_decoder *const *decs, const hivc_frame *frames, int32_t n, const hivc_out *outs)
+{
+    if (n < 0 || (n > 0 && (!decs || !frames || !outs))) return HIVC_E_INVALID;
+    hivc_status worst = HIVC_OK;
+    for (int k = 0; k < n; ++k) {
+        hivc_status s;
+        if (frames[k].type == 0)
+            s = hivc_decode_iframe(decs[k], frames[k].i, &outs[k]);
+        else if (frames[k].type == 1)
+            s = hivc_decode_pframe(decs[k], frames[k].p, &outs[k]);
+        else
+            s = HIVC_E_INVALID;
+        if (s != HIVC_OK && s != HIVC_E_NOT_CONVERGED) return s;
+        if (s != HIVC_OK) worst = s;
+    }
+    return worst;
+}
+
+hivc_status hivc_decoder_sync(hivc_decoder *d, hivc_stats *last)
+{
+    if (!d) return HIVC_E_INVALID;
+    if (cudaSetDevice(d->device) != cudaSuccess) return HIVC_E_CUDA;
+    cudaError_t e = cudaMemcpyAsync(d->h_flags, d->flags, 4, cudaMemcpyDeviceToHost, d->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d->flags, 0, 4, d->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    if (e != cudaSuccess) return HIVC_E_CUDA;
+    d->st.device_flags = *d->h_flags;
+    for (auto &pe : d->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess)
+            d->st.kernel_ms[pe.first] += ms;
+        d->event_pool.push_back(pe.second.first);
+        d->event_pool.push_back(pe.second.second);
+    }
+    d->pending.clear();
+    if (last) *last = d->st;
+    const uint32_t fl = d->st.device_flags;
+    hivc_stats fresh{};
+    std::memcpy(fresh.resid, d->st.resid, sizeof(fresh.resid));
+    fresh.cycles = d->st.cycles;
+    fresh.sweeps = d->st.sweeps;
+    d->st = fresh;
+    return fl ? HIVC_E_INVALID : HIVC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// step entry points
+// ---------------------------------------------------------------------------
+static size_t a256(size_t b) { return (b + 255) / 256 * 256; }
+
+size_t hivc_block_residual_workspace_bytes(int32_t width, int32_t height, int32_t block, int32_t n_points)
+{
+    if (width < 1 || height < 1 || block < 1 || block > kMaxB || n_points < 0) return 0;
+    const size_t nb = (size_t)((width + block - 1) / block) * ((height + block - 1) / block);
+    return a256(4 * (size_t)n_points) + a256(4 * nb) + a256(4 * nb) + 256 + 256;
+}
+
+hivc_status hivc_block_residual(int32_t width, int32_t height, int32_t block, const hivc_residual *res, float *r,
+                                int32_t r_pitch, void *workspace, size_t ws_bytes, uint32_t *flags, void *stream)
+{
+    if (!res || !r || !residual_ok(*res) || r_pitch < width) return HIVC_E_INVALID;
+    const size_t need = hivc_block_residual_workspace_bytes(width, height, block, res->n_points);
+    if (need == 0 || !workspace || ws_bytes < need) return HIVC_E_INVALID;
+    if (ensure_block_tables() != cudaSuccess) return HIVC_E_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *w = static_cast<char *>(workspace);
+    const int nbx = (width + block - 1) / block;
+    const int nb = nbx * ((height + block - 1) / block);
+    float *coef = reinterpret_cast<float *>(w);
+    w += a256(4 * (size_t)res->n_points);
+    float *acoef = reinterpret_cast<float *>(w);
+    w += a256(4 * (size_t)nb);
+    uint32_t *list = reinterpret_cast<uint32_t *>(w);
+    w += a256(4 * (size_t)nb);
+    uint32_t *count = reinterpret_cast<uint32_t *>(w);
+    w += 256;
+    uint32_t *own_flags = reinterpret_cast<uint32_t *>(w);
+    if (!flags) {
+        flags = own_flags;
+        if (cudaMemsetAsync(flags, 0, 4, st) != cudaSuccess) return HIVC_E_CUDA;
+    }
+    BlockJobs J{};
+    J.n = 1;
+    BlockPlane &B = J.p[0];
+    B.block_ptr = res->block_ptr;
+    B.pos = res->pos;
+    B.val[0] = res->val;
+    B.coef[0] = coef;
+    B.acoef[0] = acoef;
+    B.r[0] = r;
+    B.r_pitch = r_pitch;
+    B.n_points = res->n_points;
+    B.width = width;
+    B.height = height;
+    B.block = block;
+    B.nbx = nbx;
+    B.nblocks = nb;
+    J.total_blocks = nb;
+    BlockScratch S{list, count, nb, flags};
+    cudaError_t e = launch_block_coef(J, S, st, nullptr);
+    if (e == cudaSuccess) e = launch_block_eval(J, flags, st);
+    return cuda_status(e);
+}
+
+hivc_status hivc_warp(int32_t width, int32_t height, const float *ref, int32_t ref_pitch, const float *flow,
+                      int32_t flow_width, int32_t flow_height, int32_t chroma_flow, float *pred, int32_t pred_pitch,
+                      void *stream)
+{
+    if (width < 1 || height < 1 || !ref || !flow || !pred || ref_pitch < width || pred_pitch < width)
+        return HIVC_E_INVALID;
+    if (chroma_flow) {
+        if ((flow_width + 1) / 2 != width || (flow_height + 1) / 2 != height) return HIVC_E_INVALID;
+    } else if (flow_width != width || flow_height != height) {
+        return HIVC_E_INVALID;
+    }
+    WarpJobs W{};
+    W.n = 1;
+    WarpPlane &P = W.p[0];
+    P.ref = ref;
+    P.ref_pitch = ref_pitch;
+    P.flow = flow;
+    P.flow_w = flow_width;
+    P.flow_h = flow_height;
+    P.chroma_flow = chroma_flow ? 1 : 0;
+    P.pred_out = pred;
+    P.pred_pitch = pred_pitch;
+    P.width = width;
+    P.height = height;
+    return cuda_status(launch_warp_add(W, static_cast<cudaStream_t>(stream)));
+}
+
+}  // extern "C"

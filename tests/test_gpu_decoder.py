@@ -1,0 +1,209 @@
+"""GPU decoder parity against the FP64 oracle through the C ABI: intra
+frames (Sec. 2.1), inter frames (Sec. 2, 2.3), GOPs with the closed
+prediction loop, and the error paths (host-side and device-side)."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import TOL_INTRA, TOL_PSNR_DB, TOL_RECON, hivc_module, psnr, to_np, torch_cuda
+from workload import IFrame, PFrame, make_config1, make_gop, make_iframe_only, make_residual
+from workload.synth import empty_residual
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hv():
+    return hivc_module()
+
+
+def _planes(dec):
+    return [to_np(dec.reference(p)).astype(np.float64) for p in range(3 if dec.chroma else 1)]
+
+
+def test_iframe_config1(hv):
+    src, ifr, _ = make_config1(0)
+    dec = hv.Decoder(256, 144, chroma=False, iframe_tol=1e-8)
+    out = hv.alloc_out(256, 144, chroma=False)
+    dec.decode_iframe(hv.device_iframe(ifr), out)
+    st = dec.sync()
+    assert st.resid[0] <= 1e-8
+    gpu = _planes(dec)[0]
+    u, _, _, _ = oracle.inpaint(256, 144, ifr.y_idx, ifr.y_val, 1e-12)
+    assert np.abs(gpu - u).max() <= TOL_INTRA
+    # mask pixels bit-exact, in the FP32 reference and in the uint8 output
+    assert np.array_equal(gpu.reshape(-1)[ifr.y_idx], ifr.y_val.astype(np.float64))
+    assert np.array_equal(to_np(out[0]).reshape(-1)[ifr.y_idx], ifr.y_val)
+    assert np.array_equal(to_np(out[0]), oracle.to_uint8(u)) or np.abs(
+        to_np(out[0]).astype(int) - oracle.to_uint8(u).astype(int)).max() <= 1
+
+
+@pytest.mark.parametrize("W,H,frac,seed", [(203, 77, 0.05, 1), (64, 48, 0.01, 2), (1, 40, 0.2, 3), (37, 1, 0.2, 4)])
+def test_iframe_color_ragged(hv, W, H, frac, seed):
+    srcs, ifr = make_iframe_only(seed, W, H, frac, chroma=True)
+    dec = hv.Decoder(W, H, chroma=True, iframe_tol=1e-9, max_cycles=200)
+    out = hv.alloc_out(W, H)
+    dec.decode_iframe(hv.device_iframe(ifr), out)
+    dec.sync()
+    gpu = _planes(dec)
+    od = oracle.OracleDecoder(W, H, True)
+    rec, _ = od.decode_iframe(ifr)
+    for p in range(3):
+        assert np.abs(gpu[p] - rec[p]).max() <= TOL_INTRA, p
+    assert np.array_equal(gpu[1].reshape(-1)[ifr.c_idx], ifr.cb_val.astype(np.float64))
+    assert np.array_equal(gpu[2].reshape(-1)[ifr.c_idx], ifr.cr_val.astype(np.float64))
+
+
+def test_iframe_with_residual(hv):
+    srcs, ifr = make_iframe_only(5, 160, 96, 0.03, chroma=True, residual={"lam_y": 8.0, "lam_c": 4.0})
+    dec = hv.Decoder(160, 96, chroma=True)
+    out = hv.alloc_out(160, 96)
+    dec.decode_iframe(hv.device_iframe(ifr), out)
+    dec.sync()
+    rec, _ = oracle.OracleDecoder(160, 96, True).decode_iframe(ifr)
+    for p, g in enumerate(_planes(dec)):
+        assert np.abs(g - rec[p]).max() <= TOL_RECON
+
+
+def test_constant_intra_is_exact(hv):
+    W, H = 50, 30
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(W * H, 20, replace=False)).astype(np.uint32)
+    ifr = IFrame(W, H, False, idx, np.full(20, 131, np.uint8))
+    dec = hv.Decoder(W, H, chroma=False)
+    out = hv.alloc_out(W, H, chroma=False)
+    dec.decode_iframe(hv.device_iframe(ifr), out)
+    st = dec.sync()
+    assert st.cycles == 0
+    assert np.all(_planes(dec)[0] == 131.0)
+
+
+def test_pframe_config1(hv):
+    src, ifr, pfr = make_config1(0)
+    dec = hv.Decoder(256, 144, chroma=False)
+    out = hv.alloc_out(256, 144, chroma=False)
+    dec.decode_iframe(hv.device_iframe(ifr), out)
+    dec.decode_pframe(hv.device_pframe(pfr), out)
+    dec.sync()
+    od = oracle.OracleDecoder(256, 144, False)
+    od.decode_iframe(ifr)
+    rec, o8 = od.decode_pframe(pfr)
+    gpu = _planes(dec)[0]
+    assert np.abs(gpu - rec[0]).max() <= TOL_RECON
+    assert abs(psnr(gpu, src) - psnr(rec[0], src)) <= TOL_PSNR_DB
+    assert np.abs(to_np(out[0]).astype(int) - o8[0].astype(int)).max() <= 1
+
+
+def test_zero_flow_zero_residual_keeps_reference(hv):
+    src, ifr, _ = make_config1(3, 64, 40)
+    dec = hv.Decoder(64, 40, chroma=False)
+    out = hv.alloc_out(64, 40, chroma=False)
+    dec.decode_iframe(hv.device_iframe(ifr), out)
+    dec.sync()
+    before = _planes(dec)[0]
+    pfr = PFrame(np.zeros((40, 64, 2), np.float32), [empty_residual(64, 40, 16)])
+    dec.decode_pframe(hv.device_pframe(pfr), out)
+    dec.sync()
+    assert np.array_equal(_planes(dec)[0], before)
+
+
+@pytest.mark.parametrize("W,H,n,seed", [(160, 90, 8, 0), (203, 77, 5, 1)])
+def test_small_color_gop(hv, W, H, n, seed):
+    gop = make_gop(seed, W, H, n_frames=n)
+    dec = hv.Decoder(W, H, chroma=True)
+    out = hv.alloc_out(W, H)
+    frames = oracle.decode_gop(gop)
+    dec.decode_iframe(hv.device_iframe(gop.iframe), out)
+    for t in range(n):
+        if t > 0:
+            dec.decode_pframe(hv.device_pframe(gop.pframes[t - 1]), out)
+        dec.sync()
+        rec, o8 = frames[t]
+        gpu = _planes(dec)
+        for p in range(3):
+            assert np.abs(gpu[p] - rec[p]).max() <= TOL_RECON, (t, p)
+            assert abs(psnr(gpu[p], gop.sources[t][p]) - psnr(rec[p], gop.sources[t][p])) <= TOL_PSNR_DB
+            assert np.abs(to_np(out[p]).astype(int) - o8[p].astype(int)).max() <= 1
+
+
+def test_fullhd_gop_head(hv):
+    """Paper-scale frames (FullHD 4:2:0): the intra frame and two inter
+    frames, every pixel against the oracle."""
+    gop = make_gop(0, 1920, 1080, n_frames=3)
+    dec = hv.Decoder(1920, 1080, chroma=True)
+    out = hv.alloc_out(1920, 1080)
+    od = oracle.OracleDecoder(1920, 1080, True)
+    for t in range(3):
+        if t == 0:
+            dec.decode_iframe(hv.device_iframe(gop.iframe), out)
+            rec, _ = od.decode_iframe(gop.iframe)
+        else:
+            dec.decode_pframe(hv.device_pframe(gop.pframes[t - 1]), out)
+            rec, _ = od.decode_pframe(gop.pframes[t - 1])
+        dec.sync()
+        for p, g in enumerate(_planes(dec)):
+            assert np.abs(g - rec[p]).max() <= TOL_RECON, (t, p)
+            assert abs(psnr(g, gop.sources[t][p]) - psnr(rec[p], gop.sources[t][p])) <= TOL_PSNR_DB
+
+
+# ---------------------------------------------------------------------------
+# error paths: host checks return at once, device data checks surface at sync
+# ---------------------------------------------------------------------------
+def test_pframe_before_iframe(hv):
+    dec = hv.Decoder(32, 32, chroma=False)
+    out = hv.alloc_out(32, 32, chroma=False)
+    pfr = PFrame(np.zeros((32, 32, 2), np.float32), [empty_residual(32, 32, 16)])
+    with pytest.raises(hv.HivcError) as e:
+        dec.decode_pframe(hv.device_pframe(pfr), out)
+    assert e.value.status == hv.HIVC_E_NO_REFERENCE
+
+
+def test_unsorted_mask_is_reported_at_sync(hv):
+    W, H = 40, 30
+    idx = np.array([5, 100, 99, 700], np.uint32)
+    ifr = IFrame(W, H, False, idx, np.array([10, 20, 30, 40], np.uint8))
+    dec = hv.Decoder(W, H, chroma=False)
+    out = hv.alloc_out(W, H, chroma=False)
+    dec.decode_iframe(hv.device_iframe(ifr), out, allow_not_converged=True)
+    dec.sync(raise_on_error=False)
+    assert dec.last_status == hv.HIVC_E_INVALID
+
+
+def test_bad_block_data_is_reported_at_sync(hv):
+    src, ifr, pfr = make_config1(0, 64, 48)
+    bp = pfr.res[0].block_ptr.copy()
+    bp[3] = bp[4] + 5  # decreasing block_ptr
+    pfr.res[0].block_ptr = bp
+    dec = hv.Decoder(64, 48, chroma=False)
+    out = hv.alloc_out(64, 48, chroma=False)
+    dec.decode_iframe(hv.device_iframe(ifr), out)
+    dec.sync()
+    dec.decode_pframe(hv.device_pframe(pfr), out)
+    st = dec.sync(raise_on_error=False)
+    assert dec.last_status == hv.HIVC_E_INVALID and st.device_flags != 0
+    assert np.all(np.isfinite(_planes(dec)[0]))
+
+
+def test_not_converged_with_cycle_cap(hv):
+    srcs, ifr = make_iframe_only(2, 128, 96, 0.002)
+    dec = hv.Decoder(128, 96, chroma=False, iframe_tol=1e-12, max_cycles=1)
+    out = hv.alloc_out(128, 96, chroma=False)
+    st = dec.decode_iframe(hv.device_iframe(ifr), out, allow_not_converged=True)
+    assert st == hv.HIVC_E_NOT_CONVERGED
+    stats = dec.sync()
+    assert stats.cycles == 1 and stats.resid[0] > 1e-12
+
+
+def test_invalid_arguments(hv):
+    with pytest.raises(hv.HivcError):
+        hv.Decoder(0, 10)
+    with pytest.raises(hv.HivcError):
+        hv.Decoder(64, 64, block=32)
+    dec = hv.Decoder(32, 32, chroma=False)
+    ifr = IFrame(32, 32, False, np.zeros(0, np.uint32), np.zeros(0, np.uint8))
+    torch = torch_cuda()
+    f = {"y_idx": torch.zeros(0, dtype=torch.int32, device="cuda"),
+         "y_val": torch.zeros(0, dtype=torch.uint8, device="cuda")}
+    with pytest.raises(hv.HivcError) as e:
+        dec.decode_iframe(f, hv.alloc_out(32, 32, chroma=False))
+    assert e.value.status == hv.HIVC_E_INVALID
