@@ -69,8 +69,9 @@ PlaneGeom plane_geom(const hivc_config *c, int p)
     return g;
 }
 
-// Relaxation factor for red-black SOR from the mask density, for randomly
-// scattered masks: the widest mask-free disc has radius about
+// Starting relaxation factor for red-black SOR from the mask density, for
+// randomly scattered masks (the solve adapts it): the widest mask-free disc
+// has radius about
 // sqrt(ln(unknowns) / (pi * density)); its lowest Dirichlet mode sets the
 // Jacobi spectral radius rho_J ~ 1 - (2.405 / R)^2 / 4, and
 // omega = 2 / (1 + sqrt(1 - rho_J^2)) (Young's optimum).
@@ -79,7 +80,9 @@ float sor_omega(int w, int h, int n)
     const double N = (double)w * h;
     const double unknown = std::max(1.0, N - n);
     const double d = std::max(n, 1) / N;
-    double R = std::sqrt(std::log(std::max(unknown, 2.0)) / (3.14159265358979 * d));
+    // the slowest modes live in irregular mask-free regions somewhat larger
+    // than the widest empty disc (factor 1.4, measured on random masks)
+    double R = 1.4 * std::sqrt(std::log(std::max(unknown, 2.0)) / (3.14159265358979 * d));
     R = std::min(R, 0.5 * std::max(w, h));
     const double lam = std::pow(2.405 / std::max(R, 1.0), 2.0);
     const double rho = std::max(0.0, 1.0 - lam / 4.0);
@@ -102,21 +105,20 @@ struct hivc_decoder {
     int cur = 0;
     bool has_ref = false;
     // intra scratch
-    double *u[2][3]{};
+    float *uh[2][3]{}, *ul[2][3]{};
     float *res[3]{}, *e[2][3]{};
     uint8_t *mask[3]{};
-    double *sum = nullptr;
-    unsigned long long *rnorm = nullptr;
+    unsigned long long *vsum = nullptr;
+    unsigned int *rnorm = nullptr;
     // block scratch
     float *rfield[3]{}, *coef[3]{}, *acoef[3]{};
     size_t coef_cap = 0;
-    uint32_t *large_list = nullptr, *large_count = nullptr;
+    uint32_t *large_list = nullptr, *ctr = nullptr;
     int large_cap = 0;
     uint32_t *flags = nullptr;
     // host mirrors
     uint32_t *h_flags = nullptr;
-    unsigned long long *h_rnorm = nullptr;
-    uint32_t *h_large = nullptr;
+    unsigned int *h_rnorm = nullptr;
     // statistics
     hivc_stats st{};
     bool timing = false;
@@ -180,10 +182,13 @@ bool out_ok(const hivc_decoder *d, const hivc_out *o)
     return true;
 }
 
-// Block stage for one frame: coefficients, then the residual fields.
-hivc_status run_block_residual(hivc_decoder *d, const hivc_residual *res)
+// Block jobs of one frame: Y, then Cb and Cr (one paired job when they share
+// block_ptr/pos: one factorisation, two right-hand sides).
+hivc_status make_block_jobs(hivc_decoder *d, const hivc_residual *res, BlockJobs &J)
 {
-    BlockJobs J{};
+    J = BlockJobs{};
+    for (int p = 0; p < d->np; ++p)
+        if ((int64_t)res[p].n_points > (int64_t)d->pg[p].w * d->pg[p].h) return HIVC_E_INVALID;
     int base = 0;
     auto add = [&](int p, int p2) {
         BlockPlane &B = J.p[J.n++];
@@ -220,14 +225,25 @@ hivc_status run_block_residual(hivc_decoder *d, const hivc_residual *res)
         }
     }
     J.total_blocks = base;
-    for (int p = 0; p < d->np; ++p)
-        if ((int64_t)res[p].n_points > (int64_t)d->pg[p].w * d->pg[p].h) return HIVC_E_INVALID;
-    BlockScratch S{d->large_list, d->large_count, d->large_cap, d->flags};
+    return HIVC_OK;
+}
+
+BlockScratch scratch(hivc_decoder *d)
+{
+    return BlockScratch{d->large_list, d->large_cap, d->flags, d->ctr};
+}
+
+// Unfused block stage: coefficients (+ large blocks), then residual fields.
+hivc_status run_block_residual(hivc_decoder *d, const hivc_residual *res)
+{
+    BlockJobs J;
+    hivc_status s = make_block_jobs(d, res, J);
+    if (s != HIVC_OK) return s;
     cudaError_t e;
     {
         Timed t(d, 3);
         int l = 0;
-        e = launch_block_coef(J, S, d->stream, &l);
+        e = launch_block_coef(J, scratch(d), d->stream, &l);
         t.done(1);
         d->st.kernel_launches[4] += 1;
         d->st.launches += 1;
@@ -286,8 +302,10 @@ size_t hivc_decoder_bytes(const hivc_config *c)
         size_t n = (size_t)g.h * g.pitch;
         add(n * 4);
         add(n * 4);      // ref ping-pong
-        add(n * 8);
-        add(n * 8);      // u ping-pong
+        add(n * 4);
+        add(n * 4);
+        add(n * 4);
+        add(n * 4);      // u = hi + lo, ping-pong
         add(n * 4);      // res
         add(n * 4);
         add(n * 4);      // e ping-pong
@@ -298,8 +316,8 @@ size_t hivc_decoder_bytes(const hivc_config *c)
         nblocks += g.nblocks;
         maxpts = std::max(maxpts, (size_t)g.w * g.h);
     }
-    add(3 * sizeof(double));
     add(3 * sizeof(unsigned long long));
+    add(3 * sizeof(unsigned int));
     add((size_t)nblocks * 4);
     add(4);
     add(4);
@@ -332,8 +350,10 @@ hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out)
         const size_t n = (size_t)g.h * g.pitch;
         d->ref[0][p] = m.get<float>(n);
         d->ref[1][p] = m.get<float>(n);
-        d->u[0][p] = m.get<double>(n);
-        d->u[1][p] = m.get<double>(n);
+        d->uh[0][p] = m.get<float>(n);
+        d->uh[1][p] = m.get<float>(n);
+        d->ul[0][p] = m.get<float>(n);
+        d->ul[1][p] = m.get<float>(n);
         d->res[p] = m.get<float>(n);
         d->e[0][p] = m.get<float>(n);
         d->e[1][p] = m.get<float>(n);
@@ -345,11 +365,11 @@ hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out)
         maxpts = std::max(maxpts, (size_t)g.w * g.h);
     }
     d->coef_cap = maxpts;
-    d->sum = m.get<double>(3);
-    d->rnorm = m.get<unsigned long long>(3);
     d->large_cap = nblocks;
     d->large_list = m.get<uint32_t>((size_t)nblocks);
-    d->large_count = m.get<uint32_t>(1);
+    d->ctr = m.get<uint32_t>(kCtrCount);
+    d->vsum = m.get<unsigned long long>(3);
+    d->rnorm = m.get<unsigned int>(3);
     d->flags = m.get<uint32_t>(1);
     if (!m.ok) {
         m.release();
@@ -361,8 +381,7 @@ hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out)
         delete d;
         return HIVC_E_NOMEM;
     }
-    d->h_rnorm = reinterpret_cast<unsigned long long *>(d->h_flags) + 1;
-    d->h_large = d->h_flags + 8;
+    d->h_rnorm = d->h_flags + 4;
     if (cfg->stream) {
         d->stream = static_cast<cudaStream_t>(cfg->stream);
     } else {
@@ -374,7 +393,9 @@ hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out)
         }
         d->own_stream = true;
     }
-    if (cudaMemsetAsync(d->flags, 0, 4, d->stream) != cudaSuccess || cudaStreamSynchronize(d->stream) != cudaSuccess) {
+    if (cudaMemsetAsync(d->flags, 0, 4, d->stream) != cudaSuccess ||
+        cudaMemsetAsync(d->ctr, 0, kCtrCount * sizeof(uint32_t), d->stream) != cudaSuccess ||
+        cudaStreamSynchronize(d->stream) != cudaSuccess) {
         hivc_decoder_destroy(d);
         return HIVC_E_CUDA;
     }
@@ -446,14 +467,17 @@ hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc
         P.val = p == 0 ? f->y.val : (p == 1 ? f->cb_val : f->cr_val);
         P.n = p == 0 ? f->y.n : f->c_n;
         P.mask = d->mask[p];
-        P.u[0] = d->u[0][p];
-        P.u[1] = d->u[1][p];
+        P.uh[0] = d->uh[0][p];
+        P.uh[1] = d->uh[1][p];
+        P.ul[0] = d->ul[0][p];
+        P.ul[1] = d->ul[1][p];
         P.res = d->res[p];
         P.e[0] = d->e[0][p];
         P.e[1] = d->e[1][p];
-        P.sum = d->sum + p;
+        P.vsum = d->vsum + p;
         P.rnorm = d->rnorm + p;
         P.omega = sor_omega(g.w, g.h, P.n);
+        P.ff = d->cfg.precision == 0 ? 1 : 0;
     }
     cudaError_t e;
     {
@@ -465,10 +489,10 @@ hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc
     if (e != cudaSuccess) return HIVC_E_CUDA;
     auto residual = [&](IntraJobs &A, bool add_e, int eb) -> cudaError_t {
         Timed t(d, 2);
-        cudaError_t er = launch_intra_residual(A, 0, eb, add_e, st);
+        cudaError_t er = launch_intra_residual(A, eb, add_e, st);
         t.done(1);
         if (er != cudaSuccess) return er;
-        er = cudaMemcpyAsync(d->h_rnorm, d->rnorm, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+        er = cudaMemcpyAsync(d->h_rnorm, d->rnorm, 3 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
         if (er != cudaSuccess) return er;
         return cudaStreamSynchronize(st);
     };
@@ -476,48 +500,90 @@ hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc
     double rn[3] = {0, 0, 0};
     auto read_norms = [&]() {
         for (int p = 0; p < d->np; ++p) {
-            double v;
-            std::memcpy(&v, d->h_rnorm + p, sizeof(double));
+            float v;
+            std::memcpy(&v, d->h_rnorm + p, sizeof(float));
             rn[p] = v;
         }
     };
     read_norms();
     const double tol = d->cfg.iframe_tol;
-    int cycles = 0, sweeps_total = 0;
-    bool active[3] = {true, true, true};
+    int cycles = 0, sweeps_total = 0, plane_sweeps[3] = {0, 0, 0};
+    // per-plane sweep counts: each cycle aims at the FP32 floor of the inner
+    // solve (about 1e-5) or at the remaining gap to the tolerance, whichever
+    // is smaller; the rate of optimally relaxed SOR is omega - 1
+    const int spl = intra_sweeps_per_launch();
+    double rate[3];
+    for (int p = 0; p < d->np; ++p) rate[p] = J.p[p].omega - 1.0;
     while (cycles < d->cfg.max_cycles) {
-        IntraJobs A{};
-        int map[3];
+        int nl[3] = {0, 0, 0}, maxl = 0;
         for (int p = 0; p < d->np; ++p) {
-            active[p] = active[p] && !(rn[p] <= tol);
-            if (active[p]) {
-                map[A.n] = p;
-                A.p[A.n++] = J.p[p];
+            if (!(rn[p] > tol)) continue;
+            const double target = std::max(1e-5, 0.3 * tol / rn[p]);
+            const double rt = std::min(std::max(rate[p], 0.05), 0.995);
+            int sw = (int)std::ceil(std::log(target) / std::log(rt));
+            sw = std::min(std::max(sw, spl), 600);
+            nl[p] = (sw + spl - 1) / spl;
+            maxl = std::max(maxl, nl[p]);
+        }
+        if (maxl == 0) break;
+        // SOR launches in segments over the planes that still need sweeps;
+        // each plane's e[0] holds its current correction between segments
+        for (int done = 0; done < maxl;) {
+            IntraJobs A{};
+            int map[3], seg = 1 << 30;
+            for (int p = 0; p < d->np; ++p)
+                if (nl[p] > done) {
+                    map[A.n] = p;
+                    A.p[A.n++] = J.p[p];
+                    seg = std::min(seg, nl[p] - done);
+                }
+            int eb = 0;
+            {
+                Timed t(d, 1);
+                int l = 0;
+                e = launch_intra_sor(A, 0, done == 0, seg * spl, st, &eb, &l);
+                t.done(l);
             }
+            if (e != cudaSuccess) return HIVC_E_CUDA;
+            if (eb == 1)
+                for (int k = 0; k < A.n; ++k) std::swap(J.p[map[k]].e[0], J.p[map[k]].e[1]);
+            done += seg;
         }
-        if (A.n == 0) break;
-        // sweeps per cycle: about five decades of the slowest plane's SOR rate
-        float om = 1.0f;
-        for (int k = 0; k < A.n; ++k) om = std::max(om, A.p[k].omega);
-        const double rate = std::max(0.05, std::min(0.98, (double)om - 1.0));
-        int sweeps = (int)std::ceil(std::log(1e-5) / std::log(rate));
-        sweeps = std::min(std::max(sweeps, 8), 400);
-        int eb = 0;
-        {
-            Timed t(d, 1);
-            int l = 0;
-            e = launch_intra_sor(A, 0, true, sweeps, st, &eb, &l);
-            t.done(l);
-            sweeps_total += l * 4;
-        }
-        if (e != cudaSuccess) return HIVC_E_CUDA;
-        if ((e = residual(A, true, eb)) != cudaSuccess) return HIVC_E_CUDA;
-        for (int k = 0; k < A.n; ++k) {
+        IntraJobs R{};
+        int map[3];
+        for (int p = 0; p < d->np; ++p)
+            if (nl[p] > 0) {
+                map[R.n] = p;
+                R.p[R.n++] = J.p[p];
+            }
+        if ((e = residual(R, true, 0)) != cudaSuccess) return HIVC_E_CUDA;
+        for (int k = 0; k < R.n; ++k) {
             const int p = map[k];
-            std::swap(J.p[p].u[0], J.p[p].u[1]);
-            double v;
-            std::memcpy(&v, d->h_rnorm + p, sizeof(double));
+            std::swap(J.p[p].uh[0], J.p[p].uh[1]);
+            std::swap(J.p[p].ul[0], J.p[p].ul[1]);
+            float v;
+            std::memcpy(&v, d->h_rnorm + p, sizeof(float));
+            const double q = v / std::max(rn[p], 1e-30);
             rn[p] = v;
+            plane_sweeps[p] += nl[p] * spl;
+            sweeps_total = std::max(sweeps_total, plane_sweeps[p]);
+            // slower than optimal SOR at this omega predicts: omega is below
+            // the optimum; Young's relation (rho + omega - 1)^2 = rho omega^2
+            // mu^2 gives the Jacobi radius mu and the optimal omega
+            const double S = nl[p] * spl;
+            if (q > 1e-4 && q < 1.0) {
+                const double ro = std::pow(q, 1.0 / S);
+                const double om = J.p[p].omega;
+                if (ro > rate[p] + 0.01) {
+                    const double mu = (ro + om - 1.0) / (om * std::sqrt(ro));
+                    if (mu < 1.0) {
+                        const double on = 2.0 / (1.0 + std::sqrt(1.0 - mu * mu));
+                        J.p[p].omega = (float)std::min(1.98, std::max(om, on));
+                    }
+                    rate[p] = std::max((double)J.p[p].omega - 1.0, std::min(ro, 0.995));
+                    if (J.p[p].omega > om) rate[p] = J.p[p].omega - 1.0;
+                }
+            }
         }
         ++cycles;
     }
@@ -534,8 +600,9 @@ hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc
     for (int p = 0; p < d->np; ++p) {
         WarpPlane &P = W.p[p];
         const PlaneGeom &g = d->pg[p];
-        P.src64 = J.p[p].u[0];
-        P.src64_pitch = g.pitch;
+        P.src_hi = J.p[p].uh[0];
+        P.src_lo = J.p[p].ff ? J.p[p].ul[0] : nullptr;
+        P.src_pitch = g.pitch;
         P.r = f->res ? d->rfield[p] : nullptr;
         P.r_pitch = g.pitch;
         P.ref_out = d->ref[nxt][p];
@@ -567,36 +634,75 @@ hivc_status hivc_decode_pframe(hivc_decoder *d, const hivc_pframe *f, const hivc
         if (!residual_ok(f->res[p])) return HIVC_E_INVALID;
     if (!d->has_ref) return HIVC_E_NO_REFERENCE;
     if (cudaSetDevice(d->device) != cudaSuccess) return HIVC_E_CUDA;
-    hivc_status s = run_block_residual(d, f->res);
-    if (s != HIVC_OK) return s;
-    WarpJobs W{};
-    W.n = d->np;
     const int nxt = d->cur ^ 1;
-    for (int p = 0; p < d->np; ++p) {
-        WarpPlane &P = W.p[p];
-        const PlaneGeom &g = d->pg[p];
-        P.ref = d->ref[d->cur][p];
-        P.ref_pitch = g.pitch;
-        P.flow = f->flow;
-        P.flow_w = d->pg[0].w;
-        P.flow_h = d->pg[0].h;
-        P.chroma_flow = p > 0 ? 1 : 0;
-        P.r = d->rfield[p];
-        P.r_pitch = g.pitch;
-        P.ref_out = d->ref[nxt][p];
-        P.ref_out_pitch = g.pitch;
-        P.out = out->plane[p];
-        P.out_pitch = out->pitch[p];
-        P.width = g.w;
-        P.height = g.h;
-    }
     cudaError_t e;
-    {
-        Timed t(d, 6);
-        e = launch_warp_add(W, d->stream);
-        t.done(1);
+    if (fused_supported(d->cfg.block)) {
+        // three launches: coefficients (K <= 32), the rare K > 32 blocks,
+        // then one fused kernel for evaluation + warp + add + pack
+        BlockJobs J;
+        hivc_status s = make_block_jobs(d, f->res, J);
+        if (s != HIVC_OK) return s;
+        {
+            Timed t(d, 3);
+            int l = 0;
+            e = launch_block_coef(J, scratch(d), d->stream, &l);
+            t.done(1);
+            d->st.kernel_launches[4] += 1;
+            d->st.launches += 1;
+        }
+        if (e != cudaSuccess) return HIVC_E_CUDA;
+        FusedFrame F{};
+        F.nblk = J.n;
+        for (int k = 0; k < J.n; ++k) F.bp[k] = J.p[k];
+        F.flow = f->flow;
+        for (int p = 0; p < d->np; ++p) {
+            F.ref[p] = d->ref[d->cur][p];
+            F.ref_out[p] = d->ref[nxt][p];
+            F.ref_pitch[p] = d->pg[p].pitch;
+            F.out[p] = out->plane[p];
+            F.out_pitch[p] = out->pitch[p];
+        }
+        F.width = d->cfg.width;
+        F.height = d->cfg.height;
+        F.chroma = d->cfg.chroma;
+        F.block = d->cfg.block;
+        F.ctr = d->ctr;
+        {
+            Timed t(d, 7);
+            e = launch_pframe_fused(F, d->flags, d->stream);
+            t.done(1);
+        }
+        if (e != cudaSuccess) return HIVC_E_CUDA;
+    } else {
+        hivc_status s = run_block_residual(d, f->res);
+        if (s != HIVC_OK) return s;
+        WarpJobs W{};
+        W.n = d->np;
+        for (int p = 0; p < d->np; ++p) {
+            WarpPlane &P = W.p[p];
+            const PlaneGeom &g = d->pg[p];
+            P.ref = d->ref[d->cur][p];
+            P.ref_pitch = g.pitch;
+            P.flow = f->flow;
+            P.flow_w = d->pg[0].w;
+            P.flow_h = d->pg[0].h;
+            P.chroma_flow = p > 0 ? 1 : 0;
+            P.r = d->rfield[p];
+            P.r_pitch = g.pitch;
+            P.ref_out = d->ref[nxt][p];
+            P.ref_out_pitch = g.pitch;
+            P.out = out->plane[p];
+            P.out_pitch = out->pitch[p];
+            P.width = g.w;
+            P.height = g.h;
+        }
+        {
+            Timed t(d, 6);
+            e = launch_warp_add(W, d->stream);
+            t.done(1);
+        }
+        if (e != cudaSuccess) return HIVC_E_CUDA;
     }
-    if (e != cudaSuccess) return HIVC_E_CUDA;
     d->cur = nxt;
     d->st.frames += 1;
     return HIVC_OK;
@@ -676,8 +782,9 @@ hivc_status hivc_block_residual(int32_t width, int32_t height, int32_t block, co
     w += a256(4 * (size_t)nb);
     uint32_t *list = reinterpret_cast<uint32_t *>(w);
     w += a256(4 * (size_t)nb);
-    uint32_t *count = reinterpret_cast<uint32_t *>(w);
+    uint32_t *counters = reinterpret_cast<uint32_t *>(w);
     w += 256;
+    if (cudaMemsetAsync(counters, 0, kCtrCount * sizeof(uint32_t), st) != cudaSuccess) return HIVC_E_CUDA;
     uint32_t *own_flags = reinterpret_cast<uint32_t *>(w);
     if (!flags) {
         flags = own_flags;
@@ -700,8 +807,7 @@ hivc_status hivc_block_residual(int32_t width, int32_t height, int32_t block, co
     B.nbx = nbx;
     B.nblocks = nb;
     J.total_blocks = nb;
-    BlockScratch S{list, count, nb, flags};
-    cudaError_t e = launch_block_coef(J, S, st, nullptr);
+    cudaError_t e = launch_block_coef(J, BlockScratch{list, nb, flags, counters}, st, nullptr);
     if (e == cudaSuccess) e = launch_block_eval(J, flags, st);
     return cuda_status(e);
 }

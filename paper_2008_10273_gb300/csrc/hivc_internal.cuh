@@ -46,35 +46,74 @@ struct BlockJobs {
     int32_t total_blocks;
 };
 
-// Scratch for the coefficient stage of one launch.
-struct BlockScratch {
-    uint32_t *large_list;   // global block ids with K > kWarpK
-    uint32_t *large_count;  // number of entries (zeroed before the launch)
-    int32_t large_cap;
-    uint32_t *flags;        // device error word
+// Device addresses of the Green's matrices of all block shapes (uploaded
+// once per device) and the SM count of the device.
+struct BlockTables {
+    const float *G;    // rows of G per shape, padded to multiples of 8 floats
+    const int *goff;   // offset of shape (w, h) at (w-1)*16 + (h-1)
+    int sms;
 };
 
-// Uploads the DCT-II / Green's tables once per device.
-cudaError_t ensure_block_tables();
+// Scratch of the coefficient stage: blocks with K > 32 are listed for the
+// large-block kernel, whose last CTA clears the counters again.
+// Work counters (zero between launches; each kernel's last CTA clears its
+// own pair again):
+enum : int {
+    kCtrLargeCount = 0,  // entries of the large-block list
+    kCtrLargeDone = 1,
+    kCtrCoefWork = 2,    // next block quad of the coefficient kernel
+    kCtrCoefDone = 3,
+    kCtrFusedWork = 4,   // next macroblock of the fused inter kernel
+    kCtrFusedDone = 5,
+    kCtrCount = 8
+};
 
-// c, a for every block (warp per block; K > 32 deferred to the CTA kernel).
-cudaError_t launch_block_coef(const BlockJobs &jobs, const BlockScratch &s, cudaStream_t st,
-                              int *launches);
-// r-field from c, a via the DCT route (warp per block), r = v at the points.
+struct BlockScratch {
+    uint32_t *large_list;
+    int32_t large_cap;
+    uint32_t *flags;  // device error word
+    uint32_t *ctr;    // kCtrCount work counters
+};
+
+cudaError_t ensure_block_tables();
+const BlockTables &block_tables();  // of the current device
+
+// c, a for every block: 16/32-lane segments (K <= 32) + the large-block
+// kernel (K > 32, one CTA per block).  Two launches.
+cudaError_t launch_block_coef(const BlockJobs &jobs, const BlockScratch &s, cudaStream_t st, int *launches);
+// r-field from c, a (Eq. 3 by Green's rows), r = v at the points.
 cudaError_t launch_block_eval(const BlockJobs &jobs, uint32_t *flags, cudaStream_t st);
+
+// One inter frame for the fused kernel: residual blocks, flow, references.
+struct FusedFrame {
+    BlockPlane bp[3];  // Y; Cb (+ Cr when paired); Cr when not paired
+    int32_t nblk;      // 1 (grey), 2 (paired chroma) or 3
+    const float *flow;
+    const float *ref[3];
+    float *ref_out[3];
+    uint8_t *out[3];
+    int32_t ref_pitch[3], out_pitch[3];  // ref_out shares ref_pitch
+    int32_t width, height, chroma, block;
+    int32_t nmbx, nmb;  // filled by the launcher
+    uint32_t *ctr;      // the decoder's work counters
+};
+
+bool fused_supported(int block);
+cudaError_t launch_pframe_fused(FusedFrame &f, uint32_t *flags, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // warp + add + pack (Sec. 2, 2.3)
 // ---------------------------------------------------------------------------
 struct WarpPlane {
     const float *ref;    // FP32 reference plane (inter), or nullptr
-    const double *src64; // FP64 prediction (intra), used when ref == nullptr
+    const float *src_hi; // intra prediction hi (+ lo) when ref == nullptr
+    const float *src_lo; // may be nullptr
     const float *r;      // residual field or nullptr
     float *ref_out;      // new FP32 reference (clamped), or nullptr
     uint8_t *out;        // uint8 output, or nullptr
     float *pred_out;     // raw prediction (step entry point), or nullptr
     const float *flow;   // luma flow (H x W x 2) for inter planes
-    int32_t ref_pitch, src64_pitch, r_pitch, ref_out_pitch, out_pitch, pred_pitch;
+    int32_t ref_pitch, src_pitch, r_pitch, ref_out_pitch, out_pitch, pred_pitch;
     int32_t width, height;
     int32_t flow_w, flow_h;  // luma flow size
     int32_t chroma_flow;     // 1: v = half mean of the 2x2 luma vectors
@@ -98,12 +137,13 @@ struct IntraPlane {
     const uint8_t *val;            // mask values
     int32_t n;                     // mask size
     uint8_t *mask;                 // 1 = known pixel
-    double *u[2];                  // FP64 solution, ping-pong
-    float *res;                    // FP32 copy of the Eq. 1 residual
+    float *uh[2], *ul[2];          // iterate u = hi + lo ([0] current, [1] next)
+    float *res;                    // FP32 Eq. 1 residual
     float *e[2];                   // FP32 correction, ping-pong
-    double *sum;                   // scratch: sum of mask values
-    unsigned long long *rnorm;     // scratch: max |residual| as ordered bits
+    unsigned long long *vsum;      // scratch: sum of mask values
+    unsigned int *rnorm;           // scratch: max |residual| (float bits)
     float omega;                   // SOR relaxation factor
+    int32_t ff;                    // 1: float-float iterate, 0: FP32 only
     int32_t tiles_x, tile_base;    // filled by the launchers
 };
 
@@ -113,12 +153,12 @@ struct IntraJobs {
 };
 
 cudaError_t launch_intra_init(IntraJobs &jobs, uint32_t *flags, cudaStream_t st, int *launches);
-// FP64: u_out = u_in + e (unless first), res = float(L u_out) at unknowns,
-// rnorm = max |L u_out|.
-cudaError_t launch_intra_residual(IntraJobs &jobs, int in, int e_in, bool add_e, cudaStream_t st);
-// S red-black SOR sweeps of (-L_UU) e = res, from e = 0 (first) or e[e_in].
+// u_next = u + e (unless first), res = (L u_next) at unknowns, rnorm = max |res|.
+cudaError_t launch_intra_residual(IntraJobs &jobs, int e_in, bool add_e, cudaStream_t st);
+// Red-black SOR sweeps of (-L_UU) e = res, from e = 0 (first) or e[e_in].
 // Returns the index of the e buffer holding the result.
-cudaError_t launch_intra_sor(IntraJobs &jobs, int e_in, bool from_zero, int sweeps, cudaStream_t st,
-                             int *e_out, int *launches);
+cudaError_t launch_intra_sor(IntraJobs &jobs, int e_in, bool from_zero, int sweeps, cudaStream_t st, int *e_out,
+                             int *launches);
+int intra_sweeps_per_launch();
 
 }  // namespace hivc

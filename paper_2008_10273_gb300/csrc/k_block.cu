@@ -5,288 +5,299 @@
 // Per block with K points p_j and values v_j:
 //   1. coefficients: the (K+1) x (K+1) saddle system
 //        [G_PP 1; 1^T 0] [c; a] = [v; 0]
-//      solved as a = 1^T G_PP^-1 v / 1^T G_PP^-1 1, c = G_PP^-1 (v - a 1),
-//      with G_PP = L L^T (Cholesky; G_PP is SPD for 1 <= K < w*h because G
-//      is the pseudo-inverse of A and E_P x is never constant).
-//      G(x, x') is read from a per-shape table T on a 2w x 2h grid:
-//        G = T(|dx|,|dy|) + T(|dx|,sy) + T(sx,|dy|) + T(sx,sy),
-//        sx = x + x' + 1, sy = y + y' + 1,
-//        T(al, be) = 1/4 sum_{(p,q)!=0} c_p^2 c_q^2 cos(pi p al/w) cos(pi q be/h) / mu_pq,
-//      the Toeplitz-plus-Hankel structure of G stated in Sec. 2.2.
-//   2. evaluation by Eq. (4): spectrum D = lambda o C(M c) of the sparse
-//      coefficient image (lambda = 1/mu, 0 for the constant mode), inverse
-//      2-D DCT-II as two 16-point matrix passes, + a; r(p_j) = v_j.
+//      solved through the Cholesky factor of G_PP (SPD for 1 <= K < w h:
+//      G is the pseudo-inverse of A and E_P x is never constant);
+//   2. evaluation of Eq. (3): r = G M c + a, r(p_j) = v_j.
 //
-// Tables are computed on the host in double precision and stored as float.
+// G of every shape is built once on the host in double precision from the
+// DCT-II diagonalisation of A (Eq. 4): with c_p(n)^2 = 1/n (p = 0), 2/n,
+// and mu_pq = 4 sin^2(pi p / 2w) + 4 sin^2(pi q / 2h),
+//   G(x,y; x',y') = T(|x-x'|,|y-y'|) + T(|x-x'|,y+y'+1) + T(x+x'+1,|y-y'|) + T(x+x'+1,y+y'+1),
+//   T(al, be) = 1/4 sum_{(p,q) != 0} c_p^2 c_q^2 cos(pi p al / w) cos(pi q be / h) / mu_pq
+// (the Toeplitz-plus-Hankel structure of G, Sec. 2.2), stored as float.
+//
+// Kernels: the coefficient stage (16-lane segments, two blocks per warp,
+// when both have K <= 16; one block per warp for K <= 32), the large-block
+// stage (one CTA per block with K > 32, packed Cholesky in shared memory)
+// and the evaluation into a residual field.  The fused inter-frame kernel
+// (k_pframe.cu) evaluates with the same routine.
 #include <cmath>
 #include <cstring>
 #include <mutex>
 #include <vector>
 
-#include "hivc_internal.cuh"
+#include "block_device.cuh"
 
 namespace hivc {
 namespace {
 
-// ---- table layout --------------------------------------------------------
-// DCT-II basis for n = 1..16:  phi_n[p*n + x] at offset sum_{m<n} m^2.
-constexpr int kPhiSize = 1496;  // sum_{n=1}^{16} n^2
-// Per shape (w, h) in 1..16: w*h spectral weights, 4*w*h Green's table.
-constexpr int kShapeSize = 18496;  // (sum_{n=1}^{16} n)^2
-constexpr int kTSize = 4 * kShapeSize;
+constexpr int kGSize = 2283904;  // sum over shapes of N * rowlen(N)
 
-__host__ __device__ __forceinline__ int phi_off(int n) { return (n - 1) * n * (2 * n - 1) / 6; }
-__host__ __device__ __forceinline__ int tri(int n) { return n * (n + 1) / 2; }
-// offset of shape (w, h) among all shapes, w-major
-__host__ __device__ __forceinline__ int shape_off(int w, int h) { return tri(w - 1) * 136 + w * tri(h - 1); }
-
-static __device__ float d_phi[kPhiSize];
-static __device__ float d_lam[kShapeSize];
-static __device__ float d_T[kTSize];
+static __device__ __align__(256) float d_G[kGSize];
+static __device__ int d_goff[256];
 
 std::mutex g_tab_mu;
+BlockTables g_tabs[64];
 uint64_t g_tab_devices = 0;  // bit d: tables uploaded to device d
 
-void build_tables(std::vector<float> &phi, std::vector<float> &lam, std::vector<float> &T)
+void build_tables(std::vector<float> &G, std::vector<int> &goff)
 {
     const double pi = 3.14159265358979323846;
-    phi.assign(kPhiSize, 0.f);
-    lam.assign(kShapeSize, 0.f);
-    T.assign(kTSize, 0.f);
-    std::vector<double> c2(17 * 17), mu1(17 * 17);
-    for (int n = 1; n <= 16; ++n)
-        for (int p = 0; p < n; ++p) {
-            double c = p == 0 ? std::sqrt(1.0 / n) : std::sqrt(2.0 / n);
-            c2[n * 17 + p] = c * c;
-            double s = std::sin(pi * p / (2.0 * n));
-            mu1[n * 17 + p] = 4.0 * s * s;
-            for (int x = 0; x < n; ++x)
-                phi[phi_off(n) + p * n + x] = (float)(c * std::cos(pi * p * (2.0 * x + 1.0) / (2.0 * n)));
-        }
-    std::vector<double> cw(32 * 16), ch(32 * 16);
+    G.assign(kGSize, 0.f);
+    goff.assign(256, 0);
+    int off = 0;
+    std::vector<double> T, cw, chq;
     for (int w = 1; w <= 16; ++w)
         for (int h = 1; h <= 16; ++h) {
-            const int so = shape_off(w, h);
-            for (int q = 0; q < h; ++q)
-                for (int p = 0; p < w; ++p) {
-                    double mu = mu1[w * 17 + p] + mu1[h * 17 + q];
-                    lam[so + q * w + p] = (p == 0 && q == 0) ? 0.f : (float)(1.0 / mu);
-                }
+            const int N = w * h, rl = g_rowlen(N);
+            goff[shape_index(w, h)] = off;
+            T.assign(4 * N, 0.0);
+            cw.assign(2 * w * w, 0.0);
+            chq.assign(2 * h * h, 0.0);
             for (int a = 0; a < 2 * w; ++a)
-                for (int p = 0; p < w; ++p) cw[a * 16 + p] = std::cos(pi * p * a / w);
+                for (int p = 0; p < w; ++p) cw[a * w + p] = std::cos(pi * p * a / w) * (p == 0 ? 1.0 : 2.0) / w;
             for (int b = 0; b < 2 * h; ++b)
-                for (int q = 0; q < h; ++q) ch[b * 16 + q] = std::cos(pi * q * b / h);
-            float *Tw = T.data() + 4 * so;
+                for (int q = 0; q < h; ++q) chq[b * h + q] = std::cos(pi * q * b / h) * (q == 0 ? 1.0 : 2.0) / h;
             for (int b = 0; b < 2 * h; ++b)
                 for (int a = 0; a < 2 * w; ++a) {
                     double s = 0.0;
                     for (int q = 0; q < h; ++q)
                         for (int p = 0; p < w; ++p) {
                             if (p == 0 && q == 0) continue;
-                            double mu = mu1[w * 17 + p] + mu1[h * 17 + q];
-                            s += c2[w * 17 + p] * c2[h * 17 + q] * cw[a * 16 + p] * ch[b * 16 + q] / mu;
+                            const double sp = std::sin(pi * p / (2.0 * w)), sq = std::sin(pi * q / (2.0 * h));
+                            s += cw[a * w + p] * chq[b * h + q] / (4.0 * sp * sp + 4.0 * sq * sq);
                         }
-                    Tw[b * (2 * w) + a] = (float)(0.25 * s);
+                    T[b * 2 * w + a] = 0.25 * s;
                 }
+            for (int i = 0; i < N; ++i)
+                for (int j = 0; j < N; ++j) {
+                    const int xi = i % w, yi = i / w, xj = j % w, yj = j / w;
+                    const int a1 = std::abs(xi - xj), a2 = xi + xj + 1, b1 = std::abs(yi - yj), b2 = yi + yj + 1;
+                    const double g = T[b1 * 2 * w + a1] + T[b2 * 2 * w + a1] + T[b1 * 2 * w + a2] + T[b2 * 2 * w + a2];
+                    G[off + i * rl + j] = (float)g;
+                }
+            off += N * rl;
         }
 }
 
-// ---- device helpers ------------------------------------------------------
-__device__ __forceinline__ float warp_sum(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-__device__ __forceinline__ float green(const float *__restrict__ T, int w2, int xi, int yi, int xj, int yj)
-{
-    const int a1 = abs(xi - xj), a2 = xi + xj + 1, b1 = abs(yi - yj), b2 = yi + yj + 1;
-    return (__ldg(T + b1 * w2 + a1) + __ldg(T + b2 * w2 + a1)) + (__ldg(T + b1 * w2 + a2) + __ldg(T + b2 * w2 + a2));
-}
-
-__device__ __forceinline__ int find_job(const BlockJobs &J, int gb)
-{
-    int j = 0;
-#pragma unroll 1
-    for (int k = 1; k < J.n; ++k)
-        if (gb >= J.p[k].block_base) j = k;
-    return j;
-}
-
-struct BlockGeom {
-    int lb, w, h, x0, y0;
-    uint32_t s;
-    int K;
-    uint32_t bad;  // error bits for block_ptr / K
+// ---- coefficient stage ---------------------------------------------------
+// A warp takes four consecutive blocks.  When all have K <= 8 it solves them
+// at once in 8-lane segments; otherwise pairs in 16-lane segments (K <= 16)
+// or single blocks with all 32 lanes (K <= 32).  K > 32 goes to the large-
+// block kernel.
+struct SegBlock {
+    const BlockPlane *P;
+    BlockGeom g;
 };
 
-__device__ __forceinline__ BlockGeom block_geom(const BlockPlane &P, int lb)
+// geometry of global block gb (no side effects); K = 0 for missing or bad
+// blocks and for K > 32 (those go to the large-block kernel)
+__device__ __forceinline__ SegBlock seg_block(const BlockJobs &J, int gb)
 {
-    BlockGeom g;
-    g.lb = lb;
-    const int bx = lb % P.nbx, by = lb / P.nbx;
-    g.x0 = bx * P.block;
-    g.y0 = by * P.block;
-    g.w = min(P.block, P.width - g.x0);
-    g.h = min(P.block, P.height - g.y0);
-    const uint32_t s = __ldg(P.block_ptr + lb), e = __ldg(P.block_ptr + lb + 1);
-    g.bad = 0;
-    if (e < s || e > (uint32_t)P.n_points || (lb == 0 && s != 0)) g.bad = kFlagBlockPtr;
-    g.s = s;
-    g.K = g.bad ? 0 : (int)(e - s);
-    if (!g.bad && g.K > g.w * g.h - 1) {
-        g.bad = kFlagK;
-        g.K = 0;
-    }
-    return g;
+    SegBlock b;
+    b.P = nullptr;
+    b.g.K = 0;
+    b.g.bad = 0;
+    b.g.s = 0;
+    b.g.w = b.g.h = 1;
+    b.g.lb = 0;
+    if (gb >= J.total_blocks) return b;
+    b.P = &J.p[find_job(J, gb)];
+    b.g = block_geom(*b.P, gb - b.P->block_base);
+    return b;
 }
 
-// Positions of one 32-point chunk: validity (inside, increasing).
-__device__ __forceinline__ bool load_point(const BlockPlane &P, const BlockGeom &g, int j, int &px, int &py)
-{
-    const int p = __ldg(P.pos + g.s + j);
-    const int prev = j > 0 ? (int)__ldg(P.pos + g.s + j - 1) : -1;
-    px = p % g.w;
-    py = p / g.w;
-    return p < g.w * g.h && p > prev;
-}
+__device__ __forceinline__ int seg_k(const SegBlock &b) { return (b.g.bad || b.g.K > kWarpK) ? 0 : b.g.K; }
 
-// ---- coefficient stage: one warp per block, K <= 32 ----------------------
-__global__ void __launch_bounds__(128) block_coef_kernel(const __grid_constant__ BlockJobs J, BlockScratch S)
+// validity of the positions of a segment's block (inside, increasing):
+// returns K, or 0 (and a flag) when any is bad
+template <int SEG>
+__device__ __forceinline__ int seg_validate(const SegBlock &b, int i, int seg, const BlockScratch &S)
 {
-    __shared__ float smat[4][32][33];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gb = blockIdx.x * 4 + warp;
-    if (gb >= J.total_blocks) return;
-    const BlockPlane &P = J.p[find_job(J, gb)];
-    const BlockGeom g = block_geom(P, gb - P.block_base);
-    if (g.bad) {
-        if (lane == 0) atomicOr(S.flags, g.bad);
-        return;
-    }
-    const int K = g.K;
-    if (K == 0) return;
-    if (K > kWarpK) {
-        if (lane == 0) {
-            const uint32_t i = atomicAdd(S.large_count, 1u);
-            if (i < (uint32_t)S.large_cap) S.large_list[i] = (uint32_t)gb;
-        }
-        return;
-    }
-    const bool two = P.val[1] != nullptr;
-    int px = 0, py = 0;
-    float v0 = 0.f, v1 = 0.f;
+    const int K = b.g.K;
     bool ok = true;
-    if (lane < K) {
-        ok = load_point(P, g, lane, px, py);
-        v0 = (float)__ldg(P.val[0] + g.s + lane);
-        if (two) v1 = (float)__ldg(P.val[1] + g.s + lane);
+    if (i < K) {
+        int p;
+        ok = load_pos(*b.P, b.g, i, p);
     }
-    if (__any_sync(0xffffffffu, !ok)) {
-        if (lane == 0) atomicOr(S.flags, kFlagPos);
-        return;
+    const unsigned bad = __ballot_sync(0xffffffffu, !ok);
+    const unsigned mine = SEG == 32 ? bad : (bad >> (seg * SEG)) & ((1u << SEG) - 1u);
+    if (mine) {
+        if (i == 0) atomicOr(S.flags, kFlagPos);
+        return 0;
     }
-    const float *T = d_T + 4 * shape_off(g.w, g.h);
-    const int w2 = 2 * g.w;
-    float(*M)[33] = smat[warp];
-    // assemble the lower triangle of G_PP, lane i owns row i
-    for (int j = 0; j < K; ++j) {
-        const int xj = __shfl_sync(0xffffffffu, px, j), yj = __shfl_sync(0xffffffffu, py, j);
-        if (lane < K && j <= lane) M[lane][j] = green(T, w2, px, py, xj, yj);
+    return K;
+}
+
+// KM = 0: the shared-memory warp routine (16 < K <= 32)
+template <int SEG, int KM>
+__device__ __forceinline__ void seg_run(const SegBlock &b, int K, int i, float (*Lt)[SEG + 1], const BlockTables &tab,
+                                        const BlockScratch &S)
+{
+    const BlockPlane *P = b.P;
+    const bool two = K > 0 && P->val[1] != nullptr;
+    int p = 0;
+    float v0 = 0.f, v1 = 0.f;
+    if (i < K) {
+        p = __ldg(P->pos + b.g.s + i);
+        v0 = (float)__ldg(P->val[0] + b.g.s + i);
+        if (two) v1 = (float)__ldg(P->val[1] + b.g.s + i);
     }
-    __syncwarp();
-    // Cholesky G_PP = L L^T in place (right-looking)
-    bool spd = true;
-    for (int k = 0; k < K; ++k) {
-        float d = M[k][k];
-        spd = spd && (d > 0.f);
-        d = fmaxf(d, 1e-30f);
-        const float sd = sqrtf(d), isd = 1.0f / sd;
-        __syncwarp();
-        if (lane == k) M[k][k] = sd;
-        else if (lane > k && lane < K) M[lane][k] *= isd;
-        __syncwarp();
-        if (lane > k && lane < K) {
-            const float lik = M[lane][k];
-            for (int j = k + 1; j <= lane; ++j) M[lane][j] = fmaf(-lik, M[j][k], M[lane][j]);
+    const float *G = K > 0 ? green_rows(tab, b.g.w, b.g.h) : tab.G;
+    const int rl = K > 0 ? g_rowlen(b.g.w * b.g.h) : 8;
+    float c0, c1, a0, a1;
+    bool spd;
+    if constexpr (KM == 0)
+        spd = warp_block_coef_smem(G, rl, K, i, p, v0, v1, reinterpret_cast<float(*)[33]>(&Lt[0][0]), c0, c1, a0, a1);
+    else
+        spd = seg_block_coef<SEG, KM, true>(G, rl, K, i, p, v0, v1, Lt, c0, c1, a0, a1);
+    if (K > 0) {
+        if (i < K) {
+            P->coef[0][b.g.s + i] = c0;
+            if (two) P->coef[1][b.g.s + i] = c1;
         }
-        __syncwarp();
-    }
-    // L y = [v0 v1 1], then L^T z = y; lane i holds entry i
-    float b0 = v0, b1 = v1, b2 = lane < K ? 1.f : 0.f;
-    for (int k = 0; k < K; ++k) {
-        const float inv = 1.0f / M[k][k];
-        const float y0 = __shfl_sync(0xffffffffu, b0, k) * inv;
-        const float y1 = __shfl_sync(0xffffffffu, b1, k) * inv;
-        const float y2 = __shfl_sync(0xffffffffu, b2, k) * inv;
-        if (lane == k) {
-            b0 = y0; b1 = y1; b2 = y2;
-        } else if (lane > k && lane < K) {
-            const float l = M[lane][k];
-            b0 = fmaf(-l, y0, b0); b1 = fmaf(-l, y1, b1); b2 = fmaf(-l, y2, b2);
+        if (i == 0) {
+            P->acoef[0][b.g.lb] = a0;
+            if (two) P->acoef[1][b.g.lb] = a1;
+            if (!spd) atomicOr(S.flags, kFlagNotSPD);
         }
-    }
-    for (int k = K - 1; k >= 0; --k) {
-        const float inv = 1.0f / M[k][k];
-        const float z0 = __shfl_sync(0xffffffffu, b0, k) * inv;
-        const float z1 = __shfl_sync(0xffffffffu, b1, k) * inv;
-        const float z2 = __shfl_sync(0xffffffffu, b2, k) * inv;
-        if (lane == k) {
-            b0 = z0; b1 = z1; b2 = z2;
-        } else if (lane < k) {
-            const float l = M[k][lane];
-            b0 = fmaf(-l, z0, b0); b1 = fmaf(-l, z1, b1); b2 = fmaf(-l, z2, b2);
-        }
-    }
-    // a = 1^T G^-1 v / 1^T G^-1 1 ;  c = G^-1 v - a G^-1 1  (sum c = 0)
-    const float s2 = warp_sum(lane < K ? b2 : 0.f);
-    const float a0 = warp_sum(lane < K ? b0 : 0.f) / s2;
-    const float a1 = two ? warp_sum(lane < K ? b1 : 0.f) / s2 : 0.f;
-    if (lane < K) {
-        P.coef[0][g.s + lane] = fmaf(-a0, b2, b0);
-        if (two) P.coef[1][g.s + lane] = fmaf(-a1, b2, b1);
-    }
-    if (lane == 0) {
-        P.acoef[0][g.lb] = a0;
-        if (two) P.acoef[1][g.lb] = a1;
-        if (!spd) atomicOr(S.flags, kFlagNotSPD);
     }
 }
 
-// ---- coefficient stage for K > 32: one CTA per block, packed Cholesky ----
+// Clears a kernel's work/done counter pair once every CTA has finished
+// grabbing work (the last CTA to arrive resets both; no waiting).
+__device__ __forceinline__ void release_counters(uint32_t *work, uint32_t *done)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(done, 1u) == gridDim.x - 1) {
+            *work = 0;
+            *done = 0;
+            __threadfence();
+        }
+    }
+}
+
+__device__ __forceinline__ void coef_quad(const BlockJobs &J, const BlockTables &tab, const BlockScratch &S, int gb0,
+                                          int lane, float *lts)
+{
+    // lane q < 4 owns block gb0 + q: error flags and the large-block list
+    int kq;
+    {
+        const SegBlock bq = seg_block(J, gb0 + (lane & 3));
+        kq = seg_k(bq);
+        if (lane < 4 && bq.P != nullptr) {
+            if (bq.g.bad) {
+                atomicOr(S.flags, bq.g.bad);
+            } else if (bq.g.K > kWarpK) {
+                const uint32_t i = atomicAdd(S.ctr + kCtrLargeCount, 1u);
+                if (i < (uint32_t)S.large_cap) S.large_list[i] = (uint32_t)(gb0 + lane);
+            }
+        }
+    }
+    const int k0 = __shfl_sync(0xffffffffu, kq, 0), k1 = __shfl_sync(0xffffffffu, kq, 1);
+    const int k2 = __shfl_sync(0xffffffffu, kq, 2), k3 = __shfl_sync(0xffffffffu, kq, 3);
+    const int k01 = max(k0, k1), k23 = max(k2, k3);
+    if (max(k01, k23) == 0) return;
+    if (max(k01, k23) <= 8) {
+        const int seg = lane >> 3, i = lane & 7;
+        SegBlock bb = seg_block(J, gb0 + seg);
+        bb.g.K = seg_k(bb);
+        const int K = seg_validate<8>(bb, i, seg, S);
+        seg_run<8, 8>(bb, K, i, reinterpret_cast<float(*)[9]>(lts + seg * 8 * 9), tab, S);
+        __syncwarp();
+        return;
+    }
+#pragma unroll 1
+    for (int pr = 0; pr < 2; ++pr) {
+        const int kp = pr ? k23 : k01;
+        if (kp == 0) continue;
+        if (kp <= 16) {
+            const int seg = lane >> 4, i = lane & 15;
+            SegBlock bb = seg_block(J, gb0 + 2 * pr + seg);
+            bb.g.K = seg_k(bb);
+            const int K = seg_validate<16>(bb, i, seg, S);
+            const int km = __reduce_max_sync(0xffffffffu, K);
+            auto Lt = reinterpret_cast<float(*)[17]>(lts + seg * 16 * 17);
+            if (km <= 12) seg_run<16, 12>(bb, K, i, Lt, tab, S);
+            else seg_run<16, 16>(bb, K, i, Lt, tab, S);
+        } else {
+            auto Lt = reinterpret_cast<float(*)[33]>(lts);
+#pragma unroll 1
+            for (int k = 0; k < 2; ++k) {
+                SegBlock bb = seg_block(J, gb0 + 2 * pr + k);
+                bb.g.K = seg_k(bb);
+                const int K = seg_validate<32>(bb, lane, 0, S);
+                if (K == 0) continue;
+                seg_run<32, 0>(bb, K, lane, Lt, tab, S);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Persistent: each warp grabs the next quad of four blocks until none is left.
+__global__ void __launch_bounds__(128, 8) block_coef_kernel(const __grid_constant__ BlockJobs J, BlockTables tab,
+                                                            BlockScratch S)
+{
+    __shared__ float lts[4][32 * 33];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t nquad = (uint32_t)(J.total_blocks + 3) / 4;
+    for (;;) {
+        uint32_t q = 0;
+        if (lane == 0) q = atomicAdd(S.ctr + kCtrCoefWork, 1u);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if (q >= nquad) break;
+        coef_quad(J, tab, S, (int)q * 4, lane, lts[warp]);
+    }
+    release_counters(S.ctr + kCtrCoefWork, S.ctr + kCtrCoefDone);
+}
+
+// ---- large blocks (K > 32): one CTA per block, packed Cholesky -----------
 constexpr int kLargeThreads = 256;
 constexpr int kLargeMaxK = 255;
-constexpr size_t kLargeSmem =
-    sizeof(float) * ((size_t)kLargeMaxK * (kLargeMaxK + 1) / 2 + 3 * kLargeMaxK) + sizeof(int) * 2 * kLargeMaxK;
+constexpr size_t kLargeSmem = sizeof(float) * ((size_t)kLargeMaxK * (kLargeMaxK + 1) / 2 + 3 * kLargeMaxK);
 
 __device__ __forceinline__ int pk(int i, int j) { return i * (i + 1) / 2 + j; }  // j <= i
 
-__global__ void __launch_bounds__(kLargeThreads) block_coef_large_kernel(const __grid_constant__ BlockJobs J,
-                                                                         BlockScratch S)
+__device__ __forceinline__ float cta_sum(float v, float *red)
+{
+    v = seg_sum<32>(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float t = 0.f;
+    for (int k = 0; k < kLargeThreads / 32; ++k) t += red[k];
+    return t;
+}
+
+// The coefficient stage lists the K > 32 blocks; each CTA solves list
+// entries blockIdx.x, blockIdx.x + gridDim.x, ...  The last CTA to finish
+// clears the list counter for the next frame (no spin: a done counter).
+__global__ void __launch_bounds__(kLargeThreads) block_large_kernel(const __grid_constant__ BlockJobs J,
+                                                                    BlockTables tab, BlockScratch S)
 {
     extern __shared__ float sm[];
-    __shared__ float red[3][kLargeThreads / 32];
+    __shared__ float red[kLargeThreads / 32];
     __shared__ int s_bad;
+    __shared__ unsigned char s_p[kLargeMaxK];
     const int tid = threadIdx.x;
-    const uint32_t count = min(*S.large_count, (uint32_t)S.large_cap);
+    const uint32_t count = min(*(volatile uint32_t *)(S.ctr + kCtrLargeCount), (uint32_t)S.large_cap);
     for (uint32_t it = blockIdx.x; it < count; it += gridDim.x) {
         const int gb = (int)S.large_list[it];
         const BlockPlane &P = J.p[find_job(J, gb)];
         const BlockGeom g = block_geom(P, gb - P.block_base);
-        const int K = g.K;  // > 32 and valid by construction of the list
+        const int K = g.K;
         const bool two = P.val[1] != nullptr;
         float *L = sm;
         float *b = sm + (size_t)K * (K + 1) / 2;  // b[r*K + i]
-        int *px = reinterpret_cast<int *>(b + 3 * K);
-        int *py = px + K;
         if (tid == 0) s_bad = 0;
         __syncthreads();
         for (int j = tid; j < K; j += kLargeThreads) {
-            int x, y;
-            if (!load_point(P, g, j, x, y)) s_bad = 1;
-            px[j] = x;
-            py[j] = y;
+            int p;
+            if (!load_pos(P, g, j, p)) s_bad = 1;
+            s_p[j] = (unsigned char)p;
             b[j] = (float)__ldg(P.val[0] + g.s + j);
             b[K + j] = two ? (float)__ldg(P.val[1] + g.s + j) : 0.f;
             b[2 * K + j] = 1.f;
@@ -297,10 +308,10 @@ __global__ void __launch_bounds__(kLargeThreads) block_coef_large_kernel(const _
             __syncthreads();
             continue;
         }
-        const float *T = d_T + 4 * shape_off(g.w, g.h);
-        const int w2 = 2 * g.w;
+        const float *G = green_rows(tab, g.w, g.h);
+        const int rl = g_rowlen(g.w * g.h);
         for (int i = tid; i < K; i += kLargeThreads)
-            for (int j = 0; j <= i; ++j) L[pk(i, j)] = green(T, w2, px[i], py[i], px[j], py[j]);
+            for (int j = 0; j <= i; ++j) L[pk(i, j)] = __ldg(G + (size_t)s_p[i] * rl + s_p[j]);
         __syncthreads();
         bool spd = true;
         for (int k = 0; k < K; ++k) {
@@ -317,6 +328,7 @@ __global__ void __launch_bounds__(kLargeThreads) block_coef_large_kernel(const _
             }
             __syncthreads();
         }
+        // forward L y = b (three right-hand sides)
         for (int k = 0; k < K; ++k) {
             if (tid < 3) b[tid * K + k] /= L[pk(k, k)];
             __syncthreads();
@@ -328,42 +340,35 @@ __global__ void __launch_bounds__(kLargeThreads) block_coef_large_kernel(const _
             }
             __syncthreads();
         }
+        // a = (y_1 . y_v) / (y_1 . y_1), then L^T c = y_v - a y_1
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+        for (int i = tid; i < K; i += kLargeThreads) {
+            const float y2 = b[2 * K + i];
+            s0 += y2 * b[i];
+            s1 += y2 * b[K + i];
+            s2 += y2 * y2;
+        }
+        s2 = cta_sum(s2, red);
+        const float a0 = cta_sum(s0, red) / s2, a1 = cta_sum(s1, red) / s2;
+        __syncthreads();
+        for (int i = tid; i < K; i += kLargeThreads) {
+            b[i] = fmaf(-a0, b[2 * K + i], b[i]);
+            b[K + i] = fmaf(-a1, b[2 * K + i], b[K + i]);
+        }
+        __syncthreads();
         for (int k = K - 1; k >= 0; --k) {
-            if (tid < 3) b[tid * K + k] /= L[pk(k, k)];
+            if (tid < 2) b[tid * K + k] /= L[pk(k, k)];
             __syncthreads();
             for (int i = tid; i < k; i += kLargeThreads) {
                 const float l = L[pk(k, i)];
                 b[i] = fmaf(-l, b[k], b[i]);
                 b[K + i] = fmaf(-l, b[K + k], b[K + i]);
-                b[2 * K + i] = fmaf(-l, b[2 * K + k], b[2 * K + i]);
             }
             __syncthreads();
         }
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
         for (int i = tid; i < K; i += kLargeThreads) {
-            s0 += b[i];
-            s1 += b[K + i];
-            s2 += b[2 * K + i];
-        }
-        s0 = warp_sum(s0);
-        s1 = warp_sum(s1);
-        s2 = warp_sum(s2);
-        if ((tid & 31) == 0) {
-            red[0][tid >> 5] = s0;
-            red[1][tid >> 5] = s1;
-            red[2][tid >> 5] = s2;
-        }
-        __syncthreads();
-        float t0 = 0.f, t1 = 0.f, t2 = 0.f;
-        for (int k = 0; k < kLargeThreads / 32; ++k) {
-            t0 += red[0][k];
-            t1 += red[1][k];
-            t2 += red[2][k];
-        }
-        const float a0 = t0 / t2, a1 = t1 / t2;
-        for (int i = tid; i < K; i += kLargeThreads) {
-            P.coef[0][g.s + i] = fmaf(-a0, b[2 * K + i], b[i]);
-            if (two) P.coef[1][g.s + i] = fmaf(-a1, b[2 * K + i], b[K + i]);
+            P.coef[0][g.s + i] = b[i];
+            if (two) P.coef[1][g.s + i] = b[K + i];
         }
         if (tid == 0) {
             P.acoef[0][g.lb] = a0;
@@ -372,107 +377,60 @@ __global__ void __launch_bounds__(kLargeThreads) block_coef_large_kernel(const _
         }
         __syncthreads();
     }
+    release_counters(S.ctr + kCtrLargeCount, S.ctr + kCtrLargeDone);
 }
 
-// ---- evaluation stage: r = C^-1 diag(lambda) C (M c) + a, one warp/block --
-__global__ void __launch_bounds__(128) block_eval_kernel(const __grid_constant__ BlockJobs J, uint32_t *flags)
+// ---- evaluation stage into residual fields, one warp per block -----------
+__global__ void __launch_bounds__(128) block_eval_kernel(const __grid_constant__ BlockJobs J, BlockTables tab,
+                                                         uint32_t *flags)
 {
-    __shared__ float sD[4][16][17];  // D[q][p]
-    __shared__ float sE[4][16][17];  // E[q][x]
+    __shared__ float cs[4][2][256];
+    __shared__ unsigned char ps[4][256];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gb = blockIdx.x * 4 + warp;
     if (gb >= J.total_blocks) return;
     const BlockPlane &P = J.p[find_job(J, gb)];
     const BlockGeom g = block_geom(P, gb - P.block_base);
-    const int K = g.K, w = g.w, h = g.h;
+    const int K = g.K, w = g.w, N = g.w * g.h;
+    const bool two = P.val[1] != nullptr;
     bool valid = true;
     for (int j0 = 0; j0 < K; j0 += 32) {
-        int x, y;
-        const bool ok = (j0 + lane < K) ? load_point(P, g, j0 + lane, x, y) : true;
+        int p = 0;
+        const bool ok = (j0 + lane < K) ? load_pos(P, g, j0 + lane, p) : true;
         valid = valid && !__any_sync(0xffffffffu, !ok);
+        if (j0 + lane < K) {
+            ps[warp][j0 + lane] = (unsigned char)p;
+            cs[warp][0][j0 + lane] = __ldg(P.coef[0] + g.s + j0 + lane);
+            if (two) cs[warp][1][j0 + lane] = __ldg(P.coef[1] + g.s + j0 + lane);
+        }
     }
     if (!valid && lane == 0) atomicOr(flags, kFlagPos);
-    const int nch = P.val[1] != nullptr ? 2 : 1;
-    const float *phw = d_phi + phi_off(w);
-    const float *phh = d_phi + phi_off(h);
-    const float *lam = d_lam + shape_off(w, h);
-    const int p = lane & 15, xq = lane & 15, q0 = (lane >> 4) * 8;
-    for (int ch = 0; ch < nch; ++ch) {
-        float *R = P.r[ch];
-        if (R == nullptr) continue;
-        float *Rb = R + (size_t)g.y0 * P.r_pitch + g.x0;
-        if (K == 0 || !valid) {
-            for (int i = lane; i < w * h; i += 32) Rb[(i / w) * P.r_pitch + (i % w)] = 0.f;
-            continue;
+    __syncwarp();
+    const int pitch = P.r_pitch;
+    float *R0 = P.r[0] + (size_t)g.y0 * pitch + g.x0;
+    float *R1 = two && P.r[1] ? P.r[1] + (size_t)g.y0 * pitch + g.x0 : nullptr;
+    if (K == 0 || !valid) {
+        for (int i = lane; i < N; i += 32) {
+            R0[(i / w) * pitch + i % w] = 0.f;
+            if (R1) R1[(i / w) * pitch + i % w] = 0.f;
         }
-        // sparse forward transform of the coefficient image
-        float acc[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] = 0.f;
-        for (int j0 = 0; j0 < K; j0 += 32) {
-            int cx = 0, cy = 0;
-            float cc = 0.f;
-            if (j0 + lane < K) {
-                const int pp = __ldg(P.pos + g.s + j0 + lane);
-                cx = pp % w;
-                cy = pp / w;
-                cc = __ldg(P.coef[ch] + g.s + j0 + lane);
-            }
-            const int n = min(32, K - j0);
-            for (int t = 0; t < n; ++t) {
-                const int xj = __shfl_sync(0xffffffffu, cx, t);
-                const int yj = __shfl_sync(0xffffffffu, cy, t);
-                const float cj = __shfl_sync(0xffffffffu, cc, t);
-                const float tp = p < w ? cj * __ldg(phw + p * w + xj) : 0.f;
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int q = q0 + k;
-                    if (q < h) acc[k] = fmaf(tp, __ldg(phh + q * h + yj), acc[k]);
-                }
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int q = q0 + k;
-            sD[warp][q][p] = (p < w && q < h) ? acc[k] * __ldg(lam + q * w + p) : 0.f;
-        }
-        __syncwarp();
-        // inverse transform, pass 1 (x): E(q, x) = sum_p phi_w(p, x) D(p, q)
-        float e8[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) e8[k] = 0.f;
-        for (int pp = 0; pp < w; ++pp) {
-            const float f = xq < w ? __ldg(phw + pp * w + xq) : 0.f;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) e8[k] = fmaf(f, sD[warp][q0 + k][pp], e8[k]);
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) sE[warp][q0 + k][xq] = e8[k];
-        __syncwarp();
-        // pass 2 (y): r(x, y) = sum_q phi_h(q, y) E(q, x) + a
-        const float a = __ldg(P.acoef[ch] + g.lb);
-        float r8[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) r8[k] = a;
-        const int y0 = q0;
-        for (int q = 0; q < h; ++q) {
-            const float ev = sE[warp][q][xq];
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (y0 + k < h) r8[k] = fmaf(__ldg(phh + q * h + y0 + k), ev, r8[k]);
-        }
-        if (xq < w) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (y0 + k < h) Rb[(size_t)(y0 + k) * P.r_pitch + xq] = r8[k];
-        }
-        __syncwarp();
-        // the data at the points, exactly
-        for (int j = lane; j < K; j += 32) {
-            const int pp = __ldg(P.pos + g.s + j);
-            Rb[(size_t)(pp / w) * P.r_pitch + (pp % w)] = (float)__ldg(P.val[ch] + g.s + j);
-        }
-        __syncwarp();
+        return;
+    }
+    const float a0 = __ldg(P.acoef[0] + g.lb), a1 = two ? __ldg(P.acoef[1] + g.lb) : 0.f;
+    const float *G = green_rows(tab, g.w, g.h);
+    auto out = [&](int x, int y, float v0, float v1) {
+        const int o = y * pitch + x;
+        R0[o] = v0;
+        if (R1) R1[o] = v1;
+    };
+    if (two) warp_block_eval<true>(G, w, N, K, ps[warp], cs[warp][0], cs[warp][1], a0, a1, lane, out);
+    else warp_block_eval<false>(G, w, N, K, ps[warp], cs[warp][0], cs[warp][1], a0, a1, lane, out);
+    __syncwarp();
+    // the data at the points, exactly
+    for (int j = lane; j < K; j += 32) {
+        const size_t o = (size_t)(ps[warp][j] / w) * pitch + ps[warp][j] % w;
+        R0[o] = (float)__ldg(P.val[0] + g.s + j);
+        if (R1) R1[o] = (float)__ldg(P.val[1] + g.s + j);
     }
 }
 
@@ -483,31 +441,46 @@ cudaError_t ensure_block_tables()
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    if (dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_tab_mu);
-    if (dev < 64 && (g_tab_devices >> dev) & 1ull) return cudaSuccess;
-    static std::vector<float> phi, lam, T;
-    if (phi.empty()) build_tables(phi, lam, T);
-    if ((e = cudaMemcpyToSymbol(d_phi, phi.data(), phi.size() * sizeof(float))) != cudaSuccess) return e;
-    if ((e = cudaMemcpyToSymbol(d_lam, lam.data(), lam.size() * sizeof(float))) != cudaSuccess) return e;
-    if ((e = cudaMemcpyToSymbol(d_T, T.data(), T.size() * sizeof(float))) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(block_coef_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((g_tab_devices >> dev) & 1ull) return cudaSuccess;
+    static std::vector<float> G;
+    static std::vector<int> goff;
+    if (G.empty()) build_tables(G, goff);
+    if ((e = cudaMemcpyToSymbol(d_G, G.data(), G.size() * sizeof(float))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(d_goff, goff.data(), goff.size() * sizeof(int))) != cudaSuccess) return e;
+    BlockTables t{};
+    if ((e = cudaGetSymbolAddress((void **)&t.G, d_G)) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void **)&t.goff, d_goff)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(block_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kLargeSmem)) != cudaSuccess)
         return e;
-    if (dev < 64) g_tab_devices |= 1ull << dev;
+    if ((e = cudaDeviceGetAttribute(&t.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    g_tabs[dev] = t;
+    g_tab_devices |= 1ull << dev;
     return cudaSuccess;
+}
+
+const BlockTables &block_tables()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return g_tabs[dev < 64 ? dev : 0];
 }
 
 cudaError_t launch_block_coef(const BlockJobs &jobs, const BlockScratch &s, cudaStream_t st, int *launches)
 {
     if (jobs.total_blocks == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(s.large_count, 0, sizeof(uint32_t), st);
+    const BlockTables &t = block_tables();
+    static int per_sm = 0;
+    if (per_sm == 0 &&
+        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, block_coef_kernel, 128, 0) != cudaSuccess || per_sm < 1))
+        per_sm = 1;
+    const int grid = std::max(1, std::min(t.sms * per_sm, (jobs.total_blocks + 15) / 16));
+    block_coef_kernel<<<grid, 128, 0, st>>>(jobs, t, s);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    block_coef_kernel<<<(jobs.total_blocks + 3) / 4, 128, 0, st>>>(jobs, s);
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = std::max(1, std::min(sms, jobs.total_blocks));
-    block_coef_large_kernel<<<grid, kLargeThreads, kLargeSmem, st>>>(jobs, s);
+    block_large_kernel<<<t.sms, kLargeThreads, kLargeSmem, st>>>(jobs, t, s);
     if (launches) *launches += 2;
     return cudaGetLastError();
 }
@@ -515,7 +488,7 @@ cudaError_t launch_block_coef(const BlockJobs &jobs, const BlockScratch &s, cuda
 cudaError_t launch_block_eval(const BlockJobs &jobs, uint32_t *flags, cudaStream_t st)
 {
     if (jobs.total_blocks == 0) return cudaSuccess;
-    block_eval_kernel<<<(jobs.total_blocks + 3) / 4, 128, 0, st>>>(jobs, flags);
+    block_eval_kernel<<<(jobs.total_blocks + 3) / 4, 128, 0, st>>>(jobs, block_tables(), flags);
     return cudaGetLastError();
 }
 

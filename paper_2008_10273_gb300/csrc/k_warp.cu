@@ -87,7 +87,8 @@ __global__ void __launch_bounds__(kTW *kTH) warp_add_kernel(const __grid_constan
         }
         pred = sample(P.ref, P.ref_pitch, P.width, P.height, x, y, dx, dy);
     } else {
-        pred = (float)P.src64[(size_t)y * P.src64_pitch + x];
+        const size_t i = (size_t)y * P.src_pitch + x;
+        pred = P.src_lo ? __fadd_rn(P.src_hi[i], P.src_lo[i]) : P.src_hi[i];
     }
     if (P.pred_out) P.pred_out[(size_t)y * P.pred_pitch + x] = pred;
     float v = pred;

@@ -78,6 +78,19 @@ def test_constant_intra_is_exact(hv):
     assert np.all(_planes(dec)[0] == 131.0)
 
 
+def test_grey_gop_with_large_blocks(hv):
+    """Grey decoder, K up to 60 per block: warp and CTA coefficient paths."""
+    gop = make_gop(4, 96, 64, n_frames=3, chroma=False, lam_y=30.0, residual_kw={"kmax": 60})
+    dec = hv.Decoder(96, 64, chroma=False)
+    out = hv.alloc_out(96, 64, chroma=False)
+    frames = oracle.decode_gop(gop)
+    dec.decode_iframe(hv.device_iframe(gop.iframe), out)
+    for t in range(1, 3):
+        dec.decode_pframe(hv.device_pframe(gop.pframes[t - 1]), out)
+        dec.sync()
+        assert np.abs(_planes(dec)[0] - frames[t][0][0]).max() <= TOL_RECON
+
+
 def test_pframe_config1(hv):
     src, ifr, pfr = make_config1(0)
     dec = hv.Decoder(256, 144, chroma=False)
@@ -107,10 +120,12 @@ def test_zero_flow_zero_residual_keeps_reference(hv):
     assert np.array_equal(_planes(dec)[0], before)
 
 
-@pytest.mark.parametrize("W,H,n,seed", [(160, 90, 8, 0), (203, 77, 5, 1)])
-def test_small_color_gop(hv, W, H, n, seed):
-    gop = make_gop(seed, W, H, n_frames=n)
-    dec = hv.Decoder(W, H, chroma=True)
+@pytest.mark.parametrize("W,H,n,seed,B", [(160, 90, 8, 0, 16), (203, 77, 5, 1, 16), (150, 70, 4, 2, 8),
+                                           (131, 67, 4, 3, 12)])
+def test_small_color_gop(hv, W, H, n, seed, B):
+    """B = 16 and 8 run the fused inter kernel, B = 12 the three-kernel path."""
+    gop = make_gop(seed, W, H, n_frames=n, block=B)
+    dec = hv.Decoder(W, H, chroma=True, block=B)
     out = hv.alloc_out(W, H)
     frames = oracle.decode_gop(gop)
     dec.decode_iframe(hv.device_iframe(gop.iframe), out)
