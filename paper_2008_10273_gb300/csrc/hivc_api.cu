@@ -9,9 +9,36 @@
 #include <new>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "hivc_internal.cuh"
 
 using namespace hivc;
+
+bool hivc::encode_map_2d(CUtensorMap *m, const void *base, uint64_t w, uint64_t h, uint64_t row_bytes, uint32_t box_w,
+                         uint32_t box_h)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    if (!fn || ((uintptr_t)base & 15) || (row_bytes & 15) || w < box_w || h < box_h) return false;
+    const cuuint64_t dims[2] = {w, h};
+    const cuuint64_t strides[1] = {row_bytes};
+    const cuuint32_t box[2] = {box_w, box_h};
+    const cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 namespace {
 
@@ -114,8 +141,12 @@ struct hivc_decoder {
     float *rfield[3]{}, *coef[3]{}, *acoef[3]{};
     size_t coef_cap = 0;
     uint32_t *large_list = nullptr, *ctr = nullptr;
+    float *big = nullptr;
     int large_cap = 0;
     uint32_t *flags = nullptr;
+    // tensor maps of the reference planes (per ping-pong buffer)
+    FusedMaps maps[2]{};
+    bool maps_ok = false;
     // host mirrors
     uint32_t *h_flags = nullptr;
     unsigned int *h_rnorm = nullptr;
@@ -230,7 +261,7 @@ hivc_status make_block_jobs(hivc_decoder *d, const hivc_residual *res, BlockJobs
 
 BlockScratch scratch(hivc_decoder *d)
 {
-    return BlockScratch{d->large_list, d->large_cap, d->flags, d->ctr};
+    return BlockScratch{d->large_list, d->large_cap, d->flags, d->ctr, d->big};
 }
 
 // Unfused block stage: coefficients (+ large blocks), then residual fields.
@@ -245,8 +276,6 @@ hivc_status run_block_residual(hivc_decoder *d, const hivc_residual *res)
         int l = 0;
         e = launch_block_coef(J, scratch(d), d->stream, &l);
         t.done(1);
-        d->st.kernel_launches[4] += 1;
-        d->st.launches += 1;
     }
     if (e != cudaSuccess) return HIVC_E_CUDA;
     {
@@ -318,9 +347,10 @@ size_t hivc_decoder_bytes(const hivc_config *c)
     }
     add(3 * sizeof(unsigned long long));
     add(3 * sizeof(unsigned int));
-    add((size_t)nblocks * 4);
-    add(4);
-    add(4);
+    add((size_t)nblocks * 4);          // large-block list
+    add(kCtrCount * sizeof(uint32_t)); // work counters
+    add(kBigFloats * sizeof(float));   // one K > 32 system
+    add(4);                            // error word
     return b;
 }
 
@@ -368,6 +398,7 @@ hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out)
     d->large_cap = nblocks;
     d->large_list = m.get<uint32_t>((size_t)nblocks);
     d->ctr = m.get<uint32_t>(kCtrCount);
+    d->big = m.get<float>(kBigFloats);
     d->vsum = m.get<unsigned long long>(3);
     d->rnorm = m.get<unsigned int>(3);
     d->flags = m.get<uint32_t>(1);
@@ -376,6 +407,14 @@ hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out)
         delete d;
         return HIVC_E_NOMEM;
     }
+    d->maps_ok = true;
+    for (int b = 0; b < 2; ++b)
+        for (int p = 0; p < d->np; ++p) {
+            const PlaneGeom &g = d->pg[p];
+            const uint32_t box = p == 0 ? 48 : 24;
+            d->maps_ok = d->maps_ok && encode_map_2d(&d->maps[b].ref[p], d->ref[b][p], g.w, g.h,
+                                                     (uint64_t)g.pitch * 4, box, box);
+        }
     if (cudaMallocHost(&d->h_flags, 64) != cudaSuccess) {
         m.release();
         delete d;
@@ -647,8 +686,6 @@ hivc_status hivc_decode_pframe(hivc_decoder *d, const hivc_pframe *f, const hivc
             int l = 0;
             e = launch_block_coef(J, scratch(d), d->stream, &l);
             t.done(1);
-            d->st.kernel_launches[4] += 1;
-            d->st.launches += 1;
         }
         if (e != cudaSuccess) return HIVC_E_CUDA;
         FusedFrame F{};
@@ -667,9 +704,16 @@ hivc_status hivc_decode_pframe(hivc_decoder *d, const hivc_pframe *f, const hivc
         F.chroma = d->cfg.chroma;
         F.block = d->cfg.block;
         F.ctr = d->ctr;
+        // the TMA variant needs an even luma width (16-byte flow rows) and a
+        // 16-byte aligned flow
+        FusedMaps *maps = nullptr;
+        if (d->maps_ok && d->cfg.width % 2 == 0 &&
+            encode_map_2d(&d->maps[d->cur].flow, f->flow, 2 * (uint64_t)d->cfg.width, d->cfg.height,
+                          8 * (uint64_t)d->cfg.width, 64, 32))
+            maps = &d->maps[d->cur];
         {
             Timed t(d, 7);
-            e = launch_pframe_fused(F, d->flags, d->stream);
+            e = launch_pframe_fused(F, maps, d->flags, d->stream, !d->timing);
             t.done(1);
         }
         if (e != cudaSuccess) return HIVC_E_CUDA;
@@ -750,6 +794,7 @@ hivc_status hivc_decoder_sync(hivc_decoder *d, hivc_stats *last)
     fresh.cycles = d->st.cycles;
     fresh.sweeps = d->st.sweeps;
     d->st = fresh;
+    if (fl & kFlagTimeout) return HIVC_E_TIMEOUT;
     return fl ? HIVC_E_INVALID : HIVC_OK;
 }
 
@@ -762,7 +807,7 @@ size_t hivc_block_residual_workspace_bytes(int32_t width, int32_t height, int32_
 {
     if (width < 1 || height < 1 || block < 1 || block > kMaxB || n_points < 0) return 0;
     const size_t nb = (size_t)((width + block - 1) / block) * ((height + block - 1) / block);
-    return a256(4 * (size_t)n_points) + a256(4 * nb) + a256(4 * nb) + 256 + 256;
+    return a256(4 * (size_t)n_points) + a256(4 * nb) + a256(4 * nb) + 256 + 256 + a256(4 * kBigFloats);
 }
 
 hivc_status hivc_block_residual(int32_t width, int32_t height, int32_t block, const hivc_residual *res, float *r,
@@ -786,6 +831,8 @@ hivc_status hivc_block_residual(int32_t width, int32_t height, int32_t block, co
     w += 256;
     if (cudaMemsetAsync(counters, 0, kCtrCount * sizeof(uint32_t), st) != cudaSuccess) return HIVC_E_CUDA;
     uint32_t *own_flags = reinterpret_cast<uint32_t *>(w);
+    w += 256;
+    float *big = reinterpret_cast<float *>(w);
     if (!flags) {
         flags = own_flags;
         if (cudaMemsetAsync(flags, 0, 4, st) != cudaSuccess) return HIVC_E_CUDA;
@@ -807,7 +854,7 @@ hivc_status hivc_block_residual(int32_t width, int32_t height, int32_t block, co
     B.nbx = nbx;
     B.nblocks = nb;
     J.total_blocks = nb;
-    cudaError_t e = launch_block_coef(J, BlockScratch{list, nb, flags, counters}, st, nullptr);
+    cudaError_t e = launch_block_coef(J, BlockScratch{list, nb, flags, counters, big}, st, nullptr);
     if (e == cudaSuccess) e = launch_block_eval(J, flags, st);
     return cuda_status(e);
 }

@@ -2,6 +2,7 @@
 // Host launchers are plain C++ functions (no relocatable device code).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -21,6 +22,7 @@ enum : uint32_t {
     kFlagPos = 1u << 2,       // position outside the block or not increasing
     kFlagNotSPD = 1u << 3,    // non-positive Cholesky pivot
     kFlagMaskIdx = 1u << 4,   // intra mask index out of range or not increasing
+    kFlagTimeout = 1u << 5,   // a bounded wait on tensor-memory copies gave up
 };
 
 // ---------------------------------------------------------------------------
@@ -68,18 +70,22 @@ enum : int {
     kCtrCount = 8
 };
 
+constexpr int kBigMaxK = 255;  // largest K of a 16 x 16 block
+constexpr size_t kBigFloats = (size_t)kBigMaxK * (kBigMaxK + 1) / 2 + 3 * kBigMaxK;
+
 struct BlockScratch {
     uint32_t *large_list;
     int32_t large_cap;
     uint32_t *flags;  // device error word
     uint32_t *ctr;    // kCtrCount work counters
+    float *big;       // kBigFloats: one K > 32 system at a time
 };
 
 cudaError_t ensure_block_tables();
 const BlockTables &block_tables();  // of the current device
 
-// c, a for every block: 16/32-lane segments (K <= 32) + the large-block
-// kernel (K > 32, one CTA per block).  Two launches.
+// c, a for every block: 8/16/32-lane segments (K <= 32); K > 32 by the
+// kernel's last CTA.  One launch.
 cudaError_t launch_block_coef(const BlockJobs &jobs, const BlockScratch &s, cudaStream_t st, int *launches);
 // r-field from c, a (Eq. 3 by Green's rows), r = v at the points.
 cudaError_t launch_block_eval(const BlockJobs &jobs, uint32_t *flags, cudaStream_t st);
@@ -98,8 +104,22 @@ struct FusedFrame {
     uint32_t *ctr;      // the decoder's work counters
 };
 
+// Tensor maps of the TMA variant: the frame's flow (2W x H floats, box
+// 64 x 32) and the three reference planes (box 48 x 48 luma, 24 x 24
+// chroma).
+struct FusedMaps {
+    CUtensorMap flow;
+    CUtensorMap ref[3];
+};
+
 bool fused_supported(int block);
-cudaError_t launch_pframe_fused(FusedFrame &f, uint32_t *flags, cudaStream_t st);
+cudaError_t fused_init();  // once per device
+// maps == nullptr: the variant with global loads only.  pdl: launch as a
+// programmatic dependent of the previous kernel in the stream.
+cudaError_t launch_pframe_fused(FusedFrame &f, const FusedMaps *maps, uint32_t *flags, cudaStream_t st, bool pdl);
+// 2-D float32 tensor map (no swizzle, zero fill); false if not encodable
+bool encode_map_2d(CUtensorMap *m, const void *base, uint64_t w, uint64_t h, uint64_t row_bytes, uint32_t box_w,
+                   uint32_t box_h);
 
 // ---------------------------------------------------------------------------
 // warp + add + pack (Sec. 2, 2.3)

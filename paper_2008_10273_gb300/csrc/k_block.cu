@@ -218,10 +218,8 @@ __device__ __forceinline__ void coef_quad(const BlockJobs &J, const BlockTables 
             SegBlock bb = seg_block(J, gb0 + 2 * pr + seg);
             bb.g.K = seg_k(bb);
             const int K = seg_validate<16>(bb, i, seg, S);
-            const int km = __reduce_max_sync(0xffffffffu, K);
             auto Lt = reinterpret_cast<float(*)[17]>(lts + seg * 16 * 17);
-            if (km <= 12) seg_run<16, 12>(bb, K, i, Lt, tab, S);
-            else seg_run<16, 16>(bb, K, i, Lt, tab, S);
+            seg_run<16, 16>(bb, K, i, Lt, tab, S);
         } else {
             auto Lt = reinterpret_cast<float(*)[33]>(lts);
 #pragma unroll 1
@@ -230,34 +228,16 @@ __device__ __forceinline__ void coef_quad(const BlockJobs &J, const BlockTables 
                 bb.g.K = seg_k(bb);
                 const int K = seg_validate<32>(bb, lane, 0, S);
                 if (K == 0) continue;
-                seg_run<32, 0>(bb, K, lane, Lt, tab, S);
+                if (K <= 24) seg_run<32, 24>(bb, K, lane, Lt, tab, S);
+                else seg_run<32, 0>(bb, K, lane, Lt, tab, S);
             }
         }
         __syncwarp();
     }
 }
 
-// Persistent: each warp grabs the next quad of four blocks until none is left.
-__global__ void __launch_bounds__(128, 8) block_coef_kernel(const __grid_constant__ BlockJobs J, BlockTables tab,
-                                                            BlockScratch S)
-{
-    __shared__ float lts[4][32 * 33];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t nquad = (uint32_t)(J.total_blocks + 3) / 4;
-    for (;;) {
-        uint32_t q = 0;
-        if (lane == 0) q = atomicAdd(S.ctr + kCtrCoefWork, 1u);
-        q = __shfl_sync(0xffffffffu, q, 0);
-        if (q >= nquad) break;
-        coef_quad(J, tab, S, (int)q * 4, lane, lts[warp]);
-    }
-    release_counters(S.ctr + kCtrCoefWork, S.ctr + kCtrCoefDone);
-}
-
-// ---- large blocks (K > 32): one CTA per block, packed Cholesky -----------
-constexpr int kLargeThreads = 256;
-constexpr int kLargeMaxK = 255;
-constexpr size_t kLargeSmem = sizeof(float) * ((size_t)kLargeMaxK * (kLargeMaxK + 1) / 2 + 3 * kLargeMaxK);
+// ---- large blocks (K > 32): one CTA, packed Cholesky in global scratch ----
+constexpr int kCoefThreads = 128;
 
 __device__ __forceinline__ int pk(int i, int j) { return i * (i + 1) / 2 + j; }  // j <= i
 
@@ -268,116 +248,137 @@ __device__ __forceinline__ float cta_sum(float v, float *red)
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     float t = 0.f;
-    for (int k = 0; k < kLargeThreads / 32; ++k) t += red[k];
+    for (int k = 0; k < kCoefThreads / 32; ++k) t += red[k];
     return t;
 }
 
-// The coefficient stage lists the K > 32 blocks; each CTA solves list
-// entries blockIdx.x, blockIdx.x + gridDim.x, ...  The last CTA to finish
-// clears the list counter for the next frame (no spin: a done counter).
-__global__ void __launch_bounds__(kLargeThreads) block_large_kernel(const __grid_constant__ BlockJobs J,
-                                                                    BlockTables tab, BlockScratch S)
+// One block with K > 32 by the whole CTA: G_PP packed in S.big (global),
+// right-hand sides in S.big after it.  Same arithmetic as seg_block_coef.
+__device__ __noinline__ void cta_large_solve(const BlockJobs &J, const BlockTables &tab, const BlockScratch &S, int gb,
+                                unsigned char *s_p, float *red, int *s_bad)
 {
-    extern __shared__ float sm[];
-    __shared__ float red[kLargeThreads / 32];
-    __shared__ int s_bad;
-    __shared__ unsigned char s_p[kLargeMaxK];
     const int tid = threadIdx.x;
-    const uint32_t count = min(*(volatile uint32_t *)(S.ctr + kCtrLargeCount), (uint32_t)S.large_cap);
-    for (uint32_t it = blockIdx.x; it < count; it += gridDim.x) {
-        const int gb = (int)S.large_list[it];
-        const BlockPlane &P = J.p[find_job(J, gb)];
-        const BlockGeom g = block_geom(P, gb - P.block_base);
-        const int K = g.K;
-        const bool two = P.val[1] != nullptr;
-        float *L = sm;
-        float *b = sm + (size_t)K * (K + 1) / 2;  // b[r*K + i]
-        if (tid == 0) s_bad = 0;
+    const BlockPlane &P = J.p[find_job(J, gb)];
+    const BlockGeom g = block_geom(P, gb - P.block_base);
+    const int K = g.K;
+    const bool two = P.val[1] != nullptr;
+    float *L = S.big;
+    float *b = S.big + (size_t)kBigMaxK * (kBigMaxK + 1) / 2;  // b[r*K + i]
+    if (tid == 0) *s_bad = 0;
+    __syncthreads();
+    for (int j = tid; j < K; j += kCoefThreads) {
+        int p;
+        if (!load_pos(P, g, j, p)) *s_bad = 1;
+        s_p[j] = (unsigned char)p;
+        b[j] = (float)__ldg(P.val[0] + g.s + j);
+        b[K + j] = two ? (float)__ldg(P.val[1] + g.s + j) : 0.f;
+        b[2 * K + j] = 1.f;
+    }
+    __syncthreads();
+    if (*s_bad) {
+        if (tid == 0) atomicOr(S.flags, kFlagPos);
         __syncthreads();
-        for (int j = tid; j < K; j += kLargeThreads) {
-            int p;
-            if (!load_pos(P, g, j, p)) s_bad = 1;
-            s_p[j] = (unsigned char)p;
-            b[j] = (float)__ldg(P.val[0] + g.s + j);
-            b[K + j] = two ? (float)__ldg(P.val[1] + g.s + j) : 0.f;
-            b[2 * K + j] = 1.f;
-        }
+        return;
+    }
+    const float *G = green_rows(tab, g.w, g.h);
+    const int rl = g_rowlen(g.w * g.h);
+    for (int i = tid; i < K; i += kCoefThreads)
+        for (int j = 0; j <= i; ++j) L[pk(i, j)] = __ldg(G + s_p[i] * rl + s_p[j]);
+    __syncthreads();
+    bool spd = true;
+    for (int k = 0; k < K; ++k) {
+        const float d = L[pk(k, k)];
+        spd = spd && d > 0.f;
+        const float isd = rsqrtf(fmaxf(d, 1e-30f));
         __syncthreads();
-        if (s_bad) {
-            if (tid == 0) atomicOr(S.flags, kFlagPos);
-            __syncthreads();
-            continue;
-        }
-        const float *G = green_rows(tab, g.w, g.h);
-        const int rl = g_rowlen(g.w * g.h);
-        for (int i = tid; i < K; i += kLargeThreads)
-            for (int j = 0; j <= i; ++j) L[pk(i, j)] = __ldg(G + (size_t)s_p[i] * rl + s_p[j]);
+        if (tid == 0) L[pk(k, k)] = d * isd;
+        for (int i = k + 1 + tid; i < K; i += kCoefThreads) L[pk(i, k)] *= isd;
         __syncthreads();
-        bool spd = true;
-        for (int k = 0; k < K; ++k) {
-            const float d = L[pk(k, k)];
-            spd = spd && d > 0.f;
-            const float sd = sqrtf(fmaxf(d, 1e-30f)), isd = 1.0f / sd;
-            __syncthreads();
-            if (tid == 0) L[pk(k, k)] = sd;
-            for (int i = k + 1 + tid; i < K; i += kLargeThreads) L[pk(i, k)] *= isd;
-            __syncthreads();
-            for (int i = k + 1 + tid; i < K; i += kLargeThreads) {
-                const float lik = L[pk(i, k)];
-                for (int j = k + 1; j <= i; ++j) L[pk(i, j)] = fmaf(-lik, L[pk(j, k)], L[pk(i, j)]);
-            }
-            __syncthreads();
-        }
-        // forward L y = b (three right-hand sides)
-        for (int k = 0; k < K; ++k) {
-            if (tid < 3) b[tid * K + k] /= L[pk(k, k)];
-            __syncthreads();
-            for (int i = k + 1 + tid; i < K; i += kLargeThreads) {
-                const float l = L[pk(i, k)];
-                b[i] = fmaf(-l, b[k], b[i]);
-                b[K + i] = fmaf(-l, b[K + k], b[K + i]);
-                b[2 * K + i] = fmaf(-l, b[2 * K + k], b[2 * K + i]);
-            }
-            __syncthreads();
-        }
-        // a = (y_1 . y_v) / (y_1 . y_1), then L^T c = y_v - a y_1
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-        for (int i = tid; i < K; i += kLargeThreads) {
-            const float y2 = b[2 * K + i];
-            s0 += y2 * b[i];
-            s1 += y2 * b[K + i];
-            s2 += y2 * y2;
-        }
-        s2 = cta_sum(s2, red);
-        const float a0 = cta_sum(s0, red) / s2, a1 = cta_sum(s1, red) / s2;
-        __syncthreads();
-        for (int i = tid; i < K; i += kLargeThreads) {
-            b[i] = fmaf(-a0, b[2 * K + i], b[i]);
-            b[K + i] = fmaf(-a1, b[2 * K + i], b[K + i]);
-        }
-        __syncthreads();
-        for (int k = K - 1; k >= 0; --k) {
-            if (tid < 2) b[tid * K + k] /= L[pk(k, k)];
-            __syncthreads();
-            for (int i = tid; i < k; i += kLargeThreads) {
-                const float l = L[pk(k, i)];
-                b[i] = fmaf(-l, b[k], b[i]);
-                b[K + i] = fmaf(-l, b[K + k], b[K + i]);
-            }
-            __syncthreads();
-        }
-        for (int i = tid; i < K; i += kLargeThreads) {
-            P.coef[0][g.s + i] = b[i];
-            if (two) P.coef[1][g.s + i] = b[K + i];
-        }
-        if (tid == 0) {
-            P.acoef[0][g.lb] = a0;
-            if (two) P.acoef[1][g.lb] = a1;
-            if (!spd) atomicOr(S.flags, kFlagNotSPD);
+        for (int i = k + 1 + tid; i < K; i += kCoefThreads) {
+            const float lik = L[pk(i, k)];
+            for (int j = k + 1; j <= i; ++j) L[pk(i, j)] = fmaf(-lik, L[pk(j, k)], L[pk(i, j)]);
         }
         __syncthreads();
     }
-    release_counters(S.ctr + kCtrLargeCount, S.ctr + kCtrLargeDone);
+    for (int k = 0; k < K; ++k) {  // forward L y = b (three right-hand sides)
+        if (tid < 3) b[tid * K + k] /= L[pk(k, k)];
+        __syncthreads();
+        for (int i = k + 1 + tid; i < K; i += kCoefThreads) {
+            const float l = L[pk(i, k)];
+            b[i] = fmaf(-l, b[k], b[i]);
+            b[K + i] = fmaf(-l, b[K + k], b[K + i]);
+            b[2 * K + i] = fmaf(-l, b[2 * K + k], b[2 * K + i]);
+        }
+        __syncthreads();
+    }
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;  // a = (y_1 . y_v) / (y_1 . y_1)
+    for (int i = tid; i < K; i += kCoefThreads) {
+        const float y2 = b[2 * K + i];
+        s0 += y2 * b[i];
+        s1 += y2 * b[K + i];
+        s2 += y2 * y2;
+    }
+    s2 = cta_sum(s2, red);
+    const float a0 = cta_sum(s0, red) / s2, a1 = cta_sum(s1, red) / s2;
+    __syncthreads();
+    for (int i = tid; i < K; i += kCoefThreads) {
+        b[i] = fmaf(-a0, b[2 * K + i], b[i]);
+        b[K + i] = fmaf(-a1, b[2 * K + i], b[K + i]);
+    }
+    __syncthreads();
+    for (int k = K - 1; k >= 0; --k) {  // backward L^T c = y_v - a y_1
+        if (tid < 2) b[tid * K + k] /= L[pk(k, k)];
+        __syncthreads();
+        for (int i = tid; i < k; i += kCoefThreads) {
+            const float l = L[pk(k, i)];
+            b[i] = fmaf(-l, b[k], b[i]);
+            b[K + i] = fmaf(-l, b[K + k], b[K + i]);
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < K; i += kCoefThreads) {
+        P.coef[0][g.s + i] = b[i];
+        if (two) P.coef[1][g.s + i] = b[K + i];
+    }
+    if (tid == 0) {
+        P.acoef[0][g.lb] = a0;
+        if (two) P.acoef[1][g.lb] = a1;
+        if (!spd) atomicOr(S.flags, kFlagNotSPD);
+    }
+    __syncthreads();
+}
+
+// Coefficient stage: warp w of CTA c solves quad 4c + w (blocks 16c + 4w ..
+// +3).  Blocks with K > 32 are listed; the last CTA to finish solves them
+// and clears the list (a done counter, no waiting).
+__global__ void __launch_bounds__(kCoefThreads, 7) block_coef_kernel(const __grid_constant__ BlockJobs J,
+                                                                     BlockTables tab, BlockScratch S)
+{
+    __shared__ float lts[4][32 * 33];
+    __shared__ unsigned char s_p[kBigMaxK];
+    __shared__ float red[kCoefThreads / 32];
+    __shared__ int s_last, s_bad;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the fused kernel that follows may start its prologue (tensor-memory
+    // copies of flow and references) now; it waits for this grid's results
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int gb0 = (blockIdx.x * 4 + warp) * 4;
+    if (gb0 < J.total_blocks) coef_quad(J, tab, S, gb0, lane, lts[warp]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(S.ctr + kCtrCoefDone, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const uint32_t n = min(*(volatile uint32_t *)(S.ctr + kCtrLargeCount), (uint32_t)S.large_cap);
+    for (uint32_t it = 0; it < n; ++it) cta_large_solve(J, tab, S, (int)S.large_list[it], s_p, red, &s_bad);
+    if (threadIdx.x == 0) {
+        S.ctr[kCtrLargeCount] = 0;
+        S.ctr[kCtrCoefDone] = 0;
+        __threadfence();
+    }
 }
 
 // ---- evaluation stage into residual fields, one warp per block -----------
@@ -452,10 +453,8 @@ cudaError_t ensure_block_tables()
     BlockTables t{};
     if ((e = cudaGetSymbolAddress((void **)&t.G, d_G)) != cudaSuccess) return e;
     if ((e = cudaGetSymbolAddress((void **)&t.goff, d_goff)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(block_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kLargeSmem)) != cudaSuccess)
-        return e;
     if ((e = cudaDeviceGetAttribute(&t.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = fused_init()) != cudaSuccess) return e;
     g_tabs[dev] = t;
     g_tab_devices |= 1ull << dev;
     return cudaSuccess;
@@ -471,17 +470,8 @@ const BlockTables &block_tables()
 cudaError_t launch_block_coef(const BlockJobs &jobs, const BlockScratch &s, cudaStream_t st, int *launches)
 {
     if (jobs.total_blocks == 0) return cudaSuccess;
-    const BlockTables &t = block_tables();
-    static int per_sm = 0;
-    if (per_sm == 0 &&
-        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, block_coef_kernel, 128, 0) != cudaSuccess || per_sm < 1))
-        per_sm = 1;
-    const int grid = std::max(1, std::min(t.sms * per_sm, (jobs.total_blocks + 15) / 16));
-    block_coef_kernel<<<grid, 128, 0, st>>>(jobs, t, s);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    block_large_kernel<<<t.sms, kLargeThreads, kLargeSmem, st>>>(jobs, t, s);
-    if (launches) *launches += 2;
+    block_coef_kernel<<<(jobs.total_blocks + 15) / 16, kCoefThreads, 0, st>>>(jobs, block_tables(), s);
+    if (launches) *launches += 1;
     return cudaGetLastError();
 }
 
