@@ -77,6 +77,21 @@ def make_workload(a, rank=0):
     return make_gop(a.seed + rank, a.width, a.height, n_frames=a.frames)
 
 
+def replica_value(local_ms, frames_per_rank, px_scale, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas: every rank decoded
+    ``frames_per_rank`` frames in ``local_ms``; the job time is the max over
+    ranks (the only collective), the value the frames of all ranks over it."""
+    import torch
+
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    world = 1
+    if dist is not None and dist.is_initialized():
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        world = dist.get_world_size()
+    ms = float(t.item())
+    return world * frames_per_rank * px_scale / (ms / 1e3), ms
+
+
 def src_sha(path):
     with open(path, "rb") as fh:
         return hashlib.sha1(fh.read()).hexdigest()[:12]
@@ -269,13 +284,8 @@ def main(argv=None):
     frame_ms = []
     for e in ev:
         frame_ms += [e[i].elapsed_time(e[i + 1]) for i in range(nfr)]
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
     px_scale = W * H / FULLHD_PX
-    value = world * a.steps * nfr * px_scale / (total_ms / 1e3)
+    value, total_ms = replica_value(sum(step_ms), a.steps * nfr, px_scale, dist, "cuda")
 
     # roofline of the dominant kernel family (kernel-timing pass)
     fam_ms = list(kstats.kernel_ms)
@@ -360,11 +370,7 @@ def main(argv=None):
         e1.record(stream)
         torch.cuda.synchronize()
         dec.sync()
-    e2e_ms = e0.elapsed_time(e1)
-    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * a.e2e_steps * nfr * px_scale / (float(t.item()) / 1e3)
+    e2e_value, _ = replica_value(e0.elapsed_time(e1), a.e2e_steps * nfr, px_scale, dist, "cuda")
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
