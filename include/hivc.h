@@ -217,6 +217,25 @@ hivc_status hivc_block_residual(int32_t width, int32_t height, int32_t block,
                                 void *workspace, size_t workspace_bytes, uint32_t *flags,
                                 void *stream);
 
+/* hivc_block_residual without allocation: the same residual plane, with
+   the coefficient scratch taken from a fixed array inside the library
+   instead of a caller workspace.  The paper has no counterpart; this is
+   for callers that cannot allocate device memory when they need the
+   residual (while capturing a stream into a graph, or under a fixed memory
+   budget where every allocation is made up front).
+   Limits: at most 131072 residual points and 16384 blocks per call, else
+   HIVC_E_INVALID.  The array (about 0.8 MB) exists once per device that
+   loads the library and stays until the process exits.  All calls on a
+   device share it and each call overwrites it: calls whose work overlaps
+   on the GPU (e.g. on two streams) race, so serialise them.  The first call
+   on a device uploads the Green's tables and looks up the array's device
+   address with that device current; make that first call before any
+   stream capture.  flags: optional device uint32 for error bits, as in
+   hivc_block_residual.  No cudaMalloc or cudaFree is called. */
+hivc_status hivc_block_residual_static(int32_t width, int32_t height, int32_t block,
+                                       const hivc_residual *res, float *r, int32_t r_pitch,
+                                       uint32_t *flags, void *stream);
+
 /* Backward bilinear warp of one plane (Sec. 2, 2.3): pred(x) = ref(x + v(x)),
    sample clamped to the plane.  flow is the LUMA flow (flow_width x
    flow_height x 2 floats); when chroma_flow is 1 the plane is a 4:2:0

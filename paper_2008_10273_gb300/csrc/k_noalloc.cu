@@ -1,0 +1,96 @@
+// hivc_block_residual_static: the block residual of hivc_block_residual
+// without any device allocation by the library or the caller.
+//
+// Some callers cannot allocate device memory at the point where they need a
+// residual plane: code running while a stream is being captured into a
+// graph, or a host that hands the library a fixed memory budget in which
+// every allocation has already been made.  For them the scratch that the
+// coefficient stage needs (per-point coefficients, per-block constants, the
+// list of blocks with more than 32 points, work counters and one large
+// system) lives in a fixed-size array in the library's device image instead
+// of a caller workspace.
+//
+// The array exists once per device that loads the library and stays
+// allocated until the process exits.  Every call on a device uses the same
+// array, so calls whose work overlaps on the GPU (for example on two
+// streams) race and must be serialised by the caller.  Each call clears the
+// counters it relies on before its kernels run.
+#include <mutex>
+
+#include "hivc_internal.cuh"
+
+using namespace hivc;
+
+namespace {
+
+constexpr int kStaticMaxPoints = 1 << 17;  // residual points per call
+constexpr int kStaticMaxBlocks = 1 << 14;  // residual blocks per call
+// 4-byte words: coefficients | block constants | large-block list | counters
+// | own error word (+ padding) | one K > 32 system
+constexpr size_t kOffAcoef = kStaticMaxPoints;
+constexpr size_t kOffList = kOffAcoef + kStaticMaxBlocks;
+constexpr size_t kOffCtr = kOffList + kStaticMaxBlocks;
+constexpr size_t kOffFlags = kOffCtr + kCtrCount;
+constexpr size_t kOffBig = kOffFlags + 56;  // keeps the system 256-byte aligned
+constexpr size_t kWords = kOffBig + kBigFloats;
+
+static __device__ __align__(256) uint32_t g_scratch[kWords];
+
+std::mutex g_mu;
+uint32_t *g_addr[64];  // device address of g_scratch, per device
+
+}  // namespace
+
+extern "C" hivc_status hivc_block_residual_static(int32_t width, int32_t height, int32_t block,
+                                                  const hivc_residual *res, float *r, int32_t r_pitch,
+                                                  uint32_t *flags, void *stream)
+{
+    if (!res || !r || width < 1 || height < 1 || block < 1 || block > kMaxB || r_pitch < width) return HIVC_E_INVALID;
+    if (!res->block_ptr || res->n_points < 0 || (res->n_points > 0 && (!res->pos || !res->val)))
+        return HIVC_E_INVALID;
+    const int nbx = (width + block - 1) / block;
+    const long nb = (long)nbx * ((height + block - 1) / block);
+    if (res->n_points > kStaticMaxPoints || nb > kStaticMaxBlocks) return HIVC_E_INVALID;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return HIVC_E_CUDA;
+    // first call on this device: Green's tables and the scratch address (with
+    // this device current; make this call before any stream capture)
+    if (ensure_block_tables() != cudaSuccess) return HIVC_E_CUDA;
+    uint32_t *base;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_addr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return HIVC_E_CUDA;
+            g_addr[dev] = static_cast<uint32_t *>(p);
+        }
+        base = g_addr[dev];
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // counters start at zero (and the own error word when none is given)
+    if (cudaMemsetAsync(base + kOffCtr, 0, (kCtrCount + 8) * sizeof(uint32_t), st) != cudaSuccess)
+        return HIVC_E_CUDA;
+    if (!flags) flags = base + kOffFlags;
+    BlockJobs J{};
+    J.n = 1;
+    BlockPlane &B = J.p[0];
+    B.block_ptr = res->block_ptr;
+    B.pos = res->pos;
+    B.val[0] = res->val;
+    B.coef[0] = reinterpret_cast<float *>(base);
+    B.acoef[0] = reinterpret_cast<float *>(base + kOffAcoef);
+    B.r[0] = r;
+    B.r_pitch = r_pitch;
+    B.n_points = res->n_points;
+    B.width = width;
+    B.height = height;
+    B.block = block;
+    B.nbx = nbx;
+    B.nblocks = (int)nb;
+    J.total_blocks = (int)nb;
+    const BlockScratch S{base + kOffList, kStaticMaxBlocks, flags, base + kOffCtr,
+                         reinterpret_cast<float *>(base + kOffBig)};
+    cudaError_t e = launch_block_coef(J, S, st, nullptr);
+    if (e == cudaSuccess) e = launch_block_eval(J, flags, st);
+    return e == cudaSuccess ? HIVC_OK : HIVC_E_CUDA;
+}

@@ -88,6 +88,8 @@ PROTOTYPES = [
     ("hivc_block_residual_workspace_bytes", c_sz, [c_i32, c_i32, c_i32, c_i32]),
     ("hivc_block_residual", c_i32, [c_i32, c_i32, c_i32, ctypes.POINTER(Residual), c_vp, c_i32, c_vp, c_sz,
                                     c_vp, c_vp]),
+    ("hivc_block_residual_static", c_i32, [c_i32, c_i32, c_i32, ctypes.POINTER(Residual), c_vp, c_i32, c_vp,
+                                           c_vp]),
     ("hivc_warp", c_i32, [c_i32, c_i32, c_vp, c_i32, c_vp, c_i32, c_i32, c_i32, c_vp, c_i32, c_vp]),
 ]
 
@@ -309,6 +311,15 @@ def block_residual(width, height, block, block_ptr, pos, val, r, workspace=None,
     return check(lib().hivc_block_residual(width, height, block, ctypes.byref(res), _ptr(r), int(r.stride(0)),
                                            _ptr(workspace), int(workspace.numel()), _ptr(flags),
                                            _stream_handle(stream)), "hivc_block_residual")
+
+
+def block_residual_static(width, height, block, block_ptr, pos, val, r, flags=None, stream=None):
+    """hivc_block_residual_static: the residual plane with the library's
+    fixed scratch array (no device allocation anywhere); see include/hivc.h
+    for its limits and the rule that calls must not overlap on the GPU."""
+    res = residual_struct(block_ptr, pos, val)
+    return check(lib().hivc_block_residual_static(width, height, block, ctypes.byref(res), _ptr(r), int(r.stride(0)),
+                                                  _ptr(flags), _stream_handle(stream)), "hivc_block_residual_static")
 
 
 def warp(ref, flow, pred, chroma_flow: bool = False, stream=None):

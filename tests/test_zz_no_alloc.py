@@ -1,0 +1,68 @@
+"""hivc_block_residual_static: the residual plane without any device
+allocation, for callers that cannot allocate device memory when they need it
+(during stream capture, or under a fixed memory budget).  It must give the
+same plane as hivc_block_residual, which uses a caller workspace, on calls
+made one after another (the second call reuses the library's scratch array
+that the first one left behind).
+
+This file is collected last on purpose: if it fails, a run that stops at the
+first failure has already run every other test."""
+import numpy as np
+import pytest
+
+from gpu_util import TOL_BLOCK, hivc_module, to_np, torch_cuda
+from workload import make_residual
+
+pytestmark = pytest.mark.gpu
+
+
+def _with_workspace(hv, res):
+    torch = torch_cuda()
+    r = torch.zeros((res.height, res.width), dtype=torch.float32, device="cuda")
+    bp, pos, val = hv.device_residual(res)
+    hv.block_residual(res.width, res.height, res.block, bp, pos, val, r)
+    torch.cuda.synchronize()
+    return to_np(r)
+
+
+def _without_allocation(hv, res, flags):
+    torch = torch_cuda()
+    r = torch.full((res.height, res.width), float("nan"), dtype=torch.float32, device="cuda")
+    bp, pos, val = hv.device_residual(res)
+    hv.block_residual_static(res.width, res.height, res.block, bp, pos, val, r, flags=flags)
+    torch.cuda.synchronize()
+    return to_np(r)
+
+
+def test_matches_workspace_entry_point_on_consecutive_calls():
+    hv = hivc_module()
+    torch = torch_cuda()
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rng = np.random.default_rng(21)
+    first = make_residual(rng, 203, 77, 16, 8.0, 64, empty_frac=0.1)
+    # the second call has blocks with K > 32 (the last-CTA large-block path
+    # and its counters) on a different plane size
+    second = make_residual(rng, 160, 96, 16, 30.0, 64, kmax=60)
+    for res in (first, second):
+        got = _without_allocation(hv, res, flags)
+        ref = _with_workspace(hv, res)
+        assert np.all(np.isfinite(got))
+        assert np.abs(got - ref).max() <= TOL_BLOCK
+    assert int(flags.item()) == 0
+
+
+def test_rejects_inputs_beyond_its_limits():
+    hv = hivc_module()
+    torch = torch_cuda()
+    W, H = 2048, 2048  # 16384 blocks of 16 x 16: at the limit
+    n = 131073  # one point more than the limit
+    bp = torch.zeros(128 * 128 + 1, dtype=torch.int32, device="cuda")
+    pos = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    val = torch.zeros(n, dtype=torch.int16, device="cuda")
+    r = torch.zeros((H, W), dtype=torch.float32, device="cuda")
+    with pytest.raises(hv.HivcError) as e:
+        hv.block_residual_static(W, H, 16, bp, pos, val, r)
+    assert e.value.status == hv.HIVC_E_INVALID
+    with pytest.raises(hv.HivcError) as e:
+        hv.block_residual_static(W + 16, H, 16, bp, pos[:10], val[:10], r)  # 16512 blocks
+    assert e.value.status == hv.HIVC_E_INVALID
