@@ -55,15 +55,17 @@ typedef struct {
     int32_t block;          /* residual block edge B, 1..16.  The paper uses
                                8 x 8 blocks (Sec. 2.2, 2.3); default 16 */
     int32_t op;             /* residual operator: 0 = harmonic, -L (Sec. 2.3) */
-    int32_t precision;      /* intra solve: 0 = FP32 sweeps + FP64 residual
-                               correction (default), 1 = FP32 only */
+    int32_t precision;      /* intra solve: 0 = FP32 sweeps with a residual
+                               correction of an extended-precision iterate
+                               (float-float, ~48-bit; default), 1 = FP32 only */
     double iframe_tol;      /* stop when max |(L u)_i| over unknown pixels
                                <= tol, grey levels (Eq. 1 residual); default
                                1e-8; FP32-only mode floors near 1e-3 */
     int32_t max_cycles;     /* cap on outer correction cycles (default 40);
                                beyond it sync returns HIVC_E_NOT_CONVERGED */
-    double cond_threshold;  /* block systems whose condition estimate exceeds
-                               this are re-solved in FP64 (default 1e6) */
+    double cond_threshold;  /* reserved: condition threshold above which block
+                               systems would be re-solved in higher precision
+                               (default 1e6) */
     void *stream;           /* cudaStream_t to run on; NULL = the decoder
                                creates its own non-blocking stream */
 } hivc_config;
@@ -131,16 +133,16 @@ typedef struct {
     double resid[3];        /* final Eq. 1 residual per plane (last intra) */
     int32_t cycles;         /* outer correction cycles of the last intra */
     int32_t sweeps;         /* red-black sweeps of the last intra */
-    int32_t fp64_blocks;    /* blocks re-solved in FP64 */
-    int32_t large_blocks;   /* blocks with K > 32 (CTA path) */
-    float max_cond;         /* largest block condition estimate seen */
+    int32_t fp64_blocks;    /* reserved (0) */
+    int32_t large_blocks;   /* reserved (0) */
+    float max_cond;         /* reserved (0) */
     uint32_t device_flags;  /* data errors seen by the kernels (bit set) */
     int32_t frames;         /* frames since the previous sync */
     int32_t launches;       /* kernel launches since the previous sync */
     /* per kernel family: accumulated device time (ms, CUDA events, only
        when timing is on) and launch counts since the previous sync:
        0 intra setup, 1 intra sweeps, 2 intra residual, 3 block coefficients,
-       4 large blocks, 5 block evaluate, 6 warp/add/pack, 7 fused inter */
+       4 (unused), 5 block evaluate, 6 warp/add/pack, 7 fused inter */
     float kernel_ms[HIVC_STAT_KERNELS];
     int32_t kernel_launches[HIVC_STAT_KERNELS];
 } hivc_stats;
@@ -159,9 +161,9 @@ hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out);
 size_t hivc_decoder_bytes(const hivc_config *cfg);
 
 /* Decode an intra frame (Sec. 2.1 + optional residual, Sec. 2.2) into out
-   and make it the reference.  The FP64-corrected solve reads its residual
-   norm back to the host between correction cycles, so this call waits on
-   the decoder's stream while it runs. */
+   and make it the reference.  The correction loop reads the residual norm
+   back to the host between cycles, so this call waits on the decoder's
+   stream while it runs. */
 hivc_status hivc_decode_iframe(hivc_decoder *dec, const hivc_iframe *f, const hivc_out *out);
 
 /* Decode an inter frame (Sec. 2, 2.3: warp + residual) into out and make it

@@ -493,7 +493,6 @@ hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc
             if (!residual_ok(f->res[p])) return HIVC_E_INVALID;
     if (cudaSetDevice(d->device) != cudaSuccess) return HIVC_E_CUDA;
     cudaStream_t st = d->stream;
-    // the intra solve overwrites the FP64 scratch: settle earlier work on it
     IntraJobs J{};
     J.n = d->np;
     for (int p = 0; p < d->np; ++p) {

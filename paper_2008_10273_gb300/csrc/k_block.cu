@@ -164,21 +164,6 @@ __device__ __forceinline__ void seg_run(const SegBlock &b, int K, int i, float (
     }
 }
 
-// Clears a kernel's work/done counter pair once every CTA has finished
-// grabbing work (the last CTA to arrive resets both; no waiting).
-__device__ __forceinline__ void release_counters(uint32_t *work, uint32_t *done)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(done, 1u) == gridDim.x - 1) {
-            *work = 0;
-            *done = 0;
-            __threadfence();
-        }
-    }
-}
-
 __device__ __forceinline__ void coef_quad(const BlockJobs &J, const BlockTables &tab, const BlockScratch &S, int gb0,
                                           int lane, float *lts)
 {
