@@ -33,10 +33,11 @@ constexpr int kRW = 128, kRH = 64;      // staged region
 constexpr int kTX = kRW - 2 * kHL;      // 112 output columns
 constexpr int kTY = kRH - 2 * kHL;      // 48 output rows
 constexpr int kHW = kRW / 2;            // cells per colour and row
-constexpr int kTY_THREADS = 8;          // thread rows; each thread owns kRH/8 rows
+constexpr int kTY_THREADS = 8;          // thread rows; each thread owns kRH/8 consecutive rows
 constexpr int kRows = kRH / kTY_THREADS;
 
 constexpr int kResThreads = 256;
+constexpr int kRTW = 64, kRTH = 16;  // residual tile
 
 __device__ __forceinline__ int find_plane(const IntraJobs &J, int t)
 {
@@ -112,75 +113,89 @@ __global__ void intra_scatter_kernel(const __grid_constant__ IntraJobs J)
 }
 
 // u_out = u_in + e (unknown pixels; float-float), res = (L u_out)_i, and the
-// max |res| per plane.  Persistent grid: each CTA walks rows of all planes.
+// max |res| per plane.  A 64 x 16 tile with a one-pixel halo is updated once
+// per cell into shared memory; the residual reads the updated neighbours
+// from there.
 __global__ void __launch_bounds__(kResThreads) intra_residual_kernel(const __grid_constant__ IntraJobs J, int e_in,
                                                                      int add_e)
 {
+    __shared__ float sh[kRTH + 2][kRTW + 2], sl[kRTH + 2][kRTW + 2];
     __shared__ float red[kResThreads / 32];
-    for (int pl = 0; pl < J.n; ++pl) {
-        const IntraPlane &P = J.p[pl];
-        const int W = P.width, H = P.height, pitch = P.pitch;
-        const float *uh = P.uh[0], *ul = P.ul[0];
-        const float *e = P.e[e_in];
-        const bool ff = P.ff != 0;
-        float rmax = 0.f;
-        const long total = (long)H * W;
-        for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
-            const int y = (int)(k / W), x = (int)(k - (long)y * W);
-            const size_t i = (size_t)y * pitch + x;
-            auto get = [&](size_t j, float &h, float &l) {
-                h = uh[j];
-                l = ff ? ul[j] : 0.f;
-                if (add_e) {
-                    const float d = e[j];
-                    if (ff) ff_add(h, l, d, h, l);
-                    else h = __fadd_rn(h, d);
-                }
-            };
-            float ch, cl;
-            get(i, ch, cl);
+    const IntraPlane &P = J.p[find_plane(J, blockIdx.x)];
+    const int lt = blockIdx.x - P.tile_base;
+    const int x0 = (lt % P.tiles_x) * kRTW, y0 = (lt / P.tiles_x) * kRTH;
+    const int W = P.width, H = P.height, pitch = P.pitch;
+    const float *uh = P.uh[0], *ul = P.ul[0];
+    const float *e = P.e[e_in];
+    const bool ff = P.ff != 0;
+    for (int k = threadIdx.x; k < (kRTH + 2) * (kRTW + 2); k += kResThreads) {
+        const int ly = k / (kRTW + 2), lx = k - ly * (kRTW + 2);
+        const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+        float h = 0.f, l = 0.f;
+        if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+            const int i = gy * pitch + gx;
+            h = uh[i];
+            l = ff ? ul[i] : 0.f;
             if (add_e) {
-                P.uh[1][i] = ch;
-                if (ff) P.ul[1][i] = cl;
+                const float d = e[i];  // zero on the mask
+                if (ff) ff_add(h, l, d, h, l);
+                else h = __fadd_rn(h, d);
+                if (lx >= 1 && lx <= kRTW && ly >= 1 && ly <= kRTH) {
+                    P.uh[1][i] = h;
+                    if (ff) P.ul[1][i] = l;
+                }
             }
-            float r = 0.f;
-            if (!P.mask[i]) {
-                // sum_j (h_j - h_i) exactly as float-float, plus the lo parts
-                float S = 0.f, E = 0.f, tail = 0.f;
-                auto acc = [&](size_t j) {
-                    float h, l, d, de, s2, e2;
-                    get(j, h, l);
-                    two_sum(h, -ch, d, de);
-                    two_sum(S, d, s2, e2);
-                    S = s2;
-                    E = __fadd_rn(E, __fadd_rn(e2, de));
-                    tail = __fadd_rn(tail, __fsub_rn(l, cl));
-                };
-                if (x > 0) acc(i - 1);
-                if (x < W - 1) acc(i + 1);
-                if (y > 0) acc(i - pitch);
-                if (y < H - 1) acc(i + pitch);
-                r = __fadd_rn(S, __fadd_rn(E, tail));
-            }
-            P.res[i] = r;
-            rmax = fmaxf(rmax, fabsf(r));
         }
-        for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rmax;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            float m = 0.f;
-            for (int w = 0; w < kResThreads / 32; ++w) m = fmaxf(m, red[w]);
-            if (m > 0.f) atomicMax(P.rnorm, __float_as_uint(m));  // non-negative floats order like their bits
+        sh[ly][lx] = h;
+        sl[ly][lx] = l;
+    }
+    __syncthreads();
+    float rmax = 0.f;
+    for (int k = threadIdx.x; k < kRTH * kRTW; k += kResThreads) {
+        const int ly = k / kRTW, lx = k - ly * kRTW;
+        const int gx = x0 + lx, gy = y0 + ly;
+        if (gx >= W || gy >= H) continue;
+        const int i = gy * pitch + gx;
+        float r = 0.f;
+        if (!P.mask[i]) {
+            // sum_j (h_j - h_i) exactly as float-float, plus the lo parts
+            const float ch = sh[ly + 1][lx + 1], cl = sl[ly + 1][lx + 1];
+            float S = 0.f, E = 0.f, tail = 0.f;
+            auto acc = [&](int yy, int xx) {
+                float d, de, s2, e2;
+                two_sum(sh[yy][xx], -ch, d, de);
+                two_sum(S, d, s2, e2);
+                S = s2;
+                E = __fadd_rn(E, __fadd_rn(e2, de));
+                tail = __fadd_rn(tail, __fsub_rn(sl[yy][xx], cl));
+            };
+            if (gx > 0) acc(ly + 1, lx);
+            if (gx < W - 1) acc(ly + 1, lx + 2);
+            if (gy > 0) acc(ly, lx + 1);
+            if (gy < H - 1) acc(ly + 2, lx + 1);
+            r = __fadd_rn(S, __fadd_rn(E, tail));
         }
-        __syncthreads();
+        P.res[i] = r;
+        rmax = fmaxf(rmax, fabsf(r));
+    }
+    for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < kResThreads / 32; ++w) m = fmaxf(m, red[w]);
+        if (m > 0.f) atomicMax(P.rnorm, __float_as_uint(m));  // non-negative floats order like their bits
     }
 }
 
 // S red-black SOR sweeps on (-L_UU) e = res in a shared-memory tile.
-// Thread (tx, ty) owns the cell pair hx = tx (columns 2tx, 2tx+1) in rows
-// ty + 8k; within a half sweep all its cells of one colour sit at the same
-// column offset b, so per-cell coefficients stay in registers.
+// Thread (hx, ty) owns the cell pair hx (columns 2hx, 2hx+1) in the eight
+// consecutive rows 8 ty .. 8 ty + 7.  Its cells' values stay in registers,
+// indexed by colour: of the four neighbours of a cell, the vertical ones
+// and one horizontal one are the thread's own cells (except at its first
+// and last row), so a cell update reads one or two values from shared
+// memory, where every cell's latest value is kept by colour for the
+// neighbouring threads.
 __global__ void __launch_bounds__(kHW *kTY_THREADS, 2) intra_sor_kernel(const __grid_constant__ IntraJobs J, int e_in,
                                                                         int from_zero)
 {
@@ -190,24 +205,25 @@ __global__ void __launch_bounds__(kHW *kTY_THREADS, 2) intra_sor_kernel(const __
     const int tx0 = (lt % P.tiles_x) * kTX, ty0 = (lt / P.tiles_x) * kTY;
     const int gx0 = tx0 - kHL, gy0 = ty0 - kHL;
     const int W = P.width, H = P.height, pitch = P.pitch;
-    const int x = threadIdx.x, ty = threadIdx.y;
-    const int par = (tx0 + ty0) & 1;
+    const int hx = threadIdx.x, ty = threadIdx.y, ly0 = ty * kRows;
+    const int par = (tx0 + ty0) & 1;  // parity offset of local -> global coordinates
     const float *ein = P.e[e_in];
     float *eout = P.e[e_in ^ 1];
-    float inv[2][kRows], rinv[2][kRows];  // [colour][k]
-    const int col0 = (ty + par) & 1;  // colour of the pair's left cell (ly has the parity of ty)
+    // ec[k][c]: value of the thread's colour-c cell in row ly0 + k, which
+    // sits at column 2 hx + ((c + k + par) & 1); invc = 1/n, rnc = r/n
+    float ec[kRows][2], invc[kRows][2], rnc[kRows][2];
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
-        const int ly = ty + kTY_THREADS * k, gy = gy0 + ly;
+        const int ly = ly0 + k, gy = gy0 + ly;
         float ev[2], iv[2], rv[2];
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-            const int gx = gx0 + 2 * x + b;
+            const int gx = gx0 + 2 * hx + b;
             ev[b] = 0.f;
             iv[b] = 0.f;
             rv[b] = 0.f;
             if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-                const size_t i = (size_t)gy * pitch + gx;
+                const int i = gy * pitch + gx;
                 if (!P.mask[i]) {
                     const int n = (gx > 0) + (gx < W - 1) + (gy > 0) + (gy < H - 1);
                     iv[b] = n == 4 ? 0.25f : (n == 3 ? (1.0f / 3.0f) : (n == 2 ? 0.5f : 1.0f));
@@ -216,44 +232,50 @@ __global__ void __launch_bounds__(kHW *kTY_THREADS, 2) intra_sor_kernel(const __
                 }
             }
         }
-        // cell b of the pair has colour col0 ^ b
-        E[col0][ly][x] = ev[0];
-        E[col0 ^ 1][ly][x] = ev[1];
-        inv[0][k] = col0 ? iv[1] : iv[0];
-        inv[1][k] = col0 ? iv[0] : iv[1];
-        rinv[0][k] = col0 ? rv[1] : rv[0];
-        rinv[1][k] = col0 ? rv[0] : rv[1];
+        const int sw = (k + par) & 1;  // 1: the pair's left cell has colour 1
+        ec[k][0] = sw ? ev[1] : ev[0];
+        ec[k][1] = sw ? ev[0] : ev[1];
+        invc[k][0] = sw ? iv[1] : iv[0];
+        invc[k][1] = sw ? iv[0] : iv[1];
+        rnc[k][0] = sw ? rv[1] : rv[0];
+        rnc[k][1] = sw ? rv[0] : rv[1];
+        E[0][ly][hx] = ec[k][0];
+        E[1][ly][hx] = ec[k][1];
     }
     __syncthreads();
     const float omega = P.omega;
 #pragma unroll
     for (int m = 1; m <= 2 * kS; ++m) {
-        const int c = (m - 1) & 1, o = c ^ 1;
-        const int b = (c + ty + par) & 1;
-        const int lx = 2 * x + b;
-        if (lx >= m && lx < kRW - m) {
+        const int c = (m - 1) & 1, o = c ^ 1;  // red (even x + y) first
 #pragma unroll
-            for (int k = 0; k < kRows; ++k) {
-                const int ly = ty + kTY_THREADS * k;
-                if (ly >= m && ly < kRH - m) {
-                    const float s = (E[o][ly][x + b - 1] + E[o][ly][x + b]) + (E[o][ly - 1][x] + E[o][ly + 1][x]);
-                    const float e = E[c][ly][x];
-                    // fixed cells have inv = rinv = 0 and e = 0: they stay 0
-                    E[c][ly][x] = fmaf(omega, fmaf(s, inv[c][k], rinv[c][k] - e), e);
-                }
+        for (int k = 0; k < kRows; ++k) {
+            const int ly = ly0 + k;
+            const int b = (c + k + par) & 1;  // column of the colour-c cell in the pair
+            // the staged region's outer ring is never updated (its
+            // neighbours lie outside); validity shrinks by one ring per
+            // half sweep, so the output interior is exact
+            const bool ring = (ly == 0) | (ly == kRH - 1) | (hx == 0 && b == 0) | (hx == kHW - 1 && b == 1);
+            if (!ring) {
+                const float up = k > 0 ? ec[k - 1][o] : E[o][ly - 1][hx];
+                const float dn = k < kRows - 1 ? ec[k + 1][o] : E[o][ly + 1][hx];
+                const float s = (ec[k][o] + E[o][ly][hx - 1 + 2 * b]) + (up + dn);
+                // fixed cells have invc = rnc = 0 and value 0: they stay 0
+                ec[k][c] = fmaf(omega, fmaf(s, invc[k][c], rnc[k][c] - ec[k][c]), ec[k][c]);
+                E[c][ly][hx] = ec[k][c];
             }
         }
         __syncthreads();
     }
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
-        const int ly = ty + kTY_THREADS * k, gy = gy0 + ly;
+        const int ly = ly0 + k, gy = gy0 + ly;
         if (ly < kHL || ly >= kHL + kTY || gy >= H) continue;
+        const int sw = (k + par) & 1;
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-            const int lx = 2 * x + b, gx = gx0 + lx;
+            const int lx = 2 * hx + b, gx = gx0 + lx;
             if (lx < kHL || lx >= kHL + kTX || gx >= W) continue;
-            eout[(size_t)gy * pitch + gx] = E[(b + ty + par) & 1][ly][x];
+            eout[gy * pitch + gx] = (b ^ sw) ? ec[k][1] : ec[k][0];
         }
     }
 }
@@ -275,19 +297,17 @@ cudaError_t launch_intra_init(IntraJobs &J, uint32_t *flags, cudaStream_t st, in
 
 cudaError_t launch_intra_residual(IntraJobs &J, int e_in, bool add_e, cudaStream_t st)
 {
-    long px = 0;
+    int base = 0;
     for (int k = 0; k < J.n; ++k) {
-        cudaError_t e = cudaMemsetAsync(J.p[k].rnorm, 0, sizeof(unsigned int), st);
+        IntraPlane &P = J.p[k];
+        cudaError_t e = cudaMemsetAsync(P.rnorm, 0, sizeof(unsigned int), st);
         if (e != cudaSuccess) return e;
-        px += (long)J.p[k].width * J.p[k].height;
+        P.tiles_x = (P.width + kRTW - 1) / kRTW;
+        P.tile_base = base;
+        base += P.tiles_x * ((P.height + kRTH - 1) / kRTH);
     }
-    if (px == 0) return cudaSuccess;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long want = (px / 3 + kResThreads - 1) / kResThreads;
-    const int grid = (int)std::max(1L, std::min((long)sms * 8, want));
-    intra_residual_kernel<<<grid, kResThreads, 0, st>>>(J, e_in, add_e ? 1 : 0);
+    if (base == 0) return cudaSuccess;
+    intra_residual_kernel<<<base, kResThreads, 0, st>>>(J, e_in, add_e ? 1 : 0);
     return cudaGetLastError();
 }
 
