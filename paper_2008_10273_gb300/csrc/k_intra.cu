@@ -196,8 +196,8 @@ __global__ void __launch_bounds__(kResThreads) intra_residual_kernel(const __gri
 // and last row), so a cell update reads one or two values from shared
 // memory, where every cell's latest value is kept by colour for the
 // neighbouring threads.
-__global__ void __launch_bounds__(kHW *kTY_THREADS, 2) intra_sor_kernel(const __grid_constant__ IntraJobs J, int e_in,
-                                                                        int from_zero)
+template <bool FROM_ZERO>
+__global__ void __launch_bounds__(kHW *kTY_THREADS, 2) intra_sor_kernel(const __grid_constant__ IntraJobs J, int e_in)
 {
     __shared__ float E[2][kRH][kHW];
     const IntraPlane &P = J.p[find_plane(J, blockIdx.x)];
@@ -209,28 +209,42 @@ __global__ void __launch_bounds__(kHW *kTY_THREADS, 2) intra_sor_kernel(const __
     const int par = (tx0 + ty0) & 1;  // parity offset of local -> global coordinates
     const float *ein = P.e[e_in];
     float *eout = P.e[e_in ^ 1];
+    // The pair starts at an even column (tx0 and the halo are even), so its
+    // two cells are read as one 2-element vector.  Every load is issued
+    // unconditionally from a clamped address (rows into [0, H), the pair
+    // into the pitch) and cells outside the image are zeroed afterwards, so
+    // that all of them are in flight together.
+    const int gxp = gx0 + 2 * hx;
+    const int gxc = min(max(gxp, 0), pitch - 2);
+    const bool in0 = gxp >= 0 && gxp < W, in1 = gxp >= 0 && gxp + 1 < W;
+    uint32_t m2[kRows];
+    float2 r2[kRows], e2[kRows];
+#pragma unroll
+    for (int k = 0; k < kRows; ++k) {
+        const int gy = min(max(gy0 + ly0 + k, 0), H - 1);
+        const size_t i = (size_t)gy * pitch + gxc;
+        m2[k] = __ldg(reinterpret_cast<const unsigned short *>(P.mask + i));
+        r2[k] = __ldg(reinterpret_cast<const float2 *>(P.res + i));
+        if (!FROM_ZERO) e2[k] = __ldg(reinterpret_cast<const float2 *>(ein + i));
+    }
     // ec[k][c]: value of the thread's colour-c cell in row ly0 + k, which
     // sits at column 2 hx + ((c + k + par) & 1); invc = 1/n, rnc = r/n
     float ec[kRows][2], invc[kRows][2], rnc[kRows][2];
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
-        const int ly = ly0 + k, gy = gy0 + ly;
+        const int gy = gy0 + ly0 + k;
+        const bool yin = gy >= 0 && gy < H;
+        const int ny = (gy > 0) + (gy < H - 1);
         float ev[2], iv[2], rv[2];
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-            const int gx = gx0 + 2 * hx + b;
-            ev[b] = 0.f;
-            iv[b] = 0.f;
-            rv[b] = 0.f;
-            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-                const int i = gy * pitch + gx;
-                if (!P.mask[i]) {
-                    const int n = (gx > 0) + (gx < W - 1) + (gy > 0) + (gy < H - 1);
-                    iv[b] = n == 4 ? 0.25f : (n == 3 ? (1.0f / 3.0f) : (n == 2 ? 0.5f : 1.0f));
-                    rv[b] = P.res[i] * iv[b];
-                    if (!from_zero) ev[b] = ein[i];
-                }
-            }
+            const int gx = gxp + b;
+            const bool unk = yin && (b ? in1 : in0) && ((m2[k] >> (8 * b)) & 0xffu) == 0;
+            const int n = ny + (gx > 0) + (gx < W - 1);
+            const float inv = n == 4 ? 0.25f : (n == 3 ? (1.0f / 3.0f) : (n == 2 ? 0.5f : 1.0f));
+            iv[b] = unk ? inv : 0.f;
+            rv[b] = unk ? (b ? r2[k].y : r2[k].x) * inv : 0.f;
+            ev[b] = (FROM_ZERO || !unk) ? 0.f : (b ? e2[k].y : e2[k].x);
         }
         const int sw = (k + par) & 1;  // 1: the pair's left cell has colour 1
         ec[k][0] = sw ? ev[1] : ev[0];
@@ -239,8 +253,8 @@ __global__ void __launch_bounds__(kHW *kTY_THREADS, 2) intra_sor_kernel(const __
         invc[k][1] = sw ? iv[0] : iv[1];
         rnc[k][0] = sw ? rv[1] : rv[0];
         rnc[k][1] = sw ? rv[0] : rv[1];
-        E[0][ly][hx] = ec[k][0];
-        E[1][ly][hx] = ec[k][1];
+        E[0][ly0 + k][hx] = ec[k][0];
+        E[1][ly0 + k][hx] = ec[k][1];
     }
     __syncthreads();
     const float omega = P.omega;
@@ -266,17 +280,19 @@ __global__ void __launch_bounds__(kHW *kTY_THREADS, 2) intra_sor_kernel(const __
         }
         __syncthreads();
     }
+    // interior pairs are whole pairs (even halo and width); a pair that
+    // straddles an odd right edge writes its left cell only
+    const int lx = 2 * hx;
+    if (lx < kHL || lx >= kHL + kTX || gxp >= W) return;
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
         const int ly = ly0 + k, gy = gy0 + ly;
         if (ly < kHL || ly >= kHL + kTY || gy >= H) continue;
         const int sw = (k + par) & 1;
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const int lx = 2 * hx + b, gx = gx0 + lx;
-            if (lx < kHL || lx >= kHL + kTX || gx >= W) continue;
-            eout[gy * pitch + gx] = (b ^ sw) ? ec[k][1] : ec[k][0];
-        }
+        const float v0 = sw ? ec[k][1] : ec[k][0], v1 = sw ? ec[k][0] : ec[k][1];
+        float *o = eout + (size_t)gy * pitch + gxp;
+        if (in1) *reinterpret_cast<float2 *>(o) = make_float2(v0, v1);
+        else o[0] = v0;
     }
 }
 
@@ -324,7 +340,8 @@ cudaError_t launch_intra_sor(IntraJobs &J, int e_in, bool from_zero, int sweeps,
     int cur = e_in;
     const int n = (sweeps + kS - 1) / kS;
     for (int l = 0; l < n; ++l) {
-        intra_sor_kernel<<<base, dim3(kHW, kTY_THREADS), 0, st>>>(J, cur, (from_zero && l == 0) ? 1 : 0);
+        if (from_zero && l == 0) intra_sor_kernel<true><<<base, dim3(kHW, kTY_THREADS), 0, st>>>(J, cur);
+        else intra_sor_kernel<false><<<base, dim3(kHW, kTY_THREADS), 0, st>>>(J, cur);
         cur ^= 1;
     }
     if (launches) *launches += n;
