@@ -226,8 +226,9 @@ hivc_status hivc_block_residual(int32_t width, int32_t height, int32_t block,
    residual (while capturing a stream into a graph, or under a fixed memory
    budget where every allocation is made up front).
    Limits: at most 131072 residual points and 16384 blocks per call, else
-   HIVC_E_INVALID.  The array (about 0.8 MB) exists once per device that
-   loads the library and stays until the process exits.  All calls on a
+   HIVC_E_INVALID.  The array (about 17 MB: room for one block with more
+   than 32 points per range of 128 blocks) exists once per device on which
+   this function has run and stays until the process exits.  All calls on a
    device share it and each call overwrites it: calls whose work overlaps
    on the GPU (e.g. on two streams) race, so serialise them.  The first call
    on a device uploads the Green's tables and looks up the array's device

@@ -156,6 +156,7 @@ __device__ __forceinline__ bool seg_block_coef(const float *__restrict__ G, int 
     return spd;
 }
 
+
 // Coefficients of one block with 16 < K <= 32 by one warp, G_PP factored
 // in shared memory (M is 32 x 33); same outputs as seg_block_coef with
 // SEG = 32.  Lane i < K holds point p and the values.

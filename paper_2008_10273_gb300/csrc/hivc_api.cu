@@ -140,9 +140,8 @@ struct hivc_decoder {
     // block scratch
     float *rfield[3]{}, *coef[3]{}, *acoef[3]{};
     size_t coef_cap = 0;
-    uint32_t *large_list = nullptr, *ctr = nullptr;
-    float *big = nullptr;
-    int large_cap = 0;
+    float *big = nullptr;  // one K > 32 system per range of blocks
+    int big_ranges = 0;
     uint32_t *flags = nullptr;
     // tensor maps of the reference planes (per ping-pong buffer)
     FusedMaps maps[2]{};
@@ -261,7 +260,7 @@ hivc_status make_block_jobs(hivc_decoder *d, const hivc_residual *res, BlockJobs
 
 BlockScratch scratch(hivc_decoder *d)
 {
-    return BlockScratch{d->large_list, d->large_cap, d->flags, d->ctr, d->big};
+    return BlockScratch{d->flags, d->big, d->big_ranges};
 }
 
 // Unfused block stage: coefficients (+ large blocks), then residual fields.
@@ -347,9 +346,7 @@ size_t hivc_decoder_bytes(const hivc_config *c)
     }
     add(3 * sizeof(unsigned long long));
     add(3 * sizeof(unsigned int));
-    add((size_t)nblocks * 4);          // large-block list
-    add(kCtrCount * sizeof(uint32_t)); // work counters
-    add(kBigFloats * sizeof(float));   // one K > 32 system
+    add((size_t)block_ranges(nblocks) * kBigFloats * sizeof(float));  // K > 32 systems
     add(4);                            // error word
     return b;
 }
@@ -395,10 +392,8 @@ hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out)
         maxpts = std::max(maxpts, (size_t)g.w * g.h);
     }
     d->coef_cap = maxpts;
-    d->large_cap = nblocks;
-    d->large_list = m.get<uint32_t>((size_t)nblocks);
-    d->ctr = m.get<uint32_t>(kCtrCount);
-    d->big = m.get<float>(kBigFloats);
+    d->big_ranges = block_ranges(nblocks);
+    d->big = m.get<float>((size_t)d->big_ranges * kBigFloats);
     d->vsum = m.get<unsigned long long>(3);
     d->rnorm = m.get<unsigned int>(3);
     d->flags = m.get<uint32_t>(1);
@@ -432,9 +427,7 @@ hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out)
         }
         d->own_stream = true;
     }
-    if (cudaMemsetAsync(d->flags, 0, 4, d->stream) != cudaSuccess ||
-        cudaMemsetAsync(d->ctr, 0, kCtrCount * sizeof(uint32_t), d->stream) != cudaSuccess ||
-        cudaStreamSynchronize(d->stream) != cudaSuccess) {
+    if (cudaMemsetAsync(d->flags, 0, 4, d->stream) != cudaSuccess || cudaStreamSynchronize(d->stream) != cudaSuccess) {
         hivc_decoder_destroy(d);
         return HIVC_E_CUDA;
     }
@@ -675,8 +668,8 @@ hivc_status hivc_decode_pframe(hivc_decoder *d, const hivc_pframe *f, const hivc
     const int nxt = d->cur ^ 1;
     cudaError_t e;
     if (fused_supported(d->cfg.block)) {
-        // three launches: coefficients (K <= 32), the rare K > 32 blocks,
-        // then one fused kernel for evaluation + warp + add + pack
+        // two launches: the coefficients of every block, then one fused
+        // kernel for evaluation + warp + add + pack
         BlockJobs J;
         hivc_status s = make_block_jobs(d, f->res, J);
         if (s != HIVC_OK) return s;
@@ -702,7 +695,6 @@ hivc_status hivc_decode_pframe(hivc_decoder *d, const hivc_pframe *f, const hivc
         F.height = d->cfg.height;
         F.chroma = d->cfg.chroma;
         F.block = d->cfg.block;
-        F.ctr = d->ctr;
         // the TMA variant needs an even luma width (16-byte flow rows) and a
         // 16-byte aligned flow
         FusedMaps *maps = nullptr;
@@ -806,7 +798,7 @@ size_t hivc_block_residual_workspace_bytes(int32_t width, int32_t height, int32_
 {
     if (width < 1 || height < 1 || block < 1 || block > kMaxB || n_points < 0) return 0;
     const size_t nb = (size_t)((width + block - 1) / block) * ((height + block - 1) / block);
-    return a256(4 * (size_t)n_points) + a256(4 * nb) + a256(4 * nb) + 256 + 256 + a256(4 * kBigFloats);
+    return a256(4 * (size_t)n_points) + a256(4 * nb) + 256 + a256(4 * kBigFloats * (size_t)block_ranges((int)nb));
 }
 
 hivc_status hivc_block_residual(int32_t width, int32_t height, int32_t block, const hivc_residual *res, float *r,
@@ -824,11 +816,6 @@ hivc_status hivc_block_residual(int32_t width, int32_t height, int32_t block, co
     w += a256(4 * (size_t)res->n_points);
     float *acoef = reinterpret_cast<float *>(w);
     w += a256(4 * (size_t)nb);
-    uint32_t *list = reinterpret_cast<uint32_t *>(w);
-    w += a256(4 * (size_t)nb);
-    uint32_t *counters = reinterpret_cast<uint32_t *>(w);
-    w += 256;
-    if (cudaMemsetAsync(counters, 0, kCtrCount * sizeof(uint32_t), st) != cudaSuccess) return HIVC_E_CUDA;
     uint32_t *own_flags = reinterpret_cast<uint32_t *>(w);
     w += 256;
     float *big = reinterpret_cast<float *>(w);
@@ -853,7 +840,7 @@ hivc_status hivc_block_residual(int32_t width, int32_t height, int32_t block, co
     B.nbx = nbx;
     B.nblocks = nb;
     J.total_blocks = nb;
-    cudaError_t e = launch_block_coef(J, BlockScratch{list, nb, flags, counters, big}, st, nullptr);
+    cudaError_t e = launch_block_coef(J, BlockScratch{flags, big, block_ranges(nb)}, st, nullptr);
     if (e == cudaSuccess) e = launch_block_eval(J, flags, st);
     return cuda_status(e);
 }

@@ -56,36 +56,28 @@ struct BlockTables {
     int sms;
 };
 
-// Scratch of the coefficient stage: blocks with K > 32 are listed for the
-// large-block kernel, whose last CTA clears the counters again.
-// Work counters (zero between launches; each kernel's last CTA clears its
-// own pair again):
-enum : int {
-    kCtrLargeCount = 0,  // entries of the large-block list
-    kCtrLargeDone = 1,
-    kCtrCoefWork = 2,    // next block quad of the coefficient kernel
-    kCtrCoefDone = 3,
-    kCtrFusedWork = 4,   // next macroblock of the fused inter kernel
-    kCtrFusedDone = 5,
-    kCtrCount = 8
-};
-
 constexpr int kBigMaxK = 255;  // largest K of a 16 x 16 block
 constexpr size_t kBigFloats = (size_t)kBigMaxK * (kBigMaxK + 1) / 2 + 3 * kBigMaxK;
+constexpr int kRange = 128;    // blocks per range of the coefficient kernel
 
+// ranges of kRange blocks for total_blocks blocks
+__host__ __device__ inline int block_ranges(int total_blocks) { return (total_blocks + kRange - 1) / kRange; }
+
+// Scratch of the coefficient stage: room for one K > 32 system per range
+// of kRange blocks (the range's CTA solves its large blocks one after the
+// other in its slot).
 struct BlockScratch {
-    uint32_t *large_list;
-    int32_t large_cap;
     uint32_t *flags;  // device error word
-    uint32_t *ctr;    // kCtrCount work counters
-    float *big;       // kBigFloats: one K > 32 system at a time
+    float *big;       // big_ranges * kBigFloats floats
+    int32_t big_ranges;
 };
 
 cudaError_t ensure_block_tables();
 const BlockTables &block_tables();  // of the current device
 
-// c, a for every block: 8/16/32-lane segments (K <= 32); K > 32 by the
-// kernel's last CTA.  One launch.
+// c, a for every block (a = NaN: bad positions): one thread per block for
+// K <= 12, warps for K <= 32, a whole CTA for K > 32.  One launch, no
+// counters: the kernel's completion publishes every result.
 cudaError_t launch_block_coef(const BlockJobs &jobs, const BlockScratch &s, cudaStream_t st, int *launches);
 // r-field from c, a (Eq. 3 by Green's rows), r = v at the points.
 cudaError_t launch_block_eval(const BlockJobs &jobs, uint32_t *flags, cudaStream_t st);
@@ -101,7 +93,6 @@ struct FusedFrame {
     int32_t ref_pitch[3], out_pitch[3];  // ref_out shares ref_pitch
     int32_t width, height, chroma, block;
     int32_t nmbx, nmb;  // filled by the launcher
-    uint32_t *ctr;      // the decoder's work counters
 };
 
 // Tensor maps of the TMA variant: the frame's flow (2W x H floats, box

@@ -16,10 +16,10 @@
 //   T(al, be) = 1/4 sum_{(p,q) != 0} c_p^2 c_q^2 cos(pi p al / w) cos(pi q be / h) / mu_pq
 // (the Toeplitz-plus-Hankel structure of G, Sec. 2.2), stored as float.
 //
-// Kernels: the coefficient stage (16-lane segments, two blocks per warp,
-// when both have K <= 16; one block per warp for K <= 32), the large-block
-// stage (one CTA per block with K > 32, packed Cholesky in shared memory)
-// and the evaluation into a residual field.  The fused inter-frame kernel
+// Kernels: the coefficient stage (two blocks per warp: in its 16-lane
+// halves when both have K <= 16, else one after the other with all lanes
+// for K <= 32; blocks with K > 32 by the kernel's last CTA, packed Cholesky
+// in global scratch) and the evaluation into a residual field.  The fused inter-frame kernel
 // (k_pframe.cu) evaluates with the same routine.
 #include <cmath>
 #include <cstring>
@@ -81,10 +81,6 @@ void build_tables(std::vector<float> &G, std::vector<int> &goff)
 }
 
 // ---- coefficient stage ---------------------------------------------------
-// A warp takes four consecutive blocks.  When all have K <= 8 it solves them
-// at once in 8-lane segments; otherwise pairs in 16-lane segments (K <= 16)
-// or single blocks with all 32 lanes (K <= 32).  K > 32 goes to the large-
-// block kernel.
 struct SegBlock {
     const BlockPlane *P;
     BlockGeom g;
@@ -109,6 +105,14 @@ __device__ __forceinline__ SegBlock seg_block(const BlockJobs &J, int gb)
 
 __device__ __forceinline__ int seg_k(const SegBlock &b) { return (b.g.bad || b.g.K > kWarpK) ? 0 : b.g.K; }
 
+// A block whose positions are bad gets a = NaN: the evaluation (here and
+// in the fused inter-frame kernel) then takes its residual as zero.
+__device__ __forceinline__ void mark_bad(const BlockPlane &P, int lb)
+{
+    P.acoef[0][lb] = __int_as_float(0x7fc00000);
+    if (P.val[1] != nullptr) P.acoef[1][lb] = __int_as_float(0x7fc00000);
+}
+
 // validity of the positions of a segment's block (inside, increasing):
 // returns K, or 0 (and a flag) when any is bad
 template <int SEG>
@@ -123,15 +127,21 @@ __device__ __forceinline__ int seg_validate(const SegBlock &b, int i, int seg, c
     const unsigned bad = __ballot_sync(0xffffffffu, !ok);
     const unsigned mine = SEG == 32 ? bad : (bad >> (seg * SEG)) & ((1u << SEG) - 1u);
     if (mine) {
-        if (i == 0) atomicOr(S.flags, kFlagPos);
+        if (i == 0) {
+            atomicOr(S.flags, kFlagPos);
+            mark_bad(*b.P, b.g.lb);
+        }
         return 0;
     }
     return K;
 }
 
-// KM = 0: the shared-memory warp routine (16 < K <= 32)
+// One block with K <= KM <= SEG per segment of SEG lanes (lane i of the
+// segment is point i), by the register routine, or (KM = 0, SEG = 32) by
+// the shared-memory routine.  Lt: SEG x (SEG+1) floats of shared scratch.
+// Writes c (per point) and a (per block).
 template <int SEG, int KM>
-__device__ __forceinline__ void seg_run(const SegBlock &b, int K, int i, float (*Lt)[SEG + 1], const BlockTables &tab,
+__device__ __forceinline__ void seg_run(const SegBlock &b, int K, int i, float *Lt, const BlockTables &tab,
                                         const BlockScratch &S)
 {
     const BlockPlane *P = b.P;
@@ -148,9 +158,10 @@ __device__ __forceinline__ void seg_run(const SegBlock &b, int K, int i, float (
     float c0, c1, a0, a1;
     bool spd;
     if constexpr (KM == 0)
-        spd = warp_block_coef_smem(G, rl, K, i, p, v0, v1, reinterpret_cast<float(*)[33]>(&Lt[0][0]), c0, c1, a0, a1);
+        spd = warp_block_coef_smem(G, rl, K, i, p, v0, v1, reinterpret_cast<float(*)[33]>(Lt), c0, c1, a0, a1);
     else
-        spd = seg_block_coef<SEG, KM, true>(G, rl, K, i, p, v0, v1, Lt, c0, c1, a0, a1);
+        spd = seg_block_coef<SEG, KM, true>(G, rl, K, i, p, v0, v1, reinterpret_cast<float(*)[SEG + 1]>(Lt), c0, c1,
+                                            a0, a1);
     if (K > 0) {
         if (i < K) {
             P->coef[0][b.g.s + i] = c0;
@@ -164,61 +175,124 @@ __device__ __forceinline__ void seg_run(const SegBlock &b, int K, int i, float (
     }
 }
 
-__device__ __forceinline__ void coef_quad(const BlockJobs &J, const BlockTables &tab, const BlockScratch &S, int gb0,
-                                          int lane, float *lts)
+// ---- one thread per block (K <= kTK) -------------------------------------
+constexpr int kTK = 12;
+__host__ __device__ constexpr int tri(int i) { return i * (i + 1) / 2; }
+
+// Coefficients of one block by one thread, K <= kTK: G_PP padded to
+// kTK x kTK with the identity (the padding rows of L are unit rows and the
+// padding entries of every solution are zero), Cholesky-Crout in
+// registers, fully unrolled, so that no control flow depends on K.
+//   L y_v = v, L y_1 = 1 (on the K points);  a = (y_1 . y_v) / (y_1 . y_1)
+//   L^T c = y_v - a y_1
+// Returns false if a pivot of a real row was not positive.
+template <bool TWO>
+__device__ __forceinline__ bool thread_block_coef(const float *__restrict__ G, int rl, int K, const int (&p)[kTK],
+                                                  const float (&v0)[kTK], const float (&v1)[kTK], float (&c0)[kTK],
+                                                  float (&c1)[kTK], float &a0, float &a1)
 {
-    // lane q < 4 owns block gb0 + q: error flags and the large-block list
-    int kq;
-    {
-        const SegBlock bq = seg_block(J, gb0 + (lane & 3));
-        kq = seg_k(bq);
-        if (lane < 4 && bq.P != nullptr) {
-            if (bq.g.bad) {
-                atomicOr(S.flags, bq.g.bad);
-            } else if (bq.g.K > kWarpK) {
-                const uint32_t i = atomicAdd(S.ctr + kCtrLargeCount, 1u);
-                if (i < (uint32_t)S.large_cap) S.large_list[i] = (uint32_t)(gb0 + lane);
-            }
+    float L[tri(kTK)], inv[kTK];
+#pragma unroll
+    for (int i = 0; i < kTK; ++i) {
+        const float *row = G + p[i] * rl;
+#pragma unroll
+        for (int j = 0; j <= i; ++j) L[tri(i) + j] = (i < K && j < K) ? __ldg(row + p[j]) : (i == j ? 1.f : 0.f);
+    }
+    bool spd = true;
+#pragma unroll
+    for (int k = 0; k < kTK; ++k) {
+        float d = L[tri(k) + k];
+#pragma unroll
+        for (int m = 0; m < k; ++m) d = fmaf(-L[tri(k) + m], L[tri(k) + m], d);
+        spd = spd && (k >= K || d > 0.f);
+        const float isd = rsqrtf(fmaxf(d, 1e-30f));
+        L[tri(k) + k] = d * isd;
+        inv[k] = isd;
+#pragma unroll
+        for (int i = k + 1; i < kTK; ++i) {
+            float s = L[tri(i) + k];
+#pragma unroll
+            for (int m = 0; m < k; ++m) s = fmaf(-L[tri(i) + m], L[tri(k) + m], s);
+            L[tri(i) + k] = s * isd;
         }
     }
-    const int k0 = __shfl_sync(0xffffffffu, kq, 0), k1 = __shfl_sync(0xffffffffu, kq, 1);
-    const int k2 = __shfl_sync(0xffffffffu, kq, 2), k3 = __shfl_sync(0xffffffffu, kq, 3);
-    const int k01 = max(k0, k1), k23 = max(k2, k3);
-    if (max(k01, k23) == 0) return;
-    if (max(k01, k23) <= 8) {
-        const int seg = lane >> 3, i = lane & 7;
-        SegBlock bb = seg_block(J, gb0 + seg);
-        bb.g.K = seg_k(bb);
-        const int K = seg_validate<8>(bb, i, seg, S);
-        seg_run<8, 8>(bb, K, i, reinterpret_cast<float(*)[9]>(lts + seg * 8 * 9), tab, S);
-        __syncwarp();
+    float y0[kTK], y1[kTK], y2[kTK];
+#pragma unroll
+    for (int i = 0; i < kTK; ++i) {
+        float s0 = v0[i], s1 = TWO ? v1[i] : 0.f, s2 = i < K ? 1.f : 0.f;
+#pragma unroll
+        for (int m = 0; m < i; ++m) {
+            s0 = fmaf(-L[tri(i) + m], y0[m], s0);
+            if (TWO) s1 = fmaf(-L[tri(i) + m], y1[m], s1);
+            s2 = fmaf(-L[tri(i) + m], y2[m], s2);
+        }
+        y0[i] = s0 * inv[i];
+        y1[i] = TWO ? s1 * inv[i] : 0.f;
+        y2[i] = s2 * inv[i];
+    }
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < kTK; ++i) {
+        d0 = fmaf(y2[i], y0[i], d0);
+        if (TWO) d1 = fmaf(y2[i], y1[i], d1);
+        d2 = fmaf(y2[i], y2[i], d2);
+    }
+    const float r22 = __frcp_rn(d2);
+    a0 = d0 * r22;
+    a1 = TWO ? d1 * r22 : 0.f;
+#pragma unroll
+    for (int i = kTK - 1; i >= 0; --i) {
+        float s0 = fmaf(-a0, y2[i], y0[i]), s1 = TWO ? fmaf(-a1, y2[i], y1[i]) : 0.f;
+#pragma unroll
+        for (int m = i + 1; m < kTK; ++m) {
+            s0 = fmaf(-L[tri(m) + i], c0[m], s0);
+            if (TWO) s1 = fmaf(-L[tri(m) + i], c1[m], s1);
+        }
+        c0[i] = s0 * inv[i];
+        c1[i] = TWO ? s1 * inv[i] : 0.f;
+    }
+    return spd;
+}
+
+// one block with 1 <= K <= kTK by the calling thread: positions checked,
+// then c (per point) and a (per block) written
+template <bool TWO>
+__device__ __forceinline__ void thread_run(const BlockPlane &P, const BlockGeom &g, const BlockTables &tab,
+                                           const BlockScratch &S)
+{
+    const int K = g.K, N = g.w * g.h;
+    int p[kTK];
+    float v0[kTK], v1[kTK];
+    bool ok = true;
+    int prev = -1;
+#pragma unroll
+    for (int i = 0; i < kTK; ++i) {
+        p[i] = 0;
+        v0[i] = v1[i] = 0.f;
+        if (i < K) {
+            p[i] = __ldg(P.pos + g.s + i);
+            v0[i] = (float)__ldg(P.val[0] + g.s + i);
+            if (TWO) v1[i] = (float)__ldg(P.val[1] + g.s + i);
+            ok = ok && p[i] < N && p[i] > prev;
+            prev = p[i];
+        }
+    }
+    if (!ok) {
+        atomicOr(S.flags, kFlagPos);
+        mark_bad(P, g.lb);
         return;
     }
-#pragma unroll 1
-    for (int pr = 0; pr < 2; ++pr) {
-        const int kp = pr ? k23 : k01;
-        if (kp == 0) continue;
-        if (kp <= 16) {
-            const int seg = lane >> 4, i = lane & 15;
-            SegBlock bb = seg_block(J, gb0 + 2 * pr + seg);
-            bb.g.K = seg_k(bb);
-            const int K = seg_validate<16>(bb, i, seg, S);
-            auto Lt = reinterpret_cast<float(*)[17]>(lts + seg * 16 * 17);
-            seg_run<16, 16>(bb, K, i, Lt, tab, S);
-        } else {
-            auto Lt = reinterpret_cast<float(*)[33]>(lts);
-#pragma unroll 1
-            for (int k = 0; k < 2; ++k) {
-                SegBlock bb = seg_block(J, gb0 + 2 * pr + k);
-                bb.g.K = seg_k(bb);
-                const int K = seg_validate<32>(bb, lane, 0, S);
-                if (K == 0) continue;
-                if (K <= 24) seg_run<32, 24>(bb, K, lane, Lt, tab, S);
-                else seg_run<32, 0>(bb, K, lane, Lt, tab, S);
-            }
+    float c0[kTK], c1[kTK], a0, a1;
+    const bool spd = thread_block_coef<TWO>(green_rows(tab, g.w, g.h), g_rowlen(N), K, p, v0, v1, c0, c1, a0, a1);
+#pragma unroll
+    for (int i = 0; i < kTK; ++i)
+        if (i < K) {
+            P.coef[0][g.s + i] = c0[i];
+            if (TWO) P.coef[1][g.s + i] = c1[i];
         }
-        __syncwarp();
-    }
+    P.acoef[0][g.lb] = a0;
+    if (TWO) P.acoef[1][g.lb] = a1;
+    if (!spd) atomicOr(S.flags, kFlagNotSPD);
 }
 
 // ---- large blocks (K > 32): one CTA, packed Cholesky in global scratch ----
@@ -237,18 +311,19 @@ __device__ __forceinline__ float cta_sum(float v, float *red)
     return t;
 }
 
-// One block with K > 32 by the whole CTA: G_PP packed in S.big (global),
-// right-hand sides in S.big after it.  Same arithmetic as seg_block_coef.
+// One block with K > 32 by the whole CTA: G_PP packed in the scratch slot
+// big (global), the right-hand sides after it.  Same arithmetic as
+// seg_block_coef.
 __device__ __noinline__ void cta_large_solve(const BlockJobs &J, const BlockTables &tab, const BlockScratch &S, int gb,
-                                unsigned char *s_p, float *red, int *s_bad)
+                                             float *big, unsigned char *s_p, float *red, int *s_bad)
 {
     const int tid = threadIdx.x;
     const BlockPlane &P = J.p[find_job(J, gb)];
     const BlockGeom g = block_geom(P, gb - P.block_base);
     const int K = g.K;
     const bool two = P.val[1] != nullptr;
-    float *L = S.big;
-    float *b = S.big + (size_t)kBigMaxK * (kBigMaxK + 1) / 2;  // b[r*K + i]
+    float *L = big;
+    float *b = big + (size_t)kBigMaxK * (kBigMaxK + 1) / 2;  // b[r*K + i]
     if (tid == 0) *s_bad = 0;
     __syncthreads();
     for (int j = tid; j < K; j += kCoefThreads) {
@@ -261,7 +336,10 @@ __device__ __noinline__ void cta_large_solve(const BlockJobs &J, const BlockTabl
     }
     __syncthreads();
     if (*s_bad) {
-        if (tid == 0) atomicOr(S.flags, kFlagPos);
+        if (tid == 0) {
+            atomicOr(S.flags, kFlagPos);
+            mark_bad(P, g.lb);
+        }
         __syncthreads();
         return;
     }
@@ -333,37 +411,94 @@ __device__ __noinline__ void cta_large_solve(const BlockJobs &J, const BlockTabl
     __syncthreads();
 }
 
-// Coefficient stage: warp w of CTA c solves quad 4c + w (blocks 16c + 4w ..
-// +3).  Blocks with K > 32 are listed; the last CTA to finish solves them
-// and clears the list (a done counter, no waiting).
-__global__ void __launch_bounds__(kCoefThreads, 7) block_coef_kernel(const __grid_constant__ BlockJobs J,
+// Warp path: warp w of a warp-path CTA scans the 32 blocks gb0 .. gb0+31
+// and solves those with kTK < K <= 32: K <= 16 two at a time in 16-lane
+// halves, K <= 24 with all lanes (both in registers, fully unrolled: in a
+// launch over many frames many warps of an SM share the code), larger K
+// with the shared-memory routine.  Blocks with K > 32 go to the CTA's list.
+__device__ __forceinline__ void warp_path(const BlockJobs &J, const BlockTables &tab, const BlockScratch &S, int gb0,
+                                          int lane, float *sm, int *s_large, int *s_nlarge)
+{
+    const SegBlock own = seg_block(J, gb0 + lane);
+    if (own.P != nullptr && !own.g.bad && own.g.K > kWarpK) s_large[atomicAdd(s_nlarge, 1)] = gb0 + lane;
+    const int k = seg_k(own);
+    unsigned m16 = __ballot_sync(0xffffffffu, k > kTK && k <= 16);
+    unsigned m32 = __ballot_sync(0xffffffffu, k > 16);
+    const int half = lane >> 4, i = lane & 15;
+    while (m16) {
+        const int ba = __ffs(m16) - 1;
+        m16 &= m16 - 1;
+        int bb = -1;
+        if (m16) {
+            bb = __ffs(m16) - 1;
+            m16 &= m16 - 1;
+        }
+        const int mine = half ? bb : ba;
+        SegBlock b = seg_block(J, mine >= 0 ? gb0 + mine : J.total_blocks);
+        b.g.K = seg_k(b);
+        const int K = seg_validate<16>(b, i, half, S);
+        seg_run<16, 16>(b, K, i, sm + half * 16 * 17, tab, S);
+        __syncwarp();
+    }
+    while (m32) {
+        const int ba = __ffs(m32) - 1;
+        m32 &= m32 - 1;
+        SegBlock b = seg_block(J, gb0 + ba);
+        b.g.K = seg_k(b);
+        const int K = seg_validate<32>(b, lane, 0, S);
+        if (K > 24) seg_run<32, 0>(b, K, lane, sm, tab, S);
+        else if (K > 0) seg_run<32, 24>(b, K, lane, sm, tab, S);
+        __syncwarp();
+    }
+}
+
+// Coefficient stage.  The grid has two halves over the same ranges of
+// kRange blocks.  Thread-path CTA c: thread t takes block kRange c + t and
+// solves it when K <= 12.  Warp-path CTA c, at the same time: its warps
+// solve the range's blocks with 12 < K <= 32, then the whole CTA those with
+// K > 32, one after the other in the range's scratch slot.  No counters:
+// the kernel's completion publishes every result.
+__global__ void __launch_bounds__(kCoefThreads, 3) block_coef_kernel(const __grid_constant__ BlockJobs J,
                                                                      BlockTables tab, BlockScratch S)
 {
-    __shared__ float lts[4][32 * 33];
+    static_assert(kCoefThreads == kRange, "one thread per block of a range");
+    __shared__ float lts[kCoefThreads / 32][32 * 33];
     __shared__ unsigned char s_p[kBigMaxK];
     __shared__ float red[kCoefThreads / 32];
-    __shared__ int s_last, s_bad;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ int s_large[kRange], s_nlarge, s_bad;
     // the fused kernel that follows may start its prologue (tensor-memory
     // copies of flow and references) now; it waits for this grid's results
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const int gb0 = (blockIdx.x * 4 + warp) * 4;
-    if (gb0 < J.total_blocks) coef_quad(J, tab, S, gb0, lane, lts[warp]);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = atomicAdd(S.ctr + kCtrCoefDone, 1u) == gridDim.x - 1;
+    const int nrange = block_ranges(J.total_blocks);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if ((int)blockIdx.x < nrange) {
+        const int gb = blockIdx.x * kRange + threadIdx.x;
+        if (gb < J.total_blocks) {
+            const BlockPlane &P = J.p[find_job(J, gb)];
+            const BlockGeom g = block_geom(P, gb - P.block_base);
+            if (g.bad) {
+                atomicOr(S.flags, g.bad);
+            } else if (g.K > 0 && g.K <= kTK) {
+                if (P.val[1] != nullptr) thread_run<true>(P, g, tab, S);
+                else thread_run<false>(P, g, tab, S);
+            }
+        }
+        return;
     }
+    const int range = blockIdx.x - nrange;
+    if (threadIdx.x == 0) s_nlarge = 0;
     __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    const uint32_t n = min(*(volatile uint32_t *)(S.ctr + kCtrLargeCount), (uint32_t)S.large_cap);
-    for (uint32_t it = 0; it < n; ++it) cta_large_solve(J, tab, S, (int)S.large_list[it], s_p, red, &s_bad);
-    if (threadIdx.x == 0) {
-        S.ctr[kCtrLargeCount] = 0;
-        S.ctr[kCtrCoefDone] = 0;
-        __threadfence();
+    const int gb0 = range * kRange + warp * 32;
+    if (gb0 < J.total_blocks) warp_path(J, tab, S, gb0, lane, lts[warp], s_large, &s_nlarge);
+    __syncthreads();
+    const int n = s_nlarge;
+    if (n == 0) return;
+    if (range >= S.big_ranges) {  // no scratch slot: the caller sized it wrongly
+        if (threadIdx.x == 0) atomicOr(S.flags, kFlagK);
+        return;
     }
+    float *big = S.big + (size_t)range * kBigFloats;
+    for (int i = 0; i < n; ++i) cta_large_solve(J, tab, S, s_large[i], big, s_p, red, &s_bad);
 }
 
 // ---- evaluation stage into residual fields, one warp per block -----------
@@ -455,7 +590,7 @@ const BlockTables &block_tables()
 cudaError_t launch_block_coef(const BlockJobs &jobs, const BlockScratch &s, cudaStream_t st, int *launches)
 {
     if (jobs.total_blocks == 0) return cudaSuccess;
-    block_coef_kernel<<<(jobs.total_blocks + 15) / 16, kCoefThreads, 0, st>>>(jobs, block_tables(), s);
+    block_coef_kernel<<<2 * block_ranges(jobs.total_blocks), kCoefThreads, 0, st>>>(jobs, block_tables(), s);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }

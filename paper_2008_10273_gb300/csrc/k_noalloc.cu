@@ -5,16 +5,17 @@
 // residual plane: code running while a stream is being captured into a
 // graph, or a host that hands the library a fixed memory budget in which
 // every allocation has already been made.  For them the scratch that the
-// coefficient stage needs (per-point coefficients, per-block constants, the
-// list of blocks with more than 32 points, work counters and one large
-// system) lives in a fixed-size array in the library's device image instead
-// of a caller workspace.
+// coefficient stage needs (per-point coefficients, per-block constants and
+// room for one system with more than 32 points per range of 128 blocks)
+// lives in a fixed-size array in the library's device image instead of a
+// caller workspace.
 //
-// The array exists once per device that loads the library and stays
-// allocated until the process exits.  Every call on a device uses the same
-// array, so calls whose work overlaps on the GPU (for example on two
-// streams) race and must be serialised by the caller.  Each call clears the
-// counters it relies on before its kernels run.
+// The array (about 17 MB) exists once per device on which this entry point
+// has run and stays allocated until the process exits.  Every call on a
+// device uses the same array, so calls whose work overlaps on the GPU (for
+// example on two streams) race and must be serialised by the caller.  The
+// kernels keep no counters from one call to the next; a call without a
+// caller error word clears the library's own before its kernels run.
 #include <mutex>
 
 #include "hivc_internal.cuh"
@@ -25,14 +26,13 @@ namespace {
 
 constexpr int kStaticMaxPoints = 1 << 17;  // residual points per call
 constexpr int kStaticMaxBlocks = 1 << 14;  // residual blocks per call
-// 4-byte words: coefficients | block constants | large-block list | counters
-// | own error word (+ padding) | one K > 32 system
+// 4-byte words: coefficients | block constants | own error word (+ padding)
+// | one K > 32 system per range of kRange blocks
 constexpr size_t kOffAcoef = kStaticMaxPoints;
-constexpr size_t kOffList = kOffAcoef + kStaticMaxBlocks;
-constexpr size_t kOffCtr = kOffList + kStaticMaxBlocks;
-constexpr size_t kOffFlags = kOffCtr + kCtrCount;
-constexpr size_t kOffBig = kOffFlags + 56;  // keeps the system 256-byte aligned
-constexpr size_t kWords = kOffBig + kBigFloats;
+constexpr size_t kOffFlags = kOffAcoef + kStaticMaxBlocks;
+constexpr size_t kOffBig = kOffFlags + 64;  // keeps the systems 256-byte aligned
+constexpr int kStaticRanges = kStaticMaxBlocks / kRange;
+constexpr size_t kWords = kOffBig + (size_t)kStaticRanges * kBigFloats;
 
 static __device__ __align__(256) uint32_t g_scratch[kWords];
 
@@ -67,10 +67,11 @@ extern "C" hivc_status hivc_block_residual_static(int32_t width, int32_t height,
         base = g_addr[dev];
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // counters start at zero (and the own error word when none is given)
-    if (cudaMemsetAsync(base + kOffCtr, 0, (kCtrCount + 8) * sizeof(uint32_t), st) != cudaSuccess)
-        return HIVC_E_CUDA;
-    if (!flags) flags = base + kOffFlags;
+    // the own error word starts at zero when none is given
+    if (!flags) {
+        flags = base + kOffFlags;
+        if (cudaMemsetAsync(flags, 0, sizeof(uint32_t), st) != cudaSuccess) return HIVC_E_CUDA;
+    }
     BlockJobs J{};
     J.n = 1;
     BlockPlane &B = J.p[0];
@@ -88,8 +89,7 @@ extern "C" hivc_status hivc_block_residual_static(int32_t width, int32_t height,
     B.nbx = nbx;
     B.nblocks = (int)nb;
     J.total_blocks = (int)nb;
-    const BlockScratch S{base + kOffList, kStaticMaxBlocks, flags, base + kOffCtr,
-                         reinterpret_cast<float *>(base + kOffBig)};
+    const BlockScratch S{flags, reinterpret_cast<float *>(base + kOffBig), kStaticRanges};
     cudaError_t e = launch_block_coef(J, S, st, nullptr);
     if (e == cudaSuccess) e = launch_block_eval(J, flags, st);
     return e == cudaSuccess ? HIVC_OK : HIVC_E_CUDA;

@@ -1,22 +1,23 @@
 // Fused inter-frame kernel (Sec. 2, Sec. 2.2, Sec. 2.3): one CTA decodes a
-// 32 x 32 luma macroblock and its 16 x 16 Cb and Cr tiles:
-//   1. per residual block of the macroblock (one warp each): the evaluation
-//      r = a + sum_j c_j G[p_j, :] (Eq. 3) into a shared-memory residual
-//      tile, with r = v at the points; c and a come from the coefficient
-//      stage (k_block.cu), launched before;
-//   2. the backward bilinear warp of the previous reconstruction along the
+// 32 x 32 luma macroblock and its 16 x 16 Cb and Cr tiles in two phases:
+//   B. the evaluation r = a + sum_j c_j G[p_j, :] (Eq. 3) of the
+//      macroblock's residual blocks into a shared residual tile, with r = v
+//      at the points; c and a come from the coefficient kernel (k_block.cu),
+//      launched before this one;
+//   C. the backward bilinear warp of the previous reconstruction along the
 //      transmitted flow (chroma flow = half the mean of the co-sited 2 x 2
-//      luma vectors), + residual, clamp to [0, 255], the new FP32
-//      reference and the uint8 output.
+//      luma vectors), + residual, clamp to [0, 255]: the new FP32 reference
+//      and the uint8 output.
 // The residual field never goes through global memory.
 //
-// TMA variant: a persistent CTA takes macroblocks from a work counter and,
-// while it evaluates the residual of one macroblock, the tensor memory
-// accelerator copies the next macroblock's flow tile and its reference
-// tiles (with an 8-pixel luma / 4-pixel chroma halo) into a second shared
-// stage.  Samples that leave the halo read global memory.  The kernel is
-// launched with programmatic dependent launch: the first copies overlap the
-// coefficient kernel, and griddepcontrol.wait orders the coefficient reads.
+// CTA c of a grid of G decodes the macroblocks c, c + G, c + 2G, ...  In
+// the TMA variant the tensor memory accelerator copies a macroblock's flow
+// tile and its reference tiles (8-pixel luma / 4-pixel chroma halo) into
+// one of two shared stages two macroblocks ahead, so that the copies of the
+// next macroblock are in flight while one is decoded; samples that leave
+// the halo read global memory.  The kernel is launched as a programmatic
+// dependent of the coefficient kernel: its first copies overlap that grid,
+// and griddepcontrol.wait orders the coefficient reads.
 #include <cuda.h>
 
 #include "block_device.cuh"
@@ -29,11 +30,10 @@ constexpr int kThreads = 128;
 constexpr int kHalo = 8, kTL = kMB + 2 * kHalo;        // luma reference tile 48 x 48
 constexpr int kCHalo = 4, kTC = kMB / 2 + 2 * kCHalo;  // chroma reference tile 24 x 24
 constexpr long kMbarSpins = 1L << 22;                  // bounded waits
-
-struct WarpScratch {
-    float cs[2][256];
-    unsigned char ps[256];
-};
+constexpr int kRYP = kMB + 4;                          // luma residual tile pitch (16-byte rows)
+constexpr int kRCP = kMB / 2 + 4;                      // chroma residual tile pitch
+constexpr int kRCS = (kMB / 2) * kRCP + 16;            // chroma plane stride (other banks)
+constexpr float kFastFlow = 7.f;                       // |flow| below this never leaves the halo
 
 struct __align__(128) Stage {
     float flow[kMB][2 * kMB];  // 32 rows of 32 (dx, dy)
@@ -41,13 +41,18 @@ struct __align__(128) Stage {
     float rc[2][kTC][kTC];
 };
 
-struct Tiles {
-    float ry[kMB][kMB + 1];
-    float rc[2][kMB / 2][kMB / 2 + 1];
-    WarpScratch scr[kThreads / 32];
+// residual tiles of one macroblock
+struct __align__(16) Tiles {
+    float ry[kMB * kRYP];
+    float rc[2 * kRCS];
 };
 
-constexpr size_t kTmaSmem = sizeof(Stage) + sizeof(Tiles) + 64;
+// shared memory: two stages (TMA variant), the residual tiles, two barriers
+template <bool TMA>
+__host__ __device__ constexpr size_t kernel_smem()
+{
+    return (TMA ? 2 * sizeof(Stage) : 0) + sizeof(Tiles) + 16;
+}
 
 // ---- PTX helpers (TMA, mbarrier, programmatic dependent launch) ----------
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -102,107 +107,20 @@ __device__ __forceinline__ int split_axis(float d, int x, int n, float &a)
     return max(min(i0, n - 2), 0);
 }
 
-// bilinear sample at (x + dx, y + dy), clamped; from the staged tile (origin
-// tx0, ty0, edge T) when the 2 x 2 footprint lies in it, else from R
-template <int T>
-__device__ __forceinline__ float sample(const float *__restrict__ R, int pitch, int W, int H, int x, int y, float dx,
-                                        float dy, const float *tile, int tx0, int ty0)
+// bilinear sample of R at (x + dx, y + dy), clamped, from global memory: the
+// path of the samples whose footprint leaves the staged tile (rare, so it
+// is kept out of line)
+__device__ __noinline__ float sample_global(const float *__restrict__ R, int pitch, int W, int H, int x, int y,
+                                            float dx, float dy)
 {
     float ax, ay;
     const int x0 = split_axis(dx, x, W, ax), y0 = split_axis(dy, y, H, ay);
     const int ox = min(x0 + 1, W - 1) - x0, oyn = min(y0 + 1, H - 1) - y0;
     const float bx = 1.f - ax, by = 1.f - ay;
-    float r00, r01, r10, r11;
-    const int lx = x0 - tx0, ly = y0 - ty0;
-    if (T > 0 && (unsigned)lx < (unsigned)(T - 1) && (unsigned)ly < (unsigned)(T - 1)) {
-        const float *t = tile + ly * T + lx;
-        r00 = t[0];
-        r01 = t[ox];
-        r10 = t[oyn * T];
-        r11 = t[oyn * T + ox];
-    } else {
-        const float *g = R + y0 * pitch + x0;
-        r00 = __ldg(g);
-        r01 = __ldg(g + ox);
-        r10 = __ldg(g + oyn * pitch);
-        r11 = __ldg(g + oyn * pitch + ox);
-    }
+    const float *g = R + (size_t)y0 * pitch + x0;
+    const float r00 = __ldg(g), r01 = __ldg(g + ox), r10 = __ldg(g + (size_t)oyn * pitch),
+                r11 = __ldg(g + (size_t)oyn * pitch + ox);
     return bx * by * r00 + ax * by * r01 + bx * ay * r10 + ax * ay * r11;
-}
-
-// ---- residual tiles ------------------------------------------------------
-// One residual block of the macroblock into its shared tile(s).
-__device__ void mb_block(const BlockPlane &P, int lb, const BlockTables &tab, WarpScratch &S, float *tile0,
-                         float *tile1, int tpitch, int ox, int oy, int lane)
-{
-    const BlockGeom g = block_geom(P, lb);
-    const int K = g.K, w = g.w, N = g.w * g.h;
-    const bool two = P.val[1] != nullptr;
-    bool valid = g.bad == 0;  // errors are flagged by the coefficient stage
-    for (int j0 = 0; j0 < K; j0 += 32) {
-        int p = 0;
-        const bool ok = (j0 + lane < K) ? load_pos(P, g, j0 + lane, p) : true;
-        valid = valid && !__any_sync(0xffffffffu, !ok);
-        if (j0 + lane < K) {
-            S.ps[j0 + lane] = (unsigned char)p;
-            S.cs[0][j0 + lane] = __ldg(P.coef[0] + g.s + j0 + lane);
-            if (two) S.cs[1][j0 + lane] = __ldg(P.coef[1] + g.s + j0 + lane);
-        }
-    }
-    __syncwarp();
-    if (!valid || K == 0) {
-        for (int i = lane; i < N; i += 32) {
-            const int y = i / w, x = i - y * w;
-            tile0[(oy + y) * tpitch + ox + x] = 0.f;
-            if (two) tile1[(oy + y) * tpitch + ox + x] = 0.f;
-        }
-        __syncwarp();
-        return;
-    }
-    const float a0 = __ldg(P.acoef[0] + g.lb), a1 = two ? __ldg(P.acoef[1] + g.lb) : 0.f;
-    const float *G = green_rows(tab, g.w, g.h);
-    auto out = [&](int x, int y, float v0, float v1) {
-        const int o = (oy + y) * tpitch + ox + x;
-        tile0[o] = v0;
-        if (two) tile1[o] = v1;
-    };
-    if (two) warp_block_eval<true>(G, w, N, K, S.ps, S.cs[0], S.cs[1], a0, a1, lane, out);
-    else warp_block_eval<false>(G, w, N, K, S.ps, S.cs[0], S.cs[1], a0, a1, lane, out);
-    __syncwarp();
-    for (int j = lane; j < K; j += 32) {
-        const int o = (oy + S.ps[j] / w) * tpitch + ox + S.ps[j] % w;
-        tile0[o] = (float)__ldg(P.val[0] + g.s + j);
-        if (two) tile1[o] = (float)__ldg(P.val[1] + g.s + j);
-    }
-    __syncwarp();
-}
-
-template <bool CHROMA>
-__device__ __forceinline__ void mb_residual(const FusedFrame &F, const BlockTables &tab, Tiles &tl, int mx, int my,
-                                            int warp, int lane)
-{
-    const int B = F.block;
-    const int nl = kMB / B, nc = (kMB / 2) / B;  // blocks per macroblock side
-    const int nlum = nl * nl, nchr = nc * nc;
-    const int ntask = nlum + (CHROMA ? nchr * (F.nblk - 1) : 0);
-    const int W = F.width, H = F.height, cw = (W + 1) / 2, chh = (H + 1) / 2;
-    for (int t = warp; t < ntask; t += kThreads / 32) {
-        if (t < nlum) {
-            const BlockPlane &P = F.bp[0];
-            const int bx = mx * nl + t % nl, by = my * nl + t / nl;
-            if (bx * B >= W || by * B >= H) continue;
-            mb_block(P, by * P.nbx + bx, tab, tl.scr[warp], &tl.ry[0][0], nullptr, kMB + 1, (t % nl) * B,
-                     (t / nl) * B, lane);
-        } else {
-            const int u = t - nlum, job = 1 + u / nchr, k = u % nchr;
-            const BlockPlane &P = F.bp[job];
-            const int bx = mx * nc + k % nc, by = my * nc + k / nc;
-            if (bx * B >= cw || by * B >= chh) continue;
-            // job 1: Cb (+ Cr when paired), job 2: Cr
-            mb_block(P, by * P.nbx + bx, tab, tl.scr[warp], &tl.rc[job - 1][0][0], &tl.rc[1][0][0], kMB / 2 + 1,
-                     (k % nc) * B, (k / nc) * B, lane);
-        }
-    }
 }
 
 // bilinear sample from a staged tile at tile coordinates (lx + fx, ly + fy),
@@ -216,6 +134,239 @@ __device__ __forceinline__ float tile_lerp(const float *tile, int lx, int ly, fl
     return fmaf(ay, bot - top, top);
 }
 
+// residual + prediction, clamped to [0, 255]: the new FP32 reference and
+// the uint8 output (round half up)
+__device__ __forceinline__ void put_pixel(float pred, float r, float *ref_out, uint8_t *out)
+{
+    const float v = fminf(fmaxf(pred + r, 0.f), 255.f);
+    *ref_out = v;
+    *out = (uint8_t)__float2int_rd(v + 0.5f);
+}
+
+// y = p / w and x = p - y w for p < 256, w <= 16: (p + 1/2) / w lies at
+// least 1 / (2w) from an integer, far beyond the rounding of the product
+__device__ __forceinline__ void split_pos(int p, int w, float rw, int &y, int &x)
+{
+    y = __float2int_rz(((float)p + 0.5f) * rw);
+    x = p - y * w;
+}
+
+// ---- phase B: residual tiles (Eq. 3) ---------------------------------------
+// One residual block as the evaluation reads it: K = 0 for an empty block,
+// one outside the plane, and one with bad data (block pointers or K, which
+// the coefficient kernel flags, or positions, for which it sets a = NaN).
+struct BlkView {
+    const float *G;      // Green's rows of the block's shape
+    const float *cs;     // its coefficients c_j,
+    const uint8_t *ps;   // positions p_j
+    const int16_t *vs;   // and values v_j
+    int rl, w, h, K;
+    int ox, oy;          // offset in the macroblock (plane pixels)
+    float a;
+};
+
+// block (bx, by) of plane data P (value set vi), at (ox, oy) in the
+// macroblock; reads the coefficient kernel's a
+__device__ __forceinline__ BlkView block_view(const BlockPlane &P, int vi, int bx, int by, int ox, int oy,
+                                              bool present, const BlockTables &tab)
+{
+    BlkView V;
+    V.G = tab.G;
+    V.cs = nullptr;
+    V.ps = nullptr;
+    V.vs = nullptr;
+    V.rl = 8;
+    V.w = V.h = 1;
+    V.K = 0;
+    V.ox = ox;
+    V.oy = oy;
+    V.a = 0.f;
+    if (!present) return V;
+    const BlockGeom g = block_geom(P, by * P.nbx + bx);
+    V.w = g.w;
+    V.h = g.h;
+    V.rl = g_rowlen(g.w * g.h);
+    V.G = green_rows(tab, g.w, g.h);
+    if (g.bad || g.K == 0) return V;
+    const float a = __ldg(P.acoef[vi] + g.lb);
+    if (!(a == a)) return V;
+    V.K = g.K;
+    V.a = a;
+    V.cs = P.coef[vi] + g.s;
+    V.ps = P.pos + g.s;
+    V.vs = P.val[vi] + g.s;
+    return V;
+}
+
+// Whole-block rows: the N pixels q0 .. q0 + N - 1 (N = 8 or 2, q0 a
+// multiple of N) of one block, for one or two planes with the same points:
+//   r[t] = a + sum_j c_j G[p_j, q0 + t]
+// The GRP lanes of an aligned lane group share one block (GRP = 32 or 8):
+// lane u of the group holds point j0 + u of a chunk, so that the loop body
+// gets c_j and p_j by shuffles and its Green's-row loads are independent.
+// Kmax is the warp's largest K; c = 0 past a block's own K.
+template <int N, bool TWO, int GRP>
+__device__ __forceinline__ void eval_row(const float *G, int rl, const float *cs0, const float *cs1,
+                                         const uint8_t *ps, int K, int Kmax, int q0, float a0, float a1,
+                                         float (&r0)[N], float (&r1)[N])
+{
+    const int lane = threadIdx.x & 31, base = lane & ~(GRP - 1), sub = lane & (GRP - 1);
+#pragma unroll
+    for (int t = 0; t < N; ++t) {
+        r0[t] = a0;
+        r1[t] = a1;
+    }
+    const float *Gq = G + q0;
+    for (int j0 = 0; j0 < Kmax; j0 += GRP) {
+        const int jj = j0 + sub;
+        const bool live = jj < K;
+        const float h0 = live ? __ldg(cs0 + jj) : 0.f, h1 = (TWO && live) ? __ldg(cs1 + jj) : 0.f;
+        const int hp = live ? __ldg(ps + jj) : 0;
+        const int n = min(GRP, Kmax - j0);
+#pragma unroll 4
+        for (int u = 0; u < n; ++u) {
+            const float c0 = __shfl_sync(0xffffffffu, h0, base + u);
+            const float c1 = TWO ? __shfl_sync(0xffffffffu, h1, base + u) : 0.f;
+            const float *g = Gq + __shfl_sync(0xffffffffu, hp, base + u) * rl;
+            float gv[N];
+            if (N == 8) {
+                const float4 lo = __ldg(reinterpret_cast<const float4 *>(g));
+                const float4 hi = __ldg(reinterpret_cast<const float4 *>(g) + 1);
+                gv[0] = lo.x;
+                gv[1] = lo.y;
+                gv[2 % N] = lo.z;
+                gv[3 % N] = lo.w;
+                gv[4 % N] = hi.x;
+                gv[5 % N] = hi.y;
+                gv[6 % N] = hi.z;
+                gv[7 % N] = hi.w;
+            } else {
+                const float2 v = __ldg(reinterpret_cast<const float2 *>(g));
+                gv[0] = v.x;
+                gv[1 % N] = v.y;
+            }
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                r0[t] = fmaf(c0, gv[t], r0[t]);
+                if (TWO) r1[t] = fmaf(c1, gv[t], r1[t]);
+            }
+        }
+    }
+}
+
+// Any block (cut by the plane edge): N pixels of block row y from block
+// column x0, scalar loads; pixels outside the block get a.
+template <int N>
+__device__ __forceinline__ void eval_any(const BlkView &V, int y, int x0, float (&r)[N])
+{
+    int q[N];
+#pragma unroll
+    for (int t = 0; t < N; ++t) {
+        q[t] = (y < V.h && x0 + t < V.w) ? y * V.w + x0 + t : 0;
+        r[t] = V.a;
+    }
+    for (int j = 0; j < V.K; ++j) {
+        const float c = __ldg(V.cs + j);
+        const float *g = V.G + __ldg(V.ps + j) * V.rl;
+#pragma unroll
+        for (int t = 0; t < N; ++t) r[t] = fmaf(c, __ldg(g + q[t]), r[t]);
+    }
+}
+
+// r = v at the points of a block (the exact data), into a tile of pitch
+// tp; points in block rows [ylo, yhi) only
+__device__ __forceinline__ void put_points(const BlkView &V, float *tile, int tp, int ylo, int yhi, int lane)
+{
+    const float rw = __frcp_rn((float)V.w);
+    for (int j = lane; j < V.K; j += 32) {
+        int y, x;
+        split_pos(__ldg(V.ps + j), V.w, rw, y, x);
+        if (y >= ylo && y < yhi) tile[(V.oy + y) * tp + V.ox + x] = (float)__ldg(V.vs + j);
+    }
+}
+
+// Luma: B = 16, warp w evaluates block w of the macroblock (lane l: row
+// l / 2, columns 8 (l % 2) .. +7); B = 8, warp w the blocks of block row w
+// (lane l: block l / 8, row l % 8).  Eight pixels per lane, written as two
+// 16-byte rows.
+template <int B>
+__device__ __forceinline__ void phase_b_luma(const FusedFrame &F, const BlockTables &tab, Tiles &T, int mx, int my,
+                                             int warp, int lane)
+{
+    constexpr int NBL = kMB / B, LPB = B * B / 8;  // blocks per macroblock row, lanes per block
+    const int bi = B == 16 ? warp : warp * 4 + lane / LPB;
+    const int ox = (bi % NBL) * B, oy = (bi / NBL) * B;
+    const int l = lane % LPB, y = (8 * l) / B, x0 = (8 * l) % B;
+    const bool present = mx * kMB + ox < F.width && my * kMB + oy < F.height;
+    const BlkView V = block_view(F.bp[0], 0, mx * NBL + ox / B, my * NBL + oy / B, ox, oy, present, tab);
+    int Kmax = V.K;
+    if (B == 8) {
+#pragma unroll
+        for (int o = 8; o < 32; o <<= 1) Kmax = max(Kmax, __shfl_xor_sync(0xffffffffu, Kmax, o));
+    }
+    float r[8], rd[8];
+    if (__all_sync(0xffffffffu, V.w == B && V.h == B))
+        eval_row<8, false, LPB>(V.G, V.rl, V.cs, V.cs, V.ps, V.K, Kmax, 8 * l, V.a, 0.f, r, rd);
+    else
+        eval_any<8>(V, y, x0, r);
+    float *row = T.ry + (oy + y) * kRYP + ox + x0;
+    reinterpret_cast<float4 *>(row)[0] = make_float4(r[0], r[1], r[2], r[3]);
+    reinterpret_cast<float4 *>(row)[1] = make_float4(r[4], r[5], r[6], r[7]);
+    __syncwarp();
+    if (B == 16) {
+        put_points(V, T.ry, kRYP, 0, B, lane);
+    } else {
+        // the warp's four blocks one after the other, all lanes each
+#pragma unroll 1
+        for (int b = 0; b < 4; ++b) {
+            const BlkView U = block_view(F.bp[0], 0, mx * NBL + b, my * NBL + warp, b * B, warp * B,
+                                         mx * kMB + b * B < F.width && my * kMB + warp * B < F.height, tab);
+            put_points(U, T.ry, kRYP, 0, B, lane);
+        }
+    }
+}
+
+// Chroma: B = 16, warp w evaluates rows 4w .. 4w+3 of the block (lane l:
+// row 4w + l / 8, columns 2 (l % 8), +1); B = 8, warp w block w (lane l:
+// row l / 4, columns 2 (l % 4), +1).  Both planes; one loop when Cb and Cr
+// share their points.
+template <int B>
+__device__ __forceinline__ void phase_b_chroma(const FusedFrame &F, const BlockTables &tab, Tiles &T, int mx, int my,
+                                               int warp, int lane)
+{
+    constexpr int NBC = kMB / 2 / B;
+    const int blk = B == 16 ? 0 : warp;
+    const int ox = (blk % NBC) * B, oy = (blk / NBC) * B;
+    const int y = B == 16 ? 4 * warp + lane / 8 : lane / 4, x0 = B == 16 ? 2 * (lane % 8) : 2 * (lane % 4);
+    const int ylo = B == 16 ? 4 * warp : 0, yhi = B == 16 ? 4 * warp + 4 : B;
+    const int bx = mx * NBC + ox / B, by = my * NBC + oy / B;
+    const bool present = mx * (kMB / 2) + ox < (F.width + 1) / 2 && my * (kMB / 2) + oy < (F.height + 1) / 2;
+    const bool paired = F.nblk == 2;
+    const BlkView V0 = block_view(F.bp[1], 0, bx, by, ox, oy, present, tab);
+    const BlkView V1 = paired ? block_view(F.bp[1], 1, bx, by, ox, oy, present && F.bp[1].val[1] != nullptr, tab)
+                              : block_view(F.bp[2], 0, bx, by, ox, oy, present, tab);
+    const bool whole0 = V0.w == B && V0.h == B, whole1 = V1.w == B && V1.h == B;
+    float r0[2], r1[2];
+    const int q0 = y * B + x0;
+    if (paired && __all_sync(0xffffffffu, whole0 && whole1 && V0.K == V1.K)) {
+        eval_row<2, true, 32>(V0.G, V0.rl, V0.cs, V1.cs, V0.ps, V0.K, V0.K, q0, V0.a, V1.a, r0, r1);
+    } else {
+        float d[2];
+        if (__all_sync(0xffffffffu, whole0))
+            eval_row<2, false, 32>(V0.G, V0.rl, V0.cs, V0.cs, V0.ps, V0.K, V0.K, q0, V0.a, 0.f, r0, d);
+        else eval_any<2>(V0, y, x0, r0);
+        if (__all_sync(0xffffffffu, whole1))
+            eval_row<2, false, 32>(V1.G, V1.rl, V1.cs, V1.cs, V1.ps, V1.K, V1.K, q0, V1.a, 0.f, r1, d);
+        else eval_any<2>(V1, y, x0, r1);
+    }
+    *reinterpret_cast<float2 *>(T.rc + (oy + y) * kRCP + ox + x0) = make_float2(r0[0], r0[1]);
+    *reinterpret_cast<float2 *>(T.rc + kRCS + (oy + y) * kRCP + ox + x0) = make_float2(r1[0], r1[1]);
+    __syncwarp();
+    put_points(V0, T.rc, kRCP, ylo, yhi, lane);
+    put_points(V1, T.rc + kRCS, kRCP, ylo, yhi, lane);
+}
+
+// ---- phase C: warp + residual + clamp + pack -------------------------------
 struct PixelCtx {
     int W, H, cw, chh, yp, op;
     const float *ry0;
@@ -226,92 +377,6 @@ struct PixelCtx {
     uint8_t *ucp;
     int cpitch, uop;
 };
-
-// warp + residual + clamp + pack of one macroblock; st = staged tiles or null
-template <bool CHROMA>
-__device__ __forceinline__ void mb_pixels(const PixelCtx &c, const Tiles &tl, const Stage *st, int mx, int my,
-                                          const float2 *__restrict__ fl)
-{
-    const int W = c.W, H = c.H;
-    const int x = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int gx = mx * kMB + x;
-    const int tx0 = mx * kMB - kHalo, ty0 = my * kMB - kHalo;
-    // tile-coordinate window in which a sample needs neither the plane
-    // clamp nor global memory: the tile interior, intersected with the plane
-    const int lx_lo = max(0, -tx0), lx_hi = min(kTL - 2, W - 2 - tx0);
-    const int ly_lo = max(0, -ty0), ly_hi = min(kTL - 2, H - 2 - ty0);
-    const int cp = x & 1;
-    const int cxg = mx * (kMB / 2) + (x >> 1);
-    const int cx0 = mx * (kMB / 2) - kCHalo, cy0 = my * (kMB / 2) - kCHalo;
-    const int cx_lo = max(0, -cx0), cx_hi = min(kTC - 2, c.cw - 2 - cx0);
-    const int cy_lo = max(0, -cy0), cy_hi = min(kTC - 2, c.chh - 2 - cy0);
-#pragma unroll 2
-    for (int jj = 0; jj < 4; ++jj) {
-        float2 f[2];
-        bool in[2];
-        float py[2];
-#pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
-            const int ly = 2 * (ty + 4 * jj) + rr, gy = my * kMB + ly;
-            in[rr] = gx < W && gy < H;
-            if (st) f[rr] = make_float2(st->flow[ly][2 * x], st->flow[ly][2 * x + 1]);
-            else f[rr] = in[rr] ? __ldg(fl + gy * W + gx) : make_float2(0.f, 0.f);
-            // fast path: the footprint lies in the staged tile and the plane
-            const float fx = floorf(f[rr].x), fy = floorf(f[rr].y);
-            const float ax = f[rr].x - fx, ay = f[rr].y - fy;
-            const int lx = x + kHalo + __float2int_rn(fx), lyy = ly + kHalo + __float2int_rn(fy);
-            const bool fast = st != nullptr && lx >= lx_lo && lx <= lx_hi && lyy >= ly_lo && lyy <= ly_hi &&
-                              ax == ax && ay == ay;
-            if (__all_sync(0xffffffffu, fast || !in[rr])) {
-                py[rr] = fast ? tile_lerp<kTL>(&st->ry[0][0], lx, lyy, ax, ay) : 0.f;
-            } else {
-                py[rr] = in[rr] ? (st ? sample<kTL>(c.ry0, c.yp, W, H, gx, gy, f[rr].x, f[rr].y, &st->ry[0][0],
-                                                    tx0, ty0)
-                                      : sample<0>(c.ry0, c.yp, W, H, gx, gy, f[rr].x, f[rr].y, nullptr, 0, 0))
-                                : 0.f;
-            }
-        }
-#pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
-            if (!in[rr]) continue;
-            const int ly = 2 * (ty + 4 * jj) + rr, gy = my * kMB + ly;
-            const float v = fminf(fmaxf(py[rr] + tl.ry[ly][x], 0.f), 255.f);
-            c.oy0[gy * c.yp + gx] = v;
-            c.uy0[gy * c.op + gx] = (uint8_t)__float2int_rd(v + 0.5f);
-        }
-        if (CHROMA) {
-            // chroma: even lanes Cb, odd lanes Cr, one chroma column per lane pair
-            float sx = f[0].x + f[1].x, sy = f[0].y + f[1].y;
-            int n = (int)in[0] + (int)in[1];
-            sx += __shfl_xor_sync(0xffffffffu, sx, 1);
-            sy += __shfl_xor_sync(0xffffffffu, sy, 1);
-            n += __shfl_xor_sync(0xffffffffu, n, 1);
-            const float sc = n == 4 ? 0.125f : (n == 2 ? 0.25f : 0.5f);
-            const float dx = sx * sc, dy = sy * sc;
-            const int j = ty + 4 * jj, cyg = my * (kMB / 2) + j;
-            const bool cin = cxg < c.cw && cyg < c.chh;
-            const float fx = floorf(dx), fy = floorf(dy);
-            const float ax = dx - fx, ay = dy - fy;
-            const int lx = (x >> 1) + kCHalo + __float2int_rn(fx), lyy = j + kCHalo + __float2int_rn(fy);
-            const bool fast = st != nullptr && lx >= cx_lo && lx <= cx_hi && lyy >= cy_lo && lyy <= cy_hi &&
-                              ax == ax && ay == ay;
-            float pc;
-            if (__all_sync(0xffffffffu, fast || !cin)) {
-                pc = fast ? tile_lerp<kTC>(&st->rc[cp][0][0], lx, lyy, ax, ay) : 0.f;
-            } else {
-                pc = cin ? (st ? sample<kTC>(c.rcp, c.cpitch, c.cw, c.chh, cxg, cyg, dx, dy, &st->rc[cp][0][0], cx0,
-                                             cy0)
-                               : sample<0>(c.rcp, c.cpitch, c.cw, c.chh, cxg, cyg, dx, dy, nullptr, 0, 0))
-                         : 0.f;
-            }
-            if (cin) {
-                const float v = fminf(fmaxf(pc + tl.rc[cp][j][x >> 1], 0.f), 255.f);
-                c.ocp[cyg * c.cpitch + cxg] = v;
-                c.ucp[cyg * c.uop + cxg] = (uint8_t)__float2int_rd(v + 0.5f);
-            }
-        }
-    }
-}
 
 template <bool CHROMA>
 __device__ __forceinline__ PixelCtx pixel_ctx(const FusedFrame &F)
@@ -342,45 +407,99 @@ __device__ __forceinline__ PixelCtx pixel_ctx(const FusedFrame &F)
     return c;
 }
 
-// the last CTA to leave clears the macroblock counters for the next frame
-__device__ __forceinline__ void release_mb_counters(const FusedFrame &F)
+// Thread (x, ty) takes luma rows 2 ty + 8 jj + {0, 1} of column x and
+// chroma row ty + 4 jj of column x / 2 in plane x & 1, whose flow is half
+// the mean of the four co-sited luma vectors: the thread's two rows and the
+// neighbouring lane's.  FAST (macroblock inside the plane with its halo,
+// every |flow| < 7, so every footprint lies in the staged tiles): no range
+// checks.  Otherwise each sample is checked and the ones that leave the
+// staged tile (or all, st = null) read global memory.
+template <bool CHROMA, bool FAST>
+__device__ __forceinline__ void phase_c(const PixelCtx &c, const float *ryt, const float *rct, const Stage *st, int mx,
+                                        int my, const float2 *__restrict__ fl)
 {
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(F.ctr + kCtrFusedDone, 1u) == gridDim.x - 1) {
-            F.ctr[kCtrFusedWork] = 0;
-            F.ctr[kCtrFusedDone] = 0;
-            __threadfence();
+    const int W = c.W, H = c.H;
+    const int x = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int gx = mx * kMB + x;
+    const int tx0 = mx * kMB - kHalo, ty0 = my * kMB - kHalo;
+    const int lx_lo = max(0, -tx0), lx_hi = min(kTL - 2, W - 2 - tx0);
+    const int ly_lo = max(0, -ty0), ly_hi = min(kTL - 2, H - 2 - ty0);
+    const int cp = x & 1, cx = x >> 1;
+    const int cxg = mx * (kMB / 2) + cx;
+    const int cx0 = mx * (kMB / 2) - kCHalo, cy0 = my * (kMB / 2) - kCHalo;
+    const int cx_lo = max(0, -cx0), cx_hi = min(kTC - 2, c.cw - 2 - cx0);
+    const int cy_lo = max(0, -cy0), cy_hi = min(kTC - 2, c.chh - 2 - cy0);
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+        float2 f[2];
+        bool in[2];
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            const int ly = 2 * ty + 8 * jj + rr, gy = my * kMB + ly;
+            in[rr] = FAST || (gx < W && gy < H);
+            if (st) f[rr] = *reinterpret_cast<const float2 *>(&st->flow[ly][2 * x]);
+            else f[rr] = in[rr] ? __ldg(fl + (size_t)gy * W + gx) : make_float2(0.f, 0.f);
+            if (!in[rr]) continue;
+            const float fx = floorf(f[rr].x), fy = floorf(f[rr].y);
+            const float ax = f[rr].x - fx, ay = f[rr].y - fy;
+            const int lx = x + kHalo + __float2int_rn(fx), lyy = ly + kHalo + __float2int_rn(fy);
+            float pred;
+            if (FAST) {
+                pred = tile_lerp<kTL>(&st->ry[0][0], lx, lyy, ax, ay);
+            } else {
+                const bool fast = st != nullptr && lx >= lx_lo && lx <= lx_hi && lyy >= ly_lo && lyy <= ly_hi &&
+                                  ax == ax && ay == ay;
+                pred = fast ? tile_lerp<kTL>(&st->ry[0][0], lx, lyy, ax, ay)
+                            : sample_global(c.ry0, c.yp, W, H, gx, gy, f[rr].x, f[rr].y);
+            }
+            put_pixel(pred, ryt[ly * kRYP + x], c.oy0 + (size_t)gy * c.yp + gx, c.uy0 + (size_t)gy * c.op + gx);
+        }
+        if (CHROMA) {
+            float sx = f[0].x + f[1].x, sy = f[0].y + f[1].y;
+            sx += __shfl_xor_sync(0xffffffffu, sx, 1);
+            sy += __shfl_xor_sync(0xffffffffu, sy, 1);
+            int n = 4;
+            if (!FAST) {
+                n = (int)in[0] + (int)in[1];
+                n += __shfl_xor_sync(0xffffffffu, n, 1);
+            }
+            const int j = ty + 4 * jj, cyg = my * (kMB / 2) + j;
+            if (FAST || (cxg < c.cw && cyg < c.chh)) {
+                const float sc = n == 4 ? 0.125f : (n == 2 ? 0.25f : 0.5f);
+                const float dx = sx * sc, dy = sy * sc;
+                const float fx = floorf(dx), fy = floorf(dy);
+                const float ax = dx - fx, ay = dy - fy;
+                const int lx = cx + kCHalo + __float2int_rn(fx), lyy = j + kCHalo + __float2int_rn(fy);
+                float pred;
+                if (FAST) {
+                    pred = tile_lerp<kTC>(&st->rc[cp][0][0], lx, lyy, ax, ay);
+                } else {
+                    const bool fast = st != nullptr && lx >= cx_lo && lx <= cx_hi && lyy >= cy_lo && lyy <= cy_hi &&
+                                      ax == ax && ay == ay;
+                    pred = fast ? tile_lerp<kTC>(&st->rc[cp][0][0], lx, lyy, ax, ay)
+                                : sample_global(c.rcp, c.cpitch, c.cw, c.chh, cxg, cyg, dx, dy);
+                }
+                put_pixel(pred, rct[cp * kRCS + j * kRCP + cx], c.ocp + (size_t)cyg * c.cpitch + cxg,
+                          c.ucp + (size_t)cyg * c.uop + cxg);
+            }
         }
     }
 }
 
-// ---- plain variant: global loads only ------------------------------------
-template <bool CHROMA>
-__global__ void __launch_bounds__(kThreads, 8) pframe_fused_kernel(const __grid_constant__ FusedFrame F, BlockTables tab,
-                                                                uint32_t *flags)
+// every luma flow vector of the thread's pixels below kFastFlow in size
+// (false for NaN)
+__device__ __forceinline__ bool small_flow(const Stage &st)
 {
-    __shared__ Tiles tl;
-    __shared__ int s_mb;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const PixelCtx pc = pixel_ctx<CHROMA>(F);
-    const float2 *fl = reinterpret_cast<const float2 *>(F.flow);
-    grid_dependency_wait();
-    for (;;) {
-        if (threadIdx.x == 0) s_mb = (int)atomicAdd(F.ctr + kCtrFusedWork, 1u);
-        __syncthreads();
-        const int mb = s_mb;
-        if (mb >= F.nmb) break;
-        const int mx = mb % F.nmbx, my = mb / F.nmbx;
-        mb_residual<CHROMA>(F, tab, tl, mx, my, warp, lane);
-        __syncthreads();
-        mb_pixels<CHROMA>(pc, tl, nullptr, mx, my, fl);
-        __syncthreads();
+    const int x = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float2 f = *reinterpret_cast<const float2 *>(&st.flow[2 * ty + 8 * (k >> 1) + (k & 1)][2 * x]);
+        ok = ok && fabsf(f.x) < kFastFlow && fabsf(f.y) < kFastFlow;
     }
-    release_mb_counters(F);
+    return ok;
 }
 
-// ---- TMA variant ---------------------------------------------------------
 template <bool CHROMA>
 __device__ __forceinline__ void issue_stage(const FusedFrame &F, Stage &st, uint64_t *bar, int mb,
                                             const CUtensorMap *mf, const CUtensorMap *mry, const CUtensorMap *mcb,
@@ -397,67 +516,87 @@ __device__ __forceinline__ void issue_stage(const FusedFrame &F, Stage &st, uint
     }
 }
 
-template <bool CHROMA>
-__global__ void __launch_bounds__(kThreads, 6) pframe_tma_kernel(const __grid_constant__ FusedFrame F,
-                                                                 const __grid_constant__ CUtensorMap mflow,
-                                                                 const __grid_constant__ CUtensorMap mrefy,
-                                                                 const __grid_constant__ CUtensorMap mrefcb,
-                                                                 const __grid_constant__ CUtensorMap mrefcr,
-                                                                 BlockTables tab, uint32_t *flags)
+// The fused inter-frame kernel.  TMA = false reads the flow and the
+// references from global memory only (a flow whose rows a tensor map
+// cannot describe).
+template <bool CHROMA, int B, bool TMA>
+__global__ void __launch_bounds__(kThreads, TMA ? 4 : 6) pframe_kernel(const __grid_constant__ FusedFrame F,
+                                                                       const __grid_constant__ CUtensorMap mflow,
+                                                                       const __grid_constant__ CUtensorMap mrefy,
+                                                                       const __grid_constant__ CUtensorMap mrefcb,
+                                                                       const __grid_constant__ CUtensorMap mrefcr,
+                                                                       BlockTables tab, uint32_t *flags)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    Stage &st = *reinterpret_cast<Stage *>(smem);
-    Tiles &tl = *reinterpret_cast<Tiles *>(smem + sizeof(Stage));
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + sizeof(Stage) + sizeof(Tiles));
-    __shared__ int s_mb;
+    Stage *stages = reinterpret_cast<Stage *>(smem);
+    Tiles &T = *reinterpret_cast<Tiles *>(smem + (TMA ? 2 * sizeof(Stage) : 0));
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (TMA ? 2 * sizeof(Stage) : 0) + sizeof(Tiles));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int G = gridDim.x;
     const PixelCtx pc = pixel_ctx<CHROMA>(F);
     const float2 *fl = reinterpret_cast<const float2 *>(F.flow);
-    if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
+    // pend[s]: the iteration whose tiles stage s is receiving (-1: none);
+    // ph[s]: the phase of stage s's barrier at its next completion
+    // (scalars, not arrays indexed by s, which would live in local memory)
+    int pend0 = TMA && (int)blockIdx.x < F.nmb ? 0 : -1, pend1 = TMA && (int)blockIdx.x + G < F.nmb ? 1 : -1;
+    uint32_t ph0 = 0u, ph1 = 0u;
+    bool ok = true;  // false after a copy timed out: the stages are not refilled
+    if (TMA && threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         fence_proxy_async();
+        // the first two macroblocks' tiles; the flow and the references were
+        // complete before the coefficient kernel started
+        if (pend0 >= 0) issue_stage<CHROMA>(F, stages[0], &bar[0], blockIdx.x, &mflow, &mrefy, &mrefcb, &mrefcr);
+        if (pend1 >= 0) issue_stage<CHROMA>(F, stages[1], &bar[1], blockIdx.x + G, &mflow, &mrefy, &mrefcb, &mrefcr);
     }
-    uint32_t parity = 0u;
-    bool ok = true, first = true;
-    for (;;) {
-        // the CTA takes the next macroblock and starts the tensor-memory
-        // copies of its flow and reference tiles; the residual evaluation
-        // runs while they are in flight
-        if (threadIdx.x == 0) {
-            s_mb = (int)atomicAdd(F.ctr + kCtrFusedWork, 1u);
-            if (s_mb < F.nmb && ok) {
-                fence_proxy_async();  // the stage was last read by the generic proxy
-                issue_stage<CHROMA>(F, st, bar, s_mb, &mflow, &mrefy, &mrefcb, &mrefcr);
-            }
-        }
-        __syncthreads();
-        const int mb = s_mb;
-        if (mb >= F.nmb) break;
-        const bool issued = ok;
-        if (first) {
-            // the reference planes and the flow were complete before the
-            // coefficient kernel started; its coefficients are not yet
-            grid_dependency_wait();
-            first = false;
-        }
+    __syncthreads();
+    // the coefficients are read from here on
+    grid_dependency_wait();
+    int it = 0;
+    for (int mb = blockIdx.x; mb < F.nmb; mb += G, ++it) {
+        const int s = it & 1;
         const int mx = mb % F.nmbx, my = mb / F.nmbx;
-        mb_residual<CHROMA>(F, tab, tl, mx, my, warp, lane);
-        __syncthreads();
+        phase_b_luma<B>(F, tab, T, mx, my, warp, lane);
+        if (CHROMA) phase_b_chroma<B>(F, tab, T, mx, my, warp, lane);
+        const bool issued = TMA && (s ? pend1 : pend0) == it;
         bool landed = false;
         if (issued) {
-            landed = mbar_wait(bar, parity);
-            if (landed) parity ^= 1u;
-            else if (threadIdx.x == 0) atomicOr(flags, kFlagTimeout);
+            landed = mbar_wait(&bar[s], s ? ph1 : ph0);
+            if (landed) {
+                if (s) {
+                    ph1 ^= 1u;
+                    pend1 = -1;
+                } else {
+                    ph0 ^= 1u;
+                    pend0 = -1;
+                }
+            } else if (threadIdx.x == 0) {
+                atomicOr(flags, kFlagTimeout);
+            }
         }
-        // a timed-out copy may still land later: stop issuing and finish on
-        // global loads (the staged tile is not read)
-        ok = ok && landed;
-        mb_pixels<CHROMA>(pc, tl, landed ? &st : nullptr, mx, my, fl);
-        __syncthreads();
+        const Stage *st = landed ? &stages[s] : nullptr;
+        const bool interior = mx * kMB - kHalo >= 0 && my * kMB - kHalo >= 0 &&
+                              mx * kMB - kHalo + kTL <= F.width && my * kMB - kHalo + kTL <= F.height;
+        if (__syncthreads_and(landed && interior && small_flow(stages[s])))
+            phase_c<CHROMA, true>(pc, T.ry, T.rc, st, mx, my, fl);
+        else
+            phase_c<CHROMA, false>(pc, T.ry, T.rc, st, mx, my, fl);
+        // a copy that timed out may still land later: from then on no stage
+        // is refilled (the barrier also frees stage s and the tiles)
+        if (__syncthreads_or(issued && !landed)) ok = false;
+        if (TMA && ok && mb + 2 * G < F.nmb) {
+            if (s) pend1 = it + 2;
+            else pend0 = it + 2;
+            if (threadIdx.x == 0) {
+                fence_proxy_async();  // the stage was last read by the generic proxy
+                issue_stage<CHROMA>(F, stages[s], &bar[s], mb + 2 * G, &mflow, &mrefy, &mrefcb, &mrefcr);
+            }
+        }
     }
-    if (first) grid_dependency_wait();
-    if (!ok) mbar_wait(bar, parity);  // bounded: let a late copy land first
-    release_mb_counters(F);
+    // bounded: let a copy that timed out land before the CTA exits
+    if (TMA && pend0 >= 0) mbar_wait(&bar[0], ph0);
+    if (TMA && pend1 >= 0) mbar_wait(&bar[1], ph1);
 }
 
 template <class Kern>
@@ -468,6 +607,26 @@ int occupancy(Kern k, size_t smem)
     return o;
 }
 
+template <bool C, int B, bool TMA>
+cudaError_t launch_variant(FusedFrame &F, const FusedMaps *maps, uint32_t *flags, cudaLaunchConfig_t &cfg,
+                           const BlockTables &t)
+{
+    static int occ = 0;
+    if (occ == 0) occ = occupancy(pframe_kernel<C, B, TMA>, kernel_smem<TMA>());
+    cfg.gridDim = dim3(std::max(1, std::min(F.nmb, t.sms * occ)));
+    cfg.dynamicSmemBytes = kernel_smem<TMA>();
+    static const FusedMaps none{};
+    const FusedMaps &m = maps ? *maps : none;
+    return cudaLaunchKernelEx(&cfg, pframe_kernel<C, B, TMA>, F, m.flow, m.ref[0], m.ref[1], m.ref[2], t, flags);
+}
+
+template <bool C, int B, bool TMA>
+cudaError_t allow_smem()
+{
+    return cudaFuncSetAttribute(pframe_kernel<C, B, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kernel_smem<TMA>());
+}
+
 }  // namespace
 
 bool fused_supported(int block) { return block == 16 || block == 8; }
@@ -475,14 +634,15 @@ bool fused_supported(int block) { return block == 16 || block == 8; }
 cudaError_t fused_init()
 {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(pframe_tma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kTmaSmem)) != cudaSuccess)
-        return e;
-    return cudaFuncSetAttribute(pframe_tma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem);
+    if ((e = allow_smem<true, 16, true>()) != cudaSuccess) return e;
+    if ((e = allow_smem<false, 16, true>()) != cudaSuccess) return e;
+    if ((e = allow_smem<true, 8, true>()) != cudaSuccess) return e;
+    return allow_smem<false, 8, true>();
 }
 
 cudaError_t launch_pframe_fused(FusedFrame &F, const FusedMaps *maps, uint32_t *flags, cudaStream_t st, bool pdl)
 {
+    if (!fused_supported(F.block)) return cudaErrorInvalidValue;
     F.nmbx = (F.width + kMB - 1) / kMB;
     F.nmb = F.nmbx * ((F.height + kMB - 1) / kMB);
     const BlockTables &t = block_tables();
@@ -494,26 +654,19 @@ cudaError_t launch_pframe_fused(FusedFrame &F, const FusedMaps *maps, uint32_t *
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
+    const bool c = F.chroma != 0;
     if (maps) {
-        static int occ[2] = {0, 0};
-        int &o = occ[F.chroma ? 1 : 0];
-        if (o == 0)
-            o = F.chroma ? occupancy(pframe_tma_kernel<true>, kTmaSmem) : occupancy(pframe_tma_kernel<false>, kTmaSmem);
-        cfg.gridDim = dim3(std::max(1, std::min(F.nmb, t.sms * o)));
-        cfg.dynamicSmemBytes = kTmaSmem;
-        if (F.chroma)
-            return cudaLaunchKernelEx(&cfg, pframe_tma_kernel<true>, F, maps->flow, maps->ref[0], maps->ref[1],
-                                      maps->ref[2], t, flags);
-        return cudaLaunchKernelEx(&cfg, pframe_tma_kernel<false>, F, maps->flow, maps->ref[0], maps->ref[1],
-                                  maps->ref[2], t, flags);
+        if (F.block == 16)
+            return c ? launch_variant<true, 16, true>(F, maps, flags, cfg, t)
+                     : launch_variant<false, 16, true>(F, maps, flags, cfg, t);
+        return c ? launch_variant<true, 8, true>(F, maps, flags, cfg, t)
+                 : launch_variant<false, 8, true>(F, maps, flags, cfg, t);
     }
-    static int occ[2] = {0, 0};
-    int &o = occ[F.chroma ? 1 : 0];
-    if (o == 0) o = F.chroma ? occupancy(pframe_fused_kernel<true>, 0) : occupancy(pframe_fused_kernel<false>, 0);
-    cfg.gridDim = dim3(std::max(1, std::min(F.nmb, t.sms * o)));
-    cfg.dynamicSmemBytes = 0;
-    if (F.chroma) return cudaLaunchKernelEx(&cfg, pframe_fused_kernel<true>, F, t, flags);
-    return cudaLaunchKernelEx(&cfg, pframe_fused_kernel<false>, F, t, flags);
+    if (F.block == 16)
+        return c ? launch_variant<true, 16, false>(F, maps, flags, cfg, t)
+                 : launch_variant<false, 16, false>(F, maps, flags, cfg, t);
+    return c ? launch_variant<true, 8, false>(F, maps, flags, cfg, t)
+             : launch_variant<false, 8, false>(F, maps, flags, cfg, t);
 }
 
 }  // namespace hivc

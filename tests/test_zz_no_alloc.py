@@ -40,8 +40,8 @@ def test_matches_workspace_entry_point_on_consecutive_calls():
     flags = torch.zeros(1, dtype=torch.int32, device="cuda")
     rng = np.random.default_rng(21)
     first = make_residual(rng, 203, 77, 16, 8.0, 64, empty_frac=0.1)
-    # the second call has blocks with K > 32 (the last-CTA large-block path
-    # and its counters) on a different plane size
+    # the second call has blocks with K > 32 (solved by a whole CTA in its
+    # range's scratch slot) on a different plane size
     second = make_residual(rng, 160, 96, 16, 30.0, 64, kmax=60)
     for res in (first, second):
         got = _without_allocation(hv, res, flags)
