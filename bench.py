@@ -55,6 +55,9 @@ def parse_args(argv=None):
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--path", choices=["batch", "plain"], default="batch",
+                   help="decode path of the timed steps: one hivc_decode_batch call per GOP (inter frames "
+                        "share coefficient launches), or one call per frame")
     return p.parse_args(argv)
 
 
@@ -67,7 +70,7 @@ def workload_desc(a):
 def config_obj(a, world):
     return {"workload": workload_desc(a), "width": a.width, "height": a.height, "gop": a.frames,
             "block": 16, "iframe_tol": a.iframe_tol, "seed": a.seed,
-            "l2": "flushed between steps (256 MB write, outside the timed events)",
+            "l2": "flushed between steps (256 MB write, outside the timed events)", "path": a.path,
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
 
@@ -238,6 +241,18 @@ def main(argv=None):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     nfr = gop.n_frames
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nfr + 1)] for _ in range(a.steps)]
+    evb = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(a.steps)]
+    decs_b = [dec] * nfr
+    frames_b = [("i", iframe_d)] + [("p", p) for p in pframes_d]
+    outs_b = [out] * nfr  # frames of one decoder are decoded in order: one output suffices
+
+    def step_batch(events=None):
+        if events:
+            events[0].record(stream)
+        st = hivc.decode_batch(decs_b, frames_b, outs_b)
+        if events:
+            events[1].record(stream)
+        return st
 
     def step(events=None):
         if events:
@@ -251,10 +266,12 @@ def main(argv=None):
                 events[t + 2].record(stream)
         return st
 
+    timed = step_batch if a.path == "batch" else step
+    tev = evb if a.path == "batch" else ev
     with torch.cuda.stream(stream):
         for _ in range(a.warmup):
             flush.zero_()
-            step()
+            timed()
         dec.sync()
         clocks = Clocks(local)
         if not a.no_clocks:
@@ -264,10 +281,22 @@ def main(argv=None):
         torch.cuda.synchronize()
         for k in range(a.steps):
             flush.zero_()
-            step(ev[k])
+            timed(tev[k])
         torch.cuda.synchronize()
         stats = dec.sync()
         clk = clocks.stop() if not a.no_clocks else None
+        # the per-frame path once more (its frame latencies; with --path
+        # plain the timed steps above are this path already)
+        if a.path == "batch":
+            for _ in range(a.warmup):
+                flush.zero_()
+                step()
+            torch.cuda.synchronize()
+            for k in range(a.steps):
+                flush.zero_()
+                step(ev[k])
+            torch.cuda.synchronize()
+            dec.sync()
         # per-kernel device times: the same steps again with CUDA events
         # around every kernel family on the decoder's stream (events between
         # kernels keep the fused kernel from overlapping its predecessor, so
@@ -280,12 +309,14 @@ def main(argv=None):
         torch.cuda.synchronize()
         kstats = dec.sync()
         hivc.lib().hivc_decoder_set_timing(dec.handle, 0)
-    step_ms = [e[0].elapsed_time(e[-1]) for e in ev]
+    step_ms = [e[0].elapsed_time(e[-1]) for e in tev]
+    plain_ms = [e[0].elapsed_time(e[-1]) for e in ev]
     frame_ms = []
     for e in ev:
         frame_ms += [e[i].elapsed_time(e[i + 1]) for i in range(nfr)]
     px_scale = W * H / FULLHD_PX
     value, total_ms = replica_value(sum(step_ms), a.steps * nfr, px_scale, dist, "cuda")
+    plain_value, plain_total = replica_value(sum(plain_ms), a.steps * nfr, px_scale, dist, "cuda")
 
     # roofline of the dominant kernel family (kernel-timing pass)
     fam_ms = list(kstats.kernel_ms)
@@ -360,6 +391,28 @@ def main(argv=None):
             for o, oh in zip(out, out_h):
                 oh.copy_(o, non_blocking=True)
 
+    # the batch path: every input of the GOP up, one hivc_decode_batch call
+    # into one device output per frame, every output down
+    outs_e = [hivc.alloc_out(W, H) for _ in range(nfr)] if a.path == "batch" else None
+    outs_eh = [[torch.empty(o.shape, dtype=torch.uint8).pin_memory() for o in outs_e[0]] for _ in range(nfr)] \
+        if a.path == "batch" else None
+
+    def e2e_step_batch():
+        for k, v in host_i.items():
+            dev_i[k].copy_(v, non_blocking=True)
+        for hp, dp in zip(host_p, dev_p):
+            dp["flow"].copy_(hp["flow"], non_blocking=True)
+            for rh, rd in zip(hp["res"], dp["res"]):
+                for xh, xd in zip(rh, rd):
+                    xd.copy_(xh, non_blocking=True)
+        hivc.decode_batch(decs_b, [("i", dev_i)] + [("p", dp) for dp in dev_p], outs_e)
+        for oe, oh in zip(outs_e, outs_eh):
+            for o, h in zip(oe, oh):
+                h.copy_(o, non_blocking=True)
+
+    if a.path == "batch":
+        e2e_step = e2e_step_batch  # noqa: F811
+
     with torch.cuda.stream(stream):
         e2e_step()
         torch.cuda.synchronize()
@@ -388,6 +441,8 @@ def main(argv=None):
             "latency_ms": {"p50": q(sorted(frame_ms), 0.5), "p99": q(sorted(frame_ms), 0.99),
                            "inter_p50": q(pf, 0.5), "inter_p99": q(pf, 0.99), "intra_p50": q(ifm, 0.5),
                            "path": "plain (one decode call per frame, one decoder)"},
+            "plain": {"value": plain_value, "unit": UNIT, "ms_per_step": plain_total / a.steps,
+                      "path": "one decode call per frame"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "steps": a.e2e_steps},
             "roofline": roof,

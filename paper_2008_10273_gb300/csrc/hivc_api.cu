@@ -143,6 +143,9 @@ struct hivc_decoder {
     float *big = nullptr;  // one K > 32 system per range of blocks
     int big_ranges = 0;
     uint32_t *flags = nullptr;
+    // coefficients of the inter frames of one batch (grown on demand)
+    void *pool = nullptr;
+    size_t pool_bytes = 0;
     // tensor maps of the reference planes (per ping-pong buffer)
     FusedMaps maps[2]{};
     bool maps_ok = false;
@@ -213,9 +216,13 @@ bool out_ok(const hivc_decoder *d, const hivc_out *o)
 }
 
 // Block jobs of one frame: Y, then Cb and Cr (one paired job when they share
-// block_ptr/pos: one factorisation, two right-hand sides).
-hivc_status make_block_jobs(hivc_decoder *d, const hivc_residual *res, BlockJobs &J)
+// block_ptr/pos: one factorisation, two right-hand sides).  coef/acoef: the
+// per-plane coefficient arrays (the decoder's own when null).
+hivc_status make_block_jobs(hivc_decoder *d, const hivc_residual *res, BlockJobs &J, float *const *coef = nullptr,
+                            float *const *acoef = nullptr)
 {
+    if (!coef) coef = d->coef;
+    if (!acoef) acoef = d->acoef;
     J = BlockJobs{};
     for (int p = 0; p < d->np; ++p)
         if ((int64_t)res[p].n_points > (int64_t)d->pg[p].w * d->pg[p].h) return HIVC_E_INVALID;
@@ -227,10 +234,10 @@ hivc_status make_block_jobs(hivc_decoder *d, const hivc_residual *res, BlockJobs
         B.pos = res[p].pos;
         B.val[0] = res[p].val;
         B.val[1] = p2 >= 0 ? res[p2].val : nullptr;
-        B.coef[0] = d->coef[p];
-        B.coef[1] = p2 >= 0 ? d->coef[p2] : nullptr;
-        B.acoef[0] = d->acoef[p];
-        B.acoef[1] = p2 >= 0 ? d->acoef[p2] : nullptr;
+        B.coef[0] = coef[p];
+        B.coef[1] = p2 >= 0 ? coef[p2] : nullptr;
+        B.acoef[0] = acoef[p];
+        B.acoef[1] = p2 >= 0 ? acoef[p2] : nullptr;
         B.r[0] = d->rfield[p];
         B.r[1] = p2 >= 0 ? d->rfield[p2] : nullptr;
         B.r_pitch = g.pitch;
@@ -447,6 +454,7 @@ void hivc_decoder_destroy(hivc_decoder *d)
     for (cudaEvent_t e : d->event_pool) cudaEventDestroy(e);
     if (d->own_stream) cudaStreamDestroy(d->stream);
     if (d->h_flags) cudaFreeHost(d->h_flags);
+    if (d->pool) cudaFree(d->pool);
     d->mem.release();
     delete d;
 }
@@ -658,6 +666,43 @@ hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc
     return converged ? HIVC_OK : HIVC_E_NOT_CONVERGED;
 }
 
+// The fused inter-frame kernel of frame f (coefficients in J's arrays),
+// into the next reference buffer.  early: the reference planes are complete
+// when the kernel starts (the preceding launch is this frame's coefficient
+// kernel), so it may copy its first tiles before waiting for that launch.
+cudaError_t launch_fused_frame(hivc_decoder *d, const hivc_pframe *f, const hivc_out *out, const BlockJobs &J,
+                               bool early)
+{
+    const int nxt = d->cur ^ 1;
+    FusedFrame F{};
+    F.nblk = J.n;
+    for (int k = 0; k < J.n; ++k) F.bp[k] = J.p[k];
+    F.flow = f->flow;
+    for (int p = 0; p < d->np; ++p) {
+        F.ref[p] = d->ref[d->cur][p];
+        F.ref_out[p] = d->ref[nxt][p];
+        F.ref_pitch[p] = d->pg[p].pitch;
+        F.out[p] = out->plane[p];
+        F.out_pitch[p] = out->pitch[p];
+    }
+    F.width = d->cfg.width;
+    F.height = d->cfg.height;
+    F.chroma = d->cfg.chroma;
+    F.block = d->cfg.block;
+    F.early = early ? 1 : 0;
+    // the TMA variant needs an even luma width (16-byte flow rows) and a
+    // 16-byte aligned flow
+    FusedMaps *maps = nullptr;
+    if (d->maps_ok && d->cfg.width % 2 == 0 &&
+        encode_map_2d(&d->maps[d->cur].flow, f->flow, 2 * (uint64_t)d->cfg.width, d->cfg.height,
+                      8 * (uint64_t)d->cfg.width, 64, 32))
+        maps = &d->maps[d->cur];
+    Timed t(d, 7);
+    const cudaError_t e = launch_pframe_fused(F, maps, d->flags, d->stream, !d->timing);
+    t.done(1);
+    return e;
+}
+
 hivc_status hivc_decode_pframe(hivc_decoder *d, const hivc_pframe *f, const hivc_out *out)
 {
     if (!d || !f || !out_ok(d, out) || !f->flow) return HIVC_E_INVALID;
@@ -680,34 +725,7 @@ hivc_status hivc_decode_pframe(hivc_decoder *d, const hivc_pframe *f, const hivc
             t.done(1);
         }
         if (e != cudaSuccess) return HIVC_E_CUDA;
-        FusedFrame F{};
-        F.nblk = J.n;
-        for (int k = 0; k < J.n; ++k) F.bp[k] = J.p[k];
-        F.flow = f->flow;
-        for (int p = 0; p < d->np; ++p) {
-            F.ref[p] = d->ref[d->cur][p];
-            F.ref_out[p] = d->ref[nxt][p];
-            F.ref_pitch[p] = d->pg[p].pitch;
-            F.out[p] = out->plane[p];
-            F.out_pitch[p] = out->pitch[p];
-        }
-        F.width = d->cfg.width;
-        F.height = d->cfg.height;
-        F.chroma = d->cfg.chroma;
-        F.block = d->cfg.block;
-        // the TMA variant needs an even luma width (16-byte flow rows) and a
-        // 16-byte aligned flow
-        FusedMaps *maps = nullptr;
-        if (d->maps_ok && d->cfg.width % 2 == 0 &&
-            encode_map_2d(&d->maps[d->cur].flow, f->flow, 2 * (uint64_t)d->cfg.width, d->cfg.height,
-                          8 * (uint64_t)d->cfg.width, 64, 32))
-            maps = &d->maps[d->cur];
-        {
-            Timed t(d, 7);
-            e = launch_pframe_fused(F, maps, d->flags, d->stream, !d->timing);
-            t.done(1);
-        }
-        if (e != cudaSuccess) return HIVC_E_CUDA;
+        if ((e = launch_fused_frame(d, f, out, J, true)) != cudaSuccess) return HIVC_E_CUDA;
     } else {
         hivc_status s = run_block_residual(d, f->res);
         if (s != HIVC_OK) return s;
@@ -743,20 +761,148 @@ hivc_status hivc_decode_pframe(hivc_decoder *d, const hivc_pframe *f, const hivc
     return HIVC_OK;
 }
 
+namespace {
+
+size_t a256(size_t b) { return (b + 255) / 256 * 256; }
+
+bool pframe_ok(const hivc_decoder *d, const hivc_pframe *f, const hivc_out *out)
+{
+    if (!d || !f || !out_ok(d, out) || !f->flow) return false;
+    for (int p = 0; p < d->np; ++p)
+        if (!residual_ok(f->res[p]) || (int64_t)f->res[p].n_points > (int64_t)d->pg[p].w * d->pg[p].h) return false;
+    return true;
+}
+
+// The decoder's batch pool holds at least bytes (device memory; the old pool
+// is freed once the decoder's stream has finished with it).
+hivc_status ensure_pool(hivc_decoder *d, size_t bytes)
+{
+    if (d->pool_bytes >= bytes) return HIVC_OK;
+    if (d->pool) {
+        if (cudaStreamSynchronize(d->stream) != cudaSuccess) return HIVC_E_CUDA;
+        cudaFree(d->pool);
+        d->pool = nullptr;
+        d->pool_bytes = 0;
+    }
+    const size_t want = bytes + bytes / 4;
+    if (cudaMalloc(&d->pool, want) != cudaSuccess) {
+        cudaGetLastError();
+        d->pool = nullptr;
+        return HIVC_E_NOMEM;
+    }
+    d->pool_bytes = want;
+    return HIVC_OK;
+}
+
+// The inter frames frames[k] (k in ks, in order) of decoder d: coefficient
+// launches over several frames at once (up to kMaxJobs block jobs each),
+// each frame's coefficients in its own part of the batch pool, then the
+// fused kernel of each frame in order.  Every frame has been checked.
+hivc_status decode_inter_run(hivc_decoder *d, const hivc_frame *frames, const hivc_out *outs,
+                             const std::vector<int> &ks)
+{
+    if (cudaSetDevice(d->device) != cudaSuccess) return HIVC_E_CUDA;
+    const size_t nf = ks.size();
+    // pool layout: per frame and plane a256(4 n_points) + a256(4 nblocks),
+    // then the K > 32 scratch of the largest coefficient launch
+    std::vector<size_t> off(nf * 3 * 2);
+    size_t bytes = 0;
+    for (size_t k = 0; k < nf; ++k)
+        for (int p = 0; p < d->np; ++p) {
+            off[(k * 3 + p) * 2] = bytes;
+            bytes += a256(4 * (size_t)frames[ks[k]].p->res[p].n_points);
+            off[(k * 3 + p) * 2 + 1] = bytes;
+            bytes += a256(4 * (size_t)d->pg[p].nblocks);
+        }
+    int fblocks = 0;
+    for (int p = 0; p < d->np; ++p) fblocks += d->pg[p].nblocks;
+    const int per_launch = kMaxJobs / d->np;  // frames per coefficient launch (at most np jobs each)
+    const int ranges = block_ranges(per_launch * fblocks);
+    const size_t big_off = bytes;
+    bytes += (size_t)ranges * kBigFloats * sizeof(float);
+    hivc_status s = ensure_pool(d, bytes);
+    if (s != HIVC_OK) return s;
+    char *pool = static_cast<char *>(d->pool);
+    std::vector<BlockJobs> jobs(nf);
+    for (size_t k = 0; k < nf; ++k) {
+        float *coef[3], *acoef[3];
+        for (int p = 0; p < 3; ++p) {
+            coef[p] = p < d->np ? reinterpret_cast<float *>(pool + off[(k * 3 + p) * 2]) : nullptr;
+            acoef[p] = p < d->np ? reinterpret_cast<float *>(pool + off[(k * 3 + p) * 2 + 1]) : nullptr;
+        }
+        if ((s = make_block_jobs(d, frames[ks[k]].p->res, jobs[k], coef, acoef)) != HIVC_OK) return s;
+    }
+    const BlockScratch S{d->flags, reinterpret_cast<float *>(pool + big_off), ranges};
+    BlockJobs J{};
+    auto flush = [&]() -> cudaError_t {
+        if (J.n == 0) return cudaSuccess;
+        Timed t(d, 3);
+        int l = 0;
+        const cudaError_t e = launch_block_coef(J, S, d->stream, &l);
+        t.done(l);
+        J = BlockJobs{};
+        return e;
+    };
+    for (size_t k = 0; k < nf; ++k) {
+        if (J.n + jobs[k].n > kMaxJobs && flush() != cudaSuccess) return HIVC_E_CUDA;
+        for (int q = 0; q < jobs[k].n; ++q) {
+            BlockPlane B = jobs[k].p[q];
+            B.block_base = J.total_blocks;
+            J.total_blocks += B.nblocks;
+            J.p[J.n++] = B;
+        }
+    }
+    if (flush() != cudaSuccess) return HIVC_E_CUDA;
+    for (size_t k = 0; k < nf; ++k) {
+        // the reference is the previous frame's output: no early copies
+        if (launch_fused_frame(d, frames[ks[k]].p, &outs[ks[k]], jobs[k], false) != cudaSuccess) return HIVC_E_CUDA;
+        d->cur ^= 1;
+        d->st.frames += 1;
+    }
+    return HIVC_OK;
+}
+
+}  // namespace
+
 hivc_status hivc_decode_batch(hivc_decoder *const *decs, const hivc_frame *frames, int32_t n, const hivc_out *outs)
 {
     if (n < 0 || (n > 0 && (!decs || !frames || !outs))) return HIVC_E_INVALID;
     hivc_status worst = HIVC_OK;
-    for (int k = 0; k < n; ++k) {
-        hivc_status s;
-        if (frames[k].type == 0)
-            s = hivc_decode_iframe(decs[k], frames[k].i, &outs[k]);
-        else if (frames[k].type == 1)
-            s = hivc_decode_pframe(decs[k], frames[k].p, &outs[k]);
-        else
-            s = HIVC_E_INVALID;
-        if (s != HIVC_OK && s != HIVC_E_NOT_CONVERGED) return s;
-        if (s != HIVC_OK) worst = s;
+    for (int i = 0; i < n;) {
+        if (frames[i].type != 1) {
+            if (frames[i].type != 0) return HIVC_E_INVALID;
+            const hivc_status s = hivc_decode_iframe(decs[i], frames[i].i, &outs[i]);
+            if (s != HIVC_OK && s != HIVC_E_NOT_CONVERGED) return s;
+            if (s != HIVC_OK) worst = s;
+            ++i;
+            continue;
+        }
+        // a run of inter frames [i, j): checked first, then decoded per
+        // decoder (one decoder's frames stay in order on its stream)
+        int j = i;
+        while (j < n && frames[j].type == 1) ++j;
+        std::vector<hivc_decoder *> ds;
+        for (int k = i; k < j; ++k) {
+            hivc_decoder *d = decs[k];
+            if (!pframe_ok(d, frames[k].p, &outs[k])) return HIVC_E_INVALID;
+            if (!d->has_ref) return HIVC_E_NO_REFERENCE;
+            if (std::find(ds.begin(), ds.end(), d) == ds.end()) ds.push_back(d);
+        }
+        for (hivc_decoder *d : ds) {
+            std::vector<int> ks;
+            for (int k = i; k < j; ++k)
+                if (decs[k] == d) ks.push_back(k);
+            hivc_status s;
+            if (fused_supported(d->cfg.block)) {
+                s = decode_inter_run(d, frames, outs, ks);
+            } else {
+                s = HIVC_OK;
+                for (int k : ks)
+                    if ((s = hivc_decode_pframe(d, frames[k].p, &outs[k])) != HIVC_OK) break;
+            }
+            if (s != HIVC_OK) return s;
+        }
+        i = j;
     }
     return worst;
 }
@@ -792,7 +938,6 @@ hivc_status hivc_decoder_sync(hivc_decoder *d, hivc_stats *last)
 // ---------------------------------------------------------------------------
 // step entry points
 // ---------------------------------------------------------------------------
-static size_t a256(size_t b) { return (b + 255) / 256 * 256; }
 
 size_t hivc_block_residual_workspace_bytes(int32_t width, int32_t height, int32_t block, int32_t n_points)
 {

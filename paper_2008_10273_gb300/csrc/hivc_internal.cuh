@@ -92,6 +92,7 @@ struct FusedFrame {
     uint8_t *out[3];
     int32_t ref_pitch[3], out_pitch[3];  // ref_out shares ref_pitch
     int32_t width, height, chroma, block;
+    int32_t early;      // 1: the references are complete at launch (copies may start at once)
     int32_t nmbx, nmb;  // filled by the launcher
 };
 

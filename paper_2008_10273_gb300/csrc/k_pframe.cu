@@ -16,8 +16,11 @@
 // one of two shared stages two macroblocks ahead, so that the copies of the
 // next macroblock are in flight while one is decoded; samples that leave
 // the halo read global memory.  The kernel is launched as a programmatic
-// dependent of the coefficient kernel: its first copies overlap that grid,
-// and griddepcontrol.wait orders the coefficient reads.
+// dependent of the preceding launch.  After this frame's coefficient kernel
+// its first copies overlap that grid (griddepcontrol.wait orders the
+// coefficient reads); after the previous frame's fused kernel (a batch of
+// frames, coefficients already complete) it waits for that grid, which
+// wrote its references, before the first copy.
 #include <cuda.h>
 
 #include "block_device.cuh"
@@ -541,18 +544,24 @@ __global__ void __launch_bounds__(kThreads, TMA ? 4 : 6) pframe_kernel(const __g
     int pend0 = TMA && (int)blockIdx.x < F.nmb ? 0 : -1, pend1 = TMA && (int)blockIdx.x + G < F.nmb ? 1 : -1;
     uint32_t ph0 = 0u, ph1 = 0u;
     bool ok = true;  // false after a copy timed out: the stages are not refilled
+    // early: the flow and the references were complete before the preceding
+    // launch (this frame's coefficient kernel) started, so the first copies
+    // may overlap it; otherwise the preceding launch wrote the references
+    if (!F.early) grid_dependency_wait();
     if (TMA && threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_proxy_async();
-        // the first two macroblocks' tiles; the flow and the references were
-        // complete before the coefficient kernel started
+        // the first two macroblocks' tiles
         if (pend0 >= 0) issue_stage<CHROMA>(F, stages[0], &bar[0], blockIdx.x, &mflow, &mrefy, &mrefcb, &mrefcr);
         if (pend1 >= 0) issue_stage<CHROMA>(F, stages[1], &bar[1], blockIdx.x + G, &mflow, &mrefy, &mrefcb, &mrefcr);
     }
     __syncthreads();
     // the coefficients are read from here on
     grid_dependency_wait();
+    // the next launch in the stream may start now: it waits for this grid's
+    // completion before it reads what this grid writes
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     int it = 0;
     for (int mb = blockIdx.x; mb < F.nmb; mb += G, ++it) {
         const int s = it & 1;

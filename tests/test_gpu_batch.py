@@ -1,0 +1,124 @@
+"""Batched decoding (hivc_decode_batch): the inter frames of a batch share
+multi-frame coefficient launches and run their fused kernels one after the
+other.  Every block is solved by the same arithmetic as in single-frame
+decoding, so a batch must reproduce the per-frame path bit for bit, and
+with it the FP64 oracle within the parity tolerance."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import TOL_PSNR_DB, TOL_RECON, hivc_module, psnr, to_np
+from workload import make_gop
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hv():
+    return hivc_module()
+
+
+def _planes(dec):
+    return [to_np(dec.reference(p)).astype(np.float64) for p in range(3 if dec.chroma else 1)]
+
+
+def _per_frame(hv, gop, W, H, chroma, B):
+    """Reference planes and uint8 outputs after every frame, one call each."""
+    dec = hv.Decoder(W, H, chroma=chroma, block=B)
+    out = hv.alloc_out(W, H, chroma=chroma)
+    refs, outs = [], []
+    for t in range(len(gop.pframes) + 1):
+        if t == 0:
+            dec.decode_iframe(hv.device_iframe(gop.iframe), out)
+        else:
+            dec.decode_pframe(hv.device_pframe(gop.pframes[t - 1]), out)
+        dec.sync()
+        refs.append(_planes(dec))
+        outs.append([to_np(o).copy() for o in out])
+    return refs, outs
+
+
+def _batched(hv, gop, W, H, chroma, B):
+    """The whole GOP in one hivc_decode_batch call, one output per frame."""
+    dec = hv.Decoder(W, H, chroma=chroma, block=B)
+    n = len(gop.pframes) + 1
+    outs = [hv.alloc_out(W, H, chroma=chroma) for _ in range(n)]
+    frames = [("i", hv.device_iframe(gop.iframe))] + [("p", hv.device_pframe(p)) for p in gop.pframes]
+    hv.decode_batch([dec] * n, frames, outs)
+    dec.sync()
+    return dec, [[to_np(o).copy() for o in out] for out in outs]
+
+
+@pytest.mark.parametrize("W,H,n,seed,B,chroma", [(160, 90, 12, 0, 16, True), (150, 70, 10, 2, 8, True),
+                                                 (96, 64, 19, 4, 16, False), (131, 67, 5, 3, 12, True)])
+def test_batch_matches_per_frame(hv, W, H, n, seed, B, chroma):
+    """More inter frames than one coefficient launch takes (8 with chroma,
+    16 grey) for B = 16 and 8; B = 12 decodes frame by frame."""
+    gop = make_gop(seed, W, H, n_frames=n, block=B, chroma=chroma)
+    refs, outs = _per_frame(hv, gop, W, H, chroma, B)
+    dec, bouts = _batched(hv, gop, W, H, chroma, B)
+    for t in range(n):
+        for p in range(len(outs[t])):
+            assert np.array_equal(bouts[t][p], outs[t][p]), (t, p)
+    for p, g in enumerate(_planes(dec)):
+        assert np.array_equal(g, refs[-1][p]), p
+    # and the oracle, for the last frame
+    rec, _ = oracle.decode_gop(gop)[-1]
+    for p, g in enumerate(_planes(dec)):
+        assert np.abs(g - rec[p]).max() <= TOL_RECON, p
+        assert abs(psnr(g, gop.sources[-1][p]) - psnr(rec[p], gop.sources[-1][p])) <= TOL_PSNR_DB
+
+
+def test_batch_with_large_blocks(hv):
+    """Blocks with K > 32 are solved by a whole CTA in the scratch slot of
+    their range: every frame's range gets its own slot."""
+    W, H = 128, 96
+    gop = make_gop(5, W, H, n_frames=6, chroma=False, lam_y=30.0, residual_kw={"kmax": 60})
+    refs, outs = _per_frame(hv, gop, W, H, False, 16)
+    dec, bouts = _batched(hv, gop, W, H, False, 16)
+    for t in range(len(outs)):
+        assert np.array_equal(bouts[t][0], outs[t][0]), t
+    assert np.array_equal(_planes(dec)[0], refs[-1][0])
+
+
+def test_batch_two_decoders_interleaved(hv):
+    """Frames of two decoders of different sizes interleaved in one batch:
+    each decoder's frames stay in order and equal its own decoding."""
+    ga = make_gop(6, 160, 90, n_frames=4)
+    gb = make_gop(7, 96, 64, n_frames=5, chroma=False)
+    ra, oa = _per_frame(hv, ga, 160, 90, True, 16)
+    rb, ob = _per_frame(hv, gb, 96, 64, False, 16)
+    da = hv.Decoder(160, 90, chroma=True)
+    db = hv.Decoder(96, 64, chroma=False)
+    decs, frames, outs, tags = [], [], [], []
+    seq = [("a", 0), ("b", 0)] + [x for t in range(1, 5) for x in (("a", t), ("b", t)) if not (x[0] == "a" and t >= 4)]
+    for who, t in seq:
+        g, d, ch, (W, H) = (ga, da, True, (160, 90)) if who == "a" else (gb, db, False, (96, 64))
+        decs.append(d)
+        frames.append(("i", hv.device_iframe(g.iframe)) if t == 0 else ("p", hv.device_pframe(g.pframes[t - 1])))
+        outs.append(hv.alloc_out(W, H, chroma=ch))
+        tags.append((who, t))
+    hv.decode_batch(decs, frames, outs)
+    da.sync()
+    db.sync()
+    for (who, t), out in zip(tags, outs):
+        ref = oa if who == "a" else ob
+        for p, o in enumerate(out):
+            assert np.array_equal(to_np(o), ref[t][p]), (who, t, p)
+    for p, g in enumerate(_planes(da)):
+        assert np.array_equal(g, ra[-1][p])
+    assert np.array_equal(_planes(db)[0], rb[-1][0])
+
+
+def test_batch_rejects_a_bad_frame(hv):
+    """An inter run is checked before any of it is launched: an output
+    plane narrower than the frame makes the call fail with HIVC_E_INVALID."""
+    W, H = 64, 48
+    gop = make_gop(8, W, H, n_frames=3, chroma=False)
+    dec = hv.Decoder(W, H, chroma=False)
+    outs = [hv.alloc_out(W, H, chroma=False) for _ in range(2)] + [hv.alloc_out(W - 8, H, chroma=False)]
+    frames = [("i", hv.device_iframe(gop.iframe))] + [("p", hv.device_pframe(p)) for p in gop.pframes]
+    with pytest.raises(hv.HivcError) as e:
+        hv.decode_batch([dec] * 3, frames, outs)
+    assert e.value.status == hv.HIVC_E_INVALID
+    dec.sync()
