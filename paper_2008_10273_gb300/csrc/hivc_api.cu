@@ -219,10 +219,11 @@ bool out_ok(const hivc_decoder *d, const hivc_out *o)
 // block_ptr/pos: one factorisation, two right-hand sides).  coef/acoef: the
 // per-plane coefficient arrays (the decoder's own when null).
 hivc_status make_block_jobs(hivc_decoder *d, const hivc_residual *res, BlockJobs &J, float *const *coef = nullptr,
-                            float *const *acoef = nullptr)
+                            float *const *acoef = nullptr, float *const *rfield = nullptr)
 {
     if (!coef) coef = d->coef;
     if (!acoef) acoef = d->acoef;
+    if (!rfield) rfield = d->rfield;
     J = BlockJobs{};
     for (int p = 0; p < d->np; ++p)
         if ((int64_t)res[p].n_points > (int64_t)d->pg[p].w * d->pg[p].h) return HIVC_E_INVALID;
@@ -238,8 +239,8 @@ hivc_status make_block_jobs(hivc_decoder *d, const hivc_residual *res, BlockJobs
         B.coef[1] = p2 >= 0 ? coef[p2] : nullptr;
         B.acoef[0] = acoef[p];
         B.acoef[1] = p2 >= 0 ? acoef[p2] : nullptr;
-        B.r[0] = d->rfield[p];
-        B.r[1] = p2 >= 0 ? d->rfield[p2] : nullptr;
+        B.r[0] = rfield[p];
+        B.r[1] = p2 >= 0 ? rfield[p2] : nullptr;
         B.r_pitch = g.pitch;
         B.n_points = res[p].n_points;
         B.width = g.w;
@@ -703,6 +704,41 @@ cudaError_t launch_fused_frame(hivc_decoder *d, const hivc_pframe *f, const hivc
     return e;
 }
 
+// The warp + residual + pack kernel of frame f, whose residual planes
+// (plane pitches) were evaluated before, into the next reference buffer.
+cudaError_t launch_rf_frame(hivc_decoder *d, const hivc_pframe *f, const hivc_out *out, float *r0, float *r1,
+                            float *r2)
+{
+    const int nxt = d->cur ^ 1;
+    FusedFrame F{};
+    F.flow = f->flow;
+    float *const rf[3] = {r0, r1, r2};
+    FusedMaps M = d->maps[d->cur];
+    for (int p = 0; p < d->np; ++p) {
+        const PlaneGeom &g = d->pg[p];
+        F.ref[p] = d->ref[d->cur][p];
+        F.ref_out[p] = d->ref[nxt][p];
+        F.ref_pitch[p] = g.pitch;
+        F.out[p] = out->plane[p];
+        F.out_pitch[p] = out->pitch[p];
+        F.rfield[p] = rf[p];
+        F.rfield_pitch[p] = g.pitch;
+        const uint32_t box = p == 0 ? 32 : 16;
+        if (!encode_map_2d(&M.rf[p], rf[p], g.w, g.h, 4 * (uint64_t)g.pitch, box, box)) return cudaErrorInvalidValue;
+    }
+    F.width = d->cfg.width;
+    F.height = d->cfg.height;
+    F.chroma = d->cfg.chroma;
+    F.block = d->cfg.block;
+    if (!encode_map_2d(&M.flow, f->flow, 2 * (uint64_t)d->cfg.width, d->cfg.height, 8 * (uint64_t)d->cfg.width, 64,
+                       32))
+        return cudaErrorInvalidValue;
+    Timed t(d, 7);
+    const cudaError_t e = launch_pframe_rf(F, M, d->flags, d->stream, !d->timing);
+    t.done(1);
+    return e;
+}
+
 hivc_status hivc_decode_pframe(hivc_decoder *d, const hivc_pframe *f, const hivc_out *out)
 {
     if (!d || !f || !out_ok(d, out) || !f->flow) return HIVC_E_INVALID;
@@ -794,52 +830,80 @@ hivc_status ensure_pool(hivc_decoder *d, size_t bytes)
     return HIVC_OK;
 }
 
-// The inter frames frames[k] (k in ks, in order) of decoder d: coefficient
-// launches over several frames at once (up to kMaxJobs block jobs each),
-// each frame's coefficients in its own part of the batch pool, then the
-// fused kernel of each frame in order.  Every frame has been checked.
+// The inter frames frames[k] (k in ks, in order) of decoder d.  Block
+// stage over several frames at once: per up to kMaxJobs block jobs (8 FullHD
+// 4:2:0 frames) one coefficient launch and one evaluation launch into each
+// frame's residual planes, all in the batch pool; then per frame the
+// warp + residual + pack kernel with the residual tiles staged by TMA.
+// Where the flow cannot be described by a tensor map (odd width) the fused
+// kernel evaluates the residual itself.  Every frame has been checked.
 hivc_status decode_inter_run(hivc_decoder *d, const hivc_frame *frames, const hivc_out *outs,
                              const std::vector<int> &ks)
 {
     if (cudaSetDevice(d->device) != cudaSuccess) return HIVC_E_CUDA;
     const size_t nf = ks.size();
-    // pool layout: per frame and plane a256(4 n_points) + a256(4 nblocks),
-    // then the K > 32 scratch of the largest coefficient launch
-    std::vector<size_t> off(nf * 3 * 2);
+    const bool rf = d->maps_ok && d->cfg.width % 2 == 0;
+    // pool layout: per frame and plane a256(4 n_points) + a256(4 nblocks)
+    // (+ the residual plane, h x pitch floats), then the K > 32 scratch of
+    // the largest coefficient launch
+    std::vector<size_t> off(nf * 3 * 3);
     size_t bytes = 0;
     for (size_t k = 0; k < nf; ++k)
         for (int p = 0; p < d->np; ++p) {
-            off[(k * 3 + p) * 2] = bytes;
+            const PlaneGeom &g = d->pg[p];
+            off[(k * 3 + p) * 3] = bytes;
             bytes += a256(4 * (size_t)frames[ks[k]].p->res[p].n_points);
-            off[(k * 3 + p) * 2 + 1] = bytes;
-            bytes += a256(4 * (size_t)d->pg[p].nblocks);
+            off[(k * 3 + p) * 3 + 1] = bytes;
+            bytes += a256(4 * (size_t)g.nblocks);
+            off[(k * 3 + p) * 3 + 2] = bytes;
+            if (rf) bytes += a256(4 * (size_t)g.h * g.pitch);
         }
     int fblocks = 0;
     for (int p = 0; p < d->np; ++p) fblocks += d->pg[p].nblocks;
-    const int per_launch = kMaxJobs / d->np;  // frames per coefficient launch (at most np jobs each)
-    const int ranges = block_ranges(per_launch * fblocks);
+    // frames per coefficient launch: a frame has one job per plane, or one
+    // less when Cb and Cr share their layout (the job count make_block_jobs
+    // gives); the fewest jobs per frame make the largest launch
+    int min_jobs = d->np;
+    for (size_t k = 0; k < nf; ++k) {
+        const hivc_residual *r = frames[ks[k]].p->res;
+        if (d->np == 3 && r[1].block_ptr == r[2].block_ptr && r[1].pos == r[2].pos && r[1].n_points == r[2].n_points)
+            min_jobs = 2;
+    }
+    const int ranges = block_ranges((kMaxJobs / min_jobs) * fblocks);
     const size_t big_off = bytes;
     bytes += (size_t)ranges * kBigFloats * sizeof(float);
     hivc_status s = ensure_pool(d, bytes);
     if (s != HIVC_OK) return s;
     char *pool = static_cast<char *>(d->pool);
+    auto at = [&](size_t k, int p, int w) {
+        return p < d->np ? reinterpret_cast<float *>(pool + off[(k * 3 + p) * 3 + w]) : nullptr;
+    };
     std::vector<BlockJobs> jobs(nf);
     for (size_t k = 0; k < nf; ++k) {
-        float *coef[3], *acoef[3];
+        float *coef[3], *acoef[3], *rfield[3];
         for (int p = 0; p < 3; ++p) {
-            coef[p] = p < d->np ? reinterpret_cast<float *>(pool + off[(k * 3 + p) * 2]) : nullptr;
-            acoef[p] = p < d->np ? reinterpret_cast<float *>(pool + off[(k * 3 + p) * 2 + 1]) : nullptr;
+            coef[p] = at(k, p, 0);
+            acoef[p] = at(k, p, 1);
+            rfield[p] = rf ? at(k, p, 2) : nullptr;
         }
-        if ((s = make_block_jobs(d, frames[ks[k]].p->res, jobs[k], coef, acoef)) != HIVC_OK) return s;
+        if ((s = make_block_jobs(d, frames[ks[k]].p->res, jobs[k], coef, acoef, rfield)) != HIVC_OK) return s;
     }
     const BlockScratch S{d->flags, reinterpret_cast<float *>(pool + big_off), ranges};
     BlockJobs J{};
     auto flush = [&]() -> cudaError_t {
         if (J.n == 0) return cudaSuccess;
-        Timed t(d, 3);
-        int l = 0;
-        const cudaError_t e = launch_block_coef(J, S, d->stream, &l);
-        t.done(l);
+        cudaError_t e;
+        {
+            Timed t(d, 3);
+            int l = 0;
+            e = launch_block_coef(J, S, d->stream, &l);
+            t.done(l);
+        }
+        if (e == cudaSuccess && rf) {
+            Timed t(d, 5);
+            e = launch_block_eval(J, d->flags, d->stream);
+            t.done(1);
+        }
         J = BlockJobs{};
         return e;
     };
@@ -854,8 +918,14 @@ hivc_status decode_inter_run(hivc_decoder *d, const hivc_frame *frames, const hi
     }
     if (flush() != cudaSuccess) return HIVC_E_CUDA;
     for (size_t k = 0; k < nf; ++k) {
-        // the reference is the previous frame's output: no early copies
-        if (launch_fused_frame(d, frames[ks[k]].p, &outs[ks[k]], jobs[k], false) != cudaSuccess) return HIVC_E_CUDA;
+        const hivc_pframe *f = frames[ks[k]].p;
+        cudaError_t e;
+        e = rf ? launch_rf_frame(d, f, &outs[ks[k]], at(k, 0, 2), at(k, 1, 2), at(k, 2, 2)) : cudaErrorInvalidValue;
+        // no residual planes, or a flow no tensor map describes (unaligned):
+        // the fused kernel evaluates the residual from the coefficients; the
+        // reference is the previous frame's output, so no early copies
+        if (e == cudaErrorInvalidValue) e = launch_fused_frame(d, f, &outs[ks[k]], jobs[k], false);
+        if (e != cudaSuccess) return HIVC_E_CUDA;
         d->cur ^= 1;
         d->st.frames += 1;
     }

@@ -94,6 +94,9 @@ struct FusedFrame {
     int32_t width, height, chroma, block;
     int32_t early;      // 1: the references are complete at launch (copies may start at once)
     int32_t nmbx, nmb;  // filled by the launcher
+    // residual-field variant: the evaluated residual planes (pitch floats)
+    const float *rfield[3];
+    int32_t rfield_pitch[3];
 };
 
 // Tensor maps of the TMA variant: the frame's flow (2W x H floats, box
@@ -102,6 +105,7 @@ struct FusedFrame {
 struct FusedMaps {
     CUtensorMap flow;
     CUtensorMap ref[3];
+    CUtensorMap rf[3];  // residual fields (box 32 x 32 luma, 16 x 16 chroma)
 };
 
 bool fused_supported(int block);
@@ -109,6 +113,10 @@ cudaError_t fused_init();  // once per device
 // maps == nullptr: the variant with global loads only.  pdl: launch as a
 // programmatic dependent of the previous kernel in the stream.
 cudaError_t launch_pframe_fused(FusedFrame &f, const FusedMaps *maps, uint32_t *flags, cudaStream_t st, bool pdl);
+// Warp + residual + clamp + pack of a frame whose residual planes were
+// evaluated before (F.rfield, maps->rf): the fused kernel without its
+// residual phase.  maps must hold the flow, reference and residual maps.
+cudaError_t launch_pframe_rf(FusedFrame &f, const FusedMaps &maps, uint32_t *flags, cudaStream_t st, bool pdl);
 // 2-D float32 tensor map (no swizzle, zero fill); false if not encodable
 bool encode_map_2d(CUtensorMap *m, const void *base, uint64_t w, uint64_t h, uint64_t row_bytes, uint32_t box_w,
                    uint32_t box_h);

@@ -502,57 +502,126 @@ __global__ void __launch_bounds__(kCoefThreads, 3) block_coef_kernel(const __gri
 }
 
 // ---- evaluation stage into residual fields, one warp per block -----------
-__global__ void __launch_bounds__(128) block_eval_kernel(const __grid_constant__ BlockJobs J, BlockTables tab,
-                                                         uint32_t *flags)
+// Lane l covers the block pixels 8l .. 8l+7 (index y w + x).  The points sit
+// in the lanes, 32 at a time; c_j and p_j reach every lane by shuffles, and
+// the Green's rows of several points are in flight (16-byte loads) before
+// their products are summed.  The constant a is loaded beside the block
+// pointers.  A 16-wide block row goes out as two 16-byte stores per lane;
+// then the data at the points, exactly.  Bad positions give a zero block.
+template <bool TWO>
+__device__ __forceinline__ void eval_block(const BlockPlane &P, const BlockGeom &g, const float *__restrict__ G,
+                                           float a0, float a1, float *R0, float *R1, int pitch, int lane,
+                                           uint32_t *flags)
 {
-    __shared__ float cs[4][2][256];
-    __shared__ unsigned char ps[4][256];
+    const int K = g.K, w = g.w, N = g.w * g.h, rl = g_rowlen(N);
+    const int q0 = 8 * lane;
+    const bool act = q0 < N;
+    float r0[8], r1[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        r0[t] = a0;
+        r1[t] = a1;
+    }
+    bool valid = K > 0;
+    int prev = -1;
+    for (int j0 = 0; j0 < K; j0 += 32) {
+        const int j = j0 + lane;
+        int p = 0;
+        float c0 = 0.f, c1 = 0.f;
+        if (j < K) {
+            p = __ldg(P.pos + g.s + j);
+            c0 = __ldg(P.coef[0] + g.s + j);
+            if (TWO) c1 = __ldg(P.coef[1] + g.s + j);
+        }
+        // inside the block and increasing (the previous chunk's last point
+        // for lane 0)
+        const int up = __shfl_up_sync(0xffffffffu, p, 1);  // every lane takes part
+        const int before = lane == 0 ? prev : up;
+        if (__any_sync(0xffffffffu, j < K && (p >= N || p <= before))) valid = false;
+        prev = __shfl_sync(0xffffffffu, p, 31);
+        if (!valid) break;
+        const int n = min(32, K - j0);
+        const float *Gq = G + q0;
+#pragma unroll 4
+        for (int u = 0; u < n; ++u) {
+            const float cu0 = __shfl_sync(0xffffffffu, c0, u);
+            const float cu1 = TWO ? __shfl_sync(0xffffffffu, c1, u) : 0.f;
+            const int pu = __shfl_sync(0xffffffffu, p, u);
+            if (act) {
+                const float4 *row = reinterpret_cast<const float4 *>(Gq + pu * rl);
+                const float4 lo = __ldg(row), hi = __ldg(row + 1);
+                const float gv[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    r0[t] = fmaf(cu0, gv[t], r0[t]);
+                    if (TWO) r1[t] = fmaf(cu1, gv[t], r1[t]);
+                }
+            }
+        }
+    }
+    if (!valid) {
+        if (K > 0 && lane == 0) atomicOr(flags, kFlagPos);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) r0[t] = r1[t] = 0.f;
+    }
+    // 16-byte stores need 16-byte aligned rows (callers may pass any pitch)
+    const bool vec = w == 16 && ((reinterpret_cast<uintptr_t>(R0) | reinterpret_cast<uintptr_t>(R1) |
+                                  (uintptr_t)pitch * 4) & 15) == 0;
+    if (act) {
+        if (vec) {
+            // pixels 8l .. 8l+7 are columns 8 (l % 2) .. +7 of row l / 2
+            const size_t o = (size_t)(lane >> 1) * pitch + 8 * (lane & 1);
+            reinterpret_cast<float4 *>(R0 + o)[0] = make_float4(r0[0], r0[1], r0[2], r0[3]);
+            reinterpret_cast<float4 *>(R0 + o)[1] = make_float4(r0[4], r0[5], r0[6], r0[7]);
+            if (TWO && R1) {
+                reinterpret_cast<float4 *>(R1 + o)[0] = make_float4(r1[0], r1[1], r1[2], r1[3]);
+                reinterpret_cast<float4 *>(R1 + o)[1] = make_float4(r1[4], r1[5], r1[6], r1[7]);
+            }
+        } else {
+            int y = q0 / w, x = q0 - y * w;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                if (q0 + t < N) {
+                    R0[(size_t)y * pitch + x] = r0[t];
+                    if (TWO && R1) R1[(size_t)y * pitch + x] = r1[t];
+                }
+                if (++x == w) {
+                    x = 0;
+                    ++y;
+                }
+            }
+        }
+    }
+    if (!valid) return;
+    __syncwarp();
+    // the data at the points, exactly
+    const float rw = __frcp_rn((float)w);
+    for (int j = lane; j < K; j += 32) {
+        const int p = __ldg(P.pos + g.s + j);
+        const int y = __float2int_rz(((float)p + 0.5f) * rw), x = p - y * w;  // p / w, exact for p < 256
+        R0[(size_t)y * pitch + x] = (float)__ldg(P.val[0] + g.s + j);
+        if (TWO && R1) R1[(size_t)y * pitch + x] = (float)__ldg(P.val[1] + g.s + j);
+    }
+}
+
+__global__ void __launch_bounds__(128, 8) block_eval_kernel(const __grid_constant__ BlockJobs J, BlockTables tab,
+                                                            uint32_t *flags)
+{
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gb = blockIdx.x * 4 + warp;
     if (gb >= J.total_blocks) return;
     const BlockPlane &P = J.p[find_job(J, gb)];
-    const BlockGeom g = block_geom(P, gb - P.block_base);
-    const int K = g.K, w = g.w, N = g.w * g.h;
+    const int lb = gb - P.block_base;
     const bool two = P.val[1] != nullptr;
-    bool valid = true;
-    for (int j0 = 0; j0 < K; j0 += 32) {
-        int p = 0;
-        const bool ok = (j0 + lane < K) ? load_pos(P, g, j0 + lane, p) : true;
-        valid = valid && !__any_sync(0xffffffffu, !ok);
-        if (j0 + lane < K) {
-            ps[warp][j0 + lane] = (unsigned char)p;
-            cs[warp][0][j0 + lane] = __ldg(P.coef[0] + g.s + j0 + lane);
-            if (two) cs[warp][1][j0 + lane] = __ldg(P.coef[1] + g.s + j0 + lane);
-        }
-    }
-    if (!valid && lane == 0) atomicOr(flags, kFlagPos);
-    __syncwarp();
+    // a depends on the block index only: its load goes out with the pointers
+    const float a0 = __ldg(P.acoef[0] + lb), a1 = two ? __ldg(P.acoef[1] + lb) : 0.f;
+    const BlockGeom g = block_geom(P, lb);
     const int pitch = P.r_pitch;
     float *R0 = P.r[0] + (size_t)g.y0 * pitch + g.x0;
     float *R1 = two && P.r[1] ? P.r[1] + (size_t)g.y0 * pitch + g.x0 : nullptr;
-    if (K == 0 || !valid) {
-        for (int i = lane; i < N; i += 32) {
-            R0[(i / w) * pitch + i % w] = 0.f;
-            if (R1) R1[(i / w) * pitch + i % w] = 0.f;
-        }
-        return;
-    }
-    const float a0 = __ldg(P.acoef[0] + g.lb), a1 = two ? __ldg(P.acoef[1] + g.lb) : 0.f;
     const float *G = green_rows(tab, g.w, g.h);
-    auto out = [&](int x, int y, float v0, float v1) {
-        const int o = y * pitch + x;
-        R0[o] = v0;
-        if (R1) R1[o] = v1;
-    };
-    if (two) warp_block_eval<true>(G, w, N, K, ps[warp], cs[warp][0], cs[warp][1], a0, a1, lane, out);
-    else warp_block_eval<false>(G, w, N, K, ps[warp], cs[warp][0], cs[warp][1], a0, a1, lane, out);
-    __syncwarp();
-    // the data at the points, exactly
-    for (int j = lane; j < K; j += 32) {
-        const size_t o = (size_t)(ps[warp][j] / w) * pitch + ps[warp][j] % w;
-        R0[o] = (float)__ldg(P.val[0] + g.s + j);
-        if (R1) R1[o] = (float)__ldg(P.val[1] + g.s + j);
-    }
+    if (two) eval_block<true>(P, g, G, a0, a1, R0, R1, pitch, lane, flags);
+    else eval_block<false>(P, g, G, a0, a1, R0, R1, pitch, lane, flags);
 }
 
 }  // namespace

@@ -410,6 +410,15 @@ __device__ __forceinline__ PixelCtx pixel_ctx(const FusedFrame &F)
     return c;
 }
 
+// The residual of a macroblock as phase C reads it: luma rows yp floats
+// apart, the two chroma planes' rows cp floats apart (shared tiles, or the
+// global residual fields at the macroblock's origin).
+struct ResView {
+    const float *y;
+    const float *c[2];
+    int yp, cp;
+};
+
 // Thread (x, ty) takes luma rows 2 ty + 8 jj + {0, 1} of column x and
 // chroma row ty + 4 jj of column x / 2 in plane x & 1, whose flow is half
 // the mean of the four co-sited luma vectors: the thread's two rows and the
@@ -418,10 +427,11 @@ __device__ __forceinline__ PixelCtx pixel_ctx(const FusedFrame &F)
 // checks.  Otherwise each sample is checked and the ones that leave the
 // staged tile (or all, st = null) read global memory.
 template <bool CHROMA, bool FAST>
-__device__ __forceinline__ void phase_c(const PixelCtx &c, const float *ryt, const float *rct, const Stage *st, int mx,
-                                        int my, const float2 *__restrict__ fl)
+__device__ __forceinline__ void phase_c(const PixelCtx &c, const ResView &R, const Stage *st, int mx, int my,
+                                        const float2 *__restrict__ fl)
 {
     const int W = c.W, H = c.H;
+    const float *rcp = (threadIdx.x & 1) ? R.c[1] : R.c[0];
     const int x = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int gx = mx * kMB + x;
     const int tx0 = mx * kMB - kHalo, ty0 = my * kMB - kHalo;
@@ -455,7 +465,7 @@ __device__ __forceinline__ void phase_c(const PixelCtx &c, const float *ryt, con
                 pred = fast ? tile_lerp<kTL>(&st->ry[0][0], lx, lyy, ax, ay)
                             : sample_global(c.ry0, c.yp, W, H, gx, gy, f[rr].x, f[rr].y);
             }
-            put_pixel(pred, ryt[ly * kRYP + x], c.oy0 + (size_t)gy * c.yp + gx, c.uy0 + (size_t)gy * c.op + gx);
+            put_pixel(pred, R.y[ly * R.yp + x], c.oy0 + (size_t)gy * c.yp + gx, c.uy0 + (size_t)gy * c.op + gx);
         }
         if (CHROMA) {
             float sx = f[0].x + f[1].x, sy = f[0].y + f[1].y;
@@ -482,7 +492,7 @@ __device__ __forceinline__ void phase_c(const PixelCtx &c, const float *ryt, con
                     pred = fast ? tile_lerp<kTC>(&st->rc[cp][0][0], lx, lyy, ax, ay)
                                 : sample_global(c.rcp, c.cpitch, c.cw, c.chh, cxg, cyg, dx, dy);
                 }
-                put_pixel(pred, rct[cp * kRCS + j * kRCP + cx], c.ocp + (size_t)cyg * c.cpitch + cxg,
+                put_pixel(pred, rcp[j * R.cp + cx], c.ocp + (size_t)cyg * c.cpitch + cxg,
                           c.ucp + (size_t)cyg * c.uop + cxg);
             }
         }
@@ -587,10 +597,11 @@ __global__ void __launch_bounds__(kThreads, TMA ? 4 : 6) pframe_kernel(const __g
         const Stage *st = landed ? &stages[s] : nullptr;
         const bool interior = mx * kMB - kHalo >= 0 && my * kMB - kHalo >= 0 &&
                               mx * kMB - kHalo + kTL <= F.width && my * kMB - kHalo + kTL <= F.height;
+        const ResView R{T.ry, {T.rc, T.rc + kRCS}, kRYP, kRCP};
         if (__syncthreads_and(landed && interior && small_flow(stages[s])))
-            phase_c<CHROMA, true>(pc, T.ry, T.rc, st, mx, my, fl);
+            phase_c<CHROMA, true>(pc, R, st, mx, my, fl);
         else
-            phase_c<CHROMA, false>(pc, T.ry, T.rc, st, mx, my, fl);
+            phase_c<CHROMA, false>(pc, R, st, mx, my, fl);
         // a copy that timed out may still land later: from then on no stage
         // is refilled (the barrier also frees stage s and the tiles)
         if (__syncthreads_or(issued && !landed)) ok = false;
@@ -606,6 +617,123 @@ __global__ void __launch_bounds__(kThreads, TMA ? 4 : 6) pframe_kernel(const __g
     // bounded: let a copy that timed out land before the CTA exits
     if (TMA && pend0 >= 0) mbar_wait(&bar[0], ph0);
     if (TMA && pend1 >= 0) mbar_wait(&bar[1], ph1);
+}
+
+// ---- residual-field variant ----------------------------------------------
+// The stage plus the macroblock's residual tiles (the residual planes were
+// evaluated by the block kernels).
+struct __align__(128) StageR {
+    Stage s;
+    float ry[kMB][kMB];
+    float rc[2][kMB / 2][kMB / 2];
+};
+
+template <bool CHROMA>
+__device__ __forceinline__ void issue_stage_rf(const FusedFrame &F, StageR &st, uint64_t *bar, int mb,
+                                               const CUtensorMap *mf, const CUtensorMap *mry, const CUtensorMap *mcb,
+                                               const CUtensorMap *mcr, const CUtensorMap *mrfy,
+                                               const CUtensorMap *mrfb, const CUtensorMap *mrfr)
+{
+    const int mx = mb % F.nmbx, my = mb / F.nmbx;
+    const uint32_t bytes = sizeof(st.s.flow) + sizeof(st.s.ry) + sizeof(st.ry) +
+                           (CHROMA ? sizeof(st.s.rc) + sizeof(st.rc) : 0);
+    mbar_expect_tx(bar, bytes);
+    tma_load_2d(&st.s.flow[0][0], mf, mx * 2 * kMB, my * kMB, bar);
+    tma_load_2d(&st.s.ry[0][0], mry, mx * kMB - kHalo, my * kMB - kHalo, bar);
+    tma_load_2d(&st.ry[0][0], mrfy, mx * kMB, my * kMB, bar);
+    if (CHROMA) {
+        tma_load_2d(&st.s.rc[0][0][0], mcb, mx * (kMB / 2) - kCHalo, my * (kMB / 2) - kCHalo, bar);
+        tma_load_2d(&st.s.rc[1][0][0], mcr, mx * (kMB / 2) - kCHalo, my * (kMB / 2) - kCHalo, bar);
+        tma_load_2d(&st.rc[0][0][0], mrfb, mx * (kMB / 2), my * (kMB / 2), bar);
+        tma_load_2d(&st.rc[1][0][0], mrfr, mx * (kMB / 2), my * (kMB / 2), bar);
+    }
+}
+
+constexpr size_t kRfSmem = 2 * sizeof(StageR) + 16;
+
+// Warp + residual + clamp + pack with the residual tiles staged beside the
+// flow and reference tiles; the same macroblock order, stages and waits as
+// the fused kernel.  A macroblock whose copies timed out reads the
+// residual planes from global memory.
+template <bool CHROMA>
+__global__ void __launch_bounds__(kThreads, 4) pframe_rf_kernel(const __grid_constant__ FusedFrame F,
+                                                                const __grid_constant__ FusedMaps M, uint32_t *flags)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    StageR *stages = reinterpret_cast<StageR *>(smem);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * sizeof(StageR));
+    const int G = gridDim.x;
+    const PixelCtx pc = pixel_ctx<CHROMA>(F);
+    const float2 *fl = reinterpret_cast<const float2 *>(F.flow);
+    int pend0 = (int)blockIdx.x < F.nmb ? 0 : -1, pend1 = (int)blockIdx.x + G < F.nmb ? 1 : -1;
+    uint32_t ph0 = 0u, ph1 = 0u;
+    bool ok = true;
+    // the preceding launch may have written the references or the residual
+    // planes (its own frame's evaluation, or the previous frame)
+    grid_dependency_wait();
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_proxy_async();
+        if (pend0 >= 0)
+            issue_stage_rf<CHROMA>(F, stages[0], &bar[0], blockIdx.x, &M.flow, &M.ref[0], &M.ref[1], &M.ref[2],
+                                   &M.rf[0], &M.rf[1], &M.rf[2]);
+        if (pend1 >= 0)
+            issue_stage_rf<CHROMA>(F, stages[1], &bar[1], blockIdx.x + G, &M.flow, &M.ref[0], &M.ref[1], &M.ref[2],
+                                   &M.rf[0], &M.rf[1], &M.rf[2]);
+    }
+    __syncthreads();
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    int it = 0;
+    for (int mb = blockIdx.x; mb < F.nmb; mb += G, ++it) {
+        const int s = it & 1;
+        const int mx = mb % F.nmbx, my = mb / F.nmbx;
+        const bool issued = (s ? pend1 : pend0) == it;
+        bool landed = false;
+        if (issued) {
+            landed = mbar_wait(&bar[s], s ? ph1 : ph0);
+            if (landed) {
+                if (s) {
+                    ph1 ^= 1u;
+                    pend1 = -1;
+                } else {
+                    ph0 ^= 1u;
+                    pend0 = -1;
+                }
+            } else if (threadIdx.x == 0) {
+                atomicOr(flags, kFlagTimeout);
+            }
+        }
+        ResView R;
+        if (landed) {
+            R = ResView{&stages[s].ry[0][0], {&stages[s].rc[0][0][0], &stages[s].rc[1][0][0]}, kMB, kMB / 2};
+        } else {
+            const size_t cy = (size_t)my * (kMB / 2), cx = (size_t)mx * (kMB / 2);
+            R = ResView{F.rfield[0] + (size_t)my * kMB * F.rfield_pitch[0] + (size_t)mx * kMB,
+                        {CHROMA ? F.rfield[1] + cy * F.rfield_pitch[1] + cx : nullptr,
+                         CHROMA ? F.rfield[2] + cy * F.rfield_pitch[2] + cx : nullptr},
+                        F.rfield_pitch[0], CHROMA ? F.rfield_pitch[1] : 0};
+        }
+        const bool interior = mx * kMB - kHalo >= 0 && my * kMB - kHalo >= 0 &&
+                              mx * kMB - kHalo + kTL <= F.width && my * kMB - kHalo + kTL <= F.height;
+        const Stage *st = landed ? &stages[s].s : nullptr;
+        if (__syncthreads_and(landed && interior && small_flow(stages[s].s)))
+            phase_c<CHROMA, true>(pc, R, st, mx, my, fl);
+        else
+            phase_c<CHROMA, false>(pc, R, st, mx, my, fl);
+        if (__syncthreads_or(issued && !landed)) ok = false;
+        if (ok && mb + 2 * G < F.nmb) {
+            if (s) pend1 = it + 2;
+            else pend0 = it + 2;
+            if (threadIdx.x == 0) {
+                fence_proxy_async();
+                issue_stage_rf<CHROMA>(F, stages[s], &bar[s], mb + 2 * G, &M.flow, &M.ref[0], &M.ref[1], &M.ref[2],
+                                       &M.rf[0], &M.rf[1], &M.rf[2]);
+            }
+        }
+    }
+    if (pend0 >= 0) mbar_wait(&bar[0], ph0);
+    if (pend1 >= 0) mbar_wait(&bar[1], ph1);
 }
 
 template <class Kern>
@@ -646,7 +774,33 @@ cudaError_t fused_init()
     if ((e = allow_smem<true, 16, true>()) != cudaSuccess) return e;
     if ((e = allow_smem<false, 16, true>()) != cudaSuccess) return e;
     if ((e = allow_smem<true, 8, true>()) != cudaSuccess) return e;
-    return allow_smem<false, 8, true>();
+    if ((e = allow_smem<false, 8, true>()) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(pframe_rf_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kRfSmem)) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(pframe_rf_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRfSmem);
+}
+
+cudaError_t launch_pframe_rf(FusedFrame &F, const FusedMaps &maps, uint32_t *flags, cudaStream_t st, bool pdl)
+{
+    F.nmbx = (F.width + kMB - 1) / kMB;
+    F.nmb = F.nmbx * ((F.height + kMB - 1) / kMB);
+    const BlockTables &t = block_tables();
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cfg.dynamicSmemBytes = kRfSmem;
+    static int occ[2] = {0, 0};
+    const int c = F.chroma ? 1 : 0;
+    if (occ[c] == 0) occ[c] = c ? occupancy(pframe_rf_kernel<true>, kRfSmem) : occupancy(pframe_rf_kernel<false>, kRfSmem);
+    cfg.gridDim = dim3(std::max(1, std::min(F.nmb, t.sms * occ[c])));
+    if (c) return cudaLaunchKernelEx(&cfg, pframe_rf_kernel<true>, F, maps, flags);
+    return cudaLaunchKernelEx(&cfg, pframe_rf_kernel<false>, F, maps, flags);
 }
 
 cudaError_t launch_pframe_fused(FusedFrame &F, const FusedMaps *maps, uint32_t *flags, cudaStream_t st, bool pdl)

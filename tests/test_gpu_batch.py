@@ -69,16 +69,20 @@ def test_batch_matches_per_frame(hv, W, H, n, seed, B, chroma):
         assert abs(psnr(g, gop.sources[-1][p]) - psnr(rec[p], gop.sources[-1][p])) <= TOL_PSNR_DB
 
 
-def test_batch_with_large_blocks(hv):
+@pytest.mark.parametrize("chroma,n", [(False, 6), (True, 11)])
+def test_batch_with_large_blocks(hv, chroma, n):
     """Blocks with K > 32 are solved by a whole CTA in the scratch slot of
-    their range: every frame's range gets its own slot."""
+    their range: every range of a launch gets its own slot (with chroma 8
+    frames share a launch)."""
     W, H = 128, 96
-    gop = make_gop(5, W, H, n_frames=6, chroma=False, lam_y=30.0, residual_kw={"kmax": 60})
-    refs, outs = _per_frame(hv, gop, W, H, False, 16)
-    dec, bouts = _batched(hv, gop, W, H, False, 16)
+    gop = make_gop(5, W, H, n_frames=n, chroma=chroma, lam_y=30.0, lam_c=20.0, residual_kw={"kmax": 60})
+    refs, outs = _per_frame(hv, gop, W, H, chroma, 16)
+    dec, bouts = _batched(hv, gop, W, H, chroma, 16)
     for t in range(len(outs)):
-        assert np.array_equal(bouts[t][0], outs[t][0]), t
-    assert np.array_equal(_planes(dec)[0], refs[-1][0])
+        for p in range(len(outs[t])):
+            assert np.array_equal(bouts[t][p], outs[t][p]), (t, p)
+    for p, g in enumerate(_planes(dec)):
+        assert np.array_equal(g, refs[-1][p]), p
 
 
 def test_batch_two_decoders_interleaved(hv):
