@@ -195,19 +195,33 @@ __global__ void __launch_bounds__(kResThreads) intra_residual_kernel(const __gri
 // and one horizontal one are the thread's own cells (except at its first
 // and last row), so a cell update reads one or two values from shared
 // memory, where every cell's latest value is kept by colour for the
-// neighbouring threads.
+// neighbouring threads.  The colour arrays have a one-cell border, so the
+// staged region's outer ring is updated like any cell (from border
+// values): its values are not exact after the first half sweep, but
+// exactness shrinks by one ring per half sweep anyway, and the 2S half
+// sweeps leave the interior, kHL = 2S rings in, exact.  Tile corners are
+// even (kTX, kTY, kHL even), so a cell's colour is known at compile time.
+static_assert(kTX % 2 == 0 && kTY % 2 == 0 && kHL % 2 == 0, "tiles start on even cells");
 template <bool FROM_ZERO>
 __global__ void __launch_bounds__(kHW *kTY_THREADS, 2) intra_sor_kernel(const __grid_constant__ IntraJobs J, int e_in)
 {
-    __shared__ float E[2][kRH][kHW];
+    __shared__ float E[2][kRH + 2][kHW + 2];
     const IntraPlane &P = J.p[find_plane(J, blockIdx.x)];
     const int lt = blockIdx.x - P.tile_base;
     const int tx0 = (lt % P.tiles_x) * kTX, ty0 = (lt / P.tiles_x) * kTY;
     const int gx0 = tx0 - kHL, gy0 = ty0 - kHL;
     const int W = P.width, H = P.height, pitch = P.pitch;
     const int hx = threadIdx.x, ty = threadIdx.y, ly0 = ty * kRows;
-    const int par = (tx0 + ty0) & 1;  // parity offset of local -> global coordinates
     const float *ein = P.e[e_in];
+    // the border of the colour arrays: finite values
+    for (int k = hx + ty * kHW; k < 2 * (kRH + 2); k += kHW * kTY_THREADS) {
+        E[k & 1][k >> 1][0] = 0.f;
+        E[k & 1][k >> 1][kHW + 1] = 0.f;
+    }
+    for (int k = hx + ty * kHW; k < 2 * (kHW + 2); k += kHW * kTY_THREADS) {
+        E[k & 1][0][k >> 1] = 0.f;
+        E[k & 1][kRH + 1][k >> 1] = 0.f;
+    }
     float *eout = P.e[e_in ^ 1];
     // The pair starts at an even column (tx0 and the halo are even), so its
     // two cells are read as one 2-element vector.  Every load is issued
@@ -228,7 +242,7 @@ __global__ void __launch_bounds__(kHW *kTY_THREADS, 2) intra_sor_kernel(const __
         if (!FROM_ZERO) e2[k] = __ldg(reinterpret_cast<const float2 *>(ein + i));
     }
     // ec[k][c]: value of the thread's colour-c cell in row ly0 + k, which
-    // sits at column 2 hx + ((c + k + par) & 1); invc = 1/n, rnc = r/n
+    // sits at column 2 hx + ((c + k) & 1); invc = 1/n, rnc = r/n
     float ec[kRows][2], invc[kRows][2], rnc[kRows][2];
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
@@ -246,15 +260,15 @@ __global__ void __launch_bounds__(kHW *kTY_THREADS, 2) intra_sor_kernel(const __
             rv[b] = unk ? (b ? r2[k].y : r2[k].x) * inv : 0.f;
             ev[b] = (FROM_ZERO || !unk) ? 0.f : (b ? e2[k].y : e2[k].x);
         }
-        const int sw = (k + par) & 1;  // 1: the pair's left cell has colour 1
+        const int sw = k & 1;  // 1: the pair's left cell has colour 1 (ly0 is even)
         ec[k][0] = sw ? ev[1] : ev[0];
         ec[k][1] = sw ? ev[0] : ev[1];
         invc[k][0] = sw ? iv[1] : iv[0];
         invc[k][1] = sw ? iv[0] : iv[1];
         rnc[k][0] = sw ? rv[1] : rv[0];
         rnc[k][1] = sw ? rv[0] : rv[1];
-        E[0][ly0 + k][hx] = ec[k][0];
-        E[1][ly0 + k][hx] = ec[k][1];
+        E[0][ly0 + k + 1][hx + 1] = ec[k][0];
+        E[1][ly0 + k + 1][hx + 1] = ec[k][1];
     }
     __syncthreads();
     const float omega = P.omega;
@@ -263,20 +277,14 @@ __global__ void __launch_bounds__(kHW *kTY_THREADS, 2) intra_sor_kernel(const __
         const int c = (m - 1) & 1, o = c ^ 1;  // red (even x + y) first
 #pragma unroll
         for (int k = 0; k < kRows; ++k) {
-            const int ly = ly0 + k;
-            const int b = (c + k + par) & 1;  // column of the colour-c cell in the pair
-            // the staged region's outer ring is never updated (its
-            // neighbours lie outside); validity shrinks by one ring per
-            // half sweep, so the output interior is exact
-            const bool ring = (ly == 0) | (ly == kRH - 1) | (hx == 0 && b == 0) | (hx == kHW - 1 && b == 1);
-            if (!ring) {
-                const float up = k > 0 ? ec[k - 1][o] : E[o][ly - 1][hx];
-                const float dn = k < kRows - 1 ? ec[k + 1][o] : E[o][ly + 1][hx];
-                const float s = (ec[k][o] + E[o][ly][hx - 1 + 2 * b]) + (up + dn);
-                // fixed cells have invc = rnc = 0 and value 0: they stay 0
-                ec[k][c] = fmaf(omega, fmaf(s, invc[k][c], rnc[k][c] - ec[k][c]), ec[k][c]);
-                E[c][ly][hx] = ec[k][c];
-            }
+            const int ly = ly0 + k + 1;      // row in the bordered arrays
+            const int b = (c + k) & 1;       // column of the colour-c cell in the pair
+            const float up = k > 0 ? ec[k - 1][o] : E[o][ly - 1][hx + 1];
+            const float dn = k < kRows - 1 ? ec[k + 1][o] : E[o][ly + 1][hx + 1];
+            const float s = (ec[k][o] + E[o][ly][hx + 2 * b]) + (up + dn);
+            // fixed cells have invc = rnc = 0 and value 0: they stay 0
+            ec[k][c] = fmaf(omega, fmaf(s, invc[k][c], rnc[k][c] - ec[k][c]), ec[k][c]);
+            E[c][ly][hx + 1] = ec[k][c];
         }
         __syncthreads();
     }
@@ -288,7 +296,7 @@ __global__ void __launch_bounds__(kHW *kTY_THREADS, 2) intra_sor_kernel(const __
     for (int k = 0; k < kRows; ++k) {
         const int ly = ly0 + k, gy = gy0 + ly;
         if (ly < kHL || ly >= kHL + kTY || gy >= H) continue;
-        const int sw = (k + par) & 1;
+        const int sw = k & 1;
         const float v0 = sw ? ec[k][1] : ec[k][0], v1 = sw ? ec[k][0] : ec[k][1];
         float *o = eout + (size_t)gy * pitch + gxp;
         if (in1) *reinterpret_cast<float2 *>(o) = make_float2(v0, v1);
