@@ -29,12 +29,13 @@ namespace {
 // ---- SOR tile geometry ---------------------------------------------------
 constexpr int kS = 4;                   // full sweeps per launch
 constexpr int kHL = 2 * kS;             // halo
-constexpr int kRW = 128, kRH = 64;      // staged region
+constexpr int kRW = 128, kRH = 128;     // staged region
 constexpr int kTX = kRW - 2 * kHL;      // 112 output columns
-constexpr int kTY = kRH - 2 * kHL;      // 48 output rows
+constexpr int kTY = kRH - 2 * kHL;      // 112 output rows
 constexpr int kHW = kRW / 2;            // cells per colour and row
-constexpr int kTY_THREADS = 8;          // thread rows; each thread owns kRH/8 consecutive rows
+constexpr int kTY_THREADS = 16;         // thread rows; each thread owns kRH/16 consecutive rows
 constexpr int kRows = kRH / kTY_THREADS;
+constexpr size_t kSorSmem = 2 * (kRH + 2) * (kHW + 2) * sizeof(float);  // bordered colour arrays
 
 constexpr int kResThreads = 256;
 constexpr int kRTW = 64, kRTH = 16;  // residual tile
@@ -203,9 +204,10 @@ __global__ void __launch_bounds__(kResThreads) intra_residual_kernel(const __gri
 // even (kTX, kTY, kHL even), so a cell's colour is known at compile time.
 static_assert(kTX % 2 == 0 && kTY % 2 == 0 && kHL % 2 == 0, "tiles start on even cells");
 template <bool FROM_ZERO>
-__global__ void __launch_bounds__(kHW *kTY_THREADS, 2) intra_sor_kernel(const __grid_constant__ IntraJobs J, int e_in)
+__global__ void __launch_bounds__(kHW *kTY_THREADS, 1) intra_sor_kernel(const __grid_constant__ IntraJobs J, int e_in)
 {
-    __shared__ float E[2][kRH + 2][kHW + 2];
+    extern __shared__ float sor_smem[];
+    auto E = reinterpret_cast<float(*)[kRH + 2][kHW + 2]>(sor_smem);
     const IntraPlane &P = J.p[find_plane(J, blockIdx.x)];
     const int lt = blockIdx.x - P.tile_base;
     const int tx0 = (lt % P.tiles_x) * kTX, ty0 = (lt / P.tiles_x) * kTY;
@@ -345,11 +347,26 @@ cudaError_t launch_intra_sor(IntraJobs &J, int e_in, bool from_zero, int sweeps,
         P.tile_base = base;
         base += P.tiles_x * ((P.height + kTY - 1) / kTY);
     }
+    // one staged region per CTA, one CTA per SM (its colour arrays take
+    // dynamic shared memory beyond the static limit)
+    static bool attr[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(intra_sor_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kSorSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(intra_sor_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kSorSmem);
+        if (e != cudaSuccess) return e;
+        attr[dev] = true;
+    }
     int cur = e_in;
     const int n = (sweeps + kS - 1) / kS;
     for (int l = 0; l < n; ++l) {
-        if (from_zero && l == 0) intra_sor_kernel<true><<<base, dim3(kHW, kTY_THREADS), 0, st>>>(J, cur);
-        else intra_sor_kernel<false><<<base, dim3(kHW, kTY_THREADS), 0, st>>>(J, cur);
+        if (from_zero && l == 0) intra_sor_kernel<true><<<base, dim3(kHW, kTY_THREADS), kSorSmem, st>>>(J, cur);
+        else intra_sor_kernel<false><<<base, dim3(kHW, kTY_THREADS), kSorSmem, st>>>(J, cur);
         cur ^= 1;
     }
     if (launches) *launches += n;
