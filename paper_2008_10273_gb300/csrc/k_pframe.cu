@@ -375,10 +375,14 @@ struct PixelCtx {
     const float *ry0;
     float *oy0;
     uint8_t *uy0;
-    const float *rcp;
+    const float *rcp;  // this lane's chroma plane (x & 1: Cb, Cr)
     float *ocp;
     uint8_t *ucp;
     int cpitch, uop;
+    float *oc[2];      // both chroma planes (Cb, Cr)
+    uint8_t *uc[2];
+    int ocp2[2], uop2[2];
+    bool vec2;         // luma output rows take 8-byte (ref) and 2-byte (uint8) pairs
 };
 
 template <bool CHROMA>
@@ -395,6 +399,14 @@ __device__ __forceinline__ PixelCtx pixel_ctx(const FusedFrame &F)
     c.oy0 = F.ref_out[0];
     c.uy0 = F.out[0];
     const int cp = threadIdx.x & 1;
+    for (int k = 0; k < 2; ++k) {
+        c.oc[k] = F.ref_out[1 + k];
+        c.uc[k] = F.out[1 + k];
+        c.ocp2[k] = F.ref_pitch[1 + k];
+        c.uop2[k] = F.out_pitch[1 + k];
+    }
+    c.vec2 = (((uintptr_t)F.ref_out[0] | (uintptr_t)F.ref_pitch[0] * 4) & 7) == 0 &&
+             (((uintptr_t)F.out[0] | (uintptr_t)F.out_pitch[0]) & 1) == 0;
     if (CHROMA) {
         c.rcp = cp ? F.ref[2] : F.ref[1];
         c.ocp = cp ? F.ref_out[2] : F.ref_out[1];
@@ -494,6 +506,78 @@ __device__ __forceinline__ void phase_c(const PixelCtx &c, const ResView &R, con
                 }
                 put_pixel(pred, rcp[j * R.cp + cx], c.ocp + (size_t)cyg * c.cpitch + cxg,
                           c.ucp + (size_t)cyg * c.uop + cxg);
+            }
+        }
+    }
+}
+
+// The fast case (macroblock inside the plane with its halo, every
+// |flow| < 7): item (l, j) of 16 x 16 is the luma quad at columns 2l, 2l+1
+// and rows 2j, 2j+1 with the co-sited chroma pixel (l, j) of Cb and Cr,
+// whose flow is half the mean of the quad's four vectors; thread t takes
+// the items t and t + 128.  Every footprint lies in the staged tiles.  The
+// residual comes from shared tiles (luma rows RYP floats apart, chroma rows
+// RCP apart, the Cr tile RCS after Cb).  Luma results leave as pairs where
+// the output rows allow (vec2: 8-byte ref_out rows, 2-byte uint8 rows).
+template <bool CHROMA, int RYP, int RCP, int RCS>
+__device__ __forceinline__ void phase_c_quads(const PixelCtx &c, const float *ryt, const float *rct, const Stage &st,
+                                              int mx, int my)
+{
+    const bool vec2 = c.vec2;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const int item = threadIdx.x + it * kThreads, l = item & 15, j = item >> 4;
+        const int ly = 2 * j, lx = 2 * l;
+        const float4 fa = *reinterpret_cast<const float4 *>(&st.flow[ly][2 * lx]);
+        const float4 fb = *reinterpret_cast<const float4 *>(&st.flow[ly + 1][2 * lx]);
+        const float2 fv[4] = {{fa.x, fa.y}, {fa.z, fa.w}, {fb.x, fb.y}, {fb.z, fb.w}};
+        float pv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float fx = floorf(fv[q].x), fy = floorf(fv[q].y);
+            pv[q] = tile_lerp<kTL>(&st.ry[0][0], lx + (q & 1) + kHalo + __float2int_rn(fx),
+                                   ly + (q >> 1) + kHalo + __float2int_rn(fy), fv[q].x - fx, fv[q].y - fy);
+        }
+        const float2 r0 = *reinterpret_cast<const float2 *>(ryt + ly * RYP + lx);
+        const float2 r1 = *reinterpret_cast<const float2 *>(ryt + (ly + 1) * RYP + lx);
+        const float rr[4] = {r0.x, r0.y, r1.x, r1.y};
+        float v[4];
+        uint8_t u[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            v[q] = fminf(fmaxf(pv[q] + rr[q], 0.f), 255.f);
+            u[q] = (uint8_t)__float2int_rd(v[q] + 0.5f);
+        }
+        const size_t gx = (size_t)mx * kMB + lx, gy = (size_t)my * kMB + ly;
+        float *o0 = c.oy0 + gy * c.yp + gx;
+        uint8_t *b0 = c.uy0 + gy * c.op + gx;
+        if (vec2) {
+            *reinterpret_cast<float2 *>(o0) = make_float2(v[0], v[1]);
+            *reinterpret_cast<float2 *>(o0 + c.yp) = make_float2(v[2], v[3]);
+            *reinterpret_cast<uint16_t *>(b0) = (uint16_t)(u[0] | (u[1] << 8));
+            *reinterpret_cast<uint16_t *>(b0 + c.op) = (uint16_t)(u[2] | (u[3] << 8));
+        } else {
+            o0[0] = v[0];
+            o0[1] = v[1];
+            o0[c.yp] = v[2];
+            o0[c.yp + 1] = v[3];
+            b0[0] = u[0];
+            b0[1] = u[1];
+            b0[c.op] = u[2];
+            b0[c.op + 1] = u[3];
+        }
+        if (CHROMA) {
+            const float dx = ((fv[0].x + fv[1].x) + (fv[2].x + fv[3].x)) * 0.125f;
+            const float dy = ((fv[0].y + fv[1].y) + (fv[2].y + fv[3].y)) * 0.125f;
+            const float fx = floorf(dx), fy = floorf(dy);
+            const int tx = l + kCHalo + __float2int_rn(fx), tyy = j + kCHalo + __float2int_rn(fy);
+            const size_t cx = (size_t)mx * (kMB / 2) + l, cy = (size_t)my * (kMB / 2) + j;
+#pragma unroll
+            for (int pl = 0; pl < 2; ++pl) {
+                const float pred = tile_lerp<kTC>(&st.rc[pl][0][0], tx, tyy, dx - fx, dy - fy);
+                const float vv = fminf(fmaxf(pred + rct[pl * RCS + j * RCP + l], 0.f), 255.f);
+                c.oc[pl][cy * c.ocp2[pl] + cx] = vv;
+                c.uc[pl][cy * c.uop2[pl] + cx] = (uint8_t)__float2int_rd(vv + 0.5f);
             }
         }
     }
@@ -599,7 +683,7 @@ __global__ void __launch_bounds__(kThreads, TMA ? 4 : 6) pframe_kernel(const __g
                               mx * kMB - kHalo + kTL <= F.width && my * kMB - kHalo + kTL <= F.height;
         const ResView R{T.ry, {T.rc, T.rc + kRCS}, kRYP, kRCP};
         if (__syncthreads_and(landed && interior && small_flow(stages[s])))
-            phase_c<CHROMA, true>(pc, R, st, mx, my, fl);
+            phase_c_quads<CHROMA, kRYP, kRCP, kRCS>(pc, T.ry, T.rc, stages[s], mx, my);
         else
             phase_c<CHROMA, false>(pc, R, st, mx, my, fl);
         // a copy that timed out may still land later: from then on no stage
@@ -718,7 +802,8 @@ __global__ void __launch_bounds__(kThreads, 4) pframe_rf_kernel(const __grid_con
                               mx * kMB - kHalo + kTL <= F.width && my * kMB - kHalo + kTL <= F.height;
         const Stage *st = landed ? &stages[s].s : nullptr;
         if (__syncthreads_and(landed && interior && small_flow(stages[s].s)))
-            phase_c<CHROMA, true>(pc, R, st, mx, my, fl);
+            phase_c_quads<CHROMA, kMB, kMB / 2, (kMB / 2) * (kMB / 2)>(pc, &stages[s].ry[0][0], &stages[s].rc[0][0][0],
+                                                                       stages[s].s, mx, my);
         else
             phase_c<CHROMA, false>(pc, R, st, mx, my, fl);
         if (__syncthreads_or(issued && !landed)) ok = false;
