@@ -38,7 +38,10 @@ UNIT = "FullHD frames/s"
 # Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) from
 # ncu captures, keyed by kernel family, with the sha1 of the kernel's source
 # file at capture time; a changed source voids the number (reported null).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # intra_sor_kernel, one launch on the FullHD 4:2:0 GOP workload
+    "intra_sweeps": {"bytes": 32.63e6, "sha": "636fb463ab5d"},
+}
 
 
 def parse_args(argv=None):
@@ -297,15 +300,15 @@ def main(argv=None):
                 step(ev[k])
             torch.cuda.synchronize()
             dec.sync()
-        # per-kernel device times: the same steps again with CUDA events
-        # around every kernel family on the decoder's stream (events between
-        # kernels keep the fused kernel from overlapping its predecessor, so
+        # per-kernel device times: the timed path's steps again with CUDA
+        # events around every kernel family on the decoder's stream (events
+        # between kernels keep a kernel from overlapping its predecessor, so
         # this pass is not the one that gives `value`)
         kpass = max(1, min(a.steps, 5))
         hivc.lib().hivc_decoder_set_timing(dec.handle, 1)
         for k in range(kpass):
             flush.zero_()
-            step()
+            timed()
         torch.cuda.synchronize()
         kstats = dec.sync()
         hivc.lib().hivc_decoder_set_timing(dec.handle, 0)
@@ -330,12 +333,18 @@ def main(argv=None):
         # per luma pixel, 4 + 4 + 1 B per chroma pixel (flow read once), and
         # the residual data (block_ptr, pos, val, coefficients, constants)
         7: ("k_pframe.cu", W * H * (8 + 4 + 4 + 1) + 2 * cw * ch * (4 + 4 + 1) + npts * (1 + 2 + 4) + nblk * 8),
+        # inter pixels from residual planes (batches): as the fused kernel,
+        # with the residual plane read (4 B per pixel) for the block data
+        4: ("k_pframe.cu", W * H * (8 + 4 + 4 + 4 + 1) + 2 * cw * ch * (4 + 4 + 4 + 1)),
         6: ("k_warp.cu", W * H * (8 + 4 + 4 + 4 + 1) + 2 * cw * ch * (4 + 4 + 4 + 1)),
         # one SOR launch (4 sweeps): correction in/out 8 B, residual 4 B, mask 1 B per pixel
         1: ("k_intra.cu", (W * H + 2 * cw * ch) * (4 + 4 + 1 + 4)),
         # residual + update: hi/lo in 8 B, hi/lo out 8 B, correction 4 B, mask 1 B, residual 4 B
         2: ("k_intra.cu", (W * H + 2 * cw * ch) * (8 + 8 + 4 + 1 + 4)),
-        5: ("k_block.cu", (W * H + 2 * cw * ch) * 4),
+        # evaluation: the residual planes written; a batch launch covers
+        # several frames (the GOP's inter frames over its launches)
+        5: ("k_block.cu", (W * H + 2 * cw * ch) * 4 * ((nfr - 1) / max(1, fam_n[5] / kpass)
+                                                       if a.path == "batch" else 1)),
     }
     dom = max(range(len(fam_ms)), key=lambda i: fam_ms[i])
     peaks = {}

@@ -733,7 +733,7 @@ cudaError_t launch_rf_frame(hivc_decoder *d, const hivc_pframe *f, const hivc_ou
     if (!encode_map_2d(&M.flow, f->flow, 2 * (uint64_t)d->cfg.width, d->cfg.height, 8 * (uint64_t)d->cfg.width, 64,
                        32))
         return cudaErrorInvalidValue;
-    Timed t(d, 7);
+    Timed t(d, 4);
     const cudaError_t e = launch_pframe_rf(F, M, d->flags, d->stream, !d->timing);
     t.done(1);
     return e;
