@@ -58,6 +58,8 @@ def parse_args(argv=None):
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--no-serve", action="store_true", help="skip the multi-stream serving measurement")
+    p.add_argument("--serve-gop", type=int, default=30, help="frames per stream in the serving measurement")
     p.add_argument("--path", choices=["batch", "plain"], default="batch",
                    help="decode path of the timed steps: one hivc_decode_batch call per GOP (inter frames "
                         "share coefficient launches), or one call per frame")
@@ -152,6 +154,54 @@ def run_reference(a):
             "e2e": {"value": fps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ---------------------------------------------------------------------------
+# serving: 16 concurrent streams of mixed resolution as their frames arrive
+# ---------------------------------------------------------------------------
+SERVE_MIX = [(1920, 1080, 8), (1280, 720, 4), (854, 480, 4)]
+
+
+def serve_measurement(a, gops=None):
+    """Concurrent streams (8 x 1920x1080, 4 x 1280x720, 4 x 854x480, 4:2:0),
+    one GOP each, frames arriving at 30 fps per stream with exponential
+    jitter (mean 3 ms): served with continuous batching vs plain (one call
+    per frame); and a saturating run (every frame there at once).  Streams
+    of one size decode the same synthetic GOP on their own decoders."""
+    import numpy as np
+
+    from paper_2008_10273_gb300 import hivc, serve
+    from workload import make_gop
+
+    rng = np.random.default_rng(a.seed)
+    data = {}
+    for W, H, _ in SERVE_MIX:
+        g = (gops or {}).get((W, H)) or make_gop(a.seed + W, W, H, n_frames=a.serve_gop, with_sources=False)
+        data[(W, H)] = [("i", hivc.device_iframe(g.iframe))] + [("p", hivc.device_pframe(p)) for p in g.pframes]
+
+    def streams(saturate):
+        out = []
+        for W, H, n in SERVE_MIX:
+            for k in range(n):
+                fr = data[(W, H)]
+                if saturate:
+                    arr = [0.0] * len(fr)
+                else:
+                    arr = list(np.maximum.accumulate(np.arange(len(fr)) / 30.0 + rng.exponential(0.003, len(fr))))
+                out.append(serve.Stream(f"{W}x{H}#{k}", W, H, fr, arr))
+        return out
+
+    budget = 40 << 30
+    res = {}
+    for name, sat, batched in (("served", False, True), ("plain", False, False), ("saturated", True, True),
+                               ("saturated_plain", True, False)):
+        st = serve.Server(budget).run(streams(sat), batched=batched)
+        res[name] = {"value": st["fullhd_fps"], "unit": UNIT, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                     "frames": st["frames"], "wall_s": st["wall_s"], "calls": st["calls"]}
+    res["workload"] = (f"{sum(n for _, _, n in SERVE_MIX)} streams (8x1920x1080, 4x1280x720, 4x854x480, 4:2:0), "
+                       f"one GOP of {a.serve_gop} frames each; arrivals 30 fps per stream + Exp(3 ms) jitter "
+                       f"(saturated: all at t=0); HBM budget 40 GB; latency = arrival to completion event")
+    return res
 
 
 # ---------------------------------------------------------------------------
@@ -437,6 +487,9 @@ def main(argv=None):
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(a, gop)
+    served = None
+    if rank == 0 and world == 1 and not a.no_serve:
+        served = serve_measurement(a, {(W, H): gop} if (W, H) == (1920, 1080) and a.serve_gop == nfr else None)
 
     if rank == 0:
         pf = sorted(frame_ms[i] for i in range(len(frame_ms)) if i % nfr != 0)
@@ -462,6 +515,7 @@ def main(argv=None):
             "kernel_timing": f"per-kernel CUDA events in a separate pass of {kpass} steps of the same workload",
             "clocks": clk,
             "cpu_baseline": cpu,
+            "serving": served,
         }
         print(json.dumps(line), flush=True)
     dec.close()
