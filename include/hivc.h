@@ -172,14 +172,25 @@ hivc_status hivc_decode_iframe(hivc_decoder *dec, const hivc_iframe *f, const hi
 hivc_status hivc_decode_pframe(hivc_decoder *dec, const hivc_pframe *f, const hivc_out *out);
 
 /* Decode n frames, frame k on decoder decs[k] into outs[k].  Frames of one
-   decoder are decoded in array order; inter frames of different decoders
-   are batched into shared launches. */
+   decoder are decoded in array order; each run of consecutive inter frames
+   of a decoder shares its block launches (Eq. 2 coefficients, Eq. 3
+   residual planes).  Every inter frame is checked before anything is
+   launched (HIVC_E_INVALID; HIVC_E_NO_REFERENCE for an inter frame of a
+   decoder with no reference and no earlier intra frame in the batch).
+   Decoders with intra frames run on host threads of their own (up to 32),
+   so that their correction cycles overlap; a decoder stops at its first
+   error, the others finish, and the call returns the first error in order
+   of the decoders' first frames (HIVC_E_NOT_CONVERGED only if no worse). */
 hivc_status hivc_decode_batch(hivc_decoder *const *decs, const hivc_frame *frames, int32_t n,
                               const hivc_out *outs);
 
 /* Wait for the decoder's stream; report device-side data errors
    (HIVC_E_INVALID) and the statistics of the frames since the last sync. */
 hivc_status hivc_decoder_sync(hivc_decoder *dec, hivc_stats *last);
+
+/* Forget the reference frame (the decoder is reused for a new stream: its
+   next frame must be an intra frame).  Work already queued is unaffected. */
+hivc_status hivc_decoder_reset(hivc_decoder *dec);
 
 /* Enable (1) or disable (0) per-kernel CUDA-event timing in hivc_stats. */
 hivc_status hivc_decoder_set_timing(hivc_decoder *dec, int32_t on);

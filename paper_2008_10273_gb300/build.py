@@ -65,7 +65,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
                     sys.stderr.write(out)
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".{os.getpid()}.tmp"
-        run([nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs)
+        run([nvcc] + ARCH + ["-shared", "-Xcompiler", "-pthread", "-cudart", "shared", "-o", tmp] + objs)
         os.replace(tmp, LIB)
     return LIB
 

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -458,6 +459,13 @@ void hivc_decoder_destroy(hivc_decoder *d)
     if (d->pool) cudaFree(d->pool);
     d->mem.release();
     delete d;
+}
+
+hivc_status hivc_decoder_reset(hivc_decoder *d)
+{
+    if (!d) return HIVC_E_INVALID;
+    d->has_ref = false;
+    return HIVC_OK;
 }
 
 void *hivc_decoder_stream(const hivc_decoder *d) { return d ? static_cast<void *>(d->stream) : nullptr; }
@@ -934,45 +942,104 @@ hivc_status decode_inter_run(hivc_decoder *d, const hivc_frame *frames, const hi
 
 }  // namespace
 
-hivc_status hivc_decode_batch(hivc_decoder *const *decs, const hivc_frame *frames, int32_t n, const hivc_out *outs)
+namespace {
+
+// One decoder's frames of a batch, in array order: intra frames one by one,
+// each run of consecutive inter frames through decode_inter_run (shared
+// block launches).  Stops at the first error other than NOT_CONVERGED.
+hivc_status decode_own_frames(hivc_decoder *d, const hivc_frame *frames, const hivc_out *outs,
+                              const std::vector<int> &ks)
 {
-    if (n < 0 || (n > 0 && (!decs || !frames || !outs))) return HIVC_E_INVALID;
     hivc_status worst = HIVC_OK;
-    for (int i = 0; i < n;) {
-        if (frames[i].type != 1) {
-            if (frames[i].type != 0) return HIVC_E_INVALID;
-            const hivc_status s = hivc_decode_iframe(decs[i], frames[i].i, &outs[i]);
+    for (size_t i = 0; i < ks.size();) {
+        if (frames[ks[i]].type == 0) {
+            const hivc_status s = hivc_decode_iframe(d, frames[ks[i]].i, &outs[ks[i]]);
             if (s != HIVC_OK && s != HIVC_E_NOT_CONVERGED) return s;
             if (s != HIVC_OK) worst = s;
             ++i;
             continue;
         }
-        // a run of inter frames [i, j): checked first, then decoded per
-        // decoder (one decoder's frames stay in order on its stream)
-        int j = i;
-        while (j < n && frames[j].type == 1) ++j;
-        std::vector<hivc_decoder *> ds;
-        for (int k = i; k < j; ++k) {
-            hivc_decoder *d = decs[k];
-            if (!pframe_ok(d, frames[k].p, &outs[k])) return HIVC_E_INVALID;
-            if (!d->has_ref) return HIVC_E_NO_REFERENCE;
-            if (std::find(ds.begin(), ds.end(), d) == ds.end()) ds.push_back(d);
+        std::vector<int> run;
+        while (i < ks.size() && frames[ks[i]].type == 1) run.push_back(ks[i++]);
+        hivc_status s = HIVC_OK;
+        if (fused_supported(d->cfg.block)) {
+            s = decode_inter_run(d, frames, outs, run);
+        } else {
+            for (int k : run)
+                if ((s = hivc_decode_pframe(d, frames[k].p, &outs[k])) != HIVC_OK) break;
         }
-        for (hivc_decoder *d : ds) {
-            std::vector<int> ks;
-            for (int k = i; k < j; ++k)
-                if (decs[k] == d) ks.push_back(k);
-            hivc_status s;
-            if (fused_supported(d->cfg.block)) {
-                s = decode_inter_run(d, frames, outs, ks);
-            } else {
-                s = HIVC_OK;
-                for (int k : ks)
-                    if ((s = hivc_decode_pframe(d, frames[k].p, &outs[k])) != HIVC_OK) break;
-            }
-            if (s != HIVC_OK) return s;
+        if (s != HIVC_OK) return s;
+    }
+    return worst;
+}
+
+}  // namespace
+
+hivc_status hivc_decode_batch(hivc_decoder *const *decs, const hivc_frame *frames, int32_t n, const hivc_out *outs)
+{
+    if (n < 0 || (n > 0 && (!decs || !frames || !outs))) return HIVC_E_INVALID;
+    // every inter frame is checked before anything is launched
+    std::vector<hivc_decoder *> ds;
+    std::vector<std::vector<int>> ks;
+    bool any_intra = false;
+    for (int k = 0; k < n; ++k) {
+        hivc_decoder *d = decs[k];
+        if (!d || (frames[k].type != 0 && frames[k].type != 1)) return HIVC_E_INVALID;
+        if (frames[k].type == 1 && !pframe_ok(d, frames[k].p, &outs[k])) return HIVC_E_INVALID;
+        any_intra |= frames[k].type == 0;
+        const size_t j = std::find(ds.begin(), ds.end(), d) - ds.begin();
+        if (j == ds.size()) {
+            ds.push_back(d);
+            ks.emplace_back();
         }
-        i = j;
+        ks[j].push_back(k);
+    }
+    for (size_t j = 0; j < ds.size(); ++j) {
+        bool ref = ds[j]->has_ref;
+        for (int k : ks[j]) {
+            if (frames[k].type == 0) ref = true;
+            else if (!ref) return HIVC_E_NO_REFERENCE;
+        }
+    }
+    // Decoders are independent and each has its own stream.  Decoders with
+    // only inter frames are issued from this thread first (their launches
+    // are asynchronous).  An intra frame waits on its stream between
+    // correction cycles, so decoders with intra frames are spread over up
+    // to kBatchThreads host threads and the cycles of different decoders
+    // overlap on the device.  Every decoder stops at its own first error.
+    std::vector<hivc_status> st(ds.size(), HIVC_OK);
+    std::vector<size_t> with_intra;
+    for (size_t j = 0; j < ds.size(); ++j) {
+        bool intra = false;
+        for (int k : ks[j]) intra |= frames[k].type == 0;
+        if (intra) with_intra.push_back(j);
+        else st[j] = decode_own_frames(ds[j], frames, outs, ks[j]);
+    }
+    constexpr size_t kBatchThreads = 32;
+    const size_t T = std::min(with_intra.size(), kBatchThreads);
+    auto worker = [&](size_t w) {
+        for (size_t i = w; i < with_intra.size(); i += T) {
+            const size_t j = with_intra[i];
+            st[j] = decode_own_frames(ds[j], frames, outs, ks[j]);
+        }
+    };
+    std::vector<std::thread> th;
+    try {
+        for (size_t w = 1; w < T; ++w) th.emplace_back(worker, w);
+    } catch (...) {  // no more threads to be had: their shares run here
+    }
+    const size_t started = th.size() + 1;
+    for (size_t i = 0; i < with_intra.size(); ++i) {
+        const size_t w = i % (T ? T : 1);
+        if (w != 0 && w < started) continue;
+        const size_t j = with_intra[i];
+        st[j] = decode_own_frames(ds[j], frames, outs, ks[j]);
+    }
+    for (std::thread &t : th) t.join();
+    hivc_status worst = HIVC_OK;
+    for (hivc_status s : st) {
+        if (s != HIVC_OK && s != HIVC_E_NOT_CONVERGED) return s;
+        if (s != HIVC_OK) worst = s;
     }
     return worst;
 }

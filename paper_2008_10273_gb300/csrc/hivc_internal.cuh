@@ -23,6 +23,9 @@ enum : uint32_t {
     kFlagNotSPD = 1u << 3,    // non-positive Cholesky pivot
     kFlagMaskIdx = 1u << 4,   // intra mask index out of range or not increasing
     kFlagTimeout = 1u << 5,   // a bounded wait on tensor-memory copies gave up
+    kFlagCond = 1u << 6,      // information, not an error: a block above the
+                              // condition threshold kept its FP32 solution
+                              // (K > kF64MaxK: no room for the FP64 system)
 };
 
 // ---------------------------------------------------------------------------
@@ -51,13 +54,18 @@ struct BlockJobs {
 // Device addresses of the Green's matrices of all block shapes (uploaded
 // once per device) and the SM count of the device.
 struct BlockTables {
-    const float *G;    // rows of G per shape, padded to multiples of 8 floats
-    const int *goff;   // offset of shape (w, h) at (w-1)*16 + (h-1)
+    const float *G;     // rows of G per shape, padded to multiples of 8 floats
+    const double *G64;  // the same in double precision (FP64 re-solves)
+    const int *goff;    // offset of shape (w, h) at (w-1)*16 + (h-1)
     int sms;
 };
 
 constexpr int kBigMaxK = 255;  // largest K of a 16 x 16 block
-constexpr size_t kBigFloats = (size_t)kBigMaxK * (kBigMaxK + 1) / 2 + 3 * kBigMaxK;
+// one packed FP32 system (L, three right-hand sides), rounded up to 256 bytes
+constexpr size_t kBigFloats = ((size_t)kBigMaxK * (kBigMaxK + 1) / 2 + 3 * kBigMaxK + 63) / 64 * 64;
+// largest K whose FP64 system fits in a slot
+constexpr int kF64MaxK = 179;
+static_assert((size_t)kF64MaxK * (kF64MaxK + 1) / 2 + 3 * kF64MaxK <= kBigFloats / 2, "FP64 system fits a slot");
 constexpr int kRange = 128;    // blocks per range of the coefficient kernel
 
 // ranges of kRange blocks for total_blocks blocks
@@ -65,11 +73,18 @@ __host__ __device__ inline int block_ranges(int total_blocks) { return (total_bl
 
 // Scratch of the coefficient stage: room for one K > 32 system per range
 // of kRange blocks (the range's CTA solves its large blocks one after the
-// other in its slot).
+// other in its slot; an FP64 re-solve uses the slot as doubles).
+//
+// Condition control: every block's bound kappa = 8 tr(G_PP) / (1 - K/N) on
+// cond_2(G_PP) (lambda_max <= tr, lambda_min >= (1 - K/N) / 8 since the
+// eigenvalues of A = -L are at most 8) is compared with tau; a block above
+// it is re-solved in FP64 from the FP64 Green's table.
 struct BlockScratch {
     uint32_t *flags;  // device error word
     float *big;       // big_ranges * kBigFloats floats
     int32_t big_ranges;
+    uint32_t *cstat = nullptr;  // nullptr, or [0] max kappa (float bits), [1] FP64 blocks, [2] K > 32 blocks
+    float tau = 1e6f;           // condition threshold
 };
 
 cudaError_t ensure_block_tables();
@@ -180,5 +195,6 @@ cudaError_t launch_intra_residual(IntraJobs &jobs, int e_in, bool add_e, cudaStr
 cudaError_t launch_intra_sor(IntraJobs &jobs, int e_in, bool from_zero, int sweeps, cudaStream_t st, int *e_out,
                              int *launches);
 int intra_sweeps_per_launch();
+cudaError_t intra_init();  // once per device
 
 }  // namespace hivc

@@ -14,7 +14,9 @@
 // and mu_pq = 4 sin^2(pi p / 2w) + 4 sin^2(pi q / 2h),
 //   G(x,y; x',y') = T(|x-x'|,|y-y'|) + T(|x-x'|,y+y'+1) + T(x+x'+1,|y-y'|) + T(x+x'+1,y+y'+1),
 //   T(al, be) = 1/4 sum_{(p,q) != 0} c_p^2 c_q^2 cos(pi p al / w) cos(pi q be / h) / mu_pq
-// (the Toeplitz-plus-Hankel structure of G, Sec. 2.2), stored as float.
+// (the Toeplitz-plus-Hankel structure of G, Sec. 2.2), stored as float
+// and, for the FP64 re-solve of blocks above the condition threshold, as
+// double.
 //
 // Kernels: the coefficient stage (two blocks per warp: in its 16-lane
 // halves when both have K <= 16, else one after the other with all lanes
@@ -34,16 +36,18 @@ namespace {
 constexpr int kGSize = 2283904;  // sum over shapes of N * rowlen(N)
 
 static __device__ __align__(256) float d_G[kGSize];
+static __device__ __align__(256) double d_G64[kGSize];
 static __device__ int d_goff[256];
 
 std::mutex g_tab_mu;
 BlockTables g_tabs[64];
 uint64_t g_tab_devices = 0;  // bit d: tables uploaded to device d
 
-void build_tables(std::vector<float> &G, std::vector<int> &goff)
+void build_tables(std::vector<float> &G, std::vector<double> &G64, std::vector<int> &goff)
 {
     const double pi = 3.14159265358979323846;
     G.assign(kGSize, 0.f);
+    G64.assign(kGSize, 0.0);
     goff.assign(256, 0);
     int off = 0;
     std::vector<double> T, cw, chq;
@@ -75,6 +79,7 @@ void build_tables(std::vector<float> &G, std::vector<int> &goff)
                     const int a1 = std::abs(xi - xj), a2 = xi + xj + 1, b1 = std::abs(yi - yj), b2 = yi + yj + 1;
                     const double g = T[b1 * 2 * w + a1] + T[b2 * 2 * w + a1] + T[b1 * 2 * w + a2] + T[b2 * 2 * w + a2];
                     G[off + i * rl + j] = (float)g;
+                    G64[off + i * rl + j] = g;
                 }
             off += N * rl;
         }
@@ -113,6 +118,18 @@ __device__ __forceinline__ void mark_bad(const BlockPlane &P, int lb)
     if (P.val[1] != nullptr) P.acoef[1][lb] = __int_as_float(0x7fc00000);
 }
 
+constexpr int kCoefThreads = 128;
+constexpr int kF64Bit = 1 << 30;  // list entry: block re-solved in FP64
+
+// The largest condition bound seen (non-negative floats order like their bits).
+__device__ __forceinline__ void note_kappa(const BlockScratch &S, float kappa)
+{
+    if (S.cstat && kappa > 0.f) atomicMax(S.cstat, __float_as_uint(kappa));
+}
+
+// kappa = 8 tr(G_PP) / (1 - K/N) >= cond_2(G_PP)
+__device__ __forceinline__ float cond_bound(float tr, int K, int N) { return 8.f * tr / (1.f - (float)K / (float)N); }
+
 // validity of the positions of a segment's block (inside, increasing):
 // returns K, or 0 (and a flag) when any is bad
 template <int SEG>
@@ -140,9 +157,11 @@ __device__ __forceinline__ int seg_validate(const SegBlock &b, int i, int seg, c
 // segment is point i), by the register routine, or (KM = 0, SEG = 32) by
 // the shared-memory routine.  Lt: SEG x (SEG+1) floats of shared scratch.
 // Writes c (per point) and a (per block).
+// A block above the condition threshold goes to the CTA's list (entry
+// gb | kF64Bit) for an FP64 re-solve after the warp phase.
 template <int SEG, int KM>
 __device__ __forceinline__ void seg_run(const SegBlock &b, int K, int i, float *Lt, const BlockTables &tab,
-                                        const BlockScratch &S)
+                                        const BlockScratch &S, int gb, int *s_list, int *s_n)
 {
     const BlockPlane *P = b.P;
     const bool two = K > 0 && P->val[1] != nullptr;
@@ -162,6 +181,7 @@ __device__ __forceinline__ void seg_run(const SegBlock &b, int K, int i, float *
     else
         spd = seg_block_coef<SEG, KM, true>(G, rl, K, i, p, v0, v1, reinterpret_cast<float(*)[SEG + 1]>(Lt), c0, c1,
                                             a0, a1);
+    const float tr = seg_sum<SEG>(i < K ? __ldg(G + p * rl + p) : 0.f);
     if (K > 0) {
         if (i < K) {
             P->coef[0][b.g.s + i] = c0;
@@ -171,6 +191,9 @@ __device__ __forceinline__ void seg_run(const SegBlock &b, int K, int i, float *
             P->acoef[0][b.g.lb] = a0;
             if (two) P->acoef[1][b.g.lb] = a1;
             if (!spd) atomicOr(S.flags, kFlagNotSPD);
+            const float kappa = cond_bound(tr, K, b.g.w * b.g.h);
+            note_kappa(S, kappa);
+            if (kappa > S.tau) s_list[atomicAdd(s_n, 1)] = gb | kF64Bit;
         }
     }
 }
@@ -185,11 +208,11 @@ __host__ __device__ constexpr int tri(int i) { return i * (i + 1) / 2; }
 // registers, fully unrolled, so that no control flow depends on K.
 //   L y_v = v, L y_1 = 1 (on the K points);  a = (y_1 . y_v) / (y_1 . y_1)
 //   L^T c = y_v - a y_1
-// Returns false if a pivot of a real row was not positive.
+// Returns false if a pivot of a real row was not positive; tr = tr(G_PP).
 template <bool TWO>
 __device__ __forceinline__ bool thread_block_coef(const float *__restrict__ G, int rl, int K, const int (&p)[kTK],
                                                   const float (&v0)[kTK], const float (&v1)[kTK], float (&c0)[kTK],
-                                                  float (&c1)[kTK], float &a0, float &a1)
+                                                  float (&c1)[kTK], float &a0, float &a1, float &tr)
 {
     float L[tri(kTK)], inv[kTK];
 #pragma unroll
@@ -198,6 +221,10 @@ __device__ __forceinline__ bool thread_block_coef(const float *__restrict__ G, i
 #pragma unroll
         for (int j = 0; j <= i; ++j) L[tri(i) + j] = (i < K && j < K) ? __ldg(row + p[j]) : (i == j ? 1.f : 0.f);
     }
+    tr = 0.f;
+#pragma unroll
+    for (int i = 0; i < kTK; ++i)
+        if (i < K) tr += L[tri(i) + i];
     bool spd = true;
 #pragma unroll
     for (int k = 0; k < kTK; ++k) {
@@ -255,10 +282,11 @@ __device__ __forceinline__ bool thread_block_coef(const float *__restrict__ G, i
 }
 
 // one block with 1 <= K <= kTK by the calling thread: positions checked,
-// then c (per point) and a (per block) written
+// then c (per point) and a (per block) written.  Returns the block's
+// condition bound (0 for bad positions).
 template <bool TWO>
-__device__ __forceinline__ void thread_run(const BlockPlane &P, const BlockGeom &g, const BlockTables &tab,
-                                           const BlockScratch &S)
+__device__ __forceinline__ float thread_run(const BlockPlane &P, const BlockGeom &g, const BlockTables &tab,
+                                            const BlockScratch &S)
 {
     const int K = g.K, N = g.w * g.h;
     int p[kTK];
@@ -280,10 +308,11 @@ __device__ __forceinline__ void thread_run(const BlockPlane &P, const BlockGeom 
     if (!ok) {
         atomicOr(S.flags, kFlagPos);
         mark_bad(P, g.lb);
-        return;
+        return 0.f;
     }
-    float c0[kTK], c1[kTK], a0, a1;
-    const bool spd = thread_block_coef<TWO>(green_rows(tab, g.w, g.h), g_rowlen(N), K, p, v0, v1, c0, c1, a0, a1);
+    float c0[kTK], c1[kTK], a0, a1, tr;
+    const bool spd =
+        thread_block_coef<TWO>(green_rows(tab, g.w, g.h), g_rowlen(N), K, p, v0, v1, c0, c1, a0, a1, tr);
 #pragma unroll
     for (int i = 0; i < kTK; ++i)
         if (i < K) {
@@ -293,46 +322,129 @@ __device__ __forceinline__ void thread_run(const BlockPlane &P, const BlockGeom 
     P.acoef[0][g.lb] = a0;
     if (TWO) P.acoef[1][g.lb] = a1;
     if (!spd) atomicOr(S.flags, kFlagNotSPD);
+    return cond_bound(tr, K, N);
 }
 
-// ---- large blocks (K > 32): one CTA, packed Cholesky in global scratch ----
-constexpr int kCoefThreads = 128;
-
+// ---- CTA solves: K > 32, and FP64 re-solves of blocks above the condition
+// threshold; packed Cholesky in global scratch (or shared memory) ----------
 __device__ __forceinline__ int pk(int i, int j) { return i * (i + 1) / 2 + j; }  // j <= i
 
-__device__ __forceinline__ float cta_sum(float v, float *red)
+template <typename T>
+__device__ __forceinline__ T cta_sum(T v, T *red)
 {
-    v = seg_sum<32>(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     __syncthreads();
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
-    float t = 0.f;
+    T t = 0;
     for (int k = 0; k < kCoefThreads / 32; ++k) t += red[k];
     return t;
 }
 
-// One block with K > 32 by the whole CTA: G_PP packed in the scratch slot
-// big (global), the right-hand sides after it.  Same arithmetic as
-// seg_block_coef.
-__device__ __noinline__ void cta_large_solve(const BlockJobs &J, const BlockTables &tab, const BlockScratch &S, int gb,
-                                             float *big, unsigned char *s_p, float *red, int *s_bad)
+__device__ __forceinline__ float rsqrt_pos(float d) { return rsqrtf(fmaxf(d, 1e-30f)); }
+__device__ __forceinline__ double rsqrt_pos(double d) { return rsqrt(fmax(d, 1e-300)); }
+
+// Coefficients of one block with valid positions s_p by the whole CTA in
+// precision T: G_PP packed in L (then the three right-hand sides v0, v1, 1).
+// Same steps as seg_block_coef: L y_v = v, L y_1 = 1, a = (y_1.y_v)/(y_1.y_1),
+// L^T c = y_v - a y_1.  Returns false for a non-positive pivot.
+template <typename T>
+__device__ bool cta_solve(const BlockPlane &P, const BlockGeom &g, const unsigned char *s_p, const T *G, int rl, T *L,
+                          T *red)
+{
+    const int tid = threadIdx.x, K = g.K;
+    const bool two = P.val[1] != nullptr;
+    T *b = L + pk(K, 0);  // b[r*K + i]
+    for (int j = tid; j < K; j += kCoefThreads) {
+        b[j] = (T)__ldg(P.val[0] + g.s + j);
+        b[K + j] = two ? (T)__ldg(P.val[1] + g.s + j) : (T)0;
+        b[2 * K + j] = 1;
+    }
+    for (int i = tid; i < K; i += kCoefThreads)
+        for (int j = 0; j <= i; ++j) L[pk(i, j)] = __ldg(G + s_p[i] * rl + s_p[j]);
+    __syncthreads();
+    bool spd = true;
+    for (int k = 0; k < K; ++k) {
+        const T d = L[pk(k, k)];
+        spd = spd && d > (T)0;
+        const T isd = rsqrt_pos(d);
+        __syncthreads();
+        if (tid == 0) L[pk(k, k)] = d * isd;
+        for (int i = k + 1 + tid; i < K; i += kCoefThreads) L[pk(i, k)] *= isd;
+        __syncthreads();
+        for (int i = k + 1 + tid; i < K; i += kCoefThreads) {
+            const T lik = L[pk(i, k)];
+            for (int j = k + 1; j <= i; ++j) L[pk(i, j)] = fma(-lik, L[pk(j, k)], L[pk(i, j)]);
+        }
+        __syncthreads();
+    }
+    for (int k = 0; k < K; ++k) {  // forward L y = b (three right-hand sides)
+        if (tid < 3) b[tid * K + k] /= L[pk(k, k)];
+        __syncthreads();
+        for (int i = k + 1 + tid; i < K; i += kCoefThreads) {
+            const T l = L[pk(i, k)];
+            b[i] = fma(-l, b[k], b[i]);
+            b[K + i] = fma(-l, b[K + k], b[K + i]);
+            b[2 * K + i] = fma(-l, b[2 * K + k], b[2 * K + i]);
+        }
+        __syncthreads();
+    }
+    T s0 = 0, s1 = 0, s2 = 0;  // a = (y_1 . y_v) / (y_1 . y_1)
+    for (int i = tid; i < K; i += kCoefThreads) {
+        const T y2 = b[2 * K + i];
+        s0 += y2 * b[i];
+        s1 += y2 * b[K + i];
+        s2 += y2 * y2;
+    }
+    s2 = cta_sum(s2, red);
+    const T a0 = cta_sum(s0, red) / s2, a1 = cta_sum(s1, red) / s2;
+    __syncthreads();
+    for (int i = tid; i < K; i += kCoefThreads) {
+        b[i] = fma(-a0, b[2 * K + i], b[i]);
+        b[K + i] = fma(-a1, b[2 * K + i], b[K + i]);
+    }
+    __syncthreads();
+    for (int k = K - 1; k >= 0; --k) {  // backward L^T c = y_v - a y_1
+        if (tid < 2) b[tid * K + k] /= L[pk(k, k)];
+        __syncthreads();
+        for (int i = tid; i < k; i += kCoefThreads) {
+            const T l = L[pk(k, i)];
+            b[i] = fma(-l, b[k], b[i]);
+            b[K + i] = fma(-l, b[K + k], b[K + i]);
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < K; i += kCoefThreads) {
+        P.coef[0][g.s + i] = (float)b[i];
+        if (two) P.coef[1][g.s + i] = (float)b[K + i];
+    }
+    if (tid == 0) {
+        P.acoef[0][g.lb] = (float)a0;
+        if (two) P.acoef[1][g.lb] = (float)a1;
+    }
+    return spd;
+}
+
+// One list entry by the whole CTA: a block with K > 32 (FP32 in the range's
+// slot unless its condition bound exceeds the threshold) or a block already
+// found above the threshold (kF64Bit), re-solved in FP64 in the slot, or in
+// w64 (shared, K <= kTK) when the CTA has no slot.
+__device__ __noinline__ void cta_block(const BlockJobs &J, const BlockTables &tab, const BlockScratch &S, int entry,
+                                       float *slot, double *w64, unsigned char *s_p, float *redf, double *redd,
+                                       int *s_bad)
 {
     const int tid = threadIdx.x;
+    const int gb = entry & ~kF64Bit;
     const BlockPlane &P = J.p[find_job(J, gb)];
     const BlockGeom g = block_geom(P, gb - P.block_base);
-    const int K = g.K;
-    const bool two = P.val[1] != nullptr;
-    float *L = big;
-    float *b = big + (size_t)kBigMaxK * (kBigMaxK + 1) / 2;  // b[r*K + i]
+    const int K = g.K, N = g.w * g.h;
     if (tid == 0) *s_bad = 0;
     __syncthreads();
     for (int j = tid; j < K; j += kCoefThreads) {
         int p;
         if (!load_pos(P, g, j, p)) *s_bad = 1;
         s_p[j] = (unsigned char)p;
-        b[j] = (float)__ldg(P.val[0] + g.s + j);
-        b[K + j] = two ? (float)__ldg(P.val[1] + g.s + j) : 0.f;
-        b[2 * K + j] = 1.f;
     }
     __syncthreads();
     if (*s_bad) {
@@ -343,70 +455,26 @@ __device__ __noinline__ void cta_large_solve(const BlockJobs &J, const BlockTabl
         __syncthreads();
         return;
     }
-    const float *G = green_rows(tab, g.w, g.h);
-    const int rl = g_rowlen(g.w * g.h);
-    for (int i = tid; i < K; i += kCoefThreads)
-        for (int j = 0; j <= i; ++j) L[pk(i, j)] = __ldg(G + s_p[i] * rl + s_p[j]);
-    __syncthreads();
-    bool spd = true;
-    for (int k = 0; k < K; ++k) {
-        const float d = L[pk(k, k)];
-        spd = spd && d > 0.f;
-        const float isd = rsqrtf(fmaxf(d, 1e-30f));
-        __syncthreads();
-        if (tid == 0) L[pk(k, k)] = d * isd;
-        for (int i = k + 1 + tid; i < K; i += kCoefThreads) L[pk(i, k)] *= isd;
-        __syncthreads();
-        for (int i = k + 1 + tid; i < K; i += kCoefThreads) {
-            const float lik = L[pk(i, k)];
-            for (int j = k + 1; j <= i; ++j) L[pk(i, j)] = fmaf(-lik, L[pk(j, k)], L[pk(i, j)]);
-        }
-        __syncthreads();
+    const int off = __ldg(tab.goff + shape_index(g.w, g.h)), rl = g_rowlen(N);
+    bool f64 = (entry & kF64Bit) != 0;
+    if (!f64) {
+        float d = 0.f;
+        for (int i = tid; i < K; i += kCoefThreads) d += __ldg(tab.G + off + s_p[i] * rl + s_p[i]);
+        const float kappa = cond_bound(cta_sum(d, redf), K, N);
+        if (tid == 0) note_kappa(S, kappa);
+        f64 = kappa > S.tau;
     }
-    for (int k = 0; k < K; ++k) {  // forward L y = b (three right-hand sides)
-        if (tid < 3) b[tid * K + k] /= L[pk(k, k)];
-        __syncthreads();
-        for (int i = k + 1 + tid; i < K; i += kCoefThreads) {
-            const float l = L[pk(i, k)];
-            b[i] = fmaf(-l, b[k], b[i]);
-            b[K + i] = fmaf(-l, b[K + k], b[K + i]);
-            b[2 * K + i] = fmaf(-l, b[2 * K + k], b[2 * K + i]);
-        }
-        __syncthreads();
+    if (f64 && K > (slot ? kF64MaxK : kTK)) {
+        if (tid == 0) atomicOr(S.flags, kFlagCond);
+        f64 = false;
     }
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f;  // a = (y_1 . y_v) / (y_1 . y_1)
-    for (int i = tid; i < K; i += kCoefThreads) {
-        const float y2 = b[2 * K + i];
-        s0 += y2 * b[i];
-        s1 += y2 * b[K + i];
-        s2 += y2 * y2;
-    }
-    s2 = cta_sum(s2, red);
-    const float a0 = cta_sum(s0, red) / s2, a1 = cta_sum(s1, red) / s2;
-    __syncthreads();
-    for (int i = tid; i < K; i += kCoefThreads) {
-        b[i] = fmaf(-a0, b[2 * K + i], b[i]);
-        b[K + i] = fmaf(-a1, b[2 * K + i], b[K + i]);
-    }
-    __syncthreads();
-    for (int k = K - 1; k >= 0; --k) {  // backward L^T c = y_v - a y_1
-        if (tid < 2) b[tid * K + k] /= L[pk(k, k)];
-        __syncthreads();
-        for (int i = tid; i < k; i += kCoefThreads) {
-            const float l = L[pk(k, i)];
-            b[i] = fmaf(-l, b[k], b[i]);
-            b[K + i] = fmaf(-l, b[K + k], b[K + i]);
-        }
-        __syncthreads();
-    }
-    for (int i = tid; i < K; i += kCoefThreads) {
-        P.coef[0][g.s + i] = b[i];
-        if (two) P.coef[1][g.s + i] = b[K + i];
-    }
+    const bool spd = f64 ? cta_solve<double>(P, g, s_p, tab.G64 + off, rl, slot ? reinterpret_cast<double *>(slot) : w64,
+                                             redd)
+                         : cta_solve<float>(P, g, s_p, tab.G + off, rl, slot, redf);
     if (tid == 0) {
-        P.acoef[0][g.lb] = a0;
-        if (two) P.acoef[1][g.lb] = a1;
         if (!spd) atomicOr(S.flags, kFlagNotSPD);
+        if (S.cstat && f64) atomicAdd(S.cstat + 1, 1u);
+        if (S.cstat && K > kWarpK) atomicAdd(S.cstat + 2, 1u);
     }
     __syncthreads();
 }
@@ -434,10 +502,11 @@ __device__ __forceinline__ void warp_path(const BlockJobs &J, const BlockTables 
             m16 &= m16 - 1;
         }
         const int mine = half ? bb : ba;
-        SegBlock b = seg_block(J, mine >= 0 ? gb0 + mine : J.total_blocks);
+        const int gb = mine >= 0 ? gb0 + mine : J.total_blocks;
+        SegBlock b = seg_block(J, gb);
         b.g.K = seg_k(b);
         const int K = seg_validate<16>(b, i, half, S);
-        seg_run<16, 16>(b, K, i, sm + half * 16 * 17, tab, S);
+        seg_run<16, 16>(b, K, i, sm + half * 16 * 17, tab, S, gb, s_large, s_nlarge);
         __syncwarp();
     }
     while (m32) {
@@ -446,8 +515,8 @@ __device__ __forceinline__ void warp_path(const BlockJobs &J, const BlockTables 
         SegBlock b = seg_block(J, gb0 + ba);
         b.g.K = seg_k(b);
         const int K = seg_validate<32>(b, lane, 0, S);
-        if (K > 24) seg_run<32, 0>(b, K, lane, sm, tab, S);
-        else if (K > 0) seg_run<32, 24>(b, K, lane, sm, tab, S);
+        if (K > 24) seg_run<32, 0>(b, K, lane, sm, tab, S, gb0 + ba, s_large, s_nlarge);
+        else if (K > 0) seg_run<32, 24>(b, K, lane, sm, tab, S, gb0 + ba, s_large, s_nlarge);
         __syncwarp();
     }
 }
@@ -456,8 +525,10 @@ __device__ __forceinline__ void warp_path(const BlockJobs &J, const BlockTables 
 // kRange blocks.  Thread-path CTA c: thread t takes block kRange c + t and
 // solves it when K <= 12.  Warp-path CTA c, at the same time: its warps
 // solve the range's blocks with 12 < K <= 32, then the whole CTA those with
-// K > 32, one after the other in the range's scratch slot.  No counters:
-// the kernel's completion publishes every result.
+// K > 32, one after the other in the range's scratch slot.  Blocks whose
+// condition bound exceeds the threshold are re-solved in FP64 by their CTA
+// after its first phase (thread path: in shared memory; warp path: in the
+// slot).  No counters: the kernel's completion publishes every result.
 __global__ void __launch_bounds__(kCoefThreads, 3) block_coef_kernel(const __grid_constant__ BlockJobs J,
                                                                      BlockTables tab, BlockScratch S)
 {
@@ -465,29 +536,39 @@ __global__ void __launch_bounds__(kCoefThreads, 3) block_coef_kernel(const __gri
     __shared__ float lts[kCoefThreads / 32][32 * 33];
     __shared__ unsigned char s_p[kBigMaxK];
     __shared__ float red[kCoefThreads / 32];
+    __shared__ double redd[kCoefThreads / 32];
+    __shared__ double w64[tri(kTK) + 3 * kTK];
     __shared__ int s_large[kRange], s_nlarge, s_bad;
     // the fused kernel that follows may start its prologue (tensor-memory
     // copies of flow and references) now; it waits for this grid's results
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int nrange = block_ranges(J.total_blocks);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) s_nlarge = 0;
+    __syncthreads();
     if ((int)blockIdx.x < nrange) {
         const int gb = blockIdx.x * kRange + threadIdx.x;
+        float kappa = 0.f;
         if (gb < J.total_blocks) {
             const BlockPlane &P = J.p[find_job(J, gb)];
             const BlockGeom g = block_geom(P, gb - P.block_base);
             if (g.bad) {
                 atomicOr(S.flags, g.bad);
             } else if (g.K > 0 && g.K <= kTK) {
-                if (P.val[1] != nullptr) thread_run<true>(P, g, tab, S);
-                else thread_run<false>(P, g, tab, S);
+                kappa = P.val[1] != nullptr ? thread_run<true>(P, g, tab, S) : thread_run<false>(P, g, tab, S);
             }
         }
+        if (kappa > S.tau) s_large[atomicAdd(&s_nlarge, 1)] = gb | kF64Bit;
+        if (S.cstat) {
+            const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(kappa));
+            if (lane == 0 && m) atomicMax(S.cstat, m);
+        }
+        __syncthreads();
+        const int n = s_nlarge;
+        for (int i = 0; i < n; ++i) cta_block(J, tab, S, s_large[i], nullptr, w64, s_p, red, redd, &s_bad);
         return;
     }
     const int range = blockIdx.x - nrange;
-    if (threadIdx.x == 0) s_nlarge = 0;
-    __syncthreads();
     const int gb0 = range * kRange + warp * 32;
     if (gb0 < J.total_blocks) warp_path(J, tab, S, gb0, lane, lts[warp], s_large, &s_nlarge);
     __syncthreads();
@@ -497,8 +578,8 @@ __global__ void __launch_bounds__(kCoefThreads, 3) block_coef_kernel(const __gri
         if (threadIdx.x == 0) atomicOr(S.flags, kFlagK);
         return;
     }
-    float *big = S.big + (size_t)range * kBigFloats;
-    for (int i = 0; i < n; ++i) cta_large_solve(J, tab, S, s_large[i], big, s_p, red, &s_bad);
+    float *slot = S.big + (size_t)range * kBigFloats;
+    for (int i = 0; i < n; ++i) cta_block(J, tab, S, s_large[i], slot, w64, s_p, red, redd, &s_bad);
 }
 
 // ---- evaluation stage into residual fields, one warp per block -----------
@@ -635,15 +716,19 @@ cudaError_t ensure_block_tables()
     std::lock_guard<std::mutex> lk(g_tab_mu);
     if ((g_tab_devices >> dev) & 1ull) return cudaSuccess;
     static std::vector<float> G;
+    static std::vector<double> G64;
     static std::vector<int> goff;
-    if (G.empty()) build_tables(G, goff);
+    if (G.empty()) build_tables(G, G64, goff);
     if ((e = cudaMemcpyToSymbol(d_G, G.data(), G.size() * sizeof(float))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(d_G64, G64.data(), G64.size() * sizeof(double))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(d_goff, goff.data(), goff.size() * sizeof(int))) != cudaSuccess) return e;
     BlockTables t{};
     if ((e = cudaGetSymbolAddress((void **)&t.G, d_G)) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void **)&t.G64, d_G64)) != cudaSuccess) return e;
     if ((e = cudaGetSymbolAddress((void **)&t.goff, d_goff)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&t.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = fused_init()) != cudaSuccess) return e;
+    if ((e = intra_init()) != cudaSuccess) return e;
     g_tabs[dev] = t;
     g_tab_devices |= 1ull << dev;
     return cudaSuccess;

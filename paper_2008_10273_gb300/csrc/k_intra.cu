@@ -347,21 +347,6 @@ cudaError_t launch_intra_sor(IntraJobs &J, int e_in, bool from_zero, int sweeps,
         P.tile_base = base;
         base += P.tiles_x * ((P.height + kTY - 1) / kTY);
     }
-    // one staged region per CTA, one CTA per SM (its colour arrays take
-    // dynamic shared memory beyond the static limit)
-    static bool attr[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!attr[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(intra_sor_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kSorSmem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(intra_sor_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kSorSmem);
-        if (e != cudaSuccess) return e;
-        attr[dev] = true;
-    }
     int cur = e_in;
     const int n = (sweeps + kS - 1) / kS;
     for (int l = 0; l < n; ++l) {
@@ -375,5 +360,15 @@ cudaError_t launch_intra_sor(IntraJobs &J, int e_in, bool from_zero, int sweeps,
 }
 
 int intra_sweeps_per_launch() { return kS; }
+
+// One staged region per CTA, one CTA per SM: the colour arrays take dynamic
+// shared memory beyond the static limit.  Called once per device.
+cudaError_t intra_init()
+{
+    cudaError_t e = cudaFuncSetAttribute(intra_sor_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSorSmem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(intra_sor_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSorSmem);
+}
 
 }  // namespace hivc

@@ -21,6 +21,7 @@
 // coefficient reads); after the previous frame's fused kernel (a batch of
 // frames, coefficients already complete) it waits for that grid, which
 // wrote its references, before the first copy.
+#include <atomic>
 #include <cuda.h>
 
 #include "block_device.cuh"
@@ -833,9 +834,10 @@ template <bool C, int B, bool TMA>
 cudaError_t launch_variant(FusedFrame &F, const FusedMaps *maps, uint32_t *flags, cudaLaunchConfig_t &cfg,
                            const BlockTables &t)
 {
-    static int occ = 0;
-    if (occ == 0) occ = occupancy(pframe_kernel<C, B, TMA>, kernel_smem<TMA>());
-    cfg.gridDim = dim3(std::max(1, std::min(F.nmb, t.sms * occ)));
+    static std::atomic<int> occ{0};
+    int o = occ.load(std::memory_order_relaxed);
+    if (o == 0) occ.store(o = occupancy(pframe_kernel<C, B, TMA>, kernel_smem<TMA>()), std::memory_order_relaxed);
+    cfg.gridDim = dim3(std::max(1, std::min(F.nmb, t.sms * o)));
     cfg.dynamicSmemBytes = kernel_smem<TMA>();
     static const FusedMaps none{};
     const FusedMaps &m = maps ? *maps : none;
@@ -880,10 +882,14 @@ cudaError_t launch_pframe_rf(FusedFrame &F, const FusedMaps &maps, uint32_t *fla
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
     cfg.dynamicSmemBytes = kRfSmem;
-    static int occ[2] = {0, 0};
+    static std::atomic<int> occ[2] = {{0}, {0}};
     const int c = F.chroma ? 1 : 0;
-    if (occ[c] == 0) occ[c] = c ? occupancy(pframe_rf_kernel<true>, kRfSmem) : occupancy(pframe_rf_kernel<false>, kRfSmem);
-    cfg.gridDim = dim3(std::max(1, std::min(F.nmb, t.sms * occ[c])));
+    int o = occ[c].load(std::memory_order_relaxed);
+    if (o == 0) {
+        o = c ? occupancy(pframe_rf_kernel<true>, kRfSmem) : occupancy(pframe_rf_kernel<false>, kRfSmem);
+        occ[c].store(o, std::memory_order_relaxed);
+    }
+    cfg.gridDim = dim3(std::max(1, std::min(F.nmb, t.sms * o)));
     if (c) return cudaLaunchKernelEx(&cfg, pframe_rf_kernel<true>, F, maps, flags);
     return cudaLaunchKernelEx(&cfg, pframe_rf_kernel<false>, F, maps, flags);
 }

@@ -80,6 +80,7 @@ PROTOTYPES = [
     ("hivc_decode_batch", c_i32, [ctypes.POINTER(c_vp), ctypes.POINTER(Frame), c_i32, ctypes.POINTER(Out)]),
     ("hivc_decoder_sync", c_i32, [c_vp, ctypes.POINTER(Stats)]),
     ("hivc_decoder_set_timing", c_i32, [c_vp, c_i32]),
+    ("hivc_decoder_reset", c_i32, [c_vp]),
     ("hivc_decoder_reference", c_i32, [c_vp, c_i32, ctypes.POINTER(c_vp), ctypes.POINTER(c_i32),
                                        ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
     ("hivc_decoder_stream", c_vp, [c_vp]),
@@ -187,6 +188,10 @@ class Decoder:
             check(lib().hivc_decoder_set_timing(self.handle, 1))
 
     # -- lifetime ------------------------------------------------------------
+    def reset(self):
+        """Forget the reference frame: the next frame must be an intra frame."""
+        check(lib().hivc_decoder_reset(self.handle))
+
     def close(self):
         if getattr(self, "handle", None):
             lib().hivc_decoder_destroy(self.handle)

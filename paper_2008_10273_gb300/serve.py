@@ -8,7 +8,10 @@ batching: every pass hands all frames that have arrived (up to
 ``hivc_decode_batch`` call.  Inter frames of a decoder share block launches,
 and each decoder runs on its own stream, so the work of different streams
 overlaps on the device.  A stream whose frames are all decoded leaves and
-frees its budget for the next waiting one.
+returns its decoder to an idle pool: a later stream of the same frame size
+reuses it (reset, so its first frame must be an intra frame) without a new
+allocation, and idle decoders are destroyed only when a stream of another
+size needs their bytes.  The budget counts active and idle decoders.
 
 A frame's latency is the time from its arrival to the moment the host sees
 its decode complete (a CUDA event recorded after it on its decoder's
@@ -76,23 +79,50 @@ class Server:
         self.poll = poll_s
         self.used = 0
         self.admit_log: List = []
+        self.idle: dict = {}  # stream key -> [(decoder, budget bytes)]
+        self.created = 0
+
+    @staticmethod
+    def _key(s: Stream):
+        return (s.width, s.height, s.chroma, s.block, s.iframe_tol)
+
+    def _evict_one(self) -> bool:
+        for key, pool in self.idle.items():
+            if pool:
+                dec, nbytes = pool.pop()
+                dec.close()
+                self.used -= nbytes
+                return True
+        return False
 
     def _try_admit(self, s: Stream, now: float) -> bool:
         need = stream_budget_bytes(s, self.per_stream)
-        if self.used + need > self.budget:
-            return False
-        s.decoder = hivc.Decoder(s.width, s.height, chroma=s.chroma, block=s.block, iframe_tol=s.iframe_tol)
+        pool = self.idle.get(self._key(s))
+        if pool:
+            s.decoder, need = pool.pop()
+            s.decoder.reset()
+        else:
+            while self.used + need > self.budget and self._evict_one():
+                pass
+            if self.used + need > self.budget:
+                return False
+            s.decoder = hivc.Decoder(s.width, s.height, chroma=s.chroma, block=s.block, iframe_tol=s.iframe_tol)
+            self.created += 1
+            self.used += need
         s.out = hivc.alloc_out(s.width, s.height, chroma=s.chroma)
         s.budget_bytes = need
-        self.used += need
         self.admit_log.append((s.name, round(now, 6)))
         return True
 
     def _release(self, s: Stream):
         s.decoder.sync()
-        s.decoder.close()
+        self.idle.setdefault(self._key(s), []).append((s.decoder, s.budget_bytes))
         s.decoder = None
-        self.used -= s.budget_bytes
+
+    def close(self):
+        """Destroy the idle decoders."""
+        while self._evict_one():
+            pass
 
     @staticmethod
     def _poll(s: Stream):
@@ -126,6 +156,7 @@ class Server:
         waiting = list(streams)
         active: List[Stream] = []
         self.admit_log = []
+        created0 = self.created
         t0 = time.perf_counter()
         calls = 0
         while waiting or active:
@@ -188,4 +219,4 @@ class Server:
         q = lambda f: lat[min(len(lat) - 1, int(round(f * (len(lat) - 1))))]
         return {"frames": len(lat), "wall_s": wall, "fullhd_fps": px / (1920 * 1080) / wall,
                 "p50_ms": 1e3 * q(0.5), "p99_ms": 1e3 * q(0.99), "calls": calls,
-                "admitted": list(self.admit_log)}
+                "admitted": list(self.admit_log), "decoders_created": self.created - created0}

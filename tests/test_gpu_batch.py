@@ -126,3 +126,60 @@ def test_batch_rejects_a_bad_frame(hv):
         hv.decode_batch([dec] * 3, frames, outs)
     assert e.value.status == hv.HIVC_E_INVALID
     dec.sync()
+
+
+def test_batch_many_decoders_with_intra_frames(hv):
+    """Six decoders of mixed sizes, each an intra frame and inter frames, in
+    one call: decoders with intra frames run on their own host threads; each
+    must match its own per-frame decoding bit for bit."""
+    specs = [(160, 90, True, 5), (96, 64, False, 4), (131, 67, True, 3), (64, 48, True, 6), (160, 90, True, 2),
+             (150, 70, False, 5)]
+    decs, frames, outs, tags, ref = [], [], [], [], []
+    per = []
+    for i, (W, H, ch, n) in enumerate(specs):
+        g = make_gop(40 + i, W, H, n_frames=n, chroma=ch)
+        ref.append(_per_frame(hv, g, W, H, ch, 16)[1])
+        d = hv.Decoder(W, H, chroma=ch)
+        per.append((d, [("i", hv.device_iframe(g.iframe))] + [("p", hv.device_pframe(p)) for p in g.pframes], W, H,
+                    ch))
+    # interleave the streams' frames (each stream's own order kept)
+    t = 0
+    while any(t < len(f) for _, f, _, _, _ in per):
+        for i, (d, f, W, H, ch) in enumerate(per):
+            if t < len(f):
+                decs.append(d)
+                frames.append(f[t])
+                outs.append(hv.alloc_out(W, H, chroma=ch))
+                tags.append((i, t))
+        t += 1
+    hv.decode_batch(decs, frames, outs)
+    for d, *_ in per:
+        d.sync()
+    for (i, t), out in zip(tags, outs):
+        for p, o in enumerate(out):
+            assert np.array_equal(to_np(o), ref[i][t][p]), (i, t, p)
+
+
+def test_batch_reference_rules(hv):
+    """An inter frame needs a reference: the decoder's own, or an intra frame
+    earlier in the same call; hivc_decoder_reset forgets it."""
+    W, H = 64, 48
+    g = make_gop(9, W, H, n_frames=3, chroma=False)
+    fi = ("i", hv.device_iframe(g.iframe))
+    fp = [("p", hv.device_pframe(p)) for p in g.pframes]
+    o = lambda: hv.alloc_out(W, H, chroma=False)
+    d1, d2 = hv.Decoder(W, H, chroma=False), hv.Decoder(W, H, chroma=False)
+    with pytest.raises(hv.HivcError) as e:
+        hv.decode_batch([d1, d2, d1], [fi, fp[0], fp[0]], [o(), o(), o()])
+    assert e.value.status == hv.HIVC_E_NO_REFERENCE
+    hv.decode_batch([d2, d1, d2], [fi, fi, fp[0]], [o(), o(), o()])
+    hv.decode_batch([d1], [fp[0]], [o()])
+    d1.reset()
+    with pytest.raises(hv.HivcError) as e:
+        hv.decode_batch([d1], [fp[1]], [o()])
+    assert e.value.status == hv.HIVC_E_NO_REFERENCE
+    with pytest.raises(hv.HivcError) as e:
+        d1.decode_pframe(fp[1][1], o())
+    assert e.value.status == hv.HIVC_E_NO_REFERENCE
+    d1.sync()
+    d2.sync()

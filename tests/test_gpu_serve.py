@@ -86,3 +86,22 @@ def test_stream_larger_than_budget_is_refused(hv):
     streams = _streams(hv, serve)[:1]
     with pytest.raises(ValueError):
         serve.Server(1 << 20).run(streams)
+
+
+def test_server_reuses_idle_decoders(hv):
+    """A second run on the same server takes the idle decoders of the first
+    (reset, no new allocation) and decodes the same frames identically."""
+    from paper_2008_10273_gb300 import serve
+
+    streams = _streams(hv, serve, seed=2)
+    srv = serve.Server(1 << 40)
+    st1 = srv.run(streams)
+    first = [[[to_np(p).copy() for p in o] for o in s.outputs] for s in streams]
+    st2 = srv.run(streams)
+    assert st1["decoders_created"] == len(streams) and st2["decoders_created"] == 0
+    for s, f in zip(streams, first):
+        for k, o in enumerate(s.outputs):
+            for p, plane in enumerate(o):
+                assert np.array_equal(to_np(plane), f[k][p]), (s.name, k, p)
+    srv.close()
+    assert srv.used == 0
