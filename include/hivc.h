@@ -63,9 +63,15 @@ typedef struct {
                                1e-8; FP32-only mode floors near 1e-3 */
     int32_t max_cycles;     /* cap on outer correction cycles (default 40);
                                beyond it sync returns HIVC_E_NOT_CONVERGED */
-    double cond_threshold;  /* reserved: condition threshold above which block
-                               systems would be re-solved in higher precision
-                               (default 1e6) */
+    double cond_threshold;  /* >= 0 (default 1e6).  Every residual block's
+                               condition bound kappa = 8 tr(G_PP) / (1 - K/N)
+                               >= cond_2(G_PP) (Sec. 2.2: the eigenvalues of
+                               A = -L are at most 8) is compared with it; a
+                               block above it is re-solved in FP64 from an
+                               FP64 Green's table (K <= 179; larger K keep
+                               FP32 and set device flag bit 6).  No block
+                               shape reaches 4e5, so the default never
+                               triggers; 0 re-solves every block */
     void *stream;           /* cudaStream_t to run on; NULL = the decoder
                                creates its own non-blocking stream */
 } hivc_config;
@@ -133,10 +139,11 @@ typedef struct {
     double resid[3];        /* final Eq. 1 residual per plane (last intra) */
     int32_t cycles;         /* outer correction cycles of the last intra */
     int32_t sweeps;         /* red-black sweeps of the last intra */
-    int32_t fp64_blocks;    /* reserved (0) */
-    int32_t large_blocks;   /* reserved (0) */
-    float max_cond;         /* reserved (0) */
-    uint32_t device_flags;  /* data errors seen by the kernels (bit set) */
+    int32_t fp64_blocks;    /* residual blocks re-solved in FP64 */
+    int32_t large_blocks;   /* residual blocks with K > 32 (solved by a CTA) */
+    float max_cond;         /* largest residual-block condition bound kappa */
+    uint32_t device_flags;  /* data errors seen by the kernels (bit set;
+                               bit 6 is information, not an error) */
     int32_t frames;         /* frames since the previous sync */
     int32_t launches;       /* kernel launches since the previous sync */
     /* per kernel family: accumulated device time (ms, CUDA events, only

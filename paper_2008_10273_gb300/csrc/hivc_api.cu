@@ -77,11 +77,17 @@ struct PlaneGeom {
     int w, h, pitch, nblocks, nbx;
 };
 
+// device status words of a decoder: error flags, then the condition
+// statistics of the coefficient stage (max bound bits, FP64 re-solves,
+// K > 32 blocks)
+constexpr int kStatusWords = 4;
+
 bool config_ok(const hivc_config *c)
 {
     return c && c->width >= 1 && c->height >= 1 && c->width <= 16384 && c->height <= 16384 &&
            (c->chroma == 0 || c->chroma == 1) && c->block >= 1 && c->block <= kMaxB && c->op == 0 &&
-           (c->precision == 0 || c->precision == 1) && c->iframe_tol >= 0.0 && c->max_cycles >= 1;
+           (c->precision == 0 || c->precision == 1) && c->iframe_tol >= 0.0 && c->max_cycles >= 1 &&
+           c->cond_threshold >= 0.0;
 }
 
 int plane_count(const hivc_config *c) { return c->chroma ? 3 : 1; }
@@ -269,7 +275,7 @@ hivc_status make_block_jobs(hivc_decoder *d, const hivc_residual *res, BlockJobs
 
 BlockScratch scratch(hivc_decoder *d)
 {
-    return BlockScratch{d->flags, d->big, d->big_ranges};
+    return BlockScratch{d->flags, d->big, d->big_ranges, d->flags + 1, (float)d->cfg.cond_threshold};
 }
 
 // Unfused block stage: coefficients (+ large blocks), then residual fields.
@@ -405,7 +411,7 @@ hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out)
     d->big = m.get<float>((size_t)d->big_ranges * kBigFloats);
     d->vsum = m.get<unsigned long long>(3);
     d->rnorm = m.get<unsigned int>(3);
-    d->flags = m.get<uint32_t>(1);
+    d->flags = m.get<uint32_t>(kStatusWords);
     if (!m.ok) {
         m.release();
         delete d;
@@ -436,7 +442,8 @@ hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out)
         }
         d->own_stream = true;
     }
-    if (cudaMemsetAsync(d->flags, 0, 4, d->stream) != cudaSuccess || cudaStreamSynchronize(d->stream) != cudaSuccess) {
+    if (cudaMemsetAsync(d->flags, 0, 4 * kStatusWords, d->stream) != cudaSuccess ||
+        cudaStreamSynchronize(d->stream) != cudaSuccess) {
         hivc_decoder_destroy(d);
         return HIVC_E_CUDA;
     }
@@ -896,7 +903,8 @@ hivc_status decode_inter_run(hivc_decoder *d, const hivc_frame *frames, const hi
         }
         if ((s = make_block_jobs(d, frames[ks[k]].p->res, jobs[k], coef, acoef, rfield)) != HIVC_OK) return s;
     }
-    const BlockScratch S{d->flags, reinterpret_cast<float *>(pool + big_off), ranges};
+    const BlockScratch S{d->flags, reinterpret_cast<float *>(pool + big_off), ranges, d->flags + 1,
+                         (float)d->cfg.cond_threshold};
     BlockJobs J{};
     auto flush = [&]() -> cudaError_t {
         if (J.n == 0) return cudaSuccess;
@@ -1048,11 +1056,14 @@ hivc_status hivc_decoder_sync(hivc_decoder *d, hivc_stats *last)
 {
     if (!d) return HIVC_E_INVALID;
     if (cudaSetDevice(d->device) != cudaSuccess) return HIVC_E_CUDA;
-    cudaError_t e = cudaMemcpyAsync(d->h_flags, d->flags, 4, cudaMemcpyDeviceToHost, d->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d->flags, 0, 4, d->stream);
+    cudaError_t e = cudaMemcpyAsync(d->h_flags, d->flags, 4 * kStatusWords, cudaMemcpyDeviceToHost, d->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d->flags, 0, 4 * kStatusWords, d->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
     if (e != cudaSuccess) return HIVC_E_CUDA;
-    d->st.device_flags = *d->h_flags;
+    d->st.device_flags = d->h_flags[0];
+    std::memcpy(&d->st.max_cond, d->h_flags + 1, sizeof(float));
+    d->st.fp64_blocks = (int32_t)d->h_flags[2];
+    d->st.large_blocks = (int32_t)d->h_flags[3];
     for (auto &pe : d->pending) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess)
@@ -1069,7 +1080,7 @@ hivc_status hivc_decoder_sync(hivc_decoder *d, hivc_stats *last)
     fresh.sweeps = d->st.sweeps;
     d->st = fresh;
     if (fl & kFlagTimeout) return HIVC_E_TIMEOUT;
-    return fl ? HIVC_E_INVALID : HIVC_OK;
+    return (fl & ~kFlagCond) ? HIVC_E_INVALID : HIVC_OK;
 }
 
 // ---------------------------------------------------------------------------

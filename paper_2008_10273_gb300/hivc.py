@@ -173,10 +173,11 @@ class Decoder:
 
     def __init__(self, width: int, height: int, chroma: bool = True, block: int = 16,
                  iframe_tol: float = 1e-8, max_cycles: int = 40, precision: int = 0,
-                 stream=None, timing: bool = False):
+                 stream=None, timing: bool = False, cond_threshold: float = 1e6):
         cfg = config_default()
         cfg.width, cfg.height, cfg.chroma, cfg.block = width, height, int(chroma), block
         cfg.iframe_tol, cfg.max_cycles, cfg.precision = iframe_tol, max_cycles, precision
+        cfg.cond_threshold = cond_threshold
         cfg.stream = _stream_handle(stream)
         self.cfg = cfg
         self.width, self.height, self.chroma, self.block = width, height, bool(chroma), block
