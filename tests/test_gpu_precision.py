@@ -130,3 +130,23 @@ def test_fp64_resolve_batch_matches_per_frame(hv):
     for a, b in zip(*res):
         for p in range(3):
             assert np.array_equal(a[p], b[p])
+
+
+def test_fullhd_precision_report():
+    """The precision report at FullHD: every result within the parity bar
+    (0.5 grey levels, 0.01 dB), intra residuals at 1e-10, mask pixels exact,
+    no FP64 re-solve at the default threshold and all of them at 0."""
+    from precision_report import precision_report
+
+    hivc_module()
+    rep = precision_report()
+    for r in rep["intra"]:
+        assert all(x <= 1e-10 for x in r["resid"]), r
+        assert max(r["max_abs_err"]) <= TOL_RECON, r
+        assert max(abs(d) for d in r["dpsnr_db"]) <= 0.01, r
+        assert r["mask_exact"], r
+    d, f = rep["blocks"]
+    assert d["fp64_blocks"] == 0 and f["fp64_blocks"] > 0
+    for r in rep["blocks"]:
+        assert max(r["max_abs_err"]) <= TOL_RECON, r
+        assert max(abs(x) for x in r["dpsnr_db"]) <= 0.01, r
