@@ -226,54 +226,93 @@ __global__ void __launch_bounds__(kHW *kTY_THREADS, 1) intra_sor_kernel(const __
     }
     float *eout = P.e[e_in ^ 1];
     // The pair starts at an even column (tx0 and the halo are even), so its
-    // two cells are read as one 2-element vector.  Every load is issued
-    // unconditionally from a clamped address (rows into [0, H), the pair
-    // into the pitch) and cells outside the image are zeroed afterwards, so
-    // that all of them are in flight together.
+    // two cells are read as one 2-element vector.
     const int gxp = gx0 + 2 * hx;
-    const int gxc = min(max(gxp, 0), pitch - 2);
     const bool in0 = gxp >= 0 && gxp < W, in1 = gxp >= 0 && gxp + 1 < W;
-    uint32_t m2[kRows];
-    float2 r2[kRows], e2[kRows];
-#pragma unroll
-    for (int k = 0; k < kRows; ++k) {
-        const int gy = min(max(gy0 + ly0 + k, 0), H - 1);
-        const size_t i = (size_t)gy * pitch + gxc;
-        m2[k] = __ldg(reinterpret_cast<const unsigned short *>(P.mask + i));
-        r2[k] = __ldg(reinterpret_cast<const float2 *>(P.res + i));
-        if (!FROM_ZERO) e2[k] = __ldg(reinterpret_cast<const float2 *>(ein + i));
-    }
+    const float omega = P.omega, omc = 1.f - omega;
     // ec[k][c]: value of the thread's colour-c cell in row ly0 + k, which
-    // sits at column 2 hx + ((c + k) & 1); invc = 1/n, rnc = r/n
-    float ec[kRows][2], invc[kRows][2], rnc[kRows][2];
+    // sits at column 2 hx + ((c + k) & 1); wi = omega / n and wr = omega r / n
+    // for unknown cells, 0 for fixed ones (whose value is 0 and stays 0)
+    float ec[kRows][2], wi[kRows][2], wr[kRows][2];
+    // A region with every cell inside the image and off its border (all
+    // cells have four neighbours): plain loads, n = 4.
+    const bool interior = gx0 >= 1 && gy0 >= 1 && gx0 + kRW <= W - 1 && gy0 + kRH <= H - 1;
+    if (interior) {
+        const size_t i0 = (size_t)(gy0 + ly0) * pitch + gxp;
+        uint32_t m2[kRows];
+        float2 r2[kRows], e2[kRows];
+#pragma unroll
+        for (int k = 0; k < kRows; ++k) {
+            const size_t i = i0 + (size_t)k * pitch;
+            m2[k] = __ldg(reinterpret_cast<const unsigned short *>(P.mask + i));
+            r2[k] = __ldg(reinterpret_cast<const float2 *>(P.res + i));
+            if (!FROM_ZERO) e2[k] = __ldg(reinterpret_cast<const float2 *>(ein + i));
+        }
+        const float w4 = 0.25f * omega;
+#pragma unroll
+        for (int k = 0; k < kRows; ++k) {
+            float ev[2], iv[2], rv[2];
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const bool unk = ((m2[k] >> (8 * b)) & 0xffu) == 0;
+                iv[b] = unk ? w4 : 0.f;
+                rv[b] = (b ? r2[k].y : r2[k].x) * iv[b];
+                ev[b] = (FROM_ZERO || !unk) ? 0.f : (b ? e2[k].y : e2[k].x);
+            }
+            const int sw = k & 1;  // 1: the pair's left cell has colour 1 (ly0 is even)
+            ec[k][0] = ev[sw];
+            ec[k][1] = ev[sw ^ 1];
+            wi[k][0] = iv[sw];
+            wi[k][1] = iv[sw ^ 1];
+            wr[k][0] = rv[sw];
+            wr[k][1] = rv[sw ^ 1];
+        }
+    } else {
+        // Every load is issued unconditionally from a clamped address (rows
+        // into [0, H), the pair into the pitch) and cells outside the image
+        // are zeroed afterwards, so that all of them are in flight together.
+        const int gxc = min(max(gxp, 0), pitch - 2);
+        uint32_t m2[kRows];
+        float2 r2[kRows], e2[kRows];
+#pragma unroll
+        for (int k = 0; k < kRows; ++k) {
+            const int gy = min(max(gy0 + ly0 + k, 0), H - 1);
+            const size_t i = (size_t)gy * pitch + gxc;
+            m2[k] = __ldg(reinterpret_cast<const unsigned short *>(P.mask + i));
+            r2[k] = __ldg(reinterpret_cast<const float2 *>(P.res + i));
+            if (!FROM_ZERO) e2[k] = __ldg(reinterpret_cast<const float2 *>(ein + i));
+        }
+#pragma unroll
+        for (int k = 0; k < kRows; ++k) {
+            const int gy = gy0 + ly0 + k;
+            const bool yin = gy >= 0 && gy < H;
+            const int ny = (gy > 0) + (gy < H - 1);
+            float ev[2], iv[2], rv[2];
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const int gx = gxp + b;
+                const bool unk = yin && (b ? in1 : in0) && ((m2[k] >> (8 * b)) & 0xffu) == 0;
+                const int n = ny + (gx > 0) + (gx < W - 1);
+                const float inv = n == 4 ? 0.25f : (n == 3 ? (1.0f / 3.0f) : (n == 2 ? 0.5f : 1.0f));
+                iv[b] = unk ? omega * inv : 0.f;
+                rv[b] = unk ? (b ? r2[k].y : r2[k].x) * iv[b] : 0.f;
+                ev[b] = (FROM_ZERO || !unk) ? 0.f : (b ? e2[k].y : e2[k].x);
+            }
+            const int sw = k & 1;
+            ec[k][0] = ev[sw];
+            ec[k][1] = ev[sw ^ 1];
+            wi[k][0] = iv[sw];
+            wi[k][1] = iv[sw ^ 1];
+            wr[k][0] = rv[sw];
+            wr[k][1] = rv[sw ^ 1];
+        }
+    }
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
-        const int gy = gy0 + ly0 + k;
-        const bool yin = gy >= 0 && gy < H;
-        const int ny = (gy > 0) + (gy < H - 1);
-        float ev[2], iv[2], rv[2];
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const int gx = gxp + b;
-            const bool unk = yin && (b ? in1 : in0) && ((m2[k] >> (8 * b)) & 0xffu) == 0;
-            const int n = ny + (gx > 0) + (gx < W - 1);
-            const float inv = n == 4 ? 0.25f : (n == 3 ? (1.0f / 3.0f) : (n == 2 ? 0.5f : 1.0f));
-            iv[b] = unk ? inv : 0.f;
-            rv[b] = unk ? (b ? r2[k].y : r2[k].x) * inv : 0.f;
-            ev[b] = (FROM_ZERO || !unk) ? 0.f : (b ? e2[k].y : e2[k].x);
-        }
-        const int sw = k & 1;  // 1: the pair's left cell has colour 1 (ly0 is even)
-        ec[k][0] = sw ? ev[1] : ev[0];
-        ec[k][1] = sw ? ev[0] : ev[1];
-        invc[k][0] = sw ? iv[1] : iv[0];
-        invc[k][1] = sw ? iv[0] : iv[1];
-        rnc[k][0] = sw ? rv[1] : rv[0];
-        rnc[k][1] = sw ? rv[0] : rv[1];
         E[0][ly0 + k + 1][hx + 1] = ec[k][0];
         E[1][ly0 + k + 1][hx + 1] = ec[k][1];
     }
     __syncthreads();
-    const float omega = P.omega;
 #pragma unroll
     for (int m = 1; m <= 2 * kS; ++m) {
         const int c = (m - 1) & 1, o = c ^ 1;  // red (even x + y) first
@@ -284,8 +323,8 @@ __global__ void __launch_bounds__(kHW *kTY_THREADS, 1) intra_sor_kernel(const __
             const float up = k > 0 ? ec[k - 1][o] : E[o][ly - 1][hx + 1];
             const float dn = k < kRows - 1 ? ec[k + 1][o] : E[o][ly + 1][hx + 1];
             const float s = (ec[k][o] + E[o][ly][hx + 2 * b]) + (up + dn);
-            // fixed cells have invc = rnc = 0 and value 0: they stay 0
-            ec[k][c] = fmaf(omega, fmaf(s, invc[k][c], rnc[k][c] - ec[k][c]), ec[k][c]);
+            // e <- (1 - omega) e + omega (s + r) / n
+            ec[k][c] = fmaf(s, wi[k][c], fmaf(omc, ec[k][c], wr[k][c]));
             E[c][ly][hx + 1] = ec[k][c];
         }
         __syncthreads();
