@@ -19,6 +19,10 @@
 // staged in shared memory, split into its red and black cells, and S full
 // red-black sweeps run there before the interior is written back (each half
 // sweep invalidates one more halo ring).
+#include <algorithm>
+#include <vector>
+#include <mutex>
+#include <map>
 #include <cfloat>
 
 #include "hivc_internal.cuh"
@@ -29,13 +33,14 @@ namespace {
 // ---- SOR tile geometry ---------------------------------------------------
 constexpr int kS = 4;                   // full sweeps per launch
 constexpr int kHL = 2 * kS;             // halo
-constexpr int kRW = 128, kRH = 128;     // staged region
-constexpr int kTX = kRW - 2 * kHL;      // 112 output columns
+// staged region RW x kRH (RW = 128 or 112 columns: the launcher picks the
+// faster one per plane geometry), output (RW - 2 kHL) x (kRH - 2 kHL)
+constexpr int kRH = 128;
 constexpr int kTY = kRH - 2 * kHL;      // 112 output rows
-constexpr int kHW = kRW / 2;            // cells per colour and row
 constexpr int kTY_THREADS = 16;         // thread rows; each thread owns kRH/16 consecutive rows
 constexpr int kRows = kRH / kTY_THREADS;
-constexpr size_t kSorSmem = 2 * (kRH + 2) * (kHW + 2) * sizeof(float);  // bordered colour arrays
+__host__ __device__ constexpr int sor_tx(int rw) { return rw - 2 * kHL; }
+__host__ __device__ constexpr size_t sor_smem_bytes(int rw) { return 2 * (kRH + 2) * (rw / 2 + 2) * sizeof(float); }  // bordered colour arrays
 
 constexpr int kResThreads = 256;
 constexpr int kRTW = 64, kRTH = 16;  // residual tile
@@ -202,25 +207,26 @@ __global__ void __launch_bounds__(kResThreads) intra_residual_kernel(const __gri
 // exactness shrinks by one ring per half sweep anyway, and the 2S half
 // sweeps leave the interior, kHL = 2S rings in, exact.  Tile corners are
 // even (kTX, kTY, kHL even), so a cell's colour is known at compile time.
-static_assert(kTX % 2 == 0 && kTY % 2 == 0 && kHL % 2 == 0, "tiles start on even cells");
-template <bool FROM_ZERO>
-__global__ void __launch_bounds__(kHW *kTY_THREADS, 1) intra_sor_kernel(const __grid_constant__ IntraJobs J, int e_in)
+template <int RW, bool FROM_ZERO>
+__global__ void __launch_bounds__(RW / 2 * kTY_THREADS, 1) intra_sor_kernel(const __grid_constant__ IntraJobs J, int e_in)
 {
+    constexpr int HW = RW / 2, TX = sor_tx(RW);  // cells per colour and row; output columns
+    static_assert(TX % 2 == 0 && kTY % 2 == 0 && kHL % 2 == 0, "tiles start on even cells");
     extern __shared__ float sor_smem[];
-    auto E = reinterpret_cast<float(*)[kRH + 2][kHW + 2]>(sor_smem);
+    auto E = reinterpret_cast<float(*)[kRH + 2][HW + 2]>(sor_smem);
     const IntraPlane &P = J.p[find_plane(J, blockIdx.x)];
     const int lt = blockIdx.x - P.tile_base;
-    const int tx0 = (lt % P.tiles_x) * kTX, ty0 = (lt / P.tiles_x) * kTY;
+    const int tx0 = (lt % P.tiles_x) * TX, ty0 = (lt / P.tiles_x) * kTY;
     const int gx0 = tx0 - kHL, gy0 = ty0 - kHL;
     const int W = P.width, H = P.height, pitch = P.pitch;
     const int hx = threadIdx.x, ty = threadIdx.y, ly0 = ty * kRows;
     const float *ein = P.e[e_in];
     // the border of the colour arrays: finite values
-    for (int k = hx + ty * kHW; k < 2 * (kRH + 2); k += kHW * kTY_THREADS) {
+    for (int k = hx + ty * HW; k < 2 * (kRH + 2); k += HW * kTY_THREADS) {
         E[k & 1][k >> 1][0] = 0.f;
-        E[k & 1][k >> 1][kHW + 1] = 0.f;
+        E[k & 1][k >> 1][HW + 1] = 0.f;
     }
-    for (int k = hx + ty * kHW; k < 2 * (kHW + 2); k += kHW * kTY_THREADS) {
+    for (int k = hx + ty * HW; k < 2 * (HW + 2); k += HW * kTY_THREADS) {
         E[k & 1][0][k >> 1] = 0.f;
         E[k & 1][kRH + 1][k >> 1] = 0.f;
     }
@@ -236,7 +242,7 @@ __global__ void __launch_bounds__(kHW *kTY_THREADS, 1) intra_sor_kernel(const __
     float ec[kRows][2], wi[kRows][2], wr[kRows][2];
     // A region with every cell inside the image and off its border (all
     // cells have four neighbours): plain loads, n = 4.
-    const bool interior = gx0 >= 1 && gy0 >= 1 && gx0 + kRW <= W - 1 && gy0 + kRH <= H - 1;
+    const bool interior = gx0 >= 1 && gy0 >= 1 && gx0 + RW <= W - 1 && gy0 + kRH <= H - 1;
     if (interior) {
         const size_t i0 = (size_t)(gy0 + ly0) * pitch + gxp;
         uint32_t m2[kRows];
@@ -332,7 +338,7 @@ __global__ void __launch_bounds__(kHW *kTY_THREADS, 1) intra_sor_kernel(const __
     // interior pairs are whole pairs (even halo and width); a pair that
     // straddles an odd right edge writes its left cell only
     const int lx = 2 * hx;
-    if (lx < kHL || lx >= kHL + kTX || gxp >= W) return;
+    if (lx < kHL || lx >= kHL + TX || gxp >= W) return;
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
         const int ly = ly0 + k, gy = gy0 + ly;
@@ -376,21 +382,99 @@ cudaError_t launch_intra_residual(IntraJobs &J, int e_in, bool add_e, cudaStream
     return cudaGetLastError();
 }
 
-cudaError_t launch_intra_sor(IntraJobs &J, int e_in, bool from_zero, int sweeps, cudaStream_t st, int *e_out,
-                             int *launches)
+namespace {
+
+template <int RW>
+void sor_launch(IntraJobs &J, int cur, bool from_zero, cudaStream_t st)
 {
     int base = 0;
     for (int k = 0; k < J.n; ++k) {
         IntraPlane &P = J.p[k];
-        P.tiles_x = (P.width + kTX - 1) / kTX;
+        P.tiles_x = (P.width + sor_tx(RW) - 1) / sor_tx(RW);
         P.tile_base = base;
         base += P.tiles_x * ((P.height + kTY - 1) / kTY);
     }
-    int cur = e_in;
+    const dim3 block(RW / 2, kTY_THREADS);
+    if (from_zero) intra_sor_kernel<RW, true><<<base, block, sor_smem_bytes(RW), st>>>(J, cur);
+    else intra_sor_kernel<RW, false><<<base, block, sor_smem_bytes(RW), st>>>(J, cur);
+}
+
+void sor_launch_rw(int rw, IntraJobs &J, int cur, bool from_zero, cudaStream_t st)
+{
+    if (rw == 112) sor_launch<112>(J, cur, from_zero, st);
+    else sor_launch<128>(J, cur, from_zero, st);
+}
+
+// Tiling autotuner.  Both region widths perform exactly the same global
+// red-black sweeps (a cell's neighbour sum is formed in the same order), so
+// the choice changes speed only.  The first call with at least 12 launches
+// for a set of plane sizes on a device times each width on its own
+// launches (real sweeps of the solve, in alternating groups of three) and
+// keeps the narrower width only if it is at least 2 % faster.
+constexpr int kSorWidths[2] = {128, 112};
+std::mutex g_tune_mu;
+std::map<std::vector<int>, int> g_tuned;
+
+std::vector<int> tune_key(const IntraJobs &J)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::vector<int> k{dev};
+    for (int i = 0; i < J.n; ++i) {
+        k.push_back(J.p[i].width);
+        k.push_back(J.p[i].height);
+    }
+    return k;
+}
+
+}  // namespace
+
+int sor_region_width(const IntraJobs &J)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(tune_key(J));
+    return it == g_tuned.end() ? 0 : it->second;
+}
+
+cudaError_t launch_intra_sor(IntraJobs &J, int e_in, bool from_zero, int sweeps, cudaStream_t st, int *e_out,
+                             int *launches)
+{
     const int n = (sweeps + kS - 1) / kS;
-    for (int l = 0; l < n; ++l) {
-        if (from_zero && l == 0) intra_sor_kernel<true><<<base, dim3(kHW, kTY_THREADS), kSorSmem, st>>>(J, cur);
-        else intra_sor_kernel<false><<<base, dim3(kHW, kTY_THREADS), kSorSmem, st>>>(J, cur);
+    int cur = e_in, l = 0;
+    int rw = sor_region_width(J);
+    // untuned: each width timed twice over kTuneGroup consecutive launches
+    // (alternating groups), if the call has that many launches
+    constexpr int kTuneGroup = 3, kTuneLaunches = 4 * kTuneGroup;
+    if (rw == 0 && n >= kTuneLaunches) {
+        cudaEvent_t ev[5];
+        int made = 0;
+        cudaError_t e = cudaSuccess;
+        for (; made < 5 && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+        for (int t = 0; t < 4 && e == cudaSuccess; ++t) {
+            for (int g = 0; g < kTuneGroup; ++g, ++l) {
+                sor_launch_rw(kSorWidths[t & 1], J, cur, from_zero && l == 0, st);
+                cur ^= 1;
+            }
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(ev[t + 1], st);
+        }
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[4]);
+        float best[2] = {1e30f, 1e30f};
+        for (int t = 0; t < 4 && e == cudaSuccess; ++t) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, ev[t], ev[t + 1]);
+            best[t & 1] = std::min(best[t & 1], ms);
+        }
+        for (int i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
+        if (e != cudaSuccess) return e;
+        rw = best[1] < 0.98f * best[0] ? kSorWidths[1] : kSorWidths[0];
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[tune_key(J)] = rw;
+    }
+    if (rw == 0) rw = kSorWidths[0];
+    for (; l < n; ++l) {
+        sor_launch_rw(rw, J, cur, from_zero && l == 0, st);
         cur ^= 1;
     }
     if (launches) *launches += n;
@@ -404,10 +488,18 @@ int intra_sweeps_per_launch() { return kS; }
 // shared memory beyond the static limit.  Called once per device.
 cudaError_t intra_init()
 {
-    cudaError_t e = cudaFuncSetAttribute(intra_sor_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSorSmem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(intra_sor_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSorSmem);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(intra_sor_kernel<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sor_smem_bytes(128))) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(intra_sor_kernel<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sor_smem_bytes(128))) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(intra_sor_kernel<112, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sor_smem_bytes(112))) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(intra_sor_kernel<112, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sor_smem_bytes(112));
 }
 
 }  // namespace hivc

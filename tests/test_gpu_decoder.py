@@ -222,3 +222,60 @@ def test_invalid_arguments(hv):
     with pytest.raises(hv.HivcError) as e:
         dec.decode_iframe(f, hv.alloc_out(32, 32, chroma=False))
     assert e.value.status == hv.HIVC_E_INVALID
+
+
+def test_sor_tiling_choice_does_not_change_results(hv):
+    """The first intra frame of a new plane geometry times both SOR region
+    widths on real sweeps of its solve; later frames use the faster one.
+    Both widths perform the same global red-black sweeps, so a frame decoded
+    while tuning and one decoded after it are bit-identical."""
+    W, H = 1000, 610  # a geometry no other test uses
+    _, ifr = make_iframe_only(17, W, H, 0.02, chroma=True)
+    got = []
+    for _ in range(2):
+        dec = hv.Decoder(W, H, chroma=True, iframe_tol=1e-9)
+        out = hv.alloc_out(W, H)
+        dec.decode_iframe(hv.device_iframe(ifr), out)
+        st = dec.sync()
+        got.append(([to_np(dec.reference(p)) for p in range(3)], st.sweeps))
+    assert got[0][1] == got[1][1]
+    for a, b in zip(got[0][0], got[1][0]):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_inter_frames_in_a_cuda_graph(hv, batched):
+    """An inter frame's launches (coefficients, then the fused kernel; or the
+    batch path's block launches and pixel kernels) can be captured in a CUDA
+    graph on the decoder's stream: replaying the graph decodes the frame
+    exactly as a direct call, and decoding goes on from its result."""
+    torch = torch_cuda()
+    W, H = 160, 96
+    gop = make_gop(23, W, H, n_frames=4)
+    frames = [hv.device_pframe(p) for p in gop.pframes]
+    ref_dec = hv.Decoder(W, H, chroma=True)
+    o = hv.alloc_out(W, H)
+    ref_dec.decode_iframe(hv.device_iframe(gop.iframe), o)
+    want = []
+    for f in frames:
+        ref_dec.decode_pframe(f, o)
+        ref_dec.sync()
+        want.append([to_np(p).copy() for p in o])
+    s = torch.cuda.Stream()
+    dec = hv.Decoder(W, H, chroma=True, stream=s)
+    out = hv.alloc_out(W, H)
+    dec.decode_iframe(hv.device_iframe(gop.iframe), out)
+    run = (lambda f: hv.decode_batch([dec], [("p", f)], [out])) if batched else (lambda f: dec.decode_pframe(f, out))
+    run(frames[0])  # first call: lazy per-device setup and the batch pool happen outside the capture
+    dec.sync()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        run(frames[1])
+    g.replay()
+    dec.sync()
+    for p in range(3):
+        assert np.array_equal(to_np(out[p]), want[1][p]), p
+    run(frames[2])
+    dec.sync()
+    for p in range(3):
+        assert np.array_equal(to_np(out[p]), want[2][p]), p
