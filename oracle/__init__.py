@@ -69,6 +69,15 @@ def lib():
             L.oracle_block_solve.restype = c_int
             L.oracle_block_residual.argtypes = [c_int, c_int, c_int, u32p, u8p, i16p, dp]
             L.oracle_block_residual.restype = c_int
+            L.oracle_green_matrix_op.argtypes = [c_int, c_int, c_int, dp]
+            L.oracle_green_matrix_op.restype = None
+            L.oracle_block_residual_op.argtypes = [c_int, c_int, c_int, c_int, u32p, u8p, i16p, dp]
+            L.oracle_block_residual_op.restype = c_int
+            L.oracle_dequantise.argtypes = [c_int, c_double, c_double]
+            L.oracle_dequantise.restype = c_double
+            L.oracle_block_residual_coef.argtypes = [c_int, c_int, c_int, c_int, u32p, u8p,
+                                                     ctypes.POINTER(ctypes.c_int8), f32p, c_double, c_double, dp]
+            L.oracle_block_residual_coef.restype = c_int
             _lib = L
     return _lib
 
@@ -131,10 +140,11 @@ def block_eigenvalue(w: int, h: int, p: int, q: int) -> float:
     return lib().oracle_block_eigenvalue(w, h, p, q)
 
 
-def green_matrix(w: int, h: int) -> np.ndarray:
-    """Green's matrix of A = -L on a w x h block (pixel index y*w + x)."""
+def green_matrix(w: int, h: int, op: int = 0) -> np.ndarray:
+    """Green's matrix on a w x h block (pixel index y*w + x) of the harmonic
+    operator A = -L (op 0) or the biharmonic A = L^2 (op 1)."""
     G = np.empty((w * h, w * h), np.float64)
-    lib().oracle_green_matrix(w, h, _p(G, ctypes.c_double))
+    lib().oracle_green_matrix_op(w, h, op, _p(G, ctypes.c_double))
     return G
 
 
@@ -156,8 +166,9 @@ def block_solve(w: int, h: int, pos, v, G: Optional[np.ndarray] = None):
     return r.reshape(h, w), c[:K], a.value
 
 
-def block_residual(res) -> np.ndarray:
-    """Residual plane (float64 [H, W]) from a :class:`workload.Residual`."""
+def block_residual(res, op: int = 0) -> np.ndarray:
+    """Residual plane (float64 [H, W]) from a :class:`workload.Residual`
+    (values at the points; the decoder solves Eq. 2 per block)."""
     r = np.empty((res.height, res.width), np.float64)
     bp = np.ascontiguousarray(res.block_ptr, np.uint32)
     pos = np.ascontiguousarray(res.pos, np.uint8)
@@ -165,11 +176,35 @@ def block_residual(res) -> np.ndarray:
     if pos.size == 0:
         pos = np.zeros(1, np.uint8)
         val = np.zeros(1, np.int16)
-    st = lib().oracle_block_residual(res.width, res.height, res.block, _p(bp, ctypes.c_uint32),
-                                     _p(pos, ctypes.c_uint8), _p(val, ctypes.c_int16),
-                                     _p(r, ctypes.c_double))
+    st = lib().oracle_block_residual_op(res.width, res.height, res.block, op, _p(bp, ctypes.c_uint32),
+                                        _p(pos, ctypes.c_uint8), _p(val, ctypes.c_int16),
+                                        _p(r, ctypes.c_double))
     if st != OK:
         raise ValueError(f"oracle_block_residual status {st}")
+    return r
+
+
+def dequantise(q: int, step: float, offset: float) -> float:
+    """Dead-zone reconstruction of one coefficient index (Sec. 2.3)."""
+    return lib().oracle_dequantise(int(q), float(step), float(offset))
+
+
+def block_residual_coef(res, op: int = 0) -> np.ndarray:
+    """Residual plane (float64 [H, W]) from a :class:`workload.CoefResidual`
+    (coefficient mode: dequantised c and the constant a per block, Eq. 3)."""
+    r = np.empty((res.height, res.width), np.float64)
+    bp = np.ascontiguousarray(res.block_ptr, np.uint32)
+    pos = np.ascontiguousarray(res.pos, np.uint8)
+    q = np.ascontiguousarray(res.q, np.int8)
+    a = np.ascontiguousarray(res.a, np.float32)
+    if pos.size == 0:
+        pos = np.zeros(1, np.uint8)
+        q = np.zeros(1, np.int8)
+    st = lib().oracle_block_residual_coef(res.width, res.height, res.block, op, _p(bp, ctypes.c_uint32),
+                                          _p(pos, ctypes.c_uint8), _p(q, ctypes.c_int8), _p(a, ctypes.c_float),
+                                          float(res.step), float(res.offset), _p(r, ctypes.c_double))
+    if st != OK:
+        raise ValueError(f"oracle_block_residual_coef status {st}")
     return r
 
 
@@ -193,9 +228,10 @@ class OracleDecoder:
     kept unrounded (clamped float64) as the inter-frame reference."""
 
     def __init__(self, width: int, height: int, chroma: bool, block: int = 16,
-                 iframe_tol: float = 1e-12):
+                 iframe_tol: float = 1e-12, op: int = 0):
         self.width, self.height, self.chroma, self.block = width, height, chroma, block
         self.iframe_tol = iframe_tol
+        self.op = op
         self.ref: Optional[List[np.ndarray]] = None
         self.last_inpaint: List[Tuple[float, int]] = []
 
@@ -223,23 +259,42 @@ class OracleDecoder:
             preds += [warp(self.ref[1], cf), warp(self.ref[2], cf)]
         return self._correct(preds, pfr.res)
 
-    def _correct(self, preds, residuals):
+    def decode_pframe_coef(self, pfr):
+        """Inter frame whose residual comes in coefficient mode
+        (:class:`workload.PFrameCoef`)."""
+        if self.ref is None:
+            raise RuntimeError("inter frame before any intra frame")
+        sizes = plane_sizes(self.width, self.height, self.chroma)
+        preds = [warp(self.ref[0], pfr.flow)]
+        if self.chroma:
+            cf = chroma_flow(pfr.flow, sizes[1][0], sizes[1][1])
+            preds += [warp(self.ref[1], cf), warp(self.ref[2], cf)]
+        return self._correct(preds, pfr.res, coef=True)
+
+    def _correct(self, preds, residuals, coef: bool = False):
         recon = []
         for k, p in enumerate(preds):
-            r = block_residual(residuals[k]) if residuals is not None else 0.0
+            if residuals is None:
+                r = 0.0
+            elif coef:
+                r = block_residual_coef(residuals[k], self.op)
+            else:
+                r = block_residual(residuals[k], self.op)
             recon.append(np.clip(p + r, 0.0, 255.0))
         self.ref = recon
         return recon, [to_uint8(x) for x in recon]
 
 
-def decode_gop(gop, n_frames: Optional[int] = None, iframe_tol: float = 1e-12):
-    """Decode the first ``n_frames`` frames of a :class:`workload.Gop`.
-    Returns the list of (recon float64 planes, uint8 planes) per frame."""
-    dec = OracleDecoder(gop.width, gop.height, gop.chroma, gop.block, iframe_tol)
+def decode_gop(gop, n_frames: Optional[int] = None, iframe_tol: float = 1e-12, op: int = 0):
+    """Decode the first ``n_frames`` frames of a :class:`workload.Gop`
+    (inter frames in values or coefficient mode).  Returns the list of
+    (recon float64 planes, uint8 planes) per frame."""
+    dec = OracleDecoder(gop.width, gop.height, gop.chroma, gop.block, iframe_tol, op=op)
     n = gop.n_frames if n_frames is None else n_frames
     out = [dec.decode_iframe(gop.iframe)]
     for t in range(1, n):
-        out.append(dec.decode_pframe(gop.pframes[t - 1]))
+        pf = gop.pframes[t - 1]
+        out.append(dec.decode_pframe_coef(pf) if hasattr(pf.res[0], "q") else dec.decode_pframe(pf))
     return out
 
 

@@ -243,8 +243,15 @@ double oracle_block_eigenvalue(int w, int h, int p, int q)
     return 4.0 * sp * sp + 4.0 * sq * sq;
 }
 
-/* G (N x N, N = w*h, pixel index y*w + x) from the eigen-expansion. */
-void oracle_green_matrix(int w, int h, double *G)
+/*
+ * G (N x N, N = w*h, pixel index y*w + x) from the eigen-expansion, for the
+ * operator op (Sec. 2.2: the operator is defined by the eigenvalues of its
+ * Green's functions and can be replaced):
+ *   op 0: harmonic,    A = -L,     eigenvalues mu_pq,   G = sum phi phi^T / mu;
+ *   op 1: biharmonic,  A = L^2,    eigenvalues mu_pq^2, G = sum phi phi^T / mu^2.
+ * Both operators share the DCT-II eigenvectors and the constant null space.
+ */
+void oracle_green_matrix_op(int w, int h, int op, double *G)
 {
     const int N = w * h;
     double *phi = (double *)malloc((size_t)N * sizeof(double));
@@ -252,7 +259,8 @@ void oracle_green_matrix(int w, int h, double *G)
     for (int q = 0; q < h; ++q)
         for (int p = 0; p < w; ++p) {
             if (p == 0 && q == 0) continue; /* null space of A: constants */
-            double inv_mu = 1.0 / oracle_block_eigenvalue(w, h, p, q);
+            const double mu = oracle_block_eigenvalue(w, h, p, q);
+            double inv_mu = op == 1 ? 1.0 / (mu * mu) : 1.0 / mu;
             for (int y = 0; y < h; ++y)
                 for (int x = 0; x < w; ++x)
                     phi[y * w + x] = dct2_basis(w, p, x) * dct2_basis(h, q, y);
@@ -263,6 +271,9 @@ void oracle_green_matrix(int w, int h, double *G)
         }
     free(phi);
 }
+
+/* The harmonic Green's matrix (op 0). */
+void oracle_green_matrix(int w, int h, double *G) { oracle_green_matrix_op(w, h, 0, G); }
 
 /* Dense LU with partial pivoting; solves S z = b in place (n x n, row-major).
    Returns 0, or -1 when a pivot is exactly zero. */
@@ -357,8 +368,8 @@ int oracle_block_solve(int w, int h, const double *G, int K, const uint8_t *pos,
  * block_ptr has nbx*nby + 1 entries; pos/val as in oracle_block_solve.
  * r is W x H.  Returns ORACLE_OK or ORACLE_INVALID (any bad block).
  */
-int oracle_block_residual(int W, int H, int B, const uint32_t *block_ptr,
-                          const uint8_t *pos, const int16_t *val, double *r)
+int oracle_block_residual_op(int W, int H, int B, int op, const uint32_t *block_ptr,
+                             const uint8_t *pos, const int16_t *val, double *r)
 {
     if (W < 1 || H < 1 || B < 1 || B > 16) return ORACLE_INVALID;
     const int nbx = (W + B - 1) / B, nby = (H + B - 1) / B;
@@ -382,7 +393,7 @@ int oracle_block_residual(int W, int H, int B, const uint32_t *block_ptr,
                 if (shape_w[s] == w && shape_h[s] == h) G = shape_G[s];
             if (!G && K > 0) {
                 G = (double *)malloc((size_t)w * h * w * h * sizeof(double));
-                oracle_green_matrix(w, h, G);
+                oracle_green_matrix_op(w, h, op, G);
                 shape_w[n_shapes] = w; shape_h[n_shapes] = h; shape_G[n_shapes] = G;
                 ++n_shapes;
             }
@@ -397,5 +408,76 @@ int oracle_block_residual(int W, int H, int B, const uint32_t *block_ptr,
         }
     for (int s = 0; s < n_shapes; ++s) free(shape_G[s]);
     free(rb); free(vb);
+    return status;
+}
+
+/* The harmonic residual plane (op 0). */
+int oracle_block_residual(int W, int H, int B, const uint32_t *block_ptr,
+                          const uint8_t *pos, const int16_t *val, double *r)
+{
+    return oracle_block_residual_op(W, H, B, 0, block_ptr, pos, val, r);
+}
+
+/*
+ * Coefficient mode (Sec. 2.2, 2.3): the decoder receives, per block, the
+ * Green's coefficients of its points and the constant, and evaluates
+ *     r = G[:, P] c + a                                   (Eq. 3)
+ * without solving anything.  The coefficients arrive dead-zone quantised to
+ * indices q in [-127, 127] (Sec. 2.3).  Reading (the mapping's scale is not
+ * given): one quantiser step Delta per plane and a reconstruction offset
+ * delta in [0, 1), as in the usual dead-zone scalar quantiser:
+ *     c = 0 for q = 0,   c = sign(q) (|q| + delta) Delta  otherwise,
+ * so that zero coefficients reconstruct as zero.  K = 0 gives r = a.
+ * q = -128 is invalid.  pos as in oracle_block_solve (K <= w*h - 1).
+ */
+double oracle_dequantise(int q, double step, double offset)
+{
+    if (q == 0) return 0.0;
+    const double m = (fabs((double)q) + offset) * step;
+    return q < 0 ? -m : m;
+}
+
+int oracle_block_residual_coef(int W, int H, int B, int op, const uint32_t *block_ptr,
+                               const uint8_t *pos, const int8_t *q, const float *a,
+                               double step, double offset, double *r)
+{
+    if (W < 1 || H < 1 || B < 1 || B > 16) return ORACLE_INVALID;
+    const int nbx = (W + B - 1) / B, nby = (H + B - 1) / B;
+    int shape_w[4], shape_h[4], n_shapes = 0;
+    double *shape_G[4] = {0, 0, 0, 0};
+    int status = ORACLE_OK;
+    if (block_ptr[0] != 0) status = ORACLE_INVALID;
+    for (int by = 0; by < nby && status == ORACLE_OK; ++by)
+        for (int bx = 0; bx < nbx && status == ORACLE_OK; ++bx) {
+            const int b = by * nbx + bx;
+            const int w = (W - bx * B) < B ? (W - bx * B) : B;
+            const int h = (H - by * B) < B ? (H - by * B) : B;
+            const int N = w * h;
+            if (block_ptr[b + 1] < block_ptr[b]) { status = ORACLE_INVALID; break; }
+            const int K = (int)(block_ptr[b + 1] - block_ptr[b]);
+            const uint8_t *pb = pos + block_ptr[b];
+            const int8_t *qb = q + block_ptr[b];
+            if (K > N - 1) { status = ORACLE_INVALID; break; }
+            for (int j = 0; j < K; ++j)
+                if (pb[j] >= N || (j > 0 && pb[j] <= pb[j - 1]) || qb[j] == -128) status = ORACLE_INVALID;
+            if (status != ORACLE_OK) break;
+            double *G = NULL;
+            for (int s = 0; s < n_shapes; ++s)
+                if (shape_w[s] == w && shape_h[s] == h) G = shape_G[s];
+            if (!G && K > 0) {
+                G = (double *)malloc((size_t)N * N * sizeof(double));
+                oracle_green_matrix_op(w, h, op, G);
+                shape_w[n_shapes] = w; shape_h[n_shapes] = h; shape_G[n_shapes] = G;
+                ++n_shapes;
+            }
+            for (int y = 0; y < h; ++y)
+                for (int x = 0; x < w; ++x) {
+                    const int i = y * w + x;
+                    double s = a[b];
+                    for (int j = 0; j < K; ++j) s += oracle_dequantise(qb[j], step, offset) * G[(size_t)i * N + pb[j]];
+                    r[(size_t)(by * B + y) * W + bx * B + x] = s;
+                }
+        }
+    for (int s = 0; s < n_shapes; ++s) free(shape_G[s]);
     return status;
 }

@@ -7,11 +7,15 @@ Both the CPU oracle and the CUDA path consume exactly these arrays.
 """
 from .synth import (  # noqa: F401
     Residual,
+    CoefResidual,
     IFrame,
     PFrame,
+    PFrameCoef,
     Gop,
     block_grid,
     make_residual,
+    make_coef_residual,
+    coef_frame_residuals,
     make_config1,
     make_gop,
     make_iframe_only,

@@ -56,6 +56,32 @@ class Residual:
 
 
 @dataclass
+class CoefResidual:
+    """Block residual of one plane in coefficient mode (Sec. 2.2, 2.3): per
+    point a dead-zone quantisation index ``q`` in [-127, 127] of its Green's
+    coefficient, per block the constant ``a``; the plane's quantiser step
+    and reconstruction offset.  Blocks and positions as in :class:`Residual`."""
+
+    width: int
+    height: int
+    block: int
+    block_ptr: np.ndarray  # uint32 [n_blocks + 1]
+    pos: np.ndarray  # uint8  [n_points]
+    q: np.ndarray  # int8   [n_points]
+    a: np.ndarray  # float32 [n_blocks]
+    step: float = 1.0
+    offset: float = 0.5
+
+    @property
+    def n_blocks(self) -> int:
+        return int(self.block_ptr.shape[0] - 1)
+
+    @property
+    def n_points(self) -> int:
+        return int(self.pos.shape[0])
+
+
+@dataclass
 class IFrame:
     width: int
     height: int
@@ -72,6 +98,12 @@ class IFrame:
 class PFrame:
     flow: np.ndarray  # float32 [H, W, 2], (dx, dy): pred(x) = ref(x + flow(x))
     res: List[Residual]  # one per plane
+
+
+@dataclass
+class PFrameCoef:
+    flow: np.ndarray  # float32 [H, W, 2]
+    res: List[CoefResidual]  # one per plane
 
 
 @dataclass
@@ -220,6 +252,54 @@ def make_residual(
     np.cumsum(k, out=bp[1:])
     val = rng.integers(-vmax, vmax + 1, size=int(bp[-1])).astype(np.int16)
     return Residual(width, height, block, bp, pos_parts.astype(np.uint8), val)
+
+
+def make_coef_residual(
+    rng: np.random.Generator,
+    width: int,
+    height: int,
+    block: int,
+    lam: float,
+    qmax: int = 127,
+    zero_frac: float = 0.4,
+    amax: float = 8.0,
+    step: float = 1.0,
+    offset: float = 0.5,
+    kmax: Optional[int] = None,
+    positions_from: Optional[CoefResidual] = None,
+) -> CoefResidual:
+    """Random coefficient-mode residual: positions as :func:`make_residual`
+    (K ~ Poisson(lam), clipped), indices uniform in [-qmax, qmax] with a
+    ``zero_frac`` share of zeros (the dead zone's mass), constants uniform in
+    [-amax, amax].  ``positions_from`` reuses another plane's layout."""
+    if positions_from is not None:
+        bp = positions_from.block_ptr.copy()
+        pos = positions_from.pos.copy()
+    else:
+        nbx, nby, w, h = block_grid(width, height, block)
+        cap = w * h - 1
+        if kmax is not None:
+            cap = np.minimum(cap, kmax)
+        k = np.minimum(rng.poisson(lam, size=nbx * nby), cap).astype(np.int64)
+        pos = _positions_from_counts(rng, w, h, block, k).astype(np.uint8)
+        bp = np.zeros(nbx * nby + 1, np.uint32)
+        np.cumsum(k, out=bp[1:])
+    n = int(pos.shape[0])
+    q = rng.integers(-qmax, qmax + 1, size=n)
+    q[rng.random(n) < zero_frac] = 0
+    a = rng.uniform(-amax, amax, size=bp.shape[0] - 1).astype(np.float32)
+    return CoefResidual(width, height, block, bp, pos, q.astype(np.int8), a, float(step), float(offset))
+
+
+def coef_frame_residuals(rng, width, height, chroma, block, lam_y=8.0, lam_c=4.0, **kw) -> List[CoefResidual]:
+    """Coefficient-mode residuals of one frame; Cr shares the Cb layout."""
+    ry = make_coef_residual(rng, width, height, block, lam_y, **kw)
+    if not chroma:
+        return [ry]
+    cw, ch = chroma_size(width, height)
+    rcb = make_coef_residual(rng, cw, ch, block, lam_c, **kw)
+    rcr = make_coef_residual(rng, cw, ch, block, lam_c, positions_from=rcb, **kw)
+    return [ry, rcb, rcr]
 
 
 def empty_residual(width: int, height: int, block: int) -> Residual:
@@ -385,10 +465,14 @@ def make_gop(
     max_shift: float = 3.0,
     max_rot_deg: float = 0.2,
     residual_kw: Optional[dict] = None,
+    coef_mode: bool = False,
+    coef_kw: Optional[dict] = None,
 ) -> Gop:
     """A GOP of one intra frame and ``n_frames - 1`` inter frames of a moving
     synthetic scene (FullHD 4:2:0 by default).  The flow of inter frame t is
-    the exact backward displacement from frame t to frame t-1."""
+    the exact backward displacement from frame t to frame t-1.  With
+    ``coef_mode`` the inter frames carry coefficient-mode residuals
+    (:class:`PFrameCoef`)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     planes = _scene_planes(rng, width, height, chroma)
     center = (width / 2.0, height / 2.0)
@@ -421,7 +505,11 @@ def make_gop(
         qx = cp * px + sp * py + cx
         qy = -sp * px + cp * py + cy
         flow = np.stack([qx - xs, qy - ys], axis=-1).astype(np.float32)
-        pframes.append(PFrame(flow, _frame_residuals(rng, width, height, chroma, block, **rkw)))
+        if coef_mode:
+            res = coef_frame_residuals(rng, width, height, chroma, block, lam_y=lam_y, lam_c=lam_c, **(coef_kw or {}))
+            pframes.append(PFrameCoef(flow, res))
+        else:
+            pframes.append(PFrame(flow, _frame_residuals(rng, width, height, chroma, block, **rkw)))
         if with_sources:
             sources.append(render_frame(t))
     return Gop(width, height, chroma, block, ifr, pframes, sources)
