@@ -54,7 +54,10 @@ typedef struct {
     int32_t chroma;         /* 0 = grey (Y only), 1 = YCbCr 4:2:0 */
     int32_t block;          /* residual block edge B, 1..16.  The paper uses
                                8 x 8 blocks (Sec. 2.2, 2.3); default 16 */
-    int32_t op;             /* residual operator: 0 = harmonic, -L (Sec. 2.3) */
+    int32_t op;             /* residual operator (Sec. 2.2: defined by the
+                               eigenvalues of its Green's functions):
+                               0 = harmonic, A = -L (Sec. 2.3; default),
+                               1 = biharmonic, A = L^2 (eigenvalues mu^2) */
     int32_t precision;      /* intra solve: 0 = FP32 sweeps with a residual
                                correction of an extended-precision iterate
                                (float-float, ~48-bit; default), 1 = FP32 only */
@@ -101,6 +104,26 @@ typedef struct {
     int32_t n_points;          /* entries in pos/val */
 } hivc_residual;
 
+/*
+ * Block residual of one plane in coefficient mode (Sec. 2.2, 2.3): the
+ * decoder receives, per point, the Green's coefficient c_j dead-zone
+ * quantised to an index q in [-127, 127], and per block the constant a, and
+ * only evaluates r = a + sum_j c_j G(., p_j) (Eq. 3; no solve, no overwrite
+ * at the points).  Dequantisation (the paper leaves the mapping's scale
+ * open): c = 0 for q = 0, c = sign(q) (|q| + offset) step otherwise.
+ * block_ptr/pos as in hivc_residual (K_b <= w*h - 1); K_b = 0 gives r = a.
+ * An index -128 makes its block zero and is reported as HIVC_E_INVALID.
+ */
+typedef struct {
+    const uint32_t *block_ptr; /* device */
+    const uint8_t *pos;        /* device */
+    const int8_t *q;           /* device, per point */
+    const float *a;            /* device, per block */
+    int32_t n_points;
+    float step;                /* quantiser step, > 0 */
+    float offset;              /* reconstruction offset, in [0, 1) */
+} hivc_coef_residual;
+
 /* Intra frame.  The two chroma planes share one mask (Sec. 2.3). */
 typedef struct {
     hivc_points y;
@@ -120,6 +143,12 @@ typedef struct {
                              may share block_ptr/pos: one factorisation
                              then serves both */
 } hivc_pframe;
+
+/* Inter frame with its residual in coefficient mode. */
+typedef struct {
+    const float *flow;           /* device, height x width x 2 floats */
+    hivc_coef_residual res[3];   /* Y, Cb, Cr (only res[0] when grey) */
+} hivc_pframe_coef;
 
 /* uint8 output planes (device), rows pitch bytes apart. */
 typedef struct {
@@ -177,6 +206,11 @@ hivc_status hivc_decode_iframe(hivc_decoder *dec, const hivc_iframe *f, const hi
 /* Decode an inter frame (Sec. 2, 2.3: warp + residual) into out and make it
    the reference.  Asynchronous.  HIVC_E_NO_REFERENCE before any intra. */
 hivc_status hivc_decode_pframe(hivc_decoder *dec, const hivc_pframe *f, const hivc_out *out);
+
+/* Decode an inter frame whose residual comes in coefficient mode: one
+   evaluation launch for the three planes, then warp + residual + pack.
+   Asynchronous.  HIVC_E_NO_REFERENCE before any intra frame. */
+hivc_status hivc_decode_pframe_coef(hivc_decoder *dec, const hivc_pframe_coef *f, const hivc_out *out);
 
 /* Decode n frames, frame k on decoder decs[k] into outs[k].  Frames of one
    decoder are decoded in array order; each run of consecutive inter frames
@@ -237,6 +271,14 @@ hivc_status hivc_block_residual(int32_t width, int32_t height, int32_t block,
                                 const hivc_residual *res, float *r, int32_t r_pitch,
                                 void *workspace, size_t workspace_bytes, uint32_t *flags,
                                 void *stream);
+
+/* Residual plane of a coefficient-mode plane (see hivc_coef_residual) with
+   operator op (0 harmonic, 1 biharmonic) into r (device, r_pitch floats per
+   row), on stream (NULL = default).  Needs no workspace.  Data errors are
+   ORed into *flags (device word; NULL: not reported).  Asynchronous. */
+hivc_status hivc_block_residual_coef(int32_t width, int32_t height, int32_t block, int32_t op,
+                                     const hivc_coef_residual *res, float *r, int32_t r_pitch, uint32_t *flags,
+                                     void *stream);
 
 /* hivc_block_residual without allocation: the same residual plane, with
    the coefficient scratch taken from a fixed array inside the library

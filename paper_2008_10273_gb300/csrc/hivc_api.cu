@@ -85,7 +85,7 @@ constexpr int kStatusWords = 4;
 bool config_ok(const hivc_config *c)
 {
     return c && c->width >= 1 && c->height >= 1 && c->width <= 16384 && c->height <= 16384 &&
-           (c->chroma == 0 || c->chroma == 1) && c->block >= 1 && c->block <= kMaxB && c->op == 0 &&
+           (c->chroma == 0 || c->chroma == 1) && c->block >= 1 && c->block <= kMaxB && (c->op == 0 || c->op == 1) &&
            (c->precision == 0 || c->precision == 1) && c->iframe_tol >= 0.0 && c->max_cycles >= 1 &&
            c->cond_threshold >= 0.0;
 }
@@ -232,6 +232,7 @@ hivc_status make_block_jobs(hivc_decoder *d, const hivc_residual *res, BlockJobs
     if (!acoef) acoef = d->acoef;
     if (!rfield) rfield = d->rfield;
     J = BlockJobs{};
+    J.op = d->cfg.op;
     for (int p = 0; p < d->np; ++p)
         if ((int64_t)res[p].n_points > (int64_t)d->pg[p].w * d->pg[p].h) return HIVC_E_INVALID;
     int base = 0;
@@ -705,6 +706,7 @@ cudaError_t launch_fused_frame(hivc_decoder *d, const hivc_pframe *f, const hivc
     F.height = d->cfg.height;
     F.chroma = d->cfg.chroma;
     F.block = d->cfg.block;
+    F.op = d->cfg.op;
     F.early = early ? 1 : 0;
     // the TMA variant needs an even luma width (16-byte flow rows) and a
     // 16-byte aligned flow
@@ -814,6 +816,116 @@ hivc_status hivc_decode_pframe(hivc_decoder *d, const hivc_pframe *f, const hivc
 
 namespace {
 
+bool coef_residual_ok(const hivc_coef_residual &r, int w, int h)
+{
+    return r.block_ptr && r.n_points >= 0 && r.a && (r.n_points == 0 || (r.pos && r.q)) &&
+           (int64_t)r.n_points <= (int64_t)w * h && std::isfinite(r.step) && r.step > 0.f &&
+           std::isfinite(r.offset) && r.offset >= 0.f && r.offset < 1.f;
+}
+
+// A coefficient-mode plane as a block job (evaluation only).
+void coef_job(BlockPlane &B, const hivc_coef_residual &r, int w, int h, int block, float *rf, int pitch, int base)
+{
+    B = BlockPlane{};
+    B.block_ptr = r.block_ptr;
+    B.pos = r.pos;
+    B.q = r.q;
+    B.qstep = r.step;
+    B.qoff = r.offset;
+    B.acoef[0] = const_cast<float *>(r.a);
+    B.r[0] = rf;
+    B.r_pitch = pitch;
+    B.n_points = r.n_points;
+    B.width = w;
+    B.height = h;
+    B.block = block;
+    B.nbx = (w + block - 1) / block;
+    B.nblocks = B.nbx * ((h + block - 1) / block);
+    B.block_base = base;
+}
+
+}  // namespace
+
+hivc_status hivc_decode_pframe_coef(hivc_decoder *d, const hivc_pframe_coef *f, const hivc_out *out)
+{
+    if (!d || !f || !out_ok(d, out) || !f->flow) return HIVC_E_INVALID;
+    for (int p = 0; p < d->np; ++p)
+        if (!coef_residual_ok(f->res[p], d->pg[p].w, d->pg[p].h)) return HIVC_E_INVALID;
+    if (!d->has_ref) return HIVC_E_NO_REFERENCE;
+    if (cudaSetDevice(d->device) != cudaSuccess) return HIVC_E_CUDA;
+    BlockJobs J{};
+    J.op = d->cfg.op;
+    for (int p = 0; p < d->np; ++p) {
+        const PlaneGeom &g = d->pg[p];
+        coef_job(J.p[J.n++], f->res[p], g.w, g.h, d->cfg.block, d->rfield[p], g.pitch, J.total_blocks);
+        J.total_blocks += g.nblocks;
+    }
+    cudaError_t e;
+    {
+        Timed t(d, 5);
+        e = launch_block_eval(J, d->flags, d->stream);
+        t.done(1);
+    }
+    if (e != cudaSuccess) return HIVC_E_CUDA;
+    // warp + residual + pack: the staged kernel where its tensor maps can be
+    // made, else the plain one
+    hivc_pframe pf{};
+    pf.flow = f->flow;
+    const int nxt = d->cur ^ 1;
+    if (d->maps_ok && d->cfg.width % 2 == 0 &&
+        launch_rf_frame(d, &pf, out, d->rfield[0], d->rfield[1], d->rfield[2]) == cudaSuccess) {
+        // launched
+    } else {
+        cudaGetLastError();
+        WarpJobs W{};
+        W.n = d->np;
+        for (int p = 0; p < d->np; ++p) {
+            WarpPlane &P = W.p[p];
+            const PlaneGeom &g = d->pg[p];
+            P.ref = d->ref[d->cur][p];
+            P.ref_pitch = g.pitch;
+            P.flow = f->flow;
+            P.flow_w = d->pg[0].w;
+            P.flow_h = d->pg[0].h;
+            P.chroma_flow = p > 0 ? 1 : 0;
+            P.r = d->rfield[p];
+            P.r_pitch = g.pitch;
+            P.ref_out = d->ref[nxt][p];
+            P.ref_out_pitch = g.pitch;
+            P.out = out->plane[p];
+            P.out_pitch = out->pitch[p];
+            P.width = g.w;
+            P.height = g.h;
+        }
+        Timed t(d, 6);
+        e = launch_warp_add(W, d->stream);
+        t.done(1);
+        if (e != cudaSuccess) return HIVC_E_CUDA;
+    }
+    d->cur = nxt;
+    d->st.frames += 1;
+    return HIVC_OK;
+}
+
+hivc_status hivc_block_residual_coef(int32_t width, int32_t height, int32_t block, int32_t op,
+                                     const hivc_coef_residual *res, float *r, int32_t r_pitch, uint32_t *flags,
+                                     void *stream)
+{
+    if (!res || !r || width < 1 || height < 1 || block < 1 || block > kMaxB || r_pitch < width ||
+        (op != 0 && op != 1) || !coef_residual_ok(*res, width, height))
+        return HIVC_E_INVALID;
+    if (ensure_block_tables() != cudaSuccess) return HIVC_E_CUDA;
+    BlockJobs J{};
+    J.n = 1;
+    J.op = op;
+    coef_job(J.p[0], *res, width, height, block, r, r_pitch, 0);
+    J.total_blocks = J.p[0].nblocks;
+    const cudaError_t e = launch_block_eval(J, flags, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? HIVC_OK : HIVC_E_CUDA;
+}
+
+namespace {
+
 size_t a256(size_t b) { return (b + 255) / 256 * 256; }
 
 bool pframe_ok(const hivc_decoder *d, const hivc_pframe *f, const hivc_out *out)
@@ -906,6 +1018,7 @@ hivc_status decode_inter_run(hivc_decoder *d, const hivc_frame *frames, const hi
     const BlockScratch S{d->flags, reinterpret_cast<float *>(pool + big_off), ranges, d->flags + 1,
                          (float)d->cfg.cond_threshold};
     BlockJobs J{};
+    J.op = d->cfg.op;
     auto flush = [&]() -> cudaError_t {
         if (J.n == 0) return cudaSuccess;
         cudaError_t e;
@@ -921,6 +1034,7 @@ hivc_status decode_inter_run(hivc_decoder *d, const hivc_frame *frames, const hi
             t.done(1);
         }
         J = BlockJobs{};
+        J.op = d->cfg.op;
         return e;
     };
     for (size_t k = 0; k < nf; ++k) {

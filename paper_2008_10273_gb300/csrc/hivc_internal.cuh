@@ -14,6 +14,7 @@ namespace hivc {
 constexpr int kMaxB = 16;   // largest residual block edge
 constexpr int kWarpK = 32;  // blocks with K <= kWarpK are solved by one warp
 constexpr int kMaxJobs = 16;
+constexpr int kNumOps = 2;  // residual operators: 0 harmonic (A = -L), 1 biharmonic (A = L^2)
 
 // Error bits the kernels OR into a device status word (never trap).
 enum : uint32_t {
@@ -26,6 +27,7 @@ enum : uint32_t {
     kFlagCond = 1u << 6,      // information, not an error: a block above the
                               // condition threshold kept its FP32 solution
                               // (K > kF64MaxK: no room for the FP64 system)
+    kFlagQ = 1u << 7,         // coefficient index -128 (outside [-127, 127])
 };
 
 // ---------------------------------------------------------------------------
@@ -43,12 +45,18 @@ struct BlockPlane {
     float *r[2];      // residual field (eval stage), may be nullptr
     int32_t r_pitch;  // floats
     int32_t n_points, width, height, block, nbx, nblocks, block_base;
+    // coefficient mode (evaluation only): per point the dead-zone index of c
+    // (val unused), acoef[0] the transmitted constants; c = sign(q)(|q| +
+    // qoff) qstep, 0 for q = 0
+    const int8_t *q;
+    float qstep, qoff;
 };
 
 struct BlockJobs {
     BlockPlane p[kMaxJobs];
     int32_t n;
     int32_t total_blocks;
+    int32_t op;  // residual operator of every job
 };
 
 // Device addresses of the Green's matrices of all block shapes (uploaded
@@ -58,6 +66,7 @@ struct BlockTables {
     const double *G64;  // the same in double precision (FP64 re-solves)
     const int *goff;    // offset of shape (w, h) at (w-1)*16 + (h-1)
     int sms;
+    float amax;         // bound on the operator's eigenvalues (8, or 64 for L^2)
 };
 
 constexpr int kBigMaxK = 255;  // largest K of a 16 x 16 block
@@ -88,13 +97,15 @@ struct BlockScratch {
 };
 
 cudaError_t ensure_block_tables();
-const BlockTables &block_tables();  // of the current device
+const BlockTables &block_tables(int op = 0);  // of the current device, for operator op
 
 // c, a for every block (a = NaN: bad positions): one thread per block for
 // K <= 12, warps for K <= 32, a whole CTA for K > 32.  One launch, no
 // counters: the kernel's completion publishes every result.
 cudaError_t launch_block_coef(const BlockJobs &jobs, const BlockScratch &s, cudaStream_t st, int *launches);
-// r-field from c, a (Eq. 3 by Green's rows), r = v at the points.
+// r-field from c, a (Eq. 3 by Green's rows), r = v at the points; or, for
+// jobs in coefficient mode (p[k].q set, all jobs alike), from the
+// dequantised indices and the transmitted constants, with no overwrite.
 cudaError_t launch_block_eval(const BlockJobs &jobs, uint32_t *flags, cudaStream_t st);
 
 // One inter frame for the fused kernel: residual blocks, flow, references.
@@ -106,7 +117,7 @@ struct FusedFrame {
     float *ref_out[3];
     uint8_t *out[3];
     int32_t ref_pitch[3], out_pitch[3];  // ref_out shares ref_pitch
-    int32_t width, height, chroma, block;
+    int32_t width, height, chroma, block, op;
     int32_t early;      // 1: the references are complete at launch (copies may start at once)
     int32_t nmbx, nmb;  // filled by the launcher
     // residual-field variant: the evaluated residual planes (pitch floats)

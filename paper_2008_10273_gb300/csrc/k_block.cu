@@ -35,15 +35,19 @@ namespace {
 
 constexpr int kGSize = 2283904;  // sum over shapes of N * rowlen(N)
 
-static __device__ __align__(256) float d_G[kGSize];
-static __device__ __align__(256) double d_G64[kGSize];
+// one table per operator (0 harmonic, 1 biharmonic)
+static __device__ __align__(256) float d_G[kNumOps * kGSize];
+static __device__ __align__(256) double d_G64[kNumOps * kGSize];
 static __device__ int d_goff[256];
 
 std::mutex g_tab_mu;
-BlockTables g_tabs[64];
+BlockTables g_tabs[64][kNumOps];
 uint64_t g_tab_devices = 0;  // bit d: tables uploaded to device d
 
-void build_tables(std::vector<float> &G, std::vector<double> &G64, std::vector<int> &goff)
+// Tables of operator op: the Green's eigenvalues are 1/mu (harmonic) or
+// 1/mu^2 (biharmonic, A = L^2); the eigenvectors, and with them the
+// Toeplitz-plus-Hankel structure, are the same.
+void build_tables(int op, std::vector<float> &G, std::vector<double> &G64, std::vector<int> &goff)
 {
     const double pi = 3.14159265358979323846;
     G.assign(kGSize, 0.f);
@@ -69,7 +73,8 @@ void build_tables(std::vector<float> &G, std::vector<double> &G64, std::vector<i
                         for (int p = 0; p < w; ++p) {
                             if (p == 0 && q == 0) continue;
                             const double sp = std::sin(pi * p / (2.0 * w)), sq = std::sin(pi * q / (2.0 * h));
-                            s += cw[a * w + p] * chq[b * h + q] / (4.0 * sp * sp + 4.0 * sq * sq);
+                            const double mu = 4.0 * sp * sp + 4.0 * sq * sq;
+                            s += cw[a * w + p] * chq[b * h + q] / (op == 1 ? mu * mu : mu);
                         }
                     T[b * 2 * w + a] = 0.25 * s;
                 }
@@ -127,8 +132,12 @@ __device__ __forceinline__ void note_kappa(const BlockScratch &S, float kappa)
     if (S.cstat && kappa > 0.f) atomicMax(S.cstat, __float_as_uint(kappa));
 }
 
-// kappa = 8 tr(G_PP) / (1 - K/N) >= cond_2(G_PP)
-__device__ __forceinline__ float cond_bound(float tr, int K, int N) { return 8.f * tr / (1.f - (float)K / (float)N); }
+// kappa = amax tr(G_PP) / (1 - K/N) >= cond_2(G_PP), amax >= the largest
+// eigenvalue of the operator (8 harmonic, 64 biharmonic)
+__device__ __forceinline__ float cond_bound(float amax, float tr, int K, int N)
+{
+    return amax * tr / (1.f - (float)K / (float)N);
+}
 
 // validity of the positions of a segment's block (inside, increasing):
 // returns K, or 0 (and a flag) when any is bad
@@ -191,7 +200,7 @@ __device__ __forceinline__ void seg_run(const SegBlock &b, int K, int i, float *
             P->acoef[0][b.g.lb] = a0;
             if (two) P->acoef[1][b.g.lb] = a1;
             if (!spd) atomicOr(S.flags, kFlagNotSPD);
-            const float kappa = cond_bound(tr, K, b.g.w * b.g.h);
+            const float kappa = cond_bound(tab.amax, tr, K, b.g.w * b.g.h);
             note_kappa(S, kappa);
             if (kappa > S.tau) s_list[atomicAdd(s_n, 1)] = gb | kF64Bit;
         }
@@ -322,7 +331,7 @@ __device__ __forceinline__ float thread_run(const BlockPlane &P, const BlockGeom
     P.acoef[0][g.lb] = a0;
     if (TWO) P.acoef[1][g.lb] = a1;
     if (!spd) atomicOr(S.flags, kFlagNotSPD);
-    return cond_bound(tr, K, N);
+    return cond_bound(tab.amax, tr, K, N);
 }
 
 // ---- CTA solves: K > 32, and FP64 re-solves of blocks above the condition
@@ -460,7 +469,7 @@ __device__ __noinline__ void cta_block(const BlockJobs &J, const BlockTables &ta
     if (!f64) {
         float d = 0.f;
         for (int i = tid; i < K; i += kCoefThreads) d += __ldg(tab.G + off + s_p[i] * rl + s_p[i]);
-        const float kappa = cond_bound(cta_sum(d, redf), K, N);
+        const float kappa = cond_bound(tab.amax, cta_sum(d, redf), K, N);
         if (tid == 0) note_kappa(S, kappa);
         f64 = kappa > S.tau;
     }
@@ -589,7 +598,10 @@ __global__ void __launch_bounds__(kCoefThreads, 3) block_coef_kernel(const __gri
 // their products are summed.  The constant a is loaded beside the block
 // pointers.  A 16-wide block row goes out as two 16-byte stores per lane;
 // then the data at the points, exactly.  Bad positions give a zero block.
-template <bool TWO>
+// QC (coefficient mode): c_j from the dead-zone indices, a transmitted, no
+// overwrite at the points; K = 0 gives r = a.  An index -128 gives a zero
+// block and the flag kFlagQ.
+template <bool TWO, bool QC>
 __device__ __forceinline__ void eval_block(const BlockPlane &P, const BlockGeom &g, const float *__restrict__ G,
                                            float a0, float a1, float *R0, float *R1, int pitch, int lane,
                                            uint32_t *flags)
@@ -603,22 +615,34 @@ __device__ __forceinline__ void eval_block(const BlockPlane &P, const BlockGeom 
         r0[t] = a0;
         r1[t] = a1;
     }
-    bool valid = K > 0;
+    bool valid = QC || K > 0, badq = false;
     int prev = -1;
     for (int j0 = 0; j0 < K; j0 += 32) {
         const int j = j0 + lane;
         int p = 0;
         float c0 = 0.f, c1 = 0.f;
+        bool qb = false;
         if (j < K) {
             p = __ldg(P.pos + g.s + j);
-            c0 = __ldg(P.coef[0] + g.s + j);
-            if (TWO) c1 = __ldg(P.coef[1] + g.s + j);
+            if (QC) {
+                const int qi = __ldg(P.q + g.s + j);
+                qb = qi == -128;
+                const float qf = (float)qi;
+                c0 = qi == 0 ? 0.f : copysignf((fabsf(qf) + P.qoff) * P.qstep, qf);
+            } else {
+                c0 = __ldg(P.coef[0] + g.s + j);
+                if (TWO) c1 = __ldg(P.coef[1] + g.s + j);
+            }
         }
         // inside the block and increasing (the previous chunk's last point
         // for lane 0)
         const int up = __shfl_up_sync(0xffffffffu, p, 1);  // every lane takes part
         const int before = lane == 0 ? prev : up;
         if (__any_sync(0xffffffffu, j < K && (p >= N || p <= before))) valid = false;
+        if (QC && __any_sync(0xffffffffu, qb)) {
+            valid = false;
+            badq = true;
+        }
         prev = __shfl_sync(0xffffffffu, p, 31);
         if (!valid) break;
         const int n = min(32, K - j0);
@@ -641,7 +665,7 @@ __device__ __forceinline__ void eval_block(const BlockPlane &P, const BlockGeom 
         }
     }
     if (!valid) {
-        if (K > 0 && lane == 0) atomicOr(flags, kFlagPos);
+        if (K > 0 && lane == 0 && flags) atomicOr(flags, badq ? kFlagQ : kFlagPos);
 #pragma unroll
         for (int t = 0; t < 8; ++t) r0[t] = r1[t] = 0.f;
     }
@@ -673,7 +697,7 @@ __device__ __forceinline__ void eval_block(const BlockPlane &P, const BlockGeom 
             }
         }
     }
-    if (!valid) return;
+    if (QC || !valid) return;
     __syncwarp();
     // the data at the points, exactly
     const float rw = __frcp_rn((float)w);
@@ -685,6 +709,7 @@ __device__ __forceinline__ void eval_block(const BlockPlane &P, const BlockGeom 
     }
 }
 
+template <bool QC>
 __global__ void __launch_bounds__(128, 8) block_eval_kernel(const __grid_constant__ BlockJobs J, BlockTables tab,
                                                             uint32_t *flags)
 {
@@ -701,8 +726,13 @@ __global__ void __launch_bounds__(128, 8) block_eval_kernel(const __grid_constan
     float *R0 = P.r[0] + (size_t)g.y0 * pitch + g.x0;
     float *R1 = two && P.r[1] ? P.r[1] + (size_t)g.y0 * pitch + g.x0 : nullptr;
     const float *G = green_rows(tab, g.w, g.h);
-    if (two) eval_block<true>(P, g, G, a0, a1, R0, R1, pitch, lane, flags);
-    else eval_block<false>(P, g, G, a0, a1, R0, R1, pitch, lane, flags);
+    if (QC) {
+        // no coefficient stage ran: block pointer errors are reported here
+        // (the block reconstructs as zero)
+        if (g.bad && lane == 0 && flags) atomicOr(flags, g.bad);
+        eval_block<false, true>(P, g, G, g.bad ? 0.f : a0, 0.f, R0, nullptr, pitch, lane, flags);
+    } else if (two) eval_block<true, false>(P, g, G, a0, a1, R0, R1, pitch, lane, flags);
+    else eval_block<false, false>(P, g, G, a0, a1, R0, R1, pitch, lane, flags);
 }
 
 }  // namespace
@@ -715,36 +745,50 @@ cudaError_t ensure_block_tables()
     if (dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_tab_mu);
     if ((g_tab_devices >> dev) & 1ull) return cudaSuccess;
-    static std::vector<float> G;
-    static std::vector<double> G64;
+    static std::vector<float> G[kNumOps];
+    static std::vector<double> G64[kNumOps];
     static std::vector<int> goff;
-    if (G.empty()) build_tables(G, G64, goff);
-    if ((e = cudaMemcpyToSymbol(d_G, G.data(), G.size() * sizeof(float))) != cudaSuccess) return e;
-    if ((e = cudaMemcpyToSymbol(d_G64, G64.data(), G64.size() * sizeof(double))) != cudaSuccess) return e;
+    float *dG = nullptr;
+    double *dG64 = nullptr;
+    const int *dgoff = nullptr;
+    if ((e = cudaGetSymbolAddress((void **)&dG, d_G)) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void **)&dG64, d_G64)) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void **)&dgoff, d_goff)) != cudaSuccess) return e;
+    int sms = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    for (int op = 0; op < kNumOps; ++op) {
+        if (G[op].empty()) build_tables(op, G[op], G64[op], goff);
+        if ((e = cudaMemcpy(dG + (size_t)op * kGSize, G[op].data(), G[op].size() * sizeof(float),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return e;
+        if ((e = cudaMemcpy(dG64 + (size_t)op * kGSize, G64[op].data(), G64[op].size() * sizeof(double),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return e;
+        BlockTables &t = g_tabs[dev][op];
+        t.G = dG + (size_t)op * kGSize;
+        t.G64 = dG64 + (size_t)op * kGSize;
+        t.goff = dgoff;
+        t.sms = sms;
+        t.amax = op == 1 ? 64.f : 8.f;
+    }
     if ((e = cudaMemcpyToSymbol(d_goff, goff.data(), goff.size() * sizeof(int))) != cudaSuccess) return e;
-    BlockTables t{};
-    if ((e = cudaGetSymbolAddress((void **)&t.G, d_G)) != cudaSuccess) return e;
-    if ((e = cudaGetSymbolAddress((void **)&t.G64, d_G64)) != cudaSuccess) return e;
-    if ((e = cudaGetSymbolAddress((void **)&t.goff, d_goff)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&t.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = fused_init()) != cudaSuccess) return e;
     if ((e = intra_init()) != cudaSuccess) return e;
-    g_tabs[dev] = t;
     g_tab_devices |= 1ull << dev;
     return cudaSuccess;
 }
 
-const BlockTables &block_tables()
+const BlockTables &block_tables(int op)
 {
     int dev = 0;
     cudaGetDevice(&dev);
-    return g_tabs[dev < 64 ? dev : 0];
+    return g_tabs[dev < 64 ? dev : 0][op == 1 ? 1 : 0];
 }
 
 cudaError_t launch_block_coef(const BlockJobs &jobs, const BlockScratch &s, cudaStream_t st, int *launches)
 {
     if (jobs.total_blocks == 0) return cudaSuccess;
-    block_coef_kernel<<<2 * block_ranges(jobs.total_blocks), kCoefThreads, 0, st>>>(jobs, block_tables(), s);
+    block_coef_kernel<<<2 * block_ranges(jobs.total_blocks), kCoefThreads, 0, st>>>(jobs, block_tables(jobs.op), s);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
@@ -752,7 +796,9 @@ cudaError_t launch_block_coef(const BlockJobs &jobs, const BlockScratch &s, cuda
 cudaError_t launch_block_eval(const BlockJobs &jobs, uint32_t *flags, cudaStream_t st)
 {
     if (jobs.total_blocks == 0) return cudaSuccess;
-    block_eval_kernel<<<(jobs.total_blocks + 3) / 4, 128, 0, st>>>(jobs, block_tables(), flags);
+    const unsigned grid = (jobs.total_blocks + 3) / 4;
+    if (jobs.p[0].q) block_eval_kernel<true><<<grid, 128, 0, st>>>(jobs, block_tables(jobs.op), flags);
+    else block_eval_kernel<false><<<grid, 128, 0, st>>>(jobs, block_tables(jobs.op), flags);
     return cudaGetLastError();
 }
 

@@ -872,7 +872,7 @@ cudaError_t launch_pframe_rf(FusedFrame &F, const FusedMaps &maps, uint32_t *fla
 {
     F.nmbx = (F.width + kMB - 1) / kMB;
     F.nmb = F.nmbx * ((F.height + kMB - 1) / kMB);
-    const BlockTables &t = block_tables();
+    const BlockTables &t = block_tables(F.op);
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -899,7 +899,7 @@ cudaError_t launch_pframe_fused(FusedFrame &F, const FusedMaps *maps, uint32_t *
     if (!fused_supported(F.block)) return cudaErrorInvalidValue;
     F.nmbx = (F.width + kMB - 1) / kMB;
     F.nmb = F.nmbx * ((F.height + kMB - 1) / kMB);
-    const BlockTables &t = block_tables();
+    const BlockTables &t = block_tables(F.op);
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

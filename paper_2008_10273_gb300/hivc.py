@@ -44,6 +44,11 @@ class Residual(ctypes.Structure):
     _fields_ = [("block_ptr", c_vp), ("pos", c_vp), ("val", c_vp), ("n_points", c_i32)]
 
 
+class CoefResidual(ctypes.Structure):
+    _fields_ = [("block_ptr", c_vp), ("pos", c_vp), ("q", c_vp), ("a", c_vp), ("n_points", c_i32),
+                ("step", c_f32), ("offset", c_f32)]
+
+
 class IFrame(ctypes.Structure):
     _fields_ = [("y", Points), ("c_n", c_i32), ("c_idx", c_vp), ("cb_val", c_vp), ("cr_val", c_vp),
                 ("res", ctypes.POINTER(Residual))]
@@ -51,6 +56,10 @@ class IFrame(ctypes.Structure):
 
 class PFrame(ctypes.Structure):
     _fields_ = [("flow", c_vp), ("res", Residual * 3)]
+
+
+class PFrameCoef(ctypes.Structure):
+    _fields_ = [("flow", c_vp), ("res", CoefResidual * 3)]
 
 
 class Out(ctypes.Structure):
@@ -78,6 +87,9 @@ PROTOTYPES = [
     ("hivc_decode_iframe", c_i32, [c_vp, ctypes.POINTER(IFrame), ctypes.POINTER(Out)]),
     ("hivc_decode_pframe", c_i32, [c_vp, ctypes.POINTER(PFrame), ctypes.POINTER(Out)]),
     ("hivc_decode_batch", c_i32, [ctypes.POINTER(c_vp), ctypes.POINTER(Frame), c_i32, ctypes.POINTER(Out)]),
+    ("hivc_decode_pframe_coef", c_i32, [c_vp, ctypes.POINTER(PFrameCoef), ctypes.POINTER(Out)]),
+    ("hivc_block_residual_coef", c_i32, [c_i32, c_i32, c_i32, c_i32, ctypes.POINTER(CoefResidual), c_vp, c_i32,
+                                         c_vp, c_vp]),
     ("hivc_decoder_sync", c_i32, [c_vp, ctypes.POINTER(Stats)]),
     ("hivc_decoder_set_timing", c_i32, [c_vp, c_i32]),
     ("hivc_decoder_reset", c_i32, [c_vp]),
@@ -150,6 +162,19 @@ def config_default() -> Config:
     return c
 
 
+def coef_residual_struct(r) -> CoefResidual:
+    """``r``: the dict of :func:`device_coef_residual`."""
+    c = CoefResidual()
+    c.block_ptr = _ptr(r["block_ptr"])
+    c.pos = _ptr(r["pos"])
+    c.q = _ptr(r["q"])
+    c.a = _ptr(r["a"])
+    c.n_points = int(r["pos"].numel())
+    c.step = float(r["step"])
+    c.offset = float(r["offset"])
+    return c
+
+
 def residual_struct(block_ptr, pos, val) -> Residual:
     r = Residual()
     r.block_ptr = _ptr(block_ptr)
@@ -173,11 +198,12 @@ class Decoder:
 
     def __init__(self, width: int, height: int, chroma: bool = True, block: int = 16,
                  iframe_tol: float = 1e-8, max_cycles: int = 40, precision: int = 0,
-                 stream=None, timing: bool = False, cond_threshold: float = 1e6):
+                 stream=None, timing: bool = False, cond_threshold: float = 1e6, op: int = 0):
         cfg = config_default()
         cfg.width, cfg.height, cfg.chroma, cfg.block = width, height, int(chroma), block
         cfg.iframe_tol, cfg.max_cycles, cfg.precision = iframe_tol, max_cycles, precision
         cfg.cond_threshold = cond_threshold
+        cfg.op = op
         cfg.stream = _stream_handle(stream)
         self.cfg = cfg
         self.width, self.height, self.chroma, self.block = width, height, bool(chroma), block
@@ -257,6 +283,16 @@ class Decoder:
         s = self.pframe_struct(f)
         return check(lib().hivc_decode_pframe(self.handle, ctypes.byref(s), ctypes.byref(self._out(out))),
                      "hivc_decode_pframe")
+
+    def decode_pframe_coef(self, f, out) -> int:
+        """Inter frame with a coefficient-mode residual (``f`` from
+        :func:`device_pframe_coef`)."""
+        s = PFrameCoef()
+        s.flow = _ptr(f["flow"])
+        for k, r in enumerate(f["res"]):
+            s.res[k] = coef_residual_struct(r)
+        return check(lib().hivc_decode_pframe_coef(self.handle, ctypes.byref(s), ctypes.byref(self._out(out))),
+                     "hivc_decode_pframe_coef")
 
     def sync(self, raise_on_error: bool = True) -> Stats:
         st = Stats()
@@ -350,6 +386,24 @@ def _dev(a, device="cuda"):
 
 def device_residual(res, device="cuda"):
     return (_dev(res.block_ptr, device), _dev(res.pos, device), _dev(res.val, device))
+
+
+def device_coef_residual(res, device="cuda"):
+    """A :class:`workload.CoefResidual` on the device."""
+    return {"block_ptr": _dev(res.block_ptr, device), "pos": _dev(res.pos, device), "q": _dev(res.q, device),
+            "a": _dev(res.a, device), "step": res.step, "offset": res.offset}
+
+
+def device_pframe_coef(pfr, device="cuda"):
+    return {"flow": _dev(pfr.flow, device), "res": [device_coef_residual(r, device) for r in pfr.res]}
+
+
+def block_residual_coef(width, height, block, op, res, r, flags=None, stream=None):
+    """hivc_block_residual_coef: ``res`` from :func:`device_coef_residual`."""
+    c = coef_residual_struct(res)
+    return check(lib().hivc_block_residual_coef(width, height, block, op, ctypes.byref(c), _ptr(r),
+                                                int(r.stride(0)), _ptr(flags), _stream_handle(stream)),
+                 "hivc_block_residual_coef")
 
 
 def device_iframe(ifr, device="cuda"):
