@@ -40,7 +40,7 @@ UNIT = "FullHD frames/s"
 # file at capture time; a changed source voids the number (reported null).
 NCU_TRAFFIC = {
     # intra_sor_kernel, one launch on the FullHD 4:2:0 GOP workload
-    "intra_sweeps": {"bytes": 32.63e6, "sha": "636fb463ab5d"},
+    "intra_sweeps": {"bytes": 28.03e6, "sha": "bf6cd8beb4a0"},
 }
 
 
@@ -60,6 +60,8 @@ def parse_args(argv=None):
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--no-serve", action="store_true", help="skip the multi-stream serving measurement")
     p.add_argument("--serve-gop", type=int, default=30, help="frames per stream in the serving measurement")
+    p.add_argument("--no-next", action="store_true",
+                   help="skip the coefficient-mode and biharmonic measurements")
     p.add_argument("--path", choices=["batch", "plain"], default="batch",
                    help="decode path of the timed steps: one hivc_decode_batch call per GOP (inter frames "
                         "share coefficient launches), or one call per frame")
@@ -205,6 +207,97 @@ def serve_measurement(a, gops=None):
                        f"one GOP of {a.serve_gop} frames each; arrivals 30 fps per stream + Exp(3 ms) jitter "
                        f"(saturated: all at t=0); HBM budget 40 GB; latency = arrival to completion event; "
                        f"measured on a warm server (second pass, idle decoders reused)")
+    return res
+
+
+def next_rows_measurement(a, gop):
+    """The paper's coefficient mode (inter frames that carry dead-zone
+    quantised Green's coefficients and constants: evaluation only) and the
+    biharmonic operator, on the FullHD GOP workload.  Device time with CUDA
+    events, L2 flushed between steps."""
+    import torch
+
+    from paper_2008_10273_gb300 import hivc
+    from workload import make_gop
+
+    W, H = a.width, a.height
+    cw, ch = (W + 1) // 2, (H + 1) // 2
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    res = {}
+    steps, warm = 5, 2
+
+    # coefficient mode: the inter frames of a GOP
+    cg = make_gop(a.seed + 1, W, H, n_frames=a.frames, with_sources=False, coef_mode=True,
+                  coef_kw={"step": 0.1, "offset": 0.5, "kmax": 48})
+    dec = hivc.Decoder(W, H, chroma=True, iframe_tol=a.iframe_tol, stream=stream)
+    out = hivc.alloc_out(W, H)
+    pfs = [hivc.device_pframe_coef(p) for p in cg.pframes]
+    with torch.cuda.stream(stream):
+        dec.decode_iframe(hivc.device_iframe(cg.iframe), out)
+        ms = []
+        for k in range(warm + steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for f in pfs:
+                dec.decode_pframe_coef(f, out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= warm:
+                ms.append(e0.elapsed_time(e1))
+        dec.sync()
+        hivc.lib().hivc_decoder_set_timing(dec.handle, 1)
+        flush.zero_()
+        for f in pfs:
+            dec.decode_pframe_coef(f, out)
+        st = dec.sync()
+        hivc.lib().hivc_decoder_set_timing(dec.handle, 0)
+    dec.close()
+    n_in = len(pfs)
+    px = W * H / FULLHD_PX
+    npts = sum(int(r.n_points) for r in cg.pframes[0].res)
+    nblk = sum(int(r.n_blocks) for r in cg.pframes[0].res)
+    ev_ms = st.kernel_ms[5] / max(1, st.kernel_launches[5])
+    # evaluation: residual planes written (4 B per pixel), per point pos +
+    # index (2 B), per block pointer + constant (8 B)
+    ev_bytes = (W * H + 2 * cw * ch) * 4 + npts * 2 + nblk * 8
+    hbm = 6800.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            hbm = float(json.load(fh).get("hbm_gbs", hbm))
+    except OSError:
+        pass
+    res["coef_mode"] = {
+        "value": n_in * steps * px / (sum(ms) / 1e3), "unit": "FullHD inter frames/s",
+        "ms_per_frame": sum(ms) / steps / n_in,
+        "eval_kernel": {"bound": "hbm", "avg_launch_ms": ev_ms, "algorithmic_bytes_per_launch": ev_bytes,
+                        "achieved": ev_bytes / (ev_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                        "frac": ev_bytes / (ev_ms / 1e3) / 1e9 / hbm},
+        "workload": f"{n_in} FullHD 4:2:0 inter frames, coefficient-mode residuals (Poisson(8) luma / "
+                    "Poisson(4) chroma points, indices in [-127, 127] with 40% zeros, step 0.1, offset 0.5)"}
+
+    # biharmonic operator: the same GOP as the headline, batched
+    dec = hivc.Decoder(W, H, chroma=True, iframe_tol=a.iframe_tol, stream=stream, op=1)
+    frames = [("i", hivc.device_iframe(gop.iframe))] + [("p", hivc.device_pframe(p)) for p in gop.pframes]
+    outs = [out] * len(frames)
+    with torch.cuda.stream(stream):
+        ms = []
+        for k in range(warm + steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hivc.decode_batch([dec] * len(frames), frames, outs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= warm:
+                ms.append(e0.elapsed_time(e1))
+        st = dec.sync()
+    dec.close()
+    res["biharmonic"] = {"value": len(frames) * steps * px / (sum(ms) / 1e3), "unit": UNIT,
+                         "ms_per_step": sum(ms) / steps, "max_cond_bound": float(st.max_cond),
+                         "fp64_blocks": int(st.fp64_blocks),
+                         "workload": "the headline GOP decoded with the biharmonic operator (op 1), batched"}
     return res
 
 
@@ -494,6 +587,7 @@ def main(argv=None):
     served = None
     if rank == 0 and world == 1 and not a.no_serve:
         served = serve_measurement(a, {(W, H): gop} if (W, H) == (1920, 1080) and a.serve_gop == nfr else None)
+    nxt = next_rows_measurement(a, gop) if (rank == 0 and world == 1 and not a.no_next) else None
 
     if rank == 0:
         pf = sorted(frame_ms[i] for i in range(len(frame_ms)) if i % nfr != 0)
@@ -520,6 +614,7 @@ def main(argv=None):
             "clocks": clk,
             "cpu_baseline": cpu,
             "serving": served,
+            "next_rows": nxt,
         }
         print(json.dumps(line), flush=True)
     dec.close()
