@@ -73,6 +73,8 @@ def lib():
             L.oracle_green_matrix_op.restype = None
             L.oracle_block_residual_op.argtypes = [c_int, c_int, c_int, c_int, u32p, u8p, i16p, dp]
             L.oracle_block_residual_op.restype = c_int
+            L.oracle_inverse_rct.argtypes = [c_int, dp, dp, dp, u8p]
+            L.oracle_inverse_rct.restype = None
             L.oracle_dequantise.argtypes = [c_int, c_double, c_double]
             L.oracle_dequantise.restype = c_double
             L.oracle_block_residual_coef.argtypes = [c_int, c_int, c_int, c_int, u32p, u8p,
@@ -216,9 +218,21 @@ def to_uint8(recon: np.ndarray) -> np.ndarray:
 # ----------------------------------------------------------------------------
 # frames and GOPs (Sec. 2: prediction + correction, closed loop)
 # ----------------------------------------------------------------------------
-def plane_sizes(width: int, height: int, chroma: bool) -> List[Tuple[int, int]]:
+def inverse_rct(y: np.ndarray, u: np.ndarray, v: np.ndarray) -> List[np.ndarray]:
+    """R, G, B uint8 planes from reconstructed RCT planes (Sec. 2.3)."""
+    h, w = y.shape
+    out = np.empty(3 * h * w, np.uint8)
+    yy, uu, vv = (np.ascontiguousarray(a, np.float64) for a in (y, u, v))
+    lib().oracle_inverse_rct(h * w, _p(yy, ctypes.c_double), _p(uu, ctypes.c_double), _p(vv, ctypes.c_double),
+                             _p(out, ctypes.c_uint8))
+    return [out[k * h * w:(k + 1) * h * w].reshape(h, w) for k in range(3)]
+
+
+def plane_sizes(width: int, height: int, chroma: bool, rct: bool = False) -> List[Tuple[int, int]]:
     if not chroma:
         return [(width, height)]
+    if rct:
+        return [(width, height)] * 3
     cw, ch = (width + 1) // 2, (height + 1) // 2
     return [(width, height), (cw, ch), (cw, ch)]
 
@@ -228,15 +242,18 @@ class OracleDecoder:
     kept unrounded (clamped float64) as the inter-frame reference."""
 
     def __init__(self, width: int, height: int, chroma: bool, block: int = 16,
-                 iframe_tol: float = 1e-12, op: int = 0):
+                 iframe_tol: float = 1e-12, op: int = 0, rct: bool = False):
+        """``rct``: the colour path of Sec. 2.3 (4:4:4 RCT planes Y, U, V;
+        U and V clamped to [-255, 255]; the output is R, G, B)."""
         self.width, self.height, self.chroma, self.block = width, height, chroma, block
         self.iframe_tol = iframe_tol
         self.op = op
+        self.rct = bool(rct) and bool(chroma)
         self.ref: Optional[List[np.ndarray]] = None
         self.last_inpaint: List[Tuple[float, int]] = []
 
     def decode_iframe(self, ifr):
-        sizes = plane_sizes(self.width, self.height, self.chroma)
+        sizes = plane_sizes(self.width, self.height, self.chroma, self.rct)
         preds = []
         self.last_inpaint = []
         u, res, its, _ = inpaint(sizes[0][0], sizes[0][1], ifr.y_idx, ifr.y_val, self.iframe_tol)
@@ -252,10 +269,10 @@ class OracleDecoder:
     def decode_pframe(self, pfr):
         if self.ref is None:
             raise RuntimeError("inter frame before any intra frame")
-        sizes = plane_sizes(self.width, self.height, self.chroma)
+        sizes = plane_sizes(self.width, self.height, self.chroma, self.rct)
         preds = [warp(self.ref[0], pfr.flow)]
         if self.chroma:
-            cf = chroma_flow(pfr.flow, sizes[1][0], sizes[1][1])
+            cf = pfr.flow.astype(np.float64) if self.rct else chroma_flow(pfr.flow, sizes[1][0], sizes[1][1])
             preds += [warp(self.ref[1], cf), warp(self.ref[2], cf)]
         return self._correct(preds, pfr.res)
 
@@ -264,10 +281,10 @@ class OracleDecoder:
         (:class:`workload.PFrameCoef`)."""
         if self.ref is None:
             raise RuntimeError("inter frame before any intra frame")
-        sizes = plane_sizes(self.width, self.height, self.chroma)
+        sizes = plane_sizes(self.width, self.height, self.chroma, self.rct)
         preds = [warp(self.ref[0], pfr.flow)]
         if self.chroma:
-            cf = chroma_flow(pfr.flow, sizes[1][0], sizes[1][1])
+            cf = pfr.flow.astype(np.float64) if self.rct else chroma_flow(pfr.flow, sizes[1][0], sizes[1][1])
             preds += [warp(self.ref[1], cf), warp(self.ref[2], cf)]
         return self._correct(preds, pfr.res, coef=True)
 
@@ -280,8 +297,11 @@ class OracleDecoder:
                 r = block_residual_coef(residuals[k], self.op)
             else:
                 r = block_residual(residuals[k], self.op)
-            recon.append(np.clip(p + r, 0.0, 255.0))
+            lo = -255.0 if (self.rct and k > 0) else 0.0
+            recon.append(np.clip(p + r, lo, 255.0))
         self.ref = recon
+        if self.rct:
+            return recon, inverse_rct(*recon)
         return recon, [to_uint8(x) for x in recon]
 
 
@@ -289,7 +309,8 @@ def decode_gop(gop, n_frames: Optional[int] = None, iframe_tol: float = 1e-12, o
     """Decode the first ``n_frames`` frames of a :class:`workload.Gop`
     (inter frames in values or coefficient mode).  Returns the list of
     (recon float64 planes, uint8 planes) per frame."""
-    dec = OracleDecoder(gop.width, gop.height, gop.chroma, gop.block, iframe_tol, op=op)
+    dec = OracleDecoder(gop.width, gop.height, gop.chroma, gop.block, iframe_tol, op=op,
+                        rct=getattr(gop, "rct", False))
     n = gop.n_frames if n_frames is None else n_frames
     out = [dec.decode_iframe(gop.iframe)]
     for t in range(1, n):

@@ -481,3 +481,27 @@ int oracle_block_residual_coef(int W, int H, int B, int op, const uint32_t *bloc
     for (int s = 0; s < n_shapes; ++s) free(shape_G[s]);
     return status;
 }
+
+/*
+ * Colour path of Sec. 2.3: the codec works on the planes of the reversible
+ * colour transform (RCT) of JPEG2000 at full resolution (4:4:4):
+ *     Y = floor((R + 2G + B) / 4),  U = B - G,  V = R - G,
+ * so Y is in [0, 255] and U, V in [-255, 255].  The decoder's output is the
+ * inverse transform of the rounded planes:
+ *     G = Y - floor((U + V) / 4),  R = V + G,  B = U + G,
+ * with each reconstructed plane first rounded half up to an integer
+ * (reading: as for the uint8 planes) and R, G, B clamped to [0, 255].
+ * y, u, v: n reconstructed values; rgb: 3 n bytes, planes R, G, B.
+ */
+void oracle_inverse_rct(int n, const double *y, const double *u, const double *v, uint8_t *rgb)
+{
+    for (int i = 0; i < n; ++i) {
+        const double Y = floor(y[i] + 0.5), U = floor(u[i] + 0.5), V = floor(v[i] + 0.5);
+        const double G = Y - floor((U + V) / 4.0);
+        double c[3] = {V + G, G, U + G};
+        for (int k = 0; k < 3; ++k) {
+            const double x = c[k] < 0.0 ? 0.0 : (c[k] > 255.0 ? 255.0 : c[k]);
+            rgb[(size_t)k * n + i] = (uint8_t)x;
+        }
+    }
+}

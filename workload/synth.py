@@ -92,6 +92,7 @@ class IFrame:
     cb_val: Optional[np.ndarray] = None
     cr_val: Optional[np.ndarray] = None
     res: Optional[List[Residual]] = None  # None, or one Residual per plane
+    rct: bool = False  # 4:4:4 RCT planes (chroma values int16 in [-255, 255])
 
 
 @dataclass
@@ -115,6 +116,7 @@ class Gop:
     iframe: IFrame
     pframes: List[PFrame]
     sources: List[Tuple[np.ndarray, ...]] = field(default_factory=list)
+    rct: bool = False  # 4:4:4 RCT planes Y, U, V (Sec. 2.3)
 
     @property
     def n_frames(self) -> int:
@@ -291,12 +293,13 @@ def make_coef_residual(
     return CoefResidual(width, height, block, bp, pos, q.astype(np.int8), a, float(step), float(offset))
 
 
-def coef_frame_residuals(rng, width, height, chroma, block, lam_y=8.0, lam_c=4.0, **kw) -> List[CoefResidual]:
+def coef_frame_residuals(rng, width, height, chroma, block, lam_y=8.0, lam_c=4.0, rct=False,
+                         **kw) -> List[CoefResidual]:
     """Coefficient-mode residuals of one frame; Cr shares the Cb layout."""
     ry = make_coef_residual(rng, width, height, block, lam_y, **kw)
     if not chroma:
         return [ry]
-    cw, ch = chroma_size(width, height)
+    cw, ch = (width, height) if rct else chroma_size(width, height)
     rcb = make_coef_residual(rng, cw, ch, block, lam_c, **kw)
     rcr = make_coef_residual(rng, cw, ch, block, lam_c, positions_from=rcb, **kw)
     return [ry, rcb, rcr]
@@ -320,6 +323,7 @@ class _Texture:
     centers: np.ndarray  # (n, 2)
     sigmas: np.ndarray  # (n,)
     amps: np.ndarray  # (n,)
+    signed: bool = False  # an RCT chroma plane: int16 in [-255, 255]
 
 
 def _random_texture(rng, width, height, n_blobs, amp, grad_span, base=128.0):
@@ -352,6 +356,8 @@ def _render(tex: _Texture, xs: np.ndarray, ys: np.ndarray, rot: float, shift, ce
         ex = np.exp(-((xs - fx) ** 2) / (2 * sg * sg))
         ey = np.exp(-((ys - fy) ** 2) / (2 * sg * sg))
         img += a * np.outer(ey, ex)
+    if tex.signed:
+        return np.clip(np.floor(img + 0.5), -255, 255).astype(np.int16)
     return np.clip(np.floor(img + 0.5), 0, 255).astype(np.uint8)
 
 
@@ -411,11 +417,18 @@ def make_iframe_only(seed: int, width: int, height: int, mask_frac: float,
     return srcs, ifr
 
 
-def _scene_planes(rng, width, height, chroma):
+def _scene_planes(rng, width, height, chroma, rct=False):
     center = (width / 2.0, height / 2.0)
     out = [(_random_texture(rng, width, height, 12, 60.0, 30.0),
             np.arange(width, dtype=np.float64), np.arange(height, dtype=np.float64), center)]
-    if chroma:
+    if chroma and rct:
+        # 4:4:4 planes of the reversible colour transform: U = B - G and
+        # V = R - G are signed (Sec. 2.3)
+        for _ in range(2):
+            tex = _random_texture(rng, width, height, 12, 60.0, 20.0, base=0.0)
+            tex.signed = True
+            out.append((tex, np.arange(width, dtype=np.float64), np.arange(height, dtype=np.float64), center))
+    elif chroma:
         cw, ch = chroma_size(width, height)
         xs = 2.0 * np.arange(cw) + 0.5
         ys = 2.0 * np.arange(ch) + 0.5
@@ -424,11 +437,12 @@ def _scene_planes(rng, width, height, chroma):
     return out
 
 
-def _intra(rng, width, height, chroma, srcs, frac, cfrac):
+def _intra(rng, width, height, chroma, srcs, frac, cfrac, rct=False):
     idx = _mask(rng, width * height, frac)
     ifr = IFrame(width, height, chroma, idx, srcs[0].reshape(-1)[idx].copy())
+    ifr.rct = bool(rct and chroma)
     if chroma:
-        cw, ch = chroma_size(width, height)
+        cw, ch = (width, height) if rct else chroma_size(width, height)
         cidx = _mask(rng, cw * ch, cfrac)
         ifr.c_idx = cidx
         ifr.cb_val = srcs[1].reshape(-1)[cidx].copy()
@@ -436,12 +450,12 @@ def _intra(rng, width, height, chroma, srcs, frac, cfrac):
     return ifr
 
 
-def _frame_residuals(rng, width, height, chroma, block, lam_y=8.0, lam_c=4.0, vmax=64,
+def _frame_residuals(rng, width, height, chroma, block, lam_y=8.0, lam_c=4.0, vmax=64, rct=False,
                      **kw) -> List[Residual]:
     ry = make_residual(rng, width, height, block, lam_y, vmax, **kw)
     if not chroma:
         return [ry]
-    cw, ch = chroma_size(width, height)
+    cw, ch = (width, height) if rct else chroma_size(width, height)
     kwc = {k: v for k, v in kw.items() if k not in ("shared_layouts", "shared_frac")}
     rcb = make_residual(rng, cw, ch, block, lam_c, vmax, **kwc)
     rcr = make_residual(rng, cw, ch, block, lam_c, vmax, positions_from=rcb)
@@ -467,14 +481,17 @@ def make_gop(
     residual_kw: Optional[dict] = None,
     coef_mode: bool = False,
     coef_kw: Optional[dict] = None,
+    rct: bool = False,
 ) -> Gop:
     """A GOP of one intra frame and ``n_frames - 1`` inter frames of a moving
     synthetic scene (FullHD 4:2:0 by default).  The flow of inter frame t is
     the exact backward displacement from frame t to frame t-1.  With
     ``coef_mode`` the inter frames carry coefficient-mode residuals
-    (:class:`PFrameCoef`)."""
+    (:class:`PFrameCoef`); with ``rct`` the colour planes are the 4:4:4
+    planes Y, U, V of the reversible colour transform (Sec. 2.3)."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    planes = _scene_planes(rng, width, height, chroma)
+    rct = bool(rct and chroma)
+    planes = _scene_planes(rng, width, height, chroma, rct)
     center = (width / 2.0, height / 2.0)
     rots = [0.0]
     shifts = [np.zeros(2)]
@@ -487,8 +504,8 @@ def make_gop(
 
     src0 = render_frame(0)
     sources = [src0] if with_sources else []
-    ifr = _intra(rng, width, height, chroma, src0, mask_frac, chroma_mask_frac)
-    rkw = dict(lam_y=lam_y, lam_c=lam_c, vmax=vmax, **(residual_kw or {}))
+    ifr = _intra(rng, width, height, chroma, src0, mask_frac, chroma_mask_frac, rct)
+    rkw = dict(lam_y=lam_y, lam_c=lam_c, vmax=vmax, rct=rct, **(residual_kw or {}))
     if iframe_residual:
         ifr.res = _frame_residuals(rng, width, height, chroma, block, **rkw)
 
@@ -506,10 +523,11 @@ def make_gop(
         qy = -sp * px + cp * py + cy
         flow = np.stack([qx - xs, qy - ys], axis=-1).astype(np.float32)
         if coef_mode:
-            res = coef_frame_residuals(rng, width, height, chroma, block, lam_y=lam_y, lam_c=lam_c, **(coef_kw or {}))
+            res = coef_frame_residuals(rng, width, height, chroma, block, lam_y=lam_y, lam_c=lam_c, rct=rct,
+                                       **(coef_kw or {}))
             pframes.append(PFrameCoef(flow, res))
         else:
             pframes.append(PFrame(flow, _frame_residuals(rng, width, height, chroma, block, **rkw)))
         if with_sources:
             sources.append(render_frame(t))
-    return Gop(width, height, chroma, block, ifr, pframes, sources)
+    return Gop(width, height, chroma, block, ifr, pframes, sources, rct)
