@@ -13,7 +13,8 @@
  *
  * Conventions (all entry points):
  *   - Planes are row-major; luma is width x height, 4:2:0 chroma planes are
- *     ceil(width/2) x ceil(height/2).  Grey values are in [0, 255].
+ *     ceil(width/2) x ceil(height/2), 4:4:4 planes width x height.  Grey
+ *     values are in [0, 255] (RCT chroma in [-255, 255]).
  *   - Every array pointer in the input/output structs is DEVICE memory owned
  *     by the caller.  It must stay valid and unmodified until the work is
  *     complete (hivc_decoder_sync, or the caller's stream for the step
@@ -51,7 +52,13 @@ typedef enum {
 /* Decoder configuration.  hivc_config_default() fills the defaults. */
 typedef struct {
     int32_t width, height;  /* luma plane size, >= 1 */
-    int32_t chroma;         /* 0 = grey (Y only), 1 = YCbCr 4:2:0 */
+    int32_t chroma;         /* 0 = grey (Y only), 1 = YCbCr 4:2:0,
+                               2 = the paper's colour path (Sec. 2.3): 4:4:4
+                               planes Y, U = B - G, V = R - G of the
+                               reversible colour transform of JPEG2000 (U, V
+                               in [-255, 255], moved by the luma flow); the
+                               output planes are R, G, B =
+                               the inverse RCT of the rounded planes */
     int32_t block;          /* residual block edge B, 1..16.  The paper uses
                                8 x 8 blocks (Sec. 2.2, 2.3); default 16 */
     int32_t op;             /* residual operator (Sec. 2.2: defined by the
@@ -133,6 +140,8 @@ typedef struct {
     const uint8_t *cr_val;    /* device */
     const hivc_residual *res; /* NULL, or a HOST array of 1 (grey) / 3
                                  residuals added to the inpainted planes */
+    const int16_t *cu_val;    /* device, chroma 2: the U values (cb_val unused) */
+    const int16_t *cv_val;    /* device, chroma 2: the V values (cr_val unused) */
 } hivc_iframe;
 
 /* Inter frame: pred(x) = ref(x + flow(x)), bilinear, sample clamped.

@@ -85,7 +85,7 @@ constexpr int kStatusWords = 4;
 bool config_ok(const hivc_config *c)
 {
     return c && c->width >= 1 && c->height >= 1 && c->width <= 16384 && c->height <= 16384 &&
-           (c->chroma == 0 || c->chroma == 1) && c->block >= 1 && c->block <= kMaxB && (c->op == 0 || c->op == 1) &&
+           (c->chroma >= 0 && c->chroma <= 2) && c->block >= 1 && c->block <= kMaxB && (c->op == 0 || c->op == 1) &&
            (c->precision == 0 || c->precision == 1) && c->iframe_tol >= 0.0 && c->max_cycles >= 1 &&
            c->cond_threshold >= 0.0;
 }
@@ -95,8 +95,9 @@ int plane_count(const hivc_config *c) { return c->chroma ? 3 : 1; }
 PlaneGeom plane_geom(const hivc_config *c, int p)
 {
     PlaneGeom g;
-    g.w = p == 0 ? c->width : (c->width + 1) / 2;
-    g.h = p == 0 ? c->height : (c->height + 1) / 2;
+    const bool half = p > 0 && c->chroma == 1;  // 4:2:0; 4:4:4 chroma planes are full size
+    g.w = half ? (c->width + 1) / 2 : c->width;
+    g.h = half ? (c->height + 1) / 2 : c->height;
     g.pitch = round_up(g.w, kPitchAlign);
     g.nbx = (g.w + c->block - 1) / c->block;
     g.nblocks = g.nbx * ((g.h + c->block - 1) / c->block);
@@ -497,13 +498,46 @@ hivc_status hivc_decoder_reference(const hivc_decoder *d, int32_t plane, const f
     return HIVC_OK;
 }
 
+namespace {
+
+// The 4:4:4 colour path's pixel kernel for the frame being decoded: inter
+// (flow != nullptr: warp of the current references) or intra (hi/lo: the
+// inpainted planes); r: residual planes or nullptr.
+cudaError_t launch_rct_frame(hivc_decoder *d, const float *flow, float *const *hi, float *const *lo, bool residual,
+                             const hivc_out *out)
+{
+    RctFrame F{};
+    F.flow = flow;
+    const int nxt = d->cur ^ 1;
+    for (int p = 0; p < 3; ++p) {
+        F.ref[p] = d->ref[d->cur][p];
+        F.src_hi[p] = hi ? hi[p] : nullptr;
+        F.src_lo[p] = lo ? lo[p] : nullptr;
+        F.r[p] = residual ? d->rfield[p] : nullptr;
+        F.ref_out[p] = d->ref[nxt][p];
+        F.out[p] = out->plane[p];
+        F.out_pitch[p] = out->pitch[p];
+    }
+    F.pitch = d->pg[0].pitch;
+    F.width = d->cfg.width;
+    F.height = d->cfg.height;
+    Timed t(d, 6);
+    const cudaError_t e = launch_rct(F, d->stream);
+    t.done(1);
+    return e;
+}
+
+}  // namespace
+
 hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc_out *out)
 {
     if (!d || !f || !out_ok(d, out)) return HIVC_E_INVALID;
     if (f->y.n < 1 || !f->y.idx || !f->y.val) return HIVC_E_INVALID;
     if ((int64_t)f->y.n > (int64_t)d->pg[0].w * d->pg[0].h) return HIVC_E_INVALID;
+    const bool rct = d->cfg.chroma == 2;
     if (d->np == 3) {
-        if (f->c_n < 1 || !f->c_idx || !f->cb_val || !f->cr_val) return HIVC_E_INVALID;
+        if (f->c_n < 1 || !f->c_idx || (rct ? (!f->cu_val || !f->cv_val) : (!f->cb_val || !f->cr_val)))
+            return HIVC_E_INVALID;
         if ((int64_t)f->c_n > (int64_t)d->pg[1].w * d->pg[1].h) return HIVC_E_INVALID;
     }
     if (f->res)
@@ -521,6 +555,8 @@ hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc
         P.pitch = g.pitch;
         P.idx = p == 0 ? f->y.idx : f->c_idx;
         P.val = p == 0 ? f->y.val : (p == 1 ? f->cb_val : f->cr_val);
+        P.val16 = (rct && p > 0) ? (p == 1 ? f->cu_val : f->cv_val) : nullptr;
+        if (P.val16) P.val = nullptr;
         P.n = p == 0 ? f->y.n : f->c_n;
         P.mask = d->mask[p];
         P.uh[0] = d->uh[0][p];
@@ -650,9 +686,24 @@ hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc
         hivc_status s = run_block_residual(d, f->res);
         if (s != HIVC_OK) return s;
     }
+    const int nxt = d->cur ^ 1;
+    if (rct) {
+        float *hi[3], *lo[3];
+        for (int p = 0; p < 3; ++p) {
+            hi[p] = J.p[p].uh[0];
+            lo[p] = J.p[p].ff ? J.p[p].ul[0] : nullptr;
+        }
+        if (launch_rct_frame(d, nullptr, hi, lo, f->res != nullptr, out) != cudaSuccess) return HIVC_E_CUDA;
+        d->cur = nxt;
+        d->has_ref = true;
+        for (int p = 0; p < 3; ++p) d->st.resid[p] = rn[p];
+        d->st.cycles = cycles;
+        d->st.sweeps = sweeps_total;
+        d->st.frames += 1;
+        return converged ? HIVC_OK : HIVC_E_NOT_CONVERGED;
+    }
     WarpJobs W{};
     W.n = d->np;
-    const int nxt = d->cur ^ 1;
     for (int p = 0; p < d->np; ++p) {
         WarpPlane &P = W.p[p];
         const PlaneGeom &g = d->pg[p];
@@ -765,7 +816,13 @@ hivc_status hivc_decode_pframe(hivc_decoder *d, const hivc_pframe *f, const hivc
     if (cudaSetDevice(d->device) != cudaSuccess) return HIVC_E_CUDA;
     const int nxt = d->cur ^ 1;
     cudaError_t e;
-    if (fused_supported(d->cfg.block)) {
+    if (d->cfg.chroma == 2) {
+        // 4:4:4 colour path: block stage into residual planes, then the
+        // RCT pixel kernel
+        hivc_status s = run_block_residual(d, f->res);
+        if (s != HIVC_OK) return s;
+        if (launch_rct_frame(d, f->flow, nullptr, nullptr, true, out) != cudaSuccess) return HIVC_E_CUDA;
+    } else if (fused_supported(d->cfg.block)) {
         // two launches: the coefficients of every block, then one fused
         // kernel for evaluation + warp + add + pack
         BlockJobs J;
@@ -872,7 +929,9 @@ hivc_status hivc_decode_pframe_coef(hivc_decoder *d, const hivc_pframe_coef *f, 
     hivc_pframe pf{};
     pf.flow = f->flow;
     const int nxt = d->cur ^ 1;
-    if (d->maps_ok && d->cfg.width % 2 == 0 &&
+    if (d->cfg.chroma == 2) {
+        if (launch_rct_frame(d, f->flow, nullptr, nullptr, true, out) != cudaSuccess) return HIVC_E_CUDA;
+    } else if (d->maps_ok && d->cfg.width % 2 == 0 &&
         launch_rf_frame(d, &pf, out, d->rfield[0], d->rfield[1], d->rfield[2]) == cudaSuccess) {
         // launched
     } else {
@@ -1084,7 +1143,7 @@ hivc_status decode_own_frames(hivc_decoder *d, const hivc_frame *frames, const h
         std::vector<int> run;
         while (i < ks.size() && frames[ks[i]].type == 1) run.push_back(ks[i++]);
         hivc_status s = HIVC_OK;
-        if (fused_supported(d->cfg.block)) {
+        if (fused_supported(d->cfg.block) && d->cfg.chroma != 2) {
             s = decode_inter_run(d, frames, outs, run);
         } else {
             for (int k : run)

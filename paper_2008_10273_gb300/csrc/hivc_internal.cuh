@@ -174,6 +174,25 @@ struct WarpJobs {
 
 cudaError_t launch_warp_add(WarpJobs &jobs, cudaStream_t st);
 
+// One 4:4:4 frame of the colour path of Sec. 2.3 (RCT planes Y, U, V of one
+// size and pitch): prediction (backward warp of the three reference planes
+// along the luma flow, or the intra solution), + residual, clamp (Y to
+// [0, 255], U and V to [-255, 255]), new FP32 references, and the inverse
+// RCT of the rounded planes packed as R, G, B.
+struct RctFrame {
+    const float *flow;                   // inter: luma flow (H x W x 2); nullptr: intra
+    const float *ref[3];                 // inter: previous reference planes
+    const float *src_hi[3], *src_lo[3];  // intra: the inpainted planes (lo may be nullptr)
+    const float *r[3];                   // residual planes, or nullptr
+    float *ref_out[3];
+    uint8_t *out[3];                     // R, G, B
+    int32_t pitch;                       // floats, every FP32 plane
+    int32_t out_pitch[3];
+    int32_t width, height;
+};
+
+cudaError_t launch_rct(const RctFrame &f, cudaStream_t st);
+
 // ---------------------------------------------------------------------------
 // intra solve (Sec. 2.1)
 // ---------------------------------------------------------------------------
@@ -181,6 +200,7 @@ struct IntraPlane {
     int32_t width, height, pitch;  // pitch in elements
     const uint32_t *idx;           // mask indices
     const uint8_t *val;            // mask values
+    const int16_t *val16;          // signed mask values (RCT chroma) instead, or nullptr
     int32_t n;                     // mask size
     uint8_t *mask;                 // 1 = known pixel
     float *uh[2], *ul[2];          // iterate u = hi + lo ([0] current, [1] next)

@@ -74,7 +74,8 @@ __device__ __forceinline__ void ff_add(float h, float l, float e, float &oh, flo
     fast_two_sum(s, __fadd_rn(t, l), oh, ol);
 }
 
-// sum of mask values (exact, integer) + index validation; plane = blockIdx.y
+// sum of mask values (exact, integer; signed for RCT chroma) + index
+// validation; plane = blockIdx.y
 __global__ void intra_sum_kernel(const __grid_constant__ IntraJobs J, uint32_t *flags)
 {
     const IntraPlane &P = J.p[blockIdx.y];
@@ -84,7 +85,8 @@ __global__ void intra_sum_kernel(const __grid_constant__ IntraJobs J, uint32_t *
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P.n; k += gridDim.x * blockDim.x) {
         const uint32_t i = __ldg(P.idx + k);
         bad |= (i >= N) || (k > 0 && __ldg(P.idx + k - 1) >= i);
-        s += __ldg(P.val + k);
+        // two's complement: signed values add correctly modulo 2^64
+        s += P.val16 ? (unsigned long long)(long long)__ldg(P.val16 + k) : (unsigned long long)__ldg(P.val + k);
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(P.vsum, s);
@@ -95,7 +97,7 @@ __global__ void intra_sum_kernel(const __grid_constant__ IntraJobs J, uint32_t *
 __global__ void intra_fill_kernel(const __grid_constant__ IntraJobs J)
 {
     const IntraPlane &P = J.p[blockIdx.y];
-    const float mean = P.n > 0 ? (float)((double)*P.vsum / (double)P.n) : 0.f;
+    const float mean = P.n > 0 ? (float)((double)(long long)*P.vsum / (double)P.n) : 0.f;
     const size_t total = (size_t)P.height * P.pitch;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         P.uh[0][i] = mean;
@@ -113,7 +115,7 @@ __global__ void intra_scatter_kernel(const __grid_constant__ IntraJobs J)
         const uint32_t i = __ldg(P.idx + k);
         if (i >= N) continue;
         const size_t o = (size_t)(i / P.width) * P.pitch + (i % P.width);
-        P.uh[0][o] = (float)__ldg(P.val + k);
+        P.uh[0][o] = P.val16 ? (float)__ldg(P.val16 + k) : (float)__ldg(P.val + k);
         P.mask[o] = 1;
     }
 }

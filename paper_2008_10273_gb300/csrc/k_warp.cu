@@ -1,6 +1,7 @@
 // Inter prediction by backward warping (Sec. 2, Sec. 2.3) and the final
 // correction step (prediction + residual, clamped to [0, 255]), plus the
-// uint8 pack.  One launch covers all planes of a frame.
+// uint8 pack.  One launch covers all planes of a frame.  The 4:4:4 colour
+// path (RCT planes) has its own kernel that also applies the inverse RCT.
 //
 // pred(x) = ref(x + v(x)), bilinear; the sample position is clamped to the
 // plane.  The integer part and the fraction of v are split in FP32
@@ -98,7 +99,58 @@ __global__ void __launch_bounds__(kTW *kTH) warp_add_kernel(const __grid_constan
     if (P.out) P.out[(size_t)y * P.out_pitch + x] = (uint8_t)__float2int_rd(v + 0.5f);
 }
 
+// 4:4:4 colour path (Sec. 2.3): the three RCT planes of a pixel together.
+// The flow is read once and its interpolation weights serve all planes.
+__global__ void __launch_bounds__(kTW *kTH) rct_kernel(const __grid_constant__ RctFrame F)
+{
+    const int x = blockIdx.x * kTW + (threadIdx.x & 31), y = blockIdx.y * kTH + (threadIdx.x >> 5);
+    if (x >= F.width || y >= F.height) return;
+    const size_t i = (size_t)y * F.pitch + x;
+    float pred[3];
+    if (F.flow) {
+        const float2 f = __ldg(reinterpret_cast<const float2 *>(F.flow) + (size_t)y * F.width + x);
+        int x0, y0;
+        float ax, ay;
+        split_axis(f.x, x, F.width, x0, ax);
+        split_axis(f.y, y, F.height, y0, ay);
+        const int x1 = min(x0 + 1, F.width - 1), y1 = min(y0 + 1, F.height - 1);
+        const float bx = 1.f - ax, by = 1.f - ay;
+        const size_t o00 = (size_t)y0 * F.pitch + x0, o01 = (size_t)y0 * F.pitch + x1;
+        const size_t o10 = (size_t)y1 * F.pitch + x0, o11 = (size_t)y1 * F.pitch + x1;
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            const float *R = F.ref[p];
+            pred[p] = bx * by * __ldg(R + o00) + ax * by * __ldg(R + o01) + bx * ay * __ldg(R + o10) +
+                      ax * ay * __ldg(R + o11);
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < 3; ++p) pred[p] = F.src_lo[p] ? __fadd_rn(F.src_hi[p][i], F.src_lo[p][i]) : F.src_hi[p][i];
+    }
+    int q[3];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        float v = pred[p];
+        if (F.r[p]) v += F.r[p][i];
+        v = fminf(fmaxf(v, p == 0 ? 0.f : -255.f), 255.f);
+        F.ref_out[p][i] = v;
+        q[p] = __float2int_rd(v + 0.5f);
+    }
+    // inverse RCT: G = Y - floor((U + V) / 4), R = V + G, B = U + G
+    const int G = q[0] - ((q[1] + q[2]) >> 2);  // arithmetic shift: floor for negative sums
+    const int c[3] = {q[2] + G, G, q[1] + G};
+#pragma unroll
+    for (int p = 0; p < 3; ++p) F.out[p][(size_t)y * F.out_pitch[p] + x] = (uint8_t)min(max(c[p], 0), 255);
+}
+
 }  // namespace
+
+cudaError_t launch_rct(const RctFrame &f, cudaStream_t st)
+{
+    const dim3 grid((f.width + kTW - 1) / kTW, (f.height + kTH - 1) / kTH);
+    rct_kernel<<<grid, kTW * kTH, 0, st>>>(f);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_warp_add(WarpJobs &J, cudaStream_t st)
 {

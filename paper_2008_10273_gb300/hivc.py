@@ -51,7 +51,7 @@ class CoefResidual(ctypes.Structure):
 
 class IFrame(ctypes.Structure):
     _fields_ = [("y", Points), ("c_n", c_i32), ("c_idx", c_vp), ("cb_val", c_vp), ("cr_val", c_vp),
-                ("res", ctypes.POINTER(Residual))]
+                ("res", ctypes.POINTER(Residual)), ("cu_val", c_vp), ("cv_val", c_vp)]
 
 
 class PFrame(ctypes.Structure):
@@ -200,6 +200,7 @@ class Decoder:
                  iframe_tol: float = 1e-8, max_cycles: int = 40, precision: int = 0,
                  stream=None, timing: bool = False, cond_threshold: float = 1e6, op: int = 0):
         cfg = config_default()
+        # chroma: False/0 grey, True/1 4:2:0, 2 the 4:4:4 RCT colour path
         cfg.width, cfg.height, cfg.chroma, cfg.block = width, height, int(chroma), block
         cfg.iframe_tol, cfg.max_cycles, cfg.precision = iframe_tol, max_cycles, precision
         cfg.cond_threshold = cond_threshold
@@ -207,6 +208,7 @@ class Decoder:
         cfg.stream = _stream_handle(stream)
         self.cfg = cfg
         self.width, self.height, self.chroma, self.block = width, height, bool(chroma), block
+        self.rct = int(chroma) == 2
         h = c_vp()
         check(lib().hivc_decoder_create(ctypes.byref(cfg), ctypes.byref(h)), "hivc_decoder_create")
         self.handle = h
@@ -237,6 +239,7 @@ class Decoder:
     @staticmethod
     def bytes_for(width, height, chroma=True, block=16) -> int:
         cfg = config_default()
+        # chroma: False/0 grey, True/1 4:2:0, 2 the 4:4:4 RCT colour path
         cfg.width, cfg.height, cfg.chroma, cfg.block = width, height, int(chroma), block
         return int(lib().hivc_decoder_bytes(ctypes.byref(cfg)))
 
@@ -256,8 +259,12 @@ class Decoder:
         if self.chroma:
             s.c_n = int(f["c_idx"].numel())
             s.c_idx = _ptr(f["c_idx"])
-            s.cb_val = _ptr(f["cb_val"])
-            s.cr_val = _ptr(f["cr_val"])
+            if "cu_val" in f:  # 4:4:4 RCT planes: signed chroma values
+                s.cu_val = _ptr(f["cu_val"])
+                s.cv_val = _ptr(f["cv_val"])
+            else:
+                s.cb_val = _ptr(f["cb_val"])
+                s.cr_val = _ptr(f["cr_val"])
         if f.get("res") is not None:
             arr = (Residual * 3)(*[residual_struct(*r) for r in f["res"]])
             s.res = ctypes.cast(arr, ctypes.POINTER(Residual))
@@ -408,7 +415,9 @@ def block_residual_coef(width, height, block, op, res, r, flags=None, stream=Non
 
 def device_iframe(ifr, device="cuda"):
     f = {"y_idx": _dev(ifr.y_idx, device), "y_val": _dev(ifr.y_val, device)}
-    if ifr.chroma:
+    if ifr.chroma and getattr(ifr, "rct", False):
+        f.update(c_idx=_dev(ifr.c_idx, device), cu_val=_dev(ifr.cb_val, device), cv_val=_dev(ifr.cr_val, device))
+    elif ifr.chroma:
         f.update(c_idx=_dev(ifr.c_idx, device), cb_val=_dev(ifr.cb_val, device), cr_val=_dev(ifr.cr_val, device))
     if ifr.res is not None:
         f["res"] = [device_residual(r, device) for r in ifr.res]
@@ -427,10 +436,13 @@ def device_pframe(pfr, device="cuda", shared_chroma: bool = True):
 
 
 def alloc_out(width, height, chroma=True, device="cuda"):
+    """uint8 output planes: Y (+ Cb, Cr at 4:2:0); chroma=2: R, G, B."""
     import torch
 
     planes = [torch.empty((height, width), dtype=torch.uint8, device=device)]
-    if chroma:
+    if int(chroma) == 2:
+        planes += [torch.empty((height, width), dtype=torch.uint8, device=device) for _ in range(2)]
+    elif chroma:
         cw, ch = (width + 1) // 2, (height + 1) // 2
         planes += [torch.empty((ch, cw), dtype=torch.uint8, device=device) for _ in range(2)]
     return planes
