@@ -61,7 +61,7 @@ def parse_args(argv=None):
     p.add_argument("--no-serve", action="store_true", help="skip the multi-stream serving measurement")
     p.add_argument("--serve-gop", type=int, default=30, help="frames per stream in the serving measurement")
     p.add_argument("--no-next", action="store_true",
-                   help="skip the coefficient-mode and biharmonic measurements")
+                   help="skip the coefficient-mode, biharmonic and 4:4:4 colour-path measurements")
     p.add_argument("--path", choices=["batch", "plain"], default="batch",
                    help="decode path of the timed steps: one hivc_decode_batch call per GOP (inter frames "
                         "share coefficient launches), or one call per frame")
@@ -212,8 +212,9 @@ def serve_measurement(a, gops=None):
 
 def next_rows_measurement(a, gop):
     """The paper's coefficient mode (inter frames that carry dead-zone
-    quantised Green's coefficients and constants: evaluation only) and the
-    biharmonic operator, on the FullHD GOP workload.  Device time with CUDA
+    quantised Green's coefficients and constants: evaluation only), the
+    biharmonic operator and the 4:4:4 colour path of the reversible colour
+    transform, on FullHD GOP workloads.  Device time with CUDA
     events, L2 flushed between steps."""
     import torch
 
@@ -294,6 +295,40 @@ def next_rows_measurement(a, gop):
                 ms.append(e0.elapsed_time(e1))
         st = dec.sync()
     dec.close()
+    # the 4:4:4 colour path (RCT planes, R, G, B output): a GOP of its own
+    rg = make_gop(a.seed + 2, W, H, n_frames=a.frames, with_sources=False, rct=True)
+    rdec = hivc.Decoder(W, H, chroma=2, iframe_tol=a.iframe_tol, stream=stream)
+    rout = hivc.alloc_out(W, H, chroma=2)
+    rfr = [("i", hivc.device_iframe(rg.iframe))] + [("p", hivc.device_pframe(p)) for p in rg.pframes]
+    with torch.cuda.stream(stream):
+        rms = []
+        for k in range(warm + steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hivc.decode_batch([rdec] * len(rfr), rfr, [rout] * len(rfr))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= warm:
+                rms.append(e0.elapsed_time(e1))
+        rdec.sync()
+        hivc.lib().hivc_decoder_set_timing(rdec.handle, 1)
+        flush.zero_()
+        hivc.decode_batch([rdec] * len(rfr), rfr, [rout] * len(rfr))
+        rst = rdec.sync()
+        hivc.lib().hivc_decoder_set_timing(rdec.handle, 0)
+    rdec.close()
+    # RCT pixel kernel per inter frame: flow 8 B, three references 12 B, three
+    # residual planes 12 B, three new references 12 B, R, G, B 3 B per pixel
+    rk_ms = rst.kernel_ms[6] / max(1, rst.kernel_launches[6])
+    rk_bytes = W * H * (8 + 12 + 12 + 12 + 3)
+    res["rct_444"] = {
+        "value": len(rfr) * steps * px / (sum(rms) / 1e3), "unit": UNIT, "ms_per_step": sum(rms) / steps,
+        "pixel_kernel": {"bound": "hbm", "avg_launch_ms": rk_ms, "algorithmic_bytes_per_launch": rk_bytes,
+                         "achieved": rk_bytes / (rk_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": rk_bytes / (rk_ms / 1e3) / 1e9 / hbm},
+        "workload": f"FullHD GOP of {a.frames} frames on the colour path of the reversible colour transform "
+                    "(4:4:4 Y, U, V; chroma mask at half the luma density; R, G, B output), batched call"}
     res["biharmonic"] = {"value": len(frames) * steps * px / (sum(ms) / 1e3), "unit": UNIT,
                          "ms_per_step": sum(ms) / steps, "max_cond_bound": float(st.max_cond),
                          "fp64_blocks": int(st.fp64_blocks),

@@ -807,6 +807,32 @@ cudaError_t launch_rf_frame(hivc_decoder *d, const hivc_pframe *f, const hivc_ou
     return e;
 }
 
+// The unstaged pixel kernel of a frame whose residual planes (plane
+// pitches) were evaluated before, into the next reference buffer.
+cudaError_t launch_rq_frame(hivc_decoder *d, const float *flow, const hivc_out *out, float *r0, float *r1, float *r2)
+{
+    const int nxt = d->cur ^ 1;
+    FusedFrame F{};
+    F.flow = flow;
+    float *const rf[3] = {r0, r1, r2};
+    for (int p = 0; p < d->np; ++p) {
+        F.ref[p] = d->ref[d->cur][p];
+        F.ref_out[p] = d->ref[nxt][p];
+        F.ref_pitch[p] = d->pg[p].pitch;
+        F.out[p] = out->plane[p];
+        F.out_pitch[p] = out->pitch[p];
+        F.rfield[p] = rf[p];
+        F.rfield_pitch[p] = d->pg[p].pitch;
+    }
+    F.width = d->cfg.width;
+    F.height = d->cfg.height;
+    F.chroma = d->cfg.chroma;
+    Timed t(d, 4);
+    const cudaError_t e = launch_pframe_rq(F, d->stream, !d->timing);
+    t.done(1);
+    return e;
+}
+
 hivc_status hivc_decode_pframe(hivc_decoder *d, const hivc_pframe *f, const hivc_out *out)
 {
     if (!d || !f || !out_ok(d, out) || !f->flow) return HIVC_E_INVALID;
@@ -924,15 +950,11 @@ hivc_status hivc_decode_pframe_coef(hivc_decoder *d, const hivc_pframe_coef *f, 
         t.done(1);
     }
     if (e != cudaSuccess) return HIVC_E_CUDA;
-    // warp + residual + pack: the staged kernel where its tensor maps can be
-    // made, else the plain one
-    hivc_pframe pf{};
-    pf.flow = f->flow;
+    // warp + residual + pack
     const int nxt = d->cur ^ 1;
     if (d->cfg.chroma == 2) {
         if (launch_rct_frame(d, f->flow, nullptr, nullptr, true, out) != cudaSuccess) return HIVC_E_CUDA;
-    } else if (d->maps_ok && d->cfg.width % 2 == 0 &&
-        launch_rf_frame(d, &pf, out, d->rfield[0], d->rfield[1], d->rfield[2]) == cudaSuccess) {
+    } else if (launch_rq_frame(d, f->flow, out, d->rfield[0], d->rfield[1], d->rfield[2]) == cudaSuccess) {
         // launched
     } else {
         cudaGetLastError();
@@ -1028,7 +1050,7 @@ hivc_status decode_inter_run(hivc_decoder *d, const hivc_frame *frames, const hi
 {
     if (cudaSetDevice(d->device) != cudaSuccess) return HIVC_E_CUDA;
     const size_t nf = ks.size();
-    const bool rf = d->maps_ok && d->cfg.width % 2 == 0;
+    const bool rf = true;  // residual planes + the unstaged pixel kernel
     // pool layout: per frame and plane a256(4 n_points) + a256(4 nblocks)
     // (+ the residual plane, h x pitch floats), then the K > 32 scratch of
     // the largest coefficient launch
@@ -1109,7 +1131,8 @@ hivc_status decode_inter_run(hivc_decoder *d, const hivc_frame *frames, const hi
     for (size_t k = 0; k < nf; ++k) {
         const hivc_pframe *f = frames[ks[k]].p;
         cudaError_t e;
-        e = rf ? launch_rf_frame(d, f, &outs[ks[k]], at(k, 0, 2), at(k, 1, 2), at(k, 2, 2)) : cudaErrorInvalidValue;
+        e = rf ? launch_rq_frame(d, f->flow, &outs[ks[k]], at(k, 0, 2), at(k, 1, 2), at(k, 2, 2))
+               : cudaErrorInvalidValue;
         // no residual planes, or a flow no tensor map describes (unaligned):
         // the fused kernel evaluates the residual from the coefficients; the
         // reference is the previous frame's output, so no early copies

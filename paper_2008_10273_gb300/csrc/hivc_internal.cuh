@@ -143,6 +143,10 @@ cudaError_t launch_pframe_fused(FusedFrame &f, const FusedMaps *maps, uint32_t *
 // evaluated before (F.rfield, maps->rf): the fused kernel without its
 // residual phase.  maps must hold the flow, reference and residual maps.
 cudaError_t launch_pframe_rf(FusedFrame &f, const FusedMaps &maps, uint32_t *flags, cudaStream_t st, bool pdl);
+// The same pixel work without staging: one thread per luma quad and its
+// co-sited chroma pixels, every sample from global memory (F.flow, ref,
+// ref_out, out, rfield and their pitches; the same results).
+cudaError_t launch_pframe_rq(const FusedFrame &f, cudaStream_t st, bool pdl);
 // 2-D float32 tensor map (no swizzle, zero fill); false if not encodable
 bool encode_map_2d(CUtensorMap *m, const void *base, uint64_t w, uint64_t h, uint64_t row_bytes, uint32_t box_w,
                    uint32_t box_h);

@@ -120,11 +120,14 @@ __device__ __noinline__ float sample_global(const float *__restrict__ R, int pit
     float ax, ay;
     const int x0 = split_axis(dx, x, W, ax), y0 = split_axis(dy, y, H, ay);
     const int ox = min(x0 + 1, W - 1) - x0, oyn = min(y0 + 1, H - 1) - y0;
-    const float bx = 1.f - ax, by = 1.f - ay;
     const float *g = R + (size_t)y0 * pitch + x0;
     const float r00 = __ldg(g), r01 = __ldg(g + ox), r10 = __ldg(g + (size_t)oyn * pitch),
                 r11 = __ldg(g + (size_t)oyn * pitch + ox);
-    return bx * by * r00 + ax * by * r01 + bx * ay * r10 + ax * ay * r11;
+    // the same interpolation steps as tile_lerp, so that a sample gives the
+    // same value whichever path it takes
+    const float top = fmaf(ax, r01 - r00, r00);
+    const float bot = fmaf(ax, r11 - r10, r10);
+    return fmaf(ay, bot - top, top);
 }
 
 // bilinear sample from a staged tile at tile coordinates (lx + fx, ly + fy),
@@ -481,9 +484,13 @@ __device__ __forceinline__ void phase_c(const PixelCtx &c, const ResView &R, con
             put_pixel(pred, R.y[ly * R.yp + x], c.oy0 + (size_t)gy * c.yp + gx, c.uy0 + (size_t)gy * c.op + gx);
         }
         if (CHROMA) {
-            float sx = f[0].x + f[1].x, sy = f[0].y + f[1].y;
-            sx += __shfl_xor_sync(0xffffffffu, sx, 1);
-            sy += __shfl_xor_sync(0xffffffffu, sy, 1);
+            // row sums first, as in the quad paths: ((f00 + f01) + (f10 + f11)),
+            // vectors outside the plane are zero
+            const float r0x = f[0].x + __shfl_xor_sync(0xffffffffu, f[0].x, 1);
+            const float r0y = f[0].y + __shfl_xor_sync(0xffffffffu, f[0].y, 1);
+            const float r1x = f[1].x + __shfl_xor_sync(0xffffffffu, f[1].x, 1);
+            const float r1y = f[1].y + __shfl_xor_sync(0xffffffffu, f[1].y, 1);
+            const float sx = r0x + r1x, sy = r0y + r1y;
             int n = 4;
             if (!FAST) {
                 n = (int)in[0] + (int)in[1];
@@ -822,6 +829,74 @@ __global__ void __launch_bounds__(kThreads, 4) pframe_rf_kernel(const __grid_con
     if (pend1 >= 0) mbar_wait(&bar[1], ph1);
 }
 
+// ---- residual-plane variant without staging ------------------------------
+// Thread (qx, qy) takes the luma quad at columns 2 qx, 2 qx + 1 and rows
+// 2 qy, 2 qy + 1 and, with chroma, the co-sited pixel (qx, qy) of Cb and
+// Cr, all from global memory (the reference samples of neighbouring
+// threads share cache lines).  The arithmetic is the staged kernels':
+// split_axis, the lerp steps of tile_lerp, the chroma flow
+// ((f00 + f01) + (f10 + f11)) / 8 over the in-plane vectors, put_pixel.
+__device__ __forceinline__ float lerp_global(const float *__restrict__ R, int pitch, int W, int H, int x, int y,
+                                             float dx, float dy)
+{
+    float ax, ay;
+    const int x0 = split_axis(dx, x, W, ax), y0 = split_axis(dy, y, H, ay);
+    const int ox = min(x0 + 1, W - 1) - x0, oyn = min(y0 + 1, H - 1) - y0;
+    const float *g = R + (size_t)y0 * pitch + x0;
+    const float r00 = __ldg(g), r01 = __ldg(g + ox), r10 = __ldg(g + (size_t)oyn * pitch),
+                r11 = __ldg(g + (size_t)oyn * pitch + ox);
+    const float top = fmaf(ax, r01 - r00, r00);
+    const float bot = fmaf(ax, r11 - r10, r10);
+    return fmaf(ay, bot - top, top);
+}
+
+constexpr int kQX = 32, kQY = 4;  // quads per CTA: 32 x 4 (128 threads)
+
+template <bool CHROMA>
+__global__ void __launch_bounds__(kQX *kQY) pframe_rq_kernel(const __grid_constant__ FusedFrame F)
+{
+    // the preceding launch wrote the residual planes or the references
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int qx = blockIdx.x * kQX + threadIdx.x, qy = blockIdx.y * kQY + threadIdx.y;
+    const int W = F.width, H = F.height;
+    const int x0 = 2 * qx, y0 = 2 * qy;
+    if (x0 >= W || y0 >= H) return;
+    const bool in1 = x0 + 1 < W, inr = y0 + 1 < H;
+    const float2 *fl = reinterpret_cast<const float2 *>(F.flow);
+    float2 f[4];  // (row, column): 00, 01, 10, 11; zero outside the plane
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+        const bool rin = rr == 0 || inr;
+        const float2 *row = fl + (size_t)(y0 + rr) * W + x0;
+        f[2 * rr] = rin ? __ldg(row) : make_float2(0.f, 0.f);
+        f[2 * rr + 1] = (rin && in1) ? __ldg(row + 1) : make_float2(0.f, 0.f);
+    }
+    const int yp = F.ref_pitch[0], op = F.out_pitch[0], rp = F.rfield_pitch[0];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int x = x0 + (q & 1), y = y0 + (q >> 1);
+        if (!((q & 1) == 0 || in1) || !((q >> 1) == 0 || inr)) continue;
+        const float pred = lerp_global(F.ref[0], yp, W, H, x, y, f[q].x, f[q].y);
+        put_pixel(pred, __ldg(F.rfield[0] + (size_t)y * rp + x), F.ref_out[0] + (size_t)y * yp + x,
+                  F.out[0] + (size_t)y * op + x);
+    }
+    if (CHROMA) {
+        const int cw = (W + 1) / 2, ch = (H + 1) / 2;
+        if (qx >= cw || qy >= ch) return;
+        const int n = (1 + (int)in1) * (1 + (int)inr);
+        const float sc = n == 4 ? 0.125f : (n == 2 ? 0.25f : 0.5f);
+        const float dx = ((f[0].x + f[1].x) + (f[2].x + f[3].x)) * sc;
+        const float dy = ((f[0].y + f[1].y) + (f[2].y + f[3].y)) * sc;
+#pragma unroll
+        for (int pl = 1; pl < 3; ++pl) {
+            const float pred = lerp_global(F.ref[pl], F.ref_pitch[pl], cw, ch, qx, qy, dx, dy);
+            put_pixel(pred, __ldg(F.rfield[pl] + (size_t)qy * F.rfield_pitch[pl] + qx),
+                      F.ref_out[pl] + (size_t)qy * F.ref_pitch[pl] + qx, F.out[pl] + (size_t)qy * F.out_pitch[pl] + qx);
+        }
+    }
+}
+
 template <class Kern>
 int occupancy(Kern k, size_t smem)
 {
@@ -866,6 +941,22 @@ cudaError_t fused_init()
                                   (int)kRfSmem)) != cudaSuccess)
         return e;
     return cudaFuncSetAttribute(pframe_rf_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRfSmem);
+}
+
+cudaError_t launch_pframe_rq(const FusedFrame &F, cudaStream_t st, bool pdl)
+{
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    const int qw = (F.width + 1) / 2, qh = (F.height + 1) / 2;
+    cfg.gridDim = dim3((qw + kQX - 1) / kQX, (qh + kQY - 1) / kQY);
+    cfg.blockDim = dim3(kQX, kQY);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    if (F.chroma) return cudaLaunchKernelEx(&cfg, pframe_rq_kernel<true>, F);
+    return cudaLaunchKernelEx(&cfg, pframe_rq_kernel<false>, F);
 }
 
 cudaError_t launch_pframe_rf(FusedFrame &F, const FusedMaps &maps, uint32_t *flags, cudaStream_t st, bool pdl)
