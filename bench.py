@@ -511,14 +511,12 @@ def main(argv=None):
     nblk = sum(int(r.n_blocks) for r in gop.pframes[0].res)
     bytes_per_launch = {
         # family: (kernel source, algorithmic bytes per launch)
-        # fused inter: flow 8 B + reference 4 B + new reference 4 B + uint8 1 B
-        # per luma pixel, 4 + 4 + 1 B per chroma pixel (flow read once), and
-        # the residual data (block_ptr, pos, val, coefficients, constants)
-        7: ("k_pframe.cu", W * H * (8 + 4 + 4 + 1) + 2 * cw * ch * (4 + 4 + 1) + npts * (1 + 2 + 4) + nblk * 8),
-        # inter pixels from residual planes (batches): as the fused kernel,
-        # with the residual plane read (4 B per pixel) for the block data
+        # inter pixels: flow 8 B + reference 4 B + residual plane 4 B + new
+        # reference 4 B + uint8 1 B per luma pixel, 4 + 4 + 4 + 1 B per chroma
+        # pixel (the chroma flow comes from the luma flow read once)
         4: ("k_pframe.cu", W * H * (8 + 4 + 4 + 4 + 1) + 2 * cw * ch * (4 + 4 + 4 + 1)),
-        6: ("k_warp.cu", W * H * (8 + 4 + 4 + 4 + 1) + 2 * cw * ch * (4 + 4 + 4 + 1)),
+        # intra output: the solution hi/lo 8 B, new reference 4 B, uint8 1 B per pixel
+        6: ("k_warp.cu", (W * H + 2 * cw * ch) * (8 + 4 + 1)),
         # one SOR launch (4 sweeps): correction in/out 8 B, residual 4 B, mask 1 B per pixel
         1: ("k_intra.cu", (W * H + 2 * cw * ch) * (4 + 4 + 1 + 4)),
         # residual + update: hi/lo in 8 B, hi/lo out 8 B, correction 4 B, mask 1 B, residual 4 B

@@ -187,8 +187,8 @@ typedef struct {
     /* per kernel family: accumulated device time (ms, CUDA events, only
        when timing is on) and launch counts since the previous sync:
        0 intra setup, 1 intra sweeps, 2 intra residual, 3 block coefficients,
-       4 inter pixels from residual planes (batches), 5 block evaluate,
-       6 warp/add/pack, 7 fused inter */
+       4 inter pixels (warp + residual + pack), 5 block evaluate,
+       6 intra output and the 4:4:4 colour path's pixels, 7 unused */
     float kernel_ms[HIVC_STAT_KERNELS];
     int32_t kernel_launches[HIVC_STAT_KERNELS];
 } hivc_stats;

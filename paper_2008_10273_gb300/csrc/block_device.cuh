@@ -1,5 +1,5 @@
-// Device building blocks of the block residual (Sec. 2.2, Eqs. 2-3) shared
-// by the block kernels (k_block.cu) and the fused inter-frame kernel.
+// Device building blocks of the block residual (Sec. 2.2, Eqs. 2-3) used by
+// the block kernels (k_block.cu).
 //
 // G of every block shape w x h (w, h <= 16) is stored whole: row i of the
 // N x N matrix (N = w h, pixel index y w + x) at tab.G + tab.goff[shape] +
@@ -218,52 +218,6 @@ __device__ __forceinline__ bool warp_block_coef_smem(const float *__restrict__ G
     c0 = b0;
     c1 = b1;
     return spd;
-}
-
-// r = a + sum_j c_j G[p_j, :] over one block by one warp: lane l covers the
-// block pixels 8l .. 8l+7 (index y w + x).  The points' indices and
-// coefficients come from shared arrays (K entries).  out(x, y, v0, v1) is
-// called for every pixel of the block.
-template <bool TWO, class Out>
-__device__ __forceinline__ void warp_block_eval(const float *__restrict__ G, int w, int N, int K,
-                                                const unsigned char *pj, const float *cj0, const float *cj1, float a0,
-                                                float a1, int lane, Out out)
-{
-    const int rl = g_rowlen(N);
-    const int i0 = 8 * lane;
-    if (i0 >= N) return;
-    float r0[8], r1[8];
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-        r0[t] = a0;
-        r1[t] = a1;
-    }
-#pragma unroll 4
-    for (int j = 0; j < K; ++j) {
-        const float4 *row = reinterpret_cast<const float4 *>(G + pj[j] * rl + i0);
-        const float4 lo = __ldg(row), hi = __ldg(row + 1);
-        const float c = cj0[j];
-        r0[0] = fmaf(c, lo.x, r0[0]); r0[1] = fmaf(c, lo.y, r0[1]);
-        r0[2] = fmaf(c, lo.z, r0[2]); r0[3] = fmaf(c, lo.w, r0[3]);
-        r0[4] = fmaf(c, hi.x, r0[4]); r0[5] = fmaf(c, hi.y, r0[5]);
-        r0[6] = fmaf(c, hi.z, r0[6]); r0[7] = fmaf(c, hi.w, r0[7]);
-        if (TWO) {
-            const float d = cj1[j];
-            r1[0] = fmaf(d, lo.x, r1[0]); r1[1] = fmaf(d, lo.y, r1[1]);
-            r1[2] = fmaf(d, lo.z, r1[2]); r1[3] = fmaf(d, lo.w, r1[3]);
-            r1[4] = fmaf(d, hi.x, r1[4]); r1[5] = fmaf(d, hi.y, r1[5]);
-            r1[6] = fmaf(d, hi.z, r1[6]); r1[7] = fmaf(d, hi.w, r1[7]);
-        }
-    }
-    int y = i0 / w, x = i0 - y * w;
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-        if (i0 + t < N) out(x, y, r0[t], r1[t]);
-        if (++x == w) {
-            x = 0;
-            ++y;
-        }
-    }
 }
 
 }  // namespace hivc

@@ -1,7 +1,7 @@
 // C ABI of libhivc: decoder objects, argument checks, the intra correction
 // loop and the inter-frame pipeline.  Every step of the decode runs in the
-// kernels of k_intra.cu, k_block.cu and k_warp.cu; this file only
-// allocates, validates and launches.
+// kernels of k_intra.cu, k_block.cu, k_pframe.cu and k_warp.cu; this file
+// only allocates, validates and launches.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -10,36 +10,11 @@
 #include <thread>
 #include <vector>
 
-#include <cudaTypedefs.h>
-
 #include <mutex>
 
 #include "hivc_internal.cuh"
 
 using namespace hivc;
-
-bool hivc::encode_map_2d(CUtensorMap *m, const void *base, uint64_t w, uint64_t h, uint64_t row_bytes, uint32_t box_w,
-                         uint32_t box_h)
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    });
-    if (!fn || ((uintptr_t)base & 15) || (row_bytes & 15) || w < box_w || h < box_h) return false;
-    const cuuint64_t dims[2] = {w, h};
-    const cuuint64_t strides[1] = {row_bytes};
-    const cuuint32_t box[2] = {box_w, box_h};
-    const cuuint32_t es[2] = {1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
 
 namespace {
 
@@ -154,9 +129,6 @@ struct hivc_decoder {
     // coefficients of the inter frames of one batch (grown on demand)
     void *pool = nullptr;
     size_t pool_bytes = 0;
-    // tensor maps of the reference planes (per ping-pong buffer)
-    FusedMaps maps[2]{};
-    bool maps_ok = false;
     // host mirrors
     uint32_t *h_flags = nullptr;
     unsigned int *h_rnorm = nullptr;
@@ -280,7 +252,7 @@ BlockScratch scratch(hivc_decoder *d)
     return BlockScratch{d->flags, d->big, d->big_ranges, d->flags + 1, (float)d->cfg.cond_threshold};
 }
 
-// Unfused block stage: coefficients (+ large blocks), then residual fields.
+// Block stage of one frame: coefficients (+ large blocks), then residual fields.
 hivc_status run_block_residual(hivc_decoder *d, const hivc_residual *res)
 {
     BlockJobs J;
@@ -419,14 +391,6 @@ hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out)
         delete d;
         return HIVC_E_NOMEM;
     }
-    d->maps_ok = true;
-    for (int b = 0; b < 2; ++b)
-        for (int p = 0; p < d->np; ++p) {
-            const PlaneGeom &g = d->pg[p];
-            const uint32_t box = p == 0 ? 48 : 24;
-            d->maps_ok = d->maps_ok && encode_map_2d(&d->maps[b].ref[p], d->ref[b][p], g.w, g.h,
-                                                     (uint64_t)g.pitch * 4, box, box);
-        }
     if (cudaMallocHost(&d->h_flags, 64) != cudaSuccess) {
         m.release();
         delete d;
@@ -734,101 +698,27 @@ hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc
     return converged ? HIVC_OK : HIVC_E_NOT_CONVERGED;
 }
 
-// The fused inter-frame kernel of frame f (coefficients in J's arrays),
-// into the next reference buffer.  early: the reference planes are complete
-// when the kernel starts (the preceding launch is this frame's coefficient
-// kernel), so it may copy its first tiles before waiting for that launch.
-cudaError_t launch_fused_frame(hivc_decoder *d, const hivc_pframe *f, const hivc_out *out, const BlockJobs &J,
-                               bool early)
+// The pixel kernel of a frame whose residual planes (plane pitches) were
+// evaluated before, into the next reference buffer.
+cudaError_t launch_pixels(hivc_decoder *d, const float *flow, const hivc_out *out, float *const *r)
 {
     const int nxt = d->cur ^ 1;
-    FusedFrame F{};
-    F.nblk = J.n;
-    for (int k = 0; k < J.n; ++k) F.bp[k] = J.p[k];
-    F.flow = f->flow;
-    for (int p = 0; p < d->np; ++p) {
-        F.ref[p] = d->ref[d->cur][p];
-        F.ref_out[p] = d->ref[nxt][p];
-        F.ref_pitch[p] = d->pg[p].pitch;
-        F.out[p] = out->plane[p];
-        F.out_pitch[p] = out->pitch[p];
-    }
-    F.width = d->cfg.width;
-    F.height = d->cfg.height;
-    F.chroma = d->cfg.chroma;
-    F.block = d->cfg.block;
-    F.op = d->cfg.op;
-    F.early = early ? 1 : 0;
-    // the TMA variant needs an even luma width (16-byte flow rows) and a
-    // 16-byte aligned flow
-    FusedMaps *maps = nullptr;
-    if (d->maps_ok && d->cfg.width % 2 == 0 &&
-        encode_map_2d(&d->maps[d->cur].flow, f->flow, 2 * (uint64_t)d->cfg.width, d->cfg.height,
-                      8 * (uint64_t)d->cfg.width, 64, 32))
-        maps = &d->maps[d->cur];
-    Timed t(d, 7);
-    const cudaError_t e = launch_pframe_fused(F, maps, d->flags, d->stream, !d->timing);
-    t.done(1);
-    return e;
-}
-
-// The warp + residual + pack kernel of frame f, whose residual planes
-// (plane pitches) were evaluated before, into the next reference buffer.
-cudaError_t launch_rf_frame(hivc_decoder *d, const hivc_pframe *f, const hivc_out *out, float *r0, float *r1,
-                            float *r2)
-{
-    const int nxt = d->cur ^ 1;
-    FusedFrame F{};
-    F.flow = f->flow;
-    float *const rf[3] = {r0, r1, r2};
-    FusedMaps M = d->maps[d->cur];
-    for (int p = 0; p < d->np; ++p) {
-        const PlaneGeom &g = d->pg[p];
-        F.ref[p] = d->ref[d->cur][p];
-        F.ref_out[p] = d->ref[nxt][p];
-        F.ref_pitch[p] = g.pitch;
-        F.out[p] = out->plane[p];
-        F.out_pitch[p] = out->pitch[p];
-        F.rfield[p] = rf[p];
-        F.rfield_pitch[p] = g.pitch;
-        const uint32_t box = p == 0 ? 32 : 16;
-        if (!encode_map_2d(&M.rf[p], rf[p], g.w, g.h, 4 * (uint64_t)g.pitch, box, box)) return cudaErrorInvalidValue;
-    }
-    F.width = d->cfg.width;
-    F.height = d->cfg.height;
-    F.chroma = d->cfg.chroma;
-    F.block = d->cfg.block;
-    if (!encode_map_2d(&M.flow, f->flow, 2 * (uint64_t)d->cfg.width, d->cfg.height, 8 * (uint64_t)d->cfg.width, 64,
-                       32))
-        return cudaErrorInvalidValue;
-    Timed t(d, 4);
-    const cudaError_t e = launch_pframe_rf(F, M, d->flags, d->stream, !d->timing);
-    t.done(1);
-    return e;
-}
-
-// The unstaged pixel kernel of a frame whose residual planes (plane
-// pitches) were evaluated before, into the next reference buffer.
-cudaError_t launch_rq_frame(hivc_decoder *d, const float *flow, const hivc_out *out, float *r0, float *r1, float *r2)
-{
-    const int nxt = d->cur ^ 1;
-    FusedFrame F{};
+    InterFrame F{};
     F.flow = flow;
-    float *const rf[3] = {r0, r1, r2};
     for (int p = 0; p < d->np; ++p) {
         F.ref[p] = d->ref[d->cur][p];
         F.ref_out[p] = d->ref[nxt][p];
         F.ref_pitch[p] = d->pg[p].pitch;
         F.out[p] = out->plane[p];
         F.out_pitch[p] = out->pitch[p];
-        F.rfield[p] = rf[p];
-        F.rfield_pitch[p] = d->pg[p].pitch;
+        F.r[p] = r[p];
+        F.r_pitch[p] = d->pg[p].pitch;
     }
     F.width = d->cfg.width;
     F.height = d->cfg.height;
     F.chroma = d->cfg.chroma;
     Timed t(d, 4);
-    const cudaError_t e = launch_pframe_rq(F, d->stream, !d->timing);
+    const cudaError_t e = launch_pframe(F, d->stream, !d->timing);
     t.done(1);
     return e;
 }
@@ -841,57 +731,13 @@ hivc_status hivc_decode_pframe(hivc_decoder *d, const hivc_pframe *f, const hivc
     if (!d->has_ref) return HIVC_E_NO_REFERENCE;
     if (cudaSetDevice(d->device) != cudaSuccess) return HIVC_E_CUDA;
     const int nxt = d->cur ^ 1;
-    cudaError_t e;
-    if (d->cfg.chroma == 2) {
-        // 4:4:4 colour path: block stage into residual planes, then the
-        // RCT pixel kernel
-        hivc_status s = run_block_residual(d, f->res);
-        if (s != HIVC_OK) return s;
-        if (launch_rct_frame(d, f->flow, nullptr, nullptr, true, out) != cudaSuccess) return HIVC_E_CUDA;
-    } else if (fused_supported(d->cfg.block)) {
-        // two launches: the coefficients of every block, then one fused
-        // kernel for evaluation + warp + add + pack
-        BlockJobs J;
-        hivc_status s = make_block_jobs(d, f->res, J);
-        if (s != HIVC_OK) return s;
-        {
-            Timed t(d, 3);
-            int l = 0;
-            e = launch_block_coef(J, scratch(d), d->stream, &l);
-            t.done(1);
-        }
-        if (e != cudaSuccess) return HIVC_E_CUDA;
-        if ((e = launch_fused_frame(d, f, out, J, true)) != cudaSuccess) return HIVC_E_CUDA;
-    } else {
-        hivc_status s = run_block_residual(d, f->res);
-        if (s != HIVC_OK) return s;
-        WarpJobs W{};
-        W.n = d->np;
-        for (int p = 0; p < d->np; ++p) {
-            WarpPlane &P = W.p[p];
-            const PlaneGeom &g = d->pg[p];
-            P.ref = d->ref[d->cur][p];
-            P.ref_pitch = g.pitch;
-            P.flow = f->flow;
-            P.flow_w = d->pg[0].w;
-            P.flow_h = d->pg[0].h;
-            P.chroma_flow = p > 0 ? 1 : 0;
-            P.r = d->rfield[p];
-            P.r_pitch = g.pitch;
-            P.ref_out = d->ref[nxt][p];
-            P.ref_out_pitch = g.pitch;
-            P.out = out->plane[p];
-            P.out_pitch = out->pitch[p];
-            P.width = g.w;
-            P.height = g.h;
-        }
-        {
-            Timed t(d, 6);
-            e = launch_warp_add(W, d->stream);
-            t.done(1);
-        }
-        if (e != cudaSuccess) return HIVC_E_CUDA;
-    }
+    // three launches: coefficients (Eq. 2), residual planes (Eq. 3), then
+    // warp + add + pack (the 4:4:4 colour path: its RCT kernel)
+    hivc_status s = run_block_residual(d, f->res);
+    if (s != HIVC_OK) return s;
+    const cudaError_t e = d->cfg.chroma == 2 ? launch_rct_frame(d, f->flow, nullptr, nullptr, true, out)
+                                             : launch_pixels(d, f->flow, out, d->rfield);
+    if (e != cudaSuccess) return HIVC_E_CUDA;
     d->cur = nxt;
     d->st.frames += 1;
     return HIVC_OK;
@@ -952,37 +798,9 @@ hivc_status hivc_decode_pframe_coef(hivc_decoder *d, const hivc_pframe_coef *f, 
     if (e != cudaSuccess) return HIVC_E_CUDA;
     // warp + residual + pack
     const int nxt = d->cur ^ 1;
-    if (d->cfg.chroma == 2) {
-        if (launch_rct_frame(d, f->flow, nullptr, nullptr, true, out) != cudaSuccess) return HIVC_E_CUDA;
-    } else if (launch_rq_frame(d, f->flow, out, d->rfield[0], d->rfield[1], d->rfield[2]) == cudaSuccess) {
-        // launched
-    } else {
-        cudaGetLastError();
-        WarpJobs W{};
-        W.n = d->np;
-        for (int p = 0; p < d->np; ++p) {
-            WarpPlane &P = W.p[p];
-            const PlaneGeom &g = d->pg[p];
-            P.ref = d->ref[d->cur][p];
-            P.ref_pitch = g.pitch;
-            P.flow = f->flow;
-            P.flow_w = d->pg[0].w;
-            P.flow_h = d->pg[0].h;
-            P.chroma_flow = p > 0 ? 1 : 0;
-            P.r = d->rfield[p];
-            P.r_pitch = g.pitch;
-            P.ref_out = d->ref[nxt][p];
-            P.ref_out_pitch = g.pitch;
-            P.out = out->plane[p];
-            P.out_pitch = out->pitch[p];
-            P.width = g.w;
-            P.height = g.h;
-        }
-        Timed t(d, 6);
-        e = launch_warp_add(W, d->stream);
-        t.done(1);
-        if (e != cudaSuccess) return HIVC_E_CUDA;
-    }
+    e = d->cfg.chroma == 2 ? launch_rct_frame(d, f->flow, nullptr, nullptr, true, out)
+                           : launch_pixels(d, f->flow, out, d->rfield);
+    if (e != cudaSuccess) return HIVC_E_CUDA;
     d->cur = nxt;
     d->st.frames += 1;
     return HIVC_OK;
@@ -1042,17 +860,14 @@ hivc_status ensure_pool(hivc_decoder *d, size_t bytes)
 // stage over several frames at once: per up to kMaxJobs block jobs (8 FullHD
 // 4:2:0 frames) one coefficient launch and one evaluation launch into each
 // frame's residual planes, all in the batch pool; then per frame the
-// warp + residual + pack kernel with the residual tiles staged by TMA.
-// Where the flow cannot be described by a tensor map (odd width) the fused
-// kernel evaluates the residual itself.  Every frame has been checked.
+// warp + residual + pack kernel.  Every frame has been checked.
 hivc_status decode_inter_run(hivc_decoder *d, const hivc_frame *frames, const hivc_out *outs,
                              const std::vector<int> &ks)
 {
     if (cudaSetDevice(d->device) != cudaSuccess) return HIVC_E_CUDA;
     const size_t nf = ks.size();
-    const bool rf = true;  // residual planes + the unstaged pixel kernel
     // pool layout: per frame and plane a256(4 n_points) + a256(4 nblocks)
-    // (+ the residual plane, h x pitch floats), then the K > 32 scratch of
+    // + the residual plane (h x pitch floats), then the K > 32 scratch of
     // the largest coefficient launch
     std::vector<size_t> off(nf * 3 * 3);
     size_t bytes = 0;
@@ -1064,7 +879,7 @@ hivc_status decode_inter_run(hivc_decoder *d, const hivc_frame *frames, const hi
             off[(k * 3 + p) * 3 + 1] = bytes;
             bytes += a256(4 * (size_t)g.nblocks);
             off[(k * 3 + p) * 3 + 2] = bytes;
-            if (rf) bytes += a256(4 * (size_t)g.h * g.pitch);
+            bytes += a256(4 * (size_t)g.h * g.pitch);
         }
     int fblocks = 0;
     for (int p = 0; p < d->np; ++p) fblocks += d->pg[p].nblocks;
@@ -1092,7 +907,7 @@ hivc_status decode_inter_run(hivc_decoder *d, const hivc_frame *frames, const hi
         for (int p = 0; p < 3; ++p) {
             coef[p] = at(k, p, 0);
             acoef[p] = at(k, p, 1);
-            rfield[p] = rf ? at(k, p, 2) : nullptr;
+            rfield[p] = at(k, p, 2);
         }
         if ((s = make_block_jobs(d, frames[ks[k]].p->res, jobs[k], coef, acoef, rfield)) != HIVC_OK) return s;
     }
@@ -1109,7 +924,7 @@ hivc_status decode_inter_run(hivc_decoder *d, const hivc_frame *frames, const hi
             e = launch_block_coef(J, S, d->stream, &l);
             t.done(l);
         }
-        if (e == cudaSuccess && rf) {
+        if (e == cudaSuccess) {
             Timed t(d, 5);
             e = launch_block_eval(J, d->flags, d->stream);
             t.done(1);
@@ -1129,14 +944,8 @@ hivc_status decode_inter_run(hivc_decoder *d, const hivc_frame *frames, const hi
     }
     if (flush() != cudaSuccess) return HIVC_E_CUDA;
     for (size_t k = 0; k < nf; ++k) {
-        const hivc_pframe *f = frames[ks[k]].p;
-        cudaError_t e;
-        e = rf ? launch_rq_frame(d, f->flow, &outs[ks[k]], at(k, 0, 2), at(k, 1, 2), at(k, 2, 2))
-               : cudaErrorInvalidValue;
-        // no residual planes, or a flow no tensor map describes (unaligned):
-        // the fused kernel evaluates the residual from the coefficients; the
-        // reference is the previous frame's output, so no early copies
-        if (e == cudaErrorInvalidValue) e = launch_fused_frame(d, f, &outs[ks[k]], jobs[k], false);
+        float *const r[3] = {at(k, 0, 2), at(k, 1, 2), at(k, 2, 2)};
+        const cudaError_t e = launch_pixels(d, frames[ks[k]].p->flow, &outs[ks[k]], r);
         if (e != cudaSuccess) return HIVC_E_CUDA;
         d->cur ^= 1;
         d->st.frames += 1;
@@ -1166,7 +975,7 @@ hivc_status decode_own_frames(hivc_decoder *d, const hivc_frame *frames, const h
         std::vector<int> run;
         while (i < ks.size() && frames[ks[i]].type == 1) run.push_back(ks[i++]);
         hivc_status s = HIVC_OK;
-        if (fused_supported(d->cfg.block) && d->cfg.chroma != 2) {
+        if (d->cfg.chroma != 2) {
             s = decode_inter_run(d, frames, outs, run);
         } else {
             for (int k : run)

@@ -2,7 +2,6 @@
 // Host launchers are plain C++ functions (no relocatable device code).
 #pragma once
 
-#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -108,48 +107,22 @@ cudaError_t launch_block_coef(const BlockJobs &jobs, const BlockScratch &s, cuda
 // dequantised indices and the transmitted constants, with no overwrite.
 cudaError_t launch_block_eval(const BlockJobs &jobs, uint32_t *flags, cudaStream_t st);
 
-// One inter frame for the fused kernel: residual blocks, flow, references.
-struct FusedFrame {
-    BlockPlane bp[3];  // Y; Cb (+ Cr when paired); Cr when not paired
-    int32_t nblk;      // 1 (grey), 2 (paired chroma) or 3
+// One inter frame for the pixel kernel: flow, references, the residual
+// planes the block kernels evaluated, outputs.
+struct InterFrame {
     const float *flow;
     const float *ref[3];
     float *ref_out[3];
     uint8_t *out[3];
-    int32_t ref_pitch[3], out_pitch[3];  // ref_out shares ref_pitch
-    int32_t width, height, chroma, block, op;
-    int32_t early;      // 1: the references are complete at launch (copies may start at once)
-    int32_t nmbx, nmb;  // filled by the launcher
-    // residual-field variant: the evaluated residual planes (pitch floats)
-    const float *rfield[3];
-    int32_t rfield_pitch[3];
+    const float *r[3];
+    int32_t ref_pitch[3], out_pitch[3], r_pitch[3];  // ref_out shares ref_pitch
+    int32_t width, height, chroma;                   // chroma: 0 grey, 1 4:2:0
 };
 
-// Tensor maps of the TMA variant: the frame's flow (2W x H floats, box
-// 64 x 32) and the three reference planes (box 48 x 48 luma, 24 x 24
-// chroma).
-struct FusedMaps {
-    CUtensorMap flow;
-    CUtensorMap ref[3];
-    CUtensorMap rf[3];  // residual fields (box 32 x 32 luma, 16 x 16 chroma)
-};
-
-bool fused_supported(int block);
-cudaError_t fused_init();  // once per device
-// maps == nullptr: the variant with global loads only.  pdl: launch as a
-// programmatic dependent of the previous kernel in the stream.
-cudaError_t launch_pframe_fused(FusedFrame &f, const FusedMaps *maps, uint32_t *flags, cudaStream_t st, bool pdl);
-// Warp + residual + clamp + pack of a frame whose residual planes were
-// evaluated before (F.rfield, maps->rf): the fused kernel without its
-// residual phase.  maps must hold the flow, reference and residual maps.
-cudaError_t launch_pframe_rf(FusedFrame &f, const FusedMaps &maps, uint32_t *flags, cudaStream_t st, bool pdl);
-// The same pixel work without staging: one thread per luma quad and its
-// co-sited chroma pixels, every sample from global memory (F.flow, ref,
-// ref_out, out, rfield and their pitches; the same results).
-cudaError_t launch_pframe_rq(const FusedFrame &f, cudaStream_t st, bool pdl);
-// 2-D float32 tensor map (no swizzle, zero fill); false if not encodable
-bool encode_map_2d(CUtensorMap *m, const void *base, uint64_t w, uint64_t h, uint64_t row_bytes, uint32_t box_w,
-                   uint32_t box_h);
+// Warp + residual + clamp + pack, one thread per luma quad and its co-sited
+// chroma pixels.  pdl: launch as a programmatic dependent of the previous
+// kernel in the stream.
+cudaError_t launch_pframe(const InterFrame &f, cudaStream_t st, bool pdl);
 
 // ---------------------------------------------------------------------------
 // warp + add + pack (Sec. 2, 2.3)

@@ -21,8 +21,7 @@
 // Kernels: the coefficient stage (two blocks per warp: in its 16-lane
 // halves when both have K <= 16, else one after the other with all lanes
 // for K <= 32; blocks with K > 32 by the kernel's last CTA, packed Cholesky
-// in global scratch) and the evaluation into a residual field.  The fused inter-frame kernel
-// (k_pframe.cu) evaluates with the same routine.
+// in global scratch) and the evaluation into a residual field.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -115,8 +114,8 @@ __device__ __forceinline__ SegBlock seg_block(const BlockJobs &J, int gb)
 
 __device__ __forceinline__ int seg_k(const SegBlock &b) { return (b.g.bad || b.g.K > kWarpK) ? 0 : b.g.K; }
 
-// A block whose positions are bad gets a = NaN: the evaluation (here and
-// in the fused inter-frame kernel) then takes its residual as zero.
+// A block whose positions are bad gets a = NaN: the evaluation then takes
+// its residual as zero.
 __device__ __forceinline__ void mark_bad(const BlockPlane &P, int lb)
 {
     P.acoef[0][lb] = __int_as_float(0x7fc00000);
@@ -548,8 +547,8 @@ __global__ void __launch_bounds__(kCoefThreads, 3) block_coef_kernel(const __gri
     __shared__ double redd[kCoefThreads / 32];
     __shared__ double w64[tri(kTK) + 3 * kTK];
     __shared__ int s_large[kRange], s_nlarge, s_bad;
-    // the fused kernel that follows may start its prologue (tensor-memory
-    // copies of flow and references) now; it waits for this grid's results
+    // the kernel that follows may be scheduled now; it waits for this grid's
+    // results
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int nrange = block_ranges(J.total_blocks);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -772,7 +771,6 @@ cudaError_t ensure_block_tables()
         t.amax = op == 1 ? 64.f : 8.f;
     }
     if ((e = cudaMemcpyToSymbol(d_goff, goff.data(), goff.size() * sizeof(int))) != cudaSuccess) return e;
-    if ((e = fused_init()) != cudaSuccess) return e;
     if ((e = intra_init()) != cudaSuccess) return e;
     g_tab_devices |= 1ull << dev;
     return cudaSuccess;
