@@ -64,7 +64,7 @@ def stream_budget_bytes(s: Stream, per_stream: int) -> int:
     nb = lambda a, b: -(-a // s.block) * -(-b // s.block)
     blocks = nb(w, h) + (2 * nb(cw, ch) if s.chroma else 0)
     per_frame = 4 * (planes + w * h + (cw * ch * 2 if s.chroma else 0) + 2 * blocks)
-    scratch = -(-(16 * blocks) // 128) * 33405 * 4
+    scratch = -(-(16 * blocks) // 128) * 33408 * 4
     return hivc.Decoder.bytes_for(w, h, s.chroma, s.block) + per_stream * per_frame + scratch
 
 
@@ -157,12 +157,14 @@ class Server:
         active: List[Stream] = []
         self.admit_log = []
         created0 = self.created
+        max_active = 0
         t0 = time.perf_counter()
         calls = 0
         while waiting or active:
             now = time.perf_counter() - t0
             while waiting and self._try_admit(waiting[0], now):
                 active.append(waiting.pop(0))
+            max_active = max(max_active, len(active))
             if waiting and not active:
                 raise ValueError(f"stream {waiting[0].name} needs more than the whole budget "
                                  f"({stream_budget_bytes(waiting[0], self.per_stream)} > {self.budget} bytes)")
@@ -219,4 +221,5 @@ class Server:
         q = lambda f: lat[min(len(lat) - 1, int(round(f * (len(lat) - 1))))]
         return {"frames": len(lat), "wall_s": wall, "fullhd_fps": px / (1920 * 1080) / wall,
                 "p50_ms": 1e3 * q(0.5), "p99_ms": 1e3 * q(0.99), "calls": calls,
-                "admitted": list(self.admit_log), "decoders_created": self.created - created0}
+                "admitted": list(self.admit_log), "decoders_created": self.created - created0,
+                "max_active": max_active}
