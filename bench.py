@@ -61,7 +61,7 @@ def parse_args(argv=None):
     p.add_argument("--no-serve", action="store_true", help="skip the multi-stream serving measurement")
     p.add_argument("--serve-gop", type=int, default=30, help="frames per stream in the serving measurement")
     p.add_argument("--no-next", action="store_true",
-                   help="skip the coefficient-mode, biharmonic and 4:4:4 colour-path measurements")
+                   help="skip the coefficient-mode, biharmonic, 4:4:4 colour-path and batching measurements")
     p.add_argument("--path", choices=["batch", "plain"], default="batch",
                    help="decode path of the timed steps: one hivc_decode_batch call per GOP (inter frames "
                         "share coefficient launches), or one call per frame")
@@ -339,6 +339,67 @@ def next_rows_measurement(a, gop):
                          "ms_per_step": sum(ms) / steps, "max_cond_bound": float(st.max_cond),
                          "fp64_blocks": int(st.fp64_blocks),
                          "workload": "the headline GOP decoded with the biharmonic operator (op 1), batched"}
+    return res
+
+
+def batching_measurement(a):
+    """Four FullHD 4:2:0 inter frames decoded by one hivc_decode_batch call
+    (one coefficient launch and one evaluation launch over all their
+    blocks, then a pixel kernel per frame) against four single-frame calls.
+    Luma residual blocks: Poisson(8) points clipped to 0..48, 10% empty,
+    30% of the full blocks on 8 shared layouts."""
+    import torch
+
+    from paper_2008_10273_gb300 import hivc
+    from workload import make_gop
+
+    W, H = a.width, a.height
+    g = make_gop(a.seed + 3, W, H, n_frames=5, with_sources=False,
+                 residual_kw={"kmax": 48, "empty_frac": 0.1, "shared_layouts": 8, "shared_frac": 0.3})
+    stream = torch.cuda.Stream()
+    dec = hivc.Decoder(W, H, chroma=True, iframe_tol=a.iframe_tol, stream=stream)
+    out = hivc.alloc_out(W, H)
+    ifr = hivc.device_iframe(g.iframe)
+    pfs = [hivc.device_pframe(p) for p in g.pframes]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    res = {}
+    steps, warm = 10, 3
+    for name, batched in (("batched", True), ("plain", False)):
+        ms = []
+        with torch.cuda.stream(stream):
+            for k in range(warm + steps):
+                dec.decode_iframe(ifr, out)
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if batched:
+                    hivc.decode_batch([dec] * 4, [("p", f) for f in pfs], [out] * 4)
+                else:
+                    for f in pfs:
+                        dec.decode_pframe(f, out)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if k >= warm:
+                    ms.append(e0.elapsed_time(e1))
+            dec.sync()
+            hivc.lib().hivc_decoder_set_timing(dec.handle, 1)
+            dec.decode_iframe(ifr, out)
+            dec.sync()
+            if batched:
+                hivc.decode_batch([dec] * 4, [("p", f) for f in pfs], [out] * 4)
+            else:
+                for f in pfs:
+                    dec.decode_pframe(f, out)
+            st = dec.sync()
+            hivc.lib().hivc_decoder_set_timing(dec.handle, 0)
+        fam = {hivc.KERNEL_FAMILIES[i]: {"ms": st.kernel_ms[i], "launches": st.kernel_launches[i]}
+               for i in (3, 4, 5) if st.kernel_launches[i]}
+        res[name] = {"value": 4 * steps * (W * H / FULLHD_PX) / (sum(ms) / 1e3), "unit": "FullHD inter frames/s",
+                     "ms_per_4_frames": sum(ms) / steps, "kernels": fam}
+    dec.close()
+    nb = sum(int(r.n_blocks) for r in g.pframes[0].res[:1]) * 4
+    res["workload"] = (f"4 FullHD 4:2:0 inter frames, {nb} luma blocks of 16x16 (Poisson(8) points clipped "
+                       "to 0..48, 10% empty, 30% of the full blocks on 8 shared layouts), L2 flushed before each")
     return res
 
 
@@ -627,6 +688,7 @@ def main(argv=None):
     if rank == 0 and world == 1 and not a.no_serve:
         served = serve_measurement(a, {(W, H): gop} if (W, H) == (1920, 1080) and a.serve_gop == nfr else None)
     nxt = next_rows_measurement(a, gop) if (rank == 0 and world == 1 and not a.no_next) else None
+    batching = batching_measurement(a) if (rank == 0 and world == 1 and not a.no_next) else None
 
     if rank == 0:
         pf = sorted(frame_ms[i] for i in range(len(frame_ms)) if i % nfr != 0)
@@ -654,6 +716,7 @@ def main(argv=None):
             "cpu_baseline": cpu,
             "serving": served,
             "next_rows": nxt,
+            "batching": batching,
         }
         print(json.dumps(line), flush=True)
     dec.close()

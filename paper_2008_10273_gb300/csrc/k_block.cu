@@ -530,8 +530,8 @@ __device__ __forceinline__ void warp_path(const BlockJobs &J, const BlockTables 
 }
 
 // Coefficient stage.  The grid has two halves over the same ranges of
-// kRange blocks.  Thread-path CTA c: thread t takes block kRange c + t and
-// solves it when K <= 12.  Warp-path CTA c, at the same time: its warps
+// kRange blocks.  Thread-path CTA nrange + c: thread t takes block
+// kRange c + t and solves it when K <= 12.  Warp-path CTA c: its warps
 // solve the range's blocks with 12 < K <= 32, then the whole CTA those with
 // K > 32, one after the other in the range's scratch slot.  Blocks whose
 // condition bound exceeds the threshold are re-solved in FP64 by their CTA
@@ -554,8 +554,10 @@ __global__ void __launch_bounds__(kCoefThreads, 3) block_coef_kernel(const __gri
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) s_nlarge = 0;
     __syncthreads();
-    if ((int)blockIdx.x < nrange) {
-        const int gb = blockIdx.x * kRange + threadIdx.x;
+    // the heavier warp-path CTAs come first in the grid, so that the light
+    // thread-path CTAs fill the tail
+    if ((int)blockIdx.x >= nrange) {
+        const int gb = (blockIdx.x - nrange) * kRange + threadIdx.x;
         float kappa = 0.f;
         if (gb < J.total_blocks) {
             const BlockPlane &P = J.p[find_job(J, gb)];
@@ -576,7 +578,7 @@ __global__ void __launch_bounds__(kCoefThreads, 3) block_coef_kernel(const __gri
         for (int i = 0; i < n; ++i) cta_block(J, tab, S, s_large[i], nullptr, w64, s_p, red, redd, &s_bad);
         return;
     }
-    const int range = blockIdx.x - nrange;
+    const int range = blockIdx.x;
     const int gb0 = range * kRange + warp * 32;
     if (gb0 < J.total_blocks) warp_path(J, tab, S, gb0, lane, lts[warp], s_large, &s_nlarge);
     __syncthreads();
