@@ -73,6 +73,15 @@ def lib():
             L.oracle_green_matrix_op.restype = None
             L.oracle_block_residual_op.argtypes = [c_int, c_int, c_int, c_int, u32p, u8p, i16p, dp]
             L.oracle_block_residual_op.restype = c_int
+            u32p_ = ctypes.POINTER(ctypes.c_uint32)
+            lp = ctypes.POINTER(ctypes.c_long)
+            L.oracle_tree_leaves.argtypes = [c_int, c_int, c_int, c_int, u32p_, ctypes.c_long, ctypes.c_long, ip,
+                                             c_int, ip, lp]
+            L.oracle_tree_leaves.restype = c_int
+            L.oracle_flow_from_tree.argtypes = [c_int, c_int, u32p_, ctypes.c_long, f32p, c_int, f32p]
+            L.oracle_flow_from_tree.restype = c_int
+            L.oracle_masks_from_trees.argtypes = [c_int, c_int, c_int, u32p_, u32p_, u32p_, u8p, ctypes.c_long]
+            L.oracle_masks_from_trees.restype = c_int
             L.oracle_inverse_rct.argtypes = [c_int, dp, dp, dp, u8p]
             L.oracle_inverse_rct.restype = None
             L.oracle_dequantise.argtypes = [c_int, c_double, c_double]
@@ -218,6 +227,48 @@ def to_uint8(recon: np.ndarray) -> np.ndarray:
 # ----------------------------------------------------------------------------
 # frames and GOPs (Sec. 2: prediction + correction, closed loop)
 # ----------------------------------------------------------------------------
+def tree_leaves(width: int, height: int, bits: np.ndarray, nbits: int) -> np.ndarray:
+    """Leaves (x0, y0, w, h), breadth-first, of a subdivision tree over a
+    width x height rectangle (Sec. 2.3; bit format in hivc_oracle.c)."""
+    words = np.ascontiguousarray(bits, np.uint32)
+    rects = np.empty((width * height, 4), np.int32)
+    nl, used = ctypes.c_int(0), ctypes.c_long(0)
+    st = lib().oracle_tree_leaves(0, 0, width, height, _p(words, ctypes.c_uint32), 0, int(nbits),
+                                  _p(rects, ctypes.c_int), width * height, ctypes.byref(nl), ctypes.byref(used))
+    if st != OK or used.value != nbits:
+        raise ValueError("invalid subdivision tree")
+    return rects[:nl.value].copy()
+
+
+def flow_from_tree(width: int, height: int, bits: np.ndarray, nbits: int, values: np.ndarray) -> np.ndarray:
+    """Dense flow (float32 [H, W, 2]) from a subdivision tree and one
+    vector per leaf (Sec. 2.3: each region gets its average value)."""
+    words = np.ascontiguousarray(bits, np.uint32)
+    vals = np.ascontiguousarray(values, np.float32).reshape(-1)
+    flow = np.zeros((height, width, 2), np.float32)
+    st = lib().oracle_flow_from_tree(width, height, _p(words, ctypes.c_uint32), int(nbits), _p(vals, ctypes.c_float),
+                                     vals.size // 2, _p(flow, ctypes.c_float))
+    if st != OK:
+        raise ValueError("invalid subdivision tree")
+    return flow
+
+
+def masks_from_trees(width: int, height: int, block: int, bits: np.ndarray, tree_ptr: np.ndarray):
+    """Residual mask positions (block_ptr, pos) from one subdivision tree
+    per block (Sec. 2.3)."""
+    words = np.ascontiguousarray(bits, np.uint32)
+    tp = np.ascontiguousarray(tree_ptr, np.uint32)
+    nb = tp.size - 1
+    bp = np.zeros(nb + 1, np.uint32)
+    cap = width * height
+    pos = np.zeros(max(cap, 1), np.uint8)
+    st = lib().oracle_masks_from_trees(width, height, block, _p(words, ctypes.c_uint32), _p(tp, ctypes.c_uint32),
+                                       _p(bp, ctypes.c_uint32), _p(pos, ctypes.c_uint8), cap)
+    if st != OK:
+        raise ValueError("invalid subdivision trees")
+    return bp, pos[:int(bp[-1])].copy()
+
+
 def inverse_rct(y: np.ndarray, u: np.ndarray, v: np.ndarray) -> List[np.ndarray]:
     """R, G, B uint8 planes from reconstructed RCT planes (Sec. 2.3)."""
     h, w = y.shape

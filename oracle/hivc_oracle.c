@@ -505,3 +505,122 @@ void oracle_inverse_rct(int n, const double *y, const double *u, const double *v
         }
     }
 }
+
+/*
+ * Side information by rectangular subdivision (Sec. 2.3: the BOFF is coded
+ * as regions of a rectangular subdivision, each with its average value;
+ * the mask points of every residual block come from a subdivision as
+ * well).  The paper takes the subdivision from its reference [SPMEWB14]
+ * and gives no bit format; the reading used here:
+ *   - a node is a rectangle; a split halves its longer side (w >= h: the
+ *     x side), the first part ceil(len/2), the second floor(len/2) long;
+ *   - one bit per node in breadth-first order, 1 = split; a one-pixel
+ *     node must carry 0; bits are packed LSB-first in 32-bit words;
+ *   - leaves are numbered in breadth-first order;
+ *   - a mask point is the centre pixel of its leaf,
+ *     (x0 + (w-1)/2, y0 + (h-1)/2).
+ */
+static int tree_bit(const uint32_t *bits, long i) { return (int)((bits[i >> 5] >> (i & 31)) & 1u); }
+
+/* Leaves (x0, y0, w, h per leaf, breadth-first) of the tree over the
+   rectangle (x0, y0, w, h) whose bits are [b0, b0 + nbits).  Returns the
+   number of bits used through *used, or ORACLE_INVALID (a split of a
+   one-pixel node, bits exhausted, more than max_leaves leaves). */
+int oracle_tree_leaves(int x0, int y0, int w, int h, const uint32_t *bits, long b0, long nbits, int *rects,
+                       int max_leaves, int *n_leaves, long *used)
+{
+    int cap = 2 * w * h + 2;
+    int *q = (int *)malloc((size_t)cap * 4 * sizeof(int));
+    int head = 0, tail = 0, nl = 0, status = ORACLE_OK;
+    long i = 0;
+    q[0] = x0; q[1] = y0; q[2] = w; q[3] = h;
+    tail = 1;
+    while (head < tail) {
+        const int *r = q + 4 * head++;
+        if (i >= nbits) { status = ORACLE_INVALID; break; }
+        const int split = tree_bit(bits, b0 + i++);
+        if (!split) {
+            if (nl >= max_leaves) { status = ORACLE_INVALID; break; }
+            for (int k = 0; k < 4; ++k) rects[4 * nl + k] = r[k];
+            ++nl;
+            continue;
+        }
+        if (r[2] * r[3] < 2 || tail + 2 > cap) { status = ORACLE_INVALID; break; }
+        int *a = q + 4 * tail, *b = q + 4 * (tail + 1);
+        if (r[2] >= r[3]) {
+            const int w1 = r[2] - r[2] / 2;
+            a[0] = r[0]; a[1] = r[1]; a[2] = w1; a[3] = r[3];
+            b[0] = r[0] + w1; b[1] = r[1]; b[2] = r[2] / 2; b[3] = r[3];
+        } else {
+            const int h1 = r[3] - r[3] / 2;
+            a[0] = r[0]; a[1] = r[1]; a[2] = r[2]; a[3] = h1;
+            b[0] = r[0]; b[1] = r[1] + h1; b[2] = r[2]; b[3] = r[3] / 2;
+        }
+        tail += 2;
+    }
+    free(q);
+    *n_leaves = nl;
+    *used = i;
+    return status;
+}
+
+/* Dense backward flow (H x W x 2) from a subdivision tree over the plane
+   and one (dx, dy) per leaf in breadth-first order.  The tree must use all
+   nbits bits. */
+int oracle_flow_from_tree(int W, int H, const uint32_t *bits, long nbits, const float *values, int n_values,
+                          float *flow)
+{
+    int *rects = (int *)malloc((size_t)W * H * 4 * sizeof(int));
+    int nl = 0;
+    long used = 0;
+    int st = oracle_tree_leaves(0, 0, W, H, bits, 0, nbits, rects, W * H, &nl, &used);
+    if (st == ORACLE_OK && (used != nbits || nl != n_values)) st = ORACLE_INVALID;
+    if (st == ORACLE_OK)
+        for (int l = 0; l < nl; ++l) {
+            const int *r = rects + 4 * l;
+            for (int y = r[1]; y < r[1] + r[3]; ++y)
+                for (int x = r[0]; x < r[0] + r[2]; ++x) {
+                    flow[2 * ((size_t)y * W + x)] = values[2 * l];
+                    flow[2 * ((size_t)y * W + x) + 1] = values[2 * l + 1];
+                }
+        }
+    free(rects);
+    return st;
+}
+
+static int cmp_u8(const void *a, const void *b) { return (int)*(const uint8_t *)a - (int)*(const uint8_t *)b; }
+
+/* Residual mask positions of a plane's B x B blocks (raster order, edge
+   blocks cropped) from one subdivision tree per block: block b's tree uses
+   bits [tree_ptr[b], tree_ptr[b+1]) exactly.  Output as the residual data
+   takes it: block_ptr (nblocks + 1) and pos (ly w + lx, increasing within
+   a block), at most max_points points. */
+int oracle_masks_from_trees(int W, int H, int B, const uint32_t *bits, const uint32_t *tree_ptr, uint32_t *block_ptr,
+                            uint8_t *pos, long max_points)
+{
+    if (W < 1 || H < 1 || B < 1 || B > 16) return ORACLE_INVALID;
+    const int nbx = (W + B - 1) / B, nby = (H + B - 1) / B;
+    int rects[4 * 256];
+    long n = 0;
+    block_ptr[0] = 0;
+    for (int b = 0; b < nbx * nby; ++b) {
+        const int bx = b % nbx, by = b / nbx;
+        const int w = (W - bx * B) < B ? (W - bx * B) : B;
+        const int h = (H - by * B) < B ? (H - by * B) : B;
+        if (tree_ptr[b + 1] < tree_ptr[b]) return ORACLE_INVALID;
+        const long nb = (long)tree_ptr[b + 1] - tree_ptr[b];
+        int nl = 0;
+        long used = 0;
+        if (oracle_tree_leaves(0, 0, w, h, bits, tree_ptr[b], nb, rects, 256, &nl, &used) != ORACLE_OK || used != nb)
+            return ORACLE_INVALID;
+        if (n + nl > max_points) return ORACLE_INVALID;
+        for (int l = 0; l < nl; ++l) {
+            const int *r = rects + 4 * l;
+            pos[n + l] = (uint8_t)((r[1] + (r[3] - 1) / 2) * w + r[0] + (r[2] - 1) / 2);
+        }
+        qsort(pos + n, (size_t)nl, 1, cmp_u8);
+        n += nl;
+        block_ptr[b + 1] = (uint32_t)n;
+    }
+    return ORACLE_OK;
+}

@@ -531,3 +531,78 @@ def make_gop(
         if with_sources:
             sources.append(render_frame(t))
     return Gop(width, height, chroma, block, ifr, pframes, sources, rct)
+
+
+# ----------------------------------------------------------------------------
+# side information: rectangular subdivision trees (Sec. 2.3)
+# ----------------------------------------------------------------------------
+def _pack_bits(bits: List[int]) -> np.ndarray:
+    """LSB-first in 32-bit words."""
+    n = len(bits)
+    words = np.zeros(max(1, (n + 31) // 32), np.uint32)
+    if n:
+        b = np.asarray(bits, np.uint64)
+        idx = np.arange(n)
+        np.bitwise_or.at(words, idx >> 5, (b << (idx & 31).astype(np.uint64)).astype(np.uint32))
+    return words
+
+
+def _random_tree_bits(rng, w: int, h: int, n_leaves: int) -> List[int]:
+    """Breadth-first split bits of a random subdivision of a w x h rectangle
+    with about n_leaves leaves: random leaves (of two or more pixels) are
+    split until the count is reached.  A split halves the longer side (the
+    first part is the larger one); the format is the decoder's input, the
+    tree itself is not kept."""
+    children = {}
+    rect = {0: (w, h)}
+    leaves = [0]
+    nxt = 1
+    target = max(1, min(int(n_leaves), w * h))
+    while len(leaves) < target:
+        cand = [i for i, l in enumerate(leaves) if rect[l][0] * rect[l][1] >= 2]
+        if not cand:
+            break
+        k = cand[int(rng.integers(len(cand)))]
+        node = leaves.pop(k)
+        cw, ch = rect[node]
+        if cw >= ch:
+            rect[nxt], rect[nxt + 1] = (cw - cw // 2, ch), (cw // 2, ch)
+        else:
+            rect[nxt], rect[nxt + 1] = (cw, ch - ch // 2), (cw, ch // 2)
+        children[node] = (nxt, nxt + 1)
+        leaves += [nxt, nxt + 1]
+        nxt += 2
+    bits, queue, qi = [], [0], 0
+    while qi < len(queue):
+        node = queue[qi]
+        qi += 1
+        if node in children:
+            bits.append(1)
+            queue += list(children[node])
+        else:
+            bits.append(0)
+    return bits
+
+
+def make_flow_tree(rng, width: int, height: int, n_leaves: int = 400, vmax: float = 4.0):
+    """A piecewise-constant backward flow as its side information: the
+    breadth-first split bits of a random subdivision (packed words, bit
+    count) and one (dx, dy) per leaf, uniform in [-vmax, vmax]."""
+    bits = _random_tree_bits(rng, width, height, n_leaves)
+    n = sum(1 for b in bits if b == 0)
+    values = rng.uniform(-vmax, vmax, size=(n, 2)).astype(np.float32)
+    return _pack_bits(bits), len(bits), values
+
+
+def make_block_trees(rng, width: int, height: int, block: int, lam: float = 8.0):
+    """Residual mask side information: per block of the plane (raster
+    order, edge blocks cropped) the split bits of a random subdivision with
+    Poisson(lam) leaves (at least one), concatenated; tree_ptr[b] is the
+    first bit of block b."""
+    nbx, nby, w, h = block_grid(width, height, block)
+    allbits, ptr = [], [0]
+    for b in range(nbx * nby):
+        k = max(1, int(rng.poisson(lam)))
+        allbits += _random_tree_bits(rng, int(w[b]), int(h[b]), k)
+        ptr.append(len(allbits))
+    return _pack_bits(allbits), len(allbits), np.asarray(ptr, np.uint32)
