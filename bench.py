@@ -219,9 +219,11 @@ def serve_measurement(a, gops=None):
 def next_rows_measurement(a, gop):
     """The paper's coefficient mode (inter frames that carry dead-zone
     quantised Green's coefficients and constants: evaluation only), the
-    biharmonic operator and the 4:4:4 colour path of the reversible colour
-    transform, on FullHD GOP workloads.  Device time with CUDA
-    events, L2 flushed between steps."""
+    biharmonic operator, the 4:4:4 colour path of the reversible colour
+    transform and the side information by rectangular subdivision, on
+    FullHD workloads.  Device time with CUDA events, L2 flushed between
+    steps."""
+    import numpy as np
     import torch
 
     from paper_2008_10273_gb300 import hivc
@@ -335,6 +337,43 @@ def next_rows_measurement(a, gop):
                          "frac": rk_bytes / (rk_ms / 1e3) / 1e9 / hbm},
         "workload": f"FullHD GOP of {a.frames} frames on the colour path of the reversible colour transform "
                     "(4:4:4 Y, U, V; chroma mask at half the luma density; R, G, B output), batched call"}
+    # side information (rectangular subdivision): a FullHD flow from its
+    # tree (400 regions) and the mask points of the three planes' blocks
+    from workload.synth import make_block_trees, make_flow_tree
+
+    srng = np.random.default_rng(a.seed + 4)
+    fw, fnb, fv = make_flow_tree(srng, W, H, 400)
+    trees = [make_block_trees(srng, pw, ph, 16, lam) for pw, ph, lam in ((W, H, 8.0), (cw, ch, 4.0), (cw, ch, 4.0))]
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x).view(np.int32) if x.dtype == np.uint32
+                                     else np.ascontiguousarray(x)).cuda()
+    fw_d, fv_d = dev(fw), dev(fv)
+    flow_d = torch.empty((H, W, 2), dtype=torch.float32, device="cuda")
+    ws = torch.empty(hivc.lib().hivc_flow_from_tree_workspace_bytes(fnb), dtype=torch.uint8, device="cuda")
+    tr_d = [(dev(t[0]), dev(t[2]), torch.empty(len(t[2]), dtype=torch.int32, device="cuda"),
+             torch.empty(pw * ph, dtype=torch.uint8, device="cuda"), pw, ph)
+            for t, (pw, ph) in zip(trees, ((W, H), (cw, ch), (cw, ch)))]
+    sflags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    with torch.cuda.stream(stream):
+        sms, fms = [], []
+        for k in range(warm + steps):
+            flush.zero_()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            hivc.flow_from_tree(W, H, fw_d, fnb, fv_d, flow_d, flags=sflags, workspace=ws, stream=stream)
+            e1.record(stream)
+            for wb, tp, bp, pos, pw, ph in tr_d:
+                hivc.masks_from_trees(pw, ph, 16, wb, tp, bp, pos, flags=sflags, stream=stream)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            if k >= warm:
+                sms.append(e0.elapsed_time(e2))
+                fms.append(e0.elapsed_time(e1))
+    res["side_info"] = {"value": steps / (sum(sms) / 1e3) * px, "unit": "FullHD frames/s",
+                        "ms_per_frame": sum(sms) / steps, "flow_ms": sum(fms) / steps,
+                        "masks_ms": (sum(sms) - sum(fms)) / steps, "flags": int(sflags.item()),
+                        "workload": f"a FullHD backward flow from its subdivision tree ({len(fv)} regions, {fnb} bits) "
+                                    "and the residual mask points of the 4:2:0 planes' 16x16 blocks from one tree "
+                                    "per block (Poisson(8) luma / Poisson(4) chroma leaves)"}
     res["biharmonic"] = {"value": len(frames) * steps * px / (sum(ms) / 1e3), "unit": UNIT,
                          "ms_per_step": sum(ms) / steps, "max_cond_bound": float(st.max_cond),
                          "fp64_blocks": int(st.fp64_blocks),

@@ -318,6 +318,43 @@ hivc_status hivc_warp(int32_t width, int32_t height, const float *ref, int32_t r
                       const float *flow, int32_t flow_width, int32_t flow_height,
                       int32_t chroma_flow, float *pred, int32_t pred_pitch, void *stream);
 
+/*
+ * Side information by rectangular subdivision (Sec. 2.3: the backward flow
+ * is coded as the regions of a rectangular subdivision, each with its
+ * average value; the mask points of every residual block come from a
+ * subdivision as well).  The paper gives no bit format; this one is:
+ *   - a node is a rectangle; a split halves its longer side (w >= h: the x
+ *     side), the first part ceil(len/2) long, the second floor(len/2);
+ *   - one bit per node in breadth-first order, 1 = split; a one-pixel node
+ *     must carry 0; bits are packed LSB-first in 32-bit words;
+ *   - leaves are numbered in breadth-first order;
+ *   - a mask point is the centre pixel (x0 + (w-1)/2, y0 + (h-1)/2) of its
+ *     leaf.
+ * All arrays are device memory; calls are asynchronous on stream (NULL =
+ * default).  Bad trees are reported by ORing bit 8 into *flags (device
+ * word; NULL: not reported) and leave their output unwritten.
+ */
+
+/* Device scratch hivc_flow_from_tree needs for a tree of nbits bits. */
+size_t hivc_flow_from_tree_workspace_bytes(int64_t nbits);
+
+/* Dense backward flow (height x width x 2 floats, the inter frames' flow
+   layout) from the plane's tree (nbits bits, all of them used) and one
+   (dx, dy) per leaf (n_values = the number of leaves). */
+hivc_status hivc_flow_from_tree(int32_t width, int32_t height, const uint32_t *bits, int64_t nbits,
+                                const float *values, int32_t n_values, float *flow, void *workspace,
+                                size_t ws_bytes, uint32_t *flags, void *stream);
+
+/* Residual mask points of a width x height plane's block x block blocks
+   (raster order, edge blocks cropped) from one tree per block: block b's
+   tree is bits [tree_ptr[b], tree_ptr[b+1]) (nblocks + 1 entries).
+   Writes block_ptr (nblocks + 1) and pos (ly w + lx, increasing within a
+   block) as hivc_residual takes them; at most max_points points (more:
+   pos is not written and bit 8 is raised). */
+hivc_status hivc_masks_from_trees(int32_t width, int32_t height, int32_t block, const uint32_t *bits,
+                                  const uint32_t *tree_ptr, uint32_t *block_ptr, uint8_t *pos,
+                                  int64_t max_points, uint32_t *flags, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

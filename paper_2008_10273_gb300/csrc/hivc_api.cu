@@ -1171,3 +1171,39 @@ hivc_status hivc_warp(int32_t width, int32_t height, const float *ref, int32_t r
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// side information by rectangular subdivision (Sec. 2.3)
+// ---------------------------------------------------------------------------
+size_t hivc_flow_from_tree_workspace_bytes(int64_t nbits)
+{
+    return nbits < 1 ? 0 : tree_workspace_bytes(nbits);
+}
+
+hivc_status hivc_flow_from_tree(int32_t width, int32_t height, const uint32_t *bits, int64_t nbits,
+                                const float *values, int32_t n_values, float *flow, void *workspace, size_t ws_bytes,
+                                uint32_t *flags, void *stream)
+{
+    if (width < 1 || height < 1 || width > 16384 || height > 16384 || !bits || nbits < 1 ||
+        nbits > 2 * (int64_t)width * height || !values || n_values < 1 || !flow || !workspace ||
+        ws_bytes < tree_workspace_bytes(nbits) || ((uintptr_t)workspace & 15) || ((uintptr_t)flow & 7) ||
+        ((uintptr_t)values & 7))
+        return HIVC_E_INVALID;
+    if (ensure_block_tables() != cudaSuccess) return HIVC_E_CUDA;
+    const cudaError_t e = launch_flow_from_tree(width, height, bits, nbits, values, n_values, flow, workspace, flags,
+                                                block_tables().sms, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? HIVC_OK : HIVC_E_CUDA;
+}
+
+hivc_status hivc_masks_from_trees(int32_t width, int32_t height, int32_t block, const uint32_t *bits,
+                                  const uint32_t *tree_ptr, uint32_t *block_ptr, uint8_t *pos, int64_t max_points,
+                                  uint32_t *flags, void *stream)
+{
+    if (width < 1 || height < 1 || width > 16384 || height > 16384 || block < 1 || block > kMaxB || !bits ||
+        !tree_ptr || !block_ptr || (max_points > 0 && !pos) || max_points < 0)
+        return HIVC_E_INVALID;
+    if (ensure_block_tables() != cudaSuccess) return HIVC_E_CUDA;
+    const cudaError_t e = launch_masks_from_trees(width, height, block, bits, tree_ptr, block_ptr, pos, max_points,
+                                                  flags, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? HIVC_OK : HIVC_E_CUDA;
+}

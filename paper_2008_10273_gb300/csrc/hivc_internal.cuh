@@ -27,6 +27,7 @@ enum : uint32_t {
                               // condition threshold kept its FP32 solution
                               // (K > kF64MaxK: no room for the FP64 system)
     kFlagQ = 1u << 7,         // coefficient index -128 (outside [-127, 127])
+    kFlagTree = 1u << 8,      // a subdivision tree's bits are invalid (side information)
 };
 
 // ---------------------------------------------------------------------------
@@ -169,6 +170,18 @@ struct RctFrame {
 };
 
 cudaError_t launch_rct(const RctFrame &f, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// side information by rectangular subdivision (Sec. 2.3)
+// ---------------------------------------------------------------------------
+size_t tree_workspace_bytes(long long nbits);
+// dense flow from the plane's tree and one vector per leaf
+cudaError_t launch_flow_from_tree(int W, int H, const uint32_t *bits, long long nbits, const float *values,
+                                  int n_values, float *flow, void *ws, uint32_t *flags, int sms, cudaStream_t st);
+// residual mask points (block_ptr, pos) from one tree per block
+cudaError_t launch_masks_from_trees(int W, int H, int B, const uint32_t *bits, const uint32_t *tree_ptr,
+                                    uint32_t *block_ptr, uint8_t *pos, long long max_points, uint32_t *flags,
+                                    cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // intra solve (Sec. 2.1)

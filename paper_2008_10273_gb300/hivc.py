@@ -104,6 +104,9 @@ PROTOTYPES = [
     ("hivc_block_residual_static", c_i32, [c_i32, c_i32, c_i32, ctypes.POINTER(Residual), c_vp, c_i32, c_vp,
                                            c_vp]),
     ("hivc_warp", c_i32, [c_i32, c_i32, c_vp, c_i32, c_vp, c_i32, c_i32, c_i32, c_vp, c_i32, c_vp]),
+    ("hivc_flow_from_tree_workspace_bytes", c_sz, [ctypes.c_int64]),
+    ("hivc_flow_from_tree", c_i32, [c_i32, c_i32, c_vp, ctypes.c_int64, c_vp, c_i32, c_vp, c_vp, c_sz, c_vp, c_vp]),
+    ("hivc_masks_from_trees", c_i32, [c_i32, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, ctypes.c_int64, c_vp, c_vp]),
 ]
 
 
@@ -411,6 +414,27 @@ def block_residual_coef(width, height, block, op, res, r, flags=None, stream=Non
     return check(lib().hivc_block_residual_coef(width, height, block, op, ctypes.byref(c), _ptr(r),
                                                 int(r.stride(0)), _ptr(flags), _stream_handle(stream)),
                  "hivc_block_residual_coef")
+
+
+def flow_from_tree(width, height, bits, nbits, values, flow, flags=None, workspace=None, stream=None):
+    """hivc_flow_from_tree: ``bits`` (int32/uint32 words), ``values``
+    (float32 [n, 2]) and ``flow`` (float32 [H, W, 2]) are CUDA tensors."""
+    need = lib().hivc_flow_from_tree_workspace_bytes(int(nbits))
+    if workspace is None:
+        import torch
+
+        workspace = torch.empty(need, dtype=torch.uint8, device=flow.device)
+    return check(lib().hivc_flow_from_tree(width, height, _ptr(bits), int(nbits), _ptr(values), int(values.shape[0]),
+                                           _ptr(flow), _ptr(workspace), int(workspace.numel()), _ptr(flags),
+                                           _stream_handle(stream)), "hivc_flow_from_tree")
+
+
+def masks_from_trees(width, height, block, bits, tree_ptr, block_ptr, pos, flags=None, stream=None):
+    """hivc_masks_from_trees: block_ptr (nblocks + 1) and pos (capacity =
+    its length) are written."""
+    return check(lib().hivc_masks_from_trees(width, height, block, _ptr(bits), _ptr(tree_ptr), _ptr(block_ptr),
+                                             _ptr(pos), int(pos.numel()), _ptr(flags), _stream_handle(stream)),
+                 "hivc_masks_from_trees")
 
 
 def device_iframe(ifr, device="cuda"):
