@@ -21,13 +21,18 @@ __device__ __forceinline__ const float *green_rows(const BlockTables &t, int w, 
     return t.G + __ldg(t.goff + shape_index(w, h));
 }
 
+// the job holding global block gb: the last k with p[k].block_base <= gb
+// (block bases increase with k; binary search over at most kMaxJobs)
 __device__ __forceinline__ int find_job(const BlockJobs &J, int gb)
 {
-    int j = 0;
+    int lo = 0, hi = J.n - 1;
 #pragma unroll 1
-    for (int k = 1; k < J.n; ++k)
-        if (gb >= J.p[k].block_base) j = k;
-    return j;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (gb >= J.p[mid].block_base) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
 struct BlockGeom {
