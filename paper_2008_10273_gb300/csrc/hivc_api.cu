@@ -262,13 +262,13 @@ hivc_status run_block_residual(hivc_decoder *d, const hivc_residual *res)
     {
         Timed t(d, 3);
         int l = 0;
-        e = launch_block_coef(J, scratch(d), d->stream, &l);
+        e = launch_block_coef(J, scratch(d), d->stream, &l, !d->timing);
         t.done(1);
     }
     if (e != cudaSuccess) return HIVC_E_CUDA;
     {
         Timed t(d, 5);
-        e = launch_block_eval(J, d->flags, d->stream);
+        e = launch_block_eval(J, d->flags, d->stream, !d->timing);
         t.done(1);
     }
     return cuda_status(e);
@@ -792,7 +792,7 @@ hivc_status hivc_decode_pframe_coef(hivc_decoder *d, const hivc_pframe_coef *f, 
     cudaError_t e;
     {
         Timed t(d, 5);
-        e = launch_block_eval(J, d->flags, d->stream);
+        e = launch_block_eval(J, d->flags, d->stream, !d->timing);
         t.done(1);
     }
     if (e != cudaSuccess) return HIVC_E_CUDA;
@@ -921,12 +921,12 @@ hivc_status decode_inter_run(hivc_decoder *d, const hivc_frame *frames, const hi
         {
             Timed t(d, 3);
             int l = 0;
-            e = launch_block_coef(J, S, d->stream, &l);
+            e = launch_block_coef(J, S, d->stream, &l, !d->timing);
             t.done(l);
         }
         if (e == cudaSuccess) {
             Timed t(d, 5);
-            e = launch_block_eval(J, d->flags, d->stream);
+            e = launch_block_eval(J, d->flags, d->stream, !d->timing);
             t.done(1);
         }
         J = BlockJobs{};

@@ -102,11 +102,14 @@ const BlockTables &block_tables(int op = 0);  // of the current device, for oper
 // c, a for every block (a = NaN: bad positions): one thread per block for
 // K <= 12, warps for K <= 32, a whole CTA for K > 32.  One launch, no
 // counters: the kernel's completion publishes every result.
-cudaError_t launch_block_coef(const BlockJobs &jobs, const BlockScratch &s, cudaStream_t st, int *launches);
+// pdl: launch as a programmatic dependent of the previous kernel in the
+// stream (the coefficient stage overlaps it and completes after it).
+cudaError_t launch_block_coef(const BlockJobs &jobs, const BlockScratch &s, cudaStream_t st, int *launches,
+                              bool pdl = false);
 // r-field from c, a (Eq. 3 by Green's rows), r = v at the points; or, for
 // jobs in coefficient mode (p[k].q set, all jobs alike), from the
 // dequantised indices and the transmitted constants, with no overwrite.
-cudaError_t launch_block_eval(const BlockJobs &jobs, uint32_t *flags, cudaStream_t st);
+cudaError_t launch_block_eval(const BlockJobs &jobs, uint32_t *flags, cudaStream_t st, bool pdl = false);
 
 // One inter frame for the pixel kernel: flow, references, the residual
 // planes the block kernels evaluated, outputs.

@@ -537,8 +537,7 @@ __device__ __forceinline__ void warp_path(const BlockJobs &J, const BlockTables 
 // condition bound exceeds the threshold are re-solved in FP64 by their CTA
 // after its first phase (thread path: in shared memory; warp path: in the
 // slot).  No counters: the kernel's completion publishes every result.
-__global__ void __launch_bounds__(kCoefThreads, 3) block_coef_kernel(const __grid_constant__ BlockJobs J,
-                                                                     BlockTables tab, BlockScratch S)
+__device__ __forceinline__ void coef_body(const BlockJobs &J, const BlockTables &tab, const BlockScratch &S)
 {
     static_assert(kCoefThreads == kRange, "one thread per block of a range");
     __shared__ float lts[kCoefThreads / 32][32 * 33];
@@ -547,9 +546,6 @@ __global__ void __launch_bounds__(kCoefThreads, 3) block_coef_kernel(const __gri
     __shared__ double redd[kCoefThreads / 32];
     __shared__ double w64[tri(kTK) + 3 * kTK];
     __shared__ int s_large[kRange], s_nlarge, s_bad;
-    // the kernel that follows may be scheduled now; it waits for this grid's
-    // results
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int nrange = block_ranges(J.total_blocks);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) s_nlarge = 0;
@@ -590,6 +586,19 @@ __global__ void __launch_bounds__(kCoefThreads, 3) block_coef_kernel(const __gri
     }
     float *slot = S.big + (size_t)range * kBigFloats;
     for (int i = 0; i < n; ++i) cta_block(J, tab, S, s_large[i], slot, w64, s_p, red, redd, &s_bad);
+}
+
+// The coefficient stage reads only the caller's block data, never what the
+// preceding kernel wrote, so as a programmatic dependent it runs alongside
+// that kernel: the kernel after it may be scheduled at once, and the wait
+// for the preceding grid comes last, so that this grid completes after it
+// (every later kernel that waits for this grid sees the earlier ones done).
+__global__ void __launch_bounds__(kCoefThreads, 3) block_coef_kernel(const __grid_constant__ BlockJobs J,
+                                                                     BlockTables tab, BlockScratch S)
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    coef_body(J, tab, S);
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // ---- evaluation stage into residual fields, one warp per block -----------
@@ -714,6 +723,9 @@ template <bool QC>
 __global__ void __launch_bounds__(128, 8) block_eval_kernel(const __grid_constant__ BlockJobs J, BlockTables tab,
                                                             uint32_t *flags)
 {
+    // the coefficients come from the preceding grid
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gb = blockIdx.x * 4 + warp;
     if (gb >= J.total_blocks) return;
@@ -785,21 +797,40 @@ const BlockTables &block_tables(int op)
     return g_tabs[dev < 64 ? dev : 0][op == 1 ? 1 : 0];
 }
 
-cudaError_t launch_block_coef(const BlockJobs &jobs, const BlockScratch &s, cudaStream_t st, int *launches)
+namespace {
+
+struct PdlConfig {
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    PdlConfig(dim3 grid, dim3 block, cudaStream_t st, bool pdl)
+    {
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.gridDim = grid;
+        cfg.blockDim = block;
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = pdl ? 1 : 0;
+    }
+};
+
+}  // namespace
+
+cudaError_t launch_block_coef(const BlockJobs &jobs, const BlockScratch &s, cudaStream_t st, int *launches, bool pdl)
 {
     if (jobs.total_blocks == 0) return cudaSuccess;
-    block_coef_kernel<<<2 * block_ranges(jobs.total_blocks), kCoefThreads, 0, st>>>(jobs, block_tables(jobs.op), s);
+    PdlConfig c(dim3(2 * block_ranges(jobs.total_blocks)), dim3(kCoefThreads), st, pdl);
+    const cudaError_t e = cudaLaunchKernelEx(&c.cfg, block_coef_kernel, jobs, block_tables(jobs.op), s);
     if (launches) *launches += 1;
-    return cudaGetLastError();
+    return e;
 }
 
-cudaError_t launch_block_eval(const BlockJobs &jobs, uint32_t *flags, cudaStream_t st)
+cudaError_t launch_block_eval(const BlockJobs &jobs, uint32_t *flags, cudaStream_t st, bool pdl)
 {
     if (jobs.total_blocks == 0) return cudaSuccess;
-    const unsigned grid = (jobs.total_blocks + 3) / 4;
-    if (jobs.p[0].q) block_eval_kernel<true><<<grid, 128, 0, st>>>(jobs, block_tables(jobs.op), flags);
-    else block_eval_kernel<false><<<grid, 128, 0, st>>>(jobs, block_tables(jobs.op), flags);
-    return cudaGetLastError();
+    PdlConfig c(dim3((jobs.total_blocks + 3) / 4), dim3(128), st, pdl);
+    if (jobs.p[0].q) return cudaLaunchKernelEx(&c.cfg, block_eval_kernel<true>, jobs, block_tables(jobs.op), flags);
+    return cudaLaunchKernelEx(&c.cfg, block_eval_kernel<false>, jobs, block_tables(jobs.op), flags);
 }
 
 }  // namespace hivc
