@@ -1,6 +1,6 @@
 """Batched decoding (hivc_decode_batch): the inter frames of a batch share
-multi-frame coefficient launches and run their fused kernels one after the
-other.  Every block is solved by the same arithmetic as in single-frame
+multi-frame coefficient and evaluation launches and run their pixel kernels
+one after the other.  Every block is solved by the same arithmetic as in single-frame
 decoding, so a batch must reproduce the per-frame path bit for bit, and
 with it the FP64 oracle within the parity tolerance."""
 import numpy as np

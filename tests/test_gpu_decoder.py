@@ -123,7 +123,7 @@ def test_zero_flow_zero_residual_keeps_reference(hv):
 @pytest.mark.parametrize("W,H,n,seed,B", [(160, 90, 8, 0, 16), (203, 77, 5, 1, 16), (150, 70, 4, 2, 8),
                                            (131, 67, 4, 3, 12)])
 def test_small_color_gop(hv, W, H, n, seed, B):
-    """B = 16 and 8 run the fused inter kernel, B = 12 the three-kernel path."""
+    """Block sizes 16, 8 and 12 (edge blocks of every partial shape)."""
     gop = make_gop(seed, W, H, n_frames=n, block=B)
     dec = hv.Decoder(W, H, chroma=True, block=B)
     out = hv.alloc_out(W, H)
@@ -245,7 +245,7 @@ def test_sor_tiling_choice_does_not_change_results(hv):
 
 @pytest.mark.parametrize("batched", [False, True])
 def test_inter_frames_in_a_cuda_graph(hv, batched):
-    """An inter frame's launches (coefficients, then the fused kernel; or the
+    """An inter frame's launches (coefficients, residual planes, pixels; or the
     batch path's block launches and pixel kernels) can be captured in a CUDA
     graph on the decoder's stream: replaying the graph decodes the frame
     exactly as a direct call, and decoding goes on from its result."""
