@@ -82,6 +82,8 @@ def lib():
             L.oracle_flow_from_tree.restype = c_int
             L.oracle_masks_from_trees.argtypes = [c_int, c_int, c_int, u32p_, u32p_, u32p_, u8p, ctypes.c_long]
             L.oracle_masks_from_trees.restype = c_int
+            L.oracle_intra_mask_from_tree.argtypes = [c_int, c_int, u32p_, ctypes.c_long, u32p_, ip]
+            L.oracle_intra_mask_from_tree.restype = c_int
             L.oracle_inverse_rct.argtypes = [c_int, dp, dp, dp, u8p]
             L.oracle_inverse_rct.restype = None
             L.oracle_dequantise.argtypes = [c_int, c_double, c_double]
@@ -267,6 +269,19 @@ def masks_from_trees(width: int, height: int, block: int, bits: np.ndarray, tree
     if st != OK:
         raise ValueError("invalid subdivision trees")
     return bp, pos[:int(bp[-1])].copy()
+
+
+def intra_mask_from_tree(width: int, height: int, bits: np.ndarray, nbits: int) -> np.ndarray:
+    """Intra mask indices (sorted uint32, y*W + x): the leaf centres of a
+    subdivision tree over the plane (Sec. 2.3)."""
+    words = np.ascontiguousarray(bits, np.uint32)
+    idx = np.zeros(width * height, np.uint32)
+    n = ctypes.c_int(0)
+    st = lib().oracle_intra_mask_from_tree(width, height, _p(words, ctypes.c_uint32), int(nbits),
+                                           _p(idx, ctypes.c_uint32), ctypes.byref(n))
+    if st != OK:
+        raise ValueError("invalid subdivision tree")
+    return idx[:n.value].copy()
 
 
 def inverse_rct(y: np.ndarray, u: np.ndarray, v: np.ndarray) -> List[np.ndarray]:

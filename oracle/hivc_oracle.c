@@ -624,3 +624,31 @@ int oracle_masks_from_trees(int W, int H, int B, const uint32_t *bits, const uin
     }
     return ORACLE_OK;
 }
+
+static int cmp_u32(const void *a, const void *b)
+{
+    const uint32_t x = *(const uint32_t *)a, y = *(const uint32_t *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* Intra mask positions (Sec. 2.3: the intra mask comes from a rectangular
+   subdivision of the plane): the leaf centres of the plane's tree as sorted
+   linear indices y W + x.  The tree must use all nbits bits. */
+int oracle_intra_mask_from_tree(int W, int H, const uint32_t *bits, long nbits, uint32_t *idx, int *n)
+{
+    int *rects = (int *)malloc((size_t)W * H * 4 * sizeof(int));
+    int nl = 0;
+    long used = 0;
+    int st = oracle_tree_leaves(0, 0, W, H, bits, 0, nbits, rects, W * H, &nl, &used);
+    if (st == ORACLE_OK && used != nbits) st = ORACLE_INVALID;
+    if (st == ORACLE_OK) {
+        for (int l = 0; l < nl; ++l) {
+            const int *r = rects + 4 * l;
+            idx[l] = (uint32_t)(r[1] + (r[3] - 1) / 2) * (uint32_t)W + (uint32_t)(r[0] + (r[2] - 1) / 2);
+        }
+        qsort(idx, (size_t)nl, sizeof(uint32_t), cmp_u32);
+        *n = nl;
+    }
+    free(rects);
+    return st;
+}

@@ -86,3 +86,21 @@ def test_invalid_trees_are_refused():
         oracle.tree_leaves(4, 4, _pack_bits([1, 0]), 2)
     with pytest.raises(ValueError):  # bits left over
         oracle.tree_leaves(4, 4, _pack_bits([0, 0]), 2)
+
+
+def test_intra_mask_is_the_sorted_leaf_centres():
+    """The intra mask of a plane's tree: one point per leaf, inside it, and
+    the hand-decoded tree's centres as plane indices."""
+    bits, leaves, centres = _golden()
+    idx = oracle.intra_mask_from_tree(5, 3, _pack_bits(bits), len(bits))
+    assert list(idx) == centres  # a 5-wide plane: block and plane indices agree
+    rng = np.random.default_rng(6)
+    W, H = 300, 170
+    words, nbits, _ = make_flow_tree(rng, W, H, 1500)
+    idx = oracle.intra_mask_from_tree(W, H, words, nbits)
+    leaves = oracle.tree_leaves(W, H, words, nbits)
+    assert len(idx) == len(leaves) and np.all(np.diff(idx.astype(np.int64)) > 0)
+    owner = np.full(W * H, -1)
+    for k, (x0, y0, lw, lh) in enumerate(leaves):
+        owner.reshape(H, W)[y0:y0 + lh, x0:x0 + lw] = k
+    assert sorted(owner[idx]) == list(range(len(leaves)))  # one point in every leaf
