@@ -345,6 +345,18 @@ hivc_status hivc_flow_from_tree(int32_t width, int32_t height, const uint32_t *b
                                 const float *values, int32_t n_values, float *flow, void *workspace,
                                 size_t ws_bytes, uint32_t *flags, void *stream);
 
+/* Device scratch hivc_intra_mask_from_tree needs. */
+size_t hivc_intra_mask_from_tree_workspace_bytes(int32_t width, int32_t height, int64_t nbits);
+
+/* Intra mask positions (Sec. 2.3: the intra mask comes from a rectangular
+   subdivision of the plane): the leaf centres of the plane's tree as
+   sorted linear indices y*width + x in idx (at most max_points; the mask
+   values arrive in this order), their count in *n_points (device int32;
+   0 for a bad tree or too many points, with bit 8 raised). */
+hivc_status hivc_intra_mask_from_tree(int32_t width, int32_t height, const uint32_t *bits, int64_t nbits,
+                                      uint32_t *idx, int64_t max_points, int32_t *n_points,
+                                      void *workspace, size_t ws_bytes, uint32_t *flags, void *stream);
+
 /* Residual mask points of a width x height plane's block x block blocks
    (raster order, edge blocks cropped) from one tree per block: block b's
    tree is bits [tree_ptr[b], tree_ptr[b+1]) (nblocks + 1 entries).

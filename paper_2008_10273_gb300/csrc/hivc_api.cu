@@ -1207,3 +1207,23 @@ hivc_status hivc_masks_from_trees(int32_t width, int32_t height, int32_t block, 
                                                   flags, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? HIVC_OK : HIVC_E_CUDA;
 }
+
+size_t hivc_intra_mask_from_tree_workspace_bytes(int32_t width, int32_t height, int64_t nbits)
+{
+    if (width < 1 || height < 1 || nbits < 1) return 0;
+    return intra_tree_workspace_bytes(nbits, width, height);
+}
+
+hivc_status hivc_intra_mask_from_tree(int32_t width, int32_t height, const uint32_t *bits, int64_t nbits,
+                                      uint32_t *idx, int64_t max_points, int32_t *n_points, void *workspace,
+                                      size_t ws_bytes, uint32_t *flags, void *stream)
+{
+    if (width < 1 || height < 1 || width > 16384 || height > 16384 || !bits || nbits < 1 ||
+        nbits > 2 * (int64_t)width * height || max_points < 0 || (max_points > 0 && !idx) || !n_points ||
+        !workspace || ws_bytes < intra_tree_workspace_bytes(nbits, width, height) || ((uintptr_t)workspace & 15))
+        return HIVC_E_INVALID;
+    if (ensure_block_tables() != cudaSuccess) return HIVC_E_CUDA;
+    const cudaError_t e = launch_intra_mask_from_tree(width, height, bits, nbits, idx, max_points, n_points, workspace,
+                                                      flags, block_tables().sms, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? HIVC_OK : HIVC_E_CUDA;
+}

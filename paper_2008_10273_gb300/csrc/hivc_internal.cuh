@@ -181,6 +181,11 @@ size_t tree_workspace_bytes(long long nbits);
 // dense flow from the plane's tree and one vector per leaf
 cudaError_t launch_flow_from_tree(int W, int H, const uint32_t *bits, long long nbits, const float *values,
                                   int n_values, float *flow, void *ws, uint32_t *flags, int sms, cudaStream_t st);
+// intra mask indices (sorted) and their count from the plane's tree
+size_t intra_tree_workspace_bytes(long long nbits, int W, int H);
+cudaError_t launch_intra_mask_from_tree(int W, int H, const uint32_t *bits, long long nbits, uint32_t *idx,
+                                        long long max_points, int32_t *n_out, void *ws, uint32_t *flags, int sms,
+                                        cudaStream_t st);
 // residual mask points (block_ptr, pos) from one tree per block
 cudaError_t launch_masks_from_trees(int W, int H, int B, const uint32_t *bits, const uint32_t *tree_ptr,
                                     uint32_t *block_ptr, uint8_t *pos, long long max_points, uint32_t *flags,

@@ -277,7 +277,93 @@ __global__ void __launch_bounds__(kTreeThreads) scan_counts_kernel(uint32_t *blo
     }
 }
 
+// ---- intra mask points --------------------------------------------------
+// The leaf centres of the plane's tree marked in a byte map, then written
+// in raster order: the map in chunks of kMarkChunk pixels, counted per
+// chunk, the counts scanned, each chunk's points placed by a block scan.
+constexpr int kMarkChunk = 4 * kTreeThreads;
+
+__global__ void __launch_bounds__(256) mark_centres_kernel(int W, const int4 *leaves, const int *counters,
+                                                           long long nbits, uint8_t *map)
+{
+    const int nleaf = counters[1];
+    if (counters[2] != 0 || (long long)counters[0] != nbits) return;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nleaf; l += gridDim.x * blockDim.x) {
+        const int4 r = leaves[l];
+        map[(size_t)(r.y + (r.w - 1) / 2) * W + r.x + (r.z - 1) / 2] = 1;
+    }
+}
+
+// PASS 0: points per chunk into cnt[c + 1]; PASS 1: the chunk's points at
+// offset cnt[c] (after the scan), in raster order
+template <int PASS>
+__global__ void __launch_bounds__(kTreeThreads) compact_kernel(const uint8_t *map, long long npix, uint32_t *cnt,
+                                                               uint32_t *idx, long long max_points)
+{
+    __shared__ int sh[64];
+    const long long c0 = (long long)blockIdx.x * kMarkChunk;
+    int v = 0;
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const long long i = c0 + 4LL * threadIdx.x + k;
+        const int b = i < npix ? map[i] : 0;
+        m |= (uint32_t)b << k;
+        v += b;
+    }
+    int total;
+    const int before = block_scan(v, sh, &total);
+    if (PASS == 0) {
+        if (threadIdx.x == 0) cnt[blockIdx.x + 1] = (uint32_t)total;
+        return;
+    }
+    if ((long long)cnt[gridDim.x] > max_points) return;
+    uint32_t o = cnt[blockIdx.x] + (uint32_t)before;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if ((m >> k) & 1u) idx[o++] = (uint32_t)(c0 + 4LL * threadIdx.x + k);
+}
+
+// the count (or 0 and kFlagTree for a bad tree or too many points)
+__global__ void intra_count_kernel(const int *counters, long long nbits, const uint32_t *cnt, int nchunks,
+                                   long long max_points, int32_t *n_out, uint32_t *flags)
+{
+    const bool ok = counters[2] == 0 && (long long)counters[0] == nbits && (long long)cnt[nchunks] <= max_points;
+    *n_out = ok ? (int32_t)cnt[nchunks] : 0;
+    if (!ok && flags) atomicOr(flags, kFlagTree);
+}
+
 }  // namespace
+
+size_t intra_tree_workspace_bytes(long long nbits, int W, int H)
+{
+    const size_t npix = (size_t)W * H;
+    const size_t nchunks = (npix + kMarkChunk - 1) / kMarkChunk;
+    return tree_workspace_bytes(nbits) + ((npix + 255) / 256) * 256 + (nchunks + 1) * sizeof(uint32_t) + 256;
+}
+
+cudaError_t launch_intra_mask_from_tree(int W, int H, const uint32_t *bits, long long nbits, uint32_t *idx,
+                                        long long max_points, int32_t *n_out, void *ws, uint32_t *flags, int sms,
+                                        cudaStream_t st)
+{
+    const int cap = (int)(nbits < 1 ? 1 : nbits);
+    int4 *lev0 = static_cast<int4 *>(ws), *lev1 = lev0 + cap, *leaves = lev1 + cap;
+    int *counters = reinterpret_cast<int *>(leaves + cap);
+    int *chunk_base = counters + 16;
+    uint8_t *map = static_cast<uint8_t *>(ws) + tree_workspace_bytes(nbits);
+    const size_t npix = (size_t)W * H;
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(map + ((npix + 255) / 256) * 256);
+    const int nchunks = (int)((npix + kMarkChunk - 1) / kMarkChunk);
+    cudaError_t e = cudaMemsetAsync(map, 0, npix, st);
+    if (e != cudaSuccess) return e;
+    tree_decode_kernel<<<1, kTreeThreads, 0, st>>>(W, H, bits, nbits, cap, lev0, lev1, leaves, chunk_base, counters);
+    mark_centres_kernel<<<2 * sms, 256, 0, st>>>(W, leaves, counters, nbits, map);
+    compact_kernel<0><<<nchunks, kTreeThreads, 0, st>>>(map, (long long)npix, cnt, idx, max_points);
+    scan_counts_kernel<<<1, kTreeThreads, 0, st>>>(cnt, nchunks);
+    compact_kernel<1><<<nchunks, kTreeThreads, 0, st>>>(map, (long long)npix, cnt, idx, max_points);
+    intra_count_kernel<<<1, 1, 0, st>>>(counters, nbits, cnt, nchunks, max_points, n_out, flags);
+    return cudaGetLastError();
+}
 
 size_t tree_workspace_bytes(long long nbits)
 {

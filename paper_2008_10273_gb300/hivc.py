@@ -107,6 +107,9 @@ PROTOTYPES = [
     ("hivc_flow_from_tree_workspace_bytes", c_sz, [ctypes.c_int64]),
     ("hivc_flow_from_tree", c_i32, [c_i32, c_i32, c_vp, ctypes.c_int64, c_vp, c_i32, c_vp, c_vp, c_sz, c_vp, c_vp]),
     ("hivc_masks_from_trees", c_i32, [c_i32, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, ctypes.c_int64, c_vp, c_vp]),
+    ("hivc_intra_mask_from_tree_workspace_bytes", c_sz, [c_i32, c_i32, ctypes.c_int64]),
+    ("hivc_intra_mask_from_tree", c_i32, [c_i32, c_i32, c_vp, ctypes.c_int64, c_vp, ctypes.c_int64, c_vp, c_vp, c_sz,
+                                          c_vp, c_vp]),
 ]
 
 
@@ -427,6 +430,19 @@ def flow_from_tree(width, height, bits, nbits, values, flow, flags=None, workspa
     return check(lib().hivc_flow_from_tree(width, height, _ptr(bits), int(nbits), _ptr(values), int(values.shape[0]),
                                            _ptr(flow), _ptr(workspace), int(workspace.numel()), _ptr(flags),
                                            _stream_handle(stream)), "hivc_flow_from_tree")
+
+
+def intra_mask_from_tree(width, height, bits, nbits, idx, n_points, flags=None, workspace=None, stream=None):
+    """hivc_intra_mask_from_tree: sorted indices into ``idx`` (capacity =
+    its length), their count into ``n_points`` (one int32)."""
+    need = lib().hivc_intra_mask_from_tree_workspace_bytes(width, height, int(nbits))
+    if workspace is None:
+        import torch
+
+        workspace = torch.empty(need, dtype=torch.uint8, device=idx.device)
+    return check(lib().hivc_intra_mask_from_tree(width, height, _ptr(bits), int(nbits), _ptr(idx), int(idx.numel()),
+                                                 _ptr(n_points), _ptr(workspace), int(workspace.numel()), _ptr(flags),
+                                                 _stream_handle(stream)), "hivc_intra_mask_from_tree")
 
 
 def masks_from_trees(width, height, block, bits, tree_ptr, block_ptr, pos, flags=None, stream=None):

@@ -1,6 +1,7 @@
 """GPU decoding of the side information (Sec. 2.3) against the FP64
-oracle: the piecewise-constant backward flow of a rectangular subdivision
-and the residual mask points of one subdivision per block.  Both are
+oracle: the piecewise-constant backward flow of a rectangular subdivision,
+the intra mask of a subdivision of the plane and the residual mask points
+of one subdivision per block.  Both are
 integer and copy work, so the results must be identical; invalid trees are
 reported and leave the output unwritten."""
 import numpy as np
@@ -78,3 +79,25 @@ def test_invalid_trees_are_reported(hv):
     hv.masks_from_trees(17, 1, 16, _dev(torch, words), _dev(torch, tp[:3]), bp[:3], pos, flags=flags)
     torch.cuda.synchronize()
     assert int(flags.item()) & (1 << 8)
+
+
+@pytest.mark.parametrize("W,H,n,seed", [(64, 48, 30, 0), (1920, 1080, 62000, 1), (203, 77, 900, 2), (1, 1, 1, 3)])
+def test_intra_mask_from_tree(hv, W, H, n, seed):
+    torch = torch_cuda()
+    rng = np.random.default_rng(seed)
+    words, nbits, _ = make_flow_tree(rng, W, H, n)
+    want = oracle.intra_mask_from_tree(W, H, words, nbits)
+    idx = torch.zeros(W * H, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    hv.intra_mask_from_tree(W, H, _dev(torch, words), nbits, idx, cnt, flags=flags)
+    torch.cuda.synchronize()
+    assert int(flags.item()) == 0 and int(cnt.item()) == len(want)
+    assert np.array_equal(to_np(idx)[:len(want)].view(np.uint32), want)
+    # too little room: nothing written, count 0, reported
+    small = torch.full((max(1, len(want) - 1),), -1, dtype=torch.int32, device="cuda")
+    if len(want) > 1:
+        hv.intra_mask_from_tree(W, H, _dev(torch, words), nbits, small, cnt, flags=flags)
+        torch.cuda.synchronize()
+        assert int(cnt.item()) == 0 and int(flags.item()) & (1 << 8)
+        assert np.all(to_np(small) == -1)

@@ -559,11 +559,20 @@ def _random_tree_bits(rng, w: int, h: int, n_leaves: int) -> List[int]:
     nxt = 1
     target = max(1, min(int(n_leaves), w * h))
     while len(leaves) < target:
-        cand = [i for i, l in enumerate(leaves) if rect[l][0] * rect[l][1] >= 2]
-        if not cand:
-            break
-        k = cand[int(rng.integers(len(cand)))]
-        node = leaves.pop(k)
+        k = -1
+        for _ in range(32):  # a random leaf of two or more pixels
+            j = int(rng.integers(len(leaves)))
+            if rect[leaves[j]][0] * rect[leaves[j]][1] >= 2:
+                k = j
+                break
+        if k < 0:
+            cand = [i for i, l in enumerate(leaves) if rect[l][0] * rect[l][1] >= 2]
+            if not cand:
+                break
+            k = cand[int(rng.integers(len(cand)))]
+        node = leaves[k]
+        leaves[k] = leaves[-1]
+        leaves.pop()
         cw, ch = rect[node]
         if cw >= ch:
             rect[nxt], rect[nxt + 1] = (cw - cw // 2, ch), (cw // 2, ch)
