@@ -242,6 +242,14 @@ hivc_status hivc_decoder_sync(hivc_decoder *dec, hivc_stats *last);
    next frame must be an intra frame).  Work already queued is unaffected. */
 hivc_status hivc_decoder_reset(hivc_decoder *dec);
 
+/* The intra solve's red-black sweep kernel comes in variants that perform
+   the same sweeps bit for bit (0: 128-column regions, a cell pair per
+   thread; 1: 112-column regions; 2: 128-column regions, four cells per
+   thread).  By default (-1) the first solve of each plane geometry times
+   them on its own sweeps and keeps the fastest; 0..2 pin one for every
+   decoder of the process.  HIVC_E_INVALID for other values. */
+hivc_status hivc_set_sor_variant(int32_t variant);
+
 /* Enable (1) or disable (0) per-kernel CUDA-event timing in hivc_stats. */
 hivc_status hivc_decoder_set_timing(hivc_decoder *dec, int32_t on);
 

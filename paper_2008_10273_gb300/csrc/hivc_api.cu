@@ -1227,3 +1227,8 @@ hivc_status hivc_intra_mask_from_tree(int32_t width, int32_t height, const uint3
                                                       flags, block_tables().sms, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? HIVC_OK : HIVC_E_CUDA;
 }
+
+hivc_status hivc_set_sor_variant(int32_t variant)
+{
+    return set_sor_variant(variant) == 0 ? HIVC_OK : HIVC_E_INVALID;
+}

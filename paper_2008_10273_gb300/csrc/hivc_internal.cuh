@@ -225,5 +225,6 @@ cudaError_t launch_intra_sor(IntraJobs &jobs, int e_in, bool from_zero, int swee
                              int *launches);
 int intra_sweeps_per_launch();
 cudaError_t intra_init();  // once per device
+int set_sor_variant(int v);  // -1: autotune; 0..2 pin a variant (0 on success)
 
 }  // namespace hivc

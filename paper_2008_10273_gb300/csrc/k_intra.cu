@@ -20,6 +20,7 @@
 // red-black sweeps run there before the interior is written back (each half
 // sweep invalidates one more halo ring).
 #include <algorithm>
+#include <atomic>
 #include <vector>
 #include <mutex>
 #include <map>
@@ -353,6 +354,136 @@ __global__ void __launch_bounds__(RW / 2 * kTY_THREADS, 1) intra_sor_kernel(cons
     }
 }
 
+// The same sweeps with four columns per thread: a warp spans the region's
+// 128 columns (lane t holds columns 4t .. 4t+3) in 8 rows, 16 warps.  Of a
+// cell's horizontal neighbours one may sit in the next lane (a shuffle; the
+// region border is 0 beyond lanes 0 and 31), the vertical ones of the
+// warp's first and last row in the next warp (shared rows, written after
+// each half sweep, then a barrier).  The neighbour sum is formed as
+// (left + right) + (up + down) and the update as in intra_sor_kernel, so
+// the results are the same bit for bit.
+constexpr int kQWarps = kRH / kRows;  // 16 row groups of 8 rows
+constexpr int kQCols = 128;           // region columns, 4 per lane
+
+template <bool FROM_ZERO>
+__global__ void __launch_bounds__(32 * kQWarps, 1) intra_sor4_kernel(const __grid_constant__ IntraJobs J, int e_in)
+{
+    constexpr int TX = sor_tx(kQCols);
+    __shared__ float rows[kQWarps][2][kQCols];  // each warp's first and last row
+    const IntraPlane &P = J.p[find_plane(J, blockIdx.x)];
+    const int lt = blockIdx.x - P.tile_base;
+    const int tx0 = (lt % P.tiles_x) * TX, ty0 = (lt / P.tiles_x) * kTY;
+    const int gx0 = tx0 - kHL, gy0 = ty0 - kHL;
+    const int W = P.width, H = P.height, pitch = P.pitch;
+    const int lane = threadIdx.x, wq = threadIdx.y, ly0 = wq * kRows;
+    const float *ein = P.e[e_in];
+    float *eout = P.e[e_in ^ 1];
+    const int gxq = gx0 + 4 * lane;  // a multiple of 4: the quad is one 16-byte vector
+    const float omega = P.omega, omc = 1.f - omega;
+    // e[k][j], wi[k][j], wr[k][j]: the cell in row ly0 + k, column 4 lane + j
+    float e[kRows][4], wi[kRows][4], wr[kRows][4];
+    const bool interior = gx0 >= 1 && gy0 >= 1 && gx0 + kQCols <= W - 1 && gy0 + kRH <= H - 1;
+    const int gxc = min(max(gxq, 0), pitch - 4);
+    uint32_t m4[kRows];
+    float4 r4[kRows], e4[kRows];
+#pragma unroll
+    for (int k = 0; k < kRows; ++k) {
+        const int gy = interior ? gy0 + ly0 + k : min(max(gy0 + ly0 + k, 0), H - 1);
+        const size_t i = (size_t)gy * pitch + (interior ? gxq : gxc);
+        m4[k] = __ldg(reinterpret_cast<const unsigned int *>(P.mask + i));
+        r4[k] = __ldg(reinterpret_cast<const float4 *>(P.res + i));
+        if (!FROM_ZERO) e4[k] = __ldg(reinterpret_cast<const float4 *>(ein + i));
+    }
+#pragma unroll
+    for (int k = 0; k < kRows; ++k) {
+        const int gy = gy0 + ly0 + k;
+        const bool yin = gy >= 0 && gy < H;
+        const int ny = (gy > 0) + (gy < H - 1);
+        const float rr[4] = {r4[k].x, r4[k].y, r4[k].z, r4[k].w};
+        float ee[4] = {0.f, 0.f, 0.f, 0.f};
+        if (!FROM_ZERO) {
+            ee[0] = e4[k].x;
+            ee[1] = e4[k].y;
+            ee[2] = e4[k].z;
+            ee[3] = e4[k].w;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gx = gxq + j;
+            bool unk;
+            float iv;
+            if (interior) {
+                unk = ((m4[k] >> (8 * j)) & 0xffu) == 0;
+                iv = unk ? 0.25f * omega : 0.f;
+            } else {
+                unk = yin && gx >= 0 && gx < W && ((m4[k] >> (8 * j)) & 0xffu) == 0;
+                const int n = ny + (gx > 0) + (gx < W - 1);
+                const float inv = n == 4 ? 0.25f : (n == 3 ? (1.0f / 3.0f) : (n == 2 ? 0.5f : 1.0f));
+                iv = unk ? omega * inv : 0.f;
+            }
+            wi[k][j] = iv;
+            wr[k][j] = unk ? rr[j] * iv : 0.f;
+            e[k][j] = (FROM_ZERO || !unk) ? 0.f : ee[j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        rows[wq][0][4 * lane + j] = e[0][j];
+        rows[wq][1][4 * lane + j] = e[kRows - 1][j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 1; m <= 2 * kS; ++m) {
+        const int c = (m - 1) & 1;  // red (even x + y) first
+#pragma unroll
+        for (int k = 0; k < kRows; ++k) {
+            const int b = (c + k) & 1;  // the colour-c cells of the row: columns b and b + 2
+            // the neighbour beyond the quad on the needed side (every lane shuffles)
+            float beyond;
+            if (b == 0) {
+                beyond = __shfl_up_sync(0xffffffffu, e[k][3], 1);
+                if (lane == 0) beyond = 0.f;
+            } else {
+                beyond = __shfl_down_sync(0xffffffffu, e[k][0], 1);
+                if (lane == 31) beyond = 0.f;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = b + 2 * h;
+                const float L = j == 0 ? beyond : e[k][j - 1];
+                const float R = j == 3 ? beyond : e[k][j + 1];
+                const float U = k > 0 ? e[k - 1][j] : (wq > 0 ? rows[wq - 1][1][4 * lane + j] : 0.f);
+                const float D = k < kRows - 1 ? e[k + 1][j] : (wq < kQWarps - 1 ? rows[wq + 1][0][4 * lane + j] : 0.f);
+                const float sum = (L + R) + (U + D);
+                e[k][j] = fmaf(sum, wi[k][j], fmaf(omc, e[k][j], wr[k][j]));
+            }
+        }
+        // the first and last rows' new values for the neighbouring warps
+        const int b0 = c & 1, b7 = (c + kRows - 1) & 1;
+        rows[wq][0][4 * lane + b0] = e[0][b0];
+        rows[wq][0][4 * lane + b0 + 2] = e[0][b0 + 2];
+        rows[wq][1][4 * lane + b7] = e[kRows - 1][b7];
+        rows[wq][1][4 * lane + b7 + 2] = e[kRows - 1][b7 + 2];
+        __syncthreads();
+    }
+    // interior quads: columns kHL .. kHL + TX - 1 of the region
+    const int lx = 4 * lane;
+    if (lx < kHL || lx >= kHL + TX || gxq >= W) return;
+#pragma unroll
+    for (int k = 0; k < kRows; ++k) {
+        const int ly = ly0 + k, gy = gy0 + ly;
+        if (ly < kHL || ly >= kHL + kTY || gy >= H) continue;
+        float *o = eout + (size_t)gy * pitch + gxq;
+        if (gxq + 3 < W) {
+            *reinterpret_cast<float4 *>(o) = make_float4(e[k][0], e[k][1], e[k][2], e[k][3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (gxq + j < W) o[j] = e[k][j];
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_intra_init(IntraJobs &J, uint32_t *flags, cudaStream_t st, int *launches)
@@ -401,19 +532,36 @@ void sor_launch(IntraJobs &J, int cur, bool from_zero, cudaStream_t st)
     else intra_sor_kernel<RW, false><<<base, block, sor_smem_bytes(RW), st>>>(J, cur);
 }
 
-void sor_launch_rw(int rw, IntraJobs &J, int cur, bool from_zero, cudaStream_t st)
+void sor_launch_quads(IntraJobs &J, int cur, bool from_zero, cudaStream_t st)
 {
-    if (rw == 112) sor_launch<112>(J, cur, from_zero, st);
+    int base = 0;
+    for (int k = 0; k < J.n; ++k) {
+        IntraPlane &P = J.p[k];
+        P.tiles_x = (P.width + sor_tx(kQCols) - 1) / sor_tx(kQCols);
+        P.tile_base = base;
+        base += P.tiles_x * ((P.height + kTY - 1) / kTY);
+    }
+    const dim3 block(32, kQWarps);
+    if (from_zero) intra_sor4_kernel<true><<<base, block, 0, st>>>(J, cur);
+    else intra_sor4_kernel<false><<<base, block, 0, st>>>(J, cur);
+}
+
+// variant 0: 128-column regions, a cell pair per thread; 1: 112 columns;
+// 2: 128 columns, four cells per thread
+void sor_launch_rw(int variant, IntraJobs &J, int cur, bool from_zero, cudaStream_t st)
+{
+    if (variant == 1) sor_launch<112>(J, cur, from_zero, st);
+    else if (variant == 2) sor_launch_quads(J, cur, from_zero, st);
     else sor_launch<128>(J, cur, from_zero, st);
 }
 
-// Tiling autotuner.  Both region widths perform exactly the same global
+// Tiling autotuner.  The variants perform exactly the same global
 // red-black sweeps (a cell's neighbour sum is formed in the same order), so
-// the choice changes speed only.  The first call with at least 12 launches
-// for a set of plane sizes on a device times each width on its own
-// launches (real sweeps of the solve, in alternating groups of three) and
-// keeps the narrower width only if it is at least 2 % faster.
-constexpr int kSorWidths[2] = {128, 112};
+// the choice changes speed only.  The first call with enough launches for
+// a set of plane sizes on a device times each variant on its own launches
+// (real sweeps of the solve, two groups of three each, round robin) and
+// keeps another variant than the first only if it is at least 2 % faster.
+constexpr int kSorVariants = 3;
 std::mutex g_tune_mu;
 std::map<std::vector<int>, int> g_tuned;
 
@@ -431,11 +579,16 @@ std::vector<int> tune_key(const IntraJobs &J)
 
 }  // namespace
 
-int sor_region_width(const IntraJobs &J)
+std::atomic<int> g_forced{-1};  // a variant pinned by the caller, or -1
+
+// the tuned SOR variant for these planes, or -1 before tuning
+int sor_variant(const IntraJobs &J)
 {
+    const int f = g_forced.load(std::memory_order_relaxed);
+    if (f >= 0) return f;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find(tune_key(J));
-    return it == g_tuned.end() ? 0 : it->second;
+    return it == g_tuned.end() ? -1 : it->second;
 }
 
 cudaError_t launch_intra_sor(IntraJobs &J, int e_in, bool from_zero, int sweeps, cudaStream_t st, int *e_out,
@@ -443,38 +596,42 @@ cudaError_t launch_intra_sor(IntraJobs &J, int e_in, bool from_zero, int sweeps,
 {
     const int n = (sweeps + kS - 1) / kS;
     int cur = e_in, l = 0;
-    int rw = sor_region_width(J);
-    // untuned: each width timed twice over kTuneGroup consecutive launches
-    // (alternating groups), if the call has that many launches
-    constexpr int kTuneGroup = 3, kTuneLaunches = 4 * kTuneGroup;
-    if (rw == 0 && n >= kTuneLaunches) {
-        cudaEvent_t ev[5];
+    int rw = sor_variant(J);
+    // untuned: each variant timed twice over kTuneGroup consecutive launches
+    // (round robin), if the call has that many launches
+    constexpr int kTuneGroup = 3, kTuneRounds = 2, kTuneLaunches = kTuneRounds * kSorVariants * kTuneGroup;
+    if (rw < 0 && n >= kTuneLaunches) {
+        constexpr int kEv = kTuneRounds * kSorVariants + 1;
+        cudaEvent_t ev[kEv];
         int made = 0;
         cudaError_t e = cudaSuccess;
-        for (; made < 5 && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
+        for (; made < kEv && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
         if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
-        for (int t = 0; t < 4 && e == cudaSuccess; ++t) {
+        for (int t = 0; t < kEv - 1 && e == cudaSuccess; ++t) {
             for (int g = 0; g < kTuneGroup; ++g, ++l) {
-                sor_launch_rw(kSorWidths[t & 1], J, cur, from_zero && l == 0, st);
+                sor_launch_rw(t % kSorVariants, J, cur, from_zero && l == 0, st);
                 cur ^= 1;
             }
             e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaEventRecord(ev[t + 1], st);
         }
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev[4]);
-        float best[2] = {1e30f, 1e30f};
-        for (int t = 0; t < 4 && e == cudaSuccess; ++t) {
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[kEv - 1]);
+        float best[kSorVariants];
+        for (int v = 0; v < kSorVariants; ++v) best[v] = 1e30f;
+        for (int t = 0; t < kEv - 1 && e == cudaSuccess; ++t) {
             float ms = 0.f;
             e = cudaEventElapsedTime(&ms, ev[t], ev[t + 1]);
-            best[t & 1] = std::min(best[t & 1], ms);
+            best[t % kSorVariants] = std::min(best[t % kSorVariants], ms);
         }
         for (int i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
         if (e != cudaSuccess) return e;
-        rw = best[1] < 0.98f * best[0] ? kSorWidths[1] : kSorWidths[0];
+        rw = 0;
+        for (int v = 1; v < kSorVariants; ++v)
+            if (best[v] < 0.98f * best[rw]) rw = v;
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tuned[tune_key(J)] = rw;
     }
-    if (rw == 0) rw = kSorWidths[0];
+    if (rw < 0) rw = 0;
     for (; l < n; ++l) {
         sor_launch_rw(rw, J, cur, from_zero && l == 0, st);
         cur ^= 1;
@@ -485,6 +642,13 @@ cudaError_t launch_intra_sor(IntraJobs &J, int e_in, bool from_zero, int sweeps,
 }
 
 int intra_sweeps_per_launch() { return kS; }
+
+int set_sor_variant(int v)
+{
+    if (v < -1 || v >= kSorVariants) return -1;
+    g_forced.store(v, std::memory_order_relaxed);
+    return 0;
+}
 
 // One staged region per CTA, one CTA per SM: the colour arrays take dynamic
 // shared memory beyond the static limit.  Called once per device.

@@ -93,6 +93,7 @@ PROTOTYPES = [
     ("hivc_decoder_sync", c_i32, [c_vp, ctypes.POINTER(Stats)]),
     ("hivc_decoder_set_timing", c_i32, [c_vp, c_i32]),
     ("hivc_decoder_reset", c_i32, [c_vp]),
+    ("hivc_set_sor_variant", c_i32, [c_i32]),
     ("hivc_decoder_reference", c_i32, [c_vp, c_i32, ctypes.POINTER(c_vp), ctypes.POINTER(c_i32),
                                        ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
     ("hivc_decoder_stream", c_vp, [c_vp]),

@@ -279,3 +279,27 @@ def test_inter_frames_in_a_cuda_graph(hv, batched):
     dec.sync()
     for p in range(3):
         assert np.array_equal(to_np(out[p]), want[2][p]), p
+
+
+def test_sor_variants_are_bit_identical(hv):
+    """Each pinned sweep variant (pairs of 128 or 112 columns, quads of 128)
+    decodes an intra frame to the same bits, on planes with interior and
+    edge regions."""
+    W, H = 700, 333
+    _, ifr = make_iframe_only(19, W, H, 0.02, chroma=True)
+    got = []
+    try:
+        for v in (0, 1, 2):
+            hv.check(hv.lib().hivc_set_sor_variant(v))
+            dec = hv.Decoder(W, H, chroma=True, iframe_tol=1e-9)
+            out = hv.alloc_out(W, H)
+            dec.decode_iframe(hv.device_iframe(ifr), out)
+            st = dec.sync()
+            got.append(([to_np(dec.reference(p)) for p in range(3)], st.sweeps))
+    finally:
+        hv.lib().hivc_set_sor_variant(-1)
+    for planes, sweeps in got[1:]:
+        assert sweeps == got[0][1]
+        for a, b in zip(planes, got[0][0]):
+            assert np.array_equal(a, b)
+    assert hv.lib().hivc_set_sor_variant(3) == hv.HIVC_E_INVALID
