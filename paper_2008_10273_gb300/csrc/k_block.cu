@@ -1,6 +1,6 @@
 // Block-based pseudodifferential inpainting of the residual (Sec. 2.2,
-// Eqs. 2-4; Sec. 2.3), harmonic operator A = -L with mirrored boundaries on
-// each w x h block (w, h <= 16).
+// Eqs. 2-4; Sec. 2.3), harmonic operator A = -L (or the biharmonic L^2)
+// with mirrored boundaries on each w x h block (w, h <= 16).
 //
 // Per block with K points p_j and values v_j:
 //   1. coefficients: the (K+1) x (K+1) saddle system
@@ -14,14 +14,17 @@
 // and mu_pq = 4 sin^2(pi p / 2w) + 4 sin^2(pi q / 2h),
 //   G(x,y; x',y') = T(|x-x'|,|y-y'|) + T(|x-x'|,y+y'+1) + T(x+x'+1,|y-y'|) + T(x+x'+1,y+y'+1),
 //   T(al, be) = 1/4 sum_{(p,q) != 0} c_p^2 c_q^2 cos(pi p al / w) cos(pi q be / h) / mu_pq
+// (/ mu_pq^2 for the biharmonic operator)
 // (the Toeplitz-plus-Hankel structure of G, Sec. 2.2), stored as float
 // and, for the FP64 re-solve of blocks above the condition threshold, as
 // double.
 //
-// Kernels: the coefficient stage (two blocks per warp: in its 16-lane
-// halves when both have K <= 16, else one after the other with all lanes
-// for K <= 32; blocks with K > 32 by the kernel's last CTA, packed Cholesky
-// in global scratch) and the evaluation into a residual field.
+// Kernels: the coefficient stage (one thread per block for K <= 12; warps
+// for K <= 32, two blocks at once in 16-lane halves when both have
+// K <= 16; blocks with K > 32, and FP64 re-solves, by the CTA of the
+// block's range, packed Cholesky in the range's scratch slot) and the
+// evaluation into residual planes (one warp per block; also the
+// coefficient mode, which dequantises instead of solving).
 #include <cmath>
 #include <cstring>
 #include <mutex>
