@@ -68,11 +68,42 @@ def stream_budget_bytes(s: Stream, per_stream: int) -> int:
     return hivc.Decoder.bytes_for(w, h, s.chroma, s.block) + per_stream * per_frame + scratch
 
 
+class DeviceApi:
+    """What the server needs of the device: decoders, output planes, decode
+    calls and a completion event after a decoder's queued work (CUDA events
+    recorded on the decoder's stream)."""
+
+    def decoder(self, s: Stream):
+        return hivc.Decoder(s.width, s.height, chroma=s.chroma, block=s.block, iframe_tol=s.iframe_tol)
+
+    def alloc_out(self, s: Stream):
+        return hivc.alloc_out(s.width, s.height, chroma=s.chroma)
+
+    def decode_batch(self, decs, frames, outs):
+        hivc.decode_batch(decs, frames, outs)
+
+    def decode_one(self, dec, frame, out):
+        kind, f = frame
+        if kind == "i":
+            dec.decode_iframe(f, out, allow_not_converged=True)
+        else:
+            dec.decode_pframe(f, out)
+
+    def event_after(self, dec):
+        import torch
+
+        ev = torch.cuda.Event()
+        ev.record(torch.cuda.ExternalStream(dec.stream_handle))
+        return ev
+
+
 class Server:
-    """Continuous-batching decoder for many streams under an HBM budget."""
+    """Continuous-batching decoder for many streams under an HBM budget.
+    ``api`` supplies the device side (default :class:`DeviceApi`)."""
 
     def __init__(self, budget_bytes: int, per_stream: int = 8, max_frames_per_call: int = 256,
-                 poll_s: float = 2e-4):
+                 poll_s: float = 2e-4, api: Optional[DeviceApi] = None):
+        self.api = api if api is not None else DeviceApi()
         self.budget = int(budget_bytes)
         self.per_stream = per_stream
         self.max_frames = max_frames_per_call
@@ -106,10 +137,10 @@ class Server:
                 pass
             if self.used + need > self.budget:
                 return False
-            s.decoder = hivc.Decoder(s.width, s.height, chroma=s.chroma, block=s.block, iframe_tol=s.iframe_tol)
+            s.decoder = self.api.decoder(s)
             self.created += 1
             self.used += need
-        s.out = hivc.alloc_out(s.width, s.height, chroma=s.chroma)
+        s.out = self.api.alloc_out(s)
         s.budget_bytes = need
         self.admit_log.append((s.name, round(now, 6)))
         return True
@@ -139,15 +170,13 @@ class Server:
     def _output(self, s: Stream):
         if not s.keep_outputs:
             return s.out
-        o = hivc.alloc_out(s.width, s.height, chroma=s.chroma)
+        o = self.api.alloc_out(s)
         s.outputs.append(o)
         return o
 
     def run(self, streams: Sequence[Stream], batched: bool = True) -> dict:
         """Decode every frame of every stream.  Returns throughput (FullHD
         frames/s over the wall time) and per-frame latency quantiles."""
-        import torch
-
         for s in streams:
             s.finish = [0.0] * len(s.frames)
             s.next_submit = s.done = 0
@@ -190,18 +219,12 @@ class Server:
                     s.next_submit += 1
             if frames:
                 if batched:
-                    hivc.decode_batch(decs, frames, outs)
+                    self.api.decode_batch(decs, frames, outs)
                 else:
-                    kind, f = frames[0]
-                    if kind == "i":
-                        decs[0].decode_iframe(f, outs[0], allow_not_converged=True)
-                    else:
-                        decs[0].decode_pframe(f, outs[0])
+                    self.api.decode_one(decs[0], frames[0], outs[0])
                 calls += 1
                 for s, a, b in spans:
-                    ev = torch.cuda.Event()
-                    ev.record(torch.cuda.ExternalStream(s.decoder.stream_handle))
-                    s.pending.append((ev, a, b))
+                    s.pending.append((self.api.event_after(s.decoder), a, b))
             for s in active:
                 self._poll(s)
             for s in [x for x in active if x.done == len(x.frames)]:
