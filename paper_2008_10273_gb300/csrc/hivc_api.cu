@@ -3,6 +3,7 @@
 // kernels of k_intra.cu, k_block.cu, k_pframe.cu and k_warp.cu; this file
 // only allocates, validates and launches.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -135,6 +136,10 @@ struct hivc_decoder {
     // statistics
     hivc_stats st{};
     bool timing = false;
+    // side stream: the block stage of the inter frames after an intra frame
+    // runs there while the intra frame decodes (fork and join events)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
     std::vector<cudaEvent_t> event_pool;
 };
@@ -408,7 +413,10 @@ hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out)
         }
         d->own_stream = true;
     }
-    if (cudaMemsetAsync(d->flags, 0, 4 * kStatusWords, d->stream) != cudaSuccess ||
+    if (cudaStreamCreateWithFlags(&d->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&d->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&d->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMemsetAsync(d->flags, 0, 4 * kStatusWords, d->stream) != cudaSuccess ||
         cudaStreamSynchronize(d->stream) != cudaSuccess) {
         hivc_decoder_destroy(d);
         return HIVC_E_CUDA;
@@ -422,6 +430,12 @@ void hivc_decoder_destroy(hivc_decoder *d)
     if (!d) return;
     cudaSetDevice(d->device);
     if (d->stream) cudaStreamSynchronize(d->stream);
+    if (d->side) {
+        cudaStreamSynchronize(d->side);
+        cudaStreamDestroy(d->side);
+    }
+    if (d->ev_fork) cudaEventDestroy(d->ev_fork);
+    if (d->ev_join) cudaEventDestroy(d->ev_join);
     for (auto &pe : d->pending) {
         cudaEventDestroy(pe.second.first);
         cudaEventDestroy(pe.second.second);
@@ -698,9 +712,12 @@ hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc
     return converged ? HIVC_OK : HIVC_E_NOT_CONVERGED;
 }
 
+namespace {
+
 // The pixel kernel of a frame whose residual planes (plane pitches) were
 // evaluated before, into the next reference buffer.
-cudaError_t launch_pixels(hivc_decoder *d, const float *flow, const hivc_out *out, float *const *r)
+cudaError_t launch_pixels(hivc_decoder *d, const float *flow, const hivc_out *out, float *const *r,
+                          bool pdl = true)
 {
     const int nxt = d->cur ^ 1;
     InterFrame F{};
@@ -718,10 +735,12 @@ cudaError_t launch_pixels(hivc_decoder *d, const float *flow, const hivc_out *ou
     F.height = d->cfg.height;
     F.chroma = d->cfg.chroma;
     Timed t(d, 4);
-    const cudaError_t e = launch_pframe(F, d->stream, !d->timing);
+    const cudaError_t e = launch_pframe(F, d->stream, pdl && !d->timing);
     t.done(1);
     return e;
 }
+
+}  // namespace
 
 hivc_status hivc_decode_pframe(hivc_decoder *d, const hivc_pframe *f, const hivc_out *out)
 {
@@ -856,13 +875,15 @@ hivc_status ensure_pool(hivc_decoder *d, size_t bytes)
     return HIVC_OK;
 }
 
-// The inter frames frames[k] (k in ks, in order) of decoder d.  Block
-// stage over several frames at once: per up to kMaxJobs block jobs (8 FullHD
-// 4:2:0 frames) one coefficient launch and one evaluation launch into each
-// frame's residual planes, all in the batch pool; then per frame the
-// warp + residual + pack kernel.  Every frame has been checked.
-hivc_status decode_inter_run(hivc_decoder *d, const hivc_frame *frames, const hivc_out *outs,
-                             const std::vector<int> &ks)
+using ResidualPlanes = std::vector<std::array<float *, 3>>;
+
+// Block stage of the inter frames frames[k] (k in ks, in order) of decoder
+// d on stream st: per up to kMaxJobs block jobs (8 FullHD 4:2:0 frames) one
+// coefficient launch and one evaluation launch into each frame's residual
+// planes (returned in rp), all in the batch pool.  pdl: the first launch may
+// overlap the kernel before it on st.  Every frame has been checked.
+hivc_status inter_blocks(hivc_decoder *d, const hivc_frame *frames, const std::vector<int> &ks, cudaStream_t st,
+                         bool pdl, ResidualPlanes &rp)
 {
     if (cudaSetDevice(d->device) != cudaSuccess) return HIVC_E_CUDA;
     const size_t nf = ks.size();
@@ -921,12 +942,13 @@ hivc_status decode_inter_run(hivc_decoder *d, const hivc_frame *frames, const hi
         {
             Timed t(d, 3);
             int l = 0;
-            e = launch_block_coef(J, S, d->stream, &l, !d->timing);
+            e = launch_block_coef(J, S, st, &l, pdl && !d->timing);
             t.done(l);
         }
+        pdl = true;
         if (e == cudaSuccess) {
             Timed t(d, 5);
-            e = launch_block_eval(J, d->flags, d->stream, !d->timing);
+            e = launch_block_eval(J, d->flags, st, !d->timing);
             t.done(1);
         }
         J = BlockJobs{};
@@ -943,14 +965,53 @@ hivc_status decode_inter_run(hivc_decoder *d, const hivc_frame *frames, const hi
         }
     }
     if (flush() != cudaSuccess) return HIVC_E_CUDA;
-    for (size_t k = 0; k < nf; ++k) {
-        float *const r[3] = {at(k, 0, 2), at(k, 1, 2), at(k, 2, 2)};
-        const cudaError_t e = launch_pixels(d, frames[ks[k]].p->flow, &outs[ks[k]], r);
+    rp.resize(nf);
+    for (size_t k = 0; k < nf; ++k) rp[k] = {at(k, 0, 2), at(k, 1, 2), at(k, 2, 2)};
+    return HIVC_OK;
+}
+
+// Per inter frame the warp + residual + pack kernel on the decoder's stream
+// (the residual planes of inter_blocks).  pdl: the first launch may overlap
+// the kernel before it.
+hivc_status inter_pixels(hivc_decoder *d, const hivc_frame *frames, const hivc_out *outs, const std::vector<int> &ks,
+                         const ResidualPlanes &rp, bool pdl)
+{
+    for (size_t k = 0; k < ks.size(); ++k) {
+        const cudaError_t e = launch_pixels(d, frames[ks[k]].p->flow, &outs[ks[k]], rp[k].data(), pdl || k > 0);
         if (e != cudaSuccess) return HIVC_E_CUDA;
         d->cur ^= 1;
         d->st.frames += 1;
     }
     return HIVC_OK;
+}
+
+hivc_status decode_inter_run(hivc_decoder *d, const hivc_frame *frames, const hivc_out *outs,
+                             const std::vector<int> &ks)
+{
+    ResidualPlanes rp;
+    const hivc_status s = inter_blocks(d, frames, ks, d->stream, true, rp);
+    return s != HIVC_OK ? s : inter_pixels(d, frames, outs, ks, rp, true);
+}
+
+// An intra frame followed by the inter run ks: the run's block stage does
+// not depend on the intra frame, so it goes to the side stream (after all
+// earlier work of the decoder's stream, which may still read the pool) and
+// overlaps the intra frame's sweeps and the host's waits between its
+// correction cycles; the decoder's stream joins it before the first warp.
+hivc_status decode_intra_then_run(hivc_decoder *d, const hivc_frame *frames, const hivc_out *outs, int ki,
+                                  const std::vector<int> &ks, hivc_status &intra)
+{
+    if (cudaSetDevice(d->device) != cudaSuccess || cudaEventRecord(d->ev_fork, d->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(d->side, d->ev_fork, 0) != cudaSuccess)
+        return HIVC_E_CUDA;
+    ResidualPlanes rp;
+    const hivc_status sb = inter_blocks(d, frames, ks, d->side, false, rp);
+    const bool joined = cudaEventRecord(d->ev_join, d->side) == cudaSuccess;
+    intra = hivc_decode_iframe(d, frames[ki].i, &outs[ki]);
+    if (!joined || cudaStreamWaitEvent(d->stream, d->ev_join, 0) != cudaSuccess) return HIVC_E_CUDA;
+    if (intra != HIVC_OK && intra != HIVC_E_NOT_CONVERGED) return intra;
+    if (sb != HIVC_OK) return sb;
+    return inter_pixels(d, frames, outs, ks, rp, false);
 }
 
 }  // namespace
@@ -965,6 +1026,19 @@ hivc_status decode_own_frames(hivc_decoder *d, const hivc_frame *frames, const h
 {
     hivc_status worst = HIVC_OK;
     for (size_t i = 0; i < ks.size();) {
+        if (frames[ks[i]].type == 0 && i + 1 < ks.size() && frames[ks[i + 1]].type == 1 && d->cfg.chroma != 2 &&
+            !d->timing) {
+            std::vector<int> run;
+            size_t j = i + 1;
+            while (j < ks.size() && frames[ks[j]].type == 1) run.push_back(ks[j++]);
+            hivc_status intra = HIVC_OK;
+            const hivc_status s = decode_intra_then_run(d, frames, outs, ks[i], run, intra);
+            if (intra != HIVC_OK && intra != HIVC_E_NOT_CONVERGED) return intra;
+            if (intra != HIVC_OK) worst = intra;
+            if (s != HIVC_OK) return s;
+            i = j;
+            continue;
+        }
         if (frames[ks[i]].type == 0) {
             const hivc_status s = hivc_decode_iframe(d, frames[ks[i]].i, &outs[ks[i]]);
             if (s != HIVC_OK && s != HIVC_E_NOT_CONVERGED) return s;
