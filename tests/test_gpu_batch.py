@@ -183,3 +183,31 @@ def test_batch_reference_rules(hv):
     assert e.value.status == hv.HIVC_E_NO_REFERENCE
     d1.sync()
     d2.sync()
+
+
+@pytest.mark.parametrize("k,m", [(3, 6), (6, 2)])
+def test_batch_two_gops_in_one_call(hv, k, m):
+    """Two GOPs of one decoder in one call, [I P x k I P x m]: the block
+    stage of each inter run overlaps its intra frame on a side stream, and the
+    second run reuses the batch pool (grown when it is larger) only after the
+    first run's pixel kernels.  Equal to decoding frame by frame."""
+    W, H = 160, 90
+    ga = make_gop(41, W, H, n_frames=k + 1)
+    gb = make_gop(42, W, H, n_frames=m + 1)
+    frames = []
+    for g in (ga, gb):
+        frames += [("i", hv.device_iframe(g.iframe))] + [("p", hv.device_pframe(p)) for p in g.pframes]
+    dec = hv.Decoder(W, H)
+    ref = []
+    out = hv.alloc_out(W, H)
+    for kind, f in frames:
+        (dec.decode_iframe if kind == "i" else dec.decode_pframe)(f, out)
+        dec.sync()
+        ref.append([to_np(o).copy() for o in out])
+    dec2 = hv.Decoder(W, H)
+    outs = [hv.alloc_out(W, H) for _ in frames]
+    hv.decode_batch([dec2] * len(frames), frames, outs)
+    dec2.sync()
+    for t, o in enumerate(outs):
+        for p in range(3):
+            assert np.array_equal(to_np(o[p]), ref[t][p]), (t, p)
