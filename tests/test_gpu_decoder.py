@@ -141,6 +141,40 @@ def test_small_color_gop(hv, W, H, n, seed, B):
             assert np.abs(to_np(out[p]).astype(int) - o8[p].astype(int)).max() <= 1
 
 
+@pytest.mark.parametrize("W,H", [(1, 40), (37, 1), (1, 1), (3, 3), (2, 5)])
+def test_tiny_color_gop(hv, W, H):
+    """Degenerate planes through the inter path: one pixel wide or tall
+    (chroma 1 x 20, 19 x 1), a single pixel, odd 3 x 3 and 2 x 5 (chroma
+    quads cut by the edge).  Per-frame decoding against the oracle, and the
+    same GOP in one batch call equal to it bit for bit."""
+    n = 3
+    gop = make_gop(7, W, H, n_frames=n)
+    frames = oracle.decode_gop(gop)
+    dec = hv.Decoder(W, H, chroma=True)
+    out = hv.alloc_out(W, H)
+    per = []
+    for t in range(n):
+        if t == 0:
+            dec.decode_iframe(hv.device_iframe(gop.iframe), out)
+        else:
+            dec.decode_pframe(hv.device_pframe(gop.pframes[t - 1]), out)
+        dec.sync()
+        rec, o8 = frames[t]
+        gpu = _planes(dec)
+        for p in range(3):
+            assert np.abs(gpu[p] - rec[p]).max() <= TOL_RECON, (t, p)
+            assert np.abs(to_np(out[p]).astype(int) - o8[p].astype(int)).max() <= 1, (t, p)
+        per.append([to_np(o).copy() for o in out])
+    dec2 = hv.Decoder(W, H, chroma=True)
+    outs = [hv.alloc_out(W, H) for _ in range(n)]
+    fr = [("i", hv.device_iframe(gop.iframe))] + [("p", hv.device_pframe(pf)) for pf in gop.pframes]
+    hv.decode_batch([dec2] * n, fr, outs)
+    dec2.sync()
+    for t in range(n):
+        for p in range(3):
+            assert np.array_equal(to_np(outs[t][p]), per[t][p]), (t, p)
+
+
 def test_fullhd_gop_head(hv):
     """Paper-scale frames (FullHD 4:2:0): the intra frame and two inter
     frames, every pixel against the oracle."""
