@@ -64,3 +64,25 @@ def test_reference_arm_nonzero_rank_exits_without_work(monkeypatch):
 
     monkeypatch.setenv("RANK", "1")
     assert bench.run_reference(bench.parse_args(["--impl", "reference"])) == 0
+
+
+def test_reference_arm_prints_one_contract_line(monkeypatch, capsys):
+    """Rank 0 of the reference arm times the oracle on the same workload and
+    prints one JSON line with the contract's keys."""
+    import json
+
+    import bench
+
+    monkeypatch.setenv("RANK", "0")
+    a = bench.parse_args(["--impl", "reference", "--width", "48", "--height", "32", "--frames", "3",
+                          "--steps", "1", "--warmup", "1"])
+    assert bench.run_reference(a) == 0
+    lines = [x for x in capsys.readouterr().out.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 1
+    assert d["dtype"] == "f64" and d["data"] == "synthetic" and d["n_gpus"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"]
