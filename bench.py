@@ -55,7 +55,7 @@ def parse_args(argv=None):
     p.add_argument("--frames", type=int, default=30)
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--iframe-tol", type=float, default=1e-8)
-    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--no-serve", action="store_true", help="skip the multi-stream serving measurement")
@@ -690,49 +690,23 @@ def main(argv=None):
             for o, oh in zip(out, out_h):
                 oh.copy_(o, non_blocking=True)
 
-    # the batch path: every input of the GOP up, one hivc_decode_batch call
-    # into one device output per frame, every output down
-    outs_e = [hivc.alloc_out(W, H) for _ in range(nfr)] if a.path == "batch" else None
-    outs_eh = [[torch.empty(o.shape, dtype=torch.uint8).pin_memory() for o in outs_e[0]] for _ in range(nfr)] \
-        if a.path == "batch" else None
-
-    def e2e_step_batch():
-        for k, v in host_i.items():
-            dev_i[k].copy_(v, non_blocking=True)
-        for hp, dp in zip(host_p, dev_p):
-            dp["flow"].copy_(hp["flow"], non_blocking=True)
-            for rh, rd in zip(hp["res"], dp["res"]):
-                for xh, xd in zip(rh, rd):
-                    xd.copy_(xh, non_blocking=True)
-        hivc.decode_batch(decs_b, [("i", dev_i)] + [("p", dp) for dp in dev_p], outs_e)
-        for oe, oh in zip(outs_e, outs_eh):
-            for o, h in zip(oe, oh):
-                h.copy_(o, non_blocking=True)
-
-    if a.path == "batch":
-        e2e_step = e2e_step_batch  # noqa: F811
-
-    # Pipelined (the batch path): step k's inputs go up on a copy stream
-    # into one of two device input sets while step k-1 decodes, and step
-    # k's outputs come down on a third stream from one of two output sets.
+    # Pipelined (the batch path): a GOP's inputs sit in one pinned host
+    # buffer (hivc.FramePack) and go up in one copy, on a copy stream, into
+    # one of two device input sets while the previous GOP decodes; its
+    # outputs are views of one device block (hivc.alloc_out_block) and come
+    # down in one copy on a third stream, from one of two output blocks.
     # Every step's copies happen inside the timed region; a buffer is
     # reused only after the work that read it is done.
     up_s, down_s = torch.cuda.Stream(), torch.cuda.Stream()
-    dev_i2 = [dev_i, {k: torch.empty_like(v, device="cuda") for k, v in host_i.items()}]
-    dev_p2 = [dev_p, [{"flow": torch.empty_like(p["flow"], device="cuda"),
-                       "res": [tuple(torch.empty_like(x, device="cuda") for x in r) for r in p["res"]]}
-                      for p in host_p]]
-    outs_e2 = [outs_e, [hivc.alloc_out(W, H) for _ in range(nfr)]] if a.path == "batch" else None
+    if a.path == "batch":
+        gop_frames = [("i", iframe_d)] + [("p", pf) for pf in pframes_d]
+        packs = [hivc.FramePack(gop_frames), hivc.FramePack(gop_frames)]
+        oblk = [hivc.alloc_out_block(nfr, W, H), hivc.alloc_out_block(nfr, W, H)]
+        oblk_h = torch.empty(oblk[0][0].numel(), dtype=torch.uint8).pin_memory()
+        h2d, d2h = packs[0].nbytes, oblk[0][0].numel()
 
     def upload(k):
-        di, dp_ = dev_i2[k & 1], dev_p2[k & 1]
-        for key, v in host_i.items():
-            di[key].copy_(v, non_blocking=True)
-        for hp, dp in zip(host_p, dp_):
-            dp["flow"].copy_(hp["flow"], non_blocking=True)
-            for rh, rd in zip(hp["res"], dp["res"]):
-                for xh, xd in zip(rh, rd):
-                    xd.copy_(xh, non_blocking=True)
+        packs[k & 1].upload()
 
     def e2e_pipelined(nsteps):
         ev = lambda: torch.cuda.Event()
@@ -751,15 +725,12 @@ def main(argv=None):
             stream.wait_event(up_done[k])
             if k >= 2:
                 stream.wait_event(down_done[k - 2])  # the output set of step k - 2 is down
-            frames = [("i", dev_i2[k & 1])] + [("p", dp) for dp in dev_p2[k & 1]]
-            hivc.decode_batch(decs_b, frames, outs_e2[k & 1])
+            hivc.decode_batch(decs_b, packs[k & 1].frames(), oblk[k & 1][1])
             dec_done[k] = ev()
             dec_done[k].record(stream)
             with torch.cuda.stream(down_s):
                 down_s.wait_event(dec_done[k])
-                for oe, oh in zip(outs_e2[k & 1], outs_eh):
-                    for o, h in zip(oe, oh):
-                        h.copy_(o, non_blocking=True)
+                oblk_h.copy_(oblk[k & 1][0], non_blocking=True)
                 down_done[k] = ev()
                 down_done[k].record(down_s)
         stream.wait_event(down_done[nsteps - 1])
@@ -811,8 +782,9 @@ def main(argv=None):
                       "path": "one decode call per frame"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "steps": a.e2e_steps,
-                    "mode": ("pipelined: a GOP's inputs go up on a copy stream while the previous GOP decodes, "
-                             "outputs come down on another (two buffer sets each), all inside the timed region")
+                    "mode": ("pipelined: a GOP's inputs go up in one copy from one pinned buffer (hivc.FramePack) "
+                             "on a copy stream while the previous GOP decodes, its outputs come down in one copy "
+                             "on another (two buffer sets each), all inside the timed region")
                     if a.path == "batch" else "serial: copies and decode on one stream"},
             "roofline": roof,
             "kernels": kernels,

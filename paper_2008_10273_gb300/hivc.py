@@ -476,6 +476,89 @@ def device_pframe(pfr, device="cuda", shared_chroma: bool = True):
     return {"flow": _dev(pfr.flow, device), "res": res}
 
 
+def _map_tensors(obj, fn):
+    """obj with every tensor t (in dicts, lists, tuples) replaced by fn(t)."""
+    import torch
+
+    if isinstance(obj, torch.Tensor):
+        return fn(obj)
+    if isinstance(obj, dict):
+        return {k: _map_tensors(v, fn) for k, v in obj.items()}
+    if isinstance(obj, (list, tuple)):
+        return type(obj)(_map_tensors(v, fn) for v in obj)
+    return obj
+
+
+class FramePack:
+    """The inputs of several frames in one pinned host buffer and one device
+    buffer of the same layout (every array at a 256-byte offset), so that a
+    single host-to-device copy moves all of them.
+
+    ``frames`` are ``("i" | "p", frame dict)`` as made by :func:`device_iframe`
+    and :func:`device_pframe` (tensors on any device).  :meth:`frames` gives
+    the same dicts with every tensor a view of the device buffer; an array
+    that several planes share (a shared chroma layout) stays one array, so
+    the decoder still sees the shared layout."""
+
+    def __init__(self, frames, device="cuda"):
+        import torch
+
+        place = {}
+        off = 0
+
+        def note(t):
+            nonlocal off
+            if id(t) not in place:
+                place[id(t)] = (t, off)
+                off += -(-t.numel() * t.element_size() // 256) * 256
+            return t
+
+        _map_tensors(list(frames), note)
+        self.nbytes = off
+        self.host = torch.empty(max(off, 256), dtype=torch.uint8)
+        if torch.cuda.is_available():
+            self.host = self.host.pin_memory()
+        self.device = torch.empty(max(off, 256), dtype=torch.uint8, device=device)
+        views = {}
+        for key, (t, o) in place.items():
+            n = t.numel() * t.element_size()
+            self.host[o:o + n].view(t.dtype).copy_(t.reshape(-1).cpu())
+            views[key] = self.device[o:o + n].view(t.dtype).view(t.shape)
+        self._frames = [(kind, _map_tensors(f, lambda t: views[id(t)])) for kind, f in frames]
+
+    def upload(self):
+        """One host-to-device copy of every input, on the current stream."""
+        self.device[:self.nbytes].copy_(self.host[:self.nbytes], non_blocking=True)
+
+    def frames(self):
+        return self._frames
+
+
+def alloc_out_block(n, width, height, chroma=True, device="cuda"):
+    """Output planes of n frames (as :func:`alloc_out`) as views of one
+    uint8 device buffer (planes at 256-byte offsets), so that one
+    device-to-host copy brings all of them back.  Returns (buffer, outs)."""
+    import torch
+
+    cw, ch = (width + 1) // 2, (height + 1) // 2
+    shapes = [(height, width)]
+    if int(chroma) == 2:
+        shapes += [(height, width)] * 2
+    elif chroma:
+        shapes += [(ch, cw)] * 2
+    sizes = [-(-h * w // 256) * 256 for h, w in shapes]
+    per = sum(sizes)
+    buf = torch.empty(max(n * per, 256), dtype=torch.uint8, device=device)
+    outs = []
+    for k in range(n):
+        o, planes = k * per, []
+        for (h, w), sz in zip(shapes, sizes):
+            planes.append(buf[o:o + h * w].view(h, w))
+            o += sz
+        outs.append(planes)
+    return buf[:n * per], outs
+
+
 def alloc_out(width, height, chroma=True, device="cuda"):
     """uint8 output planes: Y (+ Cb, Cr at 4:2:0); chroma=2: R, G, B."""
     import torch
