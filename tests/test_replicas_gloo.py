@@ -1,6 +1,7 @@
-"""Multi-GPU path of bench.py (independent replicas, Sec. 8(e) of the build
-plan): per-rank workloads and the max-over-ranks aggregation, run as two
-gloo ranks on CPU."""
+"""Multi-GPU path of bench.py (independent replicas: each rank decodes its
+own streams and no data moves between ranks): per-rank workloads and the
+max-over-ranks aggregation, run as two gloo ranks on CPU; and the reference
+arm's output line."""
 import os
 import socket
 
