@@ -616,6 +616,9 @@ def main(argv=None):
     # roofline of the dominant kernel family (kernel-timing pass)
     fam_ms = list(kstats.kernel_ms)
     fam_n = list(kstats.kernel_launches)
+    fam_px = list(kstats.kernel_pixels)
+    px_frame = W * H + 2 * ((W + 1) // 2) * ((H + 1) // 2)
+    px_per_launch = lambda f: fam_px[f] / fam_n[f] if fam_n[f] else px_frame
     cw, ch = (W + 1) // 2, (H + 1) // 2
     npts = sum(int(r.n_points) for r in gop.pframes[0].res)
     nblk = sum(int(r.n_blocks) for r in gop.pframes[0].res)
@@ -627,10 +630,13 @@ def main(argv=None):
         4: ("k_pframe.cu", W * H * (8 + 4 + 4 + 4 + 1) + 2 * cw * ch * (4 + 4 + 4 + 1)),
         # intra output: the solution hi/lo 8 B, new reference 4 B, uint8 1 B per pixel
         6: ("k_warp.cu", (W * H + 2 * cw * ch) * (8 + 4 + 1)),
+        # the intra families cover, launch by launch, only the planes that
+        # still need sweeps: their bytes per launch come from the pixels the
+        # library counted (average over the launches)
         # one SOR launch (4 sweeps): correction in/out 8 B, residual 4 B, mask 1 B per pixel
-        1: ("k_intra.cu", (W * H + 2 * cw * ch) * (4 + 4 + 1 + 4)),
+        1: ("k_intra.cu", (4 + 4 + 1 + 4) * px_per_launch(1)),
         # residual + update: hi/lo in 8 B, hi/lo out 8 B, correction 4 B, mask 1 B, residual 4 B
-        2: ("k_intra.cu", (W * H + 2 * cw * ch) * (8 + 8 + 4 + 1 + 4)),
+        2: ("k_intra.cu", (8 + 8 + 4 + 1 + 4) * px_per_launch(2)),
         # evaluation: the residual planes written; a batch launch covers
         # several frames (the GOP's inter frames over its launches)
         5: ("k_block.cu", (W * H + 2 * cw * ch) * 4 * ((nfr - 1) / max(1, fam_n[5] / kpass)
@@ -652,11 +658,14 @@ def main(argv=None):
         tr = NCU_TRAFFIC.get(hivc.KERNEL_FAMILIES[dom])
         traffic = None
         if tr and tr["sha"] == src_sha(os.path.join(ROOT, "paper_2008_10273_gb300", "csrc", srcf)):
-            traffic = tr["bytes"]
+            # the capture is of one launch over all planes; scaled to the
+            # average launch by the pixels it covers
+            traffic = tr["bytes"] * (px_per_launch(dom) / px_frame if dom in (1, 2) else 1.0)
         roof = {"kernel": hivc.KERNEL_FAMILIES[dom], "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                 "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "algorithmic_bytes_per_launch": b, "avg_launch_ms": avg_ms}
+                "algorithmic_bytes_per_launch": b, "avg_launch_ms": avg_ms,
+                "pixels_per_launch": px_per_launch(dom) if dom in (1, 2) else px_frame}
     kernels = {hivc.KERNEL_FAMILIES[i]: {"ms": fam_ms[i], "launches": fam_n[i],
                                          "share": fam_ms[i] / max(1e-9, sum(fam_ms))}
                for i in range(len(fam_ms)) if fam_n[i] > 0}

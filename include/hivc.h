@@ -191,6 +191,11 @@ typedef struct {
        6 intra output and the 4:4:4 colour path's pixels, 7 unused */
     float kernel_ms[HIVC_STAT_KERNELS];
     int32_t kernel_launches[HIVC_STAT_KERNELS];
+    /* per kernel family: pixels processed since the previous sync, the sum
+       over launches of the pixels of the planes each launch covers.  Set
+       for families 1 and 2, whose launches may cover only the planes that
+       still need sweeps; 0 for the others. */
+    int64_t kernel_pixels[HIVC_STAT_KERNELS];
 } hivc_stats;
 
 typedef struct hivc_decoder hivc_decoder;

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -20,6 +21,8 @@ using namespace hivc;
 namespace {
 
 constexpr int kPitchAlign = 32;  // elements
+// the layout the Python binding mirrors
+static_assert(sizeof(hivc_stats) == 184 && offsetof(hivc_stats, kernel_pixels) == 120, "hivc_stats layout");
 
 int round_up(int v, int a) { return (v + a - 1) / a * a; }
 
@@ -561,6 +564,7 @@ hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc
         Timed t(d, 2);
         cudaError_t er = launch_intra_residual(A, eb, add_e, st);
         t.done(1);
+        for (int k = 0; k < A.n; ++k) d->st.kernel_pixels[2] += (int64_t)A.p[k].width * A.p[k].height;
         if (er != cudaSuccess) return er;
         er = cudaMemcpyAsync(d->h_rnorm, d->rnorm, 3 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
         if (er != cudaSuccess) return er;
@@ -613,6 +617,7 @@ hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc
                 int l = 0;
                 e = launch_intra_sor(A, 0, done == 0, seg * spl, st, &eb, &l);
                 t.done(l);
+                for (int k = 0; k < A.n; ++k) d->st.kernel_pixels[1] += (int64_t)l * A.p[k].width * A.p[k].height;
             }
             if (e != cudaSuccess) return HIVC_E_CUDA;
             if (eb == 1)

@@ -74,7 +74,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("resid", c_f64 * 3), ("cycles", c_i32), ("sweeps", c_i32), ("fp64_blocks", c_i32),
                 ("large_blocks", c_i32), ("max_cond", c_f32), ("device_flags", c_u32),
                 ("frames", c_i32), ("launches", c_i32), ("kernel_ms", c_f32 * STAT_KERNELS),
-                ("kernel_launches", c_i32 * STAT_KERNELS)]
+                ("kernel_launches", c_i32 * STAT_KERNELS), ("kernel_pixels", ctypes.c_int64 * STAT_KERNELS)]
 
 
 _lib = None

@@ -55,6 +55,8 @@ def test_host_only_entry_points(hv):
     # struct layouts the binding relies on
     assert ctypes.sizeof(hv.Config) == 56
     assert ctypes.sizeof(hv.Residual) == 32
+    # hivc_stats: the per-family int64 pixel counts follow the launch counts
+    assert hv.Stats.kernel_pixels.offset == 120 and ctypes.sizeof(hv.Stats) == 184
 
 
 def test_oracle_is_not_reachable_from_the_product():
