@@ -235,7 +235,11 @@ hivc_status hivc_decode_pframe_coef(hivc_decoder *dec, const hivc_pframe_coef *f
    Decoders with intra frames run on host threads of their own (up to 32),
    so that their correction cycles overlap; a decoder stops at its first
    error, the others finish, and the call returns the first error in order
-   of the decoders' first frames (HIVC_E_NOT_CONVERGED only if no worse). */
+   of the decoders' first frames (HIVC_E_NOT_CONVERGED only if no worse).
+   The block launches of an inter run that follows an intra frame run on a
+   stream the decoder owns, beside the intra frame; the decoder's stream
+   waits for them (an event) before the run's first warp, so work queued on
+   the decoder's stream after the call is ordered after all of it. */
 hivc_status hivc_decode_batch(hivc_decoder *const *decs, const hivc_frame *frames, int32_t n,
                               const hivc_out *outs);
 
