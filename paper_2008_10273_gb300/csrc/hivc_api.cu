@@ -1024,8 +1024,10 @@ hivc_status decode_intra_then_run(hivc_decoder *d, const hivc_frame *frames, con
 namespace {
 
 // One decoder's frames of a batch, in array order: intra frames one by one,
-// each run of consecutive inter frames through decode_inter_run (shared
-// block launches).  Stops at the first error other than NOT_CONVERGED.
+// each run of consecutive inter frames with shared block launches (through
+// decode_intra_then_run when an intra frame precedes the run, so that the
+// run's block stage overlaps it; else decode_inter_run).  Stops at the
+// first error other than NOT_CONVERGED.
 hivc_status decode_own_frames(hivc_decoder *d, const hivc_frame *frames, const hivc_out *outs,
                               const std::vector<int> &ks)
 {
