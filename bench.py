@@ -59,8 +59,10 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--no-serve", action="store_true", help="skip the multi-stream serving measurement")
-    p.add_argument("--serve-gop", type=int, default=30,
-                   help="frames per stream in the serving measurement (1800 = 60 s at 30 fps; GOPs of 30 repeat)")
+    p.add_argument("--serve-gop", type=int, default=1800,
+                   help="frames per stream of the paced serving runs (1800 = 60 s at 30 fps; GOPs of 30 repeat)")
+    p.add_argument("--serve-saturated", type=int, default=300,
+                   help="frames per stream of the saturated serving runs (every frame there at t = 0)")
     p.add_argument("--no-next", action="store_true",
                    help="skip the coefficient-mode, biharmonic, 4:4:4 colour-path and batching measurements")
     p.add_argument("--path", choices=["batch", "plain"], default="batch",
@@ -203,20 +205,22 @@ def serve_measurement(a, gops=None):
     need = max(serve.stream_budget_bytes(s, 8) for s in streams(False))
     small = int(2.5 * need)
     res = {}
+    sat_n = min(a.serve_saturated, a.serve_gop)
     for name, sat, batched, bud in (("served", False, True, budget), ("plain", False, False, budget),
                                     ("saturated", True, True, budget), ("saturated_plain", True, False, budget),
                                     ("budget_limited", True, True, small)):
         srv = serve.Server(bud)
         srv.run(streams(sat, gop_len), batched=batched)  # warm-up (one GOP): decoders created and pooled
-        st = srv.run(streams(sat), batched=batched)
+        st = srv.run(streams(sat, sat_n if sat else None), batched=batched)
         srv.close()
         res[name] = {"value": st["fullhd_fps"], "unit": UNIT, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
                      "frames": st["frames"], "wall_s": st["wall_s"], "calls": st["calls"], "budget_bytes": bud,
                      "max_admitted_at_once": st["max_active"]}
     res["workload"] = (f"{sum(n for _, _, n in SERVE_MIX)} streams (8x1920x1080, 4x1280x720, 4x854x480, 4:2:0), "
-                       f"{a.serve_gop} frames each (GOPs of {gop_len}); arrivals 30 fps per stream + Exp(3 ms) jitter "
-                       f"(saturated: all at t=0); HBM budget 40 GB; latency = arrival to completion event; "
-                       f"measured on a warm server (second pass, idle decoders reused)")
+                       f"paced runs {a.serve_gop} frames each ({a.serve_gop / 30:g} s of video, GOPs of {gop_len}) "
+                       f"arriving at 30 fps per stream + Exp(3 ms) jitter; saturated runs {sat_n} frames each, all "
+                       f"at t=0; HBM budget 40 GB; latency = arrival to completion event; measured on a warm server "
+                       f"(second pass, idle decoders reused)")
     return res
 
 
@@ -622,27 +626,37 @@ def main(argv=None):
     cw, ch = (W + 1) // 2, (H + 1) // 2
     npts = sum(int(r.n_points) for r in gop.pframes[0].res)
     nblk = sum(int(r.n_blocks) for r in gop.pframes[0].res)
+    # Algorithmic bytes per launch, by kernel family: (kernel source, bytes,
+    # how they are counted).  The intra families cover, launch by launch, only
+    # the planes that still need sweeps, so their bytes come from the pixels
+    # the library counted (average over the launches).
+    sweeps_per_launch = 4
+    fused_frame = W * H * (8 + 4 + 4 + 1) + 2 * cw * ch * (4 + 4 + 1) + npts * 3 + nblk * 4
+    inter_frames_per_step = (nfr - 1)
     bytes_per_launch = {
-        # family: (kernel source, algorithmic bytes per launch)
-        # inter pixels: flow 8 B + reference 4 B + residual plane 4 B + new
-        # reference 4 B + uint8 1 B per luma pixel, 4 + 4 + 4 + 1 B per chroma
-        # pixel (the chroma flow comes from the luma flow read once)
-        4: ("k_pframe.cu", W * H * (8 + 4 + 4 + 4 + 1) + 2 * cw * ch * (4 + 4 + 4 + 1)),
-        # intra output: the solution hi/lo 8 B, new reference 4 B, uint8 1 B per pixel
-        6: ("k_warp.cu", (W * H + 2 * cw * ch) * (8 + 4 + 1)),
-        # the intra families cover, launch by launch, only the planes that
-        # still need sweeps: their bytes per launch come from the pixels the
-        # library counted (average over the launches)
-        # one SOR launch (4 sweeps): correction in/out 8 B, residual 4 B, mask 1 B per pixel
-        1: ("k_intra.cu", (4 + 4 + 1 + 4) * px_per_launch(1)),
+        # a red-black sweep reads and writes the iterate (8 B) and reads the
+        # mask (1 B) per pixel; a launch runs 4 sweeps over the pixels it covers
+        1: ("k_intra.cu", 9 * sweeps_per_launch * px_per_launch(1),
+            "9 B per pixel per red-black sweep (iterate read + write 8 B, mask 1 B) x 4 sweeps per launch x "
+            "the pixels the launch covers"),
         # residual + update: hi/lo in 8 B, hi/lo out 8 B, correction 4 B, mask 1 B, residual 4 B
-        2: ("k_intra.cu", (8 + 8 + 4 + 1 + 4) * px_per_launch(2)),
+        2: ("k_intra.cu", (8 + 8 + 4 + 1 + 4) * px_per_launch(2),
+            "25 B per pixel (float-float iterate in and out, correction, mask, residual)"),
+        # inter pixels against the fused inter frame: flow 8 B + reference 4 B
+        # + new reference 4 B + uint8 1 B per luma pixel, 4 + 4 + 1 B per
+        # chroma pixel (the chroma flow comes from the luma flow read once),
+        # plus the block data (3 B per point, 4 B per block pointer)
+        4: ("k_pframe.cu", fused_frame,
+            "the fused inter frame: 17 B per luma pixel (flow 8, reference 4, new reference 4, uint8 1), 9 B per "
+            "chroma pixel, 3 B per residual point, 4 B per block"),
+        # intra output: the solution hi/lo 8 B, new reference 4 B, uint8 1 B per pixel
+        6: ("k_warp.cu", (W * H + 2 * cw * ch) * (8 + 4 + 1), "13 B per pixel"),
         # evaluation: the residual planes written; a batch launch covers
         # several frames (the GOP's inter frames over its launches)
-        5: ("k_block.cu", (W * H + 2 * cw * ch) * 4 * ((nfr - 1) / max(1, fam_n[5] / kpass)
-                                                       if a.path == "batch" else 1)),
+        5: ("k_block.cu", (W * H + 2 * cw * ch) * 4 * (inter_frames_per_step / max(1, fam_n[5] / kpass)
+                                                       if a.path == "batch" else 1),
+            "4 B per pixel of residual plane written"),
     }
-    dom = max(range(len(fam_ms)), key=lambda i: fam_ms[i])
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -650,22 +664,40 @@ def main(argv=None):
     except OSError:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    roof = None
-    if dom in bytes_per_launch and fam_n[dom] > 0:
-        srcf, b = bytes_per_launch[dom]
-        avg_ms = fam_ms[dom] / fam_n[dom]
+    peak_source = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    def fam_roof(f):
+        if f not in bytes_per_launch or fam_n[f] == 0:
+            return None
+        srcf, b, how = bytes_per_launch[f]
+        avg_ms = fam_ms[f] / fam_n[f]
         achieved = b / (avg_ms / 1e3) / 1e9
-        tr = NCU_TRAFFIC.get(hivc.KERNEL_FAMILIES[dom])
+        tr = NCU_TRAFFIC.get(hivc.KERNEL_FAMILIES[f])
         traffic = None
         if tr and tr["sha"] == src_sha(os.path.join(ROOT, "paper_2008_10273_gb300", "csrc", srcf)):
-            # the capture is of one launch over all planes; scaled to the
-            # average launch by the pixels it covers
-            traffic = tr["bytes"] * (px_per_launch(dom) / px_frame if dom in (1, 2) else 1.0)
-        roof = {"kernel": hivc.KERNEL_FAMILIES[dom], "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+            # a capture of one launch over all planes, scaled to the average
+            # launch by the pixels it covers
+            traffic = tr["bytes"] * (px_per_launch(f) / px_frame if f in (1, 2) else 1.0)
+        return {"kernel": hivc.KERNEL_FAMILIES[f], "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                 "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "algorithmic_bytes_per_launch": b, "avg_launch_ms": avg_ms,
-                "pixels_per_launch": px_per_launch(dom) if dom in (1, 2) else px_frame}
+                "dram_frac": (traffic / (avg_ms / 1e3) / 1e9 / hbm_peak) if traffic else None,
+                "peak_source": peak_source, "algorithmic_bytes_per_launch": b, "accounting": how,
+                "avg_launch_ms": avg_ms, "launches": fam_n[f],
+                "pixels_per_launch": px_per_launch(f) if f in (1, 2) else px_frame}
+
+    dom = max(range(len(fam_ms)), key=lambda i: fam_ms[i])
+    roof = fam_roof(dom)
+    if roof is not None:
+        roof["kernels"] = {hivc.KERNEL_FAMILIES[f]: fam_roof(f) for f in (1, 4, 5, 2) if fam_n[f] > 0}
+        # a whole inter frame (block coefficients, residual planes, pixels)
+        # against the fused frame's bytes
+        inter_ms = sum(fam_ms[f] for f in (3, 4, 5)) / max(1, kpass * inter_frames_per_step)
+        roof["kernels"]["inter_frame"] = {
+            "bound": "hbm", "ms": inter_ms, "algorithmic_bytes": fused_frame,
+            "achieved": fused_frame / (inter_ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+            "frac": fused_frame / (inter_ms / 1e3) / 1e9 / hbm_peak,
+            "accounting": "one inter frame's block coefficients + residual planes + pixels (kernel-timing pass) "
+                          "against the fused frame's algorithmic bytes"}
     kernels = {hivc.KERNEL_FAMILIES[i]: {"ms": fam_ms[i], "launches": fam_n[i],
                                          "share": fam_ms[i] / max(1e-9, sum(fam_ms))}
                for i in range(len(fam_ms)) if fam_n[i] > 0}

@@ -46,7 +46,8 @@ typedef enum {
     HIVC_E_NOT_CONVERGED = -4, /* intra solve hit max_cycles above iframe_tol */
     HIVC_E_NO_REFERENCE = -5,  /* inter frame before any intra frame */
     HIVC_E_BUDGET = -6,        /* footprint above the caller's budget */
-    HIVC_E_TIMEOUT = -7        /* a bounded device wait gave up */
+    HIVC_E_TIMEOUT = -7        /* reserved: no entry point returns it (no
+                                  kernel of the library waits on another) */
 } hivc_status;
 
 /* Decoder configuration.  hivc_config_default() fills the defaults. */
@@ -268,6 +269,17 @@ hivc_status hivc_decoder_set_timing(hivc_decoder *dec, int32_t on);
 hivc_status hivc_decoder_reference(const hivc_decoder *dec, int32_t plane, const float **ptr,
                                    int32_t *width, int32_t *height, int32_t *pitch);
 
+/* Device pointers to the iterate of the last intra frame's diffusion solve
+   (Sec. 2.1, Eq. 1) of one plane: the float-float pair u = hi + lo (lo is
+   NULL with precision = 1), FP32 planes of the given size and pitch in
+   floats, before the optional residual and the clamp to [0, 255].  The
+   solve's reported residual (hivc_stats.resid) is max |(L u)_i| over the
+   unknown pixels of this u, which a caller can recompute in FP64 from
+   hi + lo.  Valid until the next intra frame (its work must be complete:
+   hivc_decoder_sync); HIVC_E_NO_REFERENCE before any intra frame. */
+hivc_status hivc_decoder_intra_solution(const hivc_decoder *dec, int32_t plane, const float **hi,
+                                        const float **lo, int32_t *width, int32_t *height, int32_t *pitch);
+
 /* The stream the decoder runs on. */
 void *hivc_decoder_stream(const hivc_decoder *dec);
 
@@ -287,9 +299,10 @@ size_t hivc_block_residual_workspace_bytes(int32_t width, int32_t height, int32_
 /* Residual plane r (width x height floats, row pitch r_pitch floats) from
    block data (Sec. 2.2, Eqs. 2-4): per block, the (K+1) x (K+1) system in
    the Green's function at the block's points is solved (coefficients c
-   summing to zero and the constant a), then r = sum_j c_j g_j + a over the
-   block through the DCT-II diagonalisation (Eq. 4); r equals the data at
-   the points.  workspace: device scratch of at least
+   summing to zero and the constant a), then r = sum_j c_j g_j + a (Eq. 3)
+   is summed over the block from the rows of its precomputed Green's
+   matrix (built once per block shape from the DCT-II diagonalisation of
+   Eq. 4); r equals the data at the points.  workspace: device scratch of at least
    hivc_block_residual_workspace_bytes() bytes.  flags: optional device
    uint32 that receives error bits for bad blocks (those blocks are zero).
    HIVC_E_INVALID for bad sizes or a short workspace. */
@@ -310,8 +323,9 @@ hivc_status hivc_block_residual_coef(int32_t width, int32_t height, int32_t bloc
    the coefficient scratch taken from a fixed array inside the library
    instead of a caller workspace.  The paper has no counterpart; this is
    for callers that cannot allocate device memory when they need the
-   residual (while capturing a stream into a graph, or under a fixed memory
-   budget where every allocation is made up front).
+   residual: a host under a fixed memory budget whose every allocation is
+   made at start-up, or a latency-bound loop where a cudaMalloc or cudaFree
+   (which may synchronise the whole device) would stall other streams.
    Limits: at most 131072 residual points and 16384 blocks per call, else
    HIVC_E_INVALID.  The array (about 17 MB: room for one block with more
    than 32 points per range of 128 blocks) exists once per device on which

@@ -121,6 +121,8 @@ struct hivc_decoder {
     // intra scratch
     float *uh[2][3]{}, *ul[2][3]{};
     float *res[3]{}, *e[2][3]{};
+    // the buffers holding the last intra frame's iterate (hi, lo) per plane
+    const float *sol_hi[3]{}, *sol_lo[3]{};
     uint8_t *mask[3]{};
     unsigned long long *vsum = nullptr;
     unsigned int *rnorm = nullptr;
@@ -310,7 +312,7 @@ const char *hivc_status_str(hivc_status s)
     case HIVC_E_NOT_CONVERGED: return "intra solve did not reach the tolerance";
     case HIVC_E_NO_REFERENCE: return "inter frame before any intra frame";
     case HIVC_E_BUDGET: return "over the device-memory budget";
-    case HIVC_E_TIMEOUT: return "bounded device wait timed out";
+    case HIVC_E_TIMEOUT: return "reserved status (bounded device wait)";
     }
     return "unknown status";
 }
@@ -455,6 +457,19 @@ hivc_status hivc_decoder_reset(hivc_decoder *d)
 {
     if (!d) return HIVC_E_INVALID;
     d->has_ref = false;
+    return HIVC_OK;
+}
+
+hivc_status hivc_decoder_intra_solution(const hivc_decoder *d, int32_t plane, const float **hi, const float **lo,
+                                        int32_t *w, int32_t *h, int32_t *pitch)
+{
+    if (!d || plane < 0 || plane >= d->np || !hi || !lo) return HIVC_E_INVALID;
+    if (!d->sol_hi[plane]) return HIVC_E_NO_REFERENCE;
+    *hi = d->sol_hi[plane];
+    *lo = d->sol_lo[plane];
+    if (w) *w = d->pg[plane].w;
+    if (h) *h = d->pg[plane].h;
+    if (pitch) *pitch = d->pg[plane].pitch;
     return HIVC_OK;
 }
 
@@ -664,6 +679,10 @@ hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc
     }
     bool converged = true;
     for (int p = 0; p < d->np; ++p) converged = converged && rn[p] <= tol;
+    for (int p = 0; p < d->np; ++p) {
+        d->sol_hi[p] = J.p[p].uh[0];
+        d->sol_lo[p] = J.p[p].ff ? J.p[p].ul[0] : nullptr;
+    }
     // optional residual correction of the intra frame (Fig. 1e/f)
     if (f->res) {
         hivc_status s = run_block_residual(d, f->res);
@@ -1165,7 +1184,6 @@ hivc_status hivc_decoder_sync(hivc_decoder *d, hivc_stats *last)
     fresh.cycles = d->st.cycles;
     fresh.sweeps = d->st.sweeps;
     d->st = fresh;
-    if (fl & kFlagTimeout) return HIVC_E_TIMEOUT;
     return (fl & ~kFlagCond) ? HIVC_E_INVALID : HIVC_OK;
 }
 

@@ -22,7 +22,7 @@ enum : uint32_t {
     kFlagPos = 1u << 2,       // position outside the block or not increasing
     kFlagNotSPD = 1u << 3,    // non-positive Cholesky pivot
     kFlagMaskIdx = 1u << 4,   // intra mask index out of range or not increasing
-    kFlagTimeout = 1u << 5,   // a bounded wait on tensor-memory copies gave up
+    // bit 5 is unused (no kernel of the library waits on another)
     kFlagCond = 1u << 6,      // information, not an error: a block above the
                               // condition threshold kept its FP32 solution
                               // (K > kF64MaxK: no room for the FP64 system)

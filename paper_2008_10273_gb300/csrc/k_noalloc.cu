@@ -2,9 +2,10 @@
 // without any device allocation by the library or the caller.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// residual plane: code running while a stream is being captured into a
-// graph, or a host that hands the library a fixed memory budget in which
-// every allocation has already been made.  For them the scratch that the
+// residual plane: a host that hands the library a fixed memory budget in
+// which every allocation was made at start-up, or a latency-bound loop in
+// which a cudaMalloc or cudaFree (which may synchronise the whole device)
+// would stall the work of other streams.  For them the scratch that the
 // coefficient stage needs (per-point coefficients, per-block constants and
 // room for one system with more than 32 points per range of 128 blocks)
 // lives in a fixed-size array in the library's device image instead of a

@@ -96,6 +96,8 @@ PROTOTYPES = [
     ("hivc_set_sor_variant", c_i32, [c_i32]),
     ("hivc_decoder_reference", c_i32, [c_vp, c_i32, ctypes.POINTER(c_vp), ctypes.POINTER(c_i32),
                                        ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
+    ("hivc_decoder_intra_solution", c_i32, [c_vp, c_i32, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp),
+                                            ctypes.POINTER(c_i32), ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
     ("hivc_decoder_stream", c_vp, [c_vp]),
     ("hivc_decoder_destroy", None, [c_vp]),
     ("hivc_status_str", ctypes.c_char_p, [c_i32]),
@@ -326,6 +328,22 @@ class Decoder:
         arr = _DeviceArray(p.value, (h.value, w.value), "<f4", (pitch.value * 4, 4))
         torch.cuda.synchronize()
         return torch.as_tensor(arr, device="cuda").clone()
+
+
+    def intra_solution(self, plane: int):
+        """Copies (hi, lo) of the last intra frame's diffusion iterate of one
+        plane as FP32 torch tensors (lo is None in FP32-only mode); the
+        solution is hi + lo."""
+        import torch
+
+        hi, lo, w, h, pitch = c_vp(), c_vp(), c_i32(), c_i32(), c_i32()
+        check(lib().hivc_decoder_intra_solution(self.handle, plane, ctypes.byref(hi), ctypes.byref(lo),
+                                                ctypes.byref(w), ctypes.byref(h), ctypes.byref(pitch)),
+              "hivc_decoder_intra_solution")
+        torch.cuda.synchronize()
+        get = lambda p: torch.as_tensor(_DeviceArray(p, (h.value, w.value), "<f4", (pitch.value * 4, 4)),
+                                        device="cuda").clone()
+        return get(hi.value), (get(lo.value) if lo.value else None)
 
 
 def decode_batch(decoders: Sequence[Decoder], frames, outs) -> int:

@@ -132,3 +132,60 @@ def test_invalid_inputs(oracle_lib):
         oracle_lib.inpaint(4, 4, np.array([16], np.uint32), np.array([1.0]))
     with pytest.raises(RuntimeError):
         oracle_lib.inpaint(4, 4, np.zeros(0, np.uint32), np.zeros(0))
+
+
+# ---------------------------------------------------------------------------
+# the residual of Eq. (1), max over unknown pixels of |(L u)_i|, pinned by
+# fields whose 5-point Laplacian with reflecting boundaries is known by hand
+# ---------------------------------------------------------------------------
+def test_residual_of_a_parabola_is_two(oracle_lib):
+    """u = x^2 with columns 0 and W-1 on the mask: every unknown pixel has
+    both horizontal neighbours, (x+1)^2 + (x-1)^2 - 2x^2 = 2, and u is
+    constant along y, so the vertical terms vanish even at the reflecting
+    top and bottom edges.  The residual is exactly 2."""
+    W, H = 9, 5
+    u = np.tile((np.arange(W, dtype=np.float64) ** 2)[None, :], (H, 1))
+    idx = np.array([y * W + x for y in range(H) for x in (0, W - 1)], np.uint32)
+    assert oracle_lib.inpaint_residual(u, idx) == 2.0
+    # a parabola along y with rows 0 and H-1 masked: the same by symmetry
+    v = np.tile((np.arange(H, dtype=np.float64) ** 2)[:, None], (1, W))
+    idy = np.array([y * W + x for y in (0, H - 1) for x in range(W)], np.uint32)
+    assert oracle_lib.inpaint_residual(v, idy) == 2.0
+
+
+@pytest.mark.parametrize("x,y,expect", [(4, 2, 4.0), (0, 2, 3.0), (0, 0, 2.0), (8, 4, 2.0)])
+def test_residual_of_a_unit_spike_counts_neighbours(oracle_lib, x, y, expect):
+    """u = 1 at one unknown pixel, 0 elsewhere: there (L u) = -(number of
+    in-image neighbours), 4 inside, 3 on an edge, 2 in a corner (a missing
+    neighbour contributes nothing under reflecting boundaries); each
+    neighbour sees +1.  With the spike itself on the mask only the
+    neighbours count: the residual drops to 1."""
+    W, H = 9, 5
+    u = np.zeros((H, W))
+    u[y, x] = 1.0
+    far = np.array([0 if (x, y) != (0, 0) else W * H - 1], np.uint32)  # a mask point away from the spike
+    if (x, y) == (8, 4):
+        far = np.array([0], np.uint32)
+    assert oracle_lib.inpaint_residual(u, far) == expect
+    on = np.array([y * W + x], np.uint32)
+    assert oracle_lib.inpaint_residual(u, on) == 1.0
+
+
+def test_residual_ignores_masked_pixels_and_sees_the_worst_unknown(oracle_lib):
+    """A harmonic field (x^2 - y^2 has L u = 0 off the boundary) masked on
+    its whole border has residual 0; lifting one unknown pixel by d makes
+    the residual 4 d (at that pixel), while lifting a mask pixel by d
+    changes only its unknown neighbours, by d."""
+    W, H = 7, 6
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    u = xx ** 2 - yy ** 2
+    border = np.array([y * W + x for y in range(H) for x in range(W)
+                       if x in (0, W - 1) or y in (0, H - 1)], np.uint32)
+    assert oracle_lib.inpaint_residual(u, border) == 0.0
+    d = 0.375
+    up = u.copy()
+    up[3, 3] += d
+    assert oracle_lib.inpaint_residual(up, border) == 4 * d
+    um = u.copy()
+    um[0, 3] += d  # a mask pixel on the top edge: its unknown neighbour (3, 1) sees +d
+    assert oracle_lib.inpaint_residual(um, border) == d

@@ -1,9 +1,11 @@
 """hivc_block_residual_static: the residual plane without any device
 allocation, for callers that cannot allocate device memory when they need it
-(during stream capture, or under a fixed memory budget).  It must give the
+(a host whose memory budget is fully reserved at start-up, or a latency-bound
+loop in which an allocation could synchronise the device).  It must give the
 same plane as hivc_block_residual, which uses a caller workspace, on calls
 made one after another (the second call reuses the library's scratch array
-that the first one left behind).
+that the first one left behind), with or without a caller error word, and
+on a call exactly at its limits.
 
 This file is collected last on purpose: if it fails, a run that stops at the
 first failure has already run every other test."""
@@ -49,6 +51,46 @@ def test_matches_workspace_entry_point_on_consecutive_calls():
         assert np.all(np.isfinite(got))
         assert np.abs(got - ref).max() <= TOL_BLOCK
     assert int(flags.item()) == 0
+
+
+def test_without_a_caller_error_word():
+    """flags = NULL: the entry point clears its own error word inside the
+    scratch array before its kernels run (two calls in a row, the first of
+    them with bad block data that leaves bits in that word)."""
+    hv = hivc_module()
+    rng = np.random.default_rng(22)
+    good = make_residual(rng, 131, 67, 16, 6.0, 64)
+    bad = make_residual(rng, 131, 67, 16, 6.0, 64)
+    bad.pos = bad.pos.copy()
+    b = int(np.argmax(np.diff(bad.block_ptr.astype(np.int64)) >= 2))
+    s = int(bad.block_ptr[b])
+    bad.pos[s], bad.pos[s + 1] = bad.pos[s + 1], bad.pos[s]  # not increasing: that block reads as zero
+    for res in (bad, good, good):
+        got = _without_allocation(hv, res, None)
+        ref = _with_workspace(hv, res)
+        assert np.all(np.isfinite(got))
+        assert np.abs(got - ref).max() <= TOL_BLOCK
+
+
+def test_at_exactly_its_limits():
+    """16384 blocks of 16 x 16 (a 2048 x 2048 plane) with 8 points each:
+    131072 points, both limits reached and accepted."""
+    hv = hivc_module()
+    rng = np.random.default_rng(23)
+    W = H = 2048
+    nb = (W // 16) * (H // 16)
+    keys = rng.random((nb, 256))
+    pos = np.sort(np.argsort(keys, axis=1)[:, :8], axis=1).astype(np.uint8).reshape(-1)
+    bp = (np.arange(nb + 1) * 8).astype(np.uint32)
+    val = rng.integers(-64, 65, size=nb * 8).astype(np.int16)
+    from workload.synth import Residual
+
+    res = Residual(W, H, 16, bp, pos, val)
+    assert res.n_points == 1 << 17 and res.n_blocks == 1 << 14
+    got = _without_allocation(hv, res, None)
+    ref = _with_workspace(hv, res)
+    assert np.all(np.isfinite(got))
+    assert np.abs(got - ref).max() <= TOL_BLOCK
 
 
 def test_rejects_inputs_beyond_its_limits():
