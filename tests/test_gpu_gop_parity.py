@@ -29,6 +29,9 @@ def test_benchmarked_gop_frame_by_frame(hv):
         assert max(r["u8_max_diff"]) <= 1, (t, r["u8_max_diff"])
         assert r["batch_equals_prefix"], t
     assert rep["frames"][0]["mask_exact"]
+    # the FP32 chain's drift over 29 inter frames (about 9e-5 measured) stays
+    # far inside the bar
+    assert rep["max_abs_err"] <= 1e-3, rep["max_abs_err"]
     print({r["frame"]: [round(x, 6) for x in r["max_abs_err"]] for r in rep["frames"]})
 
 
