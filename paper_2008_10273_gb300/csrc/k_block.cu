@@ -605,11 +605,13 @@ __global__ void __launch_bounds__(kCoefThreads, 3) block_coef_kernel(const __gri
 }
 
 // ---- evaluation stage into residual fields, one warp per block -----------
-// Lane l covers the block pixels 8l .. 8l+7 (index y w + x).  The points sit
-// in the lanes, 32 at a time; c_j and p_j reach every lane by shuffles, and
-// the Green's rows of several points are in flight (16-byte loads) before
-// their products are summed.  The constant a is loaded beside the block
-// pointers.  A 16-wide block row goes out as two 16-byte stores per lane;
+// Lane l covers the block pixels 4l .. 4l+3 and 128 + 4l .. 128 + 4l + 3
+// (index y w + x).  The points sit in the lanes, 32 at a time; c_j and p_j
+// reach every lane by shuffles, and the Green's rows of several points are
+// in flight (16-byte loads, each warp instruction 512 contiguous bytes)
+// before their products are summed.  The constant a is loaded beside the
+// block pointers.  A 16-wide block goes out as 16-byte stores (a lane's
+// four pixels of rows l / 4 and 8 + l / 4);
 // then the data at the points, exactly.  Bad positions give a zero block.
 // QC (coefficient mode): c_j from the dead-zone indices, a transmitted, no
 // overwrite at the points; K = 0 gives r = a.  An index -128 gives a zero
@@ -620,8 +622,11 @@ __device__ __forceinline__ void eval_block(const BlockPlane &P, const BlockGeom 
                                            uint32_t *flags)
 {
     const int K = g.K, w = g.w, N = g.w * g.h, rl = g_rowlen(N);
-    const int q0 = 8 * lane;
-    const bool act = q0 < N;
+    // lane l covers pixels 4l .. 4l+3 and 128 + 4l .. 128 + 4l + 3: each
+    // 16-byte load instruction of the warp reads 512 contiguous bytes of a
+    // Green's row (four 128-byte lines)
+    const int q0 = 4 * lane, q1 = 128 + 4 * lane;
+    const bool act = q0 < N, act1 = q1 < N;
     float r0[8], r1[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
@@ -659,15 +664,16 @@ __device__ __forceinline__ void eval_block(const BlockPlane &P, const BlockGeom 
         prev = __shfl_sync(0xffffffffu, p, 31);
         if (!valid) break;
         const int n = min(32, K - j0);
-        const float *Gq = G + q0;
+        const float *Gq = G + q0;  // + 128 for the second half
 #pragma unroll 4
         for (int u = 0; u < n; ++u) {
             const float cu0 = __shfl_sync(0xffffffffu, c0, u);
             const float cu1 = TWO ? __shfl_sync(0xffffffffu, c1, u) : 0.f;
             const int pu = __shfl_sync(0xffffffffu, p, u);
             if (act) {
-                const float4 *row = reinterpret_cast<const float4 *>(Gq + pu * rl);
-                const float4 lo = __ldg(row), hi = __ldg(row + 1);
+                const float *row = Gq + pu * rl;
+                const float4 lo = __ldg(reinterpret_cast<const float4 *>(row));
+                const float4 hi = act1 ? __ldg(reinterpret_cast<const float4 *>(row + 128)) : make_float4(0.f, 0.f, 0.f, 0.f);
                 const float gv[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
@@ -687,25 +693,23 @@ __device__ __forceinline__ void eval_block(const BlockPlane &P, const BlockGeom 
                                   (uintptr_t)pitch * 4) & 15) == 0;
     if (act) {
         if (vec) {
-            // pixels 8l .. 8l+7 are columns 8 (l % 2) .. +7 of row l / 2
-            const size_t o = (size_t)(lane >> 1) * pitch + 8 * (lane & 1);
+            // pixels 4l .. 4l+3 are columns 4 (l % 4) .. +3 of row l / 4,
+            // the second half the same columns of row 8 + l / 4
+            const size_t o = (size_t)(lane >> 2) * pitch + 4 * (lane & 3), o1 = o + (size_t)8 * pitch;
             reinterpret_cast<float4 *>(R0 + o)[0] = make_float4(r0[0], r0[1], r0[2], r0[3]);
-            reinterpret_cast<float4 *>(R0 + o)[1] = make_float4(r0[4], r0[5], r0[6], r0[7]);
+            if (act1) reinterpret_cast<float4 *>(R0 + o1)[0] = make_float4(r0[4], r0[5], r0[6], r0[7]);
             if (TWO && R1) {
                 reinterpret_cast<float4 *>(R1 + o)[0] = make_float4(r1[0], r1[1], r1[2], r1[3]);
-                reinterpret_cast<float4 *>(R1 + o)[1] = make_float4(r1[4], r1[5], r1[6], r1[7]);
+                if (act1) reinterpret_cast<float4 *>(R1 + o1)[0] = make_float4(r1[4], r1[5], r1[6], r1[7]);
             }
         } else {
-            int y = q0 / w, x = q0 - y * w;
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
-                if (q0 + t < N) {
+                const int q = (t < 4 ? q0 : q1 - 4) + t;
+                if (q < N) {
+                    const int y = q / w, x = q - y * w;
                     R0[(size_t)y * pitch + x] = r0[t];
                     if (TWO && R1) R1[(size_t)y * pitch + x] = r1[t];
-                }
-                if (++x == w) {
-                    x = 0;
-                    ++y;
                 }
             }
         }

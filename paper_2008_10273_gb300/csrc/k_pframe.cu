@@ -8,9 +8,13 @@
 // 2 qy, 2 qy + 1 and, with chroma, the co-sited pixel (qx, qy) of Cb and
 // Cr.  Every access is a coalesced global load or store: the reference
 // samples of neighbouring threads share cache lines, so each reference line
-// comes from HBM about once.  (Variants that staged macroblock tiles of the
-// flow and the references in shared memory with the tensor memory
-// accelerator measured slower on this gather pattern.)
+// comes from HBM about once.  Whole quads of even-width planes take 16-byte
+// flow loads and issue all 24 bilinear samples before any store (about 12 %
+// faster than a pixel at a time, same values); edge quads and odd widths go
+// a pixel at a time.  (Variants that staged macroblock tiles of the flow and
+// the references in shared memory with the tensor memory accelerator, and
+// one that shared a 3 x 3 patch between the quad's samples, were not
+// faster on this gather pattern.)
 #include "hivc_internal.cuh"
 
 namespace hivc {
@@ -29,6 +33,15 @@ __device__ __forceinline__ int split_axis(float d, int x, int n, float &a)
     return max(min(i0, n - 2), 0);
 }
 
+// bilinear interpolation of the corners r00, r01 (next column), r10 (next
+// row), r11 with weights ax (columns) and ay (rows)
+__device__ __forceinline__ float lerp2(float ax, float ay, float r00, float r01, float r10, float r11)
+{
+    const float top = fmaf(ax, r01 - r00, r00);
+    const float bot = fmaf(ax, r11 - r10, r10);
+    return fmaf(ay, bot - top, top);
+}
+
 // bilinear sample of R at (x + dx, y + dy), sample position clamped
 __device__ __forceinline__ float sample(const float *__restrict__ R, int pitch, int W, int H, int x, int y, float dx,
                                         float dy)
@@ -39,32 +52,105 @@ __device__ __forceinline__ float sample(const float *__restrict__ R, int pitch, 
     const float *g = R + (size_t)y0 * pitch + x0;
     const float r00 = __ldg(g), r01 = __ldg(g + ox), r10 = __ldg(g + (size_t)oyn * pitch),
                 r11 = __ldg(g + (size_t)oyn * pitch + ox);
-    const float top = fmaf(ax, r01 - r00, r00);
-    const float bot = fmaf(ax, r11 - r10, r10);
-    return fmaf(ay, bot - top, top);
+    return lerp2(ax, ay, r00, r01, r10, r11);
 }
 
-// residual + prediction, clamped to [0, 255]: the new FP32 reference and
+// residual + prediction, clamped to [0, 255]: the new FP32 reference
+__device__ __forceinline__ float recon(float pred, float r) { return fminf(fmaxf(pred + r, 0.f), 255.f); }
 // the uint8 output (round half up)
+__device__ __forceinline__ uint8_t to_u8(float v) { return (uint8_t)__float2int_rd(v + 0.5f); }
+
 __device__ __forceinline__ void put_pixel(float pred, float r, float *ref_out, uint8_t *out)
 {
-    const float v = fminf(fmaxf(pred + r, 0.f), 255.f);
+    const float v = recon(pred, r);
     *ref_out = v;
-    *out = (uint8_t)__float2int_rd(v + 0.5f);
+    *out = to_u8(v);
 }
 
 constexpr int kQX = 32, kQY = 4;  // quads per CTA: 32 x 4 (128 threads)
 
+// A whole quad of an even-width plane with 8-byte aligned rows (the host
+// checks pointers and pitches): the quad's flow as two 16-byte loads, its
+// luma residual as two 8-byte loads, and every bilinear sample of the quad
+// (16 luma, 8 chroma) issued before any store, so that they are in flight
+// together; the new reference and the output go out as row pairs.  The
+// arithmetic is the scalar path's, value for value.
 template <bool CHROMA>
-__global__ void __launch_bounds__(kQX *kQY) pframe_kernel(const __grid_constant__ InterFrame F)
+__device__ __forceinline__ void whole_quad(const InterFrame &F, int qx, int qy)
 {
-    // the preceding launch wrote the residual planes or the references
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const int qx = blockIdx.x * kQX + threadIdx.x, qy = blockIdx.y * kQY + threadIdx.y;
     const int W = F.width, H = F.height;
     const int x0 = 2 * qx, y0 = 2 * qy;
-    if (x0 >= W || y0 >= H) return;
+    const int yp = F.ref_pitch[0], op = F.out_pitch[0], rp = F.r_pitch[0];
+    const float4 *fl = reinterpret_cast<const float4 *>(F.flow + 2 * (y0 * W + x0));
+    const float4 fa = __ldg(fl), fb = __ldg(fl + W / 2);
+    const float2 f[4] = {make_float2(fa.x, fa.y), make_float2(fa.z, fa.w), make_float2(fb.x, fb.y),
+                         make_float2(fb.z, fb.w)};
+    const float2 *rr0 = reinterpret_cast<const float2 *>(F.r[0] + y0 * rp + x0);
+    const float2 rl0 = __ldg(rr0), rl1 = __ldg(rr0 + rp / 2);
+    float rc[2] = {0.f, 0.f};
+    if (CHROMA) {
+        rc[0] = __ldg(F.r[1] + qy * F.r_pitch[1] + qx);
+        rc[1] = __ldg(F.r[2] + qy * F.r_pitch[2] + qx);
+    }
+    const float *__restrict__ RY = F.ref[0];
+    float ax[4], ay[4], g[4][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int sx = split_axis(f[k].x, x0 + (k & 1), W, ax[k]);
+        const int sy = split_axis(f[k].y, y0 + (k >> 1), H, ay[k]);
+        const int ox = min(sx + 1, W - 1) - sx, oy = (min(sy + 1, H - 1) - sy) * yp;
+        const int o = sy * yp + sx;
+        g[k][0] = __ldg(RY + o);
+        g[k][1] = __ldg(RY + o + ox);
+        g[k][2] = __ldg(RY + o + oy);
+        g[k][3] = __ldg(RY + o + oy + ox);
+    }
+    float cax = 0.f, cay = 0.f, c[2][4];
+    int cp = 0;
+    if (CHROMA) {
+        const int cw = (W + 1) / 2, ch = (H + 1) / 2;
+        const float dx = ((f[0].x + f[1].x) + (f[2].x + f[3].x)) * 0.125f;
+        const float dy = ((f[0].y + f[1].y) + (f[2].y + f[3].y)) * 0.125f;
+        const int cx0 = split_axis(dx, qx, cw, cax), cy0 = split_axis(dy, qy, ch, cay);
+        cp = F.ref_pitch[1];
+        const int cox = min(cx0 + 1, cw - 1) - cx0, coy = (min(cy0 + 1, ch - 1) - cy0) * cp;
+        const int co = cy0 * cp + cx0;
+#pragma unroll
+        for (int pl = 0; pl < 2; ++pl) {
+            const float *__restrict__ R = F.ref[pl + 1];
+            c[pl][0] = __ldg(R + co);
+            c[pl][1] = __ldg(R + co + cox);
+            c[pl][2] = __ldg(R + co + coy);
+            c[pl][3] = __ldg(R + co + coy + cox);
+        }
+    }
+    const float r[4] = {rl0.x, rl0.y, rl1.x, rl1.y};
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = recon(lerp2(ax[k], ay[k], g[k][0], g[k][1], g[k][2], g[k][3]), r[k]);
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+        *reinterpret_cast<float2 *>(F.ref_out[0] + (y0 + rr) * yp + x0) = make_float2(v[2 * rr], v[2 * rr + 1]);
+        *reinterpret_cast<uchar2 *>(F.out[0] + (y0 + rr) * op + x0) =
+            make_uchar2(to_u8(v[2 * rr]), to_u8(v[2 * rr + 1]));
+    }
+    if (CHROMA) {
+#pragma unroll
+        for (int pl = 0; pl < 2; ++pl) {
+            const float cv = recon(lerp2(cax, cay, c[pl][0], c[pl][1], c[pl][2], c[pl][3]), rc[pl]);
+            F.ref_out[pl + 1][qy * cp + qx] = cv;
+            F.out[pl + 1][qy * F.out_pitch[pl + 1] + qx] = to_u8(cv);
+        }
+    }
+}
+
+// Any quad (cut by the right or bottom edge, odd widths, unaligned rows):
+// one pixel at a time.
+template <bool CHROMA>
+__device__ __forceinline__ void any_quad(const InterFrame &F, int qx, int qy)
+{
+    const int W = F.width, H = F.height;
+    const int x0 = 2 * qx, y0 = 2 * qy;
     const bool in1 = x0 + 1 < W, inr = y0 + 1 < H;
     const float2 *fl = reinterpret_cast<const float2 *>(F.flow);
     float2 f[4];  // (row, column): 00, 01, 10, 11; zero outside the plane
@@ -95,9 +181,22 @@ __global__ void __launch_bounds__(kQX *kQY) pframe_kernel(const __grid_constant_
         for (int pl = 1; pl < 3; ++pl) {
             const float pred = sample(F.ref[pl], F.ref_pitch[pl], cw, ch, qx, qy, dx, dy);
             put_pixel(pred, __ldg(F.r[pl] + (size_t)qy * F.r_pitch[pl] + qx),
-                      F.ref_out[pl] + (size_t)qy * F.ref_pitch[pl] + qx, F.out[pl] + (size_t)qy * F.out_pitch[pl] + qx);
+                      F.ref_out[pl] + (size_t)qy * F.ref_pitch[pl] + qx,
+                      F.out[pl] + (size_t)qy * F.out_pitch[pl] + qx);
         }
     }
+}
+
+template <bool CHROMA>
+__global__ void __launch_bounds__(kQX *kQY, 12) pframe_kernel(const __grid_constant__ InterFrame F, int vec)
+{
+    // the preceding launch wrote the residual planes or the references
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int qx = blockIdx.x * kQX + threadIdx.x, qy = blockIdx.y * kQY + threadIdx.y;
+    if (2 * qx >= F.width || 2 * qy >= F.height) return;
+    if (vec && 2 * qy + 1 < F.height) whole_quad<CHROMA>(F, qx, qy);
+    else any_quad<CHROMA>(F, qx, qy);
 }
 
 }  // namespace
@@ -114,8 +213,15 @@ cudaError_t launch_pframe(const InterFrame &F, cudaStream_t st, bool pdl)
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    if (F.chroma) return cudaLaunchKernelEx(&cfg, pframe_kernel<true>, F);
-    return cudaLaunchKernelEx(&cfg, pframe_kernel<false>, F);
+    // the whole-quad path: an even width (16-byte flow pairs), even pitches
+    // and 8-byte (flow: 16-byte) aligned planes
+    auto al = [](const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; };
+    bool vec = F.width % 2 == 0 && al(F.flow, 16) && F.ref_pitch[0] % 2 == 0 && F.r_pitch[0] % 2 == 0 &&
+               F.out_pitch[0] % 2 == 0 && al(F.ref[0], 8) && al(F.ref_out[0], 8) && al(F.r[0], 8) &&
+               al(F.out[0], 2);
+    const int vi = vec ? 1 : 0;
+    if (F.chroma) return cudaLaunchKernelEx(&cfg, pframe_kernel<true>, F, vi);
+    return cudaLaunchKernelEx(&cfg, pframe_kernel<false>, F, vi);
 }
 
 }  // namespace hivc
