@@ -391,10 +391,12 @@ def next_rows_measurement(a, gop):
 
 def batching_measurement(a):
     """Four FullHD 4:2:0 inter frames decoded by one hivc_decode_batch call
-    (one coefficient launch and one evaluation launch over all their
-    blocks, then a pixel kernel per frame) against four single-frame calls.
-    Luma residual blocks: Poisson(8) points clipped to 0..48, 10% empty,
-    30% of the full blocks on 8 shared layouts."""
+    (the plan, one persistent coefficient launch, one evaluation launch and
+    the layout groups' tensor-core product over all their blocks, then a
+    pixel kernel per frame) against the same call with every block on its
+    own (layout groups off) and against four single-frame calls.  Luma
+    residual blocks: Poisson(8) points clipped to 0..48, 10% empty, 30% of
+    the full blocks on 8 shared layouts per frame."""
     import torch
 
     from paper_2008_10273_gb300 import hivc
@@ -404,14 +406,15 @@ def batching_measurement(a):
     g = make_gop(a.seed + 3, W, H, n_frames=5, with_sources=False,
                  residual_kw={"kmax": 48, "empty_frac": 0.1, "shared_layouts": 8, "shared_frac": 0.3})
     stream = torch.cuda.Stream()
-    dec = hivc.Decoder(W, H, chroma=True, iframe_tol=a.iframe_tol, stream=stream)
     out = hivc.alloc_out(W, H)
     ifr = hivc.device_iframe(g.iframe)
     pfs = [hivc.device_pframe(p) for p in g.pframes]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     res = {}
     steps, warm = 10, 3
-    for name, batched in (("batched", True), ("plain", False)):
+    for name, batched, groups in (("batched", True, True), ("batched_per_block", True, False),
+                                  ("plain", False, True)):
+        dec = hivc.Decoder(W, H, chroma=True, iframe_tol=a.iframe_tol, stream=stream, layout_groups=groups)
         ms = []
         with torch.cuda.stream(stream):
             for k in range(warm + steps):
@@ -432,6 +435,7 @@ def batching_measurement(a):
             hivc.lib().hivc_decoder_set_timing(dec.handle, 1)
             dec.decode_iframe(ifr, out)
             dec.sync()
+            flush.zero_()
             if batched:
                 hivc.decode_batch([dec] * 4, [("p", f) for f in pfs], [out] * 4)
             else:
@@ -439,14 +443,17 @@ def batching_measurement(a):
                     dec.decode_pframe(f, out)
             st = dec.sync()
             hivc.lib().hivc_decoder_set_timing(dec.handle, 0)
+        dec.close()
         fam = {hivc.KERNEL_FAMILIES[i]: {"ms": st.kernel_ms[i], "launches": st.kernel_launches[i]}
                for i in (3, 4, 5) if st.kernel_launches[i]}
         res[name] = {"value": 4 * steps * (W * H / FULLHD_PX) / (sum(ms) / 1e3), "unit": "FullHD inter frames/s",
-                     "ms_per_4_frames": sum(ms) / steps, "kernels": fam}
-    dec.close()
+                     "ms_per_4_frames": sum(ms) / steps, "kernels": fam,
+                     "layout_groups": int(st.layout_groups), "group_blocks": int(st.group_blocks)}
     nb = sum(int(r.n_blocks) for r in g.pframes[0].res[:1]) * 4
     res["workload"] = (f"4 FullHD 4:2:0 inter frames, {nb} luma blocks of 16x16 (Poisson(8) points clipped "
-                       "to 0..48, 10% empty, 30% of the full blocks on 8 shared layouts), L2 flushed before each")
+                       "to 0..48, 10% empty, 30% of the full blocks on 8 shared layouts per frame), L2 flushed "
+                       "before each; kernel families from a separate pass with per-family CUDA events (block_eval "
+                       "includes the layout groups' product)")
     return res
 
 

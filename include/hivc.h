@@ -85,6 +85,16 @@ typedef struct {
                                triggers; 0 re-solves every block */
     void *stream;           /* cudaStream_t to run on; NULL = the decoder
                                creates its own non-blocking stream */
+    int32_t layout_groups;  /* 1: residual blocks of a plane that share one
+                               mask layout (the same points, at least 16
+                               blocks, K <= 32, values within [-256, 256])
+                               are grouped: one factorisation per layout,
+                               and their residual planes (Eq. 3 for a fixed
+                               layout is linear in the values) as one
+                               tensor-core product; 0 (default) = every
+                               block on its own (the grouping pass costs
+                               more than it saves unless many blocks share
+                               few layouts) */
 } hivc_config;
 
 /* Intra mask of one plane: n >= 1 sorted, unique linear indices y*w + x. */
@@ -197,6 +207,10 @@ typedef struct {
        for families 1 and 2, whose launches may cover only the planes that
        still need sweeps; 0 for the others. */
     int64_t kernel_pixels[HIVC_STAT_KERNELS];
+    int32_t group_blocks;   /* residual blocks evaluated by their layout
+                               group's tensor-core product (Cb/Cr pairs
+                               count twice) */
+    int32_t layout_groups;  /* layout groups formed */
 } hivc_stats;
 
 typedef struct hivc_decoder hivc_decoder;
@@ -213,9 +227,13 @@ hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out);
 size_t hivc_decoder_bytes(const hivc_config *cfg);
 
 /* Decode an intra frame (Sec. 2.1 + optional residual, Sec. 2.2) into out
-   and make it the reference.  The correction loop reads the residual norm
-   back to the host between cycles, so this call waits on the decoder's
-   stream while it runs. */
+   and make it the reference.  Asynchronous: the correction loop decides
+   its cycles on the device (a graph with conditional loops; the residual
+   launches plan the sweeps), so the host does not wait.  Whether the solve
+   reached iframe_tol within max_cycles is reported by hivc_decoder_sync
+   (HIVC_E_NOT_CONVERGED; the residual reached in hivc_stats.resid).  The
+   first solve of a plane geometry in a process may time the sweep kernel's
+   tilings first (see hivc_tune_lookup), which waits on the stream once. */
 hivc_status hivc_decode_iframe(hivc_decoder *dec, const hivc_iframe *f, const hivc_out *out);
 
 /* Decode an inter frame (Sec. 2, 2.3: warp + residual) into out and make it
@@ -233,10 +251,11 @@ hivc_status hivc_decode_pframe_coef(hivc_decoder *dec, const hivc_pframe_coef *f
    residual planes).  Every inter frame is checked before anything is
    launched (HIVC_E_INVALID; HIVC_E_NO_REFERENCE for an inter frame of a
    decoder with no reference and no earlier intra frame in the batch).
-   Decoders with intra frames run on host threads of their own (up to 32),
-   so that their correction cycles overlap; a decoder stops at its first
-   error, the others finish, and the call returns the first error in order
-   of the decoders' first frames (HIVC_E_NOT_CONVERGED only if no worse).
+   Every call only enqueues work, so the decoders' frames overlap on the
+   GPU; a decoder stops at its first error, the others finish, and the call
+   returns the first error in order
+   of the decoders' first frames.  Intra solves that stop above the
+   tolerance are reported by hivc_decoder_sync.
    The block launches of an inter run that follows an intra frame run on a
    stream the decoder owns, beside the intra frame; the decoder's stream
    waits for them (an event) before the run's first warp, so work queued on
@@ -245,7 +264,9 @@ hivc_status hivc_decode_batch(hivc_decoder *const *decs, const hivc_frame *frame
                               const hivc_out *outs);
 
 /* Wait for the decoder's stream; report device-side data errors
-   (HIVC_E_INVALID) and the statistics of the frames since the last sync. */
+   (HIVC_E_INVALID), else HIVC_E_NOT_CONVERGED if an intra solve since the
+   last sync stopped above iframe_tol, and the statistics of the frames
+   since the last sync. */
 hivc_status hivc_decoder_sync(hivc_decoder *dec, hivc_stats *last);
 
 /* Forget the reference frame (the decoder is reused for a new stream: its
@@ -259,6 +280,20 @@ hivc_status hivc_decoder_reset(hivc_decoder *dec);
    them on its own sweeps and keeps the fastest; 0..2 pin one for every
    decoder of the process.  HIVC_E_INVALID for other values. */
 hivc_status hivc_set_sor_variant(int32_t variant);
+
+/* The autotuner's table.  The library times schedule choices that never
+   change a result (the sweep kernel's region tiling; CTAs per SM of the
+   persistent coefficient kernel) on the first call that needs one, and
+   keeps each choice under a key of the GPU's name and the shape, e.g.
+   "NVIDIA GB300|sor|1920x1080,960x540,960x540" or
+   "NVIDIA GB300|coef|16384" (block count rounded up to a power of two),
+   for the process and in a JSON file: HIVC_TUNE_CACHE, else
+   $XDG_CACHE_HOME/hivc/tune.json, else $HOME/.cache/hivc/tune.json.
+   hivc_tune_lookup returns the value under key, or -1; hivc_tune_record
+   sets one (value >= 0) and rewrites the file, so that a caller can
+   pre-seed or pin choices.  Neither needs a GPU. */
+int32_t hivc_tune_lookup(const char *key);
+hivc_status hivc_tune_record(const char *key, int32_t value);
 
 /* Enable (1) or disable (0) per-kernel CUDA-event timing in hivc_stats. */
 hivc_status hivc_decoder_set_timing(hivc_decoder *dec, int32_t on);
@@ -275,8 +310,9 @@ hivc_status hivc_decoder_reference(const hivc_decoder *dec, int32_t plane, const
    floats, before the optional residual and the clamp to [0, 255].  The
    solve's reported residual (hivc_stats.resid) is max |(L u)_i| over the
    unknown pixels of this u, which a caller can recompute in FP64 from
-   hi + lo.  Valid until the next intra frame (its work must be complete:
-   hivc_decoder_sync); HIVC_E_NO_REFERENCE before any intra frame. */
+   hi + lo.  Call after hivc_decoder_sync (which learns which buffer of the
+   solve's ping-pong holds the result); valid until the next intra frame;
+   HIVC_E_NO_REFERENCE before any intra frame. */
 hivc_status hivc_decoder_intra_solution(const hivc_decoder *dec, int32_t plane, const float **hi,
                                         const float **lo, int32_t *width, int32_t *height, int32_t *pitch);
 

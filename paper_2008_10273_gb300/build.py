@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhivc.so")
-SOURCES = ["hivc_api.cu", "k_block.cu", "k_intra.cu", "k_warp.cu", "k_pframe.cu", "k_noalloc.cu", "k_side.cu"]
+SOURCES = ["hivc_api.cu", "k_block.cu", "k_intra.cu", "k_warp.cu", "k_pframe.cu", "k_noalloc.cu", "k_side.cu", "tune.cu"]
 HEADERS = [os.path.join(CSRC, "hivc_internal.cuh"), os.path.join(CSRC, "block_device.cuh"), os.path.join(INCLUDE, "hivc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -9,7 +9,6 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
-#include <thread>
 #include <vector>
 
 #include <mutex>
@@ -22,9 +21,14 @@ namespace {
 
 constexpr int kPitchAlign = 32;  // elements
 // the layout the Python binding mirrors
-static_assert(sizeof(hivc_stats) == 184 && offsetof(hivc_stats, kernel_pixels) == 120, "hivc_stats layout");
+static_assert(sizeof(hivc_stats) == 192 && offsetof(hivc_stats, kernel_pixels) == 120, "hivc_stats layout");
 
 int round_up(int v, int a) { return (v + a - 1) / a * a; }
+
+// scratch slots (one K > 32 system each) for a launch over nblocks blocks:
+// one per range of kRange blocks, at most one per CTA of the persistent
+// coefficient kernel
+int coef_slots(int nblocks) { return std::max(1, std::min(block_ranges(nblocks), block_coef_ctas())); }
 
 struct Alloc {
     std::vector<void *> ptrs;
@@ -56,17 +60,17 @@ struct PlaneGeom {
     int w, h, pitch, nblocks, nbx;
 };
 
-// device status words of a decoder: error flags, then the condition
-// statistics of the coefficient stage (max bound bits, FP64 re-solves,
-// K > 32 blocks)
-constexpr int kStatusWords = 4;
+// device status words of a decoder: error flags, then the statistics of
+// the coefficient stage (max condition bound bits, FP64 re-solves, K > 32
+// blocks, blocks evaluated by layout groups, layout groups)
+constexpr int kStatusWords = 6;
 
 bool config_ok(const hivc_config *c)
 {
     return c && c->width >= 1 && c->height >= 1 && c->width <= 16384 && c->height <= 16384 &&
            (c->chroma >= 0 && c->chroma <= 2) && c->block >= 1 && c->block <= kMaxB && (c->op == 0 || c->op == 1) &&
            (c->precision == 0 || c->precision == 1) && c->iframe_tol >= 0.0 && c->max_cycles >= 1 &&
-           c->cond_threshold >= 0.0;
+           c->cond_threshold >= 0.0 && (c->layout_groups == 0 || c->layout_groups == 1);
 }
 
 int plane_count(const hivc_config *c) { return c->chroma ? 3 : 1; }
@@ -121,23 +125,27 @@ struct hivc_decoder {
     // intra scratch
     float *uh[2][3]{}, *ul[2][3]{};
     float *res[3]{}, *e[2][3]{};
-    // the buffers holding the last intra frame's iterate (hi, lo) per plane
-    const float *sol_hi[3]{}, *sol_lo[3]{};
     uint8_t *mask[3]{};
     unsigned long long *vsum = nullptr;
-    unsigned int *rnorm = nullptr;
+    // the intra solve's control state (device), the SOR tuner's, a pinned
+    // host copy, the loop's graph and the sweep variant it was built for
+    IntraCtl *ctl = nullptr, *tune_ctl = nullptr, *h_ctl = nullptr;
+    cudaGraphExec_t igraph = nullptr;
+    int igraph_variant = -1;
+    bool intra_pending = false;  // an intra frame since the last sync
+    bool has_intra = false;      // an intra frame was decoded
     // block scratch
     float *rfield[3]{}, *coef[3]{}, *acoef[3]{};
     size_t coef_cap = 0;
-    float *big = nullptr;  // one K > 32 system per range of blocks
+    float *big = nullptr;  // one K > 32 system per slot of the coefficient kernel
     int big_ranges = 0;
+    BlockPlan plan{};      // work lists (and layout groups) of a frame's block stage
     uint32_t *flags = nullptr;
     // coefficients of the inter frames of one batch (grown on demand)
     void *pool = nullptr;
     size_t pool_bytes = 0;
     // host mirrors
     uint32_t *h_flags = nullptr;
-    unsigned int *h_rnorm = nullptr;
     // statistics
     hivc_stats st{};
     bool timing = false;
@@ -259,7 +267,9 @@ hivc_status make_block_jobs(hivc_decoder *d, const hivc_residual *res, BlockJobs
 
 BlockScratch scratch(hivc_decoder *d)
 {
-    return BlockScratch{d->flags, d->big, d->big_ranges, d->flags + 1, (float)d->cfg.cond_threshold};
+    BlockScratch S{d->flags, d->big, d->big_ranges, d->flags + 1, (float)d->cfg.cond_threshold};
+    S.plan = d->plan;
+    return S;
 }
 
 // Block stage of one frame: coefficients (+ large blocks), then residual fields.
@@ -278,7 +288,7 @@ hivc_status run_block_residual(hivc_decoder *d, const hivc_residual *res)
     if (e != cudaSuccess) return HIVC_E_CUDA;
     {
         Timed t(d, 5);
-        e = launch_block_eval(J, d->flags, d->stream, !d->timing);
+        e = launch_block_eval(J, d->flags, d->stream, !d->timing, &d->plan);
         t.done(1);
     }
     return cuda_status(e);
@@ -300,6 +310,7 @@ void hivc_config_default(hivc_config *c)
     c->max_cycles = 40;
     c->cond_threshold = 1e6;
     c->stream = nullptr;
+    c->layout_groups = 0;
 }
 
 const char *hivc_status_str(hivc_status s)
@@ -345,7 +356,8 @@ size_t hivc_decoder_bytes(const hivc_config *c)
     }
     add(3 * sizeof(unsigned long long));
     add(3 * sizeof(unsigned int));
-    add((size_t)block_ranges(nblocks) * kBigFloats * sizeof(float));  // K > 32 systems
+    add((size_t)coef_slots(nblocks) * kBigFloats * sizeof(float));  // K > 32 systems
+    add(block_plan_bytes(nblocks, c->layout_groups != 0));          // plan of a frame's block stage
     add(4);                            // error word
     return b;
 }
@@ -391,22 +403,28 @@ hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out)
         maxpts = std::max(maxpts, (size_t)g.w * g.h);
     }
     d->coef_cap = maxpts;
-    d->big_ranges = block_ranges(nblocks);
+    d->big_ranges = coef_slots(nblocks);
     d->big = m.get<float>((size_t)d->big_ranges * kBigFloats);
+    void *plan_mem = m.get<char>(block_plan_bytes(nblocks, cfg->layout_groups != 0));
     d->vsum = m.get<unsigned long long>(3);
-    d->rnorm = m.get<unsigned int>(3);
+    d->ctl = m.get<IntraCtl>(1);
+    d->tune_ctl = m.get<IntraCtl>(1);
     d->flags = m.get<uint32_t>(kStatusWords);
+    if (m.ok) d->plan = carve_block_plan(plan_mem, nblocks, cfg->layout_groups != 0);
     if (!m.ok) {
         m.release();
         delete d;
         return HIVC_E_NOMEM;
     }
-    if (cudaMallocHost(&d->h_flags, 64) != cudaSuccess) {
+    if (cudaMallocHost(&d->h_flags, 64) != cudaSuccess || cudaMallocHost(&d->h_ctl, sizeof(IntraCtl)) != cudaSuccess) {
+        if (d->h_flags) cudaFreeHost(d->h_flags);
+    if (d->h_ctl) cudaFreeHost(d->h_ctl);
+    if (d->igraph) cudaGraphExecDestroy(d->igraph);
         m.release();
         delete d;
         return HIVC_E_NOMEM;
     }
-    d->h_rnorm = d->h_flags + 4;
+    std::memset(d->h_ctl, 0, sizeof(IntraCtl));
     if (cfg->stream) {
         d->stream = static_cast<cudaStream_t>(cfg->stream);
     } else {
@@ -422,6 +440,7 @@ hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out)
         cudaEventCreateWithFlags(&d->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&d->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaMemsetAsync(d->flags, 0, 4 * kStatusWords, d->stream) != cudaSuccess ||
+        cudaMemsetAsync(d->ctl, 0, sizeof(IntraCtl), d->stream) != cudaSuccess ||
         cudaStreamSynchronize(d->stream) != cudaSuccess) {
         hivc_decoder_destroy(d);
         return HIVC_E_CUDA;
@@ -448,6 +467,8 @@ void hivc_decoder_destroy(hivc_decoder *d)
     for (cudaEvent_t e : d->event_pool) cudaEventDestroy(e);
     if (d->own_stream) cudaStreamDestroy(d->stream);
     if (d->h_flags) cudaFreeHost(d->h_flags);
+    if (d->h_ctl) cudaFreeHost(d->h_ctl);
+    if (d->igraph) cudaGraphExecDestroy(d->igraph);
     if (d->pool) cudaFree(d->pool);
     d->mem.release();
     delete d;
@@ -464,9 +485,11 @@ hivc_status hivc_decoder_intra_solution(const hivc_decoder *d, int32_t plane, co
                                         int32_t *w, int32_t *h, int32_t *pitch)
 {
     if (!d || plane < 0 || plane >= d->np || !hi || !lo) return HIVC_E_INVALID;
-    if (!d->sol_hi[plane]) return HIVC_E_NO_REFERENCE;
-    *hi = d->sol_hi[plane];
-    *lo = d->sol_lo[plane];
+    if (!d->has_intra) return HIVC_E_NO_REFERENCE;
+    // the buffer the control state named at the last sync
+    const int u = d->h_ctl->upar[plane] & 1;
+    *hi = d->uh[u][plane];
+    *lo = d->cfg.precision == 0 ? d->ul[u][plane] : nullptr;
     if (w) *w = d->pg[plane].w;
     if (h) *h = d->pg[plane].h;
     if (pitch) *pitch = d->pg[plane].pitch;
@@ -499,16 +522,22 @@ namespace {
 // The 4:4:4 colour path's pixel kernel for the frame being decoded: inter
 // (flow != nullptr: warp of the current references) or intra (hi/lo: the
 // inpainted planes); r: residual planes or nullptr.
+// hi1, lo1, sel: the other buffers of the intra iterate's ping-pong and the
+// device words (per plane) that say which buffer holds the solution
 cudaError_t launch_rct_frame(hivc_decoder *d, const float *flow, float *const *hi, float *const *lo, bool residual,
-                             const hivc_out *out)
+                             const hivc_out *out, float *const *hi1 = nullptr, float *const *lo1 = nullptr,
+                             const int32_t *sel = nullptr)
 {
     RctFrame F{};
     F.flow = flow;
+    F.src_sel = sel;
     const int nxt = d->cur ^ 1;
     for (int p = 0; p < 3; ++p) {
         F.ref[p] = d->ref[d->cur][p];
         F.src_hi[p] = hi ? hi[p] : nullptr;
         F.src_lo[p] = lo ? lo[p] : nullptr;
+        F.src_hi1[p] = hi1 ? hi1[p] : nullptr;
+        F.src_lo1[p] = lo1 ? lo1[p] : nullptr;
         F.r[p] = residual ? d->rfield[p] : nullptr;
         F.ref_out[p] = d->ref[nxt][p];
         F.out[p] = out->plane[p];
@@ -543,6 +572,8 @@ hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc
     cudaStream_t st = d->stream;
     IntraJobs J{};
     J.n = d->np;
+    J.ctl = d->ctl;
+    float om0[3] = {1.f, 1.f, 1.f};
     for (int p = 0; p < d->np; ++p) {
         IntraPlane &P = J.p[p];
         const PlaneGeom &g = d->pg[p];
@@ -563,9 +594,8 @@ hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc
         P.e[0] = d->e[0][p];
         P.e[1] = d->e[1][p];
         P.vsum = d->vsum + p;
-        P.rnorm = d->rnorm + p;
-        P.omega = sor_omega(g.w, g.h, P.n);
         P.ff = d->cfg.precision == 0 ? 1 : 0;
+        om0[p] = sor_omega(g.w, g.h, P.n);
     }
     cudaError_t e;
     {
@@ -575,134 +605,68 @@ hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc
         t.done(l);
     }
     if (e != cudaSuccess) return HIVC_E_CUDA;
-    auto residual = [&](IntraJobs &A, bool add_e, int eb) -> cudaError_t {
-        Timed t(d, 2);
-        cudaError_t er = launch_intra_residual(A, eb, add_e, st);
-        t.done(1);
-        for (int k = 0; k < A.n; ++k) d->st.kernel_pixels[2] += (int64_t)A.p[k].width * A.p[k].height;
-        if (er != cudaSuccess) return er;
-        er = cudaMemcpyAsync(d->h_rnorm, d->rnorm, 3 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
-        if (er != cudaSuccess) return er;
-        return cudaStreamSynchronize(st);
-    };
-    if ((e = residual(J, false, 0)) != cudaSuccess) return HIVC_E_CUDA;
-    double rn[3] = {0, 0, 0};
-    auto read_norms = [&]() {
-        for (int p = 0; p < d->np; ++p) {
-            float v;
-            std::memcpy(&v, d->h_rnorm + p, sizeof(float));
-            rn[p] = v;
+    // the sweep kernel's tiling (the first solve of a geometry times the
+    // variants on launches of its own), then the correction loop, decided on
+    // the device: one graph launch, or with per-kernel timing one launch at
+    // a time with the plan read back between cycles
+    const int variant = intra_sor_variant(J, d->tune_ctl, st);
+    if (launch_intra_ctl_init(J, om0, d->cfg.iframe_tol, d->cfg.max_cycles, st) != cudaSuccess) return HIVC_E_CUDA;
+    if (d->timing) {
+        {
+            Timed t(d, 2);
+            e = launch_intra_residual(J, true, st);
+            t.done(0);
         }
-    };
-    read_norms();
-    const double tol = d->cfg.iframe_tol;
-    int cycles = 0, sweeps_total = 0, plane_sweeps[3] = {0, 0, 0};
-    // per-plane sweep counts: each cycle aims at the FP32 floor of the inner
-    // solve (about 1e-5) or at the remaining gap to the tolerance, whichever
-    // is smaller; the rate of optimally relaxed SOR is omega - 1
-    const int spl = intra_sweeps_per_launch();
-    double rate[3];
-    for (int p = 0; p < d->np; ++p) rate[p] = J.p[p].omega - 1.0;
-    while (cycles < d->cfg.max_cycles) {
-        int nl[3] = {0, 0, 0}, maxl = 0;
-        for (int p = 0; p < d->np; ++p) {
-            if (!(rn[p] > tol)) continue;
-            const double target = std::max(1e-5, 0.3 * tol / rn[p]);
-            const double rt = std::min(std::max(rate[p], 0.05), 0.995);
-            int sw = (int)std::ceil(std::log(target) / std::log(rt));
-            sw = std::min(std::max(sw, spl), 600);
-            nl[p] = (sw + spl - 1) / spl;
-            maxl = std::max(maxl, nl[p]);
-        }
-        if (maxl == 0) break;
-        // SOR launches in segments over the planes that still need sweeps;
-        // each plane's e[0] holds its current correction between segments
-        for (int done = 0; done < maxl;) {
-            IntraJobs A{};
-            int map[3], seg = 1 << 30;
-            for (int p = 0; p < d->np; ++p)
-                if (nl[p] > done) {
-                    map[A.n] = p;
-                    A.p[A.n++] = J.p[p];
-                    seg = std::min(seg, nl[p] - done);
-                }
-            int eb = 0;
-            {
+        while (e == cudaSuccess) {
+            e = cudaMemcpyAsync(d->h_ctl, d->ctl, sizeof(IntraCtl), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess || !d->h_ctl->go_outer) break;
+            const int maxl = d->h_ctl->maxl;
+            for (int l = 0; l < maxl && e == cudaSuccess; l += 2) {
                 Timed t(d, 1);
-                int l = 0;
-                e = launch_intra_sor(A, 0, done == 0, seg * spl, st, &eb, &l);
-                t.done(l);
-                for (int k = 0; k < A.n; ++k) d->st.kernel_pixels[1] += (int64_t)l * A.p[k].width * A.p[k].height;
+                e = launch_intra_sor_pair(J, variant, st);
+                t.done(0);
             }
-            if (e != cudaSuccess) return HIVC_E_CUDA;
-            if (eb == 1)
-                for (int k = 0; k < A.n; ++k) std::swap(J.p[map[k]].e[0], J.p[map[k]].e[1]);
-            done += seg;
-        }
-        IntraJobs R{};
-        int map[3];
-        for (int p = 0; p < d->np; ++p)
-            if (nl[p] > 0) {
-                map[R.n] = p;
-                R.p[R.n++] = J.p[p];
-            }
-        if ((e = residual(R, true, 0)) != cudaSuccess) return HIVC_E_CUDA;
-        for (int k = 0; k < R.n; ++k) {
-            const int p = map[k];
-            std::swap(J.p[p].uh[0], J.p[p].uh[1]);
-            std::swap(J.p[p].ul[0], J.p[p].ul[1]);
-            float v;
-            std::memcpy(&v, d->h_rnorm + p, sizeof(float));
-            const double q = v / std::max(rn[p], 1e-30);
-            rn[p] = v;
-            plane_sweeps[p] += nl[p] * spl;
-            sweeps_total = std::max(sweeps_total, plane_sweeps[p]);
-            // slower than optimal SOR at this omega predicts: omega is below
-            // the optimum; Young's relation (rho + omega - 1)^2 = rho omega^2
-            // mu^2 gives the Jacobi radius mu and the optimal omega
-            const double S = nl[p] * spl;
-            if (q > 1e-4 && q < 1.0) {
-                const double ro = std::pow(q, 1.0 / S);
-                const double om = J.p[p].omega;
-                if (ro > rate[p] + 0.01) {
-                    const double mu = (ro + om - 1.0) / (om * std::sqrt(ro));
-                    if (mu < 1.0) {
-                        const double on = 2.0 / (1.0 + std::sqrt(1.0 - mu * mu));
-                        J.p[p].omega = (float)std::min(1.98, std::max(om, on));
-                    }
-                    rate[p] = std::max((double)J.p[p].omega - 1.0, std::min(ro, 0.995));
-                    if (J.p[p].omega > om) rate[p] = J.p[p].omega - 1.0;
-                }
+            if (e == cudaSuccess) {
+                Timed t(d, 2);
+                e = launch_intra_residual(J, false, st);
+                t.done(0);
             }
         }
-        ++cycles;
+    } else {
+        if (!d->igraph || d->igraph_variant != variant) {
+            if (d->igraph) cudaGraphExecDestroy(d->igraph);
+            d->igraph = nullptr;
+            if ((e = build_intra_graph(J, variant, &d->igraph)) != cudaSuccess) return HIVC_E_CUDA;
+            d->igraph_variant = variant;
+        }
+        e = cudaGraphLaunch(d->igraph, st);
     }
-    bool converged = true;
-    for (int p = 0; p < d->np; ++p) converged = converged && rn[p] <= tol;
-    for (int p = 0; p < d->np; ++p) {
-        d->sol_hi[p] = J.p[p].uh[0];
-        d->sol_lo[p] = J.p[p].ff ? J.p[p].ul[0] : nullptr;
-    }
+    if (e != cudaSuccess) return HIVC_E_CUDA;
+    d->intra_pending = true;
+    d->has_intra = true;
     // optional residual correction of the intra frame (Fig. 1e/f)
     if (f->res) {
         hivc_status s = run_block_residual(d, f->res);
         if (s != HIVC_OK) return s;
     }
+    // the output: the solution sits in the iterate buffer the control state
+    // names (upar) per plane
     const int nxt = d->cur ^ 1;
     if (rct) {
-        float *hi[3], *lo[3];
+        float *hi[3], *lo[3], *hi1[3], *lo1[3];
         for (int p = 0; p < 3; ++p) {
             hi[p] = J.p[p].uh[0];
             lo[p] = J.p[p].ff ? J.p[p].ul[0] : nullptr;
+            hi1[p] = J.p[p].uh[1];
+            lo1[p] = J.p[p].ff ? J.p[p].ul[1] : nullptr;
         }
-        if (launch_rct_frame(d, nullptr, hi, lo, f->res != nullptr, out) != cudaSuccess) return HIVC_E_CUDA;
+        if (launch_rct_frame(d, nullptr, hi, lo, f->res != nullptr, out, hi1, lo1, d->ctl->upar) != cudaSuccess)
+            return HIVC_E_CUDA;
         d->cur = nxt;
         d->has_ref = true;
-        for (int p = 0; p < 3; ++p) d->st.resid[p] = rn[p];
-        d->st.cycles = cycles;
-        d->st.sweeps = sweeps_total;
         d->st.frames += 1;
-        return converged ? HIVC_OK : HIVC_E_NOT_CONVERGED;
+        return HIVC_OK;
     }
     WarpJobs W{};
     W.n = d->np;
@@ -711,6 +675,9 @@ hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc
         const PlaneGeom &g = d->pg[p];
         P.src_hi = J.p[p].uh[0];
         P.src_lo = J.p[p].ff ? J.p[p].ul[0] : nullptr;
+        P.src_hi1 = J.p[p].uh[1];
+        P.src_lo1 = J.p[p].ff ? J.p[p].ul[1] : nullptr;
+        P.src_sel = d->ctl->upar + p;
         P.src_pitch = g.pitch;
         P.r = f->res ? d->rfield[p] : nullptr;
         P.r_pitch = g.pitch;
@@ -729,11 +696,8 @@ hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc
     if (e != cudaSuccess) return HIVC_E_CUDA;
     d->cur = nxt;
     d->has_ref = true;
-    for (int p = 0; p < 3; ++p) d->st.resid[p] = p < d->np ? rn[p] : 0.0;
-    d->st.cycles = cycles;
-    d->st.sweeps = sweeps_total;
     d->st.frames += 1;
-    return converged ? HIVC_OK : HIVC_E_NOT_CONVERGED;
+    return HIVC_OK;
 }
 
 namespace {
@@ -937,9 +901,13 @@ hivc_status inter_blocks(hivc_decoder *d, const hivc_frame *frames, const std::v
         if (d->np == 3 && r[1].block_ptr == r[2].block_ptr && r[1].pos == r[2].pos && r[1].n_points == r[2].n_points)
             min_jobs = 2;
     }
-    const int ranges = block_ranges((kMaxJobs / min_jobs) * fblocks);
+    const int launch_blocks = (kMaxJobs / min_jobs) * fblocks;
+    const int ranges = coef_slots(launch_blocks);
     const size_t big_off = bytes;
     bytes += (size_t)ranges * kBigFloats * sizeof(float);
+    const bool groups = d->cfg.layout_groups != 0;
+    const size_t plan_off = bytes;
+    bytes += block_plan_bytes(launch_blocks, groups);
     hivc_status s = ensure_pool(d, bytes);
     if (s != HIVC_OK) return s;
     char *pool = static_cast<char *>(d->pool);
@@ -956,8 +924,9 @@ hivc_status inter_blocks(hivc_decoder *d, const hivc_frame *frames, const std::v
         }
         if ((s = make_block_jobs(d, frames[ks[k]].p->res, jobs[k], coef, acoef, rfield)) != HIVC_OK) return s;
     }
-    const BlockScratch S{d->flags, reinterpret_cast<float *>(pool + big_off), ranges, d->flags + 1,
-                         (float)d->cfg.cond_threshold};
+    BlockScratch S{d->flags, reinterpret_cast<float *>(pool + big_off), ranges, d->flags + 1,
+                   (float)d->cfg.cond_threshold};
+    S.plan = carve_block_plan(pool + plan_off, launch_blocks, groups);
     BlockJobs J{};
     J.op = d->cfg.op;
     auto flush = [&]() -> cudaError_t {
@@ -972,7 +941,7 @@ hivc_status inter_blocks(hivc_decoder *d, const hivc_frame *frames, const std::v
         pdl = true;
         if (e == cudaSuccess) {
             Timed t(d, 5);
-            e = launch_block_eval(J, d->flags, st, !d->timing);
+            e = launch_block_eval(J, d->flags, st, !d->timing, &S.plan);
             t.done(1);
         }
         J = BlockJobs{};
@@ -1114,41 +1083,12 @@ hivc_status hivc_decode_batch(hivc_decoder *const *decs, const hivc_frame *frame
             else if (!ref) return HIVC_E_NO_REFERENCE;
         }
     }
-    // Decoders are independent and each has its own stream.  Decoders with
-    // only inter frames are issued from this thread first (their launches
-    // are asynchronous).  An intra frame waits on its stream between
-    // correction cycles, so decoders with intra frames are spread over up
-    // to kBatchThreads host threads and the cycles of different decoders
-    // overlap on the device.  Every decoder stops at its own first error.
+    // Decoders are independent and each has its own stream; every call
+    // below only enqueues work (the intra solves decide their cycles on the
+    // device), so one host thread issues them all and the decoders' work
+    // overlaps on the GPU.  Every decoder stops at its own first error.
     std::vector<hivc_status> st(ds.size(), HIVC_OK);
-    std::vector<size_t> with_intra;
-    for (size_t j = 0; j < ds.size(); ++j) {
-        bool intra = false;
-        for (int k : ks[j]) intra |= frames[k].type == 0;
-        if (intra) with_intra.push_back(j);
-        else st[j] = decode_own_frames(ds[j], frames, outs, ks[j]);
-    }
-    constexpr size_t kBatchThreads = 32;
-    const size_t T = std::min(with_intra.size(), kBatchThreads);
-    auto worker = [&](size_t w) {
-        for (size_t i = w; i < with_intra.size(); i += T) {
-            const size_t j = with_intra[i];
-            st[j] = decode_own_frames(ds[j], frames, outs, ks[j]);
-        }
-    };
-    std::vector<std::thread> th;
-    try {
-        for (size_t w = 1; w < T; ++w) th.emplace_back(worker, w);
-    } catch (...) {  // no more threads to be had: their shares run here
-    }
-    const size_t started = th.size() + 1;
-    for (size_t i = 0; i < with_intra.size(); ++i) {
-        const size_t w = i % (T ? T : 1);
-        if (w != 0 && w < started) continue;
-        const size_t j = with_intra[i];
-        st[j] = decode_own_frames(ds[j], frames, outs, ks[j]);
-    }
-    for (std::thread &t : th) t.join();
+    for (size_t j = 0; j < ds.size(); ++j) st[j] = decode_own_frames(ds[j], frames, outs, ks[j]);
     hivc_status worst = HIVC_OK;
     for (hivc_status s : st) {
         if (s != HIVC_OK && s != HIVC_E_NOT_CONVERGED) return s;
@@ -1163,12 +1103,36 @@ hivc_status hivc_decoder_sync(hivc_decoder *d, hivc_stats *last)
     if (cudaSetDevice(d->device) != cudaSuccess) return HIVC_E_CUDA;
     cudaError_t e = cudaMemcpyAsync(d->h_flags, d->flags, 4 * kStatusWords, cudaMemcpyDeviceToHost, d->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d->flags, 0, 4 * kStatusWords, d->stream);
+    // the intra solves' control state and statistics (cleared for the next
+    // sync), the one read-back of the correction loop
+    const size_t stat_off = offsetof(IntraCtl, sor_launches);
+    const bool intra = d->intra_pending;
+    if (e == cudaSuccess && intra)
+        e = cudaMemcpyAsync(d->h_ctl, d->ctl, sizeof(IntraCtl), cudaMemcpyDeviceToHost, d->stream);
+    if (e == cudaSuccess && intra)
+        e = cudaMemsetAsync(reinterpret_cast<char *>(d->ctl) + stat_off, 0, sizeof(IntraCtl) - stat_off, d->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
     if (e != cudaSuccess) return HIVC_E_CUDA;
+    bool not_converged = false;
+    if (intra) {
+        const IntraCtl &c = *d->h_ctl;
+        for (int p = 0; p < 3; ++p) d->st.resid[p] = p < d->np ? c.rn[p] : 0.0;
+        d->st.cycles = c.cycles;
+        d->st.sweeps = c.sweeps_max;
+        d->st.kernel_launches[1] += (int32_t)c.sor_launches;
+        d->st.kernel_launches[2] += (int32_t)c.res_launches;
+        d->st.kernel_pixels[1] += c.sor_pixels;
+        d->st.kernel_pixels[2] += c.res_pixels;
+        d->st.launches += (int32_t)(c.sor_launches + c.res_launches);
+        not_converged = c.unconverged > 0;
+        d->intra_pending = false;
+    }
     d->st.device_flags = d->h_flags[0];
     std::memcpy(&d->st.max_cond, d->h_flags + 1, sizeof(float));
     d->st.fp64_blocks = (int32_t)d->h_flags[2];
     d->st.large_blocks = (int32_t)d->h_flags[3];
+    d->st.group_blocks = (int32_t)d->h_flags[4];
+    d->st.layout_groups = (int32_t)d->h_flags[5];
     for (auto &pe : d->pending) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess)
@@ -1184,7 +1148,8 @@ hivc_status hivc_decoder_sync(hivc_decoder *d, hivc_stats *last)
     fresh.cycles = d->st.cycles;
     fresh.sweeps = d->st.sweeps;
     d->st = fresh;
-    return (fl & ~kFlagCond) ? HIVC_E_INVALID : HIVC_OK;
+    if (fl & ~kFlagCond) return HIVC_E_INVALID;
+    return not_converged ? HIVC_E_NOT_CONVERGED : HIVC_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1195,7 +1160,8 @@ size_t hivc_block_residual_workspace_bytes(int32_t width, int32_t height, int32_
 {
     if (width < 1 || height < 1 || block < 1 || block > kMaxB || n_points < 0) return 0;
     const size_t nb = (size_t)((width + block - 1) / block) * ((height + block - 1) / block);
-    return a256(4 * (size_t)n_points) + a256(4 * nb) + 256 + a256(4 * kBigFloats * (size_t)block_ranges((int)nb));
+    return a256(4 * (size_t)n_points) + a256(4 * nb) + 256 + a256(4 * kBigFloats * (size_t)block_ranges((int)nb)) +
+           block_plan_bytes((int)nb, false);
 }
 
 hivc_status hivc_block_residual(int32_t width, int32_t height, int32_t block, const hivc_residual *res, float *r,
@@ -1216,6 +1182,9 @@ hivc_status hivc_block_residual(int32_t width, int32_t height, int32_t block, co
     uint32_t *own_flags = reinterpret_cast<uint32_t *>(w);
     w += 256;
     float *big = reinterpret_cast<float *>(w);
+    w += a256(4 * kBigFloats * (size_t)block_ranges(nb));
+    BlockScratch S{flags, big, block_ranges(nb)};
+    S.plan = carve_block_plan(w, nb, false);
     if (!flags) {
         flags = own_flags;
         if (cudaMemsetAsync(flags, 0, 4, st) != cudaSuccess) return HIVC_E_CUDA;
@@ -1237,7 +1206,8 @@ hivc_status hivc_block_residual(int32_t width, int32_t height, int32_t block, co
     B.nbx = nbx;
     B.nblocks = nb;
     J.total_blocks = nb;
-    cudaError_t e = launch_block_coef(J, BlockScratch{flags, big, block_ranges(nb)}, st, nullptr);
+    S.flags = flags;
+    cudaError_t e = launch_block_coef(J, S, st, nullptr);
     if (e == cudaSuccess) e = launch_block_eval(J, flags, st);
     return cuda_status(e);
 }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
+#include <string>
 
 #include "hivc.h"
 
@@ -80,9 +81,60 @@ constexpr int kRange = 128;    // blocks per range of the coefficient kernel
 // ranges of kRange blocks for total_blocks blocks
 __host__ __device__ inline int block_ranges(int total_blocks) { return (total_blocks + kRange - 1) / kRange; }
 
-// Scratch of the coefficient stage: room for one K > 32 system per range
-// of kRange blocks (the range's CTA solves its large blocks one after the
-// other in its slot; an FP64 re-solve uses the slot as doubles).
+// ---- planning of the block stage ------------------------------------------
+// Every launch of the coefficient stage is planned first: the blocks go to
+// work lists by their point count K (classes in queue order, heavy first:
+// K > 32, 25..32, 17..24, 13..16, 9..12, 1..8), which a persistent kernel
+// takes off one queue.  Optionally the blocks of each plane that share one
+// mask layout (the same K and positions, at least kGroupMin of them, K <=
+// kGroupMaxK) form a layout group: one factorisation for the group, and the
+// residual of all its blocks as one tensor-core product (Eq. 3 for a fixed
+// layout is linear in the values: r = E v).
+constexpr int kClasses = 6;
+constexpr int kGroupMaxK = 32;   // layouts with more points are not grouped
+constexpr int kGroupMin = 16;    // blocks of one layout before it is grouped
+constexpr int kMaxGroups = 256;  // groups per launch (more layouts stay per block)
+constexpr int kGroupRows = 256;  // pixels of the largest block (16 x 16)
+constexpr int kHashProbes = 32;  // linear probes of the layout table
+
+// device state of one planned launch, zeroed before the plan
+struct BlockPlanState {
+    uint32_t count[kClasses];    // entries per class list
+    uint32_t next;               // the coefficient kernel's main work queue
+    uint32_t next0;              // its queue of K > 32 blocks (CTAs with a slot)
+    uint32_t finished;           // CTAs of the coefficient kernel done
+    uint32_t ndef;               // FP64 re-solves deferred to the last CTA
+    uint32_t ngroups;            // layout groups claimed
+    uint32_t gfill[kMaxGroups];  // member entries listed per group
+    int32_t gslot[kMaxGroups];   // layout-table slot of group g
+    int32_t grep[kMaxGroups];    // a block of group g (its layout is the group's)
+};
+
+struct BlockPlan {
+    BlockPlanState *st;  // device
+    int32_t *list;       // kClasses x cap global block indices
+    int32_t *deferred;   // cap entries: FP64 re-solves for the last CTA
+    int32_t cap;         // >= the launch's blocks
+    // layout groups (hkey == nullptr: off)
+    unsigned long long *hkey;  // layout table: fingerprint per slot (0 = empty)
+    uint32_t *hcnt;            // blocks per slot
+    uint32_t *hgid;            // group id + 1 of the slot (0 = none)
+    uint32_t hmask;            // slots - 1 (a power of two)
+    int32_t *slot_of;          // per block: its slot, or -1
+    uint8_t *member;           // per block: 1 = evaluated by its group's product
+    int32_t *gmem;             // member entries (block * 2 + value plane), 2 x cap
+    uint16_t *E;               // per group: 3 bf16 splits of E, kGroupRows x kGroupMaxK each
+};
+
+// Device bytes of a plan for total_blocks blocks (with layout groups or
+// not), and the plan carved from such memory (256-byte aligned).
+size_t block_plan_bytes(int total_blocks, bool groups);
+BlockPlan carve_block_plan(void *mem, int total_blocks, bool groups);
+
+// Scratch of the coefficient stage: room for one K > 32 system per CTA of
+// the persistent coefficient kernel (a CTA solves its large blocks one after
+// the other in its slot; an FP64 re-solve uses the slot as doubles), and
+// the plan of the launch.
 //
 // Condition control: every block's bound kappa = 8 tr(G_PP) / (1 - K/N) on
 // cond_2(G_PP) (lambda_max <= tr, lambda_min >= (1 - K/N) / 8 since the
@@ -92,24 +144,41 @@ struct BlockScratch {
     uint32_t *flags;  // device error word
     float *big;       // big_ranges * kBigFloats floats
     int32_t big_ranges;
-    uint32_t *cstat = nullptr;  // nullptr, or [0] max kappa (float bits), [1] FP64 blocks, [2] K > 32 blocks
+    uint32_t *cstat = nullptr;  // nullptr, or [0] max kappa (float bits), [1] FP64 blocks, [2] K > 32 blocks,
+                                // [3] blocks of layout groups (per value plane), [4] layout groups
     float tau = 1e6f;           // condition threshold
+    BlockPlan plan{};           // lists and layout groups of the launch
 };
+
+// ---- autotuner table (tune.cu): choices keyed by GPU name and shape, kept
+// for the process and in a JSON file; -1 when there is none ---------------
+std::string gpu_name();  // of the current device
+int tune_lookup(const std::string &key);
+void tune_store(const std::string &key, int value);
 
 cudaError_t ensure_block_tables();
 const BlockTables &block_tables(int op = 0);  // of the current device, for operator op
 
-// c, a for every block (a = NaN: bad positions): one thread per block for
-// K <= 12, warps for K <= 32, a whole CTA for K > 32.  One launch, no
-// counters: the kernel's completion publishes every result.
-// pdl: launch as a programmatic dependent of the previous kernel in the
-// stream (the coefficient stage overlaps it and completes after it).
+// c, a for every block (a = NaN: bad positions): the plan (work lists;
+// layout groups when s.plan.hkey is set, after a clear of the layout table
+// and one pass that enters every block's layout), then one persistent launch:
+// one thread per block for K <= 12, warps for K <= 32, a whole CTA for
+// K > 32, and one CTA per layout group for its factorisation.  The
+// kernels' completion publishes every result.  pdl: the first launch may
+// start while the previous kernel in the stream finishes.
 cudaError_t launch_block_coef(const BlockJobs &jobs, const BlockScratch &s, cudaStream_t st, int *launches,
                               bool pdl = false);
 // r-field from c, a (Eq. 3 by Green's rows), r = v at the points; or, for
 // jobs in coefficient mode (p[k].q set, all jobs alike), from the
 // dequantised indices and the transmitted constants, with no overwrite.
-cudaError_t launch_block_eval(const BlockJobs &jobs, uint32_t *flags, cudaStream_t st, bool pdl = false);
+// plan: the launch's plan when its layout groups are on, else nullptr; the
+// launch's first CTAs then form the groups' residual planes, per group
+// R = V E^T on the tensor cores (bf16 values, E in three bf16 parts, FP32
+// accumulation), beside the per-block evaluation of the other blocks.
+cudaError_t launch_block_eval(const BlockJobs &jobs, uint32_t *flags, cudaStream_t st, bool pdl = false,
+                              const BlockPlan *plan = nullptr);
+// CTAs of the persistent coefficient kernel on this device (slots needed)
+int block_coef_ctas();
 
 // One inter frame for the pixel kernel: flow, references, the residual
 // planes the block kernels evaluated, outputs.
@@ -135,6 +204,8 @@ struct WarpPlane {
     const float *ref;    // FP32 reference plane (inter), or nullptr
     const float *src_hi; // intra prediction hi (+ lo) when ref == nullptr
     const float *src_lo; // may be nullptr
+    const float *src_hi1, *src_lo1;  // the other buffer of the iterate's ping-pong
+    const int32_t *src_sel;          // device: 1 = take src_hi1/src_lo1 (or nullptr)
     const float *r;      // residual field or nullptr
     float *ref_out;      // new FP32 reference (clamped), or nullptr
     uint8_t *out;        // uint8 output, or nullptr
@@ -164,6 +235,8 @@ struct RctFrame {
     const float *flow;                   // inter: luma flow (H x W x 2); nullptr: intra
     const float *ref[3];                 // inter: previous reference planes
     const float *src_hi[3], *src_lo[3];  // intra: the inpainted planes (lo may be nullptr)
+    const float *src_hi1[3], *src_lo1[3];  // the other buffers of the iterate's ping-pong
+    const int32_t *src_sel;              // device, per plane: 1 = take src_hi1/src_lo1 (or nullptr)
     const float *r[3];                   // residual planes, or nullptr
     float *ref_out[3];
     uint8_t *out[3];                     // R, G, B
@@ -201,28 +274,70 @@ struct IntraPlane {
     const int16_t *val16;          // signed mask values (RCT chroma) instead, or nullptr
     int32_t n;                     // mask size
     uint8_t *mask;                 // 1 = known pixel
-    float *uh[2], *ul[2];          // iterate u = hi + lo ([0] current, [1] next)
+    float *uh[2], *ul[2];          // iterate u = hi + lo, ping-pong (IntraCtl.upar)
     float *res;                    // FP32 Eq. 1 residual
-    float *e[2];                   // FP32 correction, ping-pong
+    float *e[2];                   // FP32 correction, ping-pong (launch it reads e[it & 1])
     unsigned long long *vsum;      // scratch: sum of mask values
-    unsigned int *rnorm;           // scratch: max |residual| (float bits)
-    float omega;                   // SOR relaxation factor
     int32_t ff;                    // 1: float-float iterate, 0: FP32 only
     int32_t tiles_x, tile_base;    // filled by the launchers
+    int32_t tiles;                 // regions of the plane (filled by the launchers)
+};
+
+// Control state of one intra solve, in device memory: the correction loop
+// decides on the device (no host read between cycles).  The last CTA of
+// each residual launch plans the next cycle (sweeps per plane from the
+// residual reached and the observed contraction, Young's relation for the
+// relaxation factor).  Sweep launches come in pairs of fixed parity (launch
+// it = 2 iter + parity reads correction buffer e[it & 1] and writes the
+// other, so a plane's correction after its nl launches sits in e[nl & 1]);
+// the last CTA of each pair's second launch advances iter.  Both publish
+// whether the loop goes on, to conditional graph nodes (h_outer, h_inner)
+// and to go_outer / go_inner.
+struct IntraCtl {
+    double tol;                // max |(L u)_i| to reach
+    double rn[3];              // residual reached per plane
+    double rate[3];            // contraction per sweep per plane
+    float omega[3];            // relaxation factor per plane
+    int32_t max_cycles, spl;   // cycle cap, sweeps per launch
+    int32_t nl[3];             // sweep launches of the current cycle per plane
+    int32_t maxl, iter, cycles;  // launches of the cycle, pairs done, cycles done
+    int32_t sweeps[3], sweeps_max;
+    int32_t upar[3];           // the u buffer holding a plane's current iterate
+    uint32_t rbits[3];         // max |residual| of the last residual launch (float bits)
+    uint32_t done_ctas;        // CTAs of the current launch that finished
+    int32_t go_outer, go_inner, converged;
+    // statistics since the decoder's last sync (kept across solves): sweep
+    // and residual launches and the pixels they covered, solves that ended
+    // above the tolerance
+    int64_t sor_launches, sor_pixels, res_launches, res_pixels, unconverged;
 };
 
 struct IntraJobs {
     IntraPlane p[3];
     int32_t n;
+    IntraCtl *ctl;                      // control state
+    unsigned long long h_outer, h_inner;  // conditional handles (0: launched from the host)
 };
 
 cudaError_t launch_intra_init(IntraJobs &jobs, uint32_t *flags, cudaStream_t st, int *launches);
-// u_next = u + e (unless first), res = (L u_next) at unknowns, rnorm = max |res|.
-cudaError_t launch_intra_residual(IntraJobs &jobs, int e_in, bool add_e, cudaStream_t st);
-// Red-black SOR sweeps of (-L_UU) e = res, from e = 0 (first) or e[e_in].
-// Returns the index of the e buffer holding the result.
-cudaError_t launch_intra_sor(IntraJobs &jobs, int e_in, bool from_zero, int sweeps, cudaStream_t st, int *e_out,
-                             int *launches);
+// The control state for a new solve: omega0 per plane, tolerance, cycle cap.
+cudaError_t launch_intra_ctl_init(const IntraJobs &jobs, const float *omega0, double tol, int max_cycles,
+                                  cudaStream_t st);
+// One residual launch: first = the start of the solve (res = L u, the
+// norms, the first cycle's plan), else the end of a cycle (u += e for the
+// planes that swept, res, norms, the next cycle's plan).
+cudaError_t launch_intra_residual(IntraJobs &jobs, bool first, cudaStream_t st);
+// One pair of launches of kS red-black sweeps each over the planes the
+// control state keeps active (variant: the region tiling, see
+// set_sor_variant).
+cudaError_t launch_intra_sor_pair(IntraJobs &jobs, int variant, cudaStream_t st);
+// The SOR tiling for these planes: tuned (timing launches on tune_ctl, a
+// control state of its own), looked up, or pinned.
+int intra_sor_variant(IntraJobs &jobs, IntraCtl *tune_ctl, cudaStream_t st);
+// The whole correction loop as a graph: the first residual launch, then
+// while the plan says so: (sweep launches while the plan says so, then a
+// residual launch).  Conditional WHILE nodes; jobs.ctl is the state.
+cudaError_t build_intra_graph(const IntraJobs &jobs, int variant, cudaGraphExec_t *exec);
 int intra_sweeps_per_launch();
 cudaError_t intra_init();  // once per device
 int set_sor_variant(int v);  // -1: autotune; 0..2 pin a variant (0 on success)

@@ -25,10 +25,14 @@
 // block's range, packed Cholesky in the range's scratch slot) and the
 // evaluation into residual planes (one warp per block; also the
 // coefficient mode, which dequantises instead of solving).
+#include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstring>
 #include <mutex>
 #include <vector>
+
+#include <cuda_bf16.h>
 
 #include "block_device.cuh"
 
@@ -213,32 +217,35 @@ __device__ __forceinline__ void seg_run(const SegBlock &b, int K, int i, float *
 constexpr int kTK = 12;
 __host__ __device__ constexpr int tri(int i) { return i * (i + 1) / 2; }
 
-// Coefficients of one block by one thread, K <= kTK: G_PP padded to
-// kTK x kTK with the identity (the padding rows of L are unit rows and the
+// Coefficients of one block by one thread, K <= KM (KM = 8 or kTK = 12):
+// G_PP padded to KM x KM with the identity (the padding rows of L are unit rows and the
 // padding entries of every solution are zero), Cholesky-Crout in
 // registers, fully unrolled, so that no control flow depends on K.
 //   L y_v = v, L y_1 = 1 (on the K points);  a = (y_1 . y_v) / (y_1 . y_1)
 //   L^T c = y_v - a y_1
 // Returns false if a pivot of a real row was not positive; tr = tr(G_PP).
-template <bool TWO>
-__device__ __forceinline__ bool thread_block_coef(const float *__restrict__ G, int rl, int K, const int (&p)[kTK],
-                                                  const float (&v0)[kTK], const float (&v1)[kTK], float (&c0)[kTK],
-                                                  float (&c1)[kTK], float &a0, float &a1, float &tr)
+// The padding leaves every real entry's arithmetic as it is (padding
+// entries of L, y and c are exact zeros that enter sums as +0), so KM = 8
+// and KM = 12 give the same bits for K <= 8.
+template <int KM, bool TWO>
+__device__ __forceinline__ bool thread_block_coef(const float *__restrict__ G, int rl, int K, const int (&p)[KM],
+                                                  const float (&v0)[KM], const float (&v1)[KM], float (&c0)[KM],
+                                                  float (&c1)[KM], float &a0, float &a1, float &tr)
 {
-    float L[tri(kTK)], inv[kTK];
+    float L[tri(KM)], inv[KM];
 #pragma unroll
-    for (int i = 0; i < kTK; ++i) {
+    for (int i = 0; i < KM; ++i) {
         const float *row = G + p[i] * rl;
 #pragma unroll
         for (int j = 0; j <= i; ++j) L[tri(i) + j] = (i < K && j < K) ? __ldg(row + p[j]) : (i == j ? 1.f : 0.f);
     }
     tr = 0.f;
 #pragma unroll
-    for (int i = 0; i < kTK; ++i)
+    for (int i = 0; i < KM; ++i)
         if (i < K) tr += L[tri(i) + i];
     bool spd = true;
 #pragma unroll
-    for (int k = 0; k < kTK; ++k) {
+    for (int k = 0; k < KM; ++k) {
         float d = L[tri(k) + k];
 #pragma unroll
         for (int m = 0; m < k; ++m) d = fmaf(-L[tri(k) + m], L[tri(k) + m], d);
@@ -247,16 +254,16 @@ __device__ __forceinline__ bool thread_block_coef(const float *__restrict__ G, i
         L[tri(k) + k] = d * isd;
         inv[k] = isd;
 #pragma unroll
-        for (int i = k + 1; i < kTK; ++i) {
+        for (int i = k + 1; i < KM; ++i) {
             float s = L[tri(i) + k];
 #pragma unroll
             for (int m = 0; m < k; ++m) s = fmaf(-L[tri(i) + m], L[tri(k) + m], s);
             L[tri(i) + k] = s * isd;
         }
     }
-    float y0[kTK], y1[kTK], y2[kTK];
+    float y0[KM], y1[KM], y2[KM];
 #pragma unroll
-    for (int i = 0; i < kTK; ++i) {
+    for (int i = 0; i < KM; ++i) {
         float s0 = v0[i], s1 = TWO ? v1[i] : 0.f, s2 = i < K ? 1.f : 0.f;
 #pragma unroll
         for (int m = 0; m < i; ++m) {
@@ -270,7 +277,7 @@ __device__ __forceinline__ bool thread_block_coef(const float *__restrict__ G, i
     }
     float d0 = 0.f, d1 = 0.f, d2 = 0.f;
 #pragma unroll
-    for (int i = 0; i < kTK; ++i) {
+    for (int i = 0; i < KM; ++i) {
         d0 = fmaf(y2[i], y0[i], d0);
         if (TWO) d1 = fmaf(y2[i], y1[i], d1);
         d2 = fmaf(y2[i], y2[i], d2);
@@ -279,10 +286,10 @@ __device__ __forceinline__ bool thread_block_coef(const float *__restrict__ G, i
     a0 = d0 * r22;
     a1 = TWO ? d1 * r22 : 0.f;
 #pragma unroll
-    for (int i = kTK - 1; i >= 0; --i) {
+    for (int i = KM - 1; i >= 0; --i) {
         float s0 = fmaf(-a0, y2[i], y0[i]), s1 = TWO ? fmaf(-a1, y2[i], y1[i]) : 0.f;
 #pragma unroll
-        for (int m = i + 1; m < kTK; ++m) {
+        for (int m = i + 1; m < KM; ++m) {
             s0 = fmaf(-L[tri(m) + i], c0[m], s0);
             if (TWO) s1 = fmaf(-L[tri(m) + i], c1[m], s1);
         }
@@ -292,20 +299,20 @@ __device__ __forceinline__ bool thread_block_coef(const float *__restrict__ G, i
     return spd;
 }
 
-// one block with 1 <= K <= kTK by the calling thread: positions checked,
+// one block with 1 <= K <= KM by the calling thread: positions checked,
 // then c (per point) and a (per block) written.  Returns the block's
 // condition bound (0 for bad positions).
-template <bool TWO>
+template <int KM, bool TWO>
 __device__ __forceinline__ float thread_run(const BlockPlane &P, const BlockGeom &g, const BlockTables &tab,
                                             const BlockScratch &S)
 {
     const int K = g.K, N = g.w * g.h;
-    int p[kTK];
-    float v0[kTK], v1[kTK];
+    int p[KM];
+    float v0[KM], v1[KM];
     bool ok = true;
     int prev = -1;
 #pragma unroll
-    for (int i = 0; i < kTK; ++i) {
+    for (int i = 0; i < KM; ++i) {
         p[i] = 0;
         v0[i] = v1[i] = 0.f;
         if (i < K) {
@@ -321,11 +328,11 @@ __device__ __forceinline__ float thread_run(const BlockPlane &P, const BlockGeom
         mark_bad(P, g.lb);
         return 0.f;
     }
-    float c0[kTK], c1[kTK], a0, a1, tr;
+    float c0[KM], c1[KM], a0, a1, tr;
     const bool spd =
-        thread_block_coef<TWO>(green_rows(tab, g.w, g.h), g_rowlen(N), K, p, v0, v1, c0, c1, a0, a1, tr);
+        thread_block_coef<KM, TWO>(green_rows(tab, g.w, g.h), g_rowlen(N), K, p, v0, v1, c0, c1, a0, a1, tr);
 #pragma unroll
-    for (int i = 0; i < kTK; ++i)
+    for (int i = 0; i < KM; ++i)
         if (i < K) {
             P.coef[0][g.s + i] = c0[i];
             if (TWO) P.coef[1][g.s + i] = c1[i];
@@ -490,118 +497,480 @@ __device__ __noinline__ void cta_block(const BlockJobs &J, const BlockTables &ta
     __syncthreads();
 }
 
-// Warp path: warp w of a warp-path CTA scans the 32 blocks gb0 .. gb0+31
-// and solves those with kTK < K <= 32: K <= 16 two at a time in 16-lane
-// halves, K <= 24 with all lanes (both in registers, fully unrolled: in a
-// launch over many frames many warps of an SM share the code), larger K
-// with the shared-memory routine.  Blocks with K > 32 go to the CTA's list.
-__device__ __forceinline__ void warp_path(const BlockJobs &J, const BlockTables &tab, const BlockScratch &S, int gb0,
-                                          int lane, float *sm, int *s_large, int *s_nlarge)
+// ---- plan of a coefficient launch ------------------------------------------
+// class of a block with K >= 1 points, in queue order (heavy first):
+// K > 32, 25..32, 17..24, 13..16, 9..12, 1..8
+__device__ __forceinline__ int k_class(int K)
 {
-    const SegBlock own = seg_block(J, gb0 + lane);
-    if (own.P != nullptr && !own.g.bad && own.g.K > kWarpK) s_large[atomicAdd(s_nlarge, 1)] = gb0 + lane;
-    const int k = seg_k(own);
-    unsigned m16 = __ballot_sync(0xffffffffu, k > kTK && k <= 16);
-    unsigned m32 = __ballot_sync(0xffffffffu, k > 16);
-    const int half = lane >> 4, i = lane & 15;
-    while (m16) {
-        const int ba = __ffs(m16) - 1;
-        m16 &= m16 - 1;
-        int bb = -1;
-        if (m16) {
-            bb = __ffs(m16) - 1;
-            m16 &= m16 - 1;
-        }
-        const int mine = half ? bb : ba;
-        const int gb = mine >= 0 ? gb0 + mine : J.total_blocks;
-        SegBlock b = seg_block(J, gb);
-        b.g.K = seg_k(b);
-        const int K = seg_validate<16>(b, i, half, S);
-        seg_run<16, 16>(b, K, i, sm + half * 16 * 17, tab, S, gb, s_large, s_nlarge);
-        __syncwarp();
+    return K > 32 ? 0 : (K > 24 ? 1 : (K > 16 ? 2 : (K > 12 ? 3 : (K > 8 ? 4 : 5))));
+}
+// blocks per work item of each class: a CTA, a warp each, two per warp,
+// a thread each
+__host__ __device__ __forceinline__ int class_item(int c)
+{
+    return c == 0 ? 1 : (c <= 2 ? kCoefThreads / 32 : (c == 3 ? 2 * kCoefThreads / 32 : kCoefThreads));
+}
+
+// FNV-1a over 32-bit words: the fingerprint of a layout
+__device__ __forceinline__ unsigned long long fnv(unsigned long long h, uint32_t v)
+{
+    return (h ^ v) * 0x100000001b3ull;
+}
+
+// Layout table (layout groups on): a block with 1 <= K <= kGroupMaxK and
+// valid positions enters its layout (job, w, h, K, positions) into the
+// table and counts it; the block that makes a layout's count kGroupMin
+// claims a group for it, unless the layout's condition bound is above the
+// threshold (those blocks stay on the FP64-aware path).  Returns the slot,
+// or -1 (not a candidate, or the table crowded).
+__device__ __forceinline__ int enter_layout(const BlockPlan &L, const BlockTables &tab, float tau, int k,
+                                            const BlockPlane &P, const BlockGeom &g, int gb)
+{
+    if (g.bad || g.K < 1 || g.K > kGroupMaxK) return -1;
+    const int K = g.K, N = g.w * g.h;
+    unsigned long long h = 0xcbf29ce484222325ull;
+    h = fnv(h, (uint32_t)k);
+    h = fnv(h, (uint32_t)(g.w | (g.h << 8) | (K << 16)));
+    int prev = -1;
+    for (int j = 0; j < K; ++j) {
+        const int p = __ldg(P.pos + g.s + j);
+        if (p >= N || p <= prev) return -1;  // the coefficient stage reports it
+        prev = p;
+        h = fnv(h, (uint32_t)p);
     }
-    while (m32) {
-        const int ba = __ffs(m32) - 1;
-        m32 &= m32 - 1;
-        SegBlock b = seg_block(J, gb0 + ba);
-        b.g.K = seg_k(b);
-        const int K = seg_validate<32>(b, lane, 0, S);
-        if (K > 24) seg_run<32, 0>(b, K, lane, sm, tab, S, gb0 + ba, s_large, s_nlarge);
-        else if (K > 0) seg_run<32, 24>(b, K, lane, sm, tab, S, gb0 + ba, s_large, s_nlarge);
-        __syncwarp();
+    if (h == 0) h = 1;
+    uint32_t slot = (uint32_t)(h ^ (h >> 32)) & L.hmask;
+    int probe = 0;
+    for (; probe < kHashProbes; ++probe) {
+        const unsigned long long old = atomicCAS(L.hkey + slot, 0ull, h);
+        if (old == 0ull || old == h) break;
+        slot = (slot + 1) & L.hmask;
+    }
+    if (probe == kHashProbes) return -1;
+    const uint32_t c = atomicAdd(L.hcnt + slot, 1u) + 1u;
+    if (c == (uint32_t)kGroupMin) {
+        const float *G = green_rows(tab, g.w, g.h);
+        const int rl = g_rowlen(N);
+        float tr = 0.f;
+        for (int j = 0; j < K; ++j) {
+            const int p = __ldg(P.pos + g.s + j);
+            tr += __ldg(G + p * rl + p);
+        }
+        if (cond_bound(tab.amax, tr, K, N) <= tau) {
+            const uint32_t gid = atomicAdd(&L.st->ngroups, 1u);
+            if (gid < (uint32_t)kMaxGroups) {
+                L.st->gslot[gid] = (int)slot;
+                L.st->grep[gid] = gb;
+                L.hgid[slot] = gid + 1;
+            }
+        }
+    }
+    return (int)slot;
+}
+
+// Exclusive prefix of f(0), ..., f(n-1) into s_out[0..n] (s_out[n] = the
+// total): a block-wide scan, a chunk of blockDim entries at a time (any
+// block size that is a multiple of 32).  Every CTA computes the same.
+template <class F>
+__device__ __forceinline__ void block_prefix(int n, F f, int *s_out)
+{
+    __shared__ int s_warp[32], s_carry;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (t == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + t;
+        const int own = i < n ? f(i) : 0;
+        int v = own;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += x;
+        }
+        if (lane == 31) s_warp[w] = v;
+        __syncthreads();
+        int before = s_carry;
+        for (int k = 0; k < w; ++k) before += s_warp[k];
+        if (i < n) s_out[i] = before + v - own;
+        __syncthreads();
+        if (t == blockDim.x - 1) s_carry = before + v;
+        __syncthreads();
+    }
+    if (t == 0) s_out[n] = s_carry;
+    __syncthreads();
+}
+
+// member-entry offset of each group into s_off (entries are reserved at two
+// per block of the group's slot count: the plane pair of a shared chroma
+// layout takes two); returns the number of groups
+__device__ __forceinline__ int group_offsets(const BlockPlan &L, int *s_off)
+{
+    const int ng = min((int)*(volatile uint32_t *)&L.st->ngroups, kMaxGroups);
+    block_prefix(ng, [&](int g) { return 2 * (int)__ldg(L.hcnt + L.st->gslot[g]); }, s_off);
+    return ng;
+}
+
+// Whether block gb (job k, geometry g) belongs to its layout's group: the
+// same job, shape, K and positions as the group's block, and values that
+// the product takes exactly.  Members are listed (one entry per value
+// plane) and marked; their coefficients are never formed.
+__device__ __forceinline__ bool group_member(const BlockJobs &J, const BlockPlan &L, int k, const BlockGeom &g,
+                                             int gb, const int *s_off)
+{
+    const int slot = L.slot_of[gb];
+    if (slot < 0) return false;
+    const int gid = (int)L.hgid[slot] - 1;
+    if (gid < 0) return false;
+    const int rep = L.st->grep[gid];
+    if (find_job(J, rep) != k) return false;
+    const BlockPlane &P = J.p[k];
+    const BlockGeom gr = block_geom(P, rep - P.block_base);
+    if (gr.w != g.w || gr.h != g.h || gr.K != g.K) return false;
+    const bool two = P.val[1] != nullptr;
+    for (int j = 0; j < g.K; ++j) {
+        if (__ldg(P.pos + g.s + j) != __ldg(P.pos + gr.s + j)) return false;
+        // the product takes the values as bf16: integers up to 256 are exact
+        if (abs((int)__ldg(P.val[0] + g.s + j)) > 256) return false;
+        if (two && abs((int)__ldg(P.val[1] + g.s + j)) > 256) return false;
+    }
+    const uint32_t idx = atomicAdd(L.st->gfill + gid, two ? 2u : 1u);
+    int32_t *e = L.gmem + s_off[gid] + idx;
+    e[0] = 2 * gb;
+    if (two) e[1] = 2 * gb + 1;
+    L.member[gb] = 1;
+    return true;
+}
+
+// The plan: every block's class, appended to the class lists by
+// warp-aggregated atomics, and (layout groups on) its layout entered into
+// the table.  Bad block pointers are reported here.
+__global__ void __launch_bounds__(256) block_plan_kernel(const __grid_constant__ BlockJobs J, BlockPlan L,
+                                                         BlockTables tab, float tau, uint32_t *flags)
+{
+    // the lists may still be read by the previous coefficient launch
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int gb = blockIdx.x * 256 + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    int cls = -1;
+    if (gb < J.total_blocks) {
+        const int k = find_job(J, gb);
+        const BlockPlane &P = J.p[k];
+        const BlockGeom g = block_geom(P, gb - P.block_base);
+        if (g.bad) atomicOr(flags, g.bad);
+        else if (g.K > 0) cls = k_class(g.K);
+        if (L.hkey) {
+            L.slot_of[gb] = enter_layout(L, tab, tau, k, P, g, gb);
+            L.member[gb] = 0;  // the coefficient kernel decides
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < kClasses; ++c) {
+        const unsigned m = __ballot_sync(0xffffffffu, cls == c);
+        if (!m) continue;
+        const int leader = __ffs(m) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(L.st->count + c, (uint32_t)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (cls == c) L.list[(size_t)c * L.cap + base + __popc(m & ((1u << lane) - 1u))] = gb;
     }
 }
 
-// Coefficient stage.  The grid has two halves over the same ranges of
-// kRange blocks.  Thread-path CTA nrange + c: thread t takes block
-// kRange c + t and solves it when K <= 12.  Warp-path CTA c: its warps
-// solve the range's blocks with 12 < K <= 32, then the whole CTA those with
-// K > 32, one after the other in the range's scratch slot.  Blocks whose
-// condition bound exceeds the threshold are re-solved in FP64 by their CTA
-// after its first phase (thread path: in shared memory; warp path: in the
-// slot).  No counters: the kernel's completion publishes every result.
-__device__ __forceinline__ void coef_body(const BlockJobs &J, const BlockTables &tab, const BlockScratch &S)
+// ---- factorisation of a layout group -------------------------------------
+// For a fixed layout P the residual is linear in the values v (Eqs. 2-3):
+// with z = G_PP^-1 1, s = 1^T z and W = G_PP^-1 - z z^T / s (symmetric),
+//   a = z^T v / s,  c = W v,  r(x) = G[x, P] c + a = E[x, :] v,
+//   E[x, :] = G[x, P] W + z^T / s.
+// G_PP^-1 comes from Gauss-Jordan elimination on [G_PP | I] (G_PP is SPD,
+// so no pivoting), K steps with the whole CTA; then every pixel's row of E
+// is an independent K x K product (no dependent chains).  The rows of E at
+// the points are the unit rows, which makes r exact there, as the
+// per-block path's overwrite does.  E is stored as three bf16 parts (hi,
+// mid, lo: 24 significant bits together) for the tensor-core product, in
+// row-major pairs of columns, kGroupMaxK columns per row (zero beyond K)
+// and kGroupRows rows (zero beyond the block's pixels).  A group takes two
+// work items: rows 0..127 and 128..255.
+constexpr int kFactorItems = 2;
+static_assert(kFactorItems * kCoefThreads == kGroupRows, "a row of E per thread");
+
+template <int KP>
+__device__ __forceinline__ void group_row(const float *__restrict__ G, int rl, int K, int x, const unsigned char *s_p,
+                                          const float (*A)[2 * kGroupMaxK + 1], const float *zs, float (&e)[kGroupMaxK])
 {
-    static_assert(kCoefThreads == kRange, "one thread per block of a range");
+    float acc[KP];
+#pragma unroll
+    for (int k = 0; k < KP; ++k) acc[k] = k < K ? zs[k] : 0.f;
+    const float *row = G + x * rl;
+    for (int j = 0; j < K; ++j) {
+        const float g = __ldg(row + s_p[j]);
+#pragma unroll
+        for (int k = 0; k < KP; ++k) acc[k] = fmaf(g, A[j][kGroupMaxK + k], acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < kGroupMaxK; ++k) e[k] = (k < KP && k < K) ? acc[k < KP ? k : 0] : 0.f;
+}
+
+__device__ __noinline__ void group_factor(const BlockJobs &J, const BlockPlan &L, const BlockTables &tab, int gid,
+                                          int part, float (*A)[2 * kGroupMaxK + 1], float *wv, unsigned char *s_p)
+{
+    const int tid = threadIdx.x;
+    const int rep = L.st->grep[gid];
+    const BlockPlane &P = J.p[find_job(J, rep)];
+    const BlockGeom g = block_geom(P, rep - P.block_base);
+    const int K = g.K, N = g.w * g.h, rl = g_rowlen(N);
+    const float *G = green_rows(tab, g.w, g.h);
+    for (int j = tid; j < K; j += kCoefThreads) s_p[j] = __ldg(P.pos + g.s + j);
+    __syncthreads();
+    // [G_PP | I]: columns 0..K-1 and kGroupMaxK .. kGroupMaxK + K - 1
+    for (int q = tid; q < K * K; q += kCoefThreads) {
+        const int i = q / K, j = q - i * K;
+        A[i][j] = __ldg(G + s_p[i] * rl + s_p[j]);
+        A[i][kGroupMaxK + j] = i == j ? 1.f : 0.f;
+    }
+    __syncthreads();
+    float *f = wv + 64;  // column k before its elimination
+    for (int k = 0; k < K; ++k) {
+        const float rp = 1.f / A[k][k];
+        for (int i = tid; i < K; i += kCoefThreads) f[i] = A[i][k];
+        __syncthreads();
+        for (int j = tid; j < 2 * kGroupMaxK; j += kCoefThreads) A[k][j] *= rp;
+        __syncthreads();
+        for (int q = tid; q < K * 2 * kGroupMaxK; q += kCoefThreads) {
+            const int i = q / (2 * kGroupMaxK), j = q - i * (2 * kGroupMaxK);
+            if (i != k) A[i][j] = fmaf(-f[i], A[k][j], A[i][j]);
+        }
+        __syncthreads();
+    }
+    // z = G_PP^-1 1, zs = z / s, W = G_PP^-1 - z z^T / s (in place)
+    if (tid < K) {
+        float z = 0.f;
+        for (int j = 0; j < K; ++j) z += A[tid][kGroupMaxK + j];
+        wv[tid] = z;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float sum = 0.f;
+        for (int j = 0; j < K; ++j) sum += wv[j];
+        wv[96] = 1.f / sum;
+    }
+    __syncthreads();
+    const float rs = wv[96];
+    for (int q = tid; q < K * K; q += kCoefThreads) {
+        const int i = q / K, j = q - i * K;
+        A[i][kGroupMaxK + j] = fmaf(-wv[i] * rs, wv[j], A[i][kGroupMaxK + j]);
+    }
+    if (tid < K) wv[32 + tid] = wv[tid] * rs;
+    __syncthreads();
+    uint32_t *E = reinterpret_cast<uint32_t *>(L.E + (size_t)gid * 3 * kGroupRows * kGroupMaxK);
+    constexpr int kPairs = kGroupMaxK / 2;
+    const int x = part * kCoefThreads + tid;  // one row of E per thread
+    float e[kGroupMaxK];
+#pragma unroll
+    for (int k = 0; k < kGroupMaxK; ++k) e[k] = 0.f;
+    int jp = -1;
+    for (int j = 0; j < K; ++j)
+        if (s_p[j] == x) jp = j;
+    if (x < N && jp >= 0) {
+#pragma unroll
+        for (int k = 0; k < kGroupMaxK; ++k) e[k] = k == jp ? 1.f : 0.f;
+    } else if (x < N) {
+        if (K <= 16) group_row<16>(G, rl, K, x, s_p, A, wv + 32, e);
+        else group_row<32>(G, rl, K, x, s_p, A, wv + 32, e);
+    }
+#pragma unroll
+    for (int q = 0; q < kPairs; ++q) {
+        uint32_t w[3];
+        float v0 = e[2 * q], v1 = e[2 * q + 1];
+#pragma unroll
+        for (int pt = 0; pt < 3; ++pt) {
+            const __nv_bfloat16 b0 = __float2bfloat16_rn(v0), b1 = __float2bfloat16_rn(v1);
+            w[pt] = (uint32_t)__bfloat16_as_ushort(b0) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
+            v0 -= __bfloat162float(b0);  // exact: the next part carries the remainder
+            v1 -= __bfloat162float(b1);
+        }
+#pragma unroll
+        for (int pt = 0; pt < 3; ++pt) E[((size_t)pt * kGroupRows + x) * kPairs + q] = w[pt];
+    }
+    __syncthreads();
+}
+
+// ---- the persistent coefficient kernel ------------------------------------
+// Work items, taken from one queue (an atomic counter) by every CTA: first
+// the layout groups' factorisations (a CTA each), then the class lists in
+// queue order: K > 32 a block per CTA, K in 17..32 a block per warp, K in
+// 13..16 two per warp (16-lane halves), K <= 12 a block per thread (the
+// system padded to 12 x 12, or 8 x 8 for K <= 8).  Blocks with K > 32 need
+// a scratch slot: they sit on a queue of their own that only the first
+// S.big_ranges CTAs (the ones with a slot) take, before the main queue.
+// Blocks above the condition threshold are re-solved in FP64 by their CTA
+// after the item (K <= 12 in shared memory, larger in the slot); a CTA
+// without a slot defers a larger one to a list that the last CTA to finish
+// drains with slot 0 (the kernel's completion count; no CTA waits).
+// a member of a layout group (groups on): listed for the group's product,
+// counted, and left without coefficients
+__device__ __forceinline__ bool take_member(const BlockJobs &J, const BlockScratch &S, int k, const BlockGeom &g,
+                                            int gb, const int *s_off)
+{
+    if (!S.plan.hkey || !group_member(J, S.plan, k, g, gb, s_off)) return false;
+    if (S.cstat) atomicAdd(S.cstat + 3, J.p[k].val[1] != nullptr ? 2u : 1u);
+    return true;
+}
+
+__device__ __forceinline__ void thread_item(const BlockJobs &J, const BlockTables &tab, const BlockScratch &S,
+                                            int c, const int32_t *lst, int n, int *s_large, int *s_nlarge,
+                                            const int *s_off)
+{
+    const int t = threadIdx.x;
+    float kappa = 0.f;
+    int gb = -1;
+    if (t < n) {
+        gb = lst[t];
+        const int k = find_job(J, gb);
+        const BlockPlane &P = J.p[k];
+        const BlockGeom g = block_geom(P, gb - P.block_base);
+        const bool two = P.val[1] != nullptr;
+        if (take_member(J, S, k, g, gb, s_off)) {
+        } else if (c == 4) {
+            kappa = two ? thread_run<kTK, true>(P, g, tab, S) : thread_run<kTK, false>(P, g, tab, S);
+        } else {
+            kappa = two ? thread_run<8, true>(P, g, tab, S) : thread_run<8, false>(P, g, tab, S);
+        }
+    }
+    if (kappa > S.tau) s_large[atomicAdd(s_nlarge, 1)] = gb | kF64Bit;
+    if (S.cstat) {
+        const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(kappa));
+        if ((t & 31) == 0 && m) atomicMax(S.cstat, m);
+    }
+}
+
+__device__ __forceinline__ void warp_item(const BlockJobs &J, const BlockTables &tab, const BlockScratch &S, int c,
+                                          const int32_t *lst, int n, float *sm, int *s_large, int *s_nlarge,
+                                          const int *s_off)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // a member of a layout group: the segment's first lane lists it, the
+    // segment solves nothing
+    auto member = [&](int gb, int seg_lane0) {
+        int mem = 0;
+        if (lane == seg_lane0 && gb < J.total_blocks) {
+            const int k = find_job(J, gb);
+            mem = take_member(J, S, k, block_geom(J.p[k], gb - J.p[k].block_base), gb, s_off) ? 1 : 0;
+        }
+        return __shfl_sync(0xffffffffu, mem, seg_lane0) != 0;
+    };
+    if (c == 3) {  // 13..16: two blocks per warp in 16-lane halves
+        const int half = lane >> 4, i = lane & 15, idx = 2 * warp + half;
+        const int gb = idx < n ? lst[idx] : J.total_blocks;
+        const bool m0 = S.plan.hkey ? member(gb, 0) : false;  // every lane takes part in both
+        const bool m1 = S.plan.hkey ? member(gb, 16) : false;
+        SegBlock b = seg_block(J, gb);
+        b.g.K = (half ? m1 : m0) ? 0 : seg_k(b);
+        const int K = seg_validate<16>(b, i, half, S);
+        seg_run<16, 16>(b, K, i, sm + half * 16 * 17, tab, S, gb, s_large, s_nlarge);
+        __syncwarp();
+        return;
+    }
+    if (warp >= n) return;  // the whole warp
+    const int gb = lst[warp];
+    if (S.plan.hkey && member(gb, 0)) return;
+    SegBlock b = seg_block(J, gb);
+    b.g.K = seg_k(b);
+    const int K = seg_validate<32>(b, lane, 0, S);
+    if (K > 24) seg_run<32, 0>(b, K, lane, sm, tab, S, gb, s_large, s_nlarge);
+    else if (K > 0) seg_run<32, 24>(b, K, lane, sm, tab, S, gb, s_large, s_nlarge);
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kCoefThreads, 3) block_coef_kernel(const __grid_constant__ BlockJobs J,
+                                                                     BlockTables tab, BlockScratch S)
+{
+    // the plan's lists come from the preceding grid
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    static_assert(kCoefThreads == kRange, "one thread per block of a thread item");
     __shared__ float lts[kCoefThreads / 32][32 * 33];
     __shared__ unsigned char s_p[kBigMaxK];
     __shared__ float red[kCoefThreads / 32];
     __shared__ double redd[kCoefThreads / 32];
     __shared__ double w64[tri(kTK) + 3 * kTK];
-    __shared__ int s_large[kRange], s_nlarge, s_bad;
-    const int nrange = block_ranges(J.total_blocks);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) s_nlarge = 0;
+    __shared__ int s_large[kRange], s_nlarge, s_bad, s_item, s_last;
+    __shared__ int s_ofs[kClasses + 1], s_cnt[kClasses];
+    __shared__ int s_off[kMaxGroups + 1];  // member-entry offsets of the layout groups
+    const BlockPlan &L = S.plan;
+    const int tid = threadIdx.x;
+    if (L.hkey) {
+        const int ng = group_offsets(L, s_off);
+        if (S.cstat && blockIdx.x == 0 && tid == 0) atomicAdd(S.cstat + 4, (uint32_t)ng);
+    }
+    const bool has_slot = (int)blockIdx.x < S.big_ranges;
+    float *slot = has_slot ? S.big + (size_t)blockIdx.x * kBigFloats : nullptr;
+    if (tid == 0) {
+        s_nlarge = 0;
+        // items of the main queue: groups, then classes 1..5
+        s_ofs[0] = L.hkey ? kFactorItems * min((int)L.st->ngroups, kMaxGroups) : 0;
+        for (int c = 0; c < kClasses; ++c) s_cnt[c] = (int)L.st->count[c];
+        for (int c = 1; c < kClasses; ++c) s_ofs[c] = s_ofs[c - 1] + (s_cnt[c] + class_item(c) - 1) / class_item(c);
+        s_ofs[kClasses] = s_ofs[kClasses - 1];
+    }
     __syncthreads();
-    // the heavier warp-path CTAs come first in the grid, so that the light
-    // thread-path CTAs fill the tail
-    if ((int)blockIdx.x >= nrange) {
-        const int gb = (blockIdx.x - nrange) * kRange + threadIdx.x;
-        float kappa = 0.f;
-        if (gb < J.total_blocks) {
-            const BlockPlane &P = J.p[find_job(J, gb)];
-            const BlockGeom g = block_geom(P, gb - P.block_base);
-            if (g.bad) {
-                atomicOr(S.flags, g.bad);
-            } else if (g.K > 0 && g.K <= kTK) {
-                kappa = P.val[1] != nullptr ? thread_run<true>(P, g, tab, S) : thread_run<false>(P, g, tab, S);
+    // K > 32: CTAs with a slot only
+    if (has_slot) {
+        for (;;) {
+            if (tid == 0) s_item = (int)atomicAdd(&L.st->next0, 1u);
+            __syncthreads();
+            const int item = s_item;
+            __syncthreads();
+            if (item >= s_cnt[0]) break;
+            cta_block(J, tab, S, L.list[item], slot, w64, s_p, red, redd, &s_bad);
+        }
+    }
+    for (;;) {
+        if (tid == 0) s_item = (int)atomicAdd(&L.st->next, 1u);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= s_ofs[kClasses - 1]) break;
+        if (item < s_ofs[0]) {
+            group_factor(J, L, tab, item / kFactorItems, item % kFactorItems,
+                         reinterpret_cast<float(*)[2 * kGroupMaxK + 1]>(lts[0]), lts[2], s_p);
+            continue;
+        }
+        int c = 1;
+        while (item >= s_ofs[c]) ++c;
+        const int first = (item - s_ofs[c - 1]) * class_item(c);
+        const int n = min(class_item(c), s_cnt[c] - first);
+        const int32_t *lst = L.list + (size_t)c * L.cap + first;
+        if (c >= 4) thread_item(J, tab, S, c, lst, n, s_large, &s_nlarge, s_off);
+        else warp_item(J, tab, S, c, lst, n, lts[tid >> 5], s_large, &s_nlarge, s_off);
+        __syncthreads();
+        const int nl = s_nlarge;
+        for (int i = 0; i < nl; ++i) {
+            const int entry = s_large[i];
+            const int gbl = entry & ~kF64Bit;
+            const BlockPlane &P = J.p[find_job(J, gbl)];
+            const int K = block_geom(P, gbl - P.block_base).K;
+            if (slot || K <= kTK) {
+                cta_block(J, tab, S, entry, slot, w64, s_p, red, redd, &s_bad);
+            } else if (tid == 0) {
+                L.deferred[atomicAdd(&L.st->ndef, 1u)] = entry;
             }
         }
-        if (kappa > S.tau) s_large[atomicAdd(&s_nlarge, 1)] = gb | kF64Bit;
-        if (S.cstat) {
-            const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(kappa));
-            if (lane == 0 && m) atomicMax(S.cstat, m);
-        }
         __syncthreads();
-        const int n = s_nlarge;
-        for (int i = 0; i < n; ++i) cta_block(J, tab, S, s_large[i], nullptr, w64, s_p, red, redd, &s_bad);
-        return;
+        if (tid == 0) s_nlarge = 0;
+        __syncthreads();
     }
-    const int range = blockIdx.x;
-    const int gb0 = range * kRange + warp * 32;
-    if (gb0 < J.total_blocks) warp_path(J, tab, S, gb0, lane, lts[warp], s_large, &s_nlarge);
+    // the last CTA to finish re-solves the deferred blocks in slot 0
     __syncthreads();
-    const int n = s_nlarge;
-    if (n == 0) return;
-    if (range >= S.big_ranges) {  // no scratch slot: the caller sized it wrongly
-        if (threadIdx.x == 0) atomicOr(S.flags, kFlagK);
-        return;
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(&L.st->finished, 1u) == gridDim.x - 1;
     }
-    float *slot = S.big + (size_t)range * kBigFloats;
-    for (int i = 0; i < n; ++i) cta_block(J, tab, S, s_large[i], slot, w64, s_p, red, redd, &s_bad);
-}
-
-// The coefficient stage reads only the caller's block data, never what the
-// preceding kernel wrote, so as a programmatic dependent it runs alongside
-// that kernel: the kernel after it may be scheduled at once, and the wait
-// for the preceding grid comes last, so that this grid completes after it
-// (every later kernel that waits for this grid sees the earlier ones done).
-__global__ void __launch_bounds__(kCoefThreads, 3) block_coef_kernel(const __grid_constant__ BlockJobs J,
-                                                                     BlockTables tab, BlockScratch S)
-{
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    coef_body(J, tab, S);
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int nd = (int)*(volatile uint32_t *)&L.st->ndef;
+    for (int i = 0; i < nd; ++i)
+        cta_block(J, tab, S, *(volatile int32_t *)(L.deferred + i), S.big, w64, s_p, red, redd, &s_bad);
 }
 
 // ---- evaluation stage into residual fields, one warp per block -----------
@@ -726,16 +1095,141 @@ __device__ __forceinline__ void eval_block(const BlockPlane &P, const BlockGeom 
     }
 }
 
+// ---- the layout groups' residual planes on the tensor cores ---------------
+// Per group, R (members x pixels) = V (members x K) E^T (K x pixels):
+// mma.sync m16n8k16 with bf16 operands and FP32 accumulation.  The values
+// are integers of at most 9 bits (|v| <= 256, checked by the plan), exact
+// in bf16; E enters as three bf16 parts, so every product is exact and the
+// sum carries FP32 rounding only.  A CTA of 8 warps takes an m-tile of 16
+// members; warp w covers pixels 32 w .. 32 w + 31 (four n-tiles of 8), its
+// E fragments loaded once per tile.  Accumulator element (m, n) is member
+// m's pixel n: two neighbouring pixels of one row per register pair.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// one member row of an m-tile: its residual plane base and values
+struct GroupRow {
+    float *R;
+    const int16_t *v;
+    int pitch;
+};
+
+__device__ __forceinline__ GroupRow group_row_of(const BlockJobs &J, int entry)
+{
+    GroupRow r{nullptr, nullptr, 0};
+    if (entry < 0) return r;
+    const int gb = entry >> 1, sel = entry & 1;
+    const BlockPlane &P = J.p[find_job(J, gb)];
+    const BlockGeom g = block_geom(P, gb - P.block_base);
+    r.pitch = P.r_pitch;
+    r.R = P.r[sel] + (size_t)g.y0 * P.r_pitch + g.x0;
+    r.v = P.val[sel] + g.s;
+    return r;
+}
+
+// The layout groups' products, by the first ncta CTAs of the evaluation
+// launch (4 warps each): work item = an m-tile of 16 member rows of one
+// group; warp w covers the pixels 64 w .. 64 w + 63 (eight n-tiles), E's
+// fragments loaded per n-tile.
+__device__ __forceinline__ void group_tiles(const BlockJobs &J, const BlockPlan &L, int cta, int ncta)
+{
+    __shared__ int s_off[kMaxGroups + 1], s_it[kMaxGroups + 1];
+    const int ng = group_offsets(L, s_off);
+    block_prefix(ng, [&](int g) { return ((int)L.st->gfill[g] + 15) / 16; }, s_it);
+    const int total = s_it[ng];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
+    constexpr int kPairs = kGroupMaxK / 2;
+    for (int item = cta; item < total; item += ncta) {
+        int g = 0;
+        while (g + 1 < ng && s_it[g + 1] <= item) ++g;
+        const int mt = item - s_it[g];
+        const int rep = L.st->grep[g];
+        const BlockPlane &Pr = J.p[find_job(J, rep)];
+        const BlockGeom gr = block_geom(Pr, rep - Pr.block_base);
+        const int K = gr.K, w = gr.w, N = gr.w * gr.h;
+        const int fill = min((int)L.st->gfill[g], s_off[g + 1] - s_off[g]);
+        const int m0 = 16 * mt + gq, m1 = m0 + 8;
+        const GroupRow r0 = group_row_of(J, m0 < fill ? L.gmem[s_off[g] + m0] : -1);
+        const GroupRow r1 = group_row_of(J, m1 < fill ? L.gmem[s_off[g] + m1] : -1);
+        const int nks = (K + 15) / 16;  // 1 or 2 k-steps
+        auto val = [&](const GroupRow &r, int k) { return (r.v && k < K) ? (float)__ldg(r.v + k) : 0.f; };
+        uint32_t a[2][4];
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            const int k = 16 * ks + 2 * tq;
+            a[ks][0] = pack_bf16(val(r0, k), val(r0, k + 1));
+            a[ks][1] = pack_bf16(val(r1, k), val(r1, k + 1));
+            a[ks][2] = pack_bf16(val(r0, k + 8), val(r0, k + 9));
+            a[ks][3] = pack_bf16(val(r1, k + 8), val(r1, k + 9));
+        }
+        const uint32_t *E = reinterpret_cast<const uint32_t *>(L.E + (size_t)g * 3 * kGroupRows * kGroupMaxK);
+        for (int nt = 0; nt < 8; ++nt) {
+            const int n0 = 64 * warp + 8 * nt;
+            if (n0 >= N) break;  // the whole warp
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                if (ks >= nks) break;
+#pragma unroll
+                for (int part = 2; part >= 0; --part) {
+                    const uint32_t *row = E + ((size_t)part * kGroupRows + n0 + gq) * kPairs + 8 * ks + tq;
+                    mma_bf16(d, a[ks], __ldg(row), __ldg(row + 4));
+                }
+            }
+            const int px = n0 + 2 * tq;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const GroupRow &r = h ? r1 : r0;
+                if (!r.R) continue;
+                const float v0 = d[2 * h], v1 = d[2 * h + 1];
+                const int y = px / w, x = px - y * w;
+                float *o = r.R + (size_t)y * r.pitch + x;
+                if (px + 1 < N && x + 1 < w && (reinterpret_cast<uintptr_t>(o) & 7) == 0) {
+                    *reinterpret_cast<float2 *>(o) = make_float2(v0, v1);
+                } else {
+                    if (px < N) *o = v0;
+                    if (px + 1 < N) {
+                        const int y1 = (px + 1) / w, x1 = px + 1 - y1 * w;
+                        r.R[(size_t)y1 * r.pitch + x1] = v1;
+                    }
+                }
+            }
+        }
+    }
+}
+// member: per block 1 when its layout group's product evaluates it (or
+// nullptr: no groups)
+// The evaluation launch.  Its first ngemm CTAs compute the layout groups'
+// products (the plan has them, groups on); the others take a block per
+// warp, skipping the groups' members.
 template <bool QC>
 __global__ void __launch_bounds__(128, 8) block_eval_kernel(const __grid_constant__ BlockJobs J, BlockTables tab,
-                                                            uint32_t *flags)
+                                                            uint32_t *flags, const __grid_constant__ BlockPlan L,
+                                                            int ngemm)
 {
-    // the coefficients come from the preceding grid
+    // the coefficients (and the groups' E) come from the preceding grid
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if ((int)blockIdx.x < ngemm) {
+        group_tiles(J, L, blockIdx.x, ngemm);
+        return;
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gb = blockIdx.x * 4 + warp;
+    const int gb = (blockIdx.x - ngemm) * 4 + warp;
     if (gb >= J.total_blocks) return;
+    if (L.hkey && L.member[gb]) return;
     const BlockPlane &P = J.p[find_job(J, gb)];
     const int lb = gb - P.block_base;
     const bool two = P.val[1] != nullptr;
@@ -754,6 +1248,7 @@ __global__ void __launch_bounds__(128, 8) block_eval_kernel(const __grid_constan
     } else if (two) eval_block<true, false>(P, g, G, a0, a1, R0, R1, pitch, lane, flags);
     else eval_block<false, false>(P, g, G, a0, a1, R0, R1, pitch, lane, flags);
 }
+
 
 }  // namespace
 
@@ -823,21 +1318,169 @@ struct PdlConfig {
 
 }  // namespace
 
+int block_coef_ctas()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    return 3 * sms;  // the kernel's launch bounds: 3 CTAs per SM
+}
+
+namespace {
+
+size_t a256(size_t b) { return (b + 255) / 256 * 256; }
+
+uint32_t table_slots(int total_blocks)
+{
+    uint32_t n = 1024;
+    while (n < 2u * (uint32_t)total_blocks && n < (1u << 20)) n <<= 1;
+    return n;
+}
+
+}  // namespace
+
+size_t block_plan_bytes(int total_blocks, bool groups)
+{
+    const size_t cap = (size_t)std::max(total_blocks, 1);
+    size_t b = a256(sizeof(BlockPlanState)) + a256(4 * cap * kClasses) + a256(4 * cap);  // + deferred
+    if (groups) {
+        const size_t slots = table_slots(total_blocks);
+        b += a256(8 * slots) + 2 * a256(4 * slots) + a256(4 * cap) + a256(cap) + a256(8 * cap) +
+             a256((size_t)kMaxGroups * 3 * kGroupRows * kGroupMaxK * 2);
+    }
+    return b;
+}
+
+BlockPlan carve_block_plan(void *mem, int total_blocks, bool groups)
+{
+    const size_t cap = (size_t)std::max(total_blocks, 1);
+    char *m = static_cast<char *>(mem);
+    auto take = [&](size_t bytes) {
+        char *q = m;
+        m += a256(bytes);
+        return q;
+    };
+    BlockPlan L{};
+    L.st = reinterpret_cast<BlockPlanState *>(take(sizeof(BlockPlanState)));
+    L.list = reinterpret_cast<int32_t *>(take(4 * cap * kClasses));
+    L.deferred = reinterpret_cast<int32_t *>(take(4 * cap));
+    L.cap = (int32_t)cap;
+    if (groups) {
+        const uint32_t slots = table_slots(total_blocks);
+        L.hmask = slots - 1;
+        L.hkey = reinterpret_cast<unsigned long long *>(take(8 * (size_t)slots));
+        L.hcnt = reinterpret_cast<uint32_t *>(take(4 * (size_t)slots));
+        L.hgid = reinterpret_cast<uint32_t *>(take(4 * (size_t)slots));
+        L.slot_of = reinterpret_cast<int32_t *>(take(4 * cap));
+        L.member = reinterpret_cast<uint8_t *>(take(cap));
+        L.gmem = reinterpret_cast<int32_t *>(take(8 * cap));
+        L.E = reinterpret_cast<uint16_t *>(take((size_t)kMaxGroups * 3 * kGroupRows * kGroupMaxK * 2));
+    }
+    return L;
+}
+
+namespace {
+
+// "<gpu>|coef|<blocks rounded up to a power of two>" in the tuner's table
+std::string coef_key(int total_blocks)
+{
+    int b = 1024;
+    while (b < total_blocks && b < (1 << 30)) b <<= 1;
+    return gpu_name() + "|coef|" + std::to_string(b);
+}
+
+// CTAs per SM of the persistent coefficient kernel, timed on this launch's
+// own work: 1, 2 and 3 per SM, twice each, round robin, with the plan's
+// queues reset before every run (each run computes the same coefficients;
+// the timing runs leave the statistics alone).  The choice goes to the
+// tuner's table; a later launch computes the coefficients once more.
+int tune_coef(const BlockJobs &jobs, const BlockScratch &s, cudaStream_t st, int sms)
+{
+    BlockScratch quiet = s;
+    quiet.cstat = nullptr;
+    quiet.plan.hkey = nullptr;  // the timing runs solve every block and list no group members
+    cudaEvent_t ev[7];
+    int made = 0;
+    cudaError_t e = cudaSuccess;
+    for (; made < 7 && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+    char *queues = reinterpret_cast<char *>(s.plan.st) + offsetof(BlockPlanState, next);
+    const size_t qbytes = offsetof(BlockPlanState, ngroups) - offsetof(BlockPlanState, next);
+    for (int t = 0; t < 6 && e == cudaSuccess; ++t) {
+        e = cudaMemsetAsync(queues, 0, qbytes, st);
+        if (e != cudaSuccess) break;
+        PdlConfig c(dim3((t % 3 + 1) * sms), dim3(kCoefThreads), st, false);
+        e = cudaLaunchKernelEx(&c.cfg, block_coef_kernel, jobs, block_tables(jobs.op), quiet);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[t + 1], st);
+    }
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[6]);
+    float best[3] = {1e30f, 1e30f, 1e30f};
+    for (int t = 0; t < 6 && e == cudaSuccess; ++t) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev[t], ev[t + 1]) == cudaSuccess) best[t % 3] = std::min(best[t % 3], ms);
+    }
+    for (int i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
+    // the queues again for the launch that follows
+    cudaMemsetAsync(queues, 0, qbytes, st);
+    if (e != cudaSuccess) return 3;
+    int pick = 3;  // the most CTAs unless fewer are at least 2 % faster
+    for (int m = 1; m <= 2; ++m)
+        if (best[m - 1] < 0.98f * best[pick - 1]) pick = m;
+    tune_store(coef_key(jobs.total_blocks), pick);
+    return pick;
+}
+
+}  // namespace
+
 cudaError_t launch_block_coef(const BlockJobs &jobs, const BlockScratch &s, cudaStream_t st, int *launches, bool pdl)
 {
     if (jobs.total_blocks == 0) return cudaSuccess;
-    PdlConfig c(dim3(2 * block_ranges(jobs.total_blocks)), dim3(kCoefThreads), st, pdl);
-    const cudaError_t e = cudaLaunchKernelEx(&c.cfg, block_coef_kernel, jobs, block_tables(jobs.op), s);
-    if (launches) *launches += 1;
+    const BlockPlan &L = s.plan;
+    if (!L.st || L.cap < jobs.total_blocks || s.big_ranges < 1) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(L.st, 0, sizeof(BlockPlanState), st);
+    if (e != cudaSuccess) return e;
+    const int nb = (jobs.total_blocks + 255) / 256;
+    int n = 0;
+    if (L.hkey) {
+        // clear the layout table (keys, counts and group ids lie back to
+        // back, carve_block_plan's order)
+        const size_t slots = (size_t)L.hmask + 1;
+        if ((e = cudaMemsetAsync(L.hkey, 0, 16 * slots, st)) != cudaSuccess) return e;
+    }
+    block_plan_kernel<<<nb, 256, 0, st>>>(jobs, L, block_tables(jobs.op), s.tau, s.flags);
+    ++n;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    (void)pdl;
+    const int sms = block_coef_ctas() / 3;
+    const std::string key = coef_key(jobs.total_blocks);
+    int per_sm = tune_lookup(key);
+    if (per_sm < 1 || per_sm > 3) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+            per_sm = tune_coef(jobs, s, st, sms);
+            n += 6;
+        } else {
+            per_sm = 3;
+        }
+    }
+    PdlConfig c(dim3(per_sm * sms), dim3(kCoefThreads), st, true);
+    e = cudaLaunchKernelEx(&c.cfg, block_coef_kernel, jobs, block_tables(jobs.op), s);
+    if (launches) *launches += n + 1;
     return e;
 }
 
-cudaError_t launch_block_eval(const BlockJobs &jobs, uint32_t *flags, cudaStream_t st, bool pdl)
+cudaError_t launch_block_eval(const BlockJobs &jobs, uint32_t *flags, cudaStream_t st, bool pdl, const BlockPlan *plan)
 {
     if (jobs.total_blocks == 0) return cudaSuccess;
-    PdlConfig c(dim3((jobs.total_blocks + 3) / 4), dim3(128), st, pdl);
-    if (jobs.p[0].q) return cudaLaunchKernelEx(&c.cfg, block_eval_kernel<true>, jobs, block_tables(jobs.op), flags);
-    return cudaLaunchKernelEx(&c.cfg, block_eval_kernel<false>, jobs, block_tables(jobs.op), flags);
+    BlockPlan L{};
+    if (plan && plan->hkey) L = *plan;
+    // the groups' products: two CTAs per SM at most, before the per-block CTAs
+    const int ngemm = L.hkey ? std::max(1, block_coef_ctas() / 3 * 2) : 0;
+    PdlConfig c(dim3(ngemm + (jobs.total_blocks + 3) / 4), dim3(128), st, pdl);
+    if (jobs.p[0].q)
+        return cudaLaunchKernelEx(&c.cfg, block_eval_kernel<true>, jobs, block_tables(jobs.op), flags, L, 0);
+    return cudaLaunchKernelEx(&c.cfg, block_eval_kernel<false>, jobs, block_tables(jobs.op), flags, L, ngemm);
 }
+
 
 }  // namespace hivc

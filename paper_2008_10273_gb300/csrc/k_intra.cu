@@ -121,80 +121,226 @@ __global__ void intra_scatter_kernel(const __grid_constant__ IntraJobs J)
     }
 }
 
+// ---- control of the correction loop, on the device ------------------------
+// The region of CTA b among the regions of the planes that work in this
+// launch (a sweep launch: launch index it < the plane's launch count; a
+// residual launch: every plane at the start, else the planes that swept),
+// in plane order: the working CTAs come first in the grid and the rest,
+// past them, exit at once.  Returns the plane (and lt, the region within
+// it), or -1.
+__device__ __forceinline__ int active_region(const IntraJobs &J, const IntraCtl *c, int it, bool residual, int b,
+                                             int &lt)
+{
+    int base = 0;
+    for (int p = 0; p < J.n; ++p) {
+        const bool on = residual ? (it != 0 || c->nl[p] > 0) : it < c->nl[p];
+        if (!on) continue;
+        if (b < base + J.p[p].tiles) {
+            lt = b - base;
+            return p;
+        }
+        base += J.p[p].tiles;
+    }
+    lt = 0;
+    return -1;
+}
+
+// Whether the calling CTA is the last of its launch to finish (every CTA
+// calls this once, after its work; no CTA waits).  The last one resets the
+// count for the next launch.
+__device__ __forceinline__ bool last_cta(IntraCtl *c, int *s_flag)
+{
+    __syncthreads();
+    // no fence: the last CTA reads no other CTA's plain stores (the residual
+    // norms are atomics, the next launch sees every store)
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const unsigned total = gridDim.x * gridDim.y;
+        const bool last = atomicAdd(&c->done_ctas, 1u) == total - 1;
+        if (last) c->done_ctas = 0;
+        *s_flag = last;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
+// Planning after a residual launch (one thread): take each swept plane's
+// residual norm; at the end of a cycle adapt the plane's relaxation factor
+// (slower than optimal SOR at this omega predicts means omega is below the
+// optimum; Young's relation (rho + omega - 1)^2 = rho omega^2 mu^2 gives the
+// Jacobi radius mu and the optimal omega); then plan the next cycle: each
+// plane above the tolerance sweeps towards the FP32 floor of the inner
+// solve (about 1e-5) or the remaining gap to the tolerance, whichever is
+// smaller, at the rate of optimally relaxed SOR, omega - 1.
+__device__ void plan_cycle(const IntraJobs &J, IntraCtl &c, bool first)
+{
+    for (int p = 0; p < J.n; ++p) {
+        if (!first && c.nl[p] == 0) continue;
+        // the max of every CTA's atomicMax, read (and cleared for the next
+        // launch) at L2, past any stale L1 line
+        const double v = (double)__uint_as_float(atomicExch(c.rbits + p, 0u));
+        c.res_pixels += (long long)J.p[p].width * J.p[p].height;
+        if (first) {
+            c.rn[p] = v;
+            c.rate[p] = (double)c.omega[p] - 1.0;
+            continue;
+        }
+        // (single precision: the plan needs a few digits, and one thread's
+        // chain of double-precision pow/log would sit on every cycle's tail)
+        const float q = (float)(v / fmax(c.rn[p], 1e-30));
+        c.rn[p] = v;
+        const int S = c.nl[p] * c.spl;
+        c.sweeps[p] += S;
+        c.sweeps_max = max(c.sweeps_max, c.sweeps[p]);
+        c.upar[p] ^= 1;  // the launch wrote u + e to the other buffer
+        if (q > 1e-4f && q < 1.f) {
+            const float ro = powf(q, 1.f / (float)S);
+            const float om = c.omega[p];
+            if (ro > (float)c.rate[p] + 0.01f) {
+                const float mu = (ro + om - 1.f) / (om * sqrtf(ro));
+                if (mu < 1.f) {
+                    const float on = 2.f / (1.f + sqrtf(1.f - mu * mu));
+                    c.omega[p] = fminf(1.98f, fmaxf(om, on));
+                }
+                c.rate[p] = fmaxf(c.omega[p] - 1.f, fminf(ro, 0.995f));
+                if (c.omega[p] > om) c.rate[p] = c.omega[p] - 1.f;
+            }
+        }
+    }
+    c.res_launches += 1;
+    if (!first) c.cycles += 1;
+    int maxl = 0;
+    bool conv = true;
+    for (int p = 0; p < J.n; ++p) {
+        c.nl[p] = 0;
+        conv = conv && c.rn[p] <= c.tol;
+        if (!(c.rn[p] > c.tol)) continue;
+        const float target = fmaxf(1e-5f, (float)(0.3 * c.tol / c.rn[p]));
+        const float rt = fminf(fmaxf((float)c.rate[p], 0.05f), 0.995f);
+        int sw = (int)ceilf(logf(target) / logf(rt));
+        sw = min(max(sw, c.spl), 600);
+        c.nl[p] = (sw + c.spl - 1) / c.spl;
+        maxl = max(maxl, c.nl[p]);
+    }
+    c.maxl = maxl;
+    c.iter = 0;
+    c.converged = conv ? 1 : 0;
+    const int go = (maxl > 0 && c.cycles < c.max_cycles) ? 1 : 0;
+    c.go_outer = go;
+    if (!go && !conv) c.unconverged += 1;
+    if (go) {  // the next cycle's sweep launches (in pairs) and the pixels they sweep
+        c.sor_launches += 2 * ((maxl + 1) / 2);
+        for (int p = 0; p < J.n; ++p) c.sor_pixels += (long long)c.nl[p] * J.p[p].width * J.p[p].height;
+    }
+    if (J.h_outer) cudaGraphSetConditional(J.h_outer, go);
+    // the sweep loop of the next cycle starts open (the last sweep launch of
+    // this cycle closed it): a cycle always has at least one launch
+    if (J.h_inner) cudaGraphSetConditional(J.h_inner, go);
+}
+
+// The control state of a new solve (one thread).
+__global__ void intra_ctl_init_kernel(IntraCtl *c, float om0, float om1, float om2, double tol, int max_cycles,
+                                      int spl)
+{
+    IntraCtl z{};
+    z.sor_launches = c->sor_launches;  // the statistics run on until the sync
+    z.sor_pixels = c->sor_pixels;
+    z.res_launches = c->res_launches;
+    z.res_pixels = c->res_pixels;
+    z.unconverged = c->unconverged;
+    z.tol = tol;
+    z.max_cycles = max_cycles;
+    z.spl = spl;
+    z.omega[0] = om0;
+    z.omega[1] = om1;
+    z.omega[2] = om2;
+    *c = z;
+}
+
 // u_out = u_in + e (unknown pixels; float-float), res = (L u_out)_i, and the
-// max |res| per plane.  A 64 x 16 tile with a one-pixel halo is updated once
-// per cell into shared memory; the residual reads the updated neighbours
-// from there.
-__global__ void __launch_bounds__(kResThreads) intra_residual_kernel(const __grid_constant__ IntraJobs J, int e_in,
-                                                                     int add_e)
+// max |res| per plane; first: res = (L u)_i of the starting iterate.  A 64 x
+// 16 tile with a one-pixel halo is updated once per cell into shared
+// memory; the residual reads the updated neighbours from there.  Planes
+// that the plan leaves out this cycle (converged) are skipped.  The
+// launch's last CTA plans the next cycle.
+__global__ void __launch_bounds__(kResThreads) intra_residual_kernel(const __grid_constant__ IntraJobs J, int first)
 {
     __shared__ float sh[kRTH + 2][kRTW + 2], sl[kRTH + 2][kRTW + 2];
     __shared__ float red[kResThreads / 32];
-    const IntraPlane &P = J.p[find_plane(J, blockIdx.x)];
-    const int lt = blockIdx.x - P.tile_base;
-    const int x0 = (lt % P.tiles_x) * kRTW, y0 = (lt / P.tiles_x) * kRTH;
-    const int W = P.width, H = P.height, pitch = P.pitch;
-    const float *uh = P.uh[0], *ul = P.ul[0];
-    const float *e = P.e[e_in];
-    const bool ff = P.ff != 0;
-    for (int k = threadIdx.x; k < (kRTH + 2) * (kRTW + 2); k += kResThreads) {
-        const int ly = k / (kRTW + 2), lx = k - ly * (kRTW + 2);
-        const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
-        float h = 0.f, l = 0.f;
-        if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-            const int i = gy * pitch + gx;
-            h = uh[i];
-            l = ff ? ul[i] : 0.f;
-            if (add_e) {
-                const float d = e[i];  // zero on the mask
-                if (ff) ff_add(h, l, d, h, l);
-                else h = __fadd_rn(h, d);
-                if (lx >= 1 && lx <= kRTW && ly >= 1 && ly <= kRTH) {
-                    P.uh[1][i] = h;
-                    if (ff) P.ul[1][i] = l;
+    __shared__ int s_last;
+    IntraCtl *c = J.ctl;
+    int lt;
+    const int pl = active_region(J, c, first, true, blockIdx.x, lt);
+    const bool add_e = !first;
+    if (pl >= 0) {
+        const IntraPlane &P = J.p[pl];
+        const int x0 = (lt % P.tiles_x) * kRTW, y0 = (lt / P.tiles_x) * kRTH;
+        const int W = P.width, H = P.height, pitch = P.pitch;
+        const int up = c->upar[pl];
+        const float *uh = P.uh[up], *ul = P.ul[up];
+        float *uh_out = P.uh[up ^ 1], *ul_out = P.ul[up ^ 1];
+        const float *e = P.e[c->nl[pl] & 1];  // after the cycle's nl launches
+        const bool ff = P.ff != 0;
+        for (int k = threadIdx.x; k < (kRTH + 2) * (kRTW + 2); k += kResThreads) {
+            const int ly = k / (kRTW + 2), lx = k - ly * (kRTW + 2);
+            const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+            float h = 0.f, l = 0.f;
+            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+                const int i = gy * pitch + gx;
+                h = uh[i];
+                l = ff ? ul[i] : 0.f;
+                if (add_e) {
+                    const float d = e[i];  // zero on the mask
+                    if (ff) ff_add(h, l, d, h, l);
+                    else h = __fadd_rn(h, d);
+                    if (lx >= 1 && lx <= kRTW && ly >= 1 && ly <= kRTH) {
+                        uh_out[i] = h;
+                        if (ff) ul_out[i] = l;
+                    }
                 }
             }
+            sh[ly][lx] = h;
+            sl[ly][lx] = l;
         }
-        sh[ly][lx] = h;
-        sl[ly][lx] = l;
-    }
-    __syncthreads();
-    float rmax = 0.f;
-    for (int k = threadIdx.x; k < kRTH * kRTW; k += kResThreads) {
-        const int ly = k / kRTW, lx = k - ly * kRTW;
-        const int gx = x0 + lx, gy = y0 + ly;
-        if (gx >= W || gy >= H) continue;
-        const int i = gy * pitch + gx;
-        float r = 0.f;
-        if (!P.mask[i]) {
-            // sum_j (h_j - h_i) exactly as float-float, plus the lo parts
-            const float ch = sh[ly + 1][lx + 1], cl = sl[ly + 1][lx + 1];
-            float S = 0.f, E = 0.f, tail = 0.f;
-            auto acc = [&](int yy, int xx) {
-                float d, de, s2, e2;
-                two_sum(sh[yy][xx], -ch, d, de);
-                two_sum(S, d, s2, e2);
-                S = s2;
-                E = __fadd_rn(E, __fadd_rn(e2, de));
-                tail = __fadd_rn(tail, __fsub_rn(sl[yy][xx], cl));
-            };
-            if (gx > 0) acc(ly + 1, lx);
-            if (gx < W - 1) acc(ly + 1, lx + 2);
-            if (gy > 0) acc(ly, lx + 1);
-            if (gy < H - 1) acc(ly + 2, lx + 1);
-            r = __fadd_rn(S, __fadd_rn(E, tail));
+        __syncthreads();
+        float rmax = 0.f;
+        for (int k = threadIdx.x; k < kRTH * kRTW; k += kResThreads) {
+            const int ly = k / kRTW, lx = k - ly * kRTW;
+            const int gx = x0 + lx, gy = y0 + ly;
+            if (gx >= W || gy >= H) continue;
+            const int i = gy * pitch + gx;
+            float r = 0.f;
+            if (!P.mask[i]) {
+                // sum_j (h_j - h_i) exactly as float-float, plus the lo parts
+                const float ch = sh[ly + 1][lx + 1], cl = sl[ly + 1][lx + 1];
+                float S = 0.f, E = 0.f, tail = 0.f;
+                auto acc = [&](int yy, int xx) {
+                    float d, de, s2, e2;
+                    two_sum(sh[yy][xx], -ch, d, de);
+                    two_sum(S, d, s2, e2);
+                    S = s2;
+                    E = __fadd_rn(E, __fadd_rn(e2, de));
+                    tail = __fadd_rn(tail, __fsub_rn(sl[yy][xx], cl));
+                };
+                if (gx > 0) acc(ly + 1, lx);
+                if (gx < W - 1) acc(ly + 1, lx + 2);
+                if (gy > 0) acc(ly, lx + 1);
+                if (gy < H - 1) acc(ly + 2, lx + 1);
+                r = __fadd_rn(S, __fadd_rn(E, tail));
+            }
+            P.res[i] = r;
+            rmax = fmaxf(rmax, fabsf(r));
         }
-        P.res[i] = r;
-        rmax = fmaxf(rmax, fabsf(r));
+        for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rmax;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float m = 0.f;
+            for (int w = 0; w < kResThreads / 32; ++w) m = fmaxf(m, red[w]);
+            if (m > 0.f) atomicMax(c->rbits + pl, __float_as_uint(m));  // non-negative floats order like their bits
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rmax;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float m = 0.f;
-        for (int w = 0; w < kResThreads / 32; ++w) m = fmaxf(m, red[w]);
-        if (m > 0.f) atomicMax(P.rnorm, __float_as_uint(m));  // non-negative floats order like their bits
-    }
+    if (!last_cta(c, &s_last)) return;
+    if (threadIdx.x == 0) plan_cycle(J, *c, first != 0);
 }
 
 // S red-black SOR sweeps on (-L_UU) e = res in a shared-memory tile.
@@ -210,35 +356,30 @@ __global__ void __launch_bounds__(kResThreads) intra_residual_kernel(const __gri
 // exactness shrinks by one ring per half sweep anyway, and the 2S half
 // sweeps leave the interior, kHL = 2S rings in, exact.  Tile corners are
 // even (kTX, kTY, kHL even), so a cell's colour is known at compile time.
-template <int RW, bool FROM_ZERO>
-__global__ void __launch_bounds__(RW / 2 * kTY_THREADS, 1) intra_sor_kernel(const __grid_constant__ IntraJobs J, int e_in)
+// Launch it = 2 iter + PAR of the cycle: sweeps from e[PAR] (from zero at
+// it = 0) into e[PAR ^ 1].  The control words (iter, the plane's launch
+// count, omega) are read beside the region's data loads, which do not
+// depend on them; a plane without this launch returns false before it
+// writes anything.
+template <int RW, int PAR>
+__device__ __forceinline__ bool sor_body(const IntraPlane &P, int pl, int lt, const IntraCtl *c)
 {
     constexpr int HW = RW / 2, TX = sor_tx(RW);  // cells per colour and row; output columns
     static_assert(TX % 2 == 0 && kTY % 2 == 0 && kHL % 2 == 0, "tiles start on even cells");
     extern __shared__ float sor_smem[];
     auto E = reinterpret_cast<float(*)[kRH + 2][HW + 2]>(sor_smem);
-    const IntraPlane &P = J.p[find_plane(J, blockIdx.x)];
-    const int lt = blockIdx.x - P.tile_base;
+    const int it = 2 * c->iter + PAR, nlp = c->nl[pl];
+    const float omega = c->omega[pl];
     const int tx0 = (lt % P.tiles_x) * TX, ty0 = (lt / P.tiles_x) * kTY;
     const int gx0 = tx0 - kHL, gy0 = ty0 - kHL;
     const int W = P.width, H = P.height, pitch = P.pitch;
     const int hx = threadIdx.x, ty = threadIdx.y, ly0 = ty * kRows;
-    const float *ein = P.e[e_in];
-    // the border of the colour arrays: finite values
-    for (int k = hx + ty * HW; k < 2 * (kRH + 2); k += HW * kTY_THREADS) {
-        E[k & 1][k >> 1][0] = 0.f;
-        E[k & 1][k >> 1][HW + 1] = 0.f;
-    }
-    for (int k = hx + ty * HW; k < 2 * (HW + 2); k += HW * kTY_THREADS) {
-        E[k & 1][0][k >> 1] = 0.f;
-        E[k & 1][kRH + 1][k >> 1] = 0.f;
-    }
-    float *eout = P.e[e_in ^ 1];
+    const float *ein = P.e[PAR];
+    float *eout = P.e[PAR ^ 1];
     // The pair starts at an even column (tx0 and the halo are even), so its
     // two cells are read as one 2-element vector.
     const int gxp = gx0 + 2 * hx;
     const bool in0 = gxp >= 0 && gxp < W, in1 = gxp >= 0 && gxp + 1 < W;
-    const float omega = P.omega, omc = 1.f - omega;
     // ec[k][c]: value of the thread's colour-c cell in row ly0 + k, which
     // sits at column 2 hx + ((c + k) & 1); wi = omega / n and wr = omega r / n
     // for unknown cells, 0 for fixed ones (whose value is 0 and stays 0)
@@ -246,6 +387,8 @@ __global__ void __launch_bounds__(RW / 2 * kTY_THREADS, 1) intra_sor_kernel(cons
     // A region with every cell inside the image and off its border (all
     // cells have four neighbours): plain loads, n = 4.
     const bool interior = gx0 >= 1 && gy0 >= 1 && gx0 + RW <= W - 1 && gy0 + kRH <= H - 1;
+    bool fz = false;
+    float omc = 0.f;
     if (interior) {
         const size_t i0 = (size_t)(gy0 + ly0) * pitch + gxp;
         uint32_t m2[kRows];
@@ -255,8 +398,11 @@ __global__ void __launch_bounds__(RW / 2 * kTY_THREADS, 1) intra_sor_kernel(cons
             const size_t i = i0 + (size_t)k * pitch;
             m2[k] = __ldg(reinterpret_cast<const unsigned short *>(P.mask + i));
             r2[k] = __ldg(reinterpret_cast<const float2 *>(P.res + i));
-            if (!FROM_ZERO) e2[k] = __ldg(reinterpret_cast<const float2 *>(ein + i));
+            e2[k] = __ldg(reinterpret_cast<const float2 *>(ein + i));
         }
+        if (it >= nlp) return false;
+        fz = it == 0;
+        omc = 1.f - omega;
         const float w4 = 0.25f * omega;
 #pragma unroll
         for (int k = 0; k < kRows; ++k) {
@@ -266,7 +412,7 @@ __global__ void __launch_bounds__(RW / 2 * kTY_THREADS, 1) intra_sor_kernel(cons
                 const bool unk = ((m2[k] >> (8 * b)) & 0xffu) == 0;
                 iv[b] = unk ? w4 : 0.f;
                 rv[b] = (b ? r2[k].y : r2[k].x) * iv[b];
-                ev[b] = (FROM_ZERO || !unk) ? 0.f : (b ? e2[k].y : e2[k].x);
+                ev[b] = (fz || !unk) ? 0.f : (b ? e2[k].y : e2[k].x);
             }
             const int sw = k & 1;  // 1: the pair's left cell has colour 1 (ly0 is even)
             ec[k][0] = ev[sw];
@@ -289,8 +435,11 @@ __global__ void __launch_bounds__(RW / 2 * kTY_THREADS, 1) intra_sor_kernel(cons
             const size_t i = (size_t)gy * pitch + gxc;
             m2[k] = __ldg(reinterpret_cast<const unsigned short *>(P.mask + i));
             r2[k] = __ldg(reinterpret_cast<const float2 *>(P.res + i));
-            if (!FROM_ZERO) e2[k] = __ldg(reinterpret_cast<const float2 *>(ein + i));
+            e2[k] = __ldg(reinterpret_cast<const float2 *>(ein + i));
         }
+        if (it >= nlp) return false;
+        fz = it == 0;
+        omc = 1.f - omega;
 #pragma unroll
         for (int k = 0; k < kRows; ++k) {
             const int gy = gy0 + ly0 + k;
@@ -305,7 +454,7 @@ __global__ void __launch_bounds__(RW / 2 * kTY_THREADS, 1) intra_sor_kernel(cons
                 const float inv = n == 4 ? 0.25f : (n == 3 ? (1.0f / 3.0f) : (n == 2 ? 0.5f : 1.0f));
                 iv[b] = unk ? omega * inv : 0.f;
                 rv[b] = unk ? (b ? r2[k].y : r2[k].x) * iv[b] : 0.f;
-                ev[b] = (FROM_ZERO || !unk) ? 0.f : (b ? e2[k].y : e2[k].x);
+                ev[b] = (fz || !unk) ? 0.f : (b ? e2[k].y : e2[k].x);
             }
             const int sw = k & 1;
             ec[k][0] = ev[sw];
@@ -315,6 +464,15 @@ __global__ void __launch_bounds__(RW / 2 * kTY_THREADS, 1) intra_sor_kernel(cons
             wr[k][0] = rv[sw];
             wr[k][1] = rv[sw ^ 1];
         }
+    }
+    // the border of the colour arrays: finite values
+    for (int k = hx + ty * HW; k < 2 * (kRH + 2); k += HW * kTY_THREADS) {
+        E[k & 1][k >> 1][0] = 0.f;
+        E[k & 1][k >> 1][HW + 1] = 0.f;
+    }
+    for (int k = hx + ty * HW; k < 2 * (HW + 2); k += HW * kTY_THREADS) {
+        E[k & 1][0][k >> 1] = 0.f;
+        E[k & 1][kRH + 1][k >> 1] = 0.f;
     }
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
@@ -341,7 +499,7 @@ __global__ void __launch_bounds__(RW / 2 * kTY_THREADS, 1) intra_sor_kernel(cons
     // interior pairs are whole pairs (even halo and width); a pair that
     // straddles an odd right edge writes its left cell only
     const int lx = 2 * hx;
-    if (lx < kHL || lx >= kHL + TX || gxp >= W) return;
+    if (lx < kHL || lx >= kHL + TX || gxp >= W) return true;
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
         const int ly = ly0 + k, gy = gy0 + ly;
@@ -352,6 +510,7 @@ __global__ void __launch_bounds__(RW / 2 * kTY_THREADS, 1) intra_sor_kernel(cons
         if (in1) *reinterpret_cast<float2 *>(o) = make_float2(v0, v1);
         else o[0] = v0;
     }
+    return true;
 }
 
 // The same sweeps with four columns per thread: a warp spans the region's
@@ -365,21 +524,21 @@ __global__ void __launch_bounds__(RW / 2 * kTY_THREADS, 1) intra_sor_kernel(cons
 constexpr int kQWarps = kRH / kRows;  // 16 row groups of 8 rows
 constexpr int kQCols = 128;           // region columns, 4 per lane
 
-template <bool FROM_ZERO>
-__global__ void __launch_bounds__(32 * kQWarps, 1) intra_sor4_kernel(const __grid_constant__ IntraJobs J, int e_in)
+// (launch parity, control words and the early return as in sor_body)
+template <int PAR>
+__device__ __forceinline__ bool sor4_body(const IntraPlane &P, int pl, int lt, const IntraCtl *c)
 {
     constexpr int TX = sor_tx(kQCols);
     __shared__ float rows[kQWarps][2][kQCols];  // each warp's first and last row
-    const IntraPlane &P = J.p[find_plane(J, blockIdx.x)];
-    const int lt = blockIdx.x - P.tile_base;
+    const int it = 2 * c->iter + PAR, nlp = c->nl[pl];
+    const float omega = c->omega[pl];
     const int tx0 = (lt % P.tiles_x) * TX, ty0 = (lt / P.tiles_x) * kTY;
     const int gx0 = tx0 - kHL, gy0 = ty0 - kHL;
     const int W = P.width, H = P.height, pitch = P.pitch;
     const int lane = threadIdx.x, wq = threadIdx.y, ly0 = wq * kRows;
-    const float *ein = P.e[e_in];
-    float *eout = P.e[e_in ^ 1];
+    const float *ein = P.e[PAR];
+    float *eout = P.e[PAR ^ 1];
     const int gxq = gx0 + 4 * lane;  // a multiple of 4: the quad is one 16-byte vector
-    const float omega = P.omega, omc = 1.f - omega;
     // e[k][j], wi[k][j], wr[k][j]: the cell in row ly0 + k, column 4 lane + j
     float e[kRows][4], wi[kRows][4], wr[kRows][4];
     const bool interior = gx0 >= 1 && gy0 >= 1 && gx0 + kQCols <= W - 1 && gy0 + kRH <= H - 1;
@@ -392,8 +551,11 @@ __global__ void __launch_bounds__(32 * kQWarps, 1) intra_sor4_kernel(const __gri
         const size_t i = (size_t)gy * pitch + (interior ? gxq : gxc);
         m4[k] = __ldg(reinterpret_cast<const unsigned int *>(P.mask + i));
         r4[k] = __ldg(reinterpret_cast<const float4 *>(P.res + i));
-        if (!FROM_ZERO) e4[k] = __ldg(reinterpret_cast<const float4 *>(ein + i));
+        e4[k] = __ldg(reinterpret_cast<const float4 *>(ein + i));
     }
+    if (it >= nlp) return false;
+    const bool fz = it == 0;
+    const float omc = 1.f - omega;
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
         const int gy = gy0 + ly0 + k;
@@ -401,7 +563,7 @@ __global__ void __launch_bounds__(32 * kQWarps, 1) intra_sor4_kernel(const __gri
         const int ny = (gy > 0) + (gy < H - 1);
         const float rr[4] = {r4[k].x, r4[k].y, r4[k].z, r4[k].w};
         float ee[4] = {0.f, 0.f, 0.f, 0.f};
-        if (!FROM_ZERO) {
+        if (!fz) {
             ee[0] = e4[k].x;
             ee[1] = e4[k].y;
             ee[2] = e4[k].z;
@@ -423,7 +585,7 @@ __global__ void __launch_bounds__(32 * kQWarps, 1) intra_sor4_kernel(const __gri
             }
             wi[k][j] = iv;
             wr[k][j] = unk ? rr[j] * iv : 0.f;
-            e[k][j] = (FROM_ZERO || !unk) ? 0.f : ee[j];
+            e[k][j] = (fz || !unk) ? 0.f : ee[j];
         }
     }
 #pragma unroll
@@ -468,7 +630,7 @@ __global__ void __launch_bounds__(32 * kQWarps, 1) intra_sor4_kernel(const __gri
     }
     // interior quads: columns kHL .. kHL + TX - 1 of the region
     const int lx = 4 * lane;
-    if (lx < kHL || lx >= kHL + TX || gxq >= W) return;
+    if (lx < kHL || lx >= kHL + TX || gxq >= W) return true;
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
         const int ly = ly0 + k, gy = gy0 + ly;
@@ -482,6 +644,58 @@ __global__ void __launch_bounds__(32 * kQWarps, 1) intra_sor4_kernel(const __gri
                 if (gxq + j < W) o[j] = e[k][j];
         }
     }
+    return true;
+}
+
+// The plane and region of CTA b of a sweep launch: a static mapping (the
+// launcher orders the chroma planes first, since they sweep longest), so a
+// CTA addresses its data before the control words arrive.
+__device__ __forceinline__ int sweep_plane(const IntraJobs &J, int b, int &lt)
+{
+    for (int p = 0; p < J.n; ++p)
+        if (b >= J.p[p].tile_base && b < J.p[p].tile_base + J.p[p].tiles) {
+            lt = b - J.p[p].tile_base;
+            return p;
+        }
+    lt = 0;
+    return 0;
+}
+
+// After the second launch of a pair (its last CTA): the pair count
+// advances, and the sweep loop goes on while the cycle has launches left.
+__device__ __forceinline__ void pair_done(const IntraJobs &J, int *s_last)
+{
+    IntraCtl *c = J.ctl;
+    if (!last_cta(c, s_last)) return;
+    if (threadIdx.x != 0 || threadIdx.y != 0) return;
+    const int iter = c->iter + 1;
+    c->iter = iter;
+    const int go = 2 * iter < c->maxl ? 1 : 0;
+    c->go_inner = go;
+    if (J.h_inner) cudaGraphSetConditional(J.h_inner, go);
+}
+
+// S red-black sweeps of launch it = 2 iter + PAR of the cycle, over the
+// planes whose launch count exceeds it (from e = 0 at it = 0, else from
+// the plane's current correction in e[PAR]).
+template <int RW, int PAR>
+__global__ void __launch_bounds__(RW / 2 * kTY_THREADS, 1) intra_sor_kernel(const __grid_constant__ IntraJobs J)
+{
+    __shared__ int s_last;
+    int lt;
+    const int pl = sweep_plane(J, blockIdx.x, lt);
+    sor_body<RW, PAR>(J.p[pl], pl, lt, J.ctl);
+    if (PAR) pair_done(J, &s_last);
+}
+
+template <int PAR>
+__global__ void __launch_bounds__(32 * kQWarps, 1) intra_sor4_kernel(const __grid_constant__ IntraJobs J)
+{
+    __shared__ int s_last;
+    int lt;
+    const int pl = sweep_plane(J, blockIdx.x, lt);
+    sor4_body<PAR>(J.p[pl], pl, lt, J.ctl);
+    if (PAR) pair_done(J, &s_last);
 }
 
 }  // namespace
@@ -499,68 +713,96 @@ cudaError_t launch_intra_init(IntraJobs &J, uint32_t *flags, cudaStream_t st, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_intra_residual(IntraJobs &J, int e_in, bool add_e, cudaStream_t st)
+cudaError_t launch_intra_ctl_init(const IntraJobs &J, const float *omega0, double tol, int max_cycles,
+                                  cudaStream_t st)
 {
-    int base = 0;
-    for (int k = 0; k < J.n; ++k) {
-        IntraPlane &P = J.p[k];
-        cudaError_t e = cudaMemsetAsync(P.rnorm, 0, sizeof(unsigned int), st);
-        if (e != cudaSuccess) return e;
-        P.tiles_x = (P.width + kRTW - 1) / kRTW;
-        P.tile_base = base;
-        base += P.tiles_x * ((P.height + kRTH - 1) / kRTH);
-    }
-    if (base == 0) return cudaSuccess;
-    intra_residual_kernel<<<base, kResThreads, 0, st>>>(J, e_in, add_e ? 1 : 0);
+    intra_ctl_init_kernel<<<1, 1, 0, st>>>(J.ctl, omega0[0], J.n > 1 ? omega0[1] : 1.f, J.n > 2 ? omega0[2] : 1.f,
+                                            tol, max_cycles, kS);
     return cudaGetLastError();
 }
 
 namespace {
 
-template <int RW>
-void sor_launch(IntraJobs &J, int cur, bool from_zero, cudaStream_t st)
+// residual tiles of 64 x 16 per plane
+int residual_tiles(IntraJobs &J)
 {
     int base = 0;
     for (int k = 0; k < J.n; ++k) {
         IntraPlane &P = J.p[k];
-        P.tiles_x = (P.width + sor_tx(RW) - 1) / sor_tx(RW);
+        P.tiles_x = (P.width + kRTW - 1) / kRTW;
         P.tile_base = base;
-        base += P.tiles_x * ((P.height + kTY - 1) / kTY);
+        P.tiles = P.tiles_x * ((P.height + kRTH - 1) / kRTH);
+        base += P.tiles;
     }
-    const dim3 block(RW / 2, kTY_THREADS);
-    if (from_zero) intra_sor_kernel<RW, true><<<base, block, sor_smem_bytes(RW), st>>>(J, cur);
-    else intra_sor_kernel<RW, false><<<base, block, sor_smem_bytes(RW), st>>>(J, cur);
+    return base;
 }
 
-void sor_launch_quads(IntraJobs &J, int cur, bool from_zero, cudaStream_t st)
+// sweep regions of the variant per plane; returns the CTAs, sets the block
+// and the dynamic shared memory
+int sor_tiles(IntraJobs &J, int variant, dim3 &block, size_t &smem)
 {
+    const int tx = variant == 1 ? sor_tx(112) : sor_tx(128);
     int base = 0;
-    for (int k = 0; k < J.n; ++k) {
-        IntraPlane &P = J.p[k];
-        P.tiles_x = (P.width + sor_tx(kQCols) - 1) / sor_tx(kQCols);
+    // chroma planes first: they sweep longest, so the launches that sweep
+    // them alone find their CTAs at the front of the grid
+    for (int q = 0; q < J.n; ++q) {
+        IntraPlane &P = J.p[J.n == 3 ? (q + 1) % 3 : q];
+        P.tiles_x = (P.width + tx - 1) / tx;
         P.tile_base = base;
-        base += P.tiles_x * ((P.height + kTY - 1) / kTY);
+        P.tiles = P.tiles_x * ((P.height + kTY - 1) / kTY);
+        base += P.tiles;
     }
-    const dim3 block(32, kQWarps);
-    if (from_zero) intra_sor4_kernel<true><<<base, block, 0, st>>>(J, cur);
-    else intra_sor4_kernel<false><<<base, block, 0, st>>>(J, cur);
+    block = variant == 2 ? dim3(32, kQWarps) : dim3((variant == 1 ? 112 : 128) / 2, kTY_THREADS);
+    smem = variant == 2 ? 0 : sor_smem_bytes(variant == 1 ? 112 : 128);
+    return base;
 }
 
-// variant 0: 128-column regions, a cell pair per thread; 1: 112 columns;
-// 2: 128 columns, four cells per thread
-void sor_launch_rw(int variant, IntraJobs &J, int cur, bool from_zero, cudaStream_t st)
+const void *sor_kernel(int variant, int par)
 {
-    if (variant == 1) sor_launch<112>(J, cur, from_zero, st);
-    else if (variant == 2) sor_launch_quads(J, cur, from_zero, st);
-    else sor_launch<128>(J, cur, from_zero, st);
+    if (variant == 1)
+        return par ? reinterpret_cast<const void *>(intra_sor_kernel<112, 1>)
+                   : reinterpret_cast<const void *>(intra_sor_kernel<112, 0>);
+    if (variant == 2)
+        return par ? reinterpret_cast<const void *>(intra_sor4_kernel<1>)
+                   : reinterpret_cast<const void *>(intra_sor4_kernel<0>);
+    return par ? reinterpret_cast<const void *>(intra_sor_kernel<128, 1>)
+               : reinterpret_cast<const void *>(intra_sor_kernel<128, 0>);
 }
+
+}  // namespace
+
+cudaError_t launch_intra_residual(IntraJobs &J, bool first, cudaStream_t st)
+{
+    const int n = residual_tiles(J);
+    if (n == 0) return cudaSuccess;
+    intra_residual_kernel<<<n, kResThreads, 0, st>>>(J, first ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_intra_sor_pair(IntraJobs &J, int variant, cudaStream_t st)
+{
+    dim3 block;
+    size_t smem;
+    const int n = sor_tiles(J, variant, block, smem);
+    if (n == 0) return cudaSuccess;
+    void *args[] = {&J};
+    cudaError_t e = cudaLaunchKernel(sor_kernel(variant, 0), dim3(n), block, args, smem, st);
+    if (e == cudaSuccess) e = cudaLaunchKernel(sor_kernel(variant, 1), dim3(n), block, args, smem, st);
+    return e;
+}
+
+namespace {
 
 // Tiling autotuner.  The variants perform exactly the same global
 // red-black sweeps (a cell's neighbour sum is formed in the same order), so
-// the choice changes speed only.  The first call with enough launches for
-// a set of plane sizes on a device times each variant on its own launches
-// (real sweeps of the solve, two groups of three each, round robin) and
-// keeps another variant than the first only if it is at least 2 % faster.
+// the choice changes speed only.  The first solve of a set of plane sizes
+// on a device times each variant, twice over groups of three launches
+// (round robin), on a control state of its own (every plane active, from
+// the current correction: the sweeps work on the decoder's buffers before
+// the solve starts, which overwrites them), and keeps another variant than
+// the first only if it is at least 2 % faster.  The choice goes to the
+// tuner's table under the GPU's name and the plane sizes, so later
+// processes on the same kind of GPU start with it.
 constexpr int kSorVariants = 3;
 std::mutex g_tune_mu;
 std::map<std::vector<int>, int> g_tuned;
@@ -577,68 +819,152 @@ std::vector<int> tune_key(const IntraJobs &J)
     return k;
 }
 
+// "<gpu>|sor|WxH,WxH,..." in the tuner's table
+std::string table_key(const IntraJobs &J)
+{
+    std::string k = gpu_name() + "|sor|";
+    for (int i = 0; i < J.n; ++i) k += (i ? "," : "") + std::to_string(J.p[i].width) + "x" + std::to_string(J.p[i].height);
+    return k;
+}
+
+// a tuning control state: every plane active for as many launches as the
+// timing needs, from the current correction (launches from it = 2 on)
+__global__ void intra_tune_ctl_kernel(IntraCtl *c)
+{
+    IntraCtl z{};
+    for (int p = 0; p < 3; ++p) {
+        z.nl[p] = 1 << 20;
+        z.omega[p] = 1.5f;
+    }
+    z.maxl = 1 << 20;
+    z.iter = 1;
+    *c = z;
+}
+
 }  // namespace
 
 std::atomic<int> g_forced{-1};  // a variant pinned by the caller, or -1
 
-// the tuned SOR variant for these planes, or -1 before tuning
-int sor_variant(const IntraJobs &J)
+int intra_sor_variant(IntraJobs &J, IntraCtl *tune_ctl, cudaStream_t st)
 {
     const int f = g_forced.load(std::memory_order_relaxed);
     if (f >= 0) return f;
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_tuned.find(tune_key(J));
-    return it == g_tuned.end() ? -1 : it->second;
+    const std::vector<int> key = tune_key(J);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) return it->second;
+        const int v = tune_lookup(table_key(J));
+        if (v >= 0 && v < kSorVariants) {
+            g_tuned[key] = v;
+            return v;
+        }
+    }
+    IntraJobs T = J;
+    T.ctl = tune_ctl;
+    T.h_outer = T.h_inner = 0;
+    constexpr int kTuneGroup = 3, kTuneRounds = 2, kEv = kTuneRounds * kSorVariants + 1;
+    cudaEvent_t ev[kEv];
+    int made = 0;
+    cudaError_t e = cudaSuccess;
+    for (; made < kEv && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
+    if (e == cudaSuccess) {
+        intra_tune_ctl_kernel<<<1, 1, 0, st>>>(tune_ctl);
+        e = cudaEventRecord(ev[0], st);
+    }
+    for (int t = 0; t < kEv - 1 && e == cudaSuccess; ++t) {
+        for (int g = 0; g < kTuneGroup && e == cudaSuccess; ++g) e = launch_intra_sor_pair(T, t % kSorVariants, st);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[t + 1], st);
+    }
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[kEv - 1]);
+    float best[kSorVariants] = {1e30f, 1e30f, 1e30f};
+    for (int t = 0; t < kEv - 1 && e == cudaSuccess; ++t) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, ev[t], ev[t + 1]);
+        best[t % kSorVariants] = std::min(best[t % kSorVariants], ms);
+    }
+    for (int i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
+    if (e != cudaSuccess) return 0;
+    int rw = 0;
+    for (int v = 1; v < kSorVariants; ++v)
+        if (best[v] < 0.98f * best[rw]) rw = v;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[key] = rw;
+    }
+    tune_store(table_key(J), rw);
+    return rw;
 }
 
-cudaError_t launch_intra_sor(IntraJobs &J, int e_in, bool from_zero, int sweeps, cudaStream_t st, int *e_out,
-                             int *launches)
+cudaError_t build_intra_graph(const IntraJobs &J0, int variant, cudaGraphExec_t *exec)
 {
-    const int n = (sweeps + kS - 1) / kS;
-    int cur = e_in, l = 0;
-    int rw = sor_variant(J);
-    // untuned: each variant timed twice over kTuneGroup consecutive launches
-    // (round robin), if the call has that many launches
-    constexpr int kTuneGroup = 3, kTuneRounds = 2, kTuneLaunches = kTuneRounds * kSorVariants * kTuneGroup;
-    if (rw < 0 && n >= kTuneLaunches) {
-        constexpr int kEv = kTuneRounds * kSorVariants + 1;
-        cudaEvent_t ev[kEv];
-        int made = 0;
-        cudaError_t e = cudaSuccess;
-        for (; made < kEv && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
-        for (int t = 0; t < kEv - 1 && e == cudaSuccess; ++t) {
-            for (int g = 0; g < kTuneGroup; ++g, ++l) {
-                sor_launch_rw(t % kSorVariants, J, cur, from_zero && l == 0, st);
-                cur ^= 1;
-            }
-            e = cudaGetLastError();
-            if (e == cudaSuccess) e = cudaEventRecord(ev[t + 1], st);
-        }
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev[kEv - 1]);
-        float best[kSorVariants];
-        for (int v = 0; v < kSorVariants; ++v) best[v] = 1e30f;
-        for (int t = 0; t < kEv - 1 && e == cudaSuccess; ++t) {
-            float ms = 0.f;
-            e = cudaEventElapsedTime(&ms, ev[t], ev[t + 1]);
-            best[t % kSorVariants] = std::min(best[t % kSorVariants], ms);
-        }
-        for (int i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
-        if (e != cudaSuccess) return e;
-        rw = 0;
-        for (int v = 1; v < kSorVariants; ++v)
-            if (best[v] < 0.98f * best[rw]) rw = v;
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[tune_key(J)] = rw;
-    }
-    if (rw < 0) rw = 0;
-    for (; l < n; ++l) {
-        sor_launch_rw(rw, J, cur, from_zero && l == 0, st);
-        cur ^= 1;
-    }
-    if (launches) *launches += n;
-    *e_out = cur;
-    return cudaGetLastError();
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return e;
+    IntraJobs J = J0;
+    auto fail = [&](cudaError_t err) {
+        cudaGraphDestroy(g);
+        return err;
+    };
+    // the outer loop's condition starts at 0; the first residual launch
+    // (its last CTA) sets it
+    if ((e = cudaGraphConditionalHandleCreate(&J.h_outer, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return fail(e);
+    cudaGraphNodeParams wp{};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = J.h_outer;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t n_res0, n_outer, n_inner, n_sor, n_res;
+    // first residual
+    IntraJobs R = J;
+    int one = 1, zero = 0;
+    const int nres = residual_tiles(R);
+    cudaKernelNodeParams kp{};
+    kp.func = reinterpret_cast<void *>(intra_residual_kernel);
+    kp.gridDim = dim3(nres);
+    kp.blockDim = dim3(kResThreads);
+    void *a0[] = {&R, &one};
+    kp.kernelParams = a0;
+    if ((e = cudaGraphAddKernelNode(&n_res0, g, nullptr, 0, &kp)) != cudaSuccess) return fail(e);
+    if ((e = cudaGraphAddNode(&n_outer, g, &n_res0, nullptr, 1, &wp)) != cudaSuccess) return fail(e);
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    // the inner loop's condition is 1 at every pass of the outer body (a
+    // cycle has at least one launch); each sweep launch sets it
+    if ((e = cudaGraphConditionalHandleCreate(&J.h_inner, body, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return fail(e);
+    cudaGraphNodeParams ip{};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = J.h_inner;
+    ip.conditional.type = cudaGraphCondTypeWhile;
+    ip.conditional.size = 1;
+    if ((e = cudaGraphAddNode(&n_inner, body, nullptr, nullptr, 0, &ip)) != cudaSuccess) return fail(e);
+    cudaGraph_t inner = ip.conditional.phGraph_out[0];
+    // the loop's body: a pair of sweep launches (parity 0, then 1)
+    IntraJobs S = J;
+    dim3 block;
+    size_t smem;
+    const int nsor = sor_tiles(S, variant, block, smem);
+    cudaKernelNodeParams sp{};
+    sp.gridDim = dim3(nsor);
+    sp.blockDim = block;
+    sp.sharedMemBytes = (unsigned)smem;
+    void *a1[] = {&S};
+    sp.kernelParams = a1;
+    cudaGraphNode_t n_sor0;
+    sp.func = const_cast<void *>(sor_kernel(variant, 0));
+    if ((e = cudaGraphAddKernelNode(&n_sor0, inner, nullptr, 0, &sp)) != cudaSuccess) return fail(e);
+    sp.func = const_cast<void *>(sor_kernel(variant, 1));
+    if ((e = cudaGraphAddKernelNode(&n_sor, inner, &n_sor0, 1, &sp)) != cudaSuccess) return fail(e);
+    // the cycle's residual launch, after the sweeps
+    IntraJobs R2 = J;
+    residual_tiles(R2);
+    void *a2[] = {&R2, &zero};
+    kp.kernelParams = a2;
+    if ((e = cudaGraphAddKernelNode(&n_res, body, &n_inner, 1, &kp)) != cudaSuccess) return fail(e);
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    return e;
 }
 
 int intra_sweeps_per_launch() { return kS; }
@@ -654,18 +980,16 @@ int set_sor_variant(int v)
 // shared memory beyond the static limit.  Called once per device.
 cudaError_t intra_init()
 {
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(intra_sor_kernel<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sor_smem_bytes(128))) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(intra_sor_kernel<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sor_smem_bytes(128))) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(intra_sor_kernel<112, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sor_smem_bytes(112))) != cudaSuccess)
-        return e;
-    return cudaFuncSetAttribute(intra_sor_kernel<112, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sor_smem_bytes(112));
+    const void *k[4] = {reinterpret_cast<const void *>(intra_sor_kernel<128, 0>),
+                        reinterpret_cast<const void *>(intra_sor_kernel<128, 1>),
+                        reinterpret_cast<const void *>(intra_sor_kernel<112, 0>),
+                        reinterpret_cast<const void *>(intra_sor_kernel<112, 1>)};
+    for (int i = 0; i < 4; ++i) {
+        const cudaError_t e = cudaFuncSetAttribute(k[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)sor_smem_bytes(i < 2 ? 128 : 112));
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace hivc

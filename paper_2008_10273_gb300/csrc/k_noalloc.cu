@@ -7,7 +7,8 @@
 // which a cudaMalloc or cudaFree (which may synchronise the whole device)
 // would stall the work of other streams.  For them the scratch that the
 // coefficient stage needs (per-point coefficients, per-block constants and
-// room for one system with more than 32 points per range of 128 blocks)
+// room for one system with more than 32 points per range of 128 blocks, and
+// the work lists of the launch)
 // lives in a fixed-size array in the library's device image instead of a
 // caller workspace.
 //
@@ -28,12 +29,18 @@ namespace {
 constexpr int kStaticMaxPoints = 1 << 17;  // residual points per call
 constexpr int kStaticMaxBlocks = 1 << 14;  // residual blocks per call
 // 4-byte words: coefficients | block constants | own error word (+ padding)
-// | one K > 32 system per range of kRange blocks
+// | one K > 32 system per range of kRange blocks | the launch's plan (work
+// lists by point count, no layout groups)
 constexpr size_t kOffAcoef = kStaticMaxPoints;
 constexpr size_t kOffFlags = kOffAcoef + kStaticMaxBlocks;
 constexpr size_t kOffBig = kOffFlags + 64;  // keeps the systems 256-byte aligned
 constexpr int kStaticRanges = kStaticMaxBlocks / kRange;
-constexpr size_t kWords = kOffBig + (size_t)kStaticRanges * kBigFloats;
+constexpr size_t kOffPlan = kOffBig + (size_t)kStaticRanges * kBigFloats;
+// at least block_plan_bytes(kStaticMaxBlocks, false): the state (under
+// 8 KB), the class lists and the deferred list (checked at run time)
+constexpr size_t kPlanWords = (8192 + 4 * (size_t)kStaticMaxBlocks * (kClasses + 1)) / 4;
+static_assert(sizeof(BlockPlanState) + 256 <= 8192, "plan state fits its share");
+constexpr size_t kWords = kOffPlan + kPlanWords;
 
 static __device__ __align__(256) uint32_t g_scratch[kWords];
 
@@ -90,7 +97,9 @@ extern "C" hivc_status hivc_block_residual_static(int32_t width, int32_t height,
     B.nbx = nbx;
     B.nblocks = (int)nb;
     J.total_blocks = (int)nb;
-    const BlockScratch S{flags, reinterpret_cast<float *>(base + kOffBig), kStaticRanges};
+    if (block_plan_bytes((int)nb, false) > 4 * kPlanWords) return HIVC_E_INVALID;
+    BlockScratch S{flags, reinterpret_cast<float *>(base + kOffBig), kStaticRanges};
+    S.plan = carve_block_plan(base + kOffPlan, (int)nb, false);
     cudaError_t e = launch_block_coef(J, S, st, nullptr);
     if (e == cudaSuccess) e = launch_block_eval(J, flags, st);
     return e == cudaSuccess ? HIVC_OK : HIVC_E_CUDA;

@@ -89,7 +89,9 @@ __global__ void __launch_bounds__(kTW *kTH) warp_add_kernel(const __grid_constan
         pred = sample(P.ref, P.ref_pitch, P.width, P.height, x, y, dx, dy);
     } else {
         const size_t i = (size_t)y * P.src_pitch + x;
-        pred = P.src_lo ? __fadd_rn(P.src_hi[i], P.src_lo[i]) : P.src_hi[i];
+        const bool s1 = P.src_sel && *P.src_sel;  // which buffer of the ping-pong holds the solution
+        const float *hi = s1 ? P.src_hi1 : P.src_hi, *lo = s1 ? P.src_lo1 : P.src_lo;
+        pred = lo ? __fadd_rn(hi[i], lo[i]) : hi[i];
     }
     if (P.pred_out) P.pred_out[(size_t)y * P.pred_pitch + x] = pred;
     float v = pred;
@@ -125,7 +127,11 @@ __global__ void __launch_bounds__(kTW *kTH) rct_kernel(const __grid_constant__ R
         }
     } else {
 #pragma unroll
-        for (int p = 0; p < 3; ++p) pred[p] = F.src_lo[p] ? __fadd_rn(F.src_hi[p][i], F.src_lo[p][i]) : F.src_hi[p][i];
+        for (int p = 0; p < 3; ++p) {
+            const bool s1 = F.src_sel && F.src_sel[p];  // which buffer of the ping-pong holds the solution
+            const float *hi = s1 ? F.src_hi1[p] : F.src_hi[p], *lo = s1 ? F.src_lo1[p] : F.src_lo[p];
+            pred[p] = lo ? __fadd_rn(hi[i], lo[i]) : hi[i];
+        }
     }
     int q[3];
 #pragma unroll

@@ -33,7 +33,7 @@ c_i32, c_u32, c_f64, c_f32, c_vp, c_sz = (ctypes.c_int32, ctypes.c_uint32, ctype
 class Config(ctypes.Structure):
     _fields_ = [("width", c_i32), ("height", c_i32), ("chroma", c_i32), ("block", c_i32),
                 ("op", c_i32), ("precision", c_i32), ("iframe_tol", c_f64), ("max_cycles", c_i32),
-                ("cond_threshold", c_f64), ("stream", c_vp)]
+                ("cond_threshold", c_f64), ("stream", c_vp), ("layout_groups", c_i32)]
 
 
 class Points(ctypes.Structure):
@@ -74,7 +74,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("resid", c_f64 * 3), ("cycles", c_i32), ("sweeps", c_i32), ("fp64_blocks", c_i32),
                 ("large_blocks", c_i32), ("max_cond", c_f32), ("device_flags", c_u32),
                 ("frames", c_i32), ("launches", c_i32), ("kernel_ms", c_f32 * STAT_KERNELS),
-                ("kernel_launches", c_i32 * STAT_KERNELS), ("kernel_pixels", ctypes.c_int64 * STAT_KERNELS)]
+                ("kernel_launches", c_i32 * STAT_KERNELS), ("kernel_pixels", ctypes.c_int64 * STAT_KERNELS),
+                ("group_blocks", c_i32), ("layout_groups", c_i32)]
 
 
 _lib = None
@@ -99,6 +100,8 @@ PROTOTYPES = [
     ("hivc_decoder_intra_solution", c_i32, [c_vp, c_i32, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp),
                                             ctypes.POINTER(c_i32), ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
     ("hivc_decoder_stream", c_vp, [c_vp]),
+    ("hivc_tune_lookup", c_i32, [ctypes.c_char_p]),
+    ("hivc_tune_record", c_i32, [ctypes.c_char_p, c_i32]),
     ("hivc_decoder_destroy", None, [c_vp]),
     ("hivc_status_str", ctypes.c_char_p, [c_i32]),
     ("hivc_block_residual_workspace_bytes", c_sz, [c_i32, c_i32, c_i32, c_i32]),
@@ -207,13 +210,16 @@ class Decoder:
 
     def __init__(self, width: int, height: int, chroma: bool = True, block: int = 16,
                  iframe_tol: float = 1e-8, max_cycles: int = 40, precision: int = 0,
-                 stream=None, timing: bool = False, cond_threshold: float = 1e6, op: int = 0):
+                 stream=None, timing: bool = False, cond_threshold: float = 1e6, op: int = 0,
+                 layout_groups: Optional[bool] = None):
         cfg = config_default()
         # chroma: False/0 grey, True/1 4:2:0, 2 the 4:4:4 RCT colour path
         cfg.width, cfg.height, cfg.chroma, cfg.block = width, height, int(chroma), block
         cfg.iframe_tol, cfg.max_cycles, cfg.precision = iframe_tol, max_cycles, precision
         cfg.cond_threshold = cond_threshold
         cfg.op = op
+        if layout_groups is not None:
+            cfg.layout_groups = int(bool(layout_groups))
         cfg.stream = _stream_handle(stream)
         self.cfg = cfg
         self.width, self.height, self.chroma, self.block = width, height, bool(chroma), block

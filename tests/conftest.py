@@ -1,5 +1,6 @@
 import os
 import sys
+import tempfile
 from fractions import Fraction
 
 import numpy as np
@@ -14,6 +15,8 @@ GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+    # the library's autotuner table: a file of this test session's own
+    os.environ.setdefault("HIVC_TUNE_CACHE", os.path.join(tempfile.gettempdir(), f"hivc_tune_{os.getpid()}.json"))
 
 
 def read_golden(name):

@@ -53,10 +53,10 @@ def test_host_only_entry_points(hv):
     assert L.hivc_block_residual_workspace_bytes(1920, 1080, 16, 70000) > 70000 * 4
     assert L.hivc_block_residual_workspace_bytes(0, 1080, 16, 10) == 0
     # struct layouts the binding relies on
-    assert ctypes.sizeof(hv.Config) == 56
+    assert ctypes.sizeof(hv.Config) == 64
     assert ctypes.sizeof(hv.Residual) == 32
     # hivc_stats: the per-family int64 pixel counts follow the launch counts
-    assert hv.Stats.kernel_pixels.offset == 120 and ctypes.sizeof(hv.Stats) == 184
+    assert hv.Stats.kernel_pixels.offset == 120 and ctypes.sizeof(hv.Stats) == 192
 
 
 def test_oracle_is_not_reachable_from_the_product():
