@@ -95,6 +95,13 @@ typedef struct {
                                block on its own (the grouping pass costs
                                more than it saves unless many blocks share
                                few layouts) */
+    int32_t batch_frames;   /* 0..4096 (default 0): the batch pool (the
+                               coefficients and residual planes of the inter
+                               frames of one hivc_decode_batch call) is made
+                               at creation for this many frames at their
+                               largest, so batches that fit never grow it; a
+                               larger batch grows it stream-ordered (no host
+                               wait).  Counted by hivc_decoder_bytes */
 } hivc_config;
 
 /* Intra mask of one plane: n >= 1 sorted, unique linear indices y*w + x. */

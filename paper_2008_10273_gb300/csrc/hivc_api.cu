@@ -70,7 +70,8 @@ bool config_ok(const hivc_config *c)
     return c && c->width >= 1 && c->height >= 1 && c->width <= 16384 && c->height <= 16384 &&
            (c->chroma >= 0 && c->chroma <= 2) && c->block >= 1 && c->block <= kMaxB && (c->op == 0 || c->op == 1) &&
            (c->precision == 0 || c->precision == 1) && c->iframe_tol >= 0.0 && c->max_cycles >= 1 &&
-           c->cond_threshold >= 0.0 && (c->layout_groups == 0 || c->layout_groups == 1);
+           c->cond_threshold >= 0.0 && (c->layout_groups == 0 || c->layout_groups == 1) && c->batch_frames >= 0 &&
+           c->batch_frames <= 4096;
 }
 
 int plane_count(const hivc_config *c) { return c->chroma ? 3 : 1; }
@@ -106,6 +107,28 @@ float sor_omega(int w, int h, int n)
     const double rho = std::max(0.0, 1.0 - lam / 4.0);
     double om = 2.0 / (1.0 + std::sqrt(std::max(0.0, 1.0 - rho * rho)));
     return (float)std::min(std::max(om, 1.0), 1.95);
+}
+
+// Batch-pool bytes for nframes inter frames at their largest (every pixel
+// a residual point; Cb and Cr sharing their layout, the largest launch):
+// per frame and plane the coefficients, block constants and residual
+// plane, then one launch's scratch slots and plan (hivc_decode_batch's
+// layout).
+size_t pool_bytes_for(const hivc_config *c, int nframes)
+{
+    auto a256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    size_t b = 0;
+    int fblocks = 0;
+    for (int k = 0; k < nframes; ++k)
+        for (int p = 0; p < plane_count(c); ++p) {
+            const PlaneGeom g = plane_geom(c, p);
+            b += a256(4 * (size_t)g.w * g.h) + a256(4 * (size_t)g.nblocks) + a256(4 * (size_t)g.h * g.pitch);
+        }
+    for (int p = 0; p < plane_count(c); ++p) fblocks += plane_geom(c, p).nblocks;
+    const int launch_blocks = (kMaxJobs / std::min(2, plane_count(c))) * fblocks;
+    b += (size_t)coef_slots(launch_blocks) * kBigFloats * sizeof(float);
+    b += block_plan_bytes(launch_blocks, c->layout_groups != 0);
+    return b;
 }
 
 }  // namespace
@@ -358,6 +381,7 @@ size_t hivc_decoder_bytes(const hivc_config *c)
     add(3 * sizeof(unsigned int));
     add((size_t)coef_slots(nblocks) * kBigFloats * sizeof(float));  // K > 32 systems
     add(block_plan_bytes(nblocks, c->layout_groups != 0));          // plan of a frame's block stage
+    if (c->batch_frames > 0) add(pool_bytes_for(c, c->batch_frames));  // the batch pool made at creation
     add(4);                            // error word
     return b;
 }
@@ -441,10 +465,13 @@ hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out)
         cudaEventCreateWithFlags(&d->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaMemsetAsync(d->flags, 0, 4 * kStatusWords, d->stream) != cudaSuccess ||
         cudaMemsetAsync(d->ctl, 0, sizeof(IntraCtl), d->stream) != cudaSuccess ||
+        (cfg->batch_frames > 0 &&
+         cudaMallocAsync(&d->pool, pool_bytes_for(cfg, cfg->batch_frames), d->stream) != cudaSuccess) ||
         cudaStreamSynchronize(d->stream) != cudaSuccess) {
         hivc_decoder_destroy(d);
         return HIVC_E_CUDA;
     }
+    if (d->pool) d->pool_bytes = pool_bytes_for(cfg, cfg->batch_frames);
     *out = d;
     return HIVC_OK;
 }
@@ -453,11 +480,11 @@ void hivc_decoder_destroy(hivc_decoder *d)
 {
     if (!d) return;
     cudaSetDevice(d->device);
+    if (d->side) cudaStreamSynchronize(d->side);
+    if (d->pool && d->stream) cudaFreeAsync(d->pool, d->stream);  // a stream-ordered allocation
+    d->pool = nullptr;
     if (d->stream) cudaStreamSynchronize(d->stream);
-    if (d->side) {
-        cudaStreamSynchronize(d->side);
-        cudaStreamDestroy(d->side);
-    }
+    if (d->side) cudaStreamDestroy(d->side);
     if (d->ev_fork) cudaEventDestroy(d->ev_fork);
     if (d->ev_join) cudaEventDestroy(d->ev_join);
     for (auto &pe : d->pending) {
@@ -469,7 +496,6 @@ void hivc_decoder_destroy(hivc_decoder *d)
     if (d->h_flags) cudaFreeHost(d->h_flags);
     if (d->h_ctl) cudaFreeHost(d->h_ctl);
     if (d->igraph) cudaGraphExecDestroy(d->igraph);
-    if (d->pool) cudaFree(d->pool);
     d->mem.release();
     delete d;
 }
@@ -842,19 +868,18 @@ bool pframe_ok(const hivc_decoder *d, const hivc_pframe *f, const hivc_out *out)
     return true;
 }
 
-// The decoder's batch pool holds at least bytes (device memory; the old pool
-// is freed once the decoder's stream has finished with it).
-hivc_status ensure_pool(hivc_decoder *d, size_t bytes)
+// The decoder's batch pool holds at least bytes.  Growth is stream-ordered
+// on st (the stream that will use the pool, ordered after all earlier work
+// of the decoder's streams): the old pool is freed and the new one made
+// there, so no host thread waits.
+hivc_status ensure_pool(hivc_decoder *d, size_t bytes, cudaStream_t st)
 {
     if (d->pool_bytes >= bytes) return HIVC_OK;
-    if (d->pool) {
-        if (cudaStreamSynchronize(d->stream) != cudaSuccess) return HIVC_E_CUDA;
-        cudaFree(d->pool);
-        d->pool = nullptr;
-        d->pool_bytes = 0;
-    }
+    if (d->pool && cudaFreeAsync(d->pool, st) != cudaSuccess) return HIVC_E_CUDA;
+    d->pool = nullptr;
+    d->pool_bytes = 0;
     const size_t want = bytes + bytes / 4;
-    if (cudaMalloc(&d->pool, want) != cudaSuccess) {
+    if (cudaMallocAsync(&d->pool, want, st) != cudaSuccess) {
         cudaGetLastError();
         d->pool = nullptr;
         return HIVC_E_NOMEM;
@@ -908,7 +933,7 @@ hivc_status inter_blocks(hivc_decoder *d, const hivc_frame *frames, const std::v
     const bool groups = d->cfg.layout_groups != 0;
     const size_t plan_off = bytes;
     bytes += block_plan_bytes(launch_blocks, groups);
-    hivc_status s = ensure_pool(d, bytes);
+    hivc_status s = ensure_pool(d, bytes, st);
     if (s != HIVC_OK) return s;
     char *pool = static_cast<char *>(d->pool);
     auto at = [&](size_t k, int p, int w) {

@@ -3,7 +3,7 @@
 //
 //   u_i = f_i on the mask,   (L u)_i = sum_{in-image nbrs j} (u_j - u_i) = 0 elsewhere.
 //
-// Correction loop (the host drives the cycles):
+// Correction loop (driven by the device; the host only launches it):
 //   the iterate u is a float-float pair (hi + lo, ~48-bit significand);
 //   r = (L u)_U is evaluated exactly enough for residuals down to ~1e-11 by
 //   TwoSum on the neighbour differences, and stored as FP32; the correction
@@ -19,6 +19,17 @@
 // staged in shared memory, split into its red and black cells, and S full
 // red-black sweeps run there before the interior is written back (each half
 // sweep invalidates one more halo ring).
+//
+// Control: an IntraCtl word block in device memory holds each plane's
+// residual norm, observed contraction rate, relaxation factor and planned
+// sweep launches.  The last CTA of every residual launch plans the next
+// cycle (plan_cycle) and the last CTA of every second sweep launch counts
+// the sweeps done; both set the handles of a CUDA graph with two nested
+// conditional WHILE nodes (cycles; sweep launches in pairs of fixed
+// parity), so a whole solve is one graph launch with no host round trip,
+// and convergence is read at the decoder's sync.  Sweep launches read the
+// plan beside their first data loads and return at once when their plane
+// has no sweep left in this cycle.  No CTA ever waits for another.
 #include <algorithm>
 #include <atomic>
 #include <vector>

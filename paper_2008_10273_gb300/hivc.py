@@ -33,7 +33,8 @@ c_i32, c_u32, c_f64, c_f32, c_vp, c_sz = (ctypes.c_int32, ctypes.c_uint32, ctype
 class Config(ctypes.Structure):
     _fields_ = [("width", c_i32), ("height", c_i32), ("chroma", c_i32), ("block", c_i32),
                 ("op", c_i32), ("precision", c_i32), ("iframe_tol", c_f64), ("max_cycles", c_i32),
-                ("cond_threshold", c_f64), ("stream", c_vp), ("layout_groups", c_i32)]
+                ("cond_threshold", c_f64), ("stream", c_vp), ("layout_groups", c_i32),
+                ("batch_frames", c_i32)]
 
 
 class Points(ctypes.Structure):
@@ -211,7 +212,7 @@ class Decoder:
     def __init__(self, width: int, height: int, chroma: bool = True, block: int = 16,
                  iframe_tol: float = 1e-8, max_cycles: int = 40, precision: int = 0,
                  stream=None, timing: bool = False, cond_threshold: float = 1e6, op: int = 0,
-                 layout_groups: Optional[bool] = None):
+                 layout_groups: Optional[bool] = None, batch_frames: int = 0):
         cfg = config_default()
         # chroma: False/0 grey, True/1 4:2:0, 2 the 4:4:4 RCT colour path
         cfg.width, cfg.height, cfg.chroma, cfg.block = width, height, int(chroma), block
@@ -220,6 +221,7 @@ class Decoder:
         cfg.op = op
         if layout_groups is not None:
             cfg.layout_groups = int(bool(layout_groups))
+        cfg.batch_frames = int(batch_frames)
         cfg.stream = _stream_handle(stream)
         self.cfg = cfg
         self.width, self.height, self.chroma, self.block = width, height, bool(chroma), block

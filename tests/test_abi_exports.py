@@ -44,6 +44,16 @@ def test_host_only_entry_points(hv):
     c.width, c.height = 1920, 1080
     b = L.hivc_decoder_bytes(ctypes.byref(c))
     assert 100e6 < b < 400e6
+    # a batch pool sized at creation for 8 inter frames is counted in
+    c.batch_frames = 8
+    assert L.hivc_decoder_bytes(ctypes.byref(c)) > b + 8 * 1920 * 1080 * 4
+    for bad in (-1, 4097):
+        c.batch_frames = bad
+        assert L.hivc_decoder_bytes(ctypes.byref(c)) == 0
+    c.batch_frames = 0
+    c.layout_groups = 2
+    assert L.hivc_decoder_bytes(ctypes.byref(c)) == 0
+    c.layout_groups = 0
     c.block = 17
     assert L.hivc_decoder_bytes(ctypes.byref(c)) == 0
     h = ctypes.c_void_p()

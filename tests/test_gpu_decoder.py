@@ -175,6 +175,27 @@ def test_tiny_color_gop(hv, W, H):
             assert np.array_equal(to_np(outs[t][p]), per[t][p]), (t, p)
 
 
+@pytest.mark.parametrize("pre", [2, 6])
+def test_batch_pool_sized_at_creation(hv, pre):
+    """A decoder created with room for `pre` inter frames in its batch pool
+    gives the same bits as one that grows its pool on demand: with 2 the
+    4-frame batch outgrows it (stream-ordered growth), with 6 it fits."""
+    W, H, n = 160, 96, 5
+    gop = make_gop(8, W, H, n_frames=n)
+    fr = [("i", hv.device_iframe(gop.iframe))] + [("p", hv.device_pframe(pf)) for pf in gop.pframes]
+    got = []
+    for kw in ({}, {"batch_frames": pre}):
+        dec = hv.Decoder(W, H, chroma=True, **kw)
+        outs = [hv.alloc_out(W, H) for _ in range(n)]
+        hv.decode_batch([dec] * n, fr, outs)
+        dec.sync()
+        got.append([[to_np(o).copy() for o in out] for out in outs] + [_planes(dec)])
+        dec.close()
+    for a, b in zip(got[0], got[1]):
+        for p in range(3):
+            assert np.array_equal(a[p], b[p])
+
+
 def test_fullhd_gop_head(hv):
     """Paper-scale frames (FullHD 4:2:0): the intra frame and two inter
     frames, every pixel against the oracle."""
