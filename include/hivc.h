@@ -102,6 +102,18 @@ typedef struct {
                                largest, so batches that fit never grow it; a
                                larger batch grows it stream-ordered (no host
                                wait).  Counted by hivc_decoder_bytes */
+    int32_t fused_residual; /* 1: an inter frame with 16 x 16 blocks, 4:2:0
+                               or grey planes of even size and no layout
+                               groups is decoded by one fused kernel that
+                               evaluates Eq. 3 block by block in shared
+                               memory, then warps, adds and packs the
+                               block's pixels: no residual planes in memory
+                               (a smaller batch pool), but slower than the
+                               default on a GB300, where the evaluation of
+                               many frames in one launch overlaps the intra
+                               frame; 0 (default): residual planes
+                               (evaluation kernel, then the pixel kernel).
+                               Both give the same bits */
 } hivc_config;
 
 /* Intra mask of one plane: n >= 1 sorted, unique linear indices y*w + x. */

@@ -71,6 +71,7 @@ bool config_ok(const hivc_config *c)
            (c->chroma >= 0 && c->chroma <= 2) && c->block >= 1 && c->block <= kMaxB && (c->op == 0 || c->op == 1) &&
            (c->precision == 0 || c->precision == 1) && c->iframe_tol >= 0.0 && c->max_cycles >= 1 &&
            c->cond_threshold >= 0.0 && (c->layout_groups == 0 || c->layout_groups == 1) && c->batch_frames >= 0 &&
+           (c->fused_residual == 0 || c->fused_residual == 1) &&
            c->batch_frames <= 4096;
 }
 
@@ -114,15 +115,27 @@ float sor_omega(int w, int h, int n)
 // per frame and plane the coefficients, block constants and residual
 // plane, then one launch's scratch slots and plan (hivc_decode_batch's
 // layout).
+// Whether the decoder's inter frames go through the fused kernel (residual
+// evaluated per block in shared memory, no residual planes; opt-in), as far
+// as its configuration decides; the frame's pointers and pitches decide the
+// rest (pframe_fused_ok).
+bool fused_cfg(const hivc_config *c)
+{
+    return c->fused_residual == 1 && c->layout_groups == 0 && c->block == 16 && (c->chroma == 0 || c->chroma == 1) &&
+           c->width % 2 == 0 && c->height % 2 == 0;
+}
+
 size_t pool_bytes_for(const hivc_config *c, int nframes)
 {
     auto a256 = [](size_t b) { return (b + 255) / 256 * 256; };
     size_t b = 0;
     int fblocks = 0;
+    const bool planes = !fused_cfg(c);  // residual planes in the pool
     for (int k = 0; k < nframes; ++k)
         for (int p = 0; p < plane_count(c); ++p) {
             const PlaneGeom g = plane_geom(c, p);
-            b += a256(4 * (size_t)g.w * g.h) + a256(4 * (size_t)g.nblocks) + a256(4 * (size_t)g.h * g.pitch);
+            b += a256(4 * (size_t)g.w * g.h) + a256(4 * (size_t)g.nblocks) +
+                 (planes ? a256(4 * (size_t)g.h * g.pitch) : 0);
         }
     for (int p = 0; p < plane_count(c); ++p) fblocks += plane_geom(c, p).nblocks;
     const int launch_blocks = (kMaxJobs / std::min(2, plane_count(c))) * fblocks;
@@ -295,12 +308,16 @@ BlockScratch scratch(hivc_decoder *d)
     return S;
 }
 
-// Block stage of one frame: coefficients (+ large blocks), then residual fields.
-hivc_status run_block_residual(hivc_decoder *d, const hivc_residual *res)
+// Block stage of one frame: coefficients (+ large blocks), then residual
+// fields (eval; else the fused pixel kernel evaluates them, from the jobs
+// returned in jobs).
+hivc_status run_block_residual(hivc_decoder *d, const hivc_residual *res, bool eval = true,
+                               BlockJobs *jobs = nullptr)
 {
     BlockJobs J;
     hivc_status s = make_block_jobs(d, res, J);
     if (s != HIVC_OK) return s;
+    if (jobs) *jobs = J;
     cudaError_t e;
     {
         Timed t(d, 3);
@@ -308,7 +325,7 @@ hivc_status run_block_residual(hivc_decoder *d, const hivc_residual *res)
         e = launch_block_coef(J, scratch(d), d->stream, &l, !d->timing);
         t.done(1);
     }
-    if (e != cudaSuccess) return HIVC_E_CUDA;
+    if (e != cudaSuccess || !eval) return cuda_status(e);
     {
         Timed t(d, 5);
         e = launch_block_eval(J, d->flags, d->stream, !d->timing, &d->plan);
@@ -728,10 +745,9 @@ hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc
 
 namespace {
 
-// The pixel kernel of a frame whose residual planes (plane pitches) were
-// evaluated before, into the next reference buffer.
-cudaError_t launch_pixels(hivc_decoder *d, const float *flow, const hivc_out *out, float *const *r,
-                          bool pdl = true)
+// The pixel kernel's view of an inter frame (r: residual planes of plane
+// pitch, or null for the fused kernel) into the next reference buffer.
+InterFrame pixel_frame(const hivc_decoder *d, const float *flow, const hivc_out *out, float *const *r)
 {
     const int nxt = d->cur ^ 1;
     InterFrame F{};
@@ -742,14 +758,50 @@ cudaError_t launch_pixels(hivc_decoder *d, const float *flow, const hivc_out *ou
         F.ref_pitch[p] = d->pg[p].pitch;
         F.out[p] = out->plane[p];
         F.out_pitch[p] = out->pitch[p];
-        F.r[p] = r[p];
+        F.r[p] = r ? r[p] : nullptr;
         F.r_pitch[p] = d->pg[p].pitch;
     }
     F.width = d->cfg.width;
     F.height = d->cfg.height;
     F.chroma = d->cfg.chroma;
+    return F;
+}
+
+// Whether an inter frame of d goes through the fused kernel.
+bool fused_frame_ok(const hivc_decoder *d, const float *flow, const hivc_out *out)
+{
+    return fused_cfg(&d->cfg) && pframe_fused_ok(pixel_frame(d, flow, out, nullptr), d->cfg.block);
+}
+
+// The pixel kernel of a frame whose residual planes (plane pitches) were
+// evaluated before, into the next reference buffer.
+cudaError_t launch_pixels(hivc_decoder *d, const float *flow, const hivc_out *out, float *const *r,
+                          bool pdl = true)
+{
+    const InterFrame F = pixel_frame(d, flow, out, r);
     Timed t(d, 4);
     const cudaError_t e = launch_pframe(F, d->stream, pdl && !d->timing);
+    t.done(1);
+    return e;
+}
+
+// The fused kernel of a frame whose coefficients the block stage of jobs J
+// (one frame: Y, then the paired chroma job or Cb and Cr) computed.
+// early: the kernel before it on the stream is the fused kernel of the
+// previous frame, which waited for the block stage.
+cudaError_t launch_fused(hivc_decoder *d, const float *flow, const hivc_out *out, const BlockJobs &J, bool pdl,
+                         bool early)
+{
+    FusedFrame F{};
+    F.px = pixel_frame(d, flow, out, nullptr);
+    F.y = J.p[0];
+    F.nc = J.n - 1;
+    for (int k = 1; k < J.n && k < 3; ++k) F.c[k - 1] = J.p[k];
+    F.op = d->cfg.op;
+    F.flags = d->flags;
+    F.early = early ? 1 : 0;
+    Timed t(d, 4);
+    const cudaError_t e = launch_pframe_fused(F, d->stream, pdl && !d->timing);
     t.done(1);
     return e;
 }
@@ -764,12 +816,17 @@ hivc_status hivc_decode_pframe(hivc_decoder *d, const hivc_pframe *f, const hivc
     if (!d->has_ref) return HIVC_E_NO_REFERENCE;
     if (cudaSetDevice(d->device) != cudaSuccess) return HIVC_E_CUDA;
     const int nxt = d->cur ^ 1;
-    // three launches: coefficients (Eq. 2), residual planes (Eq. 3), then
-    // warp + add + pack (the 4:4:4 colour path: its RCT kernel)
-    hivc_status s = run_block_residual(d, f->res);
+    // coefficients (Eq. 2), then the fused kernel (Eq. 3 per block in
+    // shared memory, warp + add + pack); or three launches: coefficients,
+    // residual planes (Eq. 3), then warp + add + pack (the 4:4:4 colour
+    // path: its RCT kernel)
+    const bool fused = fused_frame_ok(d, f->flow, out);
+    BlockJobs J;
+    hivc_status s = run_block_residual(d, f->res, !fused, &J);
     if (s != HIVC_OK) return s;
-    const cudaError_t e = d->cfg.chroma == 2 ? launch_rct_frame(d, f->flow, nullptr, nullptr, true, out)
-                                             : launch_pixels(d, f->flow, out, d->rfield);
+    const cudaError_t e = fused                ? launch_fused(d, f->flow, out, J, true, false)
+                          : d->cfg.chroma == 2 ? launch_rct_frame(d, f->flow, nullptr, nullptr, true, out)
+                                               : launch_pixels(d, f->flow, out, d->rfield);
     if (e != cudaSuccess) return HIVC_E_CUDA;
     d->cur = nxt;
     d->st.frames += 1;
@@ -888,21 +945,36 @@ hivc_status ensure_pool(hivc_decoder *d, size_t bytes, cudaStream_t st)
     return HIVC_OK;
 }
 
-using ResidualPlanes = std::vector<std::array<float *, 3>>;
+// The block stage's results of an inter run: per frame its residual
+// planes (split path) and its block jobs (coefficient arrays in the pool).
+struct RunBlocks {
+    bool fused = false;  // the fused kernel evaluates the residual
+    std::vector<std::array<float *, 3>> planes;
+    std::vector<BlockJobs> jobs;
+};
+
+// Whether every frame of the run goes through the fused kernel.
+bool fused_run(const hivc_decoder *d, const hivc_frame *frames, const hivc_out *outs, const std::vector<int> &ks)
+{
+    for (int k : ks)
+        if (!fused_frame_ok(d, frames[k].p->flow, &outs[k])) return false;
+    return !ks.empty();
+}
 
 // Block stage of the inter frames frames[k] (k in ks, in order) of decoder
 // d on stream st: per up to kMaxJobs block jobs (8 FullHD 4:2:0 frames) one
-// coefficient launch and one evaluation launch into each frame's residual
-// planes (returned in rp), all in the batch pool.  pdl: the first launch may
-// overlap the kernel before it on st.  Every frame has been checked.
+// coefficient launch and (rb.fused false) one evaluation launch into each
+// frame's residual planes, all in the batch pool; the frames' jobs and
+// planes are returned in rb.  pdl: the first launch may overlap the kernel
+// before it on st.  Every frame has been checked.
 hivc_status inter_blocks(hivc_decoder *d, const hivc_frame *frames, const std::vector<int> &ks, cudaStream_t st,
-                         bool pdl, ResidualPlanes &rp)
+                         bool pdl, RunBlocks &rb)
 {
     if (cudaSetDevice(d->device) != cudaSuccess) return HIVC_E_CUDA;
     const size_t nf = ks.size();
     // pool layout: per frame and plane a256(4 n_points) + a256(4 nblocks)
-    // + the residual plane (h x pitch floats), then the K > 32 scratch of
-    // the largest coefficient launch
+    // (+ the residual plane, h x pitch floats, on the split path), then the
+    // K > 32 scratch of the largest coefficient launch
     std::vector<size_t> off(nf * 3 * 3);
     size_t bytes = 0;
     for (size_t k = 0; k < nf; ++k)
@@ -913,7 +985,7 @@ hivc_status inter_blocks(hivc_decoder *d, const hivc_frame *frames, const std::v
             off[(k * 3 + p) * 3 + 1] = bytes;
             bytes += a256(4 * (size_t)g.nblocks);
             off[(k * 3 + p) * 3 + 2] = bytes;
-            bytes += a256(4 * (size_t)g.h * g.pitch);
+            if (!rb.fused) bytes += a256(4 * (size_t)g.h * g.pitch);
         }
     int fblocks = 0;
     for (int p = 0; p < d->np; ++p) fblocks += d->pg[p].nblocks;
@@ -937,7 +1009,8 @@ hivc_status inter_blocks(hivc_decoder *d, const hivc_frame *frames, const std::v
     if (s != HIVC_OK) return s;
     char *pool = static_cast<char *>(d->pool);
     auto at = [&](size_t k, int p, int w) {
-        return p < d->np ? reinterpret_cast<float *>(pool + off[(k * 3 + p) * 3 + w]) : nullptr;
+        return p < d->np && !(w == 2 && rb.fused) ? reinterpret_cast<float *>(pool + off[(k * 3 + p) * 3 + w])
+                                                  : nullptr;
     };
     std::vector<BlockJobs> jobs(nf);
     for (size_t k = 0; k < nf; ++k) {
@@ -964,7 +1037,7 @@ hivc_status inter_blocks(hivc_decoder *d, const hivc_frame *frames, const std::v
             t.done(l);
         }
         pdl = true;
-        if (e == cudaSuccess) {
+        if (e == cudaSuccess && !rb.fused) {
             Timed t(d, 5);
             e = launch_block_eval(J, d->flags, st, !d->timing, &S.plan);
             t.done(1);
@@ -983,19 +1056,25 @@ hivc_status inter_blocks(hivc_decoder *d, const hivc_frame *frames, const std::v
         }
     }
     if (flush() != cudaSuccess) return HIVC_E_CUDA;
-    rp.resize(nf);
-    for (size_t k = 0; k < nf; ++k) rp[k] = {at(k, 0, 2), at(k, 1, 2), at(k, 2, 2)};
+    rb.planes.resize(nf);
+    for (size_t k = 0; k < nf; ++k) rb.planes[k] = {at(k, 0, 2), at(k, 1, 2), at(k, 2, 2)};
+    rb.jobs = std::move(jobs);
     return HIVC_OK;
 }
 
-// Per inter frame the warp + residual + pack kernel on the decoder's stream
-// (the residual planes of inter_blocks).  pdl: the first launch may overlap
-// the kernel before it.
+// Per inter frame the pixel kernel on the decoder's stream: the fused
+// kernel (from the coefficients of inter_blocks), or the warp + residual +
+// pack kernel (its residual planes).  pdl: the first launch may overlap the
+// kernel before it.
 hivc_status inter_pixels(hivc_decoder *d, const hivc_frame *frames, const hivc_out *outs, const std::vector<int> &ks,
-                         const ResidualPlanes &rp, bool pdl)
+                         const RunBlocks &rb, bool pdl)
 {
     for (size_t k = 0; k < ks.size(); ++k) {
-        const cudaError_t e = launch_pixels(d, frames[ks[k]].p->flow, &outs[ks[k]], rp[k].data(), pdl || k > 0);
+        const hivc_pframe *f = frames[ks[k]].p;
+        // the first fused kernel waits for the block stage before it reads
+        // the coefficients; each later one may read them at once
+        const cudaError_t e = rb.fused ? launch_fused(d, f->flow, &outs[ks[k]], rb.jobs[k], pdl || k > 0, k > 0)
+                                       : launch_pixels(d, f->flow, &outs[ks[k]], rb.planes[k].data(), pdl || k > 0);
         if (e != cudaSuccess) return HIVC_E_CUDA;
         d->cur ^= 1;
         d->st.frames += 1;
@@ -1006,9 +1085,10 @@ hivc_status inter_pixels(hivc_decoder *d, const hivc_frame *frames, const hivc_o
 hivc_status decode_inter_run(hivc_decoder *d, const hivc_frame *frames, const hivc_out *outs,
                              const std::vector<int> &ks)
 {
-    ResidualPlanes rp;
-    const hivc_status s = inter_blocks(d, frames, ks, d->stream, true, rp);
-    return s != HIVC_OK ? s : inter_pixels(d, frames, outs, ks, rp, true);
+    RunBlocks rb;
+    rb.fused = fused_run(d, frames, outs, ks);
+    const hivc_status s = inter_blocks(d, frames, ks, d->stream, true, rb);
+    return s != HIVC_OK ? s : inter_pixels(d, frames, outs, ks, rb, true);
 }
 
 // An intra frame followed by the inter run ks: the run's block stage does
@@ -1022,14 +1102,15 @@ hivc_status decode_intra_then_run(hivc_decoder *d, const hivc_frame *frames, con
     if (cudaSetDevice(d->device) != cudaSuccess || cudaEventRecord(d->ev_fork, d->stream) != cudaSuccess ||
         cudaStreamWaitEvent(d->side, d->ev_fork, 0) != cudaSuccess)
         return HIVC_E_CUDA;
-    ResidualPlanes rp;
-    const hivc_status sb = inter_blocks(d, frames, ks, d->side, false, rp);
+    RunBlocks rb;
+    rb.fused = fused_run(d, frames, outs, ks);
+    const hivc_status sb = inter_blocks(d, frames, ks, d->side, false, rb);
     const bool joined = cudaEventRecord(d->ev_join, d->side) == cudaSuccess;
     intra = hivc_decode_iframe(d, frames[ki].i, &outs[ki]);
     if (!joined || cudaStreamWaitEvent(d->stream, d->ev_join, 0) != cudaSuccess) return HIVC_E_CUDA;
     if (intra != HIVC_OK && intra != HIVC_E_NOT_CONVERGED) return intra;
     if (sb != HIVC_OK) return sb;
-    return inter_pixels(d, frames, outs, ks, rp, false);
+    return inter_pixels(d, frames, outs, ks, rb, false);
 }
 
 }  // namespace

@@ -197,6 +197,25 @@ struct InterFrame {
 // kernel in the stream.
 cudaError_t launch_pframe(const InterFrame &f, cudaStream_t st, bool pdl);
 
+// One inter frame through the fused pixel kernel: the residual of Eq. 3
+// evaluated per block from the coefficients of the block stage into shared
+// memory, then the warp, add, clamp and pack of the block's pixels (no
+// residual planes in memory).  Same values as the evaluation kernel
+// followed by pframe_kernel, bit for bit.
+struct FusedFrame {
+    InterFrame px;        // flow, references, outputs (px.r unused)
+    BlockPlane y;         // the luma job (coefficients in coef[0], acoef[0])
+    BlockPlane c[2];      // chroma: one paired job (Cb in [0], Cr in [1] of val/coef/acoef), or the Cb and Cr jobs
+    int32_t nc;           // chroma jobs: 0 (grey), 1 (paired) or 2
+    int32_t op;           // residual operator (its Green's table)
+    uint32_t *flags;      // data errors (bad positions)
+    int32_t early;        // 1: evaluate before waiting for the preceding grid (which itself waited)
+};
+// Whether the fused kernel takes this frame: 4:2:0 or grey, 16 x 16 blocks,
+// even plane sizes and the pixel kernel's whole-quad alignment.
+bool pframe_fused_ok(const InterFrame &f, int block);
+cudaError_t launch_pframe_fused(const FusedFrame &f, cudaStream_t st, bool pdl);
+
 // ---------------------------------------------------------------------------
 // warp + add + pack (Sec. 2, 2.3)
 // ---------------------------------------------------------------------------

@@ -15,6 +15,7 @@
 // the references in shared memory with the tensor memory accelerator, and
 // one that shared a 3 x 3 patch between the quad's samples, were not
 // faster on this gather pattern.)
+#include "block_device.cuh"
 #include "hivc_internal.cuh"
 
 namespace hivc {
@@ -75,23 +76,20 @@ constexpr int kQX = 32, kQY = 4;  // quads per CTA: 32 x 4 (128 threads)
 // (16 luma, 8 chroma) issued before any store, so that they are in flight
 // together; the new reference and the output go out as row pairs.  The
 // arithmetic is the scalar path's, value for value.
-template <bool CHROMA>
-__device__ __forceinline__ void whole_quad(const InterFrame &F, int qx, int qy)
+// The residual of the quad comes from res(r, rc), called after the flow
+// loads: r the four luma pixels row by row, rc the Cb and Cr pixels.
+template <bool CHROMA, class Res>
+__device__ __forceinline__ void whole_quad_r(const InterFrame &F, int qx, int qy, const Res &res)
 {
     const int W = F.width, H = F.height;
     const int x0 = 2 * qx, y0 = 2 * qy;
-    const int yp = F.ref_pitch[0], op = F.out_pitch[0], rp = F.r_pitch[0];
+    const int yp = F.ref_pitch[0], op = F.out_pitch[0];
     const float4 *fl = reinterpret_cast<const float4 *>(F.flow + 2 * (y0 * W + x0));
     const float4 fa = __ldg(fl), fb = __ldg(fl + W / 2);
     const float2 f[4] = {make_float2(fa.x, fa.y), make_float2(fa.z, fa.w), make_float2(fb.x, fb.y),
                          make_float2(fb.z, fb.w)};
-    const float2 *rr0 = reinterpret_cast<const float2 *>(F.r[0] + y0 * rp + x0);
-    const float2 rl0 = __ldg(rr0), rl1 = __ldg(rr0 + rp / 2);
-    float rc[2] = {0.f, 0.f};
-    if (CHROMA) {
-        rc[0] = __ldg(F.r[1] + qy * F.r_pitch[1] + qx);
-        rc[1] = __ldg(F.r[2] + qy * F.r_pitch[2] + qx);
-    }
+    float r[4], rc[2] = {0.f, 0.f};
+    res(r, rc);
     const float *__restrict__ RY = F.ref[0];
     float ax[4], ay[4], g[4][4];
 #pragma unroll
@@ -124,7 +122,6 @@ __device__ __forceinline__ void whole_quad(const InterFrame &F, int qx, int qy)
             c[pl][3] = __ldg(R + co + coy + cox);
         }
     }
-    const float r[4] = {rl0.x, rl0.y, rl1.x, rl1.y};
     float v[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) v[k] = recon(lerp2(ax[k], ay[k], g[k][0], g[k][1], g[k][2], g[k][3]), r[k]);
@@ -142,6 +139,25 @@ __device__ __forceinline__ void whole_quad(const InterFrame &F, int qx, int qy)
             F.out[pl + 1][qy * F.out_pitch[pl + 1] + qx] = to_u8(cv);
         }
     }
+}
+
+// (the residual from the residual planes)
+template <bool CHROMA>
+__device__ __forceinline__ void whole_quad(const InterFrame &F, int qx, int qy)
+{
+    whole_quad_r<CHROMA>(F, qx, qy, [&](float (&r)[4], float (&rc)[2]) {
+        const int x0 = 2 * qx, y0 = 2 * qy, rp = F.r_pitch[0];
+        const float2 *rr0 = reinterpret_cast<const float2 *>(F.r[0] + y0 * rp + x0);
+        const float2 rl0 = __ldg(rr0), rl1 = __ldg(rr0 + rp / 2);
+        r[0] = rl0.x;
+        r[1] = rl0.y;
+        r[2] = rl1.x;
+        r[3] = rl1.y;
+        if (CHROMA) {
+            rc[0] = __ldg(F.r[1] + qy * F.r_pitch[1] + qx);
+            rc[1] = __ldg(F.r[2] + qy * F.r_pitch[2] + qx);
+        }
+    });
 }
 
 // Any quad (cut by the right or bottom edge, odd widths, unaligned rows):
@@ -199,6 +215,225 @@ __global__ void __launch_bounds__(kQX *kQY, 12) pframe_kernel(const __grid_const
     else any_quad<CHROMA>(F, qx, qy);
 }
 
+
+// ---- the fused kernel: residual evaluation and pixels of a frame ----------
+// A CTA takes a 32 x 32 luma macroblock.  Warp w takes the 16 x 16 luma
+// block (2 mbx + (w & 1), 2 mby + (w >> 1)) and the quarter of the chroma
+// block (mbx, mby) co-sited with it.  Phase 1 evaluates Eq. 3 for the
+// warp's pixels into shared memory with the evaluation kernel's arithmetic
+// (r = a, then r = fma(c_j, G[p_j, q], r) in the order of the points, the
+// Green's rows as 16-byte loads, then the data at the points exactly; bad
+// positions give a zero block and a flag).  Phase 2 is the pixel kernel's
+// whole-quad path with the residual read from shared memory: lane l takes
+// the two quads of luma rows 2 (l / 4) + {0, 1}, columns 4 (l % 4) .. + 3.
+// The values equal those of the evaluation kernel followed by
+// pframe_kernel, bit for bit; the residual planes never reach memory.
+// Opt-in: on a GB300 it takes about 36 us per FullHD 4:2:0 frame against
+// 15 us for pframe_kernel plus 8 us of batched evaluation.  A warp runs
+// its latency-bound evaluation and then its gathers, and with two quads a
+// lane and 32 warps an SM it keeps fewer samples in flight than
+// pframe_kernel's one quad a thread and 48 warps.
+constexpr int kFusedWarps = 4;
+
+constexpr int kFusedRow = 20;  // luma row stride: the quads' reads spread over the banks
+struct __align__(16) FusedRes {
+    float y[16][kFusedRow];  // the luma block
+    float c[2][8][8];        // the Cb and Cr quarter
+};
+
+// Eq. 3 for the luma block lb of job P into R.
+__device__ __forceinline__ void fused_luma(const BlockPlane &P, const BlockTables &tab, int lb,
+                                           float (*R)[kFusedRow], int lane, uint32_t *flags)
+{
+    const BlockGeom g = block_geom(P, lb);
+    const float a0 = __ldcg(P.acoef[0] + lb);
+    const int K = g.K, w = g.w, N = g.w * g.h, rl = g_rowlen(N);
+    const float *__restrict__ G = green_rows(tab, g.w, g.h);
+    const int q0 = 4 * lane, q1 = 128 + 4 * lane;
+    const bool act = q0 < N, act1 = q1 < N;
+    float r0[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) r0[t] = a0;
+    bool valid = K > 0;
+    int prev = -1;
+    for (int j0 = 0; j0 < K; j0 += 32) {
+        const int j = j0 + lane;
+        int p = 0;
+        float c0 = 0.f;
+        if (j < K) {
+            p = __ldg(P.pos + g.s + j);
+            c0 = __ldcg(P.coef[0] + g.s + j);
+        }
+        const int up = __shfl_up_sync(0xffffffffu, p, 1);
+        const int before = lane == 0 ? prev : up;
+        if (__any_sync(0xffffffffu, j < K && (p >= N || p <= before))) valid = false;
+        prev = __shfl_sync(0xffffffffu, p, 31);
+        if (!valid) break;
+        const int n = min(32, K - j0);
+        const float *Gq = G + q0;
+#pragma unroll 4
+        for (int u = 0; u < n; ++u) {
+            const float cu = __shfl_sync(0xffffffffu, c0, u);
+            const int pu = __shfl_sync(0xffffffffu, p, u);
+            if (act) {
+                const float *row = Gq + pu * rl;
+                const float4 lo = __ldg(reinterpret_cast<const float4 *>(row));
+                const float4 hi = act1 ? __ldg(reinterpret_cast<const float4 *>(row + 128)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float gv[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+                for (int t = 0; t < 8; ++t) r0[t] = fmaf(cu, gv[t], r0[t]);
+            }
+        }
+    }
+    if (!valid) {
+        if (K > 0 && lane == 0 && flags) atomicOr(flags, kFlagPos);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) r0[t] = 0.f;
+    }
+    if (w == 16) {
+        // pixels 4l .. 4l+3 are columns 4 (l % 4) .. +3 of row l / 4, the
+        // second half the same columns of row 8 + l / 4
+        if (act) *reinterpret_cast<float4 *>(&R[lane >> 2][4 * (lane & 3)]) = make_float4(r0[0], r0[1], r0[2], r0[3]);
+        if (act1)
+            *reinterpret_cast<float4 *>(&R[8 + (lane >> 2)][4 * (lane & 3)]) = make_float4(r0[4], r0[5], r0[6], r0[7]);
+    } else {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int q = (t < 4 ? q0 : q1 - 4) + t;
+            if (q < N) {
+                const int y = q / w;
+                R[y][q - y * w] = r0[t];
+            }
+        }
+    }
+    if (!valid) return;
+    __syncwarp();
+    // the data at the points, exactly
+    for (int j = lane; j < K; j += 32) {
+        const int p = __ldg(P.pos + g.s + j), y = p / w;
+        R[y][p - y * w] = (float)__ldg(P.val[0] + g.s + j);
+    }
+}
+
+// Eq. 3 for the quarter (qx0, qy0) + [0, 8)^2 of chroma block cb of job P
+// into R[0] (values and coefficients [0]) and, TWO, R[1] ([1]).  Lane l
+// takes the quarter's pixels (2 (l % 4) + {0, 1}, l / 4).
+template <bool TWO>
+__device__ __forceinline__ void fused_chroma(const BlockPlane &P, const BlockTables &tab, int cb, int qx0, int qy0,
+                                             float (*R0)[8], float (*R1)[8], int lane, uint32_t *flags)
+{
+    const BlockGeom g = block_geom(P, cb);
+    const float a0 = __ldcg(P.acoef[0] + cb), a1 = TWO ? __ldcg(P.acoef[1] + cb) : 0.f;
+    const int K = g.K, w = g.w, N = g.w * g.h, rl = g_rowlen(N);
+    const float *__restrict__ G = green_rows(tab, g.w, g.h);
+    const int ly = lane >> 2, lx = 2 * (lane & 3);
+    const int cy = qy0 + ly, cx = qx0 + lx;
+    const bool in0 = cy < g.h && cx < w, in1 = cy < g.h && cx + 1 < w;
+    const int qa = cy * w + cx;
+    float r0[2] = {a0, a0}, r1[2] = {a1, a1};
+    bool valid = K > 0;
+    int prev = -1;
+    for (int j0 = 0; j0 < K; j0 += 32) {
+        const int j = j0 + lane;
+        int p = 0;
+        float c0 = 0.f, c1 = 0.f;
+        if (j < K) {
+            p = __ldg(P.pos + g.s + j);
+            c0 = __ldcg(P.coef[0] + g.s + j);
+            if (TWO) c1 = __ldcg(P.coef[1] + g.s + j);
+        }
+        const int up = __shfl_up_sync(0xffffffffu, p, 1);
+        const int before = lane == 0 ? prev : up;
+        if (__any_sync(0xffffffffu, j < K && (p >= N || p <= before))) valid = false;
+        prev = __shfl_sync(0xffffffffu, p, 31);
+        if (!valid) break;
+        const int n = min(32, K - j0);
+#pragma unroll 4
+        for (int u = 0; u < n; ++u) {
+            const float cu0 = __shfl_sync(0xffffffffu, c0, u);
+            const float cu1 = TWO ? __shfl_sync(0xffffffffu, c1, u) : 0.f;
+            const int pu = __shfl_sync(0xffffffffu, p, u);
+            const float *row = G + pu * rl + qa;
+            const float g0 = in0 ? __ldg(row) : 0.f, g1 = in1 ? __ldg(row + 1) : 0.f;
+            r0[0] = fmaf(cu0, g0, r0[0]);
+            r0[1] = fmaf(cu0, g1, r0[1]);
+            if (TWO) {
+                r1[0] = fmaf(cu1, g0, r1[0]);
+                r1[1] = fmaf(cu1, g1, r1[1]);
+            }
+        }
+    }
+    if (!valid) {
+        if (K > 0 && lane == 0 && flags) atomicOr(flags, kFlagPos);
+        r0[0] = r0[1] = r1[0] = r1[1] = 0.f;
+    }
+    R0[ly][lx] = r0[0];
+    R0[ly][lx + 1] = r0[1];
+    if (TWO) {
+        R1[ly][lx] = r1[0];
+        R1[ly][lx + 1] = r1[1];
+    }
+    if (!valid) return;
+    __syncwarp();
+    for (int j = lane; j < K; j += 32) {
+        const int p = __ldg(P.pos + g.s + j), y = p / w, x = p - y * w;
+        if (y < qy0 || y >= qy0 + 8 || x < qx0 || x >= qx0 + 8) continue;
+        R0[y - qy0][x - qx0] = (float)__ldg(P.val[0] + g.s + j);
+        if (TWO) R1[y - qy0][x - qx0] = (float)__ldg(P.val[1] + g.s + j);
+    }
+}
+
+// NC: chroma jobs (0 grey, 1 paired Cb + Cr, 2 separate)
+template <int NC>
+__global__ void __launch_bounds__(32 * kFusedWarps, 8)
+    pframe_fused_kernel(const __grid_constant__ FusedFrame F, const __grid_constant__ BlockTables tab)
+{
+    constexpr bool CHROMA = NC > 0;
+    __shared__ FusedRes sres[kFusedWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bx = 2 * blockIdx.x + (warp & 1), by = 2 * blockIdx.y + (warp >> 1);
+    const int W = F.px.width, H = F.px.height;
+    const bool inside = 16 * bx < W && 16 * by < H;
+    // with early, the preceding grid waited for its own predecessor before
+    // it let this one start, so the block stage's coefficients are complete
+    if (!F.early) asm volatile("griddepcontrol.wait;" ::: "memory");
+    FusedRes &R = sres[warp];
+    if (inside) {
+        fused_luma(F.y, tab, by * F.y.nbx + bx, R.y, lane, F.flags);
+        if (CHROMA) {
+            const int cb = (by >> 1) * F.c[0].nbx + (bx >> 1), qx0 = 8 * (bx & 1), qy0 = 8 * (by & 1);
+            if (NC == 1) {
+                fused_chroma<true>(F.c[0], tab, cb, qx0, qy0, R.c[0], R.c[1], lane, F.flags);
+            } else {
+                fused_chroma<false>(F.c[0], tab, cb, qx0, qy0, R.c[0], nullptr, lane, F.flags);
+                fused_chroma<false>(F.c[1], tab, cb, qx0, qy0, R.c[1], nullptr, lane, F.flags);
+            }
+        }
+    }
+    // the preceding frame's references are read from here on
+    if (F.early) asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (!inside) return;
+    __syncwarp();
+    const int i = lane >> 2, j = lane & 3;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int qx = 8 * bx + 2 * j + k, qy = 8 * by + i;
+        if (2 * qx >= W || 2 * qy >= H) continue;
+        whole_quad_r<CHROMA>(F.px, qx, qy, [&](float (&r)[4], float (&rc)[2]) {
+            const int cx = 4 * j + 2 * k;
+            r[0] = R.y[2 * i][cx];
+            r[1] = R.y[2 * i][cx + 1];
+            r[2] = R.y[2 * i + 1][cx];
+            r[3] = R.y[2 * i + 1][cx + 1];
+            if (CHROMA) {
+                rc[0] = R.c[0][i][2 * j + k];
+                rc[1] = R.c[1][i][2 * j + k];
+            }
+        });
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_pframe(const InterFrame &F, cudaStream_t st, bool pdl)
@@ -222,6 +457,42 @@ cudaError_t launch_pframe(const InterFrame &F, cudaStream_t st, bool pdl)
     const int vi = vec ? 1 : 0;
     if (F.chroma) return cudaLaunchKernelEx(&cfg, pframe_kernel<true>, F, vi);
     return cudaLaunchKernelEx(&cfg, pframe_kernel<false>, F, vi);
+}
+
+namespace {
+bool whole_quads_ok(const InterFrame &F)
+{
+    auto al = [](const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; };
+    return F.width % 2 == 0 && al(F.flow, 16) && F.ref_pitch[0] % 2 == 0 && F.r_pitch[0] % 2 == 0 &&
+           F.out_pitch[0] % 2 == 0 && al(F.ref[0], 8) && al(F.ref_out[0], 8) && al(F.r[0], 8) && al(F.out[0], 2);
+}
+}  // namespace
+
+bool pframe_fused_ok(const InterFrame &F, int block)
+{
+    InterFrame G = F;
+    G.r_pitch[0] = 2;  // no residual planes
+    G.r[0] = F.ref[0];
+    return (F.chroma == 0 || F.chroma == 1) && block == 16 && F.width % 2 == 0 && F.height % 2 == 0 &&
+           whole_quads_ok(G);
+}
+
+cudaError_t launch_pframe_fused(const FusedFrame &f, cudaStream_t st, bool pdl)
+{
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    const int nbx = (f.px.width + 15) / 16, nby = (f.px.height + 15) / 16;
+    cfg.gridDim = dim3((nbx + 1) / 2, (nby + 1) / 2);
+    cfg.blockDim = dim3(32 * kFusedWarps);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    const BlockTables tab = block_tables(f.op);
+    if (f.px.chroma == 0) return cudaLaunchKernelEx(&cfg, pframe_fused_kernel<0>, f, tab);
+    if (f.nc == 1) return cudaLaunchKernelEx(&cfg, pframe_fused_kernel<1>, f, tab);
+    return cudaLaunchKernelEx(&cfg, pframe_fused_kernel<2>, f, tab);
 }
 
 }  // namespace hivc
