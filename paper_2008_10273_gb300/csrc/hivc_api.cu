@@ -776,11 +776,11 @@ bool fused_frame_ok(const hivc_decoder *d, const float *flow, const hivc_out *ou
 // The pixel kernel of a frame whose residual planes (plane pitches) were
 // evaluated before, into the next reference buffer.
 cudaError_t launch_pixels(hivc_decoder *d, const float *flow, const hivc_out *out, float *const *r,
-                          bool pdl = true)
+                          bool pdl = true, bool early = false)
 {
     const InterFrame F = pixel_frame(d, flow, out, r);
     Timed t(d, 4);
-    const cudaError_t e = launch_pframe(F, d->stream, pdl && !d->timing);
+    const cudaError_t e = launch_pframe(F, d->stream, pdl && !d->timing, early && pdl && !d->timing);
     t.done(1);
     return e;
 }
@@ -1074,7 +1074,8 @@ hivc_status inter_pixels(hivc_decoder *d, const hivc_frame *frames, const hivc_o
         // the first fused kernel waits for the block stage before it reads
         // the coefficients; each later one may read them at once
         const cudaError_t e = rb.fused ? launch_fused(d, f->flow, &outs[ks[k]], rb.jobs[k], pdl || k > 0, k > 0)
-                                       : launch_pixels(d, f->flow, &outs[ks[k]], rb.planes[k].data(), pdl || k > 0);
+                                       : launch_pixels(d, f->flow, &outs[ks[k]], rb.planes[k].data(), pdl || k > 0,
+                                                       k > 0);
         if (e != cudaSuccess) return HIVC_E_CUDA;
         d->cur ^= 1;
         d->st.frames += 1;

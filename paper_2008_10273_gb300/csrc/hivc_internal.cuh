@@ -194,8 +194,10 @@ struct InterFrame {
 
 // Warp + residual + clamp + pack, one thread per luma quad and its co-sited
 // chroma pixels.  pdl: launch as a programmatic dependent of the previous
-// kernel in the stream.
-cudaError_t launch_pframe(const InterFrame &f, cudaStream_t st, bool pdl);
+// kernel in the stream.  early: that kernel is the previous frame's pixel
+// kernel (which waited for the residual planes), so the flow and residual
+// loads may go out before waiting for it.
+cudaError_t launch_pframe(const InterFrame &f, cudaStream_t st, bool pdl, bool early = false);
 
 // One inter frame through the fused pixel kernel: the residual of Eq. 3
 // evaluated per block from the coefficients of the block stage into shared

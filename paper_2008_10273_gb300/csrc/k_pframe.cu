@@ -141,9 +141,10 @@ __device__ __forceinline__ void whole_quad_r(const InterFrame &F, int qx, int qy
     }
 }
 
-// (the residual from the residual planes)
+// (the residual from the residual planes; early: the preceding grid is
+// waited for only here, after the flow and residual loads are issued)
 template <bool CHROMA>
-__device__ __forceinline__ void whole_quad(const InterFrame &F, int qx, int qy)
+__device__ __forceinline__ void whole_quad(const InterFrame &F, int qx, int qy, bool early)
 {
     whole_quad_r<CHROMA>(F, qx, qy, [&](float (&r)[4], float (&rc)[2]) {
         const int x0 = 2 * qx, y0 = 2 * qy, rp = F.r_pitch[0];
@@ -156,6 +157,10 @@ __device__ __forceinline__ void whole_quad(const InterFrame &F, int qx, int qy)
         if (CHROMA) {
             rc[0] = __ldg(F.r[1] + qy * F.r_pitch[1] + qx);
             rc[1] = __ldg(F.r[2] + qy * F.r_pitch[2] + qx);
+        }
+        if (early) {
+            asm volatile("griddepcontrol.wait;" ::: "memory");
+            asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
         }
     });
 }
@@ -203,16 +208,31 @@ __device__ __forceinline__ void any_quad(const InterFrame &F, int qx, int qy)
     }
 }
 
+// early: the preceding grid is the previous frame's pixel kernel, which
+// itself waited for the residual planes; the flow and the residual planes
+// are then loaded before waiting for it (they do not depend on it), so
+// that the first CTAs of this frame fill the SMs that the previous frame's
+// last wave leaves idle.  Otherwise the preceding launch wrote the
+// residual planes, and every read waits for it.
 template <bool CHROMA>
-__global__ void __launch_bounds__(kQX *kQY, 12) pframe_kernel(const __grid_constant__ InterFrame F, int vec)
+__global__ void __launch_bounds__(kQX *kQY, 12) pframe_kernel(const __grid_constant__ InterFrame F, int vec,
+                                                               int early)
 {
-    // the preceding launch wrote the residual planes or the references
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (!early) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    }
     const int qx = blockIdx.x * kQX + threadIdx.x, qy = blockIdx.y * kQY + threadIdx.y;
     if (2 * qx >= F.width || 2 * qy >= F.height) return;
-    if (vec && 2 * qy + 1 < F.height) whole_quad<CHROMA>(F, qx, qy);
-    else any_quad<CHROMA>(F, qx, qy);
+    if (vec && 2 * qy + 1 < F.height) {
+        whole_quad<CHROMA>(F, qx, qy, early != 0);
+    } else {
+        if (early) {
+            asm volatile("griddepcontrol.wait;" ::: "memory");
+            asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+        }
+        any_quad<CHROMA>(F, qx, qy);
+    }
 }
 
 
@@ -436,7 +456,7 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 8)
 
 }  // namespace
 
-cudaError_t launch_pframe(const InterFrame &F, cudaStream_t st, bool pdl)
+cudaError_t launch_pframe(const InterFrame &F, cudaStream_t st, bool pdl, bool early)
 {
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
@@ -454,9 +474,9 @@ cudaError_t launch_pframe(const InterFrame &F, cudaStream_t st, bool pdl)
     bool vec = F.width % 2 == 0 && al(F.flow, 16) && F.ref_pitch[0] % 2 == 0 && F.r_pitch[0] % 2 == 0 &&
                F.out_pitch[0] % 2 == 0 && al(F.ref[0], 8) && al(F.ref_out[0], 8) && al(F.r[0], 8) &&
                al(F.out[0], 2);
-    const int vi = vec ? 1 : 0;
-    if (F.chroma) return cudaLaunchKernelEx(&cfg, pframe_kernel<true>, F, vi);
-    return cudaLaunchKernelEx(&cfg, pframe_kernel<false>, F, vi);
+    const int vi = vec ? 1 : 0, ei = early ? 1 : 0;
+    if (F.chroma) return cudaLaunchKernelEx(&cfg, pframe_kernel<true>, F, vi, ei);
+    return cudaLaunchKernelEx(&cfg, pframe_kernel<false>, F, vi, ei);
 }
 
 namespace {
