@@ -39,8 +39,14 @@ UNIT = "FullHD frames/s"
 # ncu captures, keyed by kernel family, with the sha1 of the kernel's source
 # file at capture time; a changed source voids the number (reported null).
 NCU_TRAFFIC = {
-    # intra_sor_kernel, one launch on the FullHD 4:2:0 GOP workload
-    "intra_sweeps": {"bytes": 28.02e6, "sha": "36db0b47cb4d"},
+    # dram__bytes_read.sum + dram__bytes_write.sum of one launch on the FullHD
+    # 4:2:0 GOP workload (profiles/*.md give the commands):
+    # intra_sor_kernel over the three planes
+    "intra_sweeps": {"bytes": 28.02e6, "sha": "3c1b50fb60f2"},
+    # pframe_kernel, one frame
+    "inter_pixels": {"bytes": 41.79e6, "sha": "55ab9c90df81"},
+    # block_eval_kernel, per frame of an 8-frame launch (49.57 MB / 8)
+    "block_eval": {"bytes": 6.196e6, "sha": "62cb19a05736"},
 }
 
 
@@ -65,6 +71,12 @@ def parse_args(argv=None):
                    help="frames per stream of the saturated serving runs (every frame there at t = 0)")
     p.add_argument("--no-next", action="store_true",
                    help="skip the coefficient-mode, biharmonic, 4:4:4 colour-path and batching measurements")
+    p.add_argument("--host-launched", action="store_true",
+                   help="launch every kernel from the host (the per-kernel timing mode) in every pass, so that a "
+                        "profiler sees the sweep and residual kernels that the intra solve's conditional graph "
+                        "otherwise launches (ncu does not profile kernel nodes of such graphs); for launch lists "
+                        "only: events between kernels keep them from overlapping, so the step times are not the "
+                        "headline")
     p.add_argument("--path", choices=["batch", "plain"], default="batch",
                    help="decode path of the timed steps: one hivc_decode_batch call per GOP (inter frames "
                         "share coefficient launches), or one call per frame")
@@ -540,7 +552,7 @@ def main(argv=None):
     gop = make_workload(a, rank)
     W, H = a.width, a.height
     stream = torch.cuda.Stream()
-    dec = hivc.Decoder(W, H, chroma=True, iframe_tol=a.iframe_tol, stream=stream, timing=False)
+    dec = hivc.Decoder(W, H, chroma=True, iframe_tol=a.iframe_tol, stream=stream, timing=a.host_launched)
     iframe_d = hivc.device_iframe(gop.iframe)
     pframes_d = [hivc.device_pframe(p) for p in gop.pframes]
     out = hivc.alloc_out(W, H)
@@ -614,7 +626,7 @@ def main(argv=None):
             timed()
         torch.cuda.synchronize()
         kstats = dec.sync()
-        hivc.lib().hivc_decoder_set_timing(dec.handle, 0)
+        hivc.lib().hivc_decoder_set_timing(dec.handle, 1 if a.host_launched else 0)
     step_ms = [e[0].elapsed_time(e[-1]) for e in tev]
     plain_ms = [e[0].elapsed_time(e[-1]) for e in ev]
     frame_ms = []
@@ -683,8 +695,14 @@ def main(argv=None):
         traffic = None
         if tr and tr["sha"] == src_sha(os.path.join(ROOT, "paper_2008_10273_gb300", "csrc", srcf)):
             # a capture of one launch over all planes, scaled to the average
-            # launch by the pixels it covers
-            traffic = tr["bytes"] * (px_per_launch(f) / px_frame if f in (1, 2) else 1.0)
+            # launch by the pixels it covers; the evaluation's per frame,
+            # scaled by the frames of the average launch
+            if f in (1, 2):
+                traffic = tr["bytes"] * px_per_launch(f) / px_frame
+            elif f == 5:
+                traffic = tr["bytes"] * (inter_frames_per_step / max(1, fam_n[5] / kpass) if a.path == "batch" else 1)
+            else:
+                traffic = tr["bytes"]
         return {"kernel": hivc.KERNEL_FAMILIES[f], "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                 "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
                 "dram_frac": (traffic / (avg_ms / 1e3) / 1e9 / hbm_peak) if traffic else None,
@@ -783,27 +801,34 @@ def main(argv=None):
                 down_done[k].record(down_s)
         stream.wait_event(down_done[nsteps - 1])
 
+    # three timed repetitions of e2e_steps steps each; the median one is
+    # reported (single repetitions on this pool occasionally ran 40 % slower
+    # with the same code, a host-side stall of the pipeline)
+    e2e_reps = []
     with torch.cuda.stream(stream):
         if a.path == "batch":
             e2e_pipelined(2)
         else:
             e2e_step()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        if a.path == "batch":
-            # the copy streams start after e0 (they wait for it), so their
-            # work is inside the timed region
-            up_s.wait_event(e0)
-            down_s.wait_event(e0)
-            e2e_pipelined(a.e2e_steps)
-        else:
-            for _ in range(a.e2e_steps):
-                e2e_step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        dec.sync()
-    e2e_value, _ = replica_value(e0.elapsed_time(e1), a.e2e_steps * nfr, px_scale, dist, "cuda")
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if a.path == "batch":
+                # the copy streams start after e0 (they wait for it), so their
+                # work is inside the timed region
+                up_s.wait_event(e0)
+                down_s.wait_event(e0)
+                e2e_pipelined(a.e2e_steps)
+            else:
+                for _ in range(a.e2e_steps):
+                    e2e_step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            dec.sync()
+            e2e_reps.append(e0.elapsed_time(e1))
+    e2e_ms = sorted(e2e_reps)[1]
+    e2e_value, _ = replica_value(e2e_ms, a.e2e_steps * nfr, px_scale, dist, "cuda")
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -830,6 +855,7 @@ def main(argv=None):
                       "path": "one decode call per frame"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "steps": a.e2e_steps,
+                    "repetitions_ms": [round(x, 4) for x in e2e_reps], "reported": "the median repetition",
                     "mode": ("pipelined: a GOP's inputs go up in one copy from one pinned buffer (hivc.FramePack) "
                              "on a copy stream while the previous GOP decodes, its outputs come down in one copy "
                              "on another (two buffer sets each), all inside the timed region")
