@@ -309,11 +309,13 @@ struct IntraPlane {
 // each residual launch plans the next cycle (sweeps per plane from the
 // residual reached and the observed contraction, Young's relation for the
 // relaxation factor).  Sweep launches come in pairs of fixed parity (launch
-// it = 2 iter + parity reads correction buffer e[it & 1] and writes the
-// other, so a plane's correction after its nl launches sits in e[nl & 1]);
-// the last CTA of each pair's second launch advances iter.  Both publish
-// whether the loop goes on, to conditional graph nodes (h_outer, h_inner)
-// and to go_outer / go_inner.
+// it = 2 i + parity of pair i reads correction buffer e[it & 1] and writes
+// the other, so a plane's correction after its nl launches sits in
+// e[nl & 1]).  A launch of parity q reads i from iter[q], and its first
+// CTA hands i on: parity 0 to iter[1], parity 1 as i + 1 to iter[0], with
+// whether the sweep loop goes on (no launch reads the word that another
+// running launch writes).  Both publish whether the loops go on, to
+// conditional graph nodes (h_outer, h_inner) and to go_outer / go_inner.
 struct IntraCtl {
     double tol;                // max |(L u)_i| to reach
     double rn[3];              // residual reached per plane
@@ -321,7 +323,8 @@ struct IntraCtl {
     float omega[3];            // relaxation factor per plane
     int32_t max_cycles, spl;   // cycle cap, sweeps per launch
     int32_t nl[3];             // sweep launches of the current cycle per plane
-    int32_t maxl, iter, cycles;  // launches of the cycle, pairs done, cycles done
+    int32_t maxl, cycles;      // launches of the cycle, cycles done
+    int32_t iter[2];           // pairs done, as the launches of parity 0 and 1 read it
     int32_t sweeps[3], sweeps_max;
     int32_t upar[3];           // the u buffer holding a plane's current iterate
     uint32_t rbits[3];         // max |residual| of the last residual launch (float bits)

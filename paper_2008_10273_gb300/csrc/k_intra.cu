@@ -23,8 +23,8 @@
 // Control: an IntraCtl word block in device memory holds each plane's
 // residual norm, observed contraction rate, relaxation factor and planned
 // sweep launches.  The last CTA of every residual launch plans the next
-// cycle (plan_cycle) and the last CTA of every second sweep launch counts
-// the sweeps done; both set the handles of a CUDA graph with two nested
+// cycle (plan_cycle) and the first CTA of every sweep launch hands the pair
+// count on (pair_step); both set the handles of a CUDA graph with two nested
 // conditional WHILE nodes (cycles; sweep launches in pairs of fixed
 // parity), so a whole solve is one graph launch with no host round trip,
 // and convergence is read at the decoder's sync.  Sweep launches read the
@@ -233,7 +233,7 @@ __device__ void plan_cycle(const IntraJobs &J, IntraCtl &c, bool first)
         maxl = max(maxl, c.nl[p]);
     }
     c.maxl = maxl;
-    c.iter = 0;
+    c.iter[0] = c.iter[1] = 0;
     c.converged = conv ? 1 : 0;
     const int go = (maxl > 0 && c.cycles < c.max_cycles) ? 1 : 0;
     c.go_outer = go;
@@ -367,8 +367,8 @@ __global__ void __launch_bounds__(kResThreads) intra_residual_kernel(const __gri
 // exactness shrinks by one ring per half sweep anyway, and the 2S half
 // sweeps leave the interior, kHL = 2S rings in, exact.  Tile corners are
 // even (kTX, kTY, kHL even), so a cell's colour is known at compile time.
-// Launch it = 2 iter + PAR of the cycle: sweeps from e[PAR] (from zero at
-// it = 0) into e[PAR ^ 1].  The control words (iter, the plane's launch
+// Launch it = 2 i + PAR of the cycle: sweeps from e[PAR] (from zero at
+// it = 0) into e[PAR ^ 1].  The control words (i, the plane's launch
 // count, omega) are read beside the region's data loads, which do not
 // depend on them; a plane without this launch returns false before it
 // writes anything.
@@ -379,7 +379,7 @@ __device__ __forceinline__ bool sor_body(const IntraPlane &P, int pl, int lt, co
     static_assert(TX % 2 == 0 && kTY % 2 == 0 && kHL % 2 == 0, "tiles start on even cells");
     extern __shared__ float sor_smem[];
     auto E = reinterpret_cast<float(*)[kRH + 2][HW + 2]>(sor_smem);
-    const int it = 2 * c->iter + PAR, nlp = c->nl[pl];
+    const int it = 2 * c->iter[PAR] + PAR, nlp = c->nl[pl];
     const float omega = c->omega[pl];
     const int tx0 = (lt % P.tiles_x) * TX, ty0 = (lt / P.tiles_x) * kTY;
     const int gx0 = tx0 - kHL, gy0 = ty0 - kHL;
@@ -541,7 +541,7 @@ __device__ __forceinline__ bool sor4_body(const IntraPlane &P, int pl, int lt, c
 {
     constexpr int TX = sor_tx(kQCols);
     __shared__ float rows[kQWarps][2][kQCols];  // each warp's first and last row
-    const int it = 2 * c->iter + PAR, nlp = c->nl[pl];
+    const int it = 2 * c->iter[PAR] + PAR, nlp = c->nl[pl];
     const float omega = c->omega[pl];
     const int tx0 = (lt % P.tiles_x) * TX, ty0 = (lt / P.tiles_x) * kTY;
     const int gx0 = tx0 - kHL, gy0 = ty0 - kHL;
@@ -672,41 +672,46 @@ __device__ __forceinline__ int sweep_plane(const IntraJobs &J, int b, int &lt)
     return 0;
 }
 
-// After the second launch of a pair (its last CTA): the pair count
-// advances, and the sweep loop goes on while the cycle has launches left.
-__device__ __forceinline__ void pair_done(const IntraJobs &J, int *s_last)
+// The pair count i handed on by the first CTA of a sweep launch (one
+// thread, before its sweeps): parity 0 to the pair's second launch, parity
+// 1 as i + 1 to the next pair's first launch, with whether the sweep loop
+// goes on (the next pair has launches left in this cycle).  Each word is
+// written while no launch that reads it runs.
+template <int PAR>
+__device__ __forceinline__ void pair_step(const IntraJobs &J)
 {
+    if (blockIdx.x != 0 || threadIdx.x != 0 || threadIdx.y != 0) return;
     IntraCtl *c = J.ctl;
-    if (!last_cta(c, s_last)) return;
-    if (threadIdx.x != 0 || threadIdx.y != 0) return;
-    const int iter = c->iter + 1;
-    c->iter = iter;
-    const int go = 2 * iter < c->maxl ? 1 : 0;
+    const int i = c->iter[PAR];
+    if (PAR == 0) {
+        c->iter[1] = i;
+        return;
+    }
+    c->iter[0] = i + 1;
+    const int go = 2 * (i + 1) < c->maxl ? 1 : 0;
     c->go_inner = go;
     if (J.h_inner) cudaGraphSetConditional(J.h_inner, go);
 }
 
-// S red-black sweeps of launch it = 2 iter + PAR of the cycle, over the
+// S red-black sweeps of launch it = 2 i + PAR of the cycle, over the
 // planes whose launch count exceeds it (from e = 0 at it = 0, else from
 // the plane's current correction in e[PAR]).
 template <int RW, int PAR>
 __global__ void __launch_bounds__(RW / 2 * kTY_THREADS, 1) intra_sor_kernel(const __grid_constant__ IntraJobs J)
 {
-    __shared__ int s_last;
+    pair_step<PAR>(J);
     int lt;
     const int pl = sweep_plane(J, blockIdx.x, lt);
     sor_body<RW, PAR>(J.p[pl], pl, lt, J.ctl);
-    if (PAR) pair_done(J, &s_last);
 }
 
 template <int PAR>
 __global__ void __launch_bounds__(32 * kQWarps, 1) intra_sor4_kernel(const __grid_constant__ IntraJobs J)
 {
-    __shared__ int s_last;
+    pair_step<PAR>(J);
     int lt;
     const int pl = sweep_plane(J, blockIdx.x, lt);
     sor4_body<PAR>(J.p[pl], pl, lt, J.ctl);
-    if (PAR) pair_done(J, &s_last);
 }
 
 }  // namespace
@@ -848,7 +853,7 @@ __global__ void intra_tune_ctl_kernel(IntraCtl *c)
         z.omega[p] = 1.5f;
     }
     z.maxl = 1 << 20;
-    z.iter = 1;
+    z.iter[0] = z.iter[1] = 1;
     *c = z;
 }
 
