@@ -403,12 +403,13 @@ def next_rows_measurement(a, gop):
 
 def batching_measurement(a):
     """Four FullHD 4:2:0 inter frames decoded by one hivc_decode_batch call
-    (the plan, one persistent coefficient launch, one evaluation launch and
-    the layout groups' tensor-core product over all their blocks, then a
-    pixel kernel per frame) against the same call with every block on its
-    own (layout groups off) and against four single-frame calls.  Luma
-    residual blocks: Poisson(8) points clipped to 0..48, 10% empty, 30% of
-    the full blocks on 8 shared layouts per frame."""
+    (the plan, one persistent coefficient launch and one evaluation launch
+    over all their blocks, then a pixel kernel per frame) against the same
+    call with layout groups on (one factorisation per shared layout, the
+    residual of its blocks as a tensor-core product) and against four
+    single-frame calls.  Luma residual blocks: Poisson(8) points clipped to
+    0..48, 10% empty, 30% of the full blocks on 8 shared layouts per
+    frame."""
     import torch
 
     from paper_2008_10273_gb300 import hivc
@@ -424,8 +425,8 @@ def batching_measurement(a):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     res = {}
     steps, warm = 10, 3
-    for name, batched, groups in (("batched", True, True), ("batched_per_block", True, False),
-                                  ("plain", False, True)):
+    for name, batched, groups in (("batched", True, False), ("batched_groups", True, True),
+                                  ("plain", False, False)):
         dec = hivc.Decoder(W, H, chroma=True, iframe_tol=a.iframe_tol, stream=stream, layout_groups=groups)
         ms = []
         with torch.cuda.stream(stream):

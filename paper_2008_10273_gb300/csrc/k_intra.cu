@@ -5,8 +5,9 @@
 //
 // Correction loop (driven by the device; the host only launches it):
 //   the iterate u is a float-float pair (hi + lo, ~48-bit significand);
-//   r = (L u)_U is evaluated exactly enough for residuals down to ~1e-11 by
-//   TwoSum on the neighbour differences, and stored as FP32; the correction
+//   r = (L u)_U is evaluated exactly enough for residuals down to ~1e-11
+//   (u as 64-bit fixed point, the neighbour sum in integers), and stored
+//   as FP32; the correction
 //   equation (-L_UU) e = r is relaxed in FP32 by red-black SOR sweeps
 //   (e = 0 on the mask); then u += e in float-float.  Each cycle shrinks the
 //   residual by the inner solve's reduction, so the iterate reaches
@@ -267,15 +268,28 @@ __global__ void intra_ctl_init_kernel(IntraCtl *c, float om0, float om1, float o
     *c = z;
 }
 
+// The iterate hi + lo as a 64-bit fixed-point number of 2^-40 grey levels
+// (|u| < 2^23: the sum of four neighbours cannot overflow).  hi * 2^40 is
+// exact and an integer for |hi| >= 2^-16; the rounding of lo * 2^40 (and
+// of hi * 2^40 below 2^-16) is at most 2^-41 grey levels, far below the
+// residuals the solve aims at, and the sums of these integers are exact.
+constexpr float kFix = 1099511627776.f;     // 2^40
+constexpr float kUnfix = 1.f / kFix;        // 2^-40, exact
+__device__ __forceinline__ long long to_fix(float h, float l)
+{
+    return __float2ll_rn(h * kFix) + __float2ll_rn(l * kFix);
+}
+
 // u_out = u_in + e (unknown pixels; float-float), res = (L u_out)_i, and the
 // max |res| per plane; first: res = (L u)_i of the starting iterate.  A 64 x
 // 16 tile with a one-pixel halo is updated once per cell into shared
-// memory; the residual reads the updated neighbours from there.  Planes
-// that the plan leaves out this cycle (converged) are skipped.  The
+// memory, as fixed-point integers (to_fix); the residual of a pixel is the
+// exact integer sum of its neighbours' differences, rounded once to FP32.
+// Planes that the plan leaves out this cycle (converged) are skipped.  The
 // launch's last CTA plans the next cycle.
 __global__ void __launch_bounds__(kResThreads) intra_residual_kernel(const __grid_constant__ IntraJobs J, int first)
 {
-    __shared__ float sh[kRTH + 2][kRTW + 2], sl[kRTH + 2][kRTW + 2];
+    __shared__ long long su[kRTH + 2][kRTW + 2];
     __shared__ float red[kResThreads / 32];
     __shared__ int s_last;
     IntraCtl *c = J.ctl;
@@ -309,8 +323,7 @@ __global__ void __launch_bounds__(kResThreads) intra_residual_kernel(const __gri
                     }
                 }
             }
-            sh[ly][lx] = h;
-            sl[ly][lx] = l;
+            su[ly][lx] = to_fix(h, l);
         }
         __syncthreads();
         float rmax = 0.f;
@@ -321,22 +334,14 @@ __global__ void __launch_bounds__(kResThreads) intra_residual_kernel(const __gri
             const int i = gy * pitch + gx;
             float r = 0.f;
             if (!P.mask[i]) {
-                // sum_j (h_j - h_i) exactly as float-float, plus the lo parts
-                const float ch = sh[ly + 1][lx + 1], cl = sl[ly + 1][lx + 1];
-                float S = 0.f, E = 0.f, tail = 0.f;
-                auto acc = [&](int yy, int xx) {
-                    float d, de, s2, e2;
-                    two_sum(sh[yy][xx], -ch, d, de);
-                    two_sum(S, d, s2, e2);
-                    S = s2;
-                    E = __fadd_rn(E, __fadd_rn(e2, de));
-                    tail = __fadd_rn(tail, __fsub_rn(sl[yy][xx], cl));
-                };
-                if (gx > 0) acc(ly + 1, lx);
-                if (gx < W - 1) acc(ly + 1, lx + 2);
-                if (gy > 0) acc(ly, lx + 1);
-                if (gy < H - 1) acc(ly + 2, lx + 1);
-                r = __fadd_rn(S, __fadd_rn(E, tail));
+                // sum_j (u_j - u_i), exact in fixed point, rounded once
+                const long long uc = su[ly + 1][lx + 1];
+                long long acc = 0;
+                if (gx > 0) acc += su[ly + 1][lx] - uc;
+                if (gx < W - 1) acc += su[ly + 1][lx + 2] - uc;
+                if (gy > 0) acc += su[ly][lx + 1] - uc;
+                if (gy < H - 1) acc += su[ly + 2][lx + 1] - uc;
+                r = __ll2float_rn(acc) * kUnfix;
             }
             P.res[i] = r;
             rmax = fmaxf(rmax, fabsf(r));
