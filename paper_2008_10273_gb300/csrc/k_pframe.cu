@@ -85,7 +85,7 @@ __device__ __forceinline__ void whole_quad_r(const InterFrame &F, int qx, int qy
     const int x0 = 2 * qx, y0 = 2 * qy;
     const int yp = F.ref_pitch[0], op = F.out_pitch[0];
     const float4 *fl = reinterpret_cast<const float4 *>(F.flow + 2 * (y0 * W + x0));
-    const float4 fa = __ldg(fl), fb = __ldg(fl + W / 2);
+    const float4 fa = __ldcs(fl), fb = __ldcs(fl + W / 2);  // read once: evict first
     const float2 f[4] = {make_float2(fa.x, fa.y), make_float2(fa.z, fa.w), make_float2(fb.x, fb.y),
                          make_float2(fb.z, fb.w)};
     float r[4], rc[2] = {0.f, 0.f};
@@ -128,15 +128,15 @@ __device__ __forceinline__ void whole_quad_r(const InterFrame &F, int qx, int qy
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
         *reinterpret_cast<float2 *>(F.ref_out[0] + (y0 + rr) * yp + x0) = make_float2(v[2 * rr], v[2 * rr + 1]);
-        *reinterpret_cast<uchar2 *>(F.out[0] + (y0 + rr) * op + x0) =
-            make_uchar2(to_u8(v[2 * rr]), to_u8(v[2 * rr + 1]));
+        __stcs(reinterpret_cast<uchar2 *>(F.out[0] + (y0 + rr) * op + x0),
+               make_uchar2(to_u8(v[2 * rr]), to_u8(v[2 * rr + 1])));
     }
     if (CHROMA) {
 #pragma unroll
         for (int pl = 0; pl < 2; ++pl) {
             const float cv = recon(lerp2(cax, cay, c[pl][0], c[pl][1], c[pl][2], c[pl][3]), rc[pl]);
             F.ref_out[pl + 1][qy * cp + qx] = cv;
-            F.out[pl + 1][qy * F.out_pitch[pl + 1] + qx] = to_u8(cv);
+            __stcs(reinterpret_cast<char *>(F.out[pl + 1] + qy * F.out_pitch[pl + 1] + qx), (char)to_u8(cv));
         }
     }
 }
@@ -149,14 +149,14 @@ __device__ __forceinline__ void whole_quad(const InterFrame &F, int qx, int qy, 
     whole_quad_r<CHROMA>(F, qx, qy, [&](float (&r)[4], float (&rc)[2]) {
         const int x0 = 2 * qx, y0 = 2 * qy, rp = F.r_pitch[0];
         const float2 *rr0 = reinterpret_cast<const float2 *>(F.r[0] + y0 * rp + x0);
-        const float2 rl0 = __ldg(rr0), rl1 = __ldg(rr0 + rp / 2);
+        const float2 rl0 = __ldcs(rr0), rl1 = __ldcs(rr0 + rp / 2);
         r[0] = rl0.x;
         r[1] = rl0.y;
         r[2] = rl1.x;
         r[3] = rl1.y;
         if (CHROMA) {
-            rc[0] = __ldg(F.r[1] + qy * F.r_pitch[1] + qx);
-            rc[1] = __ldg(F.r[2] + qy * F.r_pitch[2] + qx);
+            rc[0] = __ldcs(F.r[1] + qy * F.r_pitch[1] + qx);
+            rc[1] = __ldcs(F.r[2] + qy * F.r_pitch[2] + qx);
         }
         if (early) {
             asm volatile("griddepcontrol.wait;" ::: "memory");
