@@ -72,8 +72,9 @@ typedef struct {
     double iframe_tol;      /* stop when max |(L u)_i| over unknown pixels
                                <= tol, grey levels (Eq. 1 residual); default
                                1e-8; FP32-only mode floors near 1e-3 */
-    int32_t max_cycles;     /* cap on outer correction cycles (default 40);
-                               beyond it sync returns HIVC_E_NOT_CONVERGED */
+    int32_t max_cycles;     /* cap on outer correction cycles, 1..1000
+                               (default 40); beyond it sync returns
+                               HIVC_E_NOT_CONVERGED */
     double cond_threshold;  /* >= 0 (default 1e6).  Every residual block's
                                condition bound kappa = 8 tr(G_PP) / (1 - K/N)
                                >= cond_2(G_PP) (Sec. 2.2: the eigenvalues of

@@ -325,6 +325,7 @@ struct IntraCtl {
     int32_t nl[3];             // sweep launches of the current cycle per plane
     int32_t maxl, cycles;      // launches of the cycle, cycles done
     int32_t iter[2];           // pairs done, as the launches of parity 0 and 1 read it
+    int32_t pairs[2];          // launch pairs of the cycle: over all planes, then over the chroma planes alone
     int32_t sweeps[3], sweeps_max;
     int32_t upar[3];           // the u buffer holding a plane's current iterate
     uint32_t rbits[3];         // max |residual| of the last residual launch (float bits)
@@ -341,6 +342,8 @@ struct IntraJobs {
     int32_t n;
     IntraCtl *ctl;                      // control state
     unsigned long long h_outer, h_inner;  // conditional handles (0: launched from the host)
+    unsigned long long h_inner_c;       // the chroma phase's loop (0: launched from the host)
+    int32_t chroma_phase;               // 1: the launches that sweep only the chroma planes use regions of their own
 };
 
 cudaError_t launch_intra_init(IntraJobs &jobs, uint32_t *flags, cudaStream_t st, int *launches);
@@ -355,6 +358,9 @@ cudaError_t launch_intra_residual(IntraJobs &jobs, bool first, cudaStream_t st);
 // control state keeps active (variant: the region tiling, see
 // set_sor_variant).
 cudaError_t launch_intra_sor_pair(IntraJobs &jobs, int variant, cudaStream_t st);
+// One pair of the chroma phase's launches (jobs.chroma_phase): the chroma
+// planes alone, with regions of 128 x 88.
+cudaError_t launch_intra_sor_chroma_pair(IntraJobs &jobs, cudaStream_t st);
 // The SOR tiling for these planes: tuned (timing launches on tune_ctl, a
 // control state of its own), looked up, or pinned.
 int intra_sor_variant(IntraJobs &jobs, IntraCtl *tune_ctl, cudaStream_t st);

@@ -52,8 +52,19 @@ constexpr int kRH = 128;
 constexpr int kTY = kRH - 2 * kHL;      // 112 output rows
 constexpr int kTY_THREADS = 16;         // thread rows; each thread owns kRH/16 consecutive rows
 constexpr int kRows = kRH / kTY_THREADS;
+// the chroma phase's regions: 128 x 88 staged, 112 x 72 output, 11 thread
+// rows (the two 960 x 540 planes of FullHD 4:2:0 in 144 regions, one wave)
+constexpr int kRHc = 88;
 __host__ __device__ constexpr int sor_tx(int rw) { return rw - 2 * kHL; }
-__host__ __device__ constexpr size_t sor_smem_bytes(int rw) { return 2 * (kRH + 2) * (rw / 2 + 2) * sizeof(float); }  // bordered colour arrays
+__host__ __device__ constexpr size_t sor_smem_bytes(int rw, int rh = kRH)
+{
+    return 2 * (rh + 2) * (rw / 2 + 2) * sizeof(float);  // bordered colour arrays
+}
+// pairs of sweep launches a cycle may plan, and cycles a solve may run: a
+// loop condition never stays set beyond these, whatever the control state
+// or the configuration holds
+constexpr int kMaxPairs = 1 << 14;
+constexpr int kMaxCycles = 1000;
 
 constexpr int kResThreads = 256;
 constexpr int kRTW = 64, kRTH = 16;  // residual tile
@@ -235,18 +246,30 @@ __device__ void plan_cycle(const IntraJobs &J, IntraCtl &c, bool first)
     }
     c.maxl = maxl;
     c.iter[0] = c.iter[1] = 0;
+    // the launch pairs: with the chroma phase, the all-plane launches while
+    // luma sweeps (at least one pair: each loop runs at least once), then
+    // the chroma planes alone with regions of their own
+    int pa = (maxl + 1) / 2, pb = 0;
+    if (J.chroma_phase && J.n == 3) {
+        const int nc = max(c.nl[1], c.nl[2]);
+        pa = max(1, (c.nl[0] + 1) / 2);
+        pb = nc > 2 * pa ? (nc - 2 * pa + 1) / 2 : 0;
+    }
+    c.pairs[0] = min(pa, kMaxPairs);
+    c.pairs[1] = min(pb, kMaxPairs);
     c.converged = conv ? 1 : 0;
-    const int go = (maxl > 0 && c.cycles < c.max_cycles) ? 1 : 0;
+    const int go = (maxl > 0 && c.cycles < c.max_cycles && c.cycles < kMaxCycles) ? 1 : 0;
     c.go_outer = go;
     if (!go && !conv) c.unconverged += 1;
     if (go) {  // the next cycle's sweep launches (in pairs) and the pixels they sweep
-        c.sor_launches += 2 * ((maxl + 1) / 2);
+        c.sor_launches += 2 * (c.pairs[0] + (J.chroma_phase && J.n == 3 ? max(c.pairs[1], 1) : 0));
         for (int p = 0; p < J.n; ++p) c.sor_pixels += (long long)c.nl[p] * J.p[p].width * J.p[p].height;
     }
     if (J.h_outer) cudaGraphSetConditional(J.h_outer, go);
-    // the sweep loop of the next cycle starts open (the last sweep launch of
-    // this cycle closed it): a cycle always has at least one launch
+    // the sweep loops of the next cycle start open (the last sweep launch of
+    // each closed it): each loop runs at least one pair per cycle
     if (J.h_inner) cudaGraphSetConditional(J.h_inner, go);
+    if (J.h_inner_c) cudaGraphSetConditional(J.h_inner_c, go);
 }
 
 // The control state of a new solve (one thread).
@@ -377,16 +400,17 @@ __global__ void __launch_bounds__(kResThreads) intra_residual_kernel(const __gri
 // count, omega) are read beside the region's data loads, which do not
 // depend on them; a plane without this launch returns false before it
 // writes anything.
-template <int RW, int PAR>
+template <int RW, int RH, int PAR>
 __device__ __forceinline__ bool sor_body(const IntraPlane &P, int pl, int lt, const IntraCtl *c)
 {
     constexpr int HW = RW / 2, TX = sor_tx(RW);  // cells per colour and row; output columns
-    static_assert(TX % 2 == 0 && kTY % 2 == 0 && kHL % 2 == 0, "tiles start on even cells");
+    constexpr int TY = RH - 2 * kHL, TROWS = RH / kRows;  // output rows; thread rows
+    static_assert(TX % 2 == 0 && TY % 2 == 0 && kHL % 2 == 0 && RH % kRows == 0, "tiles start on even cells");
     extern __shared__ float sor_smem[];
-    auto E = reinterpret_cast<float(*)[kRH + 2][HW + 2]>(sor_smem);
+    auto E = reinterpret_cast<float(*)[RH + 2][HW + 2]>(sor_smem);
     const int it = 2 * c->iter[PAR] + PAR, nlp = c->nl[pl];
     const float omega = c->omega[pl];
-    const int tx0 = (lt % P.tiles_x) * TX, ty0 = (lt / P.tiles_x) * kTY;
+    const int tx0 = (lt % P.tiles_x) * TX, ty0 = (lt / P.tiles_x) * TY;
     const int gx0 = tx0 - kHL, gy0 = ty0 - kHL;
     const int W = P.width, H = P.height, pitch = P.pitch;
     const int hx = threadIdx.x, ty = threadIdx.y, ly0 = ty * kRows;
@@ -402,7 +426,7 @@ __device__ __forceinline__ bool sor_body(const IntraPlane &P, int pl, int lt, co
     float ec[kRows][2], wi[kRows][2], wr[kRows][2];
     // A region with every cell inside the image and off its border (all
     // cells have four neighbours): plain loads, n = 4.
-    const bool interior = gx0 >= 1 && gy0 >= 1 && gx0 + RW <= W - 1 && gy0 + kRH <= H - 1;
+    const bool interior = gx0 >= 1 && gy0 >= 1 && gx0 + RW <= W - 1 && gy0 + RH <= H - 1;
     bool fz = false;
     float omc = 0.f;
     if (interior) {
@@ -482,13 +506,13 @@ __device__ __forceinline__ bool sor_body(const IntraPlane &P, int pl, int lt, co
         }
     }
     // the border of the colour arrays: finite values
-    for (int k = hx + ty * HW; k < 2 * (kRH + 2); k += HW * kTY_THREADS) {
+    for (int k = hx + ty * HW; k < 2 * (RH + 2); k += HW * TROWS) {
         E[k & 1][k >> 1][0] = 0.f;
         E[k & 1][k >> 1][HW + 1] = 0.f;
     }
-    for (int k = hx + ty * HW; k < 2 * (HW + 2); k += HW * kTY_THREADS) {
+    for (int k = hx + ty * HW; k < 2 * (HW + 2); k += HW * TROWS) {
         E[k & 1][0][k >> 1] = 0.f;
-        E[k & 1][kRH + 1][k >> 1] = 0.f;
+        E[k & 1][RH + 1][k >> 1] = 0.f;
     }
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
@@ -519,7 +543,7 @@ __device__ __forceinline__ bool sor_body(const IntraPlane &P, int pl, int lt, co
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
         const int ly = ly0 + k, gy = gy0 + ly;
-        if (ly < kHL || ly >= kHL + kTY || gy >= H) continue;
+        if (ly < kHL || ly >= kHL + TY || gy >= H) continue;
         const int sw = k & 1;
         const float v0 = sw ? ec[k][1] : ec[k][0], v1 = sw ? ec[k][0] : ec[k][1];
         float *o = eout + (size_t)gy * pitch + gxp;
@@ -678,11 +702,12 @@ __device__ __forceinline__ int sweep_plane(const IntraJobs &J, int b, int &lt)
 }
 
 // The pair count i handed on by the first CTA of a sweep launch (one
-// thread, before its sweeps): parity 0 to the pair's second launch, parity
-// 1 as i + 1 to the next pair's first launch, with whether the sweep loop
-// goes on (the next pair has launches left in this cycle).  Each word is
-// written while no launch that reads it runs.
-template <int PAR>
+// thread, after its sweeps): parity 0 to the pair's second launch, parity
+// 1 as i + 1 to the next pair's first launch, with whether its loop goes
+// on: the planned pairs of the all-plane phase (pa), or of the chroma
+// phase after it (CHROMA: pairs pa .. pa + pb - 1); never beyond
+// kMaxPairs.  Each word is written while no launch that reads it runs.
+template <int PAR, bool CHROMA>
 __device__ __forceinline__ void pair_step(const IntraJobs &J)
 {
     if (blockIdx.x != 0 || threadIdx.x != 0 || threadIdx.y != 0) return;
@@ -693,30 +718,32 @@ __device__ __forceinline__ void pair_step(const IntraJobs &J)
         return;
     }
     c->iter[0] = i + 1;
-    const int go = 2 * (i + 1) < c->maxl ? 1 : 0;
-    c->go_inner = go;
-    if (J.h_inner) cudaGraphSetConditional(J.h_inner, go);
+    const int end = CHROMA ? c->pairs[0] + c->pairs[1] : c->pairs[0];
+    const int go = (i + 1 < end && i + 1 < kMaxPairs) ? 1 : 0;
+    const unsigned long long h = CHROMA ? J.h_inner_c : J.h_inner;
+    if (h) cudaGraphSetConditional(h, go);
 }
 
 // S red-black sweeps of launch it = 2 i + PAR of the cycle, over the
 // planes whose launch count exceeds it (from e = 0 at it = 0, else from
-// the plane's current correction in e[PAR]).
-template <int RW, int PAR>
-__global__ void __launch_bounds__(RW / 2 * kTY_THREADS, 1) intra_sor_kernel(const __grid_constant__ IntraJobs J)
+// the plane's current correction in e[PAR]).  RH = kRHc: the chroma
+// phase's launches (its own regions of the chroma planes).
+template <int RW, int RH, int PAR>
+__global__ void __launch_bounds__(RW / 2 * (RH / kRows), 1) intra_sor_kernel(const __grid_constant__ IntraJobs J)
 {
-    pair_step<PAR>(J);
     int lt;
     const int pl = sweep_plane(J, blockIdx.x, lt);
-    sor_body<RW, PAR>(J.p[pl], pl, lt, J.ctl);
+    sor_body<RW, RH, PAR>(J.p[pl], pl, lt, J.ctl);
+    pair_step<PAR, RH == kRHc>(J);
 }
 
 template <int PAR>
 __global__ void __launch_bounds__(32 * kQWarps, 1) intra_sor4_kernel(const __grid_constant__ IntraJobs J)
 {
-    pair_step<PAR>(J);
     int lt;
     const int pl = sweep_plane(J, blockIdx.x, lt);
     sor4_body<PAR>(J.p[pl], pl, lt, J.ctl);
+    pair_step<PAR, false>(J);
 }
 
 }  // namespace
@@ -760,34 +787,43 @@ int residual_tiles(IntraJobs &J)
 
 // sweep regions of the variant per plane; returns the CTAs, sets the block
 // and the dynamic shared memory
+// (kChromaPhase: the chroma phase's launches: regions of 128 x 88 of the
+// chroma planes only)
+constexpr int kChromaPhase = 3;
 int sor_tiles(IntraJobs &J, int variant, dim3 &block, size_t &smem)
 {
     const int tx = variant == 1 ? sor_tx(112) : sor_tx(128);
+    const int ty = variant == kChromaPhase ? kRHc - 2 * kHL : kTY;
     int base = 0;
     // chroma planes first: they sweep longest, so the launches that sweep
     // them alone find their CTAs at the front of the grid
     for (int q = 0; q < J.n; ++q) {
         IntraPlane &P = J.p[J.n == 3 ? (q + 1) % 3 : q];
+        const bool skip = variant == kChromaPhase && q == J.n - 1;  // luma: not in the chroma phase
         P.tiles_x = (P.width + tx - 1) / tx;
         P.tile_base = base;
-        P.tiles = P.tiles_x * ((P.height + kTY - 1) / kTY);
+        P.tiles = skip ? 0 : P.tiles_x * ((P.height + ty - 1) / ty);
         base += P.tiles;
     }
-    block = variant == 2 ? dim3(32, kQWarps) : dim3((variant == 1 ? 112 : 128) / 2, kTY_THREADS);
-    smem = variant == 2 ? 0 : sor_smem_bytes(variant == 1 ? 112 : 128);
+    block = variant == 2 ? dim3(32, kQWarps)
+                         : dim3((variant == 1 ? 112 : 128) / 2, (variant == kChromaPhase ? kRHc : kRH) / kRows);
+    smem = variant == 2 ? 0 : sor_smem_bytes(variant == 1 ? 112 : 128, variant == kChromaPhase ? kRHc : kRH);
     return base;
 }
 
 const void *sor_kernel(int variant, int par)
 {
     if (variant == 1)
-        return par ? reinterpret_cast<const void *>(intra_sor_kernel<112, 1>)
-                   : reinterpret_cast<const void *>(intra_sor_kernel<112, 0>);
+        return par ? reinterpret_cast<const void *>(intra_sor_kernel<112, kRH, 1>)
+                   : reinterpret_cast<const void *>(intra_sor_kernel<112, kRH, 0>);
     if (variant == 2)
         return par ? reinterpret_cast<const void *>(intra_sor4_kernel<1>)
                    : reinterpret_cast<const void *>(intra_sor4_kernel<0>);
-    return par ? reinterpret_cast<const void *>(intra_sor_kernel<128, 1>)
-               : reinterpret_cast<const void *>(intra_sor_kernel<128, 0>);
+    if (variant == kChromaPhase)
+        return par ? reinterpret_cast<const void *>(intra_sor_kernel<128, kRHc, 1>)
+                   : reinterpret_cast<const void *>(intra_sor_kernel<128, kRHc, 0>);
+    return par ? reinterpret_cast<const void *>(intra_sor_kernel<128, kRH, 1>)
+               : reinterpret_cast<const void *>(intra_sor_kernel<128, kRH, 0>);
 }
 
 }  // namespace
@@ -798,6 +834,11 @@ cudaError_t launch_intra_residual(IntraJobs &J, bool first, cudaStream_t st)
     if (n == 0) return cudaSuccess;
     intra_residual_kernel<<<n, kResThreads, 0, st>>>(J, first ? 1 : 0);
     return cudaGetLastError();
+}
+
+cudaError_t launch_intra_sor_chroma_pair(IntraJobs &J, cudaStream_t st)
+{
+    return launch_intra_sor_pair(J, kChromaPhase, st);
 }
 
 cudaError_t launch_intra_sor_pair(IntraJobs &J, int variant, cudaStream_t st)
@@ -977,12 +1018,44 @@ cudaError_t build_intra_graph(const IntraJobs &J0, int variant, cudaGraphExec_t 
     if ((e = cudaGraphAddKernelNode(&n_sor0, inner, nullptr, 0, &sp)) != cudaSuccess) return fail(e);
     sp.func = const_cast<void *>(sor_kernel(variant, 1));
     if ((e = cudaGraphAddKernelNode(&n_sor, inner, &n_sor0, 1, &sp)) != cudaSuccess) return fail(e);
+    // the chroma phase: a second loop of launch pairs over the chroma planes
+    // alone, with regions of their own (condition 1 at every pass of the
+    // outer body; each of its second launches sets it)
+    cudaGraphNode_t last = n_inner;
+    IntraJobs C = J;
+    if (J.chroma_phase && J.n == 3) {
+        if ((e = cudaGraphConditionalHandleCreate(&J.h_inner_c, body, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+            return fail(e);
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = J.h_inner_c;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t n_inner_c, n_c0, n_c1;
+        if ((e = cudaGraphAddNode(&n_inner_c, body, &n_inner, nullptr, 1, &cp)) != cudaSuccess) return fail(e);
+        cudaGraph_t cbody = cp.conditional.phGraph_out[0];
+        C = J;
+        dim3 cblock;
+        size_t csmem;
+        const int nc = sor_tiles(C, kChromaPhase, cblock, csmem);
+        cudaKernelNodeParams cq{};
+        cq.gridDim = dim3(nc);
+        cq.blockDim = cblock;
+        cq.sharedMemBytes = (unsigned)csmem;
+        void *a3[] = {&C};
+        cq.kernelParams = a3;
+        cq.func = const_cast<void *>(sor_kernel(kChromaPhase, 0));
+        if ((e = cudaGraphAddKernelNode(&n_c0, cbody, nullptr, 0, &cq)) != cudaSuccess) return fail(e);
+        cq.func = const_cast<void *>(sor_kernel(kChromaPhase, 1));
+        if ((e = cudaGraphAddKernelNode(&n_c1, cbody, &n_c0, 1, &cq)) != cudaSuccess) return fail(e);
+        last = n_inner_c;
+    }
     // the cycle's residual launch, after the sweeps
     IntraJobs R2 = J;
     residual_tiles(R2);
     void *a2[] = {&R2, &zero};
     kp.kernelParams = a2;
-    if ((e = cudaGraphAddKernelNode(&n_res, body, &n_inner, 1, &kp)) != cudaSuccess) return fail(e);
+    if ((e = cudaGraphAddKernelNode(&n_res, body, &last, 1, &kp)) != cudaSuccess) return fail(e);
     e = cudaGraphInstantiate(exec, g, 0);
     cudaGraphDestroy(g);
     return e;
@@ -1001,13 +1074,16 @@ int set_sor_variant(int v)
 // shared memory beyond the static limit.  Called once per device.
 cudaError_t intra_init()
 {
-    const void *k[4] = {reinterpret_cast<const void *>(intra_sor_kernel<128, 0>),
-                        reinterpret_cast<const void *>(intra_sor_kernel<128, 1>),
-                        reinterpret_cast<const void *>(intra_sor_kernel<112, 0>),
-                        reinterpret_cast<const void *>(intra_sor_kernel<112, 1>)};
-    for (int i = 0; i < 4; ++i) {
-        const cudaError_t e = cudaFuncSetAttribute(k[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)sor_smem_bytes(i < 2 ? 128 : 112));
+    const void *k[6] = {reinterpret_cast<const void *>(intra_sor_kernel<128, kRH, 0>),
+                        reinterpret_cast<const void *>(intra_sor_kernel<128, kRH, 1>),
+                        reinterpret_cast<const void *>(intra_sor_kernel<112, kRH, 0>),
+                        reinterpret_cast<const void *>(intra_sor_kernel<112, kRH, 1>),
+                        reinterpret_cast<const void *>(intra_sor_kernel<128, kRHc, 0>),
+                        reinterpret_cast<const void *>(intra_sor_kernel<128, kRHc, 1>)};
+    const size_t bytes[6] = {sor_smem_bytes(128), sor_smem_bytes(128), sor_smem_bytes(112), sor_smem_bytes(112),
+                             sor_smem_bytes(128, kRHc), sor_smem_bytes(128, kRHc)};
+    for (int i = 0; i < 6; ++i) {
+        const cudaError_t e = cudaFuncSetAttribute(k[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes[i]);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
