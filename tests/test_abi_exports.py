@@ -57,6 +57,10 @@ def test_host_only_entry_points(hv):
     c.fused_residual = 2
     assert L.hivc_decoder_bytes(ctypes.byref(c)) == 0
     c.fused_residual = 0
+    for bad in (0, 1001):  # the correction loop runs on the device: its cycle cap is bounded
+        c.max_cycles = bad
+        assert L.hivc_decoder_bytes(ctypes.byref(c)) == 0
+    c.max_cycles = 40
     c.block = 17
     assert L.hivc_decoder_bytes(ctypes.byref(c)) == 0
     h = ctypes.c_void_p()
