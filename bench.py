@@ -42,9 +42,9 @@ NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch on the FullHD
     # 4:2:0 GOP workload (profiles/*.md give the commands):
     # intra_sor_kernel over the three planes
-    "intra_sweeps": {"bytes": 28.02e6, "sha": "3c1b50fb60f2"},
+    "intra_sweeps": {"bytes": 28.02e6, "sha": "dbcd4b3ddf5a"},
     # pframe_kernel, one frame
-    "inter_pixels": {"bytes": 41.79e6, "sha": "55ab9c90df81"},
+    "inter_pixels": {"bytes": 41.57e6, "sha": "f98556f08c0f"},
     # block_eval_kernel, per frame of an 8-frame launch (49.57 MB / 8)
     "block_eval": {"bytes": 6.196e6, "sha": "62cb19a05736"},
 }

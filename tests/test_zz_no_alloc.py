@@ -5,7 +5,8 @@ loop in which an allocation could synchronise the device).  It must give the
 same plane as hivc_block_residual, which uses a caller workspace, on calls
 made one after another (the second call reuses the library's scratch array
 that the first one left behind), with or without a caller error word, and
-on a call exactly at its limits.
+on a call exactly at its limits; and calls after the first leave the
+device's free memory unchanged.
 
 This file is collected last on purpose: if it fails, a run that stops at the
 first failure has already run every other test."""
@@ -70,6 +71,26 @@ def test_without_a_caller_error_word():
         ref = _with_workspace(hv, res)
         assert np.all(np.isfinite(got))
         assert np.abs(got - ref).max() <= TOL_BLOCK
+
+
+def test_device_memory_unchanged_around_calls():
+    """After a first call (which loads the library's kernels and tables),
+    further calls leave the device's free memory unchanged: no allocation
+    by the library or by the runtime on its behalf."""
+    hv = hivc_module()
+    torch = torch_cuda()
+    rng = np.random.default_rng(24)
+    res = make_residual(rng, 320, 176, 16, 8.0, 64, kmax=48)
+    bp, pos, val = hv.device_residual(res)
+    r = torch.zeros((res.height, res.width), dtype=torch.float32, device="cuda")
+    hv.block_residual_static(res.width, res.height, res.block, bp, pos, val, r)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        hv.block_residual_static(res.width, res.height, res.block, bp, pos, val, r)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert np.all(np.isfinite(to_np(r)))
 
 
 def test_at_exactly_its_limits():
