@@ -54,6 +54,35 @@ def test_iframe_color_ragged(hv, W, H, frac, seed):
     assert np.array_equal(gpu[2].reshape(-1)[ifr.c_idx], ifr.cr_val.astype(np.float64))
 
 
+@pytest.mark.parametrize("W,H,cfrac,seed", [
+    (480, 272, 0.0075, 11),  # chroma mask at a quarter of luma's: a long chroma phase
+    (480, 272, 0.06, 12),    # chroma denser than luma: luma sweeps longest, the chroma loop stays empty
+    (202, 150, 0.015, 13),   # ragged planes with chroma regions cut by the edges
+])
+def test_iframe_chroma_phase(hv, W, H, cfrac, seed):
+    """4:2:0 solves run the launches that sweep only the chroma planes on
+    regions of their own.  Whatever the split between the all-plane and the
+    chroma phase, the result matches the oracle, and the graph the device
+    steers gives the same bits as the same launches sent one by one from
+    the host (per-kernel timing mode)."""
+    srcs, ifr = make_iframe_only(seed, W, H, 0.03, chroma=True, chroma_mask_frac=cfrac)
+    got = []
+    for timing in (False, True):
+        dec = hv.Decoder(W, H, chroma=True, iframe_tol=1e-9, timing=timing)
+        out = hv.alloc_out(W, H)
+        dec.decode_iframe(hv.device_iframe(ifr), out)
+        st = dec.sync()
+        got.append((_planes(dec), st.sweeps, st.cycles))
+        dec.close()
+    assert got[0][1:] == got[1][1:]
+    for a, b in zip(got[0][0], got[1][0]):
+        assert np.array_equal(a, b)
+    od = oracle.OracleDecoder(W, H, True)
+    rec, _ = od.decode_iframe(ifr)
+    for p in range(3):
+        assert np.abs(got[0][0][p] - rec[p]).max() <= TOL_INTRA, p
+
+
 def test_iframe_with_residual(hv):
     srcs, ifr = make_iframe_only(5, 160, 96, 0.03, chroma=True, residual={"lam_y": 8.0, "lam_c": 4.0})
     dec = hv.Decoder(160, 96, chroma=True)
