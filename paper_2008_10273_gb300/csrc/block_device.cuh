@@ -21,6 +21,42 @@ __device__ __forceinline__ const float *green_rows(const BlockTables &t, int w, 
     return t.G + __ldg(t.goff + shape_index(w, h));
 }
 
+// The 16 x 16 block is symmetric under the 8 symmetries of the square
+// (reflections x -> 15 - x, y -> 15 - y, the transpose), and so is its
+// operator with mirrored boundaries: G[p, q] = G[s(p), s(q)] for each such
+// s.  Every point p maps to one of the 36 points (bx, by), bx <= by <= 7,
+// by s = (reflect x if rx) then (reflect y if ry) then (transpose if tr);
+// bi = by (by + 1) / 2 + bx numbers them.  The tables are built so that
+// this holds bit for bit (the rows of the 36 points define the others).
+struct Sym16 {
+    int bi, rx, ry, tr;
+};
+__host__ __device__ __forceinline__ Sym16 sym16(int p)
+{
+    const int px = p & 15, py = p >> 4;
+    Sym16 s;
+    s.rx = px > 7;
+    s.ry = py > 7;
+    const int fx = s.rx ? 15 - px : px, fy = s.ry ? 15 - py : py;
+    s.tr = fx > fy;
+    const int bx = s.tr ? fy : fx, by = s.tr ? fx : fy;
+    s.bi = by * (by + 1) / 2 + bx;
+    return s;
+}
+// s(q) for the symmetry of sym16(p)
+__host__ __device__ __forceinline__ int sym16_apply(const Sym16 &s, int q)
+{
+    int x = q & 15, y = q >> 4;
+    x = s.rx ? 15 - x : x;
+    y = s.ry ? 15 - y : y;
+    return s.tr ? x * 16 + y : y * 16 + x;
+}
+// Rows of the 36 points in 4 orientations o = rx + 2 tr, so that a point's
+// row is read as contiguous runs: G[p, (x, y)] = G16o[o][bi][ry ? 15 - y :
+// y][x] (256 floats per row, y * 16 + x).
+constexpr int kSym16Rows = 36;
+constexpr size_t kSym16Floats = (size_t)4 * kSym16Rows * 256;
+
 // the job holding global block gb: the last k with p[k].block_base <= gb
 // (block bases increase with k; binary search over at most kMaxJobs)
 __device__ __forceinline__ int find_job(const BlockJobs &J, int gb)

@@ -64,6 +64,7 @@ struct BlockJobs {
 // once per device) and the SM count of the device.
 struct BlockTables {
     const float *G;     // rows of G per shape, padded to multiples of 8 floats
+    const float *G16o;  // the 16 x 16 shape's rows of 36 points in 4 orientations (block_device.cuh)
     const double *G64;  // the same in double precision (FP64 re-solves)
     const int *goff;    // offset of shape (w, h) at (w-1)*16 + (h-1)
     int sms;

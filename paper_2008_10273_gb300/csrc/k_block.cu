@@ -45,10 +45,13 @@ constexpr int kGSize = 2283904;  // sum over shapes of N * rowlen(N)
 static __device__ __align__(256) float d_G[kNumOps * kGSize];
 static __device__ __align__(256) double d_G64[kNumOps * kGSize];
 static __device__ int d_goff[256];
+static __device__ __align__(256) float d_G16o[kNumOps * kSym16Floats];
 
 std::mutex g_tab_mu;
 BlockTables g_tabs[64][kNumOps];
 uint64_t g_tab_devices = 0;  // bit d: tables uploaded to device d
+
+void symmetrise16(std::vector<float> &G, std::vector<double> &G64, int off);
 
 // Tables of operator op: the Green's eigenvalues are 1/mu (harmonic) or
 // 1/mu^2 (biharmonic, A = L^2); the eigenvectors, and with them the
@@ -93,6 +96,47 @@ void build_tables(int op, std::vector<float> &G, std::vector<double> &G64, std::
                     G64[off + i * rl + j] = g;
                 }
             off += N * rl;
+        }
+    symmetrise16(G, G64, goff[shape_index(16, 16)]);
+}
+
+// The 16 x 16 rows agree with the symmetries of the square only up to
+// rounding (the sums above run in different orders for a pair and its
+// images).  Each entry takes the value of one fixed member of its orbit
+// under those symmetries and under (p, q) -> (q, p), so that the table is
+// exactly symmetric and exactly invariant, and the 36 rows of the compact
+// table give back every row bit for bit.
+void symmetrise16(std::vector<float> &G, std::vector<double> &G64, int off)
+{
+    const std::vector<double> g0(G64.begin() + off, G64.begin() + off + 256 * 256);
+    for (int p = 0; p < 256; ++p)
+        for (int q = 0; q < 256; ++q) {
+            int best = 1 << 30;
+            for (int k = 0; k < 8; ++k) {
+                const Sym16 s{0, k & 1, (k >> 1) & 1, k >> 2};
+                const int a = sym16_apply(s, p), b = sym16_apply(s, q);
+                best = std::min(best, std::min(a * 256 + b, b * 256 + a));
+            }
+            G64[off + p * 256 + q] = g0[best];
+            G[off + p * 256 + q] = (float)g0[best];
+        }
+}
+
+// The compact 16 x 16 table: for each of the 36 points b = (bx, by),
+// bx <= by <= 7, and each orientation o = rx + 2 tr, the row of b read in
+// the order that a point mapped to b by (rx, ry = 0, tr) needs.
+void build_sym16(const std::vector<float> &G, int off, std::vector<float> &S)
+{
+    S.assign(kSym16Floats, 0.f);
+    for (int by = 0; by < 8; ++by)
+        for (int bx = 0; bx <= by; ++bx) {
+            const int bi = by * (by + 1) / 2 + bx, b = by * 16 + bx;
+            for (int o = 0; o < 4; ++o)
+                for (int y = 0; y < 16; ++y)
+                    for (int x = 0; x < 16; ++x) {
+                        const Sym16 s{bi, o & 1, 0, o >> 1};
+                        S[((size_t)(o * kSym16Rows + bi) * 16 + y) * 16 + x] = G[off + b * 256 + sym16_apply(s, y * 16 + x)];
+                    }
         }
 }
 
@@ -985,10 +1029,15 @@ __global__ void __launch_bounds__(kCoefThreads, 3) block_coef_kernel(const __gri
 // QC (coefficient mode): c_j from the dead-zone indices, a transmitted, no
 // overwrite at the points; K = 0 gives r = a.  An index -128 gives a zero
 // block and the flag kFlagQ.
+// A 16 x 16 block reads its rows from the compact table S (36 points in 4
+// orientations, 147 KB, which stays in L1): the lane owning point p sends
+// the offset of p's row in S and whether the row's y order is reversed
+// (bit 16) in place of p; rows 0..7 of a point's row are then rows 15..8 of
+// the stored one, in the same 512-byte span.  Other shapes send p * rl.
 template <bool TWO, bool QC>
 __device__ __forceinline__ void eval_block(const BlockPlane &P, const BlockGeom &g, const float *__restrict__ G,
-                                           float a0, float a1, float *R0, float *R1, int pitch, int lane,
-                                           uint32_t *flags)
+                                           const float *__restrict__ S, float a0, float a1, float *R0, float *R1,
+                                           int pitch, int lane, uint32_t *flags)
 {
     const int K = g.K, w = g.w, N = g.w * g.h, rl = g_rowlen(N);
     // lane l covers pixels 4l .. 4l+3 and 128 + 4l .. 128 + 4l + 3: each
@@ -996,6 +1045,10 @@ __device__ __forceinline__ void eval_block(const BlockPlane &P, const BlockGeom 
     // Green's row (four 128-byte lines)
     const int q0 = 4 * lane, q1 = 128 + 4 * lane;
     const bool act = q0 < N, act1 = q1 < N;
+    const bool sym = S != nullptr && N == 256;
+    const float *__restrict__ Gb = sym ? S : G;
+    // row offsets of the lane's pixels, as stored and y-reversed
+    const int lo_n = q0, lo_r = (15 - (lane >> 2)) * 16 + 4 * (lane & 3);
     float r0[8], r1[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
@@ -1033,16 +1086,22 @@ __device__ __forceinline__ void eval_block(const BlockPlane &P, const BlockGeom 
         prev = __shfl_sync(0xffffffffu, p, 31);
         if (!valid) break;
         const int n = min(32, K - j0);
-        const float *Gq = G + q0;  // + 128 for the second half
+        int key = p * rl;
+        if (sym) {
+            const Sym16 t = sym16(p);
+            key = ((t.rx + 2 * t.tr) * kSym16Rows + t.bi) * 256 + (t.ry << 16);
+        }
 #pragma unroll 4
         for (int u = 0; u < n; ++u) {
             const float cu0 = __shfl_sync(0xffffffffu, c0, u);
             const float cu1 = TWO ? __shfl_sync(0xffffffffu, c1, u) : 0.f;
-            const int pu = __shfl_sync(0xffffffffu, p, u);
+            const int ku = __shfl_sync(0xffffffffu, key, u);
             if (act) {
-                const float *row = Gq + pu * rl;
+                const bool rev = ku >> 16;
+                const float *row = Gb + (ku & 0xffff) + (rev ? lo_r : lo_n);
                 const float4 lo = __ldg(reinterpret_cast<const float4 *>(row));
-                const float4 hi = act1 ? __ldg(reinterpret_cast<const float4 *>(row + 128)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 hi = act1 ? __ldg(reinterpret_cast<const float4 *>(row + (rev ? -128 : 128)))
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
                 const float gv[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
@@ -1240,13 +1299,14 @@ __global__ void __launch_bounds__(128, 8) block_eval_kernel(const __grid_constan
     float *R0 = P.r[0] + (size_t)g.y0 * pitch + g.x0;
     float *R1 = two && P.r[1] ? P.r[1] + (size_t)g.y0 * pitch + g.x0 : nullptr;
     const float *G = green_rows(tab, g.w, g.h);
+    const float *S = tab.G16o;
     if (QC) {
         // no coefficient stage ran: block pointer errors are reported here
         // (the block reconstructs as zero)
         if (g.bad && lane == 0 && flags) atomicOr(flags, g.bad);
-        eval_block<false, true>(P, g, G, g.bad ? 0.f : a0, 0.f, R0, nullptr, pitch, lane, flags);
-    } else if (two) eval_block<true, false>(P, g, G, a0, a1, R0, R1, pitch, lane, flags);
-    else eval_block<false, false>(P, g, G, a0, a1, R0, R1, pitch, lane, flags);
+        eval_block<false, true>(P, g, G, S, g.bad ? 0.f : a0, 0.f, R0, nullptr, pitch, lane, flags);
+    } else if (two) eval_block<true, false>(P, g, G, S, a0, a1, R0, R1, pitch, lane, flags);
+    else eval_block<false, false>(P, g, G, S, a0, a1, R0, R1, pitch, lane, flags);
 }
 
 
@@ -1263,16 +1323,24 @@ cudaError_t ensure_block_tables()
     static std::vector<float> G[kNumOps];
     static std::vector<double> G64[kNumOps];
     static std::vector<int> goff;
-    float *dG = nullptr;
+    static std::vector<float> S[kNumOps];
+    float *dG = nullptr, *dS = nullptr;
     double *dG64 = nullptr;
     const int *dgoff = nullptr;
     if ((e = cudaGetSymbolAddress((void **)&dG, d_G)) != cudaSuccess) return e;
     if ((e = cudaGetSymbolAddress((void **)&dG64, d_G64)) != cudaSuccess) return e;
     if ((e = cudaGetSymbolAddress((void **)&dgoff, d_goff)) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void **)&dS, d_G16o)) != cudaSuccess) return e;
     int sms = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     for (int op = 0; op < kNumOps; ++op) {
-        if (G[op].empty()) build_tables(op, G[op], G64[op], goff);
+        if (G[op].empty()) {
+            build_tables(op, G[op], G64[op], goff);
+            build_sym16(G[op], goff[shape_index(16, 16)], S[op]);
+        }
+        if ((e = cudaMemcpy(dS + (size_t)op * kSym16Floats, S[op].data(), S[op].size() * sizeof(float),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return e;
         if ((e = cudaMemcpy(dG + (size_t)op * kGSize, G[op].data(), G[op].size() * sizeof(float),
                             cudaMemcpyHostToDevice)) != cudaSuccess)
             return e;
@@ -1282,6 +1350,7 @@ cudaError_t ensure_block_tables()
         BlockTables &t = g_tabs[dev][op];
         t.G = dG + (size_t)op * kGSize;
         t.G64 = dG64 + (size_t)op * kGSize;
+        t.G16o = dS + (size_t)op * kSym16Floats;
         t.goff = dgoff;
         t.sms = sms;
         t.amax = op == 1 ? 64.f : 8.f;
