@@ -189,6 +189,9 @@ struct hivc_decoder {
     // runs there while the intra frame decodes (fork and join events)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // the end of an intra frame, and of each deferred evaluation launch
+    cudaEvent_t ev_intra = nullptr;
+    std::vector<cudaEvent_t> ev_batch;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
     std::vector<cudaEvent_t> event_pool;
 };
@@ -480,6 +483,7 @@ hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out)
     if (cudaStreamCreateWithFlags(&d->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&d->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&d->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&d->ev_intra, cudaEventDisableTiming) != cudaSuccess ||
         cudaMemsetAsync(d->flags, 0, 4 * kStatusWords, d->stream) != cudaSuccess ||
         cudaMemsetAsync(d->ctl, 0, sizeof(IntraCtl), d->stream) != cudaSuccess ||
         (cfg->batch_frames > 0 &&
@@ -504,6 +508,8 @@ void hivc_decoder_destroy(hivc_decoder *d)
     if (d->side) cudaStreamDestroy(d->side);
     if (d->ev_fork) cudaEventDestroy(d->ev_fork);
     if (d->ev_join) cudaEventDestroy(d->ev_join);
+    if (d->ev_intra) cudaEventDestroy(d->ev_intra);
+    for (cudaEvent_t e : d->ev_batch) cudaEventDestroy(e);
     for (auto &pe : d->pending) {
         cudaEventDestroy(pe.second.first);
         cudaEventDestroy(pe.second.second);
@@ -957,10 +963,18 @@ hivc_status ensure_pool(hivc_decoder *d, size_t bytes, cudaStream_t st)
 
 // The block stage's results of an inter run: per frame its residual
 // planes (split path) and its block jobs (coefficient arrays in the pool).
+// After an intra frame the evaluation launches but the first wait for the
+// intra frame and then overlap the pixel kernels of the batch before them
+// (on the split path without layout groups).
+constexpr bool kDeferEval = true;
+
 struct RunBlocks {
     bool fused = false;  // the fused kernel evaluates the residual
+    bool defer = false;  // evaluation launches of batches after the first deferred
     std::vector<std::array<float *, 3>> planes;
     std::vector<BlockJobs> jobs;
+    std::vector<size_t> batch_first;  // index into ks of each launch's first frame
+    std::vector<BlockJobs> deferred;  // the deferred launches' jobs (batches 1, 2, ...)
 };
 
 // Whether every frame of the run goes through the fused kernel.
@@ -1048,16 +1062,23 @@ hivc_status inter_blocks(hivc_decoder *d, const hivc_frame *frames, const std::v
         }
         pdl = true;
         if (e == cudaSuccess && !rb.fused) {
-            Timed t(d, 5);
-            e = launch_block_eval(J, d->flags, st, !d->timing, &S.plan);
-            t.done(1);
+            if (rb.defer && rb.batch_first.size() > 1) {
+                rb.deferred.push_back(J);
+            } else {
+                Timed t(d, 5);
+                e = launch_block_eval(J, d->flags, st, !d->timing, &S.plan);
+                t.done(1);
+            }
         }
         J = BlockJobs{};
         J.op = d->cfg.op;
         return e;
     };
+    rb.batch_first.clear();
+    rb.deferred.clear();
     for (size_t k = 0; k < nf; ++k) {
         if (J.n + jobs[k].n > kMaxJobs && flush() != cudaSuccess) return HIVC_E_CUDA;
+        if (J.n == 0) rb.batch_first.push_back(k);
         for (int q = 0; q < jobs[k].n; ++q) {
             BlockPlane B = jobs[k].p[q];
             B.block_base = J.total_blocks;
@@ -1079,8 +1100,19 @@ hivc_status inter_blocks(hivc_decoder *d, const hivc_frame *frames, const std::v
 hivc_status inter_pixels(hivc_decoder *d, const hivc_frame *frames, const hivc_out *outs, const std::vector<int> &ks,
                          const RunBlocks &rb, bool pdl)
 {
+    size_t b = 1;  // the next deferred batch
     for (size_t k = 0; k < ks.size(); ++k) {
         const hivc_pframe *f = frames[ks[k]].p;
+        if (rb.defer && b < rb.batch_first.size() && k == rb.batch_first[b]) {
+            // the batch's evaluation ran on the side stream
+            if (cudaStreamWaitEvent(d->stream, d->ev_batch[b - 1], 0) != cudaSuccess) return HIVC_E_CUDA;
+            ++b;
+            const cudaError_t e = launch_pixels(d, f->flow, &outs[ks[k]], rb.planes[k].data(), false, false);
+            if (e != cudaSuccess) return HIVC_E_CUDA;
+            d->cur ^= 1;
+            d->st.frames += 1;
+            continue;
+        }
         // the first fused kernel waits for the block stage before it reads
         // the coefficients; each later one may read them at once
         const cudaError_t e = rb.fused ? launch_fused(d, f->flow, &outs[ks[k]], rb.jobs[k], pdl || k > 0, k > 0)
@@ -1115,12 +1147,31 @@ hivc_status decode_intra_then_run(hivc_decoder *d, const hivc_frame *frames, con
         return HIVC_E_CUDA;
     RunBlocks rb;
     rb.fused = fused_run(d, frames, outs, ks);
+    rb.defer = kDeferEval && !rb.fused && d->cfg.layout_groups == 0;
     const hivc_status sb = inter_blocks(d, frames, ks, d->side, false, rb);
     const bool joined = cudaEventRecord(d->ev_join, d->side) == cudaSuccess;
     intra = hivc_decode_iframe(d, frames[ki].i, &outs[ki]);
     if (!joined || cudaStreamWaitEvent(d->stream, d->ev_join, 0) != cudaSuccess) return HIVC_E_CUDA;
     if (intra != HIVC_OK && intra != HIVC_E_NOT_CONVERGED) return intra;
     if (sb != HIVC_OK) return sb;
+    if (!rb.deferred.empty()) {
+        // the deferred evaluations: after the intra frame, on the side
+        // stream, an event after each
+        while (d->ev_batch.size() < rb.deferred.size()) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return HIVC_E_CUDA;
+            d->ev_batch.push_back(e);
+        }
+        if (cudaEventRecord(d->ev_intra, d->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(d->side, d->ev_intra, 0) != cudaSuccess)
+            return HIVC_E_CUDA;
+        for (size_t b = 0; b < rb.deferred.size(); ++b) {
+            Timed t(d, 5);  // (counts only: the timing pass takes another path)
+            const cudaError_t e = launch_block_eval(rb.deferred[b], d->flags, d->side, b > 0, nullptr);
+            t.done(1);
+            if (e != cudaSuccess || cudaEventRecord(d->ev_batch[b], d->side) != cudaSuccess) return HIVC_E_CUDA;
+        }
+    }
     return inter_pixels(d, frames, outs, ks, rb, false);
 }
 

@@ -194,13 +194,13 @@ __device__ __forceinline__ bool last_cta(IntraCtl *c, int *s_flag)
 // plane above the tolerance sweeps towards the FP32 floor of the inner
 // solve (about 1e-5) or the remaining gap to the tolerance, whichever is
 // smaller, at the rate of optimally relaxed SOR, omega - 1.
-__device__ void plan_cycle(const IntraJobs &J, IntraCtl &c, bool first)
+// c is the launch's last CTA's shared-memory copy of the control block
+// (plan_cycle_cta), rb each plane's max |residual| of the launch.
+__device__ void plan_cycle(const IntraJobs &J, IntraCtl &c, const float *rb, bool first)
 {
     for (int p = 0; p < J.n; ++p) {
         if (!first && c.nl[p] == 0) continue;
-        // the max of every CTA's atomicMax, read (and cleared for the next
-        // launch) at L2, past any stale L1 line
-        const double v = (double)__uint_as_float(atomicExch(c.rbits + p, 0u));
+        const double v = (double)rb[p];
         c.res_pixels += (long long)J.p[p].width * J.p[p].height;
         if (first) {
             c.rn[p] = v;
@@ -272,6 +272,34 @@ __device__ void plan_cycle(const IntraJobs &J, IntraCtl &c, bool first)
     if (J.h_inner_c) cudaGraphSetConditional(J.h_inner_c, go);
 }
 
+// The plan, by the launch's last CTA: the control block is copied to
+// shared memory a word per thread (one round of loads instead of a chain
+// of round trips to L2 on the launch's tail), each plane's max |residual|
+// read (and cleared for the next launch) by an atomic at L2, past any
+// stale L1 line, then one thread plans, and the block goes back a word per
+// thread.  During the plan no other CTA of the launch touches the block
+// (they made their atomics before counting themselves done).
+constexpr int kCtlWords = sizeof(IntraCtl) / 4;
+static_assert(sizeof(IntraCtl) % 8 == 0, "the control block is copied in 4-byte words");
+__device__ __forceinline__ void plan_cycle_cta(const IntraJobs &J, bool first)
+{
+    __shared__ __align__(8) uint32_t s_words[kCtlWords];
+    __shared__ float s_rb[3];
+    uint32_t *g = reinterpret_cast<uint32_t *>(J.ctl);
+    const int t = threadIdx.x + threadIdx.y * blockDim.x, nt = blockDim.x * blockDim.y;
+    for (int k = t; k < kCtlWords; k += nt) s_words[k] = g[k];
+    if (t < 3) s_rb[t] = t < J.n ? __uint_as_float(atomicExch(J.ctl->rbits + t, 0u)) : 0.f;
+    __syncthreads();
+    IntraCtl &c = *reinterpret_cast<IntraCtl *>(s_words);
+    if (t == 0) {
+        c.rbits[0] = c.rbits[1] = c.rbits[2] = 0u;
+        c.done_ctas = 0;  // as the last CTA left it
+        plan_cycle(J, c, s_rb, first);
+    }
+    __syncthreads();
+    for (int k = t; k < kCtlWords; k += nt) g[k] = s_words[k];
+}
+
 // The control state of a new solve (one thread).
 __global__ void intra_ctl_init_kernel(IntraCtl *c, float om0, float om1, float om2, double tol, int max_cycles,
                                       int spl)
@@ -308,8 +336,17 @@ __device__ __forceinline__ long long to_fix(float h, float l)
 // 16 tile with a one-pixel halo is updated once per cell into shared
 // memory, as fixed-point integers (to_fix); the residual of a pixel is the
 // exact integer sum of its neighbours' differences, rounded once to FP32.
-// Planes that the plan leaves out this cycle (converged) are skipped.  The
-// launch's last CTA plans the next cycle.
+// Thread t takes the columns t % 16 + 16 j (j = 0..3) of tile row t / 16
+// (a warp reads 64 contiguous bytes per row and load, and its shared-memory
+// accesses hit consecutive words); threads 0..31 also take the same
+// columns of the halo rows above and below the tile, threads 32..63 a cell
+// of the halo columns left and right of it.  Every load of a thread is
+// issued before any of its arithmetic.  Cells outside the plane count as
+// 0 and are never written.  Planes that the plan leaves out this cycle
+// (converged) are skipped.  The launch's last CTA plans the next cycle.
+constexpr int kRQ = kRTW / 4;  // threads per tile row (4 columns each)
+static_assert(kRQ * kRTH == kResThreads && 2 * kRQ + 2 * kRTH <= kResThreads, "4 cells per thread");
+
 __global__ void __launch_bounds__(kResThreads) intra_residual_kernel(const __grid_constant__ IntraJobs J, int first)
 {
     __shared__ long long su[kRTH + 2][kRTW + 2];
@@ -326,47 +363,82 @@ __global__ void __launch_bounds__(kResThreads) intra_residual_kernel(const __gri
         const int up = c->upar[pl];
         const float *uh = P.uh[up], *ul = P.ul[up];
         float *uh_out = P.uh[up ^ 1], *ul_out = P.ul[up ^ 1];
-        const float *e = P.e[c->nl[pl] & 1];  // after the cycle's nl launches
+        const float *e = P.e[c->nl[pl] & 1];  // after the cycle's nl launches; zero on the mask
         const bool ff = P.ff != 0;
-        for (int k = threadIdx.x; k < (kRTH + 2) * (kRTW + 2); k += kResThreads) {
-            const int ly = k / (kRTW + 2), lx = k - ly * (kRTW + 2);
-            const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
-            float h = 0.f, l = 0.f;
-            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-                const int i = gy * pitch + gx;
-                h = uh[i];
-                l = ff ? ul[i] : 0.f;
-                if (add_e) {
-                    const float d = e[i];  // zero on the mask
-                    if (ff) ff_add(h, l, d, h, l);
-                    else h = __fadd_rn(h, d);
-                    if (lx >= 1 && lx <= kRTW && ly >= 1 && ly <= kRTH) {
-                        uh_out[i] = h;
-                        if (ff) ul_out[i] = l;
-                    }
-                }
+        const int t = threadIdx.x, ty = t / kRQ, tx = t % kRQ;
+        const int gy = y0 + ty, gx = x0 + tx;
+        const bool rin = gy < H;
+        const size_t i = (size_t)gy * pitch + gx;  // column j at i + kRQ j
+        // the halo: row hr (0 above, kRTH + 1 below) at the thread's
+        // columns, or the cell of column hc (0 left, kRTW + 1 right) in tile
+        // row ck
+        const bool hrow = t < 2 * kRQ, hcol = !hrow && t < 2 * kRQ + 2 * kRTH;
+        const int hr = t < kRQ ? 0 : kRTH + 1, hy = y0 - 1 + hr;
+        const int ck = (t - 2 * kRQ) % kRTH, hc = t - 2 * kRQ < kRTH ? 0 : kRTW + 1;
+        const int cy = y0 + ck, cx = x0 - 1 + hc;
+        const bool hin = hrow && hy >= 0 && hy < H;
+        const bool cin = hcol && cy < H && cx >= 0 && cx < W;
+        const size_t ih = (size_t)hy * pitch + gx, ic = (size_t)cy * pitch + cx;
+        float h[4], l[4], d[4], hh[4], hl[4], hd[4];
+        uint8_t m[4];
+        float ch = 0.f, cl = 0.f, cd = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool in = rin && gx + kRQ * j < W, inh = hin && gx + kRQ * j < W;
+            h[j] = in ? __ldg(uh + i + kRQ * j) : 0.f;
+            l[j] = in && ff ? __ldg(ul + i + kRQ * j) : 0.f;
+            d[j] = in && add_e ? __ldg(e + i + kRQ * j) : 0.f;
+            m[j] = in ? __ldg(P.mask + i + kRQ * j) : 1;
+            hh[j] = inh ? __ldg(uh + ih + kRQ * j) : 0.f;
+            hl[j] = inh && ff ? __ldg(ul + ih + kRQ * j) : 0.f;
+            hd[j] = inh && add_e ? __ldg(e + ih + kRQ * j) : 0.f;
+        }
+        if (cin) {
+            ch = __ldg(uh + ic);
+            if (ff) cl = __ldg(ul + ic);
+            if (add_e) cd = __ldg(e + ic);
+        }
+        // u + e of one cell (cells outside the plane hold 0 and stay 0; e
+        // is 0 there), into h, l; returns it as fixed point
+        auto update = [ff, add_e](float &h, float &l, float d) {
+            if (add_e) {
+                if (ff) ff_add(h, l, d, h, l);
+                else h = __fadd_rn(h, d);
             }
-            su[ly][lx] = to_fix(h, l);
+            return to_fix(h, l);
+        };
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            su[ty + 1][tx + kRQ * j + 1] = update(h[j], l[j], d[j]);
+            if (hrow) su[hr][tx + kRQ * j + 1] = update(hh[j], hl[j], hd[j]);
+        }
+        if (hcol) su[ck + 1][hc] = update(ch, cl, cd);
+        if (add_e) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (rin && gx + kRQ * j < W) {
+                    uh_out[i + kRQ * j] = h[j];
+                    if (ff) ul_out[i + kRQ * j] = l[j];
+                }
         }
         __syncthreads();
         float rmax = 0.f;
-        for (int k = threadIdx.x; k < kRTH * kRTW; k += kResThreads) {
-            const int ly = k / kRTW, lx = k - ly * kRTW;
-            const int gx = x0 + lx, gy = y0 + ly;
-            if (gx >= W || gy >= H) continue;
-            const int i = gy * pitch + gx;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int x = gx + kRQ * j, lx = tx + kRQ * j + 1;
+            if (!rin || x >= W) continue;
             float r = 0.f;
-            if (!P.mask[i]) {
+            if (!m[j]) {
                 // sum_j (u_j - u_i), exact in fixed point, rounded once
-                const long long uc = su[ly + 1][lx + 1];
+                const long long uc = su[ty + 1][lx];
                 long long acc = 0;
-                if (gx > 0) acc += su[ly + 1][lx] - uc;
-                if (gx < W - 1) acc += su[ly + 1][lx + 2] - uc;
-                if (gy > 0) acc += su[ly][lx + 1] - uc;
-                if (gy < H - 1) acc += su[ly + 2][lx + 1] - uc;
+                if (x > 0) acc += su[ty + 1][lx - 1] - uc;
+                if (x < W - 1) acc += su[ty + 1][lx + 1] - uc;
+                if (gy > 0) acc += su[ty][lx] - uc;
+                if (gy < H - 1) acc += su[ty + 2][lx] - uc;
                 r = __ll2float_rn(acc) * kUnfix;
             }
-            P.res[i] = r;
+            P.res[i + kRQ * j] = r;
             rmax = fmaxf(rmax, fabsf(r));
         }
         for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
@@ -379,7 +451,7 @@ __global__ void __launch_bounds__(kResThreads) intra_residual_kernel(const __gri
         }
     }
     if (!last_cta(c, &s_last)) return;
-    if (threadIdx.x == 0) plan_cycle(J, *c, first != 0);
+    plan_cycle_cta(J, first != 0);
 }
 
 // S red-black SOR sweeps on (-L_UU) e = res in a shared-memory tile.
