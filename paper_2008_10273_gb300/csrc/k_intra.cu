@@ -66,8 +66,10 @@ __host__ __device__ constexpr size_t sor_smem_bytes(int rw, int rh = kRH)
 constexpr int kMaxPairs = 1 << 14;
 constexpr int kMaxCycles = 1000;
 
-constexpr int kResThreads = 256;
-constexpr int kRTW = 64, kRTH = 16;  // residual tile
+// residual tile: 64 x 20 (FullHD 4:2:0 planes split into whole tiles
+// vertically, 2,430 of them: 4 waves of 4 CTAs per SM on 152 SMs)
+constexpr int kRTW = 64, kRTH = 20;
+constexpr int kResThreads = kRTW / 4 * kRTH;
 
 __device__ __forceinline__ int find_plane(const IntraJobs &J, int t)
 {
@@ -333,13 +335,13 @@ __device__ __forceinline__ long long to_fix(float h, float l)
 
 // u_out = u_in + e (unknown pixels; float-float), res = (L u_out)_i, and the
 // max |res| per plane; first: res = (L u)_i of the starting iterate.  A 64 x
-// 16 tile with a one-pixel halo is updated once per cell into shared
+// 20 tile with a one-pixel halo is updated once per cell into shared
 // memory, as fixed-point integers (to_fix); the residual of a pixel is the
 // exact integer sum of its neighbours' differences, rounded once to FP32.
 // Thread t takes the columns t % 16 + 16 j (j = 0..3) of tile row t / 16
 // (a warp reads 64 contiguous bytes per row and load, and its shared-memory
 // accesses hit consecutive words); threads 0..31 also take the same
-// columns of the halo rows above and below the tile, threads 32..63 a cell
+// columns of the halo rows above and below the tile, threads 32..71 a cell
 // of the halo columns left and right of it.  Every load of a thread is
 // issued before any of its arithmetic.  Cells outside the plane count as
 // 0 and are never written.  Planes that the plan leaves out this cycle
@@ -347,7 +349,7 @@ __device__ __forceinline__ long long to_fix(float h, float l)
 constexpr int kRQ = kRTW / 4;  // threads per tile row (4 columns each)
 static_assert(kRQ * kRTH == kResThreads && 2 * kRQ + 2 * kRTH <= kResThreads, "4 cells per thread");
 
-__global__ void __launch_bounds__(kResThreads) intra_residual_kernel(const __grid_constant__ IntraJobs J, int first)
+__global__ void __launch_bounds__(kResThreads, 4) intra_residual_kernel(const __grid_constant__ IntraJobs J, int first)
 {
     __shared__ long long su[kRTH + 2][kRTW + 2];
     __shared__ float red[kResThreads / 32];
@@ -843,7 +845,7 @@ cudaError_t launch_intra_ctl_init(const IntraJobs &J, const float *omega0, doubl
 
 namespace {
 
-// residual tiles of 64 x 16 per plane
+// residual tiles of kRTW x kRTH per plane
 int residual_tiles(IntraJobs &J)
 {
     int base = 0;
