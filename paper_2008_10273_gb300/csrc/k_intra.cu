@@ -200,18 +200,19 @@ __device__ __forceinline__ bool last_cta(IntraCtl *c, int *s_flag)
 // (plan_cycle_cta), rb each plane's max |residual| of the launch.
 __device__ void plan_cycle(const IntraJobs &J, IntraCtl &c, const float *rb, bool first)
 {
+    // (single precision throughout: the plan needs a few digits, and one
+    // thread's chain of double-precision divisions, pow and log would sit on
+    // every cycle's tail; rn holds FP32 values)
     for (int p = 0; p < J.n; ++p) {
         if (!first && c.nl[p] == 0) continue;
-        const double v = (double)rb[p];
+        const float v = rb[p];
         c.res_pixels += (long long)J.p[p].width * J.p[p].height;
         if (first) {
             c.rn[p] = v;
-            c.rate[p] = (double)c.omega[p] - 1.0;
+            c.rate[p] = c.omega[p] - 1.f;
             continue;
         }
-        // (single precision: the plan needs a few digits, and one thread's
-        // chain of double-precision pow/log would sit on every cycle's tail)
-        const float q = (float)(v / fmax(c.rn[p], 1e-30));
+        const float q = v / fmaxf((float)c.rn[p], 1e-30f);
         c.rn[p] = v;
         const int S = c.nl[p] * c.spl;
         c.sweeps[p] += S;
@@ -237,9 +238,10 @@ __device__ void plan_cycle(const IntraJobs &J, IntraCtl &c, const float *rb, boo
     bool conv = true;
     for (int p = 0; p < J.n; ++p) {
         c.nl[p] = 0;
+        // (the test against the tolerance itself in double precision)
         conv = conv && c.rn[p] <= c.tol;
         if (!(c.rn[p] > c.tol)) continue;
-        const float target = fmaxf(1e-5f, (float)(0.3 * c.tol / c.rn[p]));
+        const float target = fmaxf(1e-5f, 0.3f * (float)c.tol / (float)c.rn[p]);
         const float rt = fminf(fmaxf((float)c.rate[p], 0.05f), 0.995f);
         int sw = (int)ceilf(logf(target) / logf(rt));
         sw = min(max(sw, c.spl), 600);
