@@ -114,6 +114,60 @@ def test_batch_two_decoders_interleaved(hv):
     assert np.array_equal(_planes(db)[0], rb[-1][0])
 
 
+def _frame_list(hv, gops):
+    """The frames of consecutive GOPs of one decoder, as (type, device frame)."""
+    fr = []
+    for g in gops:
+        fr.append(("i", hv.device_iframe(g.iframe)))
+        fr += [("p", hv.device_pframe(p)) for p in g.pframes]
+    return fr
+
+
+def _per_frame_list(hv, frames, W, H, chroma):
+    """uint8 outputs after every frame of the list and the last reference planes,
+    one call per frame."""
+    dec = hv.Decoder(W, H, chroma=chroma)
+    out = hv.alloc_out(W, H, chroma=chroma)
+    outs = []
+    for kind, f in frames:
+        (dec.decode_iframe if kind == "i" else dec.decode_pframe)(f, out)
+        dec.sync()
+        outs.append([to_np(o).copy() for o in out])
+    return outs, _planes(dec)
+
+
+def test_batch_long_runs_two_decoders(hv):
+    """Two GOPs of 13 frames back to back on one 4:2:0 decoder (each run
+    needs two evaluation launches: the second waits for its intra frame and
+    overlaps the first batch's pixel kernels) interleaved with a grey
+    decoder's GOP of 21 frames (two launches of up to 16 jobs), all in one
+    call: every output equals the decoder's own frame-by-frame decoding."""
+    fa = _frame_list(hv, [make_gop(45, 160, 90, n_frames=13), make_gop(46, 160, 90, n_frames=13)])
+    fb = _frame_list(hv, [make_gop(47, 96, 64, n_frames=21, chroma=False)])
+    oa, ra = _per_frame_list(hv, fa, 160, 90, True)
+    ob, rb = _per_frame_list(hv, fb, 96, 64, False)
+    da = hv.Decoder(160, 90, chroma=True)
+    db = hv.Decoder(96, 64, chroma=False)
+    decs, frames, outs, tags = [], [], [], []
+    for t in range(max(len(fa), len(fb))):
+        for who, fl, d, ch, (W, H) in (("a", fa, da, True, (160, 90)), ("b", fb, db, False, (96, 64))):
+            if t < len(fl):
+                decs.append(d)
+                frames.append(fl[t])
+                outs.append(hv.alloc_out(W, H, chroma=ch))
+                tags.append((who, t))
+    hv.decode_batch(decs, frames, outs)
+    da.sync()
+    db.sync()
+    for (who, t), out in zip(tags, outs):
+        ref = oa if who == "a" else ob
+        for p, o in enumerate(out):
+            assert np.array_equal(to_np(o), ref[t][p]), (who, t, p)
+    for p, g in enumerate(_planes(da)):
+        assert np.array_equal(g, ra[p]), p
+    assert np.array_equal(_planes(db)[0], rb[0])
+
+
 def test_batch_rejects_a_bad_frame(hv):
     """An inter run is checked before any of it is launched: an output
     plane narrower than the frame makes the call fail with HIVC_E_INVALID."""
