@@ -115,6 +115,14 @@ typedef struct {
                                frame; 0 (default): residual planes
                                (evaluation kernel, then the pixel kernel).
                                Both give the same bits */
+    int32_t flat_start;     /* 0 (default): the intra solve starts from a
+                               coarse solution (planes of at least 32 x 32):
+                               the mask restricted to 2 x 2 cells, one
+                               correction cycle on that half-size problem,
+                               then bilinear prolongation to the unknown
+                               pixels; 1: from the mean of the mask values.
+                               Only the start differs: both stop at the same
+                               tolerance of Eq. 1 */
 } hivc_config;
 
 /* Intra mask of one plane: n >= 1 sorted, unique linear indices y*w + x. */

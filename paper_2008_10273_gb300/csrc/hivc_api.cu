@@ -20,6 +20,9 @@ using namespace hivc;
 namespace {
 
 constexpr int kPitchAlign = 32;  // elements
+// sweeps of the coarse start's one cycle, at most (a start needs the smooth
+// error only, which the half-size problem loses fast)
+constexpr int kCoarseSweeps = 24;
 // the layout the Python binding mirrors
 static_assert(sizeof(hivc_stats) == 192 && offsetof(hivc_stats, kernel_pixels) == 120, "hivc_stats layout");
 
@@ -71,7 +74,7 @@ bool config_ok(const hivc_config *c)
            (c->chroma >= 0 && c->chroma <= 2) && c->block >= 1 && c->block <= kMaxB && (c->op == 0 || c->op == 1) &&
            (c->precision == 0 || c->precision == 1) && c->iframe_tol >= 0.0 && c->max_cycles >= 1 && c->max_cycles <= 1000 &&
            c->cond_threshold >= 0.0 && (c->layout_groups == 0 || c->layout_groups == 1) && c->batch_frames >= 0 &&
-           (c->fused_residual == 0 || c->fused_residual == 1) &&
+           (c->fused_residual == 0 || c->fused_residual == 1) && (c->flat_start == 0 || c->flat_start == 1) &&
            c->batch_frames <= 4096;
 }
 
@@ -168,6 +171,14 @@ struct hivc_decoder {
     IntraCtl *ctl = nullptr, *tune_ctl = nullptr, *h_ctl = nullptr;
     cudaGraphExec_t igraph = nullptr;
     int igraph_variant = -1;
+    // the coarse start: half-size planes (iterate ping-pong, residual,
+    // correction ping-pong, mask), their control state (and its pinned host
+    // copy) and correction-loop graph
+    int cw[3]{}, chh[3]{}, cpitch[3]{};
+    float *cu[2][3]{}, *cres[3]{}, *ce[2][3]{};
+    uint8_t *cmask[3]{};
+    IntraCtl *ctl_c = nullptr, *h_ctl_c = nullptr;
+    cudaGraphExec_t igraph_c = nullptr;
     bool intra_pending = false;  // an intra frame since the last sync
     bool has_intra = false;      // an intra frame was decoded
     // block scratch
@@ -397,6 +408,13 @@ size_t hivc_decoder_bytes(const hivc_config *c)
         nblocks += g.nblocks;
         maxpts = std::max(maxpts, (size_t)g.w * g.h);
     }
+    for (int p = 0; p < plane_count(c); ++p) {  // the coarse start's half-size planes
+        const PlaneGeom g = plane_geom(c, p);
+        const size_t n = (size_t)((g.h + 1) / 2) * round_up((g.w + 1) / 2, kPitchAlign);
+        for (int k = 0; k < 5; ++k) add(n * 4);
+        add(n);
+    }
+    add(sizeof(IntraCtl));  // its control state
     add(3 * sizeof(unsigned long long));
     add(3 * sizeof(unsigned int));
     add((size_t)coef_slots(nblocks) * kBigFloats * sizeof(float));  // K > 32 systems
@@ -450,6 +468,19 @@ hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out)
     d->big_ranges = coef_slots(nblocks);
     d->big = m.get<float>((size_t)d->big_ranges * kBigFloats);
     void *plan_mem = m.get<char>(block_plan_bytes(nblocks, cfg->layout_groups != 0));
+    for (int p = 0; p < d->np; ++p) {
+        d->cw[p] = (d->pg[p].w + 1) / 2;
+        d->chh[p] = (d->pg[p].h + 1) / 2;
+        d->cpitch[p] = round_up(d->cw[p], kPitchAlign);
+        const size_t n = (size_t)d->chh[p] * d->cpitch[p];
+        d->cu[0][p] = m.get<float>(n);
+        d->cu[1][p] = m.get<float>(n);
+        d->cres[p] = m.get<float>(n);
+        d->ce[0][p] = m.get<float>(n);
+        d->ce[1][p] = m.get<float>(n);
+        d->cmask[p] = m.get<uint8_t>(n);
+    }
+    d->ctl_c = m.get<IntraCtl>(1);
     d->vsum = m.get<unsigned long long>(3);
     d->ctl = m.get<IntraCtl>(1);
     d->tune_ctl = m.get<IntraCtl>(1);
@@ -460,15 +491,17 @@ hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out)
         delete d;
         return HIVC_E_NOMEM;
     }
-    if (cudaMallocHost(&d->h_flags, 64) != cudaSuccess || cudaMallocHost(&d->h_ctl, sizeof(IntraCtl)) != cudaSuccess) {
+    if (cudaMallocHost(&d->h_flags, 64) != cudaSuccess || cudaMallocHost(&d->h_ctl, sizeof(IntraCtl)) != cudaSuccess ||
+        cudaMallocHost(&d->h_ctl_c, sizeof(IntraCtl)) != cudaSuccess) {
         if (d->h_flags) cudaFreeHost(d->h_flags);
-    if (d->h_ctl) cudaFreeHost(d->h_ctl);
-    if (d->igraph) cudaGraphExecDestroy(d->igraph);
+        if (d->h_ctl) cudaFreeHost(d->h_ctl);
+        if (d->h_ctl_c) cudaFreeHost(d->h_ctl_c);
         m.release();
         delete d;
         return HIVC_E_NOMEM;
     }
     std::memset(d->h_ctl, 0, sizeof(IntraCtl));
+    std::memset(d->h_ctl_c, 0, sizeof(IntraCtl));
     if (cfg->stream) {
         d->stream = static_cast<cudaStream_t>(cfg->stream);
     } else {
@@ -486,6 +519,7 @@ hivc_status hivc_decoder_create(const hivc_config *cfg, hivc_decoder **out)
         cudaEventCreateWithFlags(&d->ev_intra, cudaEventDisableTiming) != cudaSuccess ||
         cudaMemsetAsync(d->flags, 0, 4 * kStatusWords, d->stream) != cudaSuccess ||
         cudaMemsetAsync(d->ctl, 0, sizeof(IntraCtl), d->stream) != cudaSuccess ||
+        cudaMemsetAsync(d->ctl_c, 0, sizeof(IntraCtl), d->stream) != cudaSuccess ||
         (cfg->batch_frames > 0 &&
          cudaMallocAsync(&d->pool, pool_bytes_for(cfg, cfg->batch_frames), d->stream) != cudaSuccess) ||
         cudaStreamSynchronize(d->stream) != cudaSuccess) {
@@ -518,7 +552,9 @@ void hivc_decoder_destroy(hivc_decoder *d)
     if (d->own_stream) cudaStreamDestroy(d->stream);
     if (d->h_flags) cudaFreeHost(d->h_flags);
     if (d->h_ctl) cudaFreeHost(d->h_ctl);
+    if (d->h_ctl_c) cudaFreeHost(d->h_ctl_c);
     if (d->igraph) cudaGraphExecDestroy(d->igraph);
+    if (d->igraph_c) cudaGraphExecDestroy(d->igraph_c);
     d->mem.release();
     delete d;
 }
@@ -603,6 +639,60 @@ cudaError_t launch_rct_frame(hivc_decoder *d, const float *flow, float *const *h
 
 }  // namespace
 
+namespace {
+
+// One correction loop of J with the sweep tiling `variant`, decided on the
+// device: one launch of the graph *graph (built once; again when
+// *graph_variant, if given, names another tiling), or with per-kernel
+// timing one launch at a time, with the plan read back into h between
+// cycles.
+cudaError_t run_intra_loop(hivc_decoder *d, IntraJobs &J, int variant, cudaGraphExec_t *graph, int *graph_variant,
+                           IntraCtl *h)
+{
+    cudaStream_t st = d->stream;
+    cudaError_t e = cudaSuccess;
+    if (d->timing) {
+        {
+            Timed t(d, 2);
+            e = launch_intra_residual(J, true, st);
+            t.done(0);
+        }
+        while (e == cudaSuccess) {
+            e = cudaMemcpyAsync(h, J.ctl, sizeof(IntraCtl), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess || !h->go_outer) break;
+            // the planned pairs: over all planes, then (the chroma phase)
+            // over the chroma planes alone, at least one pair as in the graph
+            const int pa = h->pairs[0], pb = J.chroma_phase ? std::max(1, h->pairs[1]) : 0;
+            for (int l = 0; l < pa && e == cudaSuccess; ++l) {
+                Timed t(d, 1);
+                e = launch_intra_sor_pair(J, variant, st);
+                t.done(0);
+            }
+            for (int l = 0; l < pb && e == cudaSuccess; ++l) {
+                Timed t(d, 1);
+                e = launch_intra_sor_chroma_pair(J, st);
+                t.done(0);
+            }
+            if (e == cudaSuccess) {
+                Timed t(d, 2);
+                e = launch_intra_residual(J, false, st);
+                t.done(0);
+            }
+        }
+        return e;
+    }
+    if (!*graph || (graph_variant && *graph_variant != variant)) {
+        if (*graph) cudaGraphExecDestroy(*graph);
+        *graph = nullptr;
+        if ((e = build_intra_graph(J, variant, graph)) != cudaSuccess) return e;
+        if (graph_variant) *graph_variant = variant;
+    }
+    return cudaGraphLaunch(*graph, st);
+}
+
+}  // namespace
+
 hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc_out *out)
 {
     if (!d || !f || !out_ok(d, out)) return HIVC_E_INVALID;
@@ -658,49 +748,54 @@ hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc
     }
     if (e != cudaSuccess) return HIVC_E_CUDA;
     // the sweep kernel's tiling (the first solve of a geometry times the
-    // variants on launches of its own), then the correction loop, decided on
-    // the device: one graph launch, or with per-kernel timing one launch at
-    // a time with the plan read back between cycles
+    // variants on launches of its own)
     const int variant = intra_sor_variant(J, d->tune_ctl, st);
-    if (launch_intra_ctl_init(J, om0, d->cfg.iframe_tol, d->cfg.max_cycles, st) != cudaSuccess) return HIVC_E_CUDA;
-    if (d->timing) {
+    // the coarse start: the mask restricted to the half-size planes, one
+    // FP32 correction cycle there (to its floor, or the tolerance), and the
+    // unknown pixels prolonged from it
+    bool coarse = d->cfg.flat_start == 0;
+    for (int p = 0; p < d->np; ++p) coarse = coarse && d->pg[p].w >= 32 && d->pg[p].h >= 32;
+    if (coarse) {
+        IntraJobs C{};
+        C.n = d->np;
+        C.ctl = d->ctl_c;
+        float omc[3] = {1.f, 1.f, 1.f};
+        for (int p = 0; p < d->np; ++p) {
+            IntraPlane &P = C.p[p];
+            P.width = d->cw[p];
+            P.height = d->chh[p];
+            P.pitch = d->cpitch[p];
+            P.mask = d->cmask[p];
+            P.uh[0] = d->cu[0][p];
+            P.uh[1] = d->cu[1][p];
+            P.res = d->cres[p];
+            P.e[0] = d->ce[0][p];
+            P.e[1] = d->ce[1][p];
+            P.vsum = d->vsum + p;
+            P.ff = 0;
+            // a coarse cell is known when one of its four fine pixels is
+            const double N = (double)d->pg[p].w * d->pg[p].h, dens = std::min(1.0, J.p[p].n / N);
+            const double nc = (double)P.width * P.height * (1.0 - std::pow(1.0 - dens, 4.0));
+            P.n = (int32_t)std::max(1.0, nc);
+            omc[p] = sor_omega(P.width, P.height, P.n);
+        }
         {
-            Timed t(d, 2);
-            e = launch_intra_residual(J, true, st);
-            t.done(0);
+            Timed t(d, 0);
+            e = launch_intra_restrict(J, C, st);
+            t.done(1);
         }
-        while (e == cudaSuccess) {
-            e = cudaMemcpyAsync(d->h_ctl, d->ctl, sizeof(IntraCtl), cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess || !d->h_ctl->go_outer) break;
-            // the planned pairs: over all planes, then (the chroma phase)
-            // over the chroma planes alone, at least one pair as in the graph
-            const int pa = d->h_ctl->pairs[0], pb = J.chroma_phase ? std::max(1, d->h_ctl->pairs[1]) : 0;
-            for (int l = 0; l < pa && e == cudaSuccess; ++l) {
-                Timed t(d, 1);
-                e = launch_intra_sor_pair(J, variant, st);
-                t.done(0);
-            }
-            for (int l = 0; l < pb && e == cudaSuccess; ++l) {
-                Timed t(d, 1);
-                e = launch_intra_sor_chroma_pair(J, st);
-                t.done(0);
-            }
-            if (e == cudaSuccess) {
-                Timed t(d, 2);
-                e = launch_intra_residual(J, false, st);
-                t.done(0);
-            }
+        if (e == cudaSuccess) e = launch_intra_ctl_init(C, omc, d->cfg.iframe_tol, 1, st, kCoarseSweeps);
+        if (e == cudaSuccess) e = run_intra_loop(d, C, 0, &d->igraph_c, nullptr, d->h_ctl_c);
+        if (e == cudaSuccess) {
+            Timed t(d, 0);
+            e = launch_intra_prolong(J, C, st);
+            t.done(1);
         }
-    } else {
-        if (!d->igraph || d->igraph_variant != variant) {
-            if (d->igraph) cudaGraphExecDestroy(d->igraph);
-            d->igraph = nullptr;
-            if ((e = build_intra_graph(J, variant, &d->igraph)) != cudaSuccess) return HIVC_E_CUDA;
-            d->igraph_variant = variant;
-        }
-        e = cudaGraphLaunch(d->igraph, st);
+        if (e != cudaSuccess) return HIVC_E_CUDA;
     }
+    // the correction loop, decided on the device
+    if (launch_intra_ctl_init(J, om0, d->cfg.iframe_tol, d->cfg.max_cycles, st) != cudaSuccess) return HIVC_E_CUDA;
+    e = run_intra_loop(d, J, variant, &d->igraph, &d->igraph_variant, d->h_ctl);
     if (e != cudaSuccess) return HIVC_E_CUDA;
     d->intra_pending = true;
     d->has_intra = true;
@@ -1279,6 +1374,11 @@ hivc_status hivc_decoder_sync(hivc_decoder *d, hivc_stats *last)
         e = cudaMemcpyAsync(d->h_ctl, d->ctl, sizeof(IntraCtl), cudaMemcpyDeviceToHost, d->stream);
     if (e == cudaSuccess && intra)
         e = cudaMemsetAsync(reinterpret_cast<char *>(d->ctl) + stat_off, 0, sizeof(IntraCtl) - stat_off, d->stream);
+    // (the coarse start's statistics: launches and pixels only)
+    if (e == cudaSuccess && intra)
+        e = cudaMemcpyAsync(d->h_ctl_c, d->ctl_c, sizeof(IntraCtl), cudaMemcpyDeviceToHost, d->stream);
+    if (e == cudaSuccess && intra)
+        e = cudaMemsetAsync(reinterpret_cast<char *>(d->ctl_c) + stat_off, 0, sizeof(IntraCtl) - stat_off, d->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
     if (e != cudaSuccess) return HIVC_E_CUDA;
     bool not_converged = false;
@@ -1292,6 +1392,12 @@ hivc_status hivc_decoder_sync(hivc_decoder *d, hivc_stats *last)
         d->st.kernel_pixels[1] += c.sor_pixels;
         d->st.kernel_pixels[2] += c.res_pixels;
         d->st.launches += (int32_t)(c.sor_launches + c.res_launches);
+        const IntraCtl &cc = *d->h_ctl_c;
+        d->st.kernel_launches[1] += (int32_t)cc.sor_launches;
+        d->st.kernel_launches[2] += (int32_t)cc.res_launches;
+        d->st.kernel_pixels[1] += cc.sor_pixels;
+        d->st.kernel_pixels[2] += cc.res_pixels;
+        d->st.launches += (int32_t)(cc.sor_launches + cc.res_launches);
         not_converged = c.unconverged > 0;
         d->intra_pending = false;
     }

@@ -323,6 +323,7 @@ struct IntraCtl {
     double rate[3];            // contraction per sweep per plane
     float omega[3];            // relaxation factor per plane
     int32_t max_cycles, spl;   // cycle cap, sweeps per launch
+    int32_t max_sweeps, pad0;  // cap on a plane's sweeps in one cycle
     int32_t nl[3];             // sweep launches of the current cycle per plane
     int32_t maxl, cycles;      // launches of the cycle, cycles done
     int32_t iter[2];           // pairs done, as the launches of parity 0 and 1 read it
@@ -348,9 +349,15 @@ struct IntraJobs {
 };
 
 cudaError_t launch_intra_init(IntraJobs &jobs, uint32_t *flags, cudaStream_t st, int *launches);
-// The control state for a new solve: omega0 per plane, tolerance, cycle cap.
+// The coarse start: the fine planes' mask restricted to the half-size
+// planes of C (after launch_intra_init), and, after C's solve, the
+// unknown fine pixels set from C's solution.
+cudaError_t launch_intra_restrict(const IntraJobs &fine, const IntraJobs &coarse, cudaStream_t st);
+cudaError_t launch_intra_prolong(const IntraJobs &fine, const IntraJobs &coarse, cudaStream_t st);
+// The control state for a new solve: omega0 per plane, tolerance, cycle
+// cap, and the cap on a plane's sweeps in one cycle (kS .. 600).
 cudaError_t launch_intra_ctl_init(const IntraJobs &jobs, const float *omega0, double tol, int max_cycles,
-                                  cudaStream_t st);
+                                  cudaStream_t st, int max_sweeps = 600);
 // One residual launch: first = the start of the solve (res = L u, the
 // norms, the first cycle's plan), else the end of a cycle (u += e for the
 // planes that swept, res, norms, the next cycle's plan).

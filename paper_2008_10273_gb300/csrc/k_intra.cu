@@ -114,21 +114,39 @@ __global__ void intra_sum_kernel(const __grid_constant__ IntraJobs J, uint32_t *
         // two's complement: signed values add correctly modulo 2^64
         s += P.val16 ? (unsigned long long)(long long)__ldg(P.val16 + k) : (unsigned long long)__ldg(P.val + k);
     }
+    // one atomic per CTA (the launch has a point per thread)
+    __shared__ unsigned long long s_part[32];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0 && s) atomicAdd(P.vsum, s);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = s;
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, kFlagMaskIdx);
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_part[w];
+        if (t) atomicAdd(P.vsum, t);
+    }
+}
+
+// the mean mask value of plane P, formed once per CTA (one thread's
+// double-precision division) and shared
+__device__ __forceinline__ float plane_mean(const IntraPlane &P)
+{
+    __shared__ float s_mean;
+    if (threadIdx.x == 0) s_mean = P.n > 0 ? (float)((double)(long long)*P.vsum / (double)P.n) : 0.f;
+    __syncthreads();
+    return s_mean;
 }
 
 // u = mean mask value (hi), lo = 0, mask = 0
 __global__ void intra_fill_kernel(const __grid_constant__ IntraJobs J)
 {
     const IntraPlane &P = J.p[blockIdx.y];
-    const float mean = P.n > 0 ? (float)((double)(long long)*P.vsum / (double)P.n) : 0.f;
-    const size_t total = (size_t)P.height * P.pitch;
+    const float mean = plane_mean(P);
+    // 4 pixels a thread (rows are multiples of 32 pixels)
+    const size_t total = (size_t)P.height * P.pitch / 4;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        P.uh[0][i] = mean;
-        P.ul[0][i] = 0.f;
-        P.mask[i] = 0;
+        reinterpret_cast<float4 *>(P.uh[0])[i] = make_float4(mean, mean, mean, mean);
+        reinterpret_cast<float4 *>(P.ul[0])[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        reinterpret_cast<uint32_t *>(P.mask)[i] = 0u;
     }
 }
 
@@ -143,6 +161,66 @@ __global__ void intra_scatter_kernel(const __grid_constant__ IntraJobs J)
         const size_t o = (size_t)(i / P.width) * P.pitch + (i % P.width);
         P.uh[0][o] = P.val16 ? (float)__ldg(P.val16 + k) : (float)__ldg(P.val + k);
         P.mask[o] = 1;
+    }
+}
+
+// ---- the coarse start ------------------------------------------------------
+// A two-level cascade for the starting iterate (a pixel per thread): coarse pixel (X, Y) of a
+// plane covers the fine pixels 2X .. 2X + 1 x 2Y .. 2Y + 1.  It is known
+// when one of them is, with the mean of their values; otherwise it starts
+// at the plane's mean mask value.  (Fine planes after the scatter; plane =
+// blockIdx.y.)
+__global__ void intra_restrict_kernel(const __grid_constant__ IntraJobs F, const __grid_constant__ IntraJobs C)
+{
+    const IntraPlane &Pf = F.p[blockIdx.y];
+    const IntraPlane &Pc = C.p[blockIdx.y];
+    const float mean = plane_mean(Pf);
+    const int Wc = Pc.width, total = Pc.width * Pc.height;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int Y = i / Wc, X = i - Y * Wc;
+        float s = 0.f;
+        int k = 0;
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                const int x = 2 * X + dx, y = 2 * Y + dy;
+                if (x >= Pf.width || y >= Pf.height) continue;
+                const size_t o = (size_t)y * Pf.pitch + x;
+                if (Pf.mask[o]) {
+                    s += Pf.uh[0][o];
+                    ++k;
+                }
+            }
+        const size_t oc = (size_t)Y * Pc.pitch + X;
+        Pc.uh[0][oc] = k ? s / (float)k : mean;
+        Pc.mask[oc] = k ? 1 : 0;
+    }
+}
+
+// The unknown fine pixels from the coarse solution (the iterate buffer the
+// coarse control state names): bilinear between coarse cell centres (fine
+// x at coarse (x - 1/2) / 2), the edge cells replicated.  lo stays 0 (the
+// fill kernel's); the mask pixels keep their values.
+__global__ void intra_prolong_kernel(const __grid_constant__ IntraJobs F, const __grid_constant__ IntraJobs C)
+{
+    const IntraPlane &Pf = F.p[blockIdx.y];
+    const IntraPlane &Pc = C.p[blockIdx.y];
+    const float *__restrict__ uc = Pc.uh[C.ctl->upar[blockIdx.y] & 1];
+    const int W = Pf.width, Wc = Pc.width, Hc = Pc.height, total = Pf.width * Pf.height;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int y = i / W, x = i - y * W;
+        const size_t o = (size_t)y * Pf.pitch + x;
+        if (Pf.mask[o]) continue;
+        const float xs = 0.5f * (float)x - 0.25f, ys = 0.5f * (float)y - 0.25f;
+        const float fx = floorf(xs), fy = floorf(ys);
+        const float ax = xs - fx, ay = ys - fy;
+        const int x0 = (int)fx, y0 = (int)fy;
+        const int xa = min(max(x0, 0), Wc - 1), xb = min(max(x0 + 1, 0), Wc - 1);
+        const int ya = min(max(y0, 0), Hc - 1), yb = min(max(y0 + 1, 0), Hc - 1);
+        const float *ra = uc + (size_t)ya * Pc.pitch, *rb = uc + (size_t)yb * Pc.pitch;
+        const float top = fmaf(ax, ra[xb] - ra[xa], ra[xa]), bot = fmaf(ax, rb[xb] - rb[xa], rb[xa]);
+        Pf.uh[0][o] = fmaf(ay, bot - top, top);
     }
 }
 
@@ -244,7 +322,7 @@ __device__ void plan_cycle(const IntraJobs &J, IntraCtl &c, const float *rb, boo
         const float target = fmaxf(1e-5f, 0.3f * (float)c.tol / (float)c.rn[p]);
         const float rt = fminf(fmaxf((float)c.rate[p], 0.05f), 0.995f);
         int sw = (int)ceilf(logf(target) / logf(rt));
-        sw = min(max(sw, c.spl), 600);
+        sw = min(max(sw, c.spl), c.max_sweeps);
         c.nl[p] = (sw + c.spl - 1) / c.spl;
         maxl = max(maxl, c.nl[p]);
     }
@@ -306,7 +384,7 @@ __device__ __forceinline__ void plan_cycle_cta(const IntraJobs &J, bool first)
 
 // The control state of a new solve (one thread).
 __global__ void intra_ctl_init_kernel(IntraCtl *c, float om0, float om1, float om2, double tol, int max_cycles,
-                                      int spl)
+                                      int spl, int max_sweeps)
 {
     IntraCtl z{};
     z.sor_launches = c->sor_launches;  // the statistics run on until the sync
@@ -317,6 +395,7 @@ __global__ void intra_ctl_init_kernel(IntraCtl *c, float om0, float om1, float o
     z.tol = tol;
     z.max_cycles = max_cycles;
     z.spl = spl;
+    z.max_sweeps = max_sweeps;
     z.omega[0] = om0;
     z.omega[1] = om1;
     z.omega[2] = om2;
@@ -830,18 +909,43 @@ cudaError_t launch_intra_init(IntraJobs &J, uint32_t *flags, cudaStream_t st, in
         cudaError_t e = cudaMemsetAsync(J.p[k].vsum, 0, sizeof(unsigned long long), st);
         if (e != cudaSuccess) return e;
     }
-    intra_sum_kernel<<<dim3(32, J.n), 256, 0, st>>>(J, flags);
-    intra_fill_kernel<<<dim3(304, J.n), 256, 0, st>>>(J);
-    intra_scatter_kernel<<<dim3(64, J.n), 256, 0, st>>>(J);
+    // a point, four pixels, a point per thread: every load of a launch in
+    // flight at once (the loops inside stay correct for any grid)
+    int n = 1;
+    size_t px = 1;
+    for (int k = 0; k < J.n; ++k) {
+        n = std::max(n, J.p[k].n);
+        px = std::max(px, (size_t)J.p[k].height * J.p[k].pitch / 4);
+    }
+    const unsigned gp = (unsigned)std::min((n + 255) / 256, 8192), gf = (unsigned)std::min<size_t>((px + 255) / 256, 16384);
+    intra_sum_kernel<<<dim3(gp, J.n), 256, 0, st>>>(J, flags);
+    intra_fill_kernel<<<dim3(gf, J.n), 256, 0, st>>>(J);
+    intra_scatter_kernel<<<dim3(gp, J.n), 256, 0, st>>>(J);
     if (launches) *launches += 3;
     return cudaGetLastError();
 }
 
+cudaError_t launch_intra_restrict(const IntraJobs &F, const IntraJobs &C, cudaStream_t st)
+{
+    size_t px = 1;
+    for (int k = 0; k < C.n; ++k) px = std::max(px, (size_t)C.p[k].width * C.p[k].height);
+    intra_restrict_kernel<<<dim3((unsigned)std::min<size_t>((px + 255) / 256, 16384), F.n), 256, 0, st>>>(F, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_intra_prolong(const IntraJobs &F, const IntraJobs &C, cudaStream_t st)
+{
+    size_t px = 1;
+    for (int k = 0; k < F.n; ++k) px = std::max(px, (size_t)F.p[k].width * F.p[k].height);
+    intra_prolong_kernel<<<dim3((unsigned)std::min<size_t>((px + 255) / 256, 16384), F.n), 256, 0, st>>>(F, C);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_intra_ctl_init(const IntraJobs &J, const float *omega0, double tol, int max_cycles,
-                                  cudaStream_t st)
+                                  cudaStream_t st, int max_sweeps)
 {
     intra_ctl_init_kernel<<<1, 1, 0, st>>>(J.ctl, omega0[0], J.n > 1 ? omega0[1] : 1.f, J.n > 2 ? omega0[2] : 1.f,
-                                            tol, max_cycles, kS);
+                                            tol, max_cycles, kS, std::min(std::max(max_sweeps, kS), 600));
     return cudaGetLastError();
 }
 

@@ -34,7 +34,7 @@ class Config(ctypes.Structure):
     _fields_ = [("width", c_i32), ("height", c_i32), ("chroma", c_i32), ("block", c_i32),
                 ("op", c_i32), ("precision", c_i32), ("iframe_tol", c_f64), ("max_cycles", c_i32),
                 ("cond_threshold", c_f64), ("stream", c_vp), ("layout_groups", c_i32),
-                ("batch_frames", c_i32), ("fused_residual", c_i32)]
+                ("batch_frames", c_i32), ("fused_residual", c_i32), ("flat_start", c_i32)]
 
 
 class Points(ctypes.Structure):
@@ -212,7 +212,8 @@ class Decoder:
     def __init__(self, width: int, height: int, chroma: bool = True, block: int = 16,
                  iframe_tol: float = 1e-8, max_cycles: int = 40, precision: int = 0,
                  stream=None, timing: bool = False, cond_threshold: float = 1e6, op: int = 0,
-                 layout_groups: Optional[bool] = None, batch_frames: int = 0, fused_residual: bool = False):
+                 layout_groups: Optional[bool] = None, batch_frames: int = 0, fused_residual: bool = False,
+                 flat_start: bool = False):
         cfg = config_default()
         # chroma: False/0 grey, True/1 4:2:0, 2 the 4:4:4 RCT colour path
         cfg.width, cfg.height, cfg.chroma, cfg.block = width, height, int(chroma), block
@@ -223,6 +224,7 @@ class Decoder:
             cfg.layout_groups = int(bool(layout_groups))
         cfg.batch_frames = int(batch_frames)
         cfg.fused_residual = int(bool(fused_residual))
+        cfg.flat_start = int(bool(flat_start))
         cfg.stream = _stream_handle(stream)
         self.cfg = cfg
         self.width, self.height, self.chroma, self.block = width, height, bool(chroma), block

@@ -57,6 +57,9 @@ def test_host_only_entry_points(hv):
     c.fused_residual = 2
     assert L.hivc_decoder_bytes(ctypes.byref(c)) == 0
     c.fused_residual = 0
+    c.flat_start = 2
+    assert L.hivc_decoder_bytes(ctypes.byref(c)) == 0
+    c.flat_start = 0
     for bad in (0, 1001):  # the correction loop runs on the device: its cycle cap is bounded
         c.max_cycles = bad
         assert L.hivc_decoder_bytes(ctypes.byref(c)) == 0
@@ -70,7 +73,7 @@ def test_host_only_entry_points(hv):
     assert L.hivc_block_residual_workspace_bytes(1920, 1080, 16, 70000) > 70000 * 4
     assert L.hivc_block_residual_workspace_bytes(0, 1080, 16, 10) == 0
     # struct layouts the binding relies on
-    assert ctypes.sizeof(hv.Config) == 72
+    assert ctypes.sizeof(hv.Config) == 72 and hv.Config.flat_start.offset == 68
     assert ctypes.sizeof(hv.Residual) == 32
     # hivc_stats: the per-family int64 pixel counts follow the launch counts
     assert hv.Stats.kernel_pixels.offset == 120 and ctypes.sizeof(hv.Stats) == 192

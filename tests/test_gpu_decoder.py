@@ -83,6 +83,35 @@ def test_iframe_chroma_phase(hv, W, H, cfrac, seed):
         assert np.abs(got[0][0][p] - rec[p]).max() <= TOL_INTRA, p
 
 
+@pytest.mark.parametrize("W,H,chroma,seed", [(480, 272, True, 21), (202, 150, True, 22), (333, 97, False, 23)])
+def test_coarse_start(hv, W, H, chroma, seed):
+    """The default solve starts from a half-size solution prolonged to the
+    unknown pixels; flat_start = 1 starts from the mean of the mask values.
+    Only the start differs: both reach the tolerance and the oracle's
+    solution, and the graph and the launches sent one by one from the host
+    give the same bits with the coarse start."""
+    srcs, ifr = make_iframe_only(seed, W, H, 0.03, chroma=chroma)
+    rec, _ = oracle.OracleDecoder(W, H, chroma).decode_iframe(ifr)
+    got = {}
+    for flat, timing in ((0, False), (0, True), (1, False)):
+        dec = hv.Decoder(W, H, chroma=chroma, iframe_tol=1e-9, flat_start=flat, timing=timing)
+        out = hv.alloc_out(W, H, chroma=chroma)
+        dec.decode_iframe(hv.device_iframe(ifr), out)
+        st = dec.sync()
+        assert max(st.resid) <= 1e-9
+        got[(flat, timing)] = (_planes(dec), st.sweeps, st.cycles, st.kernel_launches[0])
+        dec.close()
+    a, b = got[(0, False)], got[(0, True)]
+    assert a[1:3] == b[1:3]
+    for x, y in zip(a[0], b[0]):
+        assert np.array_equal(x, y)
+    # the setup family holds the restriction and the prolongation
+    assert got[(0, False)][3] == got[(1, False)][3] + 2
+    for flat in (0, 1):
+        for p, g in enumerate(got[(flat, False)][0]):
+            assert np.abs(g - rec[p]).max() <= TOL_INTRA, (flat, p)
+
+
 def test_iframe_with_residual(hv):
     srcs, ifr = make_iframe_only(5, 160, 96, 0.03, chroma=True, residual={"lam_y": 8.0, "lam_c": 4.0})
     dec = hv.Decoder(160, 96, chroma=True)
