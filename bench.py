@@ -42,7 +42,7 @@ NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch on the FullHD
     # 4:2:0 GOP workload (profiles/*.md give the commands):
     # intra_sor_kernel over the three planes
-    "intra_sweeps": {"bytes": 28.02e6, "sha": "0da1d88a4425"},
+    "intra_sweeps": {"bytes": 28.02e6, "sha": "0d2f62bc133f"},
     # pframe_kernel, one frame
     "inter_pixels": {"bytes": 41.57e6, "sha": "f98556f08c0f"},
     # block_eval_kernel, per frame of an 8-frame launch (49.12 MB / 8)
