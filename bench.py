@@ -659,6 +659,9 @@ def main(argv=None):
         1: ("k_intra.cu", 9 * sweeps_per_launch * px_per_launch(1),
             "9 B per pixel per red-black sweep (iterate read + write 8 B, mask 1 B) x 4 sweeps per launch x "
             "the pixels the launch covers"),
+        # the same kernel on the coarse start's half-size planes
+        7: ("k_intra.cu", 9 * sweeps_per_launch * px_per_launch(7),
+            "9 B per pixel per red-black sweep x 4 sweeps per launch x the half-size pixels the launch covers"),
         # residual + update: hi/lo in 8 B, hi/lo out 8 B, correction 4 B, mask 1 B, residual 4 B
         2: ("k_intra.cu", (8 + 8 + 4 + 1 + 4) * px_per_launch(2),
             "25 B per pixel (float-float iterate in and out, correction, mask, residual)"),
@@ -709,12 +712,12 @@ def main(argv=None):
                 "dram_frac": (traffic / (avg_ms / 1e3) / 1e9 / hbm_peak) if traffic else None,
                 "peak_source": peak_source, "algorithmic_bytes_per_launch": b, "accounting": how,
                 "avg_launch_ms": avg_ms, "launches": fam_n[f],
-                "pixels_per_launch": px_per_launch(f) if f in (1, 2) else px_frame}
+                "pixels_per_launch": px_per_launch(f) if f in (1, 2, 7) else px_frame}
 
     dom = max(range(len(fam_ms)), key=lambda i: fam_ms[i])
     roof = fam_roof(dom)
     if roof is not None:
-        roof["kernels"] = {hivc.KERNEL_FAMILIES[f]: fam_roof(f) for f in (1, 4, 5, 2) if fam_n[f] > 0}
+        roof["kernels"] = {hivc.KERNEL_FAMILIES[f]: fam_roof(f) for f in (1, 4, 5, 2, 7) if fam_n[f] > 0}
         # a whole inter frame (block coefficients, residual planes, pixels)
         # against the fused frame's bytes
         inter_ms = sum(fam_ms[f] for f in (3, 4, 5)) / max(1, kpass * inter_frames_per_step)

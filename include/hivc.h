@@ -227,13 +227,14 @@ typedef struct {
        when timing is on) and launch counts since the previous sync:
        0 intra setup, 1 intra sweeps, 2 intra residual, 3 block coefficients,
        4 inter pixels (warp + residual + pack), 5 block evaluate,
-       6 intra output and the 4:4:4 colour path's pixels, 7 unused */
+       6 intra output and the 4:4:4 colour path's pixels, 7 the sweeps of
+       the intra solve's coarse start (its residual launches count in 2) */
     float kernel_ms[HIVC_STAT_KERNELS];
     int32_t kernel_launches[HIVC_STAT_KERNELS];
     /* per kernel family: pixels processed since the previous sync, the sum
        over launches of the pixels of the planes each launch covers.  Set
-       for families 1 and 2, whose launches may cover only the planes that
-       still need sweeps; 0 for the others. */
+       for families 1, 2 and 7, whose launches may cover only the planes
+       that still need sweeps; 0 for the others. */
     int64_t kernel_pixels[HIVC_STAT_KERNELS];
     int32_t group_blocks;   /* residual blocks evaluated by their layout
                                group's tensor-core product (Cb/Cr pairs

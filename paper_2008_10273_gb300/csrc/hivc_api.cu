@@ -647,7 +647,7 @@ namespace {
 // timing one launch at a time, with the plan read back into h between
 // cycles.
 cudaError_t run_intra_loop(hivc_decoder *d, IntraJobs &J, int variant, cudaGraphExec_t *graph, int *graph_variant,
-                           IntraCtl *h)
+                           IntraCtl *h, int fam_sweeps)
 {
     cudaStream_t st = d->stream;
     cudaError_t e = cudaSuccess;
@@ -665,12 +665,12 @@ cudaError_t run_intra_loop(hivc_decoder *d, IntraJobs &J, int variant, cudaGraph
             // over the chroma planes alone, at least one pair as in the graph
             const int pa = h->pairs[0], pb = J.chroma_phase ? std::max(1, h->pairs[1]) : 0;
             for (int l = 0; l < pa && e == cudaSuccess; ++l) {
-                Timed t(d, 1);
+                Timed t(d, fam_sweeps);
                 e = launch_intra_sor_pair(J, variant, st);
                 t.done(0);
             }
             for (int l = 0; l < pb && e == cudaSuccess; ++l) {
-                Timed t(d, 1);
+                Timed t(d, fam_sweeps);
                 e = launch_intra_sor_chroma_pair(J, st);
                 t.done(0);
             }
@@ -785,7 +785,7 @@ hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc
             t.done(1);
         }
         if (e == cudaSuccess) e = launch_intra_ctl_init(C, omc, d->cfg.iframe_tol, 1, st, kCoarseSweeps);
-        if (e == cudaSuccess) e = run_intra_loop(d, C, 0, &d->igraph_c, nullptr, d->h_ctl_c);
+        if (e == cudaSuccess) e = run_intra_loop(d, C, 0, &d->igraph_c, nullptr, d->h_ctl_c, 7);
         if (e == cudaSuccess) {
             Timed t(d, 0);
             e = launch_intra_prolong(J, C, st);
@@ -795,7 +795,7 @@ hivc_status hivc_decode_iframe(hivc_decoder *d, const hivc_iframe *f, const hivc
     }
     // the correction loop, decided on the device
     if (launch_intra_ctl_init(J, om0, d->cfg.iframe_tol, d->cfg.max_cycles, st) != cudaSuccess) return HIVC_E_CUDA;
-    e = run_intra_loop(d, J, variant, &d->igraph, &d->igraph_variant, d->h_ctl);
+    e = run_intra_loop(d, J, variant, &d->igraph, &d->igraph_variant, d->h_ctl, 1);
     if (e != cudaSuccess) return HIVC_E_CUDA;
     d->intra_pending = true;
     d->has_intra = true;
@@ -1392,10 +1392,10 @@ hivc_status hivc_decoder_sync(hivc_decoder *d, hivc_stats *last)
         d->st.kernel_pixels[1] += c.sor_pixels;
         d->st.kernel_pixels[2] += c.res_pixels;
         d->st.launches += (int32_t)(c.sor_launches + c.res_launches);
-        const IntraCtl &cc = *d->h_ctl_c;
-        d->st.kernel_launches[1] += (int32_t)cc.sor_launches;
+        const IntraCtl &cc = *d->h_ctl_c;  // the coarse start's sweeps: a family of their own
+        d->st.kernel_launches[7] += (int32_t)cc.sor_launches;
         d->st.kernel_launches[2] += (int32_t)cc.res_launches;
-        d->st.kernel_pixels[1] += cc.sor_pixels;
+        d->st.kernel_pixels[7] += cc.sor_pixels;
         d->st.kernel_pixels[2] += cc.res_pixels;
         d->st.launches += (int32_t)(cc.sor_launches + cc.res_launches);
         not_converged = c.unconverged > 0;

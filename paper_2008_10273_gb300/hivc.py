@@ -24,7 +24,7 @@ HIVC_E_BUDGET = -6
 HIVC_E_TIMEOUT = -7
 STAT_KERNELS = 8
 KERNEL_FAMILIES = ("intra_setup", "intra_sweeps", "intra_residual", "block_coef",
-                   "inter_pixels", "block_eval", "warp_add", "unused")
+                   "inter_pixels", "block_eval", "warp_add", "intra_coarse_sweeps")
 
 c_i32, c_u32, c_f64, c_f32, c_vp, c_sz = (ctypes.c_int32, ctypes.c_uint32, ctypes.c_double,
                                           ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t)

@@ -99,7 +99,7 @@ def test_coarse_start(hv, W, H, chroma, seed):
         dec.decode_iframe(hv.device_iframe(ifr), out)
         st = dec.sync()
         assert max(st.resid) <= 1e-9
-        got[(flat, timing)] = (_planes(dec), st.sweeps, st.cycles, st.kernel_launches[0])
+        got[(flat, timing)] = (_planes(dec), st.sweeps, st.cycles, st.kernel_launches[0], st.kernel_launches[7])
         dec.close()
     a, b = got[(0, False)], got[(0, True)]
     assert a[1:3] == b[1:3]
@@ -107,6 +107,8 @@ def test_coarse_start(hv, W, H, chroma, seed):
         assert np.array_equal(x, y)
     # the setup family holds the restriction and the prolongation
     assert got[(0, False)][3] == got[(1, False)][3] + 2
+    # and the coarse sweeps are counted in a family of their own
+    assert got[(0, False)][4] > 0 and got[(1, False)][4] == 0
     for flat in (0, 1):
         for p, g in enumerate(got[(flat, False)][0]):
             assert np.abs(g - rec[p]).max() <= TOL_INTRA, (flat, p)
