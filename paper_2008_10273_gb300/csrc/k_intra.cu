@@ -131,7 +131,7 @@ __global__ void intra_sum_kernel(const __grid_constant__ IntraJobs J, uint32_t *
 __device__ __forceinline__ float plane_mean(const IntraPlane &P)
 {
     __shared__ float s_mean;
-    if (threadIdx.x == 0) s_mean = P.n > 0 ? (float)((double)(long long)*P.vsum / (double)P.n) : 0.f;
+    if (threadIdx.x == 0 && threadIdx.y == 0) s_mean = P.n > 0 ? (float)((double)(long long)*P.vsum / (double)P.n) : 0.f;
     __syncthreads();
     return s_mean;
 }
@@ -165,62 +165,86 @@ __global__ void intra_scatter_kernel(const __grid_constant__ IntraJobs J)
 }
 
 // ---- the coarse start ------------------------------------------------------
-// A two-level cascade for the starting iterate (a pixel per thread): coarse pixel (X, Y) of a
+// A two-level cascade for the starting iterate: coarse pixel (X, Y) of a
 // plane covers the fine pixels 2X .. 2X + 1 x 2Y .. 2Y + 1.  It is known
 // when one of them is, with the mean of their values; otherwise it starts
-// at the plane's mean mask value.  (Fine planes after the scatter; plane =
-// blockIdx.y.)
+// at the plane's mean mask value.  (Fine planes after the scatter, whose
+// row padding holds mask 0; plane = blockIdx.z.)  Thread (x, y) of the
+// 32 x 8 CTAs takes the coarse pixels 4 t .. 4 t + 3 of row Y (t the
+// thread's column), reading the eight fine mask bytes of each fine row at
+// once.
 __global__ void intra_restrict_kernel(const __grid_constant__ IntraJobs F, const __grid_constant__ IntraJobs C)
 {
-    const IntraPlane &Pf = F.p[blockIdx.y];
-    const IntraPlane &Pc = C.p[blockIdx.y];
+    const IntraPlane &Pf = F.p[blockIdx.z];
+    const IntraPlane &Pc = C.p[blockIdx.z];
     const float mean = plane_mean(Pf);
-    const int Wc = Pc.width, total = Pc.width * Pc.height;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-        const int Y = i / Wc, X = i - Y * Wc;
+    const int X4 = 4 * (blockIdx.x * blockDim.x + threadIdx.x), Y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (X4 >= Pc.width || Y >= Pc.height) return;
+    uint2 m[2];
+    for (int dy = 0; dy < 2; ++dy) {
+        const int y = 2 * Y + dy;
+        m[dy] = y < Pf.height ? __ldg(reinterpret_cast<const uint2 *>(Pf.mask + (size_t)y * Pf.pitch + 2 * X4))
+                              : make_uint2(0u, 0u);
+    }
+    float v[4];
+    uint32_t known = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
         float s = 0.f;
         int k = 0;
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
             for (int dx = 0; dx < 2; ++dx) {
-                const int x = 2 * X + dx, y = 2 * Y + dy;
-                if (x >= Pf.width || y >= Pf.height) continue;
-                const size_t o = (size_t)y * Pf.pitch + x;
-                if (Pf.mask[o]) {
-                    s += Pf.uh[0][o];
+                const int b = 2 * j + dx;  // byte of the row's eight
+                const uint32_t w = b < 4 ? m[dy].x : m[dy].y;
+                if ((w >> (8 * (b & 3))) & 0xffu) {
+                    s += __ldg(Pf.uh[0] + (size_t)(2 * Y + dy) * Pf.pitch + 2 * X4 + b);
                     ++k;
                 }
             }
-        const size_t oc = (size_t)Y * Pc.pitch + X;
-        Pc.uh[0][oc] = k ? s / (float)k : mean;
-        Pc.mask[oc] = k ? 1 : 0;
+        v[j] = k ? s / (float)k : mean;
+        known |= (k ? 1u : 0u) << (8 * j);
     }
+    const size_t oc = (size_t)Y * Pc.pitch + X4;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (X4 + j < Pc.width) {
+            Pc.uh[0][oc + j] = v[j];
+            Pc.mask[oc + j] = (known >> (8 * j)) & 1u;
+        }
 }
 
 // The unknown fine pixels from the coarse solution (the iterate buffer the
 // coarse control state names): bilinear between coarse cell centres (fine
 // x at coarse (x - 1/2) / 2), the edge cells replicated.  lo stays 0 (the
-// fill kernel's); the mask pixels keep their values.
+// fill kernel's); the mask pixels keep their values.  Thread (x, y) of the
+// 32 x 8 CTAs takes fine pixels 4 t .. 4 t + 3 of row y (t the thread's
+// column): one 4-byte mask load, then all their samples.
 __global__ void intra_prolong_kernel(const __grid_constant__ IntraJobs F, const __grid_constant__ IntraJobs C)
 {
-    const IntraPlane &Pf = F.p[blockIdx.y];
-    const IntraPlane &Pc = C.p[blockIdx.y];
-    const float *__restrict__ uc = Pc.uh[C.ctl->upar[blockIdx.y] & 1];
-    const int W = Pf.width, Wc = Pc.width, Hc = Pc.height, total = Pf.width * Pf.height;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-        const int y = i / W, x = i - y * W;
-        const size_t o = (size_t)y * Pf.pitch + x;
-        if (Pf.mask[o]) continue;
-        const float xs = 0.5f * (float)x - 0.25f, ys = 0.5f * (float)y - 0.25f;
-        const float fx = floorf(xs), fy = floorf(ys);
-        const float ax = xs - fx, ay = ys - fy;
-        const int x0 = (int)fx, y0 = (int)fy;
+    const IntraPlane &Pf = F.p[blockIdx.z];
+    const IntraPlane &Pc = C.p[blockIdx.z];
+    const int x4 = 4 * (blockIdx.x * blockDim.x + threadIdx.x), y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x4 >= Pf.width || y >= Pf.height) return;
+    const float *__restrict__ uc = Pc.uh[C.ctl->upar[blockIdx.z] & 1];
+    const int Wc = Pc.width, Hc = Pc.height;
+    const size_t o = (size_t)y * Pf.pitch + x4;
+    const uint32_t m = __ldg(reinterpret_cast<const uint32_t *>(Pf.mask + o));
+    const float ys = 0.5f * (float)y - 0.25f, fy = floorf(ys), ay = ys - fy;
+    const int y0 = (int)fy;
+    const int ya = min(max(y0, 0), Hc - 1), yb = min(max(y0 + 1, 0), Hc - 1);
+    const float *ra = uc + (size_t)ya * Pc.pitch, *rb = uc + (size_t)yb * Pc.pitch;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int x = x4 + j;
+        if (x >= Pf.width || ((m >> (8 * j)) & 0xffu)) continue;
+        const float xs = 0.5f * (float)x - 0.25f, fx = floorf(xs), ax = xs - fx;
+        const int x0 = (int)fx;
         const int xa = min(max(x0, 0), Wc - 1), xb = min(max(x0 + 1, 0), Wc - 1);
-        const int ya = min(max(y0, 0), Hc - 1), yb = min(max(y0 + 1, 0), Hc - 1);
-        const float *ra = uc + (size_t)ya * Pc.pitch, *rb = uc + (size_t)yb * Pc.pitch;
-        const float top = fmaf(ax, ra[xb] - ra[xa], ra[xa]), bot = fmaf(ax, rb[xb] - rb[xa], rb[xa]);
-        Pf.uh[0][o] = fmaf(ay, bot - top, top);
+        const float a0 = __ldg(ra + xa), a1 = __ldg(ra + xb), b0 = __ldg(rb + xa), b1 = __ldg(rb + xb);
+        const float top = fmaf(ax, a1 - a0, a0), bot = fmaf(ax, b1 - b0, b0);
+        Pf.uh[0][o + j] = fmaf(ay, bot - top, top);
     }
 }
 
@@ -927,17 +951,23 @@ cudaError_t launch_intra_init(IntraJobs &J, uint32_t *flags, cudaStream_t st, in
 
 cudaError_t launch_intra_restrict(const IntraJobs &F, const IntraJobs &C, cudaStream_t st)
 {
-    size_t px = 1;
-    for (int k = 0; k < C.n; ++k) px = std::max(px, (size_t)C.p[k].width * C.p[k].height);
-    intra_restrict_kernel<<<dim3((unsigned)std::min<size_t>((px + 255) / 256, 16384), F.n), 256, 0, st>>>(F, C);
+    int w = 1, h = 1;  // the largest coarse plane: 4 pixels a thread in x
+    for (int k = 0; k < C.n; ++k) {
+        w = std::max(w, C.p[k].width);
+        h = std::max(h, C.p[k].height);
+    }
+    intra_restrict_kernel<<<dim3(((w + 3) / 4 + 31) / 32, (h + 7) / 8, F.n), dim3(32, 8), 0, st>>>(F, C);
     return cudaGetLastError();
 }
 
 cudaError_t launch_intra_prolong(const IntraJobs &F, const IntraJobs &C, cudaStream_t st)
 {
-    size_t px = 1;
-    for (int k = 0; k < F.n; ++k) px = std::max(px, (size_t)F.p[k].width * F.p[k].height);
-    intra_prolong_kernel<<<dim3((unsigned)std::min<size_t>((px + 255) / 256, 16384), F.n), 256, 0, st>>>(F, C);
+    int w = 1, h = 1;  // the largest fine plane: 4 pixels a thread in x
+    for (int k = 0; k < F.n; ++k) {
+        w = std::max(w, F.p[k].width);
+        h = std::max(h, F.p[k].height);
+    }
+    intra_prolong_kernel<<<dim3(((w + 3) / 4 + 31) / 32, (h + 7) / 8, F.n), dim3(32, 8), 0, st>>>(F, C);
     return cudaGetLastError();
 }
 
